@@ -1,0 +1,170 @@
+"""Finite elements for the oracle: element matrices, global assembly, direct solve.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
+
+The paper's starting point is the assembled system K u = f of a finite-element
+discretisation; the local subdomain matrix K_i is obtained "by sub-assembling element
+matrices" (Sec. 2, Eq. psi_def context).  Element types (Sec. 4): linear elasticity and, as
+the scalar model problem of the first workload, the Laplace operator.
+
+Element conventions
+  * Q1 element on 2**dim nodes, local node a has reference position xi_a[d] = 2*bit_d(a) - 1
+    (lexicographic order, x fastest); 2-point Gauss rule per direction.
+  * Elasticity DOF order inside an element is (node a, component c) -> 3a + c; strains use
+    Voigt order [xx, yy, zz, yz, xz, xy] with engineering shears; isotropic D with
+    lambda = E nu / ((1+nu)(1-2nu)), mu = E / (2(1+nu)).
+
+Parity: pinned (closed-form 2D Laplace element, rigid-body null space, constant-strain
+energies, Poisson and elasticity patch tests) in ``tests/test_oracle_fem.py``.
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+GAUSS2 = np.array([-1.0, 1.0]) / np.sqrt(3.0)
+
+
+def q1_ref_nodes(dim: int) -> np.ndarray:
+    """Reference positions of the 2**dim lexicographically numbered Q1 nodes."""
+    return np.array([[2.0 * ((a >> d) & 1) - 1.0 for d in range(dim)] for a in range(2 ** dim)])
+
+
+def q1_grad_ref(dim: int, xi: np.ndarray) -> np.ndarray:
+    """dN_a/dxi_d at reference point xi, shape [2**dim, dim]; N_a = prod_d (1 + xi_a,d xi_d)/2."""
+    nodes = q1_ref_nodes(dim)
+    g = np.empty((2 ** dim, dim))
+    for a in range(2 ** dim):
+        for d in range(dim):
+            v = nodes[a, d] / 2.0
+            for e in range(dim):
+                if e != d:
+                    v *= (1.0 + nodes[a, e] * xi[e]) / 2.0
+            g[a, d] = v
+    return g
+
+
+def gauss_points(dim: int):
+    for pt in itertools.product(GAUSS2, repeat=dim):
+        yield np.array(pt), 1.0
+
+
+def element_laplace(X: np.ndarray, coef: float = 1.0) -> np.ndarray:
+    """K_e[a, b] = coef * int grad N_a . grad N_b over a Q1 element with node coordinates X."""
+    dim = X.shape[1]
+    K = np.zeros((2 ** dim, 2 ** dim))
+    for xi, w in gauss_points(dim):
+        G = q1_grad_ref(dim, xi)          # [nn, dim] in reference coords
+        J = X.T @ G                       # dx/dxi, [dim, dim]
+        detJ = np.linalg.det(J)
+        Gx = G @ np.linalg.inv(J)         # physical gradients [nn, dim]
+        K += coef * w * detJ * (Gx @ Gx.T)
+    return K
+
+
+def elasticity_D(E: float, nu: float) -> np.ndarray:
+    lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
+    mu = E / (2.0 * (1.0 + nu))
+    D = np.zeros((6, 6))
+    D[:3, :3] = lam
+    D[[0, 1, 2], [0, 1, 2]] += 2.0 * mu
+    D[[3, 4, 5], [3, 4, 5]] = mu
+    return D
+
+
+def elasticity_B(Gx: np.ndarray) -> np.ndarray:
+    """Strain-displacement matrix, Voigt [xx, yy, zz, yz, xz, xy], DOF order 3a + c."""
+    nn = Gx.shape[0]
+    B = np.zeros((6, 3 * nn))
+    for a in range(nn):
+        dx, dy, dz = Gx[a]
+        B[0, 3 * a + 0] = dx
+        B[1, 3 * a + 1] = dy
+        B[2, 3 * a + 2] = dz
+        B[3, 3 * a + 1] = dz
+        B[3, 3 * a + 2] = dy
+        B[4, 3 * a + 0] = dz
+        B[4, 3 * a + 2] = dx
+        B[5, 3 * a + 0] = dy
+        B[5, 3 * a + 1] = dx
+    return B
+
+
+def element_elasticity(X: np.ndarray, E: float, nu: float) -> np.ndarray:
+    """K_e = int B^T D B dV over a trilinear hex, 2x2x2 Gauss."""
+    D = elasticity_D(E, nu)
+    K = np.zeros((24, 24))
+    for xi, w in gauss_points(3):
+        G = q1_grad_ref(3, xi)
+        J = X.T @ G
+        detJ = np.linalg.det(J)
+        Gx = G @ np.linalg.inv(J)
+        B = elasticity_B(Gx)
+        K += w * detJ * (B.T @ D @ B)
+    return K
+
+
+def element_matrices(prob) -> np.ndarray:
+    """All element matrices of a Problem, [n_elems, ne, ne], each scaled by its coefficient.
+
+    Structured box meshes have congruent elements, so elements with identical geometry
+    reuse one unit-coefficient matrix (scaled by coef_e); this is exact, not an approximation.
+    """
+    X = prob.coords[prob.conn]                        # [nel, nn, dim]
+    shape_key = np.round(X - X[:, :1, :], 14).reshape(X.shape[0], -1)
+    uniq, inv = np.unique(shape_key, axis=0, return_inverse=True)
+    inv = inv.ravel()
+    unit = []
+    for u in range(uniq.shape[0]):
+        e = int(np.nonzero(inv == u)[0][0])
+        if prob.physics == 0:
+            unit.append(element_laplace(X[e], 1.0))
+        elif prob.physics == 1:
+            unit.append(element_elasticity(X[e], 1.0, prob.nu))
+        else:
+            raise NotImplementedError("physics")
+    unit = np.stack(unit)
+    return unit[inv] * prob.coef[:, None, None]
+
+
+def element_dofs(prob) -> np.ndarray:
+    """Global DOF ids (node * ndof + comp) of every element, [n_elems, nn * ndof]."""
+    nd = prob.dofs_per_node
+    return (prob.conn[:, :, None].astype(np.int64) * nd + np.arange(nd)[None, None, :]).reshape(
+        prob.n_elems, -1)
+
+
+def assemble(prob, Ke=None):
+    """Global stiffness over all DOFs (CSR).  K = sum_e P_e^T K_e P_e."""
+    if Ke is None:
+        Ke = element_matrices(prob)
+    ed = element_dofs(prob)
+    n = prob.n_nodes * prob.dofs_per_node
+    rows = np.repeat(ed, ed.shape[1], axis=1).ravel()
+    cols = np.tile(ed, (1, ed.shape[1])).ravel()
+    K = sp.coo_matrix((Ke.ravel(), (rows, cols)), shape=(n, n)).tocsr()
+    K.sum_duplicates()
+    return K
+
+
+def free_system(prob, K=None):
+    """K_ff, f_f with Dirichlet DOFs eliminated (zero or prescribed values lifted to the RHS)."""
+    if K is None:
+        K = assemble(prob)
+    free = prob.free
+    Kff = K[free][:, free].tocsc()
+    f = prob.f_full[free].copy()
+    if prob.dir_values is not None:
+        ud = prob.dir_values[~free]
+        f -= (K[free][:, ~free] @ ud)[:, None]
+    return Kff, f
+
+
+def direct_solve(prob, K=None):
+    """u = K_ff^{-1} f over the free DOFs (SuperLU), [n_free, nrhs]."""
+    Kff, f = free_system(prob, K)
+    lu = spla.splu(Kff)
+    return lu.solve(f)

@@ -1,0 +1,326 @@
+"""Oracle index analysis of one BDDC level (Sec. 2-3, Algorithm 1).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
+
+Algorithm 1 asks, per level, to divide the (pseudo-)mesh into subdomains, classify the
+interface into faces, edges and vertices, select corners, and -- for levels above the
+first -- build a pseudo-mesh whose "elements" are the subdomains and whose "nodes" are the
+corners, edges and faces.  The constraint matrices C_i hold one row per constraint: corner
+values and arithmetic averages over edges and faces (Sec. 2 after Eq. psi_def; Sec. 4).
+The coarse restriction R_Ci maps global coarse DOFs to the local ones (Sec. 2).
+
+The paper gives no rule for the classification or for the cited face-based corner
+selection; this oracle takes the following readings (the CUDA library takes the same):
+
+  * interface node: a node contained in >= 2 subdomains.
+  * glob: a maximal set of interface nodes with identical sharing sets, split into
+    components connected through shared (pseudo-)elements; globs are ordered by their
+    smallest node id.
+  * type: sharing set of size 2 -> face (3D) / edge (2D); size >= 3 -> vertex when the glob
+    is a single node, edge otherwise.
+  * corners are the vertex globs.  Per subdomain a rigid-body sufficiency test counts as
+    points the centroids of globs constrained in every component and the nodes whose DOFs
+    are all prescribed; scalar problems need one point, 2D elasticity two distinct points,
+    3D elasticity three non-collinear points.  A failing subdomain (ascending order)
+    promotes one of its interface nodes with all DOFs free to an extra corner: the smallest
+    id when it has no point, else the node farthest from the first point (one point) or
+    from the line through the first point and the point farthest from it; ties go to the
+    smaller id.  Promoted corners are appended after the regular globs.
+  * constraint rows: for every constrained glob and component with a free DOF on the glob,
+    one coarse DOF; its row averages (weight 1/count) that component over the glob's free
+    DOFs.  Coarse DOFs are numbered by (glob order, component).
+  * local DOF order of a subdomain: interior DOFs ascending by global id, then interface
+    DOFs ascending.  The global interface numbers the interface DOFs ascending.
+  * multiplicity weight of an interface DOF: 1 / |sharing set of its node|.
+  * pseudo-mesh of the next level: one pseudo-node per glob carrying coarse DOFs (in glob
+    order) with coordinates at the centroid of the glob's nodes that carry a free DOF; one
+    pseudo-element per subdomain whose DOFs are its coarse DOFs in ascending order.
+
+Parity: pinned by hand-counted structured sizes (interface and coarse counts) and by the
+partition-of-unity identity sum_i R_i^T D_i R_i = I in ``tests/test_oracle_maps.py``.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import Dict, List, Tuple
+
+import numpy as np
+
+VERTEX, EDGE, FACE = 0, 1, 2
+CORNERS, EDGES, FACES = 1, 2, 4
+
+
+@dataclasses.dataclass
+class LevelMesh:
+    """A (pseudo-)mesh: nodes with component DOFs, elements as node lists, a partition."""
+    dim: int
+    ncomp: int
+    coords: np.ndarray                 # [n_nodes, dim]
+    node_dofs: List[np.ndarray]        # per node: array of (comp, dof) pairs, dof = -1 prescribed
+    elem_nodes: List[np.ndarray]       # per element: node ids (ascending not required)
+    elem_dofs: List[np.ndarray]        # per element: its matrix's DOF ids (-1 = prescribed)
+    part: np.ndarray                   # [n_elems] -> subdomain
+    n_sub: int
+    n_dof: int                         # number of free DOFs of this level
+
+
+@dataclasses.dataclass
+class Glob:
+    nodes: np.ndarray
+    subs: Tuple[int, ...]
+    kind: int
+    promoted: bool = False
+
+
+@dataclasses.dataclass
+class LevelMaps:
+    mesh: LevelMesh
+    node_subs: List[Tuple[int, ...]]
+    globs: List[Glob]
+    coarse_glob: np.ndarray            # [n_coarse] glob index of every coarse DOF
+    coarse_comp: np.ndarray            # [n_coarse] component of every coarse DOF
+    iface_dofs: np.ndarray             # global interface: free DOF ids ascending
+    sub_elems: List[np.ndarray]
+    sub_dofs: List[np.ndarray]         # local order: interior then interface (global DOF ids)
+    sub_nI: List[int]
+    sub_iface: List[np.ndarray]        # positions of the local interface DOFs in iface_dofs
+    sub_coarse: List[np.ndarray]       # R_Ci: global coarse ids, ascending
+    sub_C: List[np.ndarray]            # dense C_i [n_c, n_local]
+    sub_wmult: List[np.ndarray]        # multiplicity weights of the local interface DOFs
+    n_promoted: int
+
+    @property
+    def n_coarse(self) -> int:
+        return int(self.coarse_glob.shape[0])
+
+
+def mesh_level1(prob) -> LevelMesh:
+    """Level-1 mesh from a Problem: DOF node*ndof+comp, free DOFs numbered ascending."""
+    nd = prob.dofs_per_node
+    free = prob.dirichlet == 0
+    dof_id = np.full(prob.n_nodes * nd, -1, dtype=np.int64)
+    dof_id[free] = np.arange(int(free.sum()))
+    node_dofs = [np.array([(c, dof_id[p * nd + c]) for c in range(nd)], dtype=np.int64)
+                 for p in range(prob.n_nodes)]
+    elem_nodes = [np.asarray(r, dtype=np.int64) for r in prob.conn]
+    elem_dofs = [dof_id[(r[:, None].astype(np.int64) * nd + np.arange(nd)).ravel()] for r in prob.conn]
+    return LevelMesh(prob.dim, nd, prob.coords, node_dofs, elem_nodes, elem_dofs,
+                     np.asarray(prob.parts[0]), int(prob.n_parts[0]), int(free.sum()))
+
+
+def _find(parent, x):
+    while parent[x] != x:
+        parent[x] = parent[parent[x]]
+        x = parent[x]
+    return x
+
+
+def analyze(mesh: LevelMesh, constraints: int, all_corners: bool = False) -> LevelMaps:
+    """Interface classification, corner selection and coarse numbering of one level.
+
+    ``all_corners`` makes every interface node a glob of its own (a corner); the coarse
+    space then spans the whole interface, the special case in which BDDC is exact.
+    """
+    n_nodes = mesh.coords.shape[0]
+    nsub = mesh.n_sub
+    sub_elems = [[] for _ in range(nsub)]
+    for e, s in enumerate(mesh.part):
+        sub_elems[int(s)].append(e)
+    sub_elems = [np.array(v, dtype=np.int64) for v in sub_elems]
+
+    # sharing sets
+    subsets = [set() for _ in range(n_nodes)]
+    for e, s in enumerate(mesh.part):
+        for p in mesh.elem_nodes[e]:
+            subsets[int(p)].add(int(s))
+    node_subs = [tuple(sorted(x)) for x in subsets]
+    iface = np.array([len(x) >= 2 for x in node_subs])
+
+    # globs: equal sharing sets, connected through elements
+    parent = np.arange(n_nodes)
+    for e in range(len(mesh.elem_nodes)):
+        by_set: Dict[Tuple[int, ...], int] = {}
+        for p in mesh.elem_nodes[e]:
+            p = int(p)
+            if not iface[p]:
+                continue
+            q = by_set.setdefault(node_subs[p], p)
+            if q != p:
+                a, b = _find(parent, p), _find(parent, q)
+                if a != b:
+                    parent[max(a, b)] = min(a, b)
+    comp: Dict[int, List[int]] = {}
+    for p in np.nonzero(iface)[0]:
+        comp.setdefault(int(p) if all_corners else _find(parent, int(p)), []).append(int(p))
+    globs = []
+    for root in sorted(comp, key=lambda r: min(comp[r])):
+        nodes = np.array(sorted(comp[root]), dtype=np.int64)
+        subs = node_subs[int(nodes[0])]
+        if all_corners:
+            kind = VERTEX
+        elif len(subs) == 2:
+            kind = FACE if mesh.dim == 3 else EDGE
+        else:
+            kind = VERTEX if nodes.size == 1 else EDGE
+        globs.append(Glob(nodes, subs, kind))
+
+    def glob_is_constrained(g: Glob) -> bool:
+        if g.promoted:
+            return True
+        return bool(constraints & {VERTEX: CORNERS, EDGE: EDGES, FACE: FACES}[g.kind])
+
+    def glob_free_comps(g: Glob):
+        comps = []
+        for c in range(mesh.ncomp):
+            if any(int(d) >= 0 for p in g.nodes for cc, d in mesh.node_dofs[int(p)] if cc == c):
+                comps.append(c)
+        return comps
+
+    def glob_centroid(g: Glob):
+        pts = [p for p in g.nodes if any(int(d) >= 0 for _, d in mesh.node_dofs[int(p)])]
+        if not pts:
+            pts = list(g.nodes)
+        return mesh.coords[np.array(pts)].sum(axis=0) / len(pts)
+
+    # corner selection with the rigid-body sufficiency test
+    sub_nodes = []
+    for s in range(nsub):
+        ns = set()
+        for e in sub_elems[s]:
+            ns.update(int(p) for p in mesh.elem_nodes[e])
+        sub_nodes.append(np.array(sorted(ns), dtype=np.int64))
+    n_promoted = 0
+    corner_nodes = set()
+    for g in globs:
+        if g.kind == VERTEX and glob_is_constrained(g):
+            corner_nodes.add(int(g.nodes[0]))
+    diam = np.linalg.norm(mesh.coords.max(axis=0) - mesh.coords.min(axis=0))
+    tol = 1e-12 * diam * diam
+
+    def points_of(s):
+        pts = []
+        for g in globs:
+            if s in g.subs and glob_is_constrained(g):
+                if len(glob_free_comps(g)) == mesh.ncomp:
+                    pts.append(glob_centroid(g))
+        for p in sub_nodes[s]:
+            nd = mesh.node_dofs[int(p)]
+            if len(nd) and all(int(d) < 0 for _, d in nd):
+                pts.append(mesh.coords[int(p)])
+        return np.array(pts).reshape(-1, mesh.dim)
+
+    def sufficient(pts):
+        if mesh.ncomp == 1:
+            return pts.shape[0] >= 1
+        if pts.shape[0] == 0:
+            return False
+        d0 = np.linalg.norm(pts - pts[0], axis=1)
+        j = int(np.argmax(d0))
+        if mesh.dim == 2:
+            return d0[j] * d0[j] > tol
+        if d0[j] * d0[j] <= tol:
+            return False
+        u = pts[j] - pts[0]
+        cr = np.linalg.norm(np.cross(pts - pts[0], u), axis=1)
+        return cr.max() > tol
+
+    for s in range(nsub):
+        for _ in range(16):
+            pts = points_of(s)
+            if sufficient(pts):
+                break
+            cand = [int(p) for p in sub_nodes[s] if iface[p] and int(p) not in corner_nodes
+                    and len(mesh.node_dofs[int(p)]) == mesh.ncomp
+                    and all(int(d) >= 0 for _, d in mesh.node_dofs[int(p)])]
+            if not cand:
+                raise ValueError(f"subdomain {s}: no candidate corner")
+            cand = np.array(cand, dtype=np.int64)
+            X = mesh.coords[cand]
+            if pts.shape[0] == 0:
+                pick = int(cand[0])
+            else:
+                d0 = np.linalg.norm(pts - pts[0], axis=1)
+                j = int(np.argmax(d0))
+                if d0[j] * d0[j] <= tol or mesh.dim == 2:
+                    dist = np.linalg.norm(X - pts[0], axis=1)
+                else:
+                    u = (pts[j] - pts[0]) / d0[j]
+                    dist = np.linalg.norm(np.cross(X - pts[0], u), axis=1)
+                pick = int(cand[int(np.argmax(dist))])   # argmax returns the first maximum
+            globs.append(Glob(np.array([pick], dtype=np.int64), node_subs[pick], VERTEX, True))
+            corner_nodes.add(pick)
+            n_promoted += 1
+        else:
+            raise ValueError(f"subdomain {s}: corner selection did not terminate")
+
+    # coarse DOFs
+    cg, cc = [], []
+    for gi, g in enumerate(globs):
+        if glob_is_constrained(g):
+            for c in glob_free_comps(g):
+                cg.append(gi)
+                cc.append(c)
+    coarse_glob = np.array(cg, dtype=np.int64)
+    coarse_comp = np.array(cc, dtype=np.int64)
+
+    # global interface numbering
+    iface_dofs = sorted(int(d) for p in np.nonzero(iface)[0] for _, d in mesh.node_dofs[int(p)] if d >= 0)
+    iface_dofs = np.array(iface_dofs, dtype=np.int64)
+    iface_pos = {d: k for k, d in enumerate(iface_dofs)}
+
+    sub_dofs, sub_nI, sub_iface, sub_coarse, sub_C, sub_w = [], [], [], [], [], []
+    for s in range(nsub):
+        interior, inter = [], []
+        for p in sub_nodes[s]:
+            for _, d in mesh.node_dofs[int(p)]:
+                if d >= 0:
+                    (inter if iface[p] else interior).append(int(d))
+        interior.sort()
+        inter.sort()
+        dofs = np.array(interior + inter, dtype=np.int64)
+        loc = {d: k for k, d in enumerate(dofs)}
+        sub_dofs.append(dofs)
+        sub_nI.append(len(interior))
+        sub_iface.append(np.array([iface_pos[d] for d in inter], dtype=np.int64))
+        mult = {}
+        for p in sub_nodes[s]:
+            if iface[p]:
+                for _, d in mesh.node_dofs[int(p)]:
+                    if d >= 0:
+                        mult[int(d)] = 1.0 / len(node_subs[int(p)])
+        sub_w.append(np.array([mult[d] for d in inter]))
+        rows = [k for k in range(coarse_glob.shape[0]) if s in globs[coarse_glob[k]].subs]
+        sub_coarse.append(np.array(rows, dtype=np.int64))
+        C = np.zeros((len(rows), dofs.size))
+        for r, k in enumerate(rows):
+            g = globs[coarse_glob[k]]
+            c = coarse_comp[k]
+            ds = [int(d) for p in g.nodes for cc2, d in mesh.node_dofs[int(p)] if cc2 == c and d >= 0]
+            for d in ds:
+                C[r, loc[d]] = 1.0 / len(ds)
+        sub_C.append(C)
+
+    return LevelMaps(mesh, node_subs, globs, coarse_glob, coarse_comp, iface_dofs, sub_elems,
+                     sub_dofs, sub_nI, sub_iface, sub_coarse, sub_C, sub_w, n_promoted)
+
+
+def next_level_mesh(maps: LevelMaps, part_next: np.ndarray, n_sub_next: int) -> LevelMesh:
+    """Pseudo-mesh of level l+1 (Algorithm 1): subdomains -> 'elements', globs -> 'nodes'."""
+    mesh = maps.mesh
+    carrying = sorted(set(int(g) for g in maps.coarse_glob))
+    node_of_glob = {g: q for q, g in enumerate(carrying)}
+    coords = []
+    node_dofs = []
+    for g in carrying:
+        glob = maps.globs[g]
+        pts = [p for p in glob.nodes if any(int(d) >= 0 for _, d in mesh.node_dofs[int(p)])]
+        coords.append(mesh.coords[np.array(pts)].sum(axis=0) / len(pts))
+        ks = np.nonzero(maps.coarse_glob == g)[0]
+        node_dofs.append(np.array([(int(maps.coarse_comp[k]), int(k)) for k in ks], dtype=np.int64))
+    elem_nodes, elem_dofs = [], []
+    for s in range(mesh.n_sub):
+        gl = sorted(set(int(maps.coarse_glob[k]) for k in maps.sub_coarse[s]))
+        elem_nodes.append(np.array([node_of_glob[g] for g in gl], dtype=np.int64))
+        elem_dofs.append(maps.sub_coarse[s].copy())
+    return LevelMesh(mesh.dim, mesh.ncomp, np.array(coords), node_dofs, elem_nodes, elem_dofs,
+                     np.asarray(part_next), int(n_sub_next), maps.n_coarse)

@@ -1,0 +1,351 @@
+"""Seeded synthetic inputs: structured meshes, coefficients, boundary masks, loads, partitions.
+
+This module is shared by the tests, the oracle-side checks and the benchmark.  It holds
+none of the solver's arithmetic: no element integrals, no assembly, no interface analysis.
+It only lays out the problem data that the paper's workloads are made of (Sec. 4):
+
+* ``box_mesh``         -- structured Q1 meshes of the unit square / cube.  Node ids are
+                          lexicographic with x fastest; element ids likewise; the local node
+                          order inside an element is lexicographic too (a = ix + 2 iy + 4 iz).
+* ``box_mesh_q2``      -- the 27-node Q2 hex mesh used by the Taylor--Hood cavity problem.
+* ``loguniform_coef``  -- per-element Young's modulus E = 10**(3 U), U ~ U[0,1) (seeded).
+* masks                -- clamped face x = 0, or the whole boundary.
+* ``box_body_load``    -- nodal load of a constant body force on axis-aligned box elements
+                          (each node of a box element receives vol / 2**dim of the force).
+* partitions           -- cubic blocks, seeded Lloyd k-means, and block groupings for the
+                          higher levels (Sec. 3, Algorithm 1: the division into subdomains
+                          is an input of the solver).
+
+All random numbers come from ``numpy.random.default_rng(seed)`` (PCG64) and are drawn on
+the host once; both the CUDA path and the oracle receive the same arrays.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional
+
+import numpy as np
+
+POISSON = 0
+ELASTICITY = 1
+STOKES = 2
+
+CORNERS = 1
+EDGES = 2
+FACES = 4
+
+
+@dataclasses.dataclass
+class Problem:
+    """One synthetic workload, in the layout of the C ABI's ``bddc_mesh``/``bddc_partition``."""
+    name: str
+    dim: int
+    nodes_per_elem: int
+    dofs_per_node: int
+    physics: int
+    coords: np.ndarray          # [n_nodes, dim] float64
+    conn: np.ndarray            # [n_elems, nodes_per_elem] int32
+    coef: np.ndarray            # [n_elems] float64
+    nu: float
+    dirichlet: np.ndarray       # [n_nodes * dofs_per_node] uint8, 1 = prescribed
+    f_full: np.ndarray          # [n_nodes * dofs_per_node, nrhs] float64 nodal loads
+    parts: List[np.ndarray]     # parts[0]: elem -> level-1 sub; parts[l]: level-l sub -> level-(l+1) sub
+    n_parts: List[int]
+    n_levels: int
+    constraints: int
+    dir_values: Optional[np.ndarray] = None
+
+    @property
+    def n_nodes(self) -> int:
+        return self.coords.shape[0]
+
+    @property
+    def n_elems(self) -> int:
+        return self.conn.shape[0]
+
+    @property
+    def free(self) -> np.ndarray:
+        return self.dirichlet == 0
+
+    @property
+    def n_free(self) -> int:
+        return int(self.free.sum())
+
+    @property
+    def f(self) -> np.ndarray:
+        """Loads restricted to the free DOFs (ascending global DOF order), [n_free, nrhs]."""
+        return np.ascontiguousarray(self.f_full[self.free])
+
+
+# ----------------------------------------------------------------------------- meshes
+def box_mesh(dim: int, n: int, length: float = 1.0):
+    """Structured Q1 mesh of [0, length]^dim with n elements per side."""
+    h = length / n
+    m = n + 1
+    if dim == 2:
+        iy, ix = np.meshgrid(np.arange(m), np.arange(m), indexing="ij")
+        coords = np.stack([ix.ravel() * h, iy.ravel() * h], axis=1)
+        ey, ex = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+        base = (ey * m + ex).ravel()
+        offs = np.array([0, 1, m, m + 1])
+    elif dim == 3:
+        iz, iy, ix = np.meshgrid(np.arange(m), np.arange(m), np.arange(m), indexing="ij")
+        coords = np.stack([ix.ravel() * h, iy.ravel() * h, iz.ravel() * h], axis=1)
+        ez, ey, ex = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+        base = ((ez * m + ey) * m + ex).ravel()
+        offs = np.array([0, 1, m, m + 1, m * m, m * m + 1, m * m + m, m * m + m + 1])
+    else:
+        raise ValueError("dim must be 2 or 3")
+    conn = (base[:, None] + offs[None, :]).astype(np.int32)
+    return coords.astype(np.float64), conn
+
+
+def box_mesh_q2(n: int, length: float = 1.0):
+    """Structured 27-node Q2 hex mesh of [0, length]^3 with n elements per side.
+
+    Nodes form the (2n+1)^3 lattice, lexicographic with x fastest; local node order is
+    lexicographic a = ix + 3 iy + 9 iz with ix, iy, iz in {0, 1, 2}.  The Q1 pressure
+    nodes of the Taylor--Hood pair are the lattice points with all-even indices.
+    """
+    m = 2 * n + 1
+    h = length / (2 * n)
+    iz, iy, ix = np.meshgrid(np.arange(m), np.arange(m), np.arange(m), indexing="ij")
+    coords = np.stack([ix.ravel() * h, iy.ravel() * h, iz.ravel() * h], axis=1)
+    ez, ey, ex = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    base = ((2 * ez * m + 2 * ey) * m + 2 * ex).ravel()
+    offs = np.array([(kz * m + ky) * m + kx for kz in range(3) for ky in range(3) for kx in range(3)])
+    conn = (base[:, None] + offs[None, :]).astype(np.int32)
+    return coords.astype(np.float64), conn
+
+
+def loguniform_coef(n_elems: int, seed: int, decades: float = 3.0) -> np.ndarray:
+    """E_e = 10**(decades * U_e), U_e ~ U[0, 1) from default_rng(seed)."""
+    u = np.random.default_rng(seed).random(n_elems)
+    return 10.0 ** (decades * u)
+
+
+def mask_face_x0(coords: np.ndarray, ndof: int) -> np.ndarray:
+    on = coords[:, 0] == 0.0
+    return np.repeat(on, ndof).astype(np.uint8)
+
+
+def mask_boundary(coords: np.ndarray, ndof: int, length: float = 1.0) -> np.ndarray:
+    on = np.any((coords == 0.0) | (coords == length), axis=1)
+    return np.repeat(on, ndof).astype(np.uint8)
+
+
+def box_body_load(coords: np.ndarray, conn: np.ndarray, ndof: int, b) -> np.ndarray:
+    """Nodal load of a constant body force b on axis-aligned box elements.
+
+    The node count of a box element is 2**dim; each node receives vol/2**dim * b.
+    """
+    dim = coords.shape[1]
+    b = np.asarray(b, dtype=np.float64).reshape(ndof)
+    lo = coords[conn[:, 0]]
+    hi = coords[conn[:, -1]]
+    vol = np.prod(hi - lo, axis=1)
+    share = vol / (2 ** dim)
+    f = np.zeros(coords.shape[0] * ndof)
+    nodes = conn.ravel()
+    w = np.repeat(share, conn.shape[1])
+    for c in range(ndof):
+        np.add.at(f, nodes * ndof + c, w * b[c])
+    return f
+
+
+# ----------------------------------------------------------------------------- partitions
+def cubic_partition(dim: int, n: int, nsub: int) -> np.ndarray:
+    """Element -> subdomain for nsub^dim cubic blocks of (n/nsub)^dim elements.
+
+    Subdomain ids are lexicographic in the block grid, x fastest.
+    """
+    if n % nsub:
+        raise ValueError("n must be a multiple of nsub")
+    s = n // nsub
+    idx = np.arange(n)
+    if dim == 2:
+        ey, ex = np.meshgrid(idx, idx, indexing="ij")
+        p = (ey // s) * nsub + ex // s
+    else:
+        ez, ey, ex = np.meshgrid(idx, idx, idx, indexing="ij")
+        p = ((ez // s) * nsub + ey // s) * nsub + ex // s
+    return p.ravel().astype(np.int32)
+
+
+def block_grouping(dim: int, nsub: int, group: int) -> np.ndarray:
+    """Level-l subdomain (lexicographic in an nsub^dim grid) -> level-(l+1) block of group^dim."""
+    ng = nsub // group
+    idx = np.arange(nsub)
+    if dim == 2:
+        sy, sx = np.meshgrid(idx, idx, indexing="ij")
+        p = (sy // group) * ng + sx // group
+    else:
+        sz, sy, sx = np.meshgrid(idx, idx, idx, indexing="ij")
+        p = ((sz // group) * ng + sy // group) * ng + sx // group
+    return p.ravel().astype(np.int32)
+
+
+def kmeans(points: np.ndarray, k: int, seed: int, iters: int = 5) -> np.ndarray:
+    """Lloyd's k-means: default_rng(seed) uniform initial centres inside the points' bounding
+    box, exactly ``iters`` update steps, nearest centre with ties to the lower index."""
+    rng = np.random.default_rng(seed)
+    lo, hi = points.min(axis=0), points.max(axis=0)
+    centres = lo + (hi - lo) * rng.random((k, points.shape[1]))
+    lab = _nearest(points, centres)
+    for _ in range(iters):
+        for j in range(k):
+            sel = lab == j
+            if sel.any():
+                centres[j] = points[sel].mean(axis=0)
+        lab = _nearest(points, centres)
+    return lab.astype(np.int32)
+
+
+def _nearest(points, centres, chunk=65536):
+    out = np.empty(points.shape[0], dtype=np.int64)
+    for s in range(0, points.shape[0], chunk):
+        p = points[s:s + chunk]
+        d = ((p[:, None, :] - centres[None, :, :]) ** 2).sum(axis=2)
+        out[s:s + chunk] = np.argmin(d, axis=1)
+    return out
+
+
+def face_connected_fix(conn: np.ndarray, part: np.ndarray, dim: int) -> np.ndarray:
+    """Make every subdomain face-connected: each face-connected component other than the
+    largest one (ties: the one holding the smallest element id) moves to the face-adjacent
+    subdomain with the smallest id.  Repeats until stable; empty labels are then compacted.
+
+    Only structured Q1 meshes (lexicographic local order) are handled.
+    """
+    part = part.copy()
+    nel = conn.shape[0]
+    if dim == 2:
+        faces = [(0, 1), (2, 3), (0, 2), (1, 3)]
+    else:
+        faces = [(0, 1, 2, 3), (4, 5, 6, 7), (0, 1, 4, 5), (2, 3, 6, 7), (0, 2, 4, 6), (1, 3, 5, 7)]
+    keys = {}
+    nbr = [[] for _ in range(nel)]
+    for e in range(nel):
+        for f in faces:
+            key = tuple(sorted(int(conn[e, a]) for a in f))
+            o = keys.get(key)
+            if o is None:
+                keys[key] = e
+            else:
+                nbr[e].append(o)
+                nbr[o].append(e)
+    for _ in range(100):
+        changed = False
+        seen = np.full(nel, -1, dtype=np.int64)
+        comps = {}
+        for e in range(nel):
+            if seen[e] >= 0:
+                continue
+            stack = [e]
+            seen[e] = e
+            members = []
+            while stack:
+                x = stack.pop()
+                members.append(x)
+                for y in nbr[x]:
+                    if seen[y] < 0 and part[y] == part[e]:
+                        seen[y] = e
+                        stack.append(y)
+            comps.setdefault(int(part[e]), []).append(sorted(members))
+        for p, cl in comps.items():
+            if len(cl) < 2:
+                continue
+            cl.sort(key=lambda m: (-len(m), m[0]))
+            for m in cl[1:]:
+                adj = sorted({int(part[y]) for x in m for y in nbr[x] if part[y] != p})
+                if adj:
+                    part[np.array(m)] = adj[0]
+                    changed = True
+        if not changed:
+            break
+    _, part = np.unique(part, return_inverse=True)
+    return part.astype(np.int32)
+
+
+# ----------------------------------------------------------------------------- configurations
+def poisson2d(n: int = 32, nsub: int = 4) -> Problem:
+    """-Laplace u = 1 on the unit square, Q1, homogeneous Dirichlet, nsub^2 square subdomains,
+    corner constraints only, two levels."""
+    coords, conn = box_mesh(2, n)
+    dirichlet = mask_boundary(coords, 1)
+    f = box_body_load(coords, conn, 1, [1.0])[:, None]
+    return Problem(
+        name=f"poisson2d_{n}_{nsub}x{nsub}", dim=2, nodes_per_elem=4, dofs_per_node=1,
+        physics=POISSON, coords=coords, conn=conn, coef=np.ones(conn.shape[0]), nu=0.0,
+        dirichlet=dirichlet, f_full=f, parts=[cubic_partition(2, n, nsub)], n_parts=[nsub * nsub],
+        n_levels=2, constraints=CORNERS)
+
+
+def elasticity3d(n: int, nsub: int, seed: int, nrhs: int = 1, group: int = 0,
+                 constraints: int = CORNERS | EDGES | FACES, nu: float = 0.3) -> Problem:
+    """Linear elasticity on the unit cube, Q1 hexes n^3, clamped at x = 0, gravity (0,0,-1),
+    E_e log-uniform in [1, 1e3] from default_rng(seed), nsub^3 cubic subdomains.
+
+    ``group`` > 0 adds a level grouping group^3 level-1 subdomains per level-2 subdomain.
+    Load cases beyond the first add N(0,1)/sqrt(n_free) noise on the free DOFs drawn from
+    default_rng(seed + k) for load case k (k = 0 is also perturbed when nrhs > 1).
+    """
+    coords, conn = box_mesh(3, n)
+    coef = loguniform_coef(conn.shape[0], seed)
+    dirichlet = mask_face_x0(coords, 3)
+    g = box_body_load(coords, conn, 3, [0.0, 0.0, -1.0])
+    f = np.repeat(g[:, None], nrhs, axis=1)
+    if nrhs > 1:
+        free = dirichlet == 0
+        nf = int(free.sum())
+        for k in range(nrhs):
+            noise = np.random.default_rng(seed + k).standard_normal(nf) / math.sqrt(nf)
+            f[free, k] += noise
+    parts = [cubic_partition(3, n, nsub)]
+    n_parts = [nsub ** 3]
+    levels = 2
+    if group:
+        parts.append(block_grouping(3, nsub, group))
+        n_parts.append((nsub // group) ** 3)
+        levels = 3
+    return Problem(
+        name=f"elasticity3d_{n}_{nsub}", dim=3, nodes_per_elem=8, dofs_per_node=3,
+        physics=ELASTICITY, coords=coords, conn=conn, coef=coef, nu=nu, dirichlet=dirichlet,
+        f_full=f, parts=parts, n_parts=n_parts, n_levels=levels, constraints=constraints)
+
+
+def elasticity3d_kmeans(n: int, nsub: int, ngroup: int, seed: int, seed2: int) -> Problem:
+    """Elasticity as ``elasticity3d`` with a seeded k-means split of element centroids into
+    nsub subdomains (made face-connected), grouped by k-means of subdomain centroids into
+    ngroup level-2 subdomains; three levels."""
+    coords, conn = box_mesh(3, n)
+    coef = loguniform_coef(conn.shape[0], seed)
+    dirichlet = mask_face_x0(coords, 3)
+    g = box_body_load(coords, conn, 3, [0.0, 0.0, -1.0])
+    cent = coords[conn].mean(axis=1)
+    p1 = kmeans(cent, nsub, seed)
+    p1 = face_connected_fix(conn, p1, 3)
+    ns = int(p1.max()) + 1
+    scent = np.stack([np.bincount(p1, weights=cent[:, d], minlength=ns) for d in range(3)], axis=1)
+    scent /= np.bincount(p1, minlength=ns)[:, None]
+    p2 = kmeans(scent, ngroup, seed2)
+    _, p2 = np.unique(p2, return_inverse=True)
+    return Problem(
+        name=f"elasticity3d_kmeans_{n}_{ns}_{ngroup}", dim=3, nodes_per_elem=8, dofs_per_node=3,
+        physics=ELASTICITY, coords=coords, conn=conn, coef=coef, nu=0.3, dirichlet=dirichlet,
+        f_full=g[:, None], parts=[p1, p2.astype(np.int32)], n_parts=[ns, int(p2.max()) + 1],
+        n_levels=3, constraints=CORNERS | EDGES | FACES)
+
+
+def config(name: str) -> Problem:
+    """The named workloads: the paper's problem classes (Sec. 4) at synthetic sizes."""
+    if name == "poisson2d_32":
+        return poisson2d(32, 4)
+    if name == "elasticity3d_48":
+        return elasticity3d(48, 4, seed=2)
+    if name == "elasticity3d_96_kmeans":
+        return elasticity3d_kmeans(96, 512, 8, seed=3, seed2=33)
+    if name == "elasticity3d_64_16rhs":
+        return elasticity3d(64, 8, seed=5, nrhs=16)
+    raise KeyError(name)

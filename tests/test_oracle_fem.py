@@ -1,0 +1,97 @@
+"""Pins of the oracle's finite elements against closed forms and patch tests."""
+import numpy as np
+import pytest
+
+from oracle import fem
+from paper_1201_5991_gb300 import meshgen
+
+
+def test_q1_laplace_rectangle_closed_form():
+    # Bilinear element on [0,a]x[0,b], lexicographic nodes (0,0),(a,0),(0,b),(a,b).
+    # Textbook closed form: K = (b/a)/6 * Kx + (a/b)/6 * Ky with
+    # Kx = [[2,-2,1,-1],[-2,2,-1,1],[1,-1,2,-2],[-1,1,-2,2]] (x-derivative part) and
+    # Ky = [[2,1,-2,-1],[1,2,-1,-2],[-2,-1,2,1],[-1,-2,1,2]] (y-derivative part).
+    a, b = 0.5, 2.0
+    X = np.array([[0, 0], [a, 0], [0, b], [a, b]], dtype=float)
+    Kx = np.array([[2, -2, 1, -1], [-2, 2, -1, 1], [1, -1, 2, -2], [-1, 1, -2, 2]], float)
+    Ky = np.array([[2, 1, -2, -1], [1, 2, -1, -2], [-2, -1, 2, 1], [-1, -2, 1, 2]], float)
+    ref = (b / a) / 6.0 * Kx + (a / b) / 6.0 * Ky
+    np.testing.assert_allclose(fem.element_laplace(X), ref, rtol=0, atol=1e-14)
+    # the unit square reduces to (1/6)[[4,-1,-1,-2],...]
+    K1 = fem.element_laplace(np.array([[0, 0], [1, 0], [0, 1], [1, 1]], float))
+    np.testing.assert_allclose(K1[0], np.array([4, -1, -1, -2]) / 6.0, atol=1e-15)
+
+
+def _hex(a=1.0, b=1.0, c=1.0):
+    return np.array([[(i & 1) * a, ((i >> 1) & 1) * b, ((i >> 2) & 1) * c] for i in range(8)], float)
+
+
+def test_q1_elasticity_rigid_null_space():
+    X = _hex(0.5, 1.0, 2.0)
+    K = fem.element_elasticity(X, 3.0, 0.3)
+    assert np.allclose(K, K.T, atol=1e-13)
+    ev = np.linalg.eigvalsh(K)
+    assert np.sum(np.abs(ev) < 1e-10 * ev.max()) == 6
+    assert ev.min() > -1e-12 * ev.max()
+    # explicit rigid motions: translations and infinitesimal rotations omega x x
+    for t in np.eye(3):
+        u = np.tile(t, 8)
+        assert np.linalg.norm(K @ u) < 1e-12
+    for w in np.eye(3):
+        u = np.cross(w, X).ravel()
+        assert np.linalg.norm(K @ u) < 1e-12
+
+
+@pytest.mark.parametrize("case", ["uniaxial", "shear"])
+def test_q1_elasticity_constant_strain_energy(case):
+    # u = G x gives a constant strain; energy = vol * 0.5 * eps:sigma exactly (trilinear
+    # interpolation is exact for linear fields, 2x2x2 Gauss exact for constants).
+    E, nu = 1.0, 0.3
+    lam = 0.3 / (1.3 * 0.4)          # E nu / ((1+nu)(1-2nu)) with E=1, nu=0.3
+    mu = 1.0 / 2.6                   # E / (2(1+nu))
+    dims = (0.5, 1.0, 2.0)
+    X = _hex(*dims)
+    vol = np.prod(dims)
+    G = np.zeros((3, 3))
+    if case == "uniaxial":
+        G[0, 0] = 1.0                # eps_xx = 1 -> density (lam + 2 mu)/2
+        dens = 0.5 * (lam + 2 * mu)
+    else:
+        G[0, 1] = 1.0                # u_x = y -> gamma_xy = 1 -> density mu/2
+        dens = 0.5 * mu
+    u = (X @ G.T).ravel()
+    K = fem.element_elasticity(X, E, nu)
+    np.testing.assert_allclose(0.5 * u @ K @ u, dens * vol, rtol=1e-13)
+
+
+def test_poisson_patch_bilinear_exact():
+    # u = 1 + 2x + 3y + 4xy is bilinear and harmonic; with Dirichlet data u and f = 0 the
+    # Q1 solution equals u at every node.
+    p = meshgen.poisson2d(8, 2)
+    x, y = p.coords[:, 0], p.coords[:, 1]
+    uex = 1 + 2 * x + 3 * y + 4 * x * y
+    p.f_full = np.zeros_like(p.f_full)
+    p.dir_values = uex.copy()
+    u = fem.direct_solve(p)[:, 0]
+    np.testing.assert_allclose(u, uex[p.free], atol=1e-12)
+
+
+def test_elasticity_patch_linear_exact():
+    # Homogeneous material, f = 0, u = a + B x prescribed on the whole boundary: the
+    # interior nodes reproduce the linear field exactly (patch test).
+    p = meshgen.elasticity3d(4, 2, seed=0)
+    p.coef = np.full(p.n_elems, 2.5)
+    p.dirichlet = meshgen.mask_boundary(p.coords, 3)
+    rng = np.random.default_rng(1)
+    a, B = rng.standard_normal(3), rng.standard_normal((3, 3))
+    uex = (a[None, :] + p.coords @ B.T).ravel()
+    p.f_full = np.zeros_like(p.f_full)
+    p.dir_values = uex
+    u = fem.direct_solve(p)[:, 0]
+    np.testing.assert_allclose(u, uex[p.free], atol=1e-12)
+
+
+def test_body_load_sums_to_total_force():
+    p = meshgen.elasticity3d(6, 2, seed=0)
+    tot = p.f_full[:, 0].reshape(-1, 3).sum(axis=0)
+    np.testing.assert_allclose(tot, [0, 0, -1.0], atol=1e-14)   # unit cube, b = (0,0,-1)
