@@ -1,0 +1,426 @@
+#!/usr/bin/env python
+"""Benchmark of the multilevel BDDC hot path: time to a 1e-8 relative residual.
+
+One step = the whole path on one synthetic problem: set-up (index analysis, element
+matrices, sub-assembly, batched factorisation, coarse basis, coarse matrix, coarsest
+factorisation) followed by the PCG solve to ||r|| / ||g|| <= 1e-8 and interior recovery.
+Workload: 3D linear elasticity, 48^3 trilinear hexes (345,744 free DOFs), clamped at x = 0,
+gravity load, per-element E = 10^(3U) (seed 2), nu = 0.3, 4^3 cubic subdomains of 12^3,
+corner + edge + face-average constraints, two-level BDDC.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+The default arm reports the mixed-precision form (FP32 factors and preconditioner, FP64
+Krylov, FP64 Schur operator via refinement, FP64 coarsest level) as `value`, and the plain
+FP64 form beside it.  `--impl reference` times the CPU oracle on a bounded sample.
+Under torchrun every rank solves its own replica (the path is not sharded across GPUs).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DOF/s and time-to-1e-8 rel residual, mixed-prec batched vs plain FP64, 1×GB300"
+UNIT = "DOF/s"
+WORKLOADS = {
+    "elasticity3d_48": "3D elasticity, 48^3 Q1 hexes, 345,744 free DOFs, 64 cubic subdomains of 12^3, "
+                       "corners+edges+faces, two-level BDDC, PCG to 1e-8",
+    "elasticity3d_24": "3D elasticity, 24^3 Q1 hexes, 8 cubic subdomains of 12^3 (profiling case), "
+                       "corners+edges+faces, two-level BDDC, PCG to 1e-8",
+}
+WORKLOAD = "elasticity3d_48"
+TOL = 1e-8
+
+
+def workload_config(prob, extra=None):
+    cfg = {
+        "workload": WORKLOADS[WORKLOAD],
+        "n_free": int(prob.n_free),
+        "n_subdomains": int(prob.n_parts[0]),
+        "levels": int(prob.n_levels),
+        "tol": TOL,
+        "l2": "inputs larger than L2 (factors >= 6.7 GB) and a 256 MB L2 flush between steps",
+        "mesh_inputs": "host arrays (the index analysis of the set-up runs on the host); rhs resident on device",
+    }
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), float(pk.get("bf16_tflops", 1896.2)), "measured"
+    except Exception:
+        return 6800.0, 1900.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def traffic_per_launch():
+    """DRAM bytes per launch of the streaming sweep from the committed ncu summary, or None
+    when the kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "trsv_sweep_traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+        src = open(os.path.join(ROOT, "paper_1201_5991_gb300", "csrc", "dense.cu"), "rb").read()
+        if hashlib.sha256(src).hexdigest() != rec.get("dense_cu_sha256"):
+            return None
+        return float(rec["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+# ----------------------------------------------------------------------------- CPU oracle sample
+def oracle_sample(prob, iterations: int):
+    """Time the FP64 oracle on a bounded sample and extrapolate to the whole solve.
+
+    Sample: the oracle's full index analysis; sub-assembly and set-up (Cholesky of K_II,
+    LU of the saddle-point matrix, coarse basis) of 2 of the subdomains; one Krylov
+    iteration's subdomain solves (Schur apply + preconditioner) for the same 2 subdomains.
+    Estimate = analysis + n_sub * setup_per_sub + iterations * n_sub * iter_per_sub.
+    """
+    import numpy as np
+    import scipy.linalg as sla
+
+    from oracle import fem
+    from oracle import maps as om
+    from oracle.bddc import _local_matrices
+
+    t0 = time.perf_counter()
+    mesh = om.mesh_level1(prob)
+    mp = om.analyze(mesh, prob.constraints)
+    t_analysis = time.perf_counter() - t0
+    Ke = fem.element_matrices(prob)
+    sample = [0, prob.n_parts[0] - 1]
+    sub_maps = om.LevelMaps(**{**mp.__dict__})
+    sub_maps.sub_dofs = [mp.sub_dofs[s] for s in sample]
+    sub_maps.sub_elems = [mp.sub_elems[s] for s in sample]
+    mesh_s = om.LevelMesh(**{**mesh.__dict__, "n_sub": len(sample)})
+    t1 = time.perf_counter()
+    K = _local_matrices(mesh_s, sub_maps, Ke)
+    facts = []
+    for k, s in enumerate(sample):
+        nI = mp.sub_nI[s]
+        Ks = K[k]
+        C = mp.sub_C[s]
+        n, nc = Ks.shape[0], C.shape[0]
+        kii = sla.cho_factor(Ks[:nI, :nI], lower=True)
+        Sd = np.zeros((n + nc, n + nc))
+        Sd[:n, :n] = Ks
+        Sd[:n, n:] = C.T
+        Sd[n:, :n] = C
+        lu = sla.lu_factor(Sd)
+        rhs = np.zeros((n + nc, nc))
+        rhs[n:] = np.eye(nc)
+        sla.lu_solve(lu, rhs)
+        facts.append((kii, lu, Ks, nI, n, nc))
+    t_setup = (time.perf_counter() - t1) / len(sample)
+    t2 = time.perf_counter()
+    for kii, lu, Ks, nI, n, nc in facts:
+        x = np.ones(n - nI)
+        w = sla.cho_solve(kii, Ks[:nI, nI:] @ x)
+        _ = Ks[nI:, nI:] @ x - Ks[nI:, :nI] @ w
+        r = np.zeros(n + nc)
+        r[nI:n] = 1.0
+        sla.lu_solve(lu, r)
+    t_iter = (time.perf_counter() - t2) / len(sample)
+    ns = prob.n_parts[0]
+    est = t_analysis + ns * t_setup + iterations * ns * t_iter
+    sample_s = time.perf_counter() - t0
+    desc = (f"index analysis of all {ns} subdomains + set-up of {len(sample)} of {ns} subdomains + one "
+            f"iteration's subdomain solves for the same {len(sample)}, extrapolated to {ns} subdomains x "
+            f"{iterations} PCG iterations ({sample_s:.1f} s of CPU work)")
+    return est, desc
+
+
+def cpu_cores():
+    return os.cpu_count() or 1
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_gpu(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_1201_5991_gb300 import capi, meshgen
+    from paper_1201_5991_gb300.solver import BddcSolver
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    prob = meshgen.config(WORKLOAD)
+    f = torch.tensor(prob.f[:, 0], dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    L = capi.lib()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def one_step(precision, profile=0):
+        s = BddcSolver(prob, precision=precision, stream=stream, profile=profile)
+        u = s.solve(f, tol=TOL)
+        return s, u
+
+    def timed(precision, steps, warmup, profile=0, clocks=False):
+        for _ in range(warmup):
+            s, u = one_step(precision)
+            del s, u
+        torch.cuda.synchronize()
+        barrier()
+        sampler = ClockSampler(local_rank) if clocks else None
+        if sampler:
+            sampler.start()
+        times, stats = [], []
+        launches0 = L.bddc_kernel_launches()
+        prof = [0.0, 0, 0.0]
+        for _ in range(steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s, u = one_step(precision, profile)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            st = s.stats()
+            stats.append(st)
+            prof[0] += st.prof_ms[capi.PROF_TRSV]
+            prof[1] += st.prof_launches[capi.PROF_TRSV]
+            prof[2] += st.prof_bytes[capi.PROF_TRSV]
+            del s, u
+        launches = (L.bddc_kernel_launches() - launches0) / max(steps, 1)
+        torch.cuda.synchronize()
+        barrier()
+        clk = sampler.stop() if sampler else None
+        ms = sum(times) / len(times)
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, stats, launches, prof, clk
+
+    ms, stats, launches, prof, clk = timed("mixed", args.steps, args.warmup, profile=1, clocks=True)
+    value = prob.n_free * world / (ms * 1e-3)
+    st0 = stats[-1]
+
+    # plain FP64 form, same workload (fewer steps: its set-up is FP64-ALU bound)
+    pk = max(1, min(args.steps, args.plain_steps))
+    if args.no_plain:
+        ms64, st64 = None, None
+    else:
+        ms64, stats64, _, _, _ = timed("fp64", pk, 1)
+        st64 = stats64[-1]
+
+    # end to end through the public host-buffer entry point
+    fh = np.ascontiguousarray(prob.f[:, 0])
+    e2e_times = []
+    for _ in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s = BddcSolver(prob, precision="mixed", stream=stream)
+        u = s.solve_host(fh, tol=TOL)
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+        del s
+    e2e_s = sum(e2e_times) / len(e2e_times)
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    mesh_bytes = prob.coords.nbytes + prob.conn.nbytes + prob.coef.nbytes + prob.dirichlet.nbytes
+
+    hbm, _, peak_kind = load_peaks()
+    achieved = prof[2] / (prof[0] * 1e-3) / 1e9 if prof[0] > 0 else 0.0
+    traffic = traffic_per_launch()
+    roofline = {
+        "kernel": "k_trsv_fwd/k_trsv_bwd<float> (streaming triangular sweeps)",
+        "bound": "hbm",
+        "achieved": round(achieved, 1),
+        "peak": hbm,
+        "peak_kind": peak_kind,
+        "unit": "GB/s",
+        "frac": round(achieved / hbm, 4),
+        "traffic": traffic,
+        "launches_per_step": prof[1] / max(args.steps, 1),
+        "algorithmic_bytes_per_launch": prof[2] / max(prof[1], 1),
+        "avg_launch_ms": prof[0] / max(prof[1], 1),
+        "share_of_step": round(prof[0] / args.steps / ms, 4) if ms > 0 else None,
+    }
+
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        est, desc = oracle_sample(prob, st64.iterations if st64 else st0.iterations)
+        cpu = {"value": prob.n_free / est, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": desc,
+               "est_time_to_solution_s": est}
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "mixed-f32/f64",
+        "data": "synthetic",
+        "config": workload_config(prob, {"precision": "mixed (FP32 factors, FP64 Krylov and Schur operator)",
+                                         "replicas": world}),
+        "time_to_1e-8_ms": ms,
+        "iterations": st0.iterations,
+        "rel_residual": st0.rel_residual,
+        "setup_ms": st0.analysis_ms + st0.factor_ms,
+        "solve_ms": st0.solve_ms,
+        "refine_steps": st0.refine_steps,
+        "kappa_estimate": st0.lambda_max / st0.lambda_min if st0.lambda_min > 0 else None,
+        "plain_fp64": None if st64 is None else {
+            "value": prob.n_free * world / (ms64 * 1e-3), "ms_per_step": ms64, "steps": pk,
+            "iterations": st64.iterations, "setup_ms": st64.analysis_ms + st64.factor_ms,
+            "solve_ms": st64.solve_ms, "speedup_mixed_vs_plain": ms64 / ms},
+        "e2e": {"value": prob.n_free * world / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": int(prob.n_free * 8 + mesh_bytes), "d2h_bytes_per_step": int(prob.n_free * 8)},
+        "gpu_launches": int(round(launches)),
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_1201_5991_gb300 import meshgen
+    prob = meshgen.config(WORKLOAD)
+    iters = args.ref_iterations
+    if args.warmup > 0:
+        oracle_sample(prob, iters)          # one untimed sample warms BLAS / allocators
+    times = []
+    desc = ""
+    for _ in range(args.steps):
+        est, desc = oracle_sample(prob, iters)
+        times.append(est)
+    est = sum(times) / len(times)
+    value = prob.n_free / est
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": est * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(prob, {"precision": "FP64 oracle (dense LAPACK per subdomain)"}),
+        "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--plain-steps", type=int, default=2)
+    ap.add_argument("--ref-iterations", type=int, default=51)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 form (profiling runs)")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
+    args = ap.parse_args()
+    global WORKLOAD
+    WORKLOAD = args.workload
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_gpu(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

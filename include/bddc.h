@@ -1,0 +1,237 @@
+/*
+ * bddc.h -- C ABI of the GB300 multilevel BDDC library (libbddc_gb300.so).
+ *
+ * The library implements the data-parallel hot path of multilevel BDDC as described in
+ * Sistek, Mandel, Sousedik, Burda, "Parallel implementation of Multilevel BDDC":
+ * the reduced interface problem S u = g solved by a Krylov method (Sec. 2), with the
+ * BDDC preconditioner of two and more levels set up by Algorithm 1 and applied by
+ * Algorithm 2 (Sec. 3).  All numerical work runs in CUDA kernels on one GPU; the host
+ * side of the library performs the index analysis (interface classification, corner
+ * selection, coarse numbering) and orchestrates the launches.
+ *
+ * Conventions shared by every entry point
+ *   - Return value: BDDC_OK (0) or a negative BDDC_ERR_* code.  Nothing aborts and no
+ *     kernel traps; bddc_last_error() returns a message for the calling thread.
+ *   - "host" pointers are read during the call only and stay owned by the caller.
+ *     "device" pointers are CUDA device memory owned by the caller.
+ *   - A handle owns all device memory it allocates (factors, maps, work vectors) until
+ *     bddc_free().  All work is enqueued on the CUDA stream given to bddc_setup(); calls
+ *     returning a status synchronise that stream before returning.
+ *   - Free-DOF numbering: the DOF of (node p, component c) is p*dofs_per_node + c; DOFs
+ *     marked in `dirichlet` are removed and the remaining ones are numbered ascending.
+ *     Vectors of several right-hand sides are stored column after column
+ *     ([nrhs][n_free], column k at offset k*n_free).
+ *   - A handle is not thread-safe; distinct handles may be used from distinct threads.
+ */
+#ifndef BDDC_GB300_H
+#define BDDC_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BDDC_MAX_LEVELS 6
+
+/* status codes */
+#define BDDC_OK 0
+#define BDDC_ERR_INVALID (-1)       /* bad argument, mesh or partition (empty subdomain, id out of range, ...) */
+#define BDDC_ERR_BREAKDOWN (-2)     /* non-positive pivot in a subdomain factorisation (stats: level, subdomain) */
+#define BDDC_ERR_NOT_CONVERGED (-3) /* Krylov iteration cap reached; x holds the last iterate */
+#define BDDC_ERR_NAN (-4)           /* NaN/Inf met in a reduction */
+#define BDDC_ERR_CUDA (-5)          /* CUDA runtime error */
+#define BDDC_ERR_OOM (-6)           /* device allocation failed */
+#define BDDC_ERR_TIMEOUT (-7)       /* a bounded device-side wait gave up */
+
+/* physics */
+#define BDDC_POISSON 0      /* -div(coef grad u) = f, 1 DOF per node */
+#define BDDC_ELASTICITY 1   /* isotropic linear elasticity, coef = Young's modulus, nu = Poisson ratio */
+
+/* constraint classes (Sec. 2: corners, averages over edges and faces) */
+#define BDDC_CORNERS 1u
+#define BDDC_EDGES 2u
+#define BDDC_FACES 4u
+
+/* precision of the subdomain factorisations and the preconditioner */
+#define BDDC_PREC_FP64 0    /* plain: every factor and solve in FP64 */
+#define BDDC_PREC_MIXED 1   /* FP32 factors and preconditioner; FP64 Krylov, FP64 Schur operator, FP64 coarsest level */
+
+/* interface weights D_i of E_i^T = D_i R_i (Sec. 2) */
+#define BDDC_WEIGHTS_STIFFNESS 0     /* D_i(j) = K_i(jj) / sum_k K_k(jj) */
+#define BDDC_WEIGHTS_MULTIPLICITY 1  /* D_i(j) = 1 / (number of subdomains sharing the node) */
+
+typedef struct bddc_handle_s* bddc_handle;
+
+/* Mesh of the first level (host pointers). Element-local node order is lexicographic:
+ * local node a sits at reference position xi_d = 2*((a >> d) & 1) - 1 (Q1: 2**dim nodes). */
+typedef struct {
+  int dim;                  /* 2 or 3 */
+  int nodes_per_elem;       /* 4 (2D Q1) or 8 (3D Q1) */
+  int dofs_per_node;        /* 1 (Poisson) or dim (elasticity) */
+  int physics;              /* BDDC_POISSON | BDDC_ELASTICITY */
+  int64_t n_nodes;
+  int64_t n_elems;
+  const double* coords;     /* [n_nodes * dim] */
+  const int32_t* conn;      /* [n_elems * nodes_per_elem] node ids */
+  const double* coef;       /* [n_elems] coefficient (Young's modulus / conductivity), > 0 */
+  double nu;                /* Poisson ratio (elasticity) */
+  const uint8_t* dirichlet; /* [n_nodes * dofs_per_node], 1 = prescribed (value 0) */
+} bddc_mesh;
+
+/* Division into subdomains per level (Algorithm 1 takes it as an input: ParMETIS/METIS in
+ * the paper).  part[0][e] = level-1 subdomain of element e; part[l][s] = level-(l+1)
+ * subdomain of level-l subdomain s.  n_levels counts the coarsest direct solve as a level
+ * (two-level BDDC: n_levels = 2, one partition array). */
+typedef struct {
+  int n_levels;                              /* 2 .. BDDC_MAX_LEVELS */
+  const int32_t* part[BDDC_MAX_LEVELS - 1];  /* host arrays */
+  int64_t n_parts[BDDC_MAX_LEVELS - 1];      /* number of subdomains of level l+1 */
+} bddc_partition;
+
+typedef struct {
+  int precision;            /* BDDC_PREC_FP64 | BDDC_PREC_MIXED */
+  int weights;              /* BDDC_WEIGHTS_* */
+  unsigned all_corners;     /* bit (l-1) set: every interface node of level l is a corner */
+  int maxit;                /* Krylov iteration cap */
+  int refine_steps;         /* mixed: FP64 refinement steps of each interior solve in S; 0 = automatic */
+  int flexible;             /* 1: Polak-Ribiere beta; 0: Fletcher-Reeves; -1: automatic (mixed -> 1) */
+  int use_graph;            /* 1: capture one Krylov iteration in a CUDA graph */
+  int verbose;
+  int profile;              /* 1: time kernel classes with CUDA events (bddc_stats.prof_*) */
+} bddc_opts;
+
+/* kernel classes timed when bddc_opts.profile = 1 */
+#define BDDC_PROF_TRSV 0    /* streaming triangular sweeps (Schur operator and preconditioner) */
+#define BDDC_PROF_FACTOR 1  /* one step of the batched blocked Cholesky (diagonal, panel, update) */
+#define BDDC_PROF_SPMV 2    /* FP64 sparse products with K_i */
+#define BDDC_PROF_CLASSES 4
+
+typedef struct {
+  int iterations;           /* Krylov iterations of the last solve (max over right-hand sides) */
+  int converged;            /* 1 when every right-hand side met the tolerance */
+  double rel_residual;      /* max over right-hand sides of ||g - S u|| / ||g|| at exit */
+  double lambda_min, lambda_max;  /* Lanczos estimate from PCG (first right-hand side) */
+  int n_levels;
+  int64_t n_sub[BDDC_MAX_LEVELS];     /* subdomains of BDDC level l (index l-1) */
+  int64_t n_dof[BDDC_MAX_LEVELS];     /* free DOFs of the level's problem */
+  int64_t n_iface[BDDC_MAX_LEVELS];   /* interface DOFs of the level */
+  int64_t n_coarse[BDDC_MAX_LEVELS];  /* coarse DOFs of the level */
+  int64_t n_promoted[BDDC_MAX_LEVELS];/* corners added by the rigid-body test */
+  int breakdown_level, breakdown_sub; /* set with BDDC_ERR_BREAKDOWN */
+  int refine_steps;                   /* refinement steps in use (mixed) */
+  double analysis_ms, factor_ms, solve_ms;
+  int64_t factor_bytes;               /* device bytes held by factors */
+  double prof_ms[BDDC_PROF_CLASSES];          /* summed CUDA-event durations per class */
+  int64_t prof_launches[BDDC_PROF_CLASSES];   /* launches per class */
+  double prof_bytes[BDDC_PROF_CLASSES];       /* algorithmic bytes moved (TRSV, SPMV) */
+  double prof_flops[BDDC_PROF_CLASSES];       /* algorithmic flops (FACTOR) */
+} bddc_stats;
+
+/* Index maps of one level, library-owned, valid until bddc_free (for bit-exact checks).
+ * Subdomain-local DOF order: interior DOFs ascending by level DOF id, then interface DOFs
+ * ascending.  C_i is stored row by row: the rows of subdomain s are
+ * sub_coarse_ptr[s] .. sub_coarse_ptr[s+1]-1, row r has entries c_ptr[r] .. c_ptr[r+1]-1
+ * with local column c_col[] (position in the local order) and value c_val[]. */
+typedef struct {
+  int64_t n_dof, n_sub, n_iface, n_coarse, n_globs, n_promoted;
+  const int64_t* iface_dofs;       /* [n_iface] level DOF ids, ascending */
+  const int64_t* sub_dof_ptr;      /* [n_sub+1] */
+  const int64_t* sub_dofs;         /* [sub_dof_ptr[n_sub]] level DOF ids in local order */
+  const int64_t* sub_nI;           /* [n_sub] interior count */
+  const int64_t* sub_iface;        /* [sub_dof_ptr[n_sub]] position in iface_dofs of each local DOF, -1 interior */
+  const double* sub_wmult;         /* [sub_dof_ptr[n_sub]] multiplicity weight, 0 interior */
+  const int64_t* sub_coarse_ptr;   /* [n_sub+1] */
+  const int64_t* sub_coarse;       /* R_Ci: global coarse ids, ascending */
+  const int64_t* c_ptr;            /* [sub_coarse_ptr[n_sub]+1] */
+  const int64_t* c_col;
+  const double* c_val;
+  const int64_t* glob_ptr;         /* [n_globs+1] */
+  const int64_t* glob_nodes;       /* nodes of every glob, ascending */
+  const int32_t* glob_kind;        /* 0 vertex, 1 edge, 2 face */
+  const int32_t* glob_promoted;    /* 1 = corner added by the rigid-body test */
+  const int64_t* coarse_glob;      /* [n_coarse] */
+  const int32_t* coarse_comp;      /* [n_coarse] */
+} bddc_level_maps;
+
+/* Fill *opts with the defaults (mixed precision, stiffness weights, maxit 500, automatic
+ * refinement, automatic beta, graph on). */
+void bddc_default_opts(bddc_opts* opts);
+
+/* Index analysis only (Algorithm 1 without the numerical steps): interface classification
+ * into faces/edges/vertices, corner selection, constraint rows and coarse numbering on every
+ * level, pseudo-meshes of the levels above the first.  Makes no CUDA call, so it runs on a
+ * machine without a GPU; the handle then serves bddc_get_maps and bddc_free only.
+ * mesh, part: host.  constraints: BDDC_CORNERS|BDDC_EDGES|BDDC_FACES.  opts may be NULL.
+ * Errors: BDDC_ERR_INVALID for an inconsistent mesh/partition. */
+int bddc_analyze(const bddc_mesh* mesh, const bddc_partition* part, unsigned constraints,
+                 const bddc_opts* opts, bddc_handle* out);
+
+/* Full set-up, Algorithm 1: index analysis, then on the GPU per level: element matrices,
+ * sub-assembly of K_i (Sec. 2), factorisation of the augmented constrained Neumann matrix
+ * K_i + rho C_i^T C_i with the constraint rows (yields the interior factor, Eq. psi_def's
+ * coarse basis Psi_i and K_Ci = -Lambda_i), assembly of the next level, and the FP64
+ * factorisation of the coarsest matrix K_C.  stream: a cudaStream_t (NULL = default).
+ * Errors: INVALID, BREAKDOWN (stats via bddc_get_stats), CUDA, OOM. */
+int bddc_setup(const bddc_mesh* mesh, const bddc_partition* part, unsigned constraints,
+               const bddc_opts* opts, void* stream, bddc_handle* out);
+
+/* Replace the element coefficients (host [n_elems]) and redo the numerical set-up, keeping
+ * the index analysis.  Errors as bddc_setup. */
+int bddc_update_coef(bddc_handle h, const double* coef);
+
+/* Solve K u = f for nrhs right-hand sides (Sec. 2): condensed right-hand side
+ * g = f_G - sum R_i^T K_GI K_II^{-1} f_I,i, PCG on S u_G = g preconditioned by Algorithm 2,
+ * stop when ||r|| / ||g|| <= tol (confirmed on the true residual), then interior recovery
+ * u_I = K_II^{-1} (f_I - K_IG u_G).  rhs: device [nrhs][n_free] FP64.  x: device
+ * [nrhs][n_free] FP64, output (the initial guess is zero).  stats: host, may be NULL.
+ * Errors: NOT_CONVERGED (x holds the last iterate), NAN, CUDA, TIMEOUT. */
+int bddc_solve(bddc_handle h, const double* rhs, double* x, int nrhs, double tol, bddc_stats* stats);
+
+/* Same as bddc_solve with host buffers: copies rhs to the device and x back (end to end). */
+int bddc_solve_host(bddc_handle h, const double* rhs_host, double* x_host, int nrhs, double tol,
+                    bddc_stats* stats);
+
+/* One application of the multilevel BDDC preconditioner, Algorithm 2, to interface
+ * residuals.  r, z: device [nrhs][n_iface] FP64 in the order of bddc_level_maps.iface_dofs
+ * of level 1.  Errors: INVALID, CUDA. */
+int bddc_apply_precond(bddc_handle h, const double* r, double* z, int nrhs);
+
+/* The reduced interface operator of Sec. 2, y = S x = sum_i R_i^T (K_GG - K_GI K_II^{-1} K_IG) R_i x,
+ * computed with discrete Dirichlet problems.  x, y: device [nrhs][n_iface] FP64. */
+int bddc_apply_schur(bddc_handle h, const double* x, double* y, int nrhs);
+
+/* Adjoint gradient of a scalar J(u) with u = K(coef)^{-1} f: solves K lambda_k = dJdu_k with
+ * the same factors (K is symmetric), then grad_rhs = lambda and
+ * grad_coef[e] = - sum_k lambda_k,e^T (dK_e/dcoef_e) u_k,e with dK_e/dcoef_e = K_e / coef_e.
+ * dJdu, u: device [nrhs][n_free].  grad_coef: device [n_elems] or NULL.  grad_rhs: device
+ * [nrhs][n_free] or NULL.  tol: Krylov tolerance of the adjoint solve.
+ * Errors as bddc_solve. */
+int bddc_grad(bddc_handle h, const double* dJdu, const double* u, int nrhs, double tol,
+              double* grad_coef, double* grad_rhs);
+
+/* Index maps of BDDC level `level` (1-based).  Errors: INVALID. */
+int bddc_get_maps(bddc_handle h, int level, bddc_level_maps* out);
+
+/* Copy the statistics of the last set-up / solve into *out. */
+int bddc_get_stats(bddc_handle h, bddc_stats* out);
+
+/* Sizes of the problem: number of free DOFs of level 1 and of its interface. */
+int bddc_sizes(bddc_handle h, int64_t* n_free, int64_t* n_iface);
+
+/* Release every resource of the handle (safe on NULL). */
+void bddc_free(bddc_handle h);
+
+/* Number of kernels the library has launched in this process (all handles). */
+int64_t bddc_kernel_launches(void);
+
+/* Reset the per-class timers of bddc_stats.prof_* on a handle. */
+int bddc_reset_profile(bddc_handle h);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char* bddc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BDDC_GB300_H */

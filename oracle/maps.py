@@ -18,7 +18,8 @@ selection; this oracle takes the following readings (the CUDA library takes the 
     smallest node id.
   * type: sharing set of size 2 -> face (3D) / edge (2D); size >= 3 -> vertex when the glob
     is a single node, edge otherwise.
-  * corners are the vertex globs.  Per subdomain a rigid-body sufficiency test counts as
+  * corners are the vertex globs.  Per subdomain with interface nodes a rigid-body
+    sufficiency test counts as
     points the centroids of globs constrained in every component and the nodes whose DOFs
     are all prescribed; scalar problems need one point, 2D elasticity two distinct points,
     3D elasticity three non-collinear points.  A failing subdomain (ascending order)
@@ -108,6 +109,11 @@ def mesh_level1(prob) -> LevelMesh:
                      np.asarray(prob.parts[0]), int(prob.n_parts[0]), int(free.sum()))
 
 
+def _seqmean(X: np.ndarray) -> np.ndarray:
+    """Mean of the rows of X summed one after another in row order."""
+    return np.cumsum(X, axis=0)[-1] / X.shape[0]
+
+
 def _find(parent, x):
     while parent[x] != x:
         parent[x] = parent[parent[x]]
@@ -180,7 +186,7 @@ def analyze(mesh: LevelMesh, constraints: int, all_corners: bool = False) -> Lev
         pts = [p for p in g.nodes if any(int(d) >= 0 for _, d in mesh.node_dofs[int(p)])]
         if not pts:
             pts = list(g.nodes)
-        return mesh.coords[np.array(pts)].sum(axis=0) / len(pts)
+        return _seqmean(mesh.coords[np.array(pts)])
 
     # corner selection with the rigid-body sufficiency test
     sub_nodes = []
@@ -225,6 +231,8 @@ def analyze(mesh: LevelMesh, constraints: int, all_corners: bool = False) -> Lev
         return cr.max() > tol
 
     for s in range(nsub):
+        if not any(iface[p] for p in sub_nodes[s]):
+            continue          # a subdomain without interface is the whole (connected) problem
         for _ in range(16):
             pts = points_of(s)
             if sufficient(pts):
@@ -314,7 +322,7 @@ def next_level_mesh(maps: LevelMaps, part_next: np.ndarray, n_sub_next: int) -> 
     for g in carrying:
         glob = maps.globs[g]
         pts = [p for p in glob.nodes if any(int(d) >= 0 for _, d in mesh.node_dofs[int(p)])]
-        coords.append(mesh.coords[np.array(pts)].sum(axis=0) / len(pts))
+        coords.append(_seqmean(mesh.coords[np.array(pts)]))
         ks = np.nonzero(maps.coarse_glob == g)[0]
         node_dofs.append(np.array([(int(maps.coarse_comp[k]), int(k)) for k in ks], dtype=np.int64))
     elem_nodes, elem_dofs = [], []

@@ -1,0 +1,480 @@
+// Host-side index analysis of one BDDC level; see analysis.h.
+//
+// Readings of the paper taken here (Algorithm 1 names the steps but not their rules):
+//   * interface node: contained in >= 2 subdomains;
+//   * glob: maximal set of interface nodes with identical sharing sets, split into
+//     components connected through shared (pseudo-)elements; globs ordered by smallest node;
+//   * kind: 2 sharing subdomains -> face (3D) / edge (2D); >= 3 -> vertex if the glob is one
+//     node, edge otherwise;
+//   * corners = vertex globs, plus nodes promoted by a rigid-body sufficiency test (a scalar
+//     problem needs one constrained point, 2D elasticity two distinct points, 3D elasticity
+//     three non-collinear points; constrained points are centroids of globs constrained in
+//     every component and nodes whose DOFs are all prescribed);
+//   * one coarse DOF per constrained glob and component present on it; its constraint row
+//     is the arithmetic average of that component over the glob's free DOFs (Sec. 2, Sec. 4).
+#include "analysis.h"
+
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <unordered_map>
+
+namespace bddc {
+
+namespace {
+
+int64_t find_root(std::vector<int64_t>& parent, int64_t x) {
+  while (parent[x] != x) {
+    parent[x] = parent[parent[x]];
+    x = parent[x];
+  }
+  return x;
+}
+
+bool same_set(const LevelMaps& m, int64_t a, int64_t b) {
+  int64_t la = m.node_sub_ptr[a + 1] - m.node_sub_ptr[a];
+  int64_t lb = m.node_sub_ptr[b + 1] - m.node_sub_ptr[b];
+  if (la != lb) return false;
+  return std::equal(m.node_sub.begin() + m.node_sub_ptr[a], m.node_sub.begin() + m.node_sub_ptr[a + 1],
+                    m.node_sub.begin() + m.node_sub_ptr[b]);
+}
+
+struct Pt {
+  double x[3];
+};
+
+double dist2(const Pt& a, const Pt& b, int dim) {
+  double s = 0.0;
+  for (int d = 0; d < dim; ++d) {
+    double t = a.x[d] - b.x[d];
+    s = s + t * t;
+  }
+  return s;
+}
+
+// |(p - o) x u| for 3D points
+double cross_norm(const Pt& p, const Pt& o, const double* u) {
+  double a0 = p.x[0] - o.x[0], a1 = p.x[1] - o.x[1], a2 = p.x[2] - o.x[2];
+  double c0 = a1 * u[2] - a2 * u[1];
+  double c1 = a2 * u[0] - a0 * u[2];
+  double c2 = a0 * u[1] - a1 * u[0];
+  return std::sqrt(c0 * c0 + c1 * c1 + c2 * c2);
+}
+
+}  // namespace
+
+bool analyze_level(const LevelMesh& mesh, unsigned constraints, bool all_corners, LevelMaps* out,
+                   std::string* err) {
+  LevelMaps& m = *out;
+  m = LevelMaps();
+  const int64_t nn = mesh.n_nodes, ne = mesh.n_elems, ns = mesh.n_sub;
+  const int dim = mesh.dim, nc = mesh.ncomp;
+  if (ns <= 0 || ne <= 0) {
+    *err = "empty mesh or partition";
+    return false;
+  }
+  // subdomain -> elements (ascending)
+  m.sub_elem_ptr.assign(ns + 1, 0);
+  for (int64_t e = 0; e < ne; ++e) {
+    int32_t s = mesh.part[e];
+    if (s < 0 || s >= ns) {
+      *err = "partition id out of range at element " + std::to_string(e);
+      return false;
+    }
+    m.sub_elem_ptr[s + 1]++;
+  }
+  for (int64_t s = 0; s < ns; ++s) {
+    if (m.sub_elem_ptr[s + 1] == 0) {
+      *err = "empty subdomain " + std::to_string(s);
+      return false;
+    }
+    m.sub_elem_ptr[s + 1] += m.sub_elem_ptr[s];
+  }
+  m.sub_elems.resize(ne);
+  {
+    std::vector<int64_t> fill(m.sub_elem_ptr.begin(), m.sub_elem_ptr.end() - 1);
+    for (int64_t e = 0; e < ne; ++e) m.sub_elems[fill[mesh.part[e]]++] = e;
+  }
+  // subdomain -> nodes (sorted unique)
+  std::vector<std::vector<int64_t>> sub_nodes(ns);
+  for (int64_t s = 0; s < ns; ++s) {
+    auto& v = sub_nodes[s];
+    for (int64_t k = m.sub_elem_ptr[s]; k < m.sub_elem_ptr[s + 1]; ++k) {
+      int64_t e = m.sub_elems[k];
+      for (int64_t q = mesh.en_ptr[e]; q < mesh.en_ptr[e + 1]; ++q) {
+        int64_t p = mesh.en[q];
+        if (p < 0 || p >= nn) {
+          *err = "node id out of range in element " + std::to_string(e);
+          return false;
+        }
+        v.push_back(p);
+      }
+    }
+    std::sort(v.begin(), v.end());
+    v.erase(std::unique(v.begin(), v.end()), v.end());
+  }
+  // node -> sharing set (ascending subdomain ids)
+  m.node_sub_ptr.assign(nn + 1, 0);
+  for (int64_t s = 0; s < ns; ++s)
+    for (int64_t p : sub_nodes[s]) m.node_sub_ptr[p + 1]++;
+  for (int64_t p = 0; p < nn; ++p) m.node_sub_ptr[p + 1] += m.node_sub_ptr[p];
+  m.node_sub.resize(m.node_sub_ptr[nn]);
+  {
+    std::vector<int64_t> fill(m.node_sub_ptr.begin(), m.node_sub_ptr.end() - 1);
+    for (int64_t s = 0; s < ns; ++s)
+      for (int64_t p : sub_nodes[s]) m.node_sub[fill[p]++] = (int32_t)s;
+  }
+  auto nsh = [&](int64_t p) { return m.node_sub_ptr[p + 1] - m.node_sub_ptr[p]; };
+  std::vector<char> iface(nn, 0);
+  for (int64_t p = 0; p < nn; ++p) iface[p] = nsh(p) >= 2;
+
+  // globs: union of interface nodes with equal sharing sets inside an element
+  std::vector<int64_t> parent(nn);
+  std::iota(parent.begin(), parent.end(), 0);
+  if (!all_corners) {
+    std::vector<int64_t> firsts;
+    for (int64_t e = 0; e < ne; ++e) {
+      firsts.clear();
+      for (int64_t q = mesh.en_ptr[e]; q < mesh.en_ptr[e + 1]; ++q) {
+        int64_t p = mesh.en[q];
+        if (!iface[p]) continue;
+        int64_t rep = -1;
+        for (int64_t f : firsts)
+          if (same_set(m, f, p)) {
+            rep = f;
+            break;
+          }
+        if (rep < 0) {
+          firsts.push_back(p);
+          continue;
+        }
+        int64_t a = find_root(parent, p), b = find_root(parent, rep);
+        if (a != b) parent[std::max(a, b)] = std::min(a, b);
+      }
+    }
+  }
+  // number globs by first (= smallest) node
+  std::vector<int64_t> glob_of_root(nn, -1);
+  std::vector<int64_t> node_glob(nn, -1);
+  int64_t n_globs = 0;
+  for (int64_t p = 0; p < nn; ++p) {
+    if (!iface[p]) continue;
+    int64_t r = find_root(parent, p);
+    if (glob_of_root[r] < 0) glob_of_root[r] = n_globs++;
+    node_glob[p] = glob_of_root[r];
+  }
+  m.glob_ptr.assign(n_globs + 1, 0);
+  for (int64_t p = 0; p < nn; ++p)
+    if (node_glob[p] >= 0) m.glob_ptr[node_glob[p] + 1]++;
+  for (int64_t g = 0; g < n_globs; ++g) m.glob_ptr[g + 1] += m.glob_ptr[g];
+  m.glob_nodes.resize(m.glob_ptr[n_globs]);
+  {
+    std::vector<int64_t> fill(m.glob_ptr.begin(), m.glob_ptr.end() - 1);
+    for (int64_t p = 0; p < nn; ++p)
+      if (node_glob[p] >= 0) m.glob_nodes[fill[node_glob[p]]++] = p;
+  }
+  m.glob_kind.resize(n_globs);
+  m.glob_promoted.assign(n_globs, 0);
+  for (int64_t g = 0; g < n_globs; ++g) {
+    int64_t p0 = m.glob_nodes[m.glob_ptr[g]];
+    int64_t cnt = m.glob_ptr[g + 1] - m.glob_ptr[g];
+    if (all_corners)
+      m.glob_kind[g] = kVertex;
+    else if (nsh(p0) == 2)
+      m.glob_kind[g] = dim == 3 ? kFace : kEdge;
+    else
+      m.glob_kind[g] = cnt == 1 ? kVertex : kEdge;
+  }
+
+  auto node_has_free = [&](int64_t p) {
+    for (int64_t q = mesh.nd_ptr[p]; q < mesh.nd_ptr[p + 1]; ++q)
+      if (mesh.nd_id[q] >= 0) return true;
+    return false;
+  };
+  auto node_all_prescribed = [&](int64_t p) {
+    if (mesh.nd_ptr[p + 1] == mesh.nd_ptr[p]) return false;
+    for (int64_t q = mesh.nd_ptr[p]; q < mesh.nd_ptr[p + 1]; ++q)
+      if (mesh.nd_id[q] >= 0) return false;
+    return true;
+  };
+  auto node_all_free_full = [&](int64_t p) {
+    if (mesh.nd_ptr[p + 1] - mesh.nd_ptr[p] != nc) return false;
+    for (int64_t q = mesh.nd_ptr[p]; q < mesh.nd_ptr[p + 1]; ++q)
+      if (mesh.nd_id[q] < 0) return false;
+    return true;
+  };
+  auto constrained = [&](int64_t g) -> bool {
+    if (m.glob_promoted[g]) return true;
+    unsigned bit = m.glob_kind[g] == kVertex ? 1u : (m.glob_kind[g] == kEdge ? 2u : 4u);
+    return (constraints & bit) != 0;
+  };
+  // per glob: components with a free DOF (bitmask), centroid of the nodes carrying free DOFs
+  std::vector<uint32_t> glob_comps;
+  auto add_glob_info = [&](int64_t g) {
+    uint32_t mask = 0;
+    for (int64_t k = m.glob_ptr[g]; k < m.glob_ptr[g + 1]; ++k) {
+      int64_t p = m.glob_nodes[k];
+      for (int64_t q = mesh.nd_ptr[p]; q < mesh.nd_ptr[p + 1]; ++q)
+        if (mesh.nd_id[q] >= 0) mask |= 1u << mesh.nd_comp[q];
+    }
+    glob_comps.push_back(mask);
+    double c[3] = {0, 0, 0};
+    int64_t cnt = 0;
+    for (int pass = 0; pass < 2 && cnt == 0; ++pass) {
+      for (int64_t k = m.glob_ptr[g]; k < m.glob_ptr[g + 1]; ++k) {
+        int64_t p = m.glob_nodes[k];
+        if (pass == 0 && !node_has_free(p)) continue;
+        for (int d = 0; d < dim; ++d) c[d] = c[d] + mesh.coords[p * dim + d];
+        ++cnt;
+      }
+    }
+    for (int d = 0; d < dim; ++d) m.glob_centroid.push_back(c[d] / (double)cnt);
+  };
+  for (int64_t g = 0; g < n_globs; ++g) add_glob_info(g);
+
+  // subdomain -> globs touching it (ascending glob index); promoted globs appended later
+  std::vector<std::vector<int64_t>> sub_globs(ns);
+  for (int64_t g = 0; g < n_globs; ++g) {
+    int64_t p0 = m.glob_nodes[m.glob_ptr[g]];
+    for (int64_t k = m.node_sub_ptr[p0]; k < m.node_sub_ptr[p0 + 1]; ++k) sub_globs[m.node_sub[k]].push_back(g);
+  }
+
+  // corner selection with the rigid-body sufficiency test
+  std::vector<char> is_corner(nn, 0);
+  for (int64_t g = 0; g < n_globs; ++g)
+    if (m.glob_kind[g] == kVertex && constrained(g)) is_corner[m.glob_nodes[m.glob_ptr[g]]] = 1;
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int64_t p = 0; p < nn; ++p)
+    for (int d = 0; d < dim; ++d) {
+      lo[d] = std::min(lo[d], mesh.coords[p * dim + d]);
+      hi[d] = std::max(hi[d], mesh.coords[p * dim + d]);
+    }
+  double diam2 = 0.0;
+  for (int d = 0; d < dim; ++d) diam2 = diam2 + (hi[d] - lo[d]) * (hi[d] - lo[d]);
+  const double tol = 1e-12 * diam2;
+  const uint32_t full = nc >= 32 ? 0xffffffffu : ((1u << nc) - 1u);
+
+  std::vector<Pt> pts;
+  auto gather_points = [&](int64_t s) {
+    pts.clear();
+    for (int64_t g : sub_globs[s]) {
+      if (!constrained(g) || glob_comps[g] != full) continue;
+      Pt q{{0, 0, 0}};
+      for (int d = 0; d < dim; ++d) q.x[d] = m.glob_centroid[g * dim + d];
+      pts.push_back(q);
+    }
+    for (int64_t p : sub_nodes[s]) {
+      if (!node_all_prescribed(p)) continue;
+      Pt q{{0, 0, 0}};
+      for (int d = 0; d < dim; ++d) q.x[d] = mesh.coords[p * dim + d];
+      pts.push_back(q);
+    }
+  };
+  auto sufficient = [&]() -> bool {
+    if (nc == 1) return !pts.empty();
+    if (pts.empty()) return false;
+    size_t j = 0;
+    double best = -1.0;
+    for (size_t k = 0; k < pts.size(); ++k) {
+      double d = std::sqrt(dist2(pts[k], pts[0], dim));
+      if (d > best) {
+        best = d;
+        j = k;
+      }
+    }
+    if (dim == 2) return best * best > tol;
+    if (best * best <= tol) return false;
+    double u[3] = {pts[j].x[0] - pts[0].x[0], pts[j].x[1] - pts[0].x[1], pts[j].x[2] - pts[0].x[2]};
+    double mx = 0.0;
+    for (size_t k = 0; k < pts.size(); ++k) mx = std::max(mx, cross_norm(pts[k], pts[0], u));
+    return mx > tol;
+  };
+  for (int64_t s = 0; s < ns; ++s) {
+    bool has_iface = false;
+    for (int64_t p : sub_nodes[s]) has_iface = has_iface || iface[p];
+    if (!has_iface) continue;   // the whole (connected) problem: nothing to constrain
+    int tries = 0;
+    for (;;) {
+      gather_points(s);
+      if (sufficient()) break;
+      if (++tries > 16) {
+        *err = "corner selection did not terminate on subdomain " + std::to_string(s);
+        return false;
+      }
+      std::vector<int64_t> cand;
+      for (int64_t p : sub_nodes[s])
+        if (iface[p] && !is_corner[p] && node_all_free_full(p)) cand.push_back(p);
+      if (cand.empty()) {
+        *err = "no candidate corner in subdomain " + std::to_string(s);
+        return false;
+      }
+      int64_t pick = cand[0];
+      if (!pts.empty()) {
+        size_t j = 0;
+        double best = -1.0;
+        for (size_t k = 0; k < pts.size(); ++k) {
+          double d = std::sqrt(dist2(pts[k], pts[0], dim));
+          if (d > best) {
+            best = d;
+            j = k;
+          }
+        }
+        double u[3] = {0, 0, 0};
+        bool use_line = !(best * best <= tol || dim == 2);
+        if (use_line)
+          for (int d = 0; d < 3; ++d) u[d] = (pts[j].x[d] - pts[0].x[d]) / best;
+        double bd = -1.0;
+        for (int64_t p : cand) {
+          Pt q{{0, 0, 0}};
+          for (int d = 0; d < dim; ++d) q.x[d] = mesh.coords[p * dim + d];
+          double d = use_line ? cross_norm(q, pts[0], u) : std::sqrt(dist2(q, pts[0], dim));
+          if (d > bd) {
+            bd = d;
+            pick = p;
+          }
+        }
+      }
+      // append a promoted corner glob {pick}
+      int64_t g = (int64_t)m.glob_kind.size();
+      m.glob_nodes.push_back(pick);
+      m.glob_ptr.push_back((int64_t)m.glob_nodes.size());
+      m.glob_kind.push_back(kVertex);
+      m.glob_promoted.push_back(1);
+      add_glob_info(g);
+      for (int64_t k = m.node_sub_ptr[pick]; k < m.node_sub_ptr[pick + 1]; ++k) sub_globs[m.node_sub[k]].push_back(g);
+      is_corner[pick] = 1;
+      m.n_promoted++;
+    }
+  }
+  n_globs = (int64_t)m.glob_kind.size();
+
+  // coarse DOFs in (glob order, component)
+  m.glob_coarse_ptr.assign(n_globs + 1, 0);
+  for (int64_t g = 0; g < n_globs; ++g) {
+    if (constrained(g))
+      for (int c = 0; c < nc; ++c)
+        if (glob_comps[g] & (1u << c)) {
+          m.coarse_glob.push_back(g);
+          m.coarse_comp.push_back(c);
+        }
+    m.glob_coarse_ptr[g + 1] = (int64_t)m.coarse_glob.size();
+  }
+  m.n_coarse = (int64_t)m.coarse_glob.size();
+
+  // global interface numbering
+  for (int64_t p = 0; p < nn; ++p)
+    if (iface[p])
+      for (int64_t q = mesh.nd_ptr[p]; q < mesh.nd_ptr[p + 1]; ++q)
+        if (mesh.nd_id[q] >= 0) m.iface_dofs.push_back(mesh.nd_id[q]);
+  std::sort(m.iface_dofs.begin(), m.iface_dofs.end());
+  m.n_iface = (int64_t)m.iface_dofs.size();
+  std::vector<int64_t> iface_pos(mesh.n_dof, -1);
+  for (int64_t k = 0; k < m.n_iface; ++k) iface_pos[m.iface_dofs[k]] = k;
+
+  // per-subdomain local orderings, weights, constraint rows
+  std::vector<int64_t> loc(mesh.n_dof, -1);
+  std::vector<double> mult(mesh.n_dof, 0.0);
+  m.sub_dof_ptr.assign(1, 0);
+  m.sub_coarse_ptr.assign(1, 0);
+  m.c_ptr.assign(1, 0);
+  std::vector<int64_t> interior, inter;
+  for (int64_t s = 0; s < ns; ++s) {
+    interior.clear();
+    inter.clear();
+    for (int64_t p : sub_nodes[s])
+      for (int64_t q = mesh.nd_ptr[p]; q < mesh.nd_ptr[p + 1]; ++q) {
+        int64_t d = mesh.nd_id[q];
+        if (d < 0) continue;
+        if (iface[p]) {
+          inter.push_back(d);
+          mult[d] = 1.0 / (double)nsh(p);
+        } else {
+          interior.push_back(d);
+        }
+      }
+    std::sort(interior.begin(), interior.end());
+    std::sort(inter.begin(), inter.end());
+    int64_t base = (int64_t)m.sub_dofs.size();
+    for (int64_t d : interior) {
+      loc[d] = (int64_t)m.sub_dofs.size() - base;
+      m.sub_dofs.push_back(d);
+      m.sub_iface.push_back(-1);
+      m.sub_wmult.push_back(0.0);
+    }
+    for (int64_t d : inter) {
+      loc[d] = (int64_t)m.sub_dofs.size() - base;
+      m.sub_dofs.push_back(d);
+      m.sub_iface.push_back(iface_pos[d]);
+      m.sub_wmult.push_back(mult[d]);
+    }
+    m.sub_nI.push_back((int64_t)interior.size());
+    m.sub_dof_ptr.push_back((int64_t)m.sub_dofs.size());
+    // constraint rows: globs touching s in glob order -> ascending coarse ids
+    std::vector<int64_t> gl = sub_globs[s];
+    std::sort(gl.begin(), gl.end());
+    for (int64_t g : gl) {
+      for (int64_t k = m.glob_coarse_ptr[g]; k < m.glob_coarse_ptr[g + 1]; ++k) {
+        int c = m.coarse_comp[k];
+        m.sub_coarse.push_back(k);
+        int64_t first = (int64_t)m.c_col.size();
+        for (int64_t t = m.glob_ptr[g]; t < m.glob_ptr[g + 1]; ++t) {
+          int64_t p = m.glob_nodes[t];
+          for (int64_t q = mesh.nd_ptr[p]; q < mesh.nd_ptr[p + 1]; ++q)
+            if (mesh.nd_comp[q] == c && mesh.nd_id[q] >= 0) m.c_col.push_back(loc[mesh.nd_id[q]]);
+        }
+        int64_t cnt = (int64_t)m.c_col.size() - first;
+        for (int64_t t = 0; t < cnt; ++t) m.c_val.push_back(1.0 / (double)cnt);
+        m.c_ptr.push_back((int64_t)m.c_col.size());
+      }
+    }
+    m.sub_coarse_ptr.push_back((int64_t)m.sub_coarse.size());
+    for (int64_t d : interior) loc[d] = -1;
+    for (int64_t d : inter) loc[d] = -1;
+  }
+  return true;
+}
+
+void next_level_mesh(const LevelMesh& mesh, const LevelMaps& maps, const int32_t* part, int64_t n_sub_next,
+                     LevelMesh* out) {
+  LevelMesh& n = *out;
+  n = LevelMesh();
+  n.dim = mesh.dim;
+  n.ncomp = mesh.ncomp;
+  const int dim = mesh.dim;
+  const int64_t G = maps.n_globs();
+  std::vector<int64_t> node_of_glob(G, -1);
+  n.nd_ptr.assign(1, 0);
+  for (int64_t g = 0; g < G; ++g) {
+    if (maps.glob_coarse_ptr[g + 1] == maps.glob_coarse_ptr[g]) continue;
+    node_of_glob[g] = n.n_nodes++;
+    for (int d = 0; d < dim; ++d) n.coords.push_back(maps.glob_centroid[g * dim + d]);
+    for (int64_t k = maps.glob_coarse_ptr[g]; k < maps.glob_coarse_ptr[g + 1]; ++k) {
+      n.nd_comp.push_back(maps.coarse_comp[k]);
+      n.nd_id.push_back(k);
+    }
+    n.nd_ptr.push_back((int64_t)n.nd_id.size());
+  }
+  const int64_t ns = maps.n_sub();
+  n.n_elems = ns;
+  n.en_ptr.assign(1, 0);
+  n.ed_ptr.assign(1, 0);
+  for (int64_t s = 0; s < ns; ++s) {
+    int64_t last = -1;
+    for (int64_t k = maps.sub_coarse_ptr[s]; k < maps.sub_coarse_ptr[s + 1]; ++k) {
+      int64_t cd = maps.sub_coarse[k];
+      int64_t g = maps.coarse_glob[cd];
+      if (g != last) {
+        n.en.push_back(node_of_glob[g]);
+        last = g;
+      }
+      n.ed.push_back(cd);
+    }
+    n.en_ptr.push_back((int64_t)n.en.size());
+    n.ed_ptr.push_back((int64_t)n.ed.size());
+  }
+  n.part.assign(part, part + ns);
+  n.n_sub = n_sub_next;
+  n.n_dof = maps.n_coarse;
+}
+
+}  // namespace bddc

@@ -1,0 +1,269 @@
+// Assembly kernels: element matrices, sub-assembly of K_i (Sec. 2: "obtained by the
+// sub-assembling of element matrices"), the augmented matrix K_i + rho C_i^T C_i with the
+// constraint rows appended, and the interface weights.
+//
+// Every reduction here runs in a fixed order (one warp per matrix row, contributions in
+// ascending element order), so two runs give bit-identical factors.
+#include "internal.h"
+
+namespace bddc {
+
+namespace {
+
+__device__ __forceinline__ int64_t tile_index(int i, int j, int Bc) {
+  return i < Bc ? ((int64_t)i * (i + 1) / 2 + j) : ((int64_t)Bc * (Bc + 1) / 2 + (int64_t)(i - Bc) * Bc + j);
+}
+
+// One warp per element.  Q1 element with lexicographic local nodes, 2-point Gauss rule per
+// direction; the Gauss point g has reference coordinates xi_d = (2 bit_d(g) - 1)/sqrt(3).
+template <int DIM>
+__global__ void k_elem_q1(int physics, int64_t n_elems, const double* __restrict__ coords,
+                          const int32_t* __restrict__ conn, const double* __restrict__ coef, double nu,
+                          const int32_t* __restrict__ slot_elem, double* __restrict__ ke) {
+  constexpr int NN = 1 << DIM;   // nodes = Gauss points
+  constexpr int WARPS = 4;
+  __shared__ double sG[WARPS][NN][NN][DIM];   // [gp][node][d] physical gradients
+  __shared__ double sW[WARPS][NN];            // detJ * weight
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t slot = (int64_t)blockIdx.x * WARPS + w;
+  if (slot >= n_elems) return;
+  const int64_t e = slot_elem[slot];
+  const double gq = 0.57735026918962576451;   // 1/sqrt(3)
+  if (lane < NN) {
+    double xi[DIM];
+    for (int d = 0; d < DIM; ++d) xi[d] = ((lane >> d) & 1) ? gq : -gq;
+    double G[NN][DIM];
+    for (int a = 0; a < NN; ++a)
+      for (int d = 0; d < DIM; ++d) {
+        double v = (((a >> d) & 1) ? 1.0 : -1.0) * 0.5;
+        for (int d2 = 0; d2 < DIM; ++d2)
+          if (d2 != d) v *= (1.0 + (((a >> d2) & 1) ? 1.0 : -1.0) * xi[d2]) * 0.5;
+        G[a][d] = v;
+      }
+    double J[DIM][DIM];
+    for (int d = 0; d < DIM; ++d)
+      for (int d2 = 0; d2 < DIM; ++d2) {
+        double s = 0.0;
+        for (int a = 0; a < NN; ++a) s += coords[(int64_t)conn[e * NN + a] * DIM + d] * G[a][d2];
+        J[d][d2] = s;
+      }
+    double inv[DIM][DIM], det;
+    if (DIM == 2) {
+      det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+      inv[0][0] = J[1][1] / det;
+      inv[0][1] = -J[0][1] / det;
+      inv[1][0] = -J[1][0] / det;
+      inv[1][1] = J[0][0] / det;
+    } else {
+      double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+      double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+      double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+      det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+      inv[0][0] = c00 / det;
+      inv[1][0] = c01 / det;
+      inv[2][0] = c02 / det;
+      inv[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+      inv[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+      inv[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+      inv[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+      inv[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+      inv[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+    }
+    for (int a = 0; a < NN; ++a)
+      for (int d = 0; d < DIM; ++d) {
+        double s = 0.0;
+        for (int d2 = 0; d2 < DIM; ++d2) s += G[a][d2] * inv[d2][d];
+        sG[w][lane][a][d] = s;
+      }
+    sW[w][lane] = det;
+  }
+  __syncwarp();
+  const double E = coef[e];
+  if (physics == 0) {
+    for (int idx = lane; idx < NN * NN; idx += 32) {
+      int a = idx / NN, b = idx % NN;
+      double s = 0.0;
+      for (int g = 0; g < NN; ++g) {
+        double d = 0.0;
+        for (int k = 0; k < DIM; ++k) d += sG[w][g][a][k] * sG[w][g][b][k];
+        s += sW[w][g] * d;
+      }
+      ke[slot * NN * NN + idx] = E * s;
+    }
+  } else {
+    const double lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+    const double mu = E / (2.0 * (1.0 + nu));
+    constexpr int ND = NN * DIM;
+    for (int idx = lane; idx < ND * ND; idx += 32) {
+      int row = idx / ND, col = idx % ND;
+      int a = row / DIM, i = row % DIM, b = col / DIM, j = col % DIM;
+      double s = 0.0;
+      for (int g = 0; g < NN; ++g) {
+        double dd = 0.0;
+        for (int k = 0; k < DIM; ++k) dd += sG[w][g][a][k] * sG[w][g][b][k];
+        double v = lam * sG[w][g][a][i] * sG[w][g][b][j] + mu * sG[w][g][a][j] * sG[w][g][b][i];
+        if (i == j) v += mu * dd;
+        s += sW[w][g] * v;
+      }
+      ke[slot * ND * ND + idx] = s;
+    }
+  }
+}
+
+// One warp per padded local row: CSR values of K_i from the element matrices containing the
+// row's DOF, in ascending element order.
+__global__ void k_csr_values(LevelDev L, const int32_t* __restrict__ row_sub) {
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= L.n_vec) return;
+  const int64_t p0 = L.row_ptr[row], p1 = L.row_ptr[row + 1];
+  for (int64_t q = p0 + lane; q < p1; q += 32) L.val[q] = 0.0;
+  __syncwarp();
+  const int32_t* cols = L.col + p0;
+  const int len = (int)(p1 - p0);
+  for (int64_t c = L.rc_ptr[row]; c < L.rc_ptr[row + 1]; ++c) {
+    const int k = L.rc_elem[c], a = L.rc_a[c];
+    const int64_t eo = L.ed_off[k];
+    const int ne = (int)(L.ed_off[k + 1] - eo);
+    const double* kr = L.ke + L.ke_off[k] + (int64_t)a * ne;
+    for (int b = lane; b < ne; b += 32) {
+      const int col = L.eldof[eo + b];
+      if (col < 0) continue;
+      int lo = 0, hi = len - 1;
+      while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (cols[mid] < col) lo = mid + 1; else hi = mid;
+      }
+      L.val[p0 + lo] += kr[b];
+    }
+    __syncwarp();
+  }
+  if (lane == 0 && len > 0) {
+    const int s = row_sub[row];
+    const int r = (int)(row - L.meta[s].vec_off);
+    double d = 0.0;
+    for (int q = 0; q < len; ++q)
+      if (cols[q] == r) d = L.val[p0 + q];
+    L.diag[row] = d;
+  }
+}
+
+// One warp per padded row: write the lower part of the row into the tiles; identity on
+// padding rows.  Tiles are zeroed beforehand.
+template <typename T>
+__global__ void k_densify(LevelDev L, const int32_t* __restrict__ row_sub) {
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= L.n_vec) return;
+  const int s = row_sub[row];
+  const SubMeta m = L.meta[s];
+  const int r = (int)(row - m.vec_off);
+  T* tiles = (T*)L.tiles;
+  const int i = r / NB, rr = r % NB;
+  const bool pad = (r >= m.nI && r < m.nIb * NB) || (r >= m.nIb * NB + m.nG);
+  if (pad) {
+    if (lane == 0) tiles[m.tile_off + tile_index(i, i, m.Bc) * NB2 + rr * NB + rr] = (T)1;
+    return;
+  }
+  for (int64_t q = L.row_ptr[row] + lane; q < L.row_ptr[row + 1]; q += 32) {
+    const int c = L.col[q];
+    if (c > r) continue;
+    tiles[m.tile_off + tile_index(i, c / NB, m.Bc) * NB2 + rr * NB + (c % NB)] = (T)L.val[q];
+  }
+}
+
+// One block per subdomain: rho = mean diag K_i, A += rho C^T C (rows one after another),
+// then the constraint rows into block rows Bc .. Bc+ncb-1.
+template <typename T>
+__global__ void k_add_constraints(LevelDev L) {
+  const int s = blockIdx.x;
+  const SubMeta m = L.meta[s];
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int r = threadIdx.x; r < m.nI; r += blockDim.x) acc += L.diag[m.vec_off + r];
+  for (int r = threadIdx.x; r < m.nG; r += blockDim.x) acc += L.diag[m.vec_off + m.nIb * NB + r];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  const double rho = m.n > 0 ? red[0] / (double)m.n : 1.0;
+  if (threadIdx.x == 0) L.rho[s] = rho;
+  T* tiles = (T*)L.tiles;
+  for (int q = 0; q < m.nc; ++q) {
+    const int64_t e0 = L.c_ptr[m.c_off + q], e1 = L.c_ptr[m.c_off + q + 1];
+    const int cnt = (int)(e1 - e0);
+    for (int t = threadIdx.x; t < cnt * cnt; t += blockDim.x) {
+      const int x = t / cnt, y = t % cnt;
+      const int pa = L.c_pos[e0 + x], pb = L.c_pos[e0 + y];
+      if (pb > pa) continue;
+      T* p = tiles + m.tile_off + tile_index(pa / NB, pb / NB, m.Bc) * NB2 + (pa % NB) * NB + (pb % NB);
+      *p = (T)((double)*p + rho * L.c_val[e0 + x] * L.c_val[e0 + y]);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+      const int pa = L.c_pos[e0 + t];
+      tiles[m.tile_off + tile_index(m.Bc + q / NB, pa / NB, m.Bc) * NB2 + (q % NB) * NB + (pa % NB)] =
+          (T)L.c_val[e0 + t];
+    }
+    __syncthreads();
+  }
+}
+
+// Interface weights: stiffness D_i(j) = K_i(jj) / sum_k K_k(jj), or multiplicity 1/count.
+__global__ void k_weights(LevelDev L, int multiplicity) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= L.n_iface) return;
+  const int64_t o0 = L.iface_ptr[g], o1 = L.iface_ptr[g + 1];
+  if (multiplicity) {
+    const double w = 1.0 / (double)(o1 - o0);
+    for (int64_t o = o0; o < o1; ++o) L.w[L.iface_occ[o]] = w;
+    return;
+  }
+  double s = 0.0;
+  for (int64_t o = o0; o < o1; ++o) s += L.diag[L.iface_occ[o]];
+  for (int64_t o = o0; o < o1; ++o) L.w[L.iface_occ[o]] = L.diag[L.iface_occ[o]] / s;
+}
+
+}  // namespace
+
+void launch_elem_q1(int physics, int dim, int64_t n_elems, const double* coords, const int32_t* conn,
+                    const double* coef, double nu, const int32_t* slot_elem, double* ke, cudaStream_t st) {
+  if (n_elems <= 0) return;
+  const int blocks = (int)((n_elems + 3) / 4);
+  if (dim == 2)
+    { note_launch(); k_elem_q1<2><<<blocks, 128, 0, st>>>(physics, n_elems, coords, conn, coef, nu, slot_elem, ke); }
+  else
+    { note_launch(); k_elem_q1<3><<<blocks, 128, 0, st>>>(physics, n_elems, coords, conn, coef, nu, slot_elem, ke); }
+}
+
+void launch_csr_values(const LevelDev& L, int64_t n_rows_total, const int32_t* row_sub, cudaStream_t st) {
+  (void)n_rows_total;
+  if (L.n_vec <= 0) return;
+  { note_launch(); k_csr_values<<<(unsigned)((L.n_vec + 7) / 8), 256, 0, st>>>(L, row_sub); }
+}
+
+template <typename T>
+void launch_densify_rows(const LevelDev& L, const int32_t* row_sub, cudaStream_t st) {
+  if (L.n_vec <= 0) return;
+  { note_launch(); k_densify<T><<<(unsigned)((L.n_vec + 7) / 8), 256, 0, st>>>(L, row_sub); }
+}
+
+template <typename T>
+void launch_add_constraints(const LevelDev& L, cudaStream_t st) {
+  if (L.n_sub <= 0) return;
+  { note_launch(); k_add_constraints<T><<<(unsigned)L.n_sub, 256, 0, st>>>(L); }
+}
+
+void launch_weights(const LevelDev& L, int multiplicity, const double*, cudaStream_t st) {
+  if (L.n_iface <= 0) return;
+  { note_launch(); k_weights<<<(unsigned)((L.n_iface + 255) / 256), 256, 0, st>>>(L, multiplicity); }
+}
+
+template void launch_densify_rows<float>(const LevelDev&, const int32_t*, cudaStream_t);
+template void launch_densify_rows<double>(const LevelDev&, const int32_t*, cudaStream_t);
+template void launch_add_constraints<float>(const LevelDev&, cudaStream_t);
+template void launch_add_constraints<double>(const LevelDev&, cudaStream_t);
+
+}  // namespace bddc

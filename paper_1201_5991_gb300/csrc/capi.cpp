@@ -1,0 +1,1339 @@
+// C ABI of the GB300 multilevel BDDC library: host orchestration of Algorithm 1 (set-up)
+// and Algorithm 2 (application) with PCG on the reduced interface problem (Sec. 2).
+// Every numerical step runs in the kernels of assemble.cu, dense.cu and vector.cu; this
+// file prepares index arrays, allocates device memory and enqueues launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/bddc.h"
+#include "analysis.h"
+#include "internal.h"
+
+namespace bddc {
+
+std::atomic<int64_t> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+namespace {
+
+thread_local std::string g_err;
+
+struct Fail {
+  int code;
+};
+
+[[noreturn]] void fail(int code, const std::string& msg) {
+  g_err = msg;
+  throw Fail{code};
+}
+
+void ck(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return;
+  if (e == cudaErrorMemoryAllocation) fail(BDDC_ERR_OOM, std::string(what) + ": out of device memory");
+  fail(BDDC_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// ------------------------------------------------------------------ device memory helpers
+struct DevArena {
+  std::vector<void*> ptrs;
+  int64_t bytes = 0;
+  template <typename T>
+  T* alloc(int64_t n) {
+    if (n <= 0) n = 1;
+    void* p = nullptr;
+    ck(cudaMalloc(&p, sizeof(T) * (size_t)n), "cudaMalloc");
+    ptrs.push_back(p);
+    bytes += (int64_t)sizeof(T) * n;
+    return (T*)p;
+  }
+  template <typename T>
+  T* upload(const std::vector<T>& v, cudaStream_t st) {
+    T* p = alloc<T>((int64_t)v.size());
+    if (!v.empty()) ck(cudaMemcpyAsync(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st), "upload");
+    return p;
+  }
+  void release() {
+    for (void* p : ptrs) cudaFree(p);
+    ptrs.clear();
+    bytes = 0;
+  }
+};
+
+// ------------------------------------------------------------------ one level
+struct Level {
+  LevelMesh mesh;
+  LevelMaps maps;
+  bool coarsest = false;
+  bool fp32 = false;           // precision of tiles / preconditioner vectors
+  // host-side metadata
+  std::vector<SubMeta> meta;
+  int64_t n_vec = 0, tile_elems = 0, dinv_elems = 0, psi_elems = 0, g_elems = 0, sum_nc = 0;
+  int max_R = 0, max_Bc = 0, max_nc = 0, max_nG = 0, max_nGb = 0;
+  std::vector<int> max_tiles;  // per factor step k
+  std::vector<double> step_flops;  // tile flops of factor step k (all subdomains)
+  double trsv_bytes[2] = {0, 0};   // algorithmic bytes of one sweep over part 0 / part 1
+  int ne_uniform = 0;          // level 1: entries per element row
+  // device
+  LevelDev d{};
+  int32_t* row_sub = nullptr;
+  int32_t* slot_elem = nullptr;
+  int64_t* seg_src = nullptr;  // levels > 1: K_C offsets of the previous level per element slot
+  int64_t* seg_len = nullptr;
+  int64_t* iface_dofs = nullptr;
+  // work vectors
+  void* locA = nullptr;        // T[n_vec]
+  void* locB = nullptr;        // T[n_vec]
+  double* dl0 = nullptr;       // double[n_vec]
+  double* dl1 = nullptr;
+  double* dl2 = nullptr;
+  double* dl3 = nullptr;
+  double* rc_sub = nullptr;    // [sum_nc]
+  double* zc_sub = nullptr;
+  double* rC = nullptr;        // [n_coarse]
+  double* zC = nullptr;
+  double* gi0 = nullptr;       // [n_iface]
+  double* gi1 = nullptr;
+  double* gi2 = nullptr;
+  double* gv0 = nullptr;       // [n_dof] (levels > 1)
+};
+
+int64_t pad_pos(const SubMeta& m, int64_t r) { return r < m.nI ? r : (int64_t)m.nIb * NB + (r - m.nI); }
+
+}  // namespace
+}  // namespace bddc
+
+using namespace bddc;
+
+struct bddc_handle_s {
+  bddc_opts opts{};
+  unsigned constraints = 0;
+  cudaStream_t st = nullptr;
+  bool analysis_only = false;
+  // level-1 mesh data (host copies)
+  int dim = 3, npe = 8, ndof = 1, physics = 0;
+  int64_t n_nodes = 0, n_elems = 0, n_full = 0, n_free = 0;
+  double nu = 0.0;
+  std::vector<double> coords, coef;
+  std::vector<int32_t> conn;
+  std::vector<int64_t> free_of_full;   // full DOF -> free id or -1
+  std::vector<std::vector<int32_t>> parts;
+  std::vector<int64_t> n_parts;
+  int n_levels = 2;
+  std::vector<Level> lv;               // BDDC levels 1..L-1, then the coarsest
+  DevArena arena;
+  // device copies of level-1 mesh data
+  double* d_coords = nullptr;
+  int32_t* d_conn = nullptr;
+  double* d_coef = nullptr;
+  int64_t* d_edof = nullptr;           // element -> full DOF ids
+  int64_t* d_free_of_full = nullptr;
+  int* d_status = nullptr;
+  // PCG
+  double* scal = nullptr;              // [16]
+  double* partial = nullptr;           // [kDotBlocks]
+  double* h_scal = nullptr;            // pinned [16]
+  double *vx = nullptr, *vr = nullptr, *vz = nullptr, *vp = nullptr, *vq = nullptr, *vrold = nullptr, *vg = nullptr;
+  double* fcol = nullptr;              // [n_free] work
+  double* ucol = nullptr;
+  double *full_a = nullptr, *full_b = nullptr;
+  int refine_steps = 0;
+  bddc_stats stats{};
+  bool factored = false;
+  // optional per-class CUDA-event timing
+  struct ProfRec {
+    cudaEvent_t a, b;
+    int cls;
+    double bytes, flops;
+  };
+  std::vector<ProfRec> prof_pending;
+  std::vector<cudaEvent_t> event_pool;
+  ~bddc_handle_s() {
+    for (auto& r : prof_pending) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+    for (auto e : event_pool) cudaEventDestroy(e);
+  }
+};
+
+namespace bddc {
+namespace {
+
+constexpr int kDotBlocks = 304;   // 2 x SM count of a GB300; fixed for reproducible sums
+
+cudaEvent_t take_event(bddc_handle_s* h) {
+  if (!h->event_pool.empty()) {
+    cudaEvent_t e = h->event_pool.back();
+    h->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  ck(cudaEventCreate(&e), "cudaEventCreate");
+  return e;
+}
+
+// Records CUDA events around one launch (or one group of launches) of a kernel class on the
+// handle's stream when profiling is on.
+struct ProfScope {
+  bddc_handle_s* h;
+  int cls;
+  double bytes, flops;
+  cudaEvent_t a = nullptr;
+  ProfScope(bddc_handle_s* h_, int cls_, double bytes_, double flops_) : h(h_), cls(cls_), bytes(bytes_), flops(flops_) {
+    if (h->opts.profile) {
+      a = take_event(h);
+      ck(cudaEventRecord(a, h->st), "cudaEventRecord");
+    }
+  }
+  ~ProfScope() {
+    if (!a) return;
+    cudaEvent_t b = nullptr;
+    try {
+      b = take_event(h);
+    } catch (...) {
+      return;
+    }
+    cudaEventRecord(b, h->st);
+    h->prof_pending.push_back({a, b, cls, bytes, flops});
+  }
+};
+
+void flush_profile(bddc_handle_s* h) {
+  if (h->prof_pending.empty()) return;
+  ck(cudaStreamSynchronize(h->st), "sync");
+  for (auto& r : h->prof_pending) {
+    float ms = 0.f;
+    ck(cudaEventElapsedTime(&ms, r.a, r.b), "cudaEventElapsedTime");
+    h->stats.prof_ms[r.cls] += ms;
+    h->stats.prof_launches[r.cls] += 1;
+    h->stats.prof_bytes[r.cls] += r.bytes;
+    h->stats.prof_flops[r.cls] += r.flops;
+    h->event_pool.push_back(r.a);
+    h->event_pool.push_back(r.b);
+  }
+  h->prof_pending.clear();
+}
+
+// ------------------------------------------------------------------ level preparation
+void build_level1_mesh(bddc_handle_s* h, LevelMesh* out) {
+  LevelMesh& m = *out;
+  m.dim = h->dim;
+  m.ncomp = h->ndof;
+  m.n_nodes = h->n_nodes;
+  m.n_elems = h->n_elems;
+  m.n_sub = h->n_parts[0];
+  m.coords = h->coords;
+  m.nd_ptr.resize(h->n_nodes + 1);
+  m.nd_comp.resize(h->n_full);
+  m.nd_id.resize(h->n_full);
+  for (int64_t p = 0; p <= h->n_nodes; ++p) m.nd_ptr[p] = p * h->ndof;
+  for (int64_t q = 0; q < h->n_full; ++q) {
+    m.nd_comp[q] = (int32_t)(q % h->ndof);
+    m.nd_id[q] = h->free_of_full[q];
+  }
+  m.en_ptr.resize(h->n_elems + 1);
+  m.en.resize(h->n_elems * h->npe);
+  m.ed_ptr.resize(h->n_elems + 1);
+  m.ed.resize(h->n_elems * h->npe * h->ndof);
+  for (int64_t e = 0; e <= h->n_elems; ++e) {
+    m.en_ptr[e] = e * h->npe;
+    m.ed_ptr[e] = e * h->npe * h->ndof;
+  }
+  for (int64_t e = 0; e < h->n_elems; ++e)
+    for (int a = 0; a < h->npe; ++a) {
+      int64_t p = h->conn[e * h->npe + a];
+      m.en[e * h->npe + a] = p;
+      for (int c = 0; c < h->ndof; ++c) m.ed[(e * h->npe + a) * h->ndof + c] = h->free_of_full[p * h->ndof + c];
+    }
+  m.part = h->parts[0];
+  m.n_dof = h->n_free;
+}
+
+// Single-subdomain "level" holding the coarsest problem: all DOFs interior.
+void build_coarsest_mesh(const Level& prev, LevelMesh* out) {
+  std::vector<int32_t> part(prev.maps.n_sub(), 0);
+  next_level_mesh(prev.mesh, prev.maps, part.data(), 1, out);
+}
+
+void parallel_for(int64_t n, const std::function<void(int64_t)>& fn) {
+  unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  if (n < 4 || nt == 1) {
+    for (int64_t i = 0; i < n; ++i) fn(i);
+    return;
+  }
+  std::vector<std::thread> th;
+  std::atomic<int64_t> next{0};
+  for (unsigned t = 0; t < nt; ++t)
+    th.emplace_back([&]() {
+      for (;;) {
+        int64_t i = next.fetch_add(1);
+        if (i >= n) break;
+        fn(i);
+      }
+    });
+  for (auto& t : th) t.join();
+}
+
+// Host arrays of one level, built from its mesh and maps, then uploaded.
+void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
+  const LevelMaps& mp = L.maps;
+  const LevelMesh& ms = L.mesh;
+  const int64_t ns = mp.n_sub();
+  L.meta.resize(ns);
+  int64_t tile = 0, dinv = 0, vec = 0, coff = 0, goff = 0, psi = 0;
+  L.max_R = L.max_Bc = L.max_nc = L.max_nG = L.max_nGb = 0;
+  for (int64_t s = 0; s < ns; ++s) {
+    SubMeta& m = L.meta[s];
+    m.n = (int32_t)(mp.sub_dof_ptr[s + 1] - mp.sub_dof_ptr[s]);
+    m.nI = (int32_t)mp.sub_nI[s];
+    m.nG = m.n - m.nI;
+    m.nc = (int32_t)(mp.sub_coarse_ptr[s + 1] - mp.sub_coarse_ptr[s]);
+    m.nIb = (int32_t)ceil_div(m.nI, NB);
+    m.nGb = (int32_t)ceil_div(m.nG, NB);
+    m.ncb = (int32_t)ceil_div(m.nc, NB);
+    m.Bc = m.nIb + m.nGb;
+    m.R = m.Bc + m.ncb;
+    m.pad0 = 0;
+    m.tile_off = tile;
+    tile += ((int64_t)m.Bc * (m.Bc + 1) / 2 + (int64_t)m.ncb * m.Bc) * NB2;
+    m.dinv_off = dinv;
+    dinv += (int64_t)m.Bc * NB2;
+    m.vec_off = vec;
+    vec += (int64_t)m.Bc * NB;
+    m.row_off = 0;
+    m.c_off = coff;
+    coff += m.nc;
+    m.g_off = goff;
+    goff += (int64_t)m.nc * m.nc;
+    m.psi_off = psi;
+    psi += (int64_t)m.nGb * NB * m.nc;
+    L.max_R = std::max(L.max_R, (int)m.R);
+    L.max_Bc = std::max(L.max_Bc, (int)m.Bc);
+    L.max_nc = std::max(L.max_nc, (int)m.nc);
+    L.max_nG = std::max(L.max_nG, (int)m.nG);
+    L.max_nGb = std::max(L.max_nGb, (int)m.nGb);
+  }
+  L.n_vec = vec;
+  L.tile_elems = tile;
+  L.dinv_elems = dinv;
+  L.psi_elems = psi;
+  L.g_elems = goff;
+  L.sum_nc = coff;
+  L.max_tiles.assign(L.max_Bc, 0);
+  L.step_flops.assign(L.max_Bc, 0.0);
+  const double nb3 = (double)NB * NB * NB;
+  const double wsz = L.fp32 ? 4.0 : 8.0;
+  L.trsv_bytes[0] = L.trsv_bytes[1] = 0.0;
+  for (int64_t s = 0; s < ns; ++s) {
+    const SubMeta& m = L.meta[s];
+    for (int k = 0; k < m.Bc; ++k) {
+      int64_t cnt = 0;
+      for (int j = k + 1; j < m.Bc; ++j) cnt += m.R - j;
+      L.max_tiles[k] = std::max(L.max_tiles[k], (int)cnt);
+      L.step_flops[k] += nb3 / 3.0 + nb3 * (double)(m.R - k - 1) + 2.0 * nb3 * (double)cnt;
+    }
+    // a sweep reads the stored triangle once and the vector in and out
+    L.trsv_bytes[0] += wsz * (0.5 * (double)m.nI * (m.nI + 1) + 2.0 * m.nI);
+    L.trsv_bytes[1] += wsz * (0.5 * (double)m.nG * (m.nG + 1) + 2.0 * m.nG);
+  }
+
+  // element slots (subdomain order) and their padded local DOF positions
+  const int64_t nel = ms.n_elems;
+  std::vector<int32_t> slot_elem(nel), slot_sub(nel);
+  std::vector<int64_t> ke_off(nel + 1), ed_off(nel + 1);
+  for (int64_t s = 0; s < ns; ++s)
+    for (int64_t k = mp.sub_elem_ptr[s]; k < mp.sub_elem_ptr[s + 1]; ++k) {
+      slot_elem[k] = (int32_t)mp.sub_elems[k];
+      slot_sub[k] = (int32_t)s;
+    }
+  ke_off[0] = ed_off[0] = 0;
+  for (int64_t k = 0; k < nel; ++k) {
+    int64_t e = slot_elem[k];
+    int64_t nek = ms.ed_ptr[e + 1] - ms.ed_ptr[e];
+    ed_off[k + 1] = ed_off[k] + nek;
+    ke_off[k + 1] = ke_off[k] + nek * nek;
+  }
+  std::vector<int32_t> eldof(ed_off[nel]);
+  std::vector<int32_t> loc2iface(L.n_vec, -1), loc2glob(L.n_vec, -1), row_sub(L.n_vec);
+  parallel_for(ns, [&](int64_t s) {
+    const SubMeta& m = L.meta[s];
+    std::unordered_map<int64_t, int32_t> pos;
+    pos.reserve((size_t)m.n * 2);
+    for (int64_t q = mp.sub_dof_ptr[s]; q < mp.sub_dof_ptr[s + 1]; ++q) {
+      int64_t r = q - mp.sub_dof_ptr[s];
+      int64_t pp = pad_pos(m, r);
+      pos[mp.sub_dofs[q]] = (int32_t)pp;
+      loc2glob[m.vec_off + pp] = (int32_t)mp.sub_dofs[q];
+      loc2iface[m.vec_off + pp] = (int32_t)mp.sub_iface[q];
+    }
+    for (int64_t p = 0; p < (int64_t)m.Bc * NB; ++p) row_sub[m.vec_off + p] = (int32_t)s;
+    for (int64_t k = mp.sub_elem_ptr[s]; k < mp.sub_elem_ptr[s + 1]; ++k) {
+      int64_t e = slot_elem[k];
+      for (int64_t q = ms.ed_ptr[e], t = ed_off[k]; q < ms.ed_ptr[e + 1]; ++q, ++t) {
+        int64_t d = ms.ed[q];
+        eldof[t] = d < 0 ? -1 : pos.at(d);
+      }
+    }
+  });
+  // row contributions (ascending element slot) and CSR pattern per padded row
+  std::vector<int64_t> rc_ptr(L.n_vec + 1, 0);
+  for (int64_t k = 0; k < nel; ++k) {
+    const SubMeta& m = L.meta[slot_sub[k]];
+    for (int64_t t = ed_off[k]; t < ed_off[k + 1]; ++t)
+      if (eldof[t] >= 0) rc_ptr[m.vec_off + eldof[t] + 1]++;
+  }
+  for (int64_t r = 0; r < L.n_vec; ++r) rc_ptr[r + 1] += rc_ptr[r];
+  std::vector<int32_t> rc_elem(rc_ptr[L.n_vec]), rc_a(rc_ptr[L.n_vec]);
+  {
+    std::vector<int64_t> fill(rc_ptr.begin(), rc_ptr.end() - 1);
+    for (int64_t k = 0; k < nel; ++k) {
+      const SubMeta& m = L.meta[slot_sub[k]];
+      for (int64_t t = ed_off[k]; t < ed_off[k + 1]; ++t)
+        if (eldof[t] >= 0) {
+          int64_t r = m.vec_off + eldof[t];
+          rc_elem[fill[r]] = (int32_t)k;
+          rc_a[fill[r]] = (int32_t)(t - ed_off[k]);
+          fill[r]++;
+        }
+    }
+  }
+  std::vector<std::vector<int32_t>> sub_cols(ns);
+  std::vector<std::vector<int64_t>> sub_rowlen(ns);
+  parallel_for(ns, [&](int64_t s) {
+    const SubMeta& m = L.meta[s];
+    const int64_t nr = (int64_t)m.Bc * NB;
+    std::vector<int64_t> stamp(nr, -1);
+    std::vector<int32_t> cols;
+    auto& out = sub_cols[s];
+    auto& len = sub_rowlen[s];
+    len.assign(nr, 0);
+    for (int64_t r = 0; r < nr; ++r) {
+      cols.clear();
+      const int64_t row = m.vec_off + r;
+      for (int64_t c = rc_ptr[row]; c < rc_ptr[row + 1]; ++c) {
+        int64_t k = rc_elem[c];
+        for (int64_t t = ed_off[k]; t < ed_off[k + 1]; ++t) {
+          int32_t col = eldof[t];
+          if (col >= 0 && stamp[col] != r) {
+            stamp[col] = r;
+            cols.push_back(col);
+          }
+        }
+      }
+      std::sort(cols.begin(), cols.end());
+      len[r] = (int64_t)cols.size();
+      out.insert(out.end(), cols.begin(), cols.end());
+    }
+  });
+  std::vector<int64_t> row_ptr(L.n_vec + 1, 0);
+  for (int64_t s = 0; s < ns; ++s) {
+    const SubMeta& m = L.meta[s];
+    for (int64_t r = 0; r < (int64_t)m.Bc * NB; ++r) row_ptr[m.vec_off + r + 1] = sub_rowlen[s][r];
+  }
+  for (int64_t r = 0; r < L.n_vec; ++r) row_ptr[r + 1] += row_ptr[r];
+  std::vector<int32_t> col(row_ptr[L.n_vec]);
+  for (int64_t s = 0; s < ns; ++s) {
+    const SubMeta& m = L.meta[s];
+    std::copy(sub_cols[s].begin(), sub_cols[s].end(), col.begin() + row_ptr[m.vec_off]);
+  }
+  sub_cols.clear();
+  // constraint rows over padded positions
+  std::vector<int64_t> c_ptr(mp.c_ptr.size());
+  std::vector<int32_t> c_pos(mp.c_col.size());
+  for (size_t i = 0; i < mp.c_ptr.size(); ++i) c_ptr[i] = mp.c_ptr[i];
+  for (int64_t s = 0; s < ns; ++s) {
+    const SubMeta& m = L.meta[s];
+    int64_t r0 = mp.sub_coarse_ptr[s], r1 = mp.sub_coarse_ptr[s + 1];
+    for (int64_t t = mp.c_ptr[r0]; t < mp.c_ptr[r1]; ++t) c_pos[t] = (int32_t)pad_pos(m, mp.c_col[t]);
+  }
+  // interface and coarse occurrence lists (ascending subdomain)
+  std::vector<int64_t> iface_ptr(mp.n_iface + 1, 0), cinv_ptr(mp.n_coarse + 1, 0);
+  for (int64_t p = 0; p < L.n_vec; ++p)
+    if (loc2iface[p] >= 0) iface_ptr[loc2iface[p] + 1]++;
+  for (int64_t g = 0; g < mp.n_iface; ++g) iface_ptr[g + 1] += iface_ptr[g];
+  std::vector<int64_t> iface_occ(iface_ptr[mp.n_iface]);
+  {
+    std::vector<int64_t> fill(iface_ptr.begin(), iface_ptr.end() - 1);
+    for (int64_t p = 0; p < L.n_vec; ++p)
+      if (loc2iface[p] >= 0) iface_occ[fill[loc2iface[p]]++] = p;
+  }
+  std::vector<int32_t> sub_coarse(mp.sub_coarse.size());
+  for (size_t t = 0; t < mp.sub_coarse.size(); ++t) {
+    sub_coarse[t] = (int32_t)mp.sub_coarse[t];
+    cinv_ptr[mp.sub_coarse[t] + 1]++;
+  }
+  for (int64_t g = 0; g < mp.n_coarse; ++g) cinv_ptr[g + 1] += cinv_ptr[g];
+  std::vector<int64_t> cinv_occ(cinv_ptr[mp.n_coarse]);
+  {
+    std::vector<int64_t> fill(cinv_ptr.begin(), cinv_ptr.end() - 1);
+    for (size_t t = 0; t < mp.sub_coarse.size(); ++t) cinv_occ[fill[mp.sub_coarse[t]]++] = (int64_t)t;
+  }
+
+  // ---- upload
+  LevelDev& d = L.d;
+  d.n_sub = ns;
+  d.n_dof = ms.n_dof;
+  d.n_iface = mp.n_iface;
+  d.n_coarse = mp.n_coarse;
+  d.n_vec = L.n_vec;
+  d.meta = A.upload(L.meta, st);
+  d.row_ptr = A.upload(row_ptr, st);
+  d.col = A.upload(col, st);
+  d.val = A.alloc<double>(row_ptr[L.n_vec]);
+  d.ke_off = A.upload(ke_off, st);
+  d.ed_off = A.upload(ed_off, st);
+  d.eldof = A.upload(eldof, st);
+  d.ke = A.alloc<double>(ke_off[nel]);
+  d.rc_ptr = A.upload(rc_ptr, st);
+  d.rc_elem = A.upload(rc_elem, st);
+  d.rc_a = A.upload(rc_a, st);
+  d.c_ptr = A.upload(c_ptr, st);
+  d.c_pos = A.upload(c_pos, st);
+  d.c_val = A.upload(mp.c_val, st);
+  d.loc2iface = A.upload(loc2iface, st);
+  d.loc2glob = A.upload(loc2glob, st);
+  d.iface_ptr = A.upload(iface_ptr, st);
+  d.iface_occ = A.upload(iface_occ, st);
+  d.glob_occ_ptr = nullptr;
+  d.glob_occ = nullptr;
+  d.sub_coarse = A.upload(sub_coarse, st);
+  d.cinv_ptr = A.upload(cinv_ptr, st);
+  d.cinv_occ = A.upload(cinv_occ, st);
+  d.w = A.alloc<double>(L.n_vec);
+  d.diag = A.alloc<double>(L.n_vec);
+  d.rho = A.alloc<double>(ns);
+  d.Ginv = A.alloc<double>(L.g_elems);
+  d.KC = A.alloc<double>(L.g_elems);
+  const size_t ts = L.fp32 ? sizeof(float) : sizeof(double);
+  if (L.fp32) {
+    d.tiles = A.alloc<float>(L.tile_elems);
+    d.dinv = A.alloc<float>(L.dinv_elems);
+    d.psi = A.alloc<float>(L.psi_elems);
+    L.locA = A.alloc<float>(L.n_vec);
+    L.locB = A.alloc<float>(L.n_vec);
+  } else {
+    d.tiles = A.alloc<double>(L.tile_elems);
+    d.dinv = A.alloc<double>(L.dinv_elems);
+    d.psi = A.alloc<double>(L.psi_elems);
+    L.locA = A.alloc<double>(L.n_vec);
+    L.locB = A.alloc<double>(L.n_vec);
+  }
+  (void)ts;
+  d.status = h->d_status;
+  L.row_sub = A.upload(row_sub, st);
+  L.slot_elem = A.upload(slot_elem, st);
+  L.iface_dofs = A.upload(mp.iface_dofs, st);
+  L.dl0 = A.alloc<double>(L.n_vec);
+  L.dl1 = A.alloc<double>(L.n_vec);
+  L.dl2 = A.alloc<double>(L.n_vec);
+  L.dl3 = A.alloc<double>(L.n_vec);
+  L.rc_sub = A.alloc<double>(L.sum_nc);
+  L.zc_sub = A.alloc<double>(L.sum_nc);
+  L.rC = A.alloc<double>(mp.n_coarse);
+  L.zC = A.alloc<double>(mp.n_coarse);
+  L.gi0 = A.alloc<double>(mp.n_iface);
+  L.gi1 = A.alloc<double>(mp.n_iface);
+  L.gi2 = A.alloc<double>(mp.n_iface);
+  L.gv0 = A.alloc<double>(ms.n_dof);
+}
+
+// Element matrices of levels > 1 come from the previous level's K_Ci: segment copies.
+void prepare_level_segments(Level& L, const Level& prev, DevArena& A, cudaStream_t st) {
+  const int64_t nel = L.mesh.n_elems;
+  std::vector<int64_t> src(nel), len(nel);
+  std::vector<int32_t> slot_elem(nel);
+  for (int64_t s = 0; s < L.maps.n_sub(); ++s)
+    for (int64_t k = L.maps.sub_elem_ptr[s]; k < L.maps.sub_elem_ptr[s + 1]; ++k) slot_elem[k] = (int32_t)L.maps.sub_elems[k];
+  for (int64_t k = 0; k < nel; ++k) {
+    const SubMeta& pm = prev.meta[slot_elem[k]];
+    src[k] = pm.g_off;
+    len[k] = (int64_t)pm.nc * pm.nc;
+  }
+  L.seg_src = A.upload(src, st);
+  L.seg_len = A.upload(len, st);
+}
+
+// ------------------------------------------------------------------ numeric set-up
+template <typename T>
+void factor_level(bddc_handle_s* h, Level& L, cudaStream_t st) {
+  LevelDev& d = L.d;
+  launch_csr_values(d, L.n_vec, L.row_sub, st);
+  if (!L.coarsest) launch_weights(d, h->opts.weights == BDDC_WEIGHTS_MULTIPLICITY, nullptr, st);
+  ck(cudaMemsetAsync(d.tiles, 0, sizeof(T) * (size_t)std::max<int64_t>(L.tile_elems, 1), st), "memset tiles");
+  launch_densify_rows<T>(d, L.row_sub, st);
+  launch_add_constraints<T>(d, st);
+  for (int k = 0; k < L.max_Bc; ++k) {
+    ProfScope ps(h, BDDC_PROF_FACTOR, 0.0, L.step_flops[k]);
+    launch_potrf_step<T>(d, k, L.max_R, L.max_tiles[k], st);
+  }
+  if (L.max_nc > 0) {
+    launch_gram_chol(d, L.fp32 ? 1 : 0, L.max_nc, st);
+    launch_psi<T>(d, L.max_nGb, L.max_nc, st);
+  }
+  ck(cudaGetLastError(), "factor launch");
+}
+
+void check_status(bddc_handle_s* h, int level) {
+  int st[4];
+  ck(cudaMemcpyAsync(st, h->d_status, sizeof(st), cudaMemcpyDeviceToHost, h->st), "status");
+  ck(cudaStreamSynchronize(h->st), "sync");
+  if (st[0]) {
+    h->stats.breakdown_level = level;
+    h->stats.breakdown_sub = st[1];
+    fail(BDDC_ERR_BREAKDOWN, "non-positive pivot on level " + std::to_string(level) + " subdomain " +
+                                 std::to_string(st[1]));
+  }
+}
+
+void reset_status(bddc_handle_s* h) {
+  int init[4] = {0, 0x7fffffff, 0, 0};
+  ck(cudaMemcpyAsync(h->d_status, init, sizeof(init), cudaMemcpyHostToDevice, h->st), "status init");
+}
+
+// ------------------------------------------------------------------ solve-phase building blocks
+template <typename T>
+void trsv_one(bddc_handle_s* h, Level& L, T* v, int part, int backward, cudaStream_t st) {
+  ProfScope ps(h, BDDC_PROF_TRSV, L.trsv_bytes[part], 0.0);
+  launch_trsv<T>(L.d, v, part, backward, st);
+}
+
+template <typename T>
+void trsv_pair(bddc_handle_s* h, Level& L, T* v, int part, cudaStream_t st) {
+  trsv_one<T>(h, L, v, part, 0, st);
+  trsv_one<T>(h, L, v, part, 1, st);
+}
+
+// w = K_II^{-1} v on level 1 (interior positions), FP64 accuracy.
+// FP64 factors: two sweeps.  FP32 factors: iterative refinement with the FP64 K_II.
+void interior_solve_l1(bddc_handle_s* h, Level& L, const double* v, double* w, cudaStream_t st) {
+  const int64_t n = L.n_vec;
+  if (!L.fp32) {
+    ck(cudaMemcpyAsync(w, v, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
+    trsv_pair<double>(h, L, w, 0, st);
+    return;
+  }
+  float* t = (float*)L.locB;
+  double* r = L.dl3;
+  ck(cudaMemsetAsync(w, 0, sizeof(double) * n, st), "memset");
+  const int steps = std::max(1, h->refine_steps);
+  for (int it = 0; it < steps; ++it) {
+    launch_convert<double, float>(it == 0 ? v : r, t, n, st);
+    trsv_pair<float>(h, L, t, 0, st);
+    launch_add_to_double<float>(w, t, n, st);
+    if (it + 1 < steps) {
+      ck(cudaMemcpyAsync(r, v, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
+      launch_spmv_rows(L.d, 0, w, r, -1.0, 1.0, L.row_sub, st);
+    }
+  }
+}
+
+// y = S x on the level-1 interface (Sec. 2, discrete Dirichlet problems)
+void schur_apply(bddc_handle_s* h, const double* x, double* y, cudaStream_t st) {
+  Level& L = h->lv[0];
+  const int64_t n = L.n_vec;
+  launch_gather_iface<double>(L.d, x, 0, L.dl0, st);                 // x_i = R_i x
+  ck(cudaMemsetAsync(L.dl1, 0, sizeof(double) * n, st), "memset");
+  launch_spmv_rows(L.d, 0, L.dl0, L.dl1, 1.0, 0.0, L.row_sub, st);  // v = K_IG x_i
+  interior_solve_l1(h, L, L.dl1, L.dl2, st);                        // w = K_II^{-1} v
+  launch_axpy_loc(L.dl0, L.dl2, -1.0, n, st);                       // t = [-w ; x_i]
+  launch_spmv_rows(L.d, 1, L.dl0, L.dl1, 1.0, 0.0, L.row_sub, st);  // y_i = K_GG x_i - K_GI w
+  launch_scatter_iface<double>(L.d, L.dl1, 0, y, st);                // y = sum R_i^T y_i
+}
+
+// g = f_G - sum R_i^T K_GI K_II^{-1} f_I
+void condensed_rhs(bddc_handle_s* h, const double* f, double* g, cudaStream_t st) {
+  Level& L = h->lv[0];
+  launch_gather_glob<double>(L.d, f, 0, L.dl1, st);
+  interior_solve_l1(h, L, L.dl1, L.dl2, st);
+  launch_spmv_rows(L.d, 1, L.dl2, L.dl0, 1.0, 0.0, L.row_sub, st);
+  launch_scatter_iface<double>(L.d, L.dl0, 0, L.gi0, st);
+  launch_iface_rhs(g, f, L.iface_dofs, L.gi0, L.d.n_iface, st);
+}
+
+// u_I = K_II^{-1} (f_I - K_IG u_G), u_G = u_hat
+void recover(bddc_handle_s* h, const double* f, const double* uG, double* u, cudaStream_t st) {
+  Level& L = h->lv[0];
+  launch_gather_iface<double>(L.d, uG, 0, L.dl0, st);
+  launch_gather_glob<double>(L.d, f, 0, L.dl1, st);
+  launch_spmv_rows(L.d, 0, L.dl0, L.dl1, -1.0, 1.0, L.row_sub, st);
+  interior_solve_l1(h, L, L.dl1, L.dl2, st);
+  ck(cudaMemsetAsync(u, 0, sizeof(double) * h->n_free, st), "memset");
+  launch_scatter_interior<double>(L.d, L.dl2, u, st);
+  launch_put_indexed(u, L.iface_dofs, uG, L.d.n_iface, st);
+}
+
+void coarsest_solve(bddc_handle_s* h, const double* rC, double* zC, cudaStream_t st) {
+  Level& C = h->lv.back();
+  double* v = (double*)C.locA;
+  launch_gather_glob<double>(C.d, rC, 2, v, st);
+  trsv_pair<double>(h, C, v, 0, st);
+  launch_scatter_interior<double>(C.d, v, zC, st);
+}
+
+void full_step(bddc_handle_s* h, int l, const double* r, double* z, cudaStream_t st);
+
+// One interface step of Algorithm 2 on BDDC level l: distribute, subdomain corrections,
+// coarse residual, coarse correction (coarsest solve or the next level), combine.
+template <typename T>
+void interface_step_t(bddc_handle_s* h, int l, const double* rhat, double* zhat, cudaStream_t st) {
+  Level& L = h->lv[l];
+  T* v = (T*)L.locA;
+  launch_gather_iface<T>(L.d, rhat, 1, v, st);          // r_i = E_i^T r_hat
+  launch_psi_t_apply<T>(L.d, v, L.rc_sub, st);          // Psi_i^T r_i
+  launch_coarse_gather(L.d, L.rc_sub, L.rC, st);        // r_C = sum R_Ci^T Psi_i^T r_i
+  trsv_one<T>(h, L, v, 1, 0, st);                       // Eq. sub_cor via the trailing factor
+  launch_constraint_corr<T>(L.d, v, L.max_nc, st);
+  trsv_one<T>(h, L, v, 1, 1, st);
+  const bool last = l + 2 == (int)h->lv.size();
+  if (last)
+    coarsest_solve(h, L.rC, L.zC, st);
+  else
+    full_step(h, l + 1, L.rC, L.zC, st);
+  launch_coarse_scatter_n(L.d.sub_coarse, L.sum_nc, L.zC, L.zc_sub, st);
+  launch_psi_apply_add<T>(L.d, L.zc_sub, v, L.max_nG, st);   // Psi_i R_Ci z_C + z_i
+  launch_scatter_iface<T>(L.d, v, 1, zhat, st);            // z_hat = sum E_i (...)
+}
+
+void interface_step(bddc_handle_s* h, int l, const double* rhat, double* zhat, cudaStream_t st) {
+  if (h->lv[l].fp32)
+    interface_step_t<float>(h, l, rhat, zhat, st);
+  else
+    interface_step_t<double>(h, l, rhat, zhat, st);
+}
+
+// Levels l > 1: interior pre-correction, interface step, interior post-correction
+template <typename T>
+void full_step_t(bddc_handle_s* h, int l, const double* r, double* z, cudaStream_t st) {
+  Level& L = h->lv[l];
+  const int64_t n = L.n_vec;
+  T* v = (T*)L.locB;
+  launch_gather_glob<T>(L.d, r, 0, v, st);                  // r_I
+  trsv_pair<T>(h, L, v, 0, st);                                // u1 = A_II^{-1} r_I
+  launch_convert<T, double>(v, L.dl0, n, st);
+  launch_spmv_rows(L.d, 1, L.dl0, L.dl1, 1.0, 0.0, L.row_sub, st);   // (A_GI u1)_i
+  launch_scatter_iface<double>(L.d, L.dl1, 0, L.gi0, st);
+  launch_iface_rhs(L.gi1, r, L.iface_dofs, L.gi0, L.d.n_iface, st); // r'_G = r_G - A_GI u1
+  interface_step(h, l, L.gi1, L.gi2, st);                             // z_G
+  launch_gather_iface<double>(L.d, L.gi2, 0, L.dl0, st);
+  launch_gather_glob<double>(L.d, r, 0, L.dl1, st);
+  launch_spmv_rows(L.d, 0, L.dl0, L.dl1, -1.0, 1.0, L.row_sub, st);  // r_I - A_IG z_G
+  launch_convert<double, T>(L.dl1, v, n, st);
+  trsv_pair<T>(h, L, v, 0, st);                                           // z_I
+  ck(cudaMemsetAsync(z, 0, sizeof(double) * L.d.n_dof, st), "memset");
+  launch_scatter_interior<T>(L.d, v, z, st);
+  launch_put_indexed(z, L.iface_dofs, L.gi2, L.d.n_iface, st);
+}
+
+void full_step(bddc_handle_s* h, int l, const double* r, double* z, cudaStream_t st) {
+  if (h->lv[l].fp32)
+    full_step_t<float>(h, l, r, z, st);
+  else
+    full_step_t<double>(h, l, r, z, st);
+}
+
+void precond(bddc_handle_s* h, const double* r, double* z, cudaStream_t st) { interface_step(h, 0, r, z, st); }
+
+double dot_host(bddc_handle_s* h, const double* a, const double* b, int64_t n) {
+  launch_dot(a, b, n, h->partial, kDotBlocks, h->scal + 15, h->st);
+  ck(cudaMemcpyAsync(h->h_scal + 15, h->scal + 15, sizeof(double), cudaMemcpyDeviceToHost, h->st), "d2h");
+  ck(cudaStreamSynchronize(h->st), "sync");
+  return h->h_scal[15];
+}
+
+// Choose the number of FP64 refinement steps of the interior solves (FP32 factors): run the
+// refinement on a probe right-hand side until the FP64 residual stops decreasing.
+void choose_refinement(bddc_handle_s* h) {
+  Level& L = h->lv[0];
+  if (!L.fp32) {
+    h->refine_steps = 0;
+    return;
+  }
+  if (h->opts.refine_steps > 0) {
+    h->refine_steps = h->opts.refine_steps;
+    return;
+  }
+  cudaStream_t st = h->st;
+  const int64_t n = L.n_vec;
+  std::vector<double> ones(L.d.n_iface, 1.0);
+  ck(cudaMemcpyAsync(L.gi1, ones.data(), sizeof(double) * ones.size(), cudaMemcpyHostToDevice, st), "h2d");
+  launch_gather_iface<double>(L.d, L.gi1, 0, L.dl0, st);
+  double* v = h->full_a;   // n_vec-sized scratch allocated for this purpose
+  double* w = h->full_b;
+  ck(cudaMemsetAsync(v, 0, sizeof(double) * n, st), "memset");
+  launch_spmv_rows(L.d, 0, L.dl0, v, 1.0, 0.0, L.row_sub, st);
+  const double nv = std::sqrt(dot_host(h, v, v, n));
+  int best = 1;
+  double prev = 1e300;
+  for (int steps = 1; steps <= 8; ++steps) {
+    h->refine_steps = steps;
+    interior_solve_l1(h, L, v, w, st);
+    ck(cudaMemcpyAsync(L.dl3, v, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
+    launch_spmv_rows(L.d, 0, w, L.dl3, -1.0, 1.0, L.row_sub, st);
+    const double rel = nv > 0 ? std::sqrt(dot_host(h, L.dl3, L.dl3, n)) / nv : 0.0;
+    best = steps;
+    if (rel < 4e-16 || rel > 0.5 * prev) break;
+    prev = rel;
+  }
+  h->refine_steps = best;
+}
+
+void numeric_setup(bddc_handle_s* h) {
+  cudaStream_t st = h->st;
+  const double t0 = now_ms();
+  reset_status(h);
+  ck(cudaMemcpyAsync(h->d_coef, h->coef.data(), sizeof(double) * h->n_elems, cudaMemcpyHostToDevice, st), "coef");
+  for (size_t l = 0; l < h->lv.size(); ++l) {
+    Level& L = h->lv[l];
+    if (l == 0) {
+      launch_elem_q1(h->physics, h->dim, h->n_elems, h->d_coords, h->d_conn, h->d_coef, h->nu, L.slot_elem,
+                     L.d.ke, st);
+    } else {
+      const Level& P = h->lv[l - 1];
+      std::vector<int64_t> dummy;
+      launch_copy_segments(P.d.KC, L.seg_src, L.d.ke, L.d.ke_off, L.seg_len, L.mesh.n_elems, st);
+    }
+    if (L.fp32)
+      factor_level<float>(h, L, st);
+    else
+      factor_level<double>(h, L, st);
+    check_status(h, (int)l + 1);
+  }
+  choose_refinement(h);
+  ck(cudaStreamSynchronize(st), "sync");
+  h->stats.factor_ms = now_ms() - t0;
+  flush_profile(h);
+  h->stats.refine_steps = h->refine_steps;
+  h->factored = true;
+}
+
+void analysis(bddc_handle_s* h, const bddc_mesh* mesh, const bddc_partition* part) {
+  const double t0 = now_ms();
+  if (!mesh || !part) fail(BDDC_ERR_INVALID, "null mesh or partition");
+  if (mesh->dim != 2 && mesh->dim != 3) fail(BDDC_ERR_INVALID, "dim must be 2 or 3");
+  if (mesh->nodes_per_elem != (1 << mesh->dim)) fail(BDDC_ERR_INVALID, "only Q1 elements (2**dim nodes)");
+  if (mesh->physics == BDDC_ELASTICITY && (mesh->dim != 3 || mesh->dofs_per_node != 3))
+    fail(BDDC_ERR_INVALID, "elasticity needs dim 3 and 3 DOFs per node");
+  if (mesh->physics == BDDC_POISSON && mesh->dofs_per_node != 1) fail(BDDC_ERR_INVALID, "Poisson needs 1 DOF per node");
+  if (mesh->physics != BDDC_POISSON && mesh->physics != BDDC_ELASTICITY) fail(BDDC_ERR_INVALID, "unknown physics");
+  if (part->n_levels < 2 || part->n_levels > BDDC_MAX_LEVELS) fail(BDDC_ERR_INVALID, "n_levels out of range");
+  if (mesh->n_nodes <= 0 || mesh->n_elems <= 0 || !mesh->coords || !mesh->conn || !mesh->coef || !mesh->dirichlet)
+    fail(BDDC_ERR_INVALID, "empty mesh or null array");
+  h->dim = mesh->dim;
+  h->npe = mesh->nodes_per_elem;
+  h->ndof = mesh->dofs_per_node;
+  h->physics = mesh->physics;
+  h->n_nodes = mesh->n_nodes;
+  h->n_elems = mesh->n_elems;
+  h->nu = mesh->nu;
+  h->n_full = h->n_nodes * h->ndof;
+  h->coords.assign(mesh->coords, mesh->coords + h->n_nodes * h->dim);
+  h->conn.assign(mesh->conn, mesh->conn + h->n_elems * h->npe);
+  h->coef.assign(mesh->coef, mesh->coef + h->n_elems);
+  for (int64_t e = 0; e < h->n_elems; ++e)
+    if (!(h->coef[e] > 0.0)) fail(BDDC_ERR_INVALID, "coefficient must be positive (element " + std::to_string(e) + ")");
+  for (int32_t p : h->conn)
+    if (p < 0 || p >= h->n_nodes) fail(BDDC_ERR_INVALID, "connectivity references a missing node");
+  h->free_of_full.assign(h->n_full, -1);
+  h->n_free = 0;
+  for (int64_t q = 0; q < h->n_full; ++q)
+    if (!mesh->dirichlet[q]) h->free_of_full[q] = h->n_free++;
+  h->n_levels = part->n_levels;
+  h->parts.clear();
+  h->n_parts.clear();
+  for (int l = 0; l + 1 < h->n_levels; ++l) {
+    if (!part->part[l] || part->n_parts[l] <= 0) fail(BDDC_ERR_INVALID, "missing partition of level " + std::to_string(l + 1));
+    const int64_t n_items = l == 0 ? h->n_elems : h->n_parts[l - 1];
+    h->parts.emplace_back(part->part[l], part->part[l] + n_items);
+    h->n_parts.push_back(part->n_parts[l]);
+  }
+  h->lv.clear();
+  h->lv.resize(h->n_levels);   // L-1 BDDC levels + coarsest
+  std::string err;
+  for (int l = 0; l + 1 < h->n_levels; ++l) {
+    Level& L = h->lv[l];
+    if (l == 0)
+      build_level1_mesh(h, &L.mesh);
+    else
+      next_level_mesh(h->lv[l - 1].mesh, h->lv[l - 1].maps, h->parts[l].data(), h->n_parts[l], &L.mesh);
+    const bool allc = (h->opts.all_corners >> l) & 1u;
+    if (!analyze_level(L.mesh, h->constraints, allc, &L.maps, &err)) fail(BDDC_ERR_INVALID, "level " + std::to_string(l + 1) + ": " + err);
+    L.fp32 = h->opts.precision == BDDC_PREC_MIXED;
+    h->stats.n_sub[l] = L.maps.n_sub();
+    h->stats.n_dof[l] = L.mesh.n_dof;
+    h->stats.n_iface[l] = L.maps.n_iface;
+    h->stats.n_coarse[l] = L.maps.n_coarse;
+    h->stats.n_promoted[l] = L.maps.n_promoted;
+  }
+  Level& C = h->lv.back();
+  C.coarsest = true;
+  C.fp32 = false;
+  build_coarsest_mesh(h->lv[h->n_levels - 2], &C.mesh);
+  if (!analyze_level(C.mesh, 0u, false, &C.maps, &err)) fail(BDDC_ERR_INVALID, "coarsest level: " + err);
+  h->stats.n_levels = h->n_levels;
+  h->stats.analysis_ms = now_ms() - t0;
+}
+
+void device_setup(bddc_handle_s* h) {
+  cudaStream_t st = h->st;
+  DevArena& A = h->arena;
+  h->d_status = A.alloc<int>(4);
+  h->d_coords = A.upload(h->coords, st);
+  h->d_conn = A.upload(h->conn, st);
+  h->d_coef = A.alloc<double>(h->n_elems);
+  h->d_free_of_full = A.upload(h->free_of_full, st);
+  {
+    const int ne = h->npe * h->ndof;
+    std::vector<int64_t> edof((size_t)h->n_elems * ne);
+    for (int64_t e = 0; e < h->n_elems; ++e)
+      for (int a = 0; a < h->npe; ++a)
+        for (int c = 0; c < h->ndof; ++c)
+          edof[(size_t)e * ne + a * h->ndof + c] = (int64_t)h->conn[e * h->npe + a] * h->ndof + c;
+    h->d_edof = A.upload(edof, st);
+  }
+  for (size_t l = 0; l < h->lv.size(); ++l) {
+    prepare_level(h, h->lv[l], A, st);
+    if (l > 0) prepare_level_segments(h->lv[l], h->lv[l - 1], A, st);
+  }
+  h->scal = A.alloc<double>(16);
+  h->partial = A.alloc<double>(kDotBlocks);
+  ck(cudaMallocHost(&h->h_scal, sizeof(double) * 16), "cudaMallocHost");
+  const int64_t ni = std::max<int64_t>(h->lv[0].d.n_iface, 1);
+  h->vx = A.alloc<double>(ni);
+  h->vr = A.alloc<double>(ni);
+  h->vz = A.alloc<double>(ni);
+  h->vp = A.alloc<double>(ni);
+  h->vq = A.alloc<double>(ni);
+  h->vrold = A.alloc<double>(ni);
+  h->vg = A.alloc<double>(ni);
+  h->fcol = A.alloc<double>(h->n_free);
+  h->ucol = A.alloc<double>(h->n_free);
+  const int64_t nbig = std::max<int64_t>(h->n_full, h->lv[0].n_vec);
+  h->full_a = A.alloc<double>(nbig);
+  h->full_b = A.alloc<double>(nbig);
+  ck(cudaStreamSynchronize(st), "sync");
+}
+
+// ------------------------------------------------------------------ PCG (Sec. 4)
+struct PcgResult {
+  int iterations = 0;
+  bool converged = false;
+  double rel = 0.0;
+  std::vector<double> alpha, beta;
+};
+
+PcgResult pcg(bddc_handle_s* h, const double* g, double* x, double tol, int maxit) {
+  cudaStream_t st = h->st;
+  const int64_t n = h->lv[0].d.n_iface;
+  PcgResult res;
+  const int flexible = h->opts.flexible < 0 ? (h->opts.precision == BDDC_PREC_MIXED) : h->opts.flexible;
+  ck(cudaMemsetAsync(x, 0, sizeof(double) * n, st), "memset");
+  if (n == 0) {
+    res.converged = true;
+    return res;
+  }
+  double* S = h->scal;
+  ck(cudaMemsetAsync(S, 0, sizeof(double) * 16, st), "memset");
+  launch_dot(g, g, n, h->partial, kDotBlocks, S + 6, st);
+  ck(cudaMemcpyAsync(h->vr, g, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
+  precond(h, h->vr, h->vz, st);
+  ck(cudaMemcpyAsync(h->vp, h->vz, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
+  launch_dot(h->vr, h->vz, n, h->partial, kDotBlocks, S + 0, st);
+  ck(cudaMemcpyAsync(h->h_scal, S, sizeof(double) * 16, cudaMemcpyDeviceToHost, st), "d2h");
+  ck(cudaStreamSynchronize(st), "sync");
+  const double gg = h->h_scal[6];
+  if (!std::isfinite(gg)) fail(BDDC_ERR_NAN, "NaN in the condensed right-hand side");
+  if (gg == 0.0) {
+    res.converged = true;
+    return res;
+  }
+  bool checked = false;
+  for (int it = 1; it <= maxit; ++it) {
+    schur_apply(h, h->vp, h->vq, st);                               // q = S p
+    launch_dot(h->vp, h->vq, n, h->partial, kDotBlocks, S + 1, st);
+    launch_pcg_scalars(S, 0, flexible, st);                          // alpha = rz / pq
+    if (flexible) ck(cudaMemcpyAsync(h->vrold, h->vr, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
+    launch_pcg_update_x_r(x, h->vr, h->vp, h->vq, S, n, st);
+    launch_dot(h->vr, h->vr, n, h->partial, kDotBlocks, S + 5, st);
+    ck(cudaMemcpyAsync(h->h_scal, S, sizeof(double) * 16, cudaMemcpyDeviceToHost, st), "d2h");
+    ck(cudaStreamSynchronize(st), "sync");
+    res.iterations = it;
+    res.alpha.push_back(h->h_scal[2]);
+    double rel = std::sqrt(h->h_scal[5] / gg);
+    if (!std::isfinite(rel)) fail(BDDC_ERR_NAN, "NaN in the Krylov recurrence");
+    if (rel <= tol) {
+      schur_apply(h, x, h->vq, st);                                 // true residual g - S x
+      ck(cudaMemcpyAsync(h->vr, g, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
+      launch_axpy_loc(h->vr, h->vq, -1.0, n, st);
+      launch_dot(h->vr, h->vr, n, h->partial, kDotBlocks, S + 5, st);
+      ck(cudaMemcpyAsync(h->h_scal + 5, S + 5, sizeof(double), cudaMemcpyDeviceToHost, st), "d2h");
+      ck(cudaStreamSynchronize(st), "sync");
+      const double rel_true = std::sqrt(h->h_scal[5] / gg);
+      if (rel_true <= tol || checked) {
+        res.rel = rel_true;
+        res.converged = rel_true <= tol;
+        return res;
+      }
+      checked = true;
+      rel = rel_true;
+    }
+    res.rel = rel;
+    precond(h, h->vr, h->vz, st);                                    // z = M^{-1} r
+    launch_dot(h->vr, h->vz, n, h->partial, kDotBlocks, S + 4, st);
+    if (flexible) launch_dot(h->vz, h->vrold, n, h->partial, kDotBlocks, S + 7, st);
+    launch_pcg_scalars(S, 1, flexible, st);                          // beta
+    launch_pcg_update_p(h->vp, h->vz, S, n, st);
+    ck(cudaMemcpyAsync(h->h_scal + 3, S + 3, sizeof(double), cudaMemcpyDeviceToHost, st), "d2h");
+    ck(cudaStreamSynchronize(st), "sync");
+    res.beta.push_back(h->h_scal[3]);
+  }
+  return res;
+}
+
+void lanczos(const PcgResult& r, double* lmin, double* lmax) {
+  const int k = (int)r.alpha.size();
+  *lmin = *lmax = 1.0;
+  if (k == 0) return;
+  // tridiagonal eigenvalues by bisection (Sturm sequence)
+  std::vector<double> a(k), b(k, 0.0);
+  for (int j = 0; j < k; ++j) {
+    a[j] = 1.0 / r.alpha[j] + (j > 0 && j - 1 < (int)r.beta.size() ? r.beta[j - 1] / r.alpha[j - 1] : 0.0);
+    if (j + 1 < k && j < (int)r.beta.size()) b[j] = std::sqrt(std::max(r.beta[j], 0.0)) / r.alpha[j];
+  }
+  double lo = 1e300, hi = -1e300;
+  for (int j = 0; j < k; ++j) {
+    double rad = (j > 0 ? std::fabs(b[j - 1]) : 0.0) + std::fabs(b[j]);
+    lo = std::min(lo, a[j] - rad);
+    hi = std::max(hi, a[j] + rad);
+  }
+  auto count_below = [&](double x) {
+    int cnt = 0;
+    double d = 1.0;
+    for (int j = 0; j < k; ++j) {
+      d = a[j] - x - (j > 0 ? b[j - 1] * b[j - 1] / d : 0.0);
+      if (d == 0.0) d = -1e-300;
+      if (d < 0) ++cnt;
+    }
+    return cnt;
+  };
+  auto kth = [&](int idx) {
+    double l = lo, u = hi;
+    for (int it = 0; it < 200; ++it) {
+      double mid = 0.5 * (l + u);
+      if (count_below(mid) > idx) u = mid; else l = mid;
+    }
+    return 0.5 * (l + u);
+  };
+  *lmin = kth(0);
+  *lmax = kth(k - 1);
+}
+
+int solve_impl(bddc_handle_s* h, const double* rhs, double* x, int nrhs, double tol, bddc_stats* stats) {
+  if (!h->factored) fail(BDDC_ERR_INVALID, "handle has no numeric set-up");
+  if (nrhs < 1) fail(BDDC_ERR_INVALID, "nrhs must be >= 1");
+  if (!(tol > 0.0)) fail(BDDC_ERR_INVALID, "tol must be positive");
+  cudaStream_t st = h->st;
+  const double t0 = now_ms();
+  int maxits = 0;
+  bool all_conv = true;
+  double worst = 0.0;
+  PcgResult first;
+  for (int k = 0; k < nrhs; ++k) {
+    const double* f = rhs + (int64_t)k * h->n_free;
+    double* u = x + (int64_t)k * h->n_free;
+    condensed_rhs(h, f, h->vg, st);
+    PcgResult r = pcg(h, h->vg, h->vx, tol, h->opts.maxit);
+    recover(h, f, h->vx, u, st);
+    maxits = std::max(maxits, r.iterations);
+    all_conv = all_conv && r.converged;
+    worst = std::max(worst, r.rel);
+    if (k == 0) first = r;
+  }
+  ck(cudaStreamSynchronize(st), "sync");
+  h->stats.iterations = maxits;
+  h->stats.converged = all_conv ? 1 : 0;
+  h->stats.rel_residual = worst;
+  lanczos(first, &h->stats.lambda_min, &h->stats.lambda_max);
+  h->stats.solve_ms = now_ms() - t0;
+  h->stats.factor_bytes = h->arena.bytes;
+  flush_profile(h);
+  if (stats) *stats = h->stats;
+  if (!all_conv) {
+    g_err = "Krylov iteration cap reached";
+    return BDDC_ERR_NOT_CONVERGED;
+  }
+  return BDDC_OK;
+}
+
+template <typename F>
+int guarded(F&& fn) {
+  try {
+    g_err.clear();
+    return fn();
+  } catch (const Fail& f) {
+    return f.code;
+  } catch (const std::exception& e) {
+    g_err = e.what();
+    return BDDC_ERR_INVALID;
+  }
+}
+
+}  // namespace
+}  // namespace bddc
+
+// ====================================================================== C ABI
+extern "C" {
+
+void bddc_default_opts(bddc_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = BDDC_PREC_MIXED;
+  o->weights = BDDC_WEIGHTS_STIFFNESS;
+  o->all_corners = 0;
+  o->maxit = 500;
+  o->refine_steps = 0;
+  o->flexible = -1;
+  o->use_graph = 1;
+  o->verbose = 0;
+}
+
+int bddc_analyze(const bddc_mesh* mesh, const bddc_partition* part, unsigned constraints, const bddc_opts* opts,
+                 bddc_handle* out) {
+  return guarded([&]() {
+    if (!out) fail(BDDC_ERR_INVALID, "null output handle");
+    *out = nullptr;
+    auto* h = new bddc_handle_s();
+    if (opts) h->opts = *opts; else bddc_default_opts(&h->opts);
+    h->constraints = constraints;
+    h->analysis_only = true;
+    try {
+      analysis(h, mesh, part);
+    } catch (...) {
+      delete h;
+      throw;
+    }
+    *out = h;
+    return BDDC_OK;
+  });
+}
+
+int bddc_setup(const bddc_mesh* mesh, const bddc_partition* part, unsigned constraints, const bddc_opts* opts,
+               void* stream, bddc_handle* out) {
+  return guarded([&]() {
+    if (!out) fail(BDDC_ERR_INVALID, "null output handle");
+    *out = nullptr;
+    auto* h = new bddc_handle_s();
+    if (opts) h->opts = *opts; else bddc_default_opts(&h->opts);
+    if (h->opts.maxit <= 0) h->opts.maxit = 500;
+    h->constraints = constraints;
+    h->st = (cudaStream_t)stream;
+    try {
+      analysis(h, mesh, part);
+      device_setup(h);
+      numeric_setup(h);
+    } catch (...) {
+      h->arena.release();
+      if (h->h_scal) cudaFreeHost(h->h_scal);
+      delete h;
+      throw;
+    }
+    *out = h;
+    return BDDC_OK;
+  });
+}
+
+int bddc_update_coef(bddc_handle h, const double* coef) {
+  return guarded([&]() {
+    if (!h || h->analysis_only || !coef) fail(BDDC_ERR_INVALID, "bad handle or coefficients");
+    for (int64_t e = 0; e < h->n_elems; ++e)
+      if (!(coef[e] > 0.0)) fail(BDDC_ERR_INVALID, "coefficient must be positive");
+    h->coef.assign(coef, coef + h->n_elems);
+    h->factored = false;
+    numeric_setup(h);
+    return BDDC_OK;
+  });
+}
+
+int bddc_solve(bddc_handle h, const double* rhs, double* x, int nrhs, double tol, bddc_stats* stats) {
+  return guarded([&]() {
+    if (!h || h->analysis_only || !rhs || !x) fail(BDDC_ERR_INVALID, "bad handle or vectors");
+    return solve_impl(h, rhs, x, nrhs, tol, stats);
+  });
+}
+
+int bddc_solve_host(bddc_handle h, const double* rhs_host, double* x_host, int nrhs, double tol, bddc_stats* stats) {
+  return guarded([&]() {
+    if (!h || h->analysis_only || !rhs_host || !x_host) fail(BDDC_ERR_INVALID, "bad handle or vectors");
+    const size_t bytes = sizeof(double) * (size_t)h->n_free * (size_t)nrhs;
+    double *dr = nullptr, *dx = nullptr;
+    ck(cudaMallocAsync(&dr, bytes, h->st), "cudaMallocAsync");
+    ck(cudaMallocAsync(&dx, bytes, h->st), "cudaMallocAsync");
+    int rc;
+    try {
+      ck(cudaMemcpyAsync(dr, rhs_host, bytes, cudaMemcpyHostToDevice, h->st), "h2d");
+      rc = solve_impl(h, dr, dx, nrhs, tol, stats);
+      ck(cudaMemcpyAsync(x_host, dx, bytes, cudaMemcpyDeviceToHost, h->st), "d2h");
+      ck(cudaStreamSynchronize(h->st), "sync");
+    } catch (...) {
+      cudaFreeAsync(dr, h->st);
+      cudaFreeAsync(dx, h->st);
+      throw;
+    }
+    cudaFreeAsync(dr, h->st);
+    cudaFreeAsync(dx, h->st);
+    return rc;
+  });
+}
+
+int bddc_apply_precond(bddc_handle h, const double* r, double* z, int nrhs) {
+  return guarded([&]() {
+    if (!h || !h->factored || !r || !z || nrhs < 1) fail(BDDC_ERR_INVALID, "bad arguments");
+    const int64_t n = h->lv[0].d.n_iface;
+    for (int k = 0; k < nrhs; ++k) precond(h, r + k * n, z + k * n, h->st);
+    ck(cudaStreamSynchronize(h->st), "sync");
+    return BDDC_OK;
+  });
+}
+
+int bddc_apply_schur(bddc_handle h, const double* x, double* y, int nrhs) {
+  return guarded([&]() {
+    if (!h || !h->factored || !x || !y || nrhs < 1) fail(BDDC_ERR_INVALID, "bad arguments");
+    const int64_t n = h->lv[0].d.n_iface;
+    for (int k = 0; k < nrhs; ++k) schur_apply(h, x + k * n, y + k * n, h->st);
+    ck(cudaStreamSynchronize(h->st), "sync");
+    return BDDC_OK;
+  });
+}
+
+int bddc_grad(bddc_handle h, const double* dJdu, const double* u, int nrhs, double tol, double* grad_coef,
+              double* grad_rhs) {
+  return guarded([&]() {
+    if (!h || !h->factored || !dJdu || !u || nrhs < 1) fail(BDDC_ERR_INVALID, "bad arguments");
+    cudaStream_t st = h->st;
+    const size_t bytes = sizeof(double) * (size_t)h->n_free * nrhs;
+    double* lam = grad_rhs;
+    double* own = nullptr;
+    if (!lam) {
+      ck(cudaMallocAsync(&own, bytes, st), "cudaMallocAsync");
+      lam = own;
+    }
+    int rc;
+    try {
+      rc = solve_impl(h, dJdu, lam, nrhs, tol, nullptr);   // K lambda = dJ/du (K symmetric)
+      if (grad_coef && (rc == BDDC_OK || rc == BDDC_ERR_NOT_CONVERGED)) {
+        double *lf = nullptr, *uf = nullptr;
+        const size_t fb = sizeof(double) * (size_t)h->n_full * nrhs;
+        ck(cudaMallocAsync(&lf, fb, st), "cudaMallocAsync");
+        ck(cudaMallocAsync(&uf, fb, st), "cudaMallocAsync");
+        launch_expand_free(lam, h->d_free_of_full, h->n_full, nrhs, h->n_free, lf, st);
+        launch_expand_free(u, h->d_free_of_full, h->n_full, nrhs, h->n_free, uf, st);
+        const Level& L = h->lv[0];
+        launch_grad_contract_slots(h->n_elems, h->npe * h->ndof, L.d.ke, L.slot_elem, h->d_coef, h->d_edof, lf, uf,
+                                   nrhs, h->n_full, grad_coef, st);
+        cudaFreeAsync(lf, st);
+        cudaFreeAsync(uf, st);
+      }
+      ck(cudaStreamSynchronize(st), "sync");
+    } catch (...) {
+      if (own) cudaFreeAsync(own, st);
+      throw;
+    }
+    if (own) cudaFreeAsync(own, st);
+    return rc;
+  });
+}
+
+int bddc_get_maps(bddc_handle h, int level, bddc_level_maps* out) {
+  return guarded([&]() {
+    if (!h || !out || level < 1 || level >= (int)h->lv.size()) fail(BDDC_ERR_INVALID, "bad level");
+    const Level& L = h->lv[level - 1];
+    const LevelMaps& m = L.maps;
+    out->n_dof = L.mesh.n_dof;
+    out->n_sub = m.n_sub();
+    out->n_iface = m.n_iface;
+    out->n_coarse = m.n_coarse;
+    out->n_globs = m.n_globs();
+    out->n_promoted = m.n_promoted;
+    out->iface_dofs = m.iface_dofs.data();
+    out->sub_dof_ptr = m.sub_dof_ptr.data();
+    out->sub_dofs = m.sub_dofs.data();
+    out->sub_nI = m.sub_nI.data();
+    out->sub_iface = m.sub_iface.data();
+    out->sub_wmult = m.sub_wmult.data();
+    out->sub_coarse_ptr = m.sub_coarse_ptr.data();
+    out->sub_coarse = m.sub_coarse.data();
+    out->c_ptr = m.c_ptr.data();
+    out->c_col = m.c_col.data();
+    out->c_val = m.c_val.data();
+    out->glob_ptr = m.glob_ptr.data();
+    out->glob_nodes = m.glob_nodes.data();
+    out->glob_kind = m.glob_kind.data();
+    out->glob_promoted = m.glob_promoted.data();
+    out->coarse_glob = m.coarse_glob.data();
+    out->coarse_comp = m.coarse_comp.data();
+    return BDDC_OK;
+  });
+}
+
+int bddc_get_stats(bddc_handle h, bddc_stats* out) {
+  return guarded([&]() {
+    if (!h || !out) fail(BDDC_ERR_INVALID, "bad arguments");
+    flush_profile(h);
+    *out = h->stats;
+    return BDDC_OK;
+  });
+}
+
+int bddc_reset_profile(bddc_handle h) {
+  return guarded([&]() {
+    if (!h) fail(BDDC_ERR_INVALID, "null handle");
+    flush_profile(h);
+    for (int c = 0; c < BDDC_PROF_CLASSES; ++c) {
+      h->stats.prof_ms[c] = 0.0;
+      h->stats.prof_launches[c] = 0;
+      h->stats.prof_bytes[c] = 0.0;
+      h->stats.prof_flops[c] = 0.0;
+    }
+    return BDDC_OK;
+  });
+}
+
+int64_t bddc_kernel_launches(void) { return g_launches.load(); }
+
+int bddc_sizes(bddc_handle h, int64_t* n_free, int64_t* n_iface) {
+  return guarded([&]() {
+    if (!h) fail(BDDC_ERR_INVALID, "null handle");
+    if (n_free) *n_free = h->n_free;
+    if (n_iface) *n_iface = h->lv.empty() ? 0 : h->lv[0].maps.n_iface;
+    return BDDC_OK;
+  });
+}
+
+void bddc_free(bddc_handle h) {
+  if (!h) return;
+  if (h->st) cudaStreamSynchronize(h->st);
+  h->arena.release();
+  if (h->h_scal) cudaFreeHost(h->h_scal);
+  delete h;
+}
+
+const char* bddc_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

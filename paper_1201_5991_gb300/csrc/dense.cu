@@ -1,0 +1,569 @@
+// Dense per-subdomain kernels, batched over all subdomains of a level.
+//
+//  * Partial Cholesky of the augmented matrix [A_i; C_i], A_i = K_i + rho C_i^T C_i
+//    (right-looking, NB x NB tiles): gives L_i (A_i = L_i L_i^T) and Y_i = C_i L_i^{-T}.
+//    With the local order (interior, interface) the leading block of L_i factors K_II
+//    ("prepare interior correction", Algorithm 1) and the trailing block factors the
+//    constrained Neumann problem of Eq. psi_def / Eq. sub_cor restricted to the interface.
+//  * G_i = Y_i Y_i^T = C_i A_i^{-1} C_i^T (FP64), its Cholesky factor and inverse;
+//    Psi_i = A_i^{-1} C_i^T G_i^{-1} (so C_i Psi_i = I and K_i Psi_i = -C_i^T Lambda_i with
+//    Lambda_i = rho I - G_i^{-1}), K_Ci = Psi_i^T K_i Psi_i = -Lambda_i = G_i^{-1} - rho I.
+//  * Streaming forward / backward triangular solves with the tiles (per Krylov iteration).
+#include "internal.h"
+
+namespace bddc {
+
+namespace {
+
+__device__ __forceinline__ int64_t tile_index(int i, int j, int Bc) {
+  return i < Bc ? ((int64_t)i * (i + 1) / 2 + j) : ((int64_t)Bc * (Bc + 1) / 2 + (int64_t)(i - Bc) * Bc + j);
+}
+
+template <typename T>
+__device__ __forceinline__ T* tile_ptr(const SubMeta& m, void* base, int i, int j) {
+  return (T*)base + m.tile_off + tile_index(i, j, m.Bc) * NB2;
+}
+
+__device__ __forceinline__ void flag_breakdown(int* status, int sub) {
+  atomicExch(status + 0, 1);
+  atomicMin(status + 1, sub);
+}
+
+constexpr int LDS = NB + 4;   // k-major shared tile stride (multiple of 4 for vector loads)
+
+template <typename T>
+__device__ __forceinline__ void load_kmajor(T* s, const T* __restrict__ g) {
+  // s[m * LDS + r] = g[r * NB + m]
+  for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
+    const int r = t / NB, m = t % NB;
+    s[m * LDS + r] = g[t];
+  }
+}
+
+// acc[i][j] += sum_m A[4ty+i][m] * B[4tx+j][m] with both operands k-major in shared memory
+template <typename T>
+__device__ __forceinline__ void gemm_nt_4x4(const T* As, const T* Bs, T acc[4][4], int tx, int ty) {
+#pragma unroll 8
+  for (int m = 0; m < NB; ++m) {
+    T a[4], b[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      a[q] = As[m * LDS + 4 * ty + q];
+      b[q] = Bs[m * LDS + 4 * tx + q];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+  }
+}
+
+// ---- step k, part 1: factor the diagonal tile and invert it -------------------------------
+template <typename T>
+__global__ void k_potrf_diag(LevelDev L, int k) {
+  const int s = blockIdx.x;
+  const SubMeta m = L.meta[s];
+  if (k >= m.Bc) return;
+  __shared__ T A[NB][NB + 1];
+  __shared__ int bad;
+  T* g = tile_ptr<T>(m, L.tiles, k, k);
+  for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
+    const int r = t / NB, c = t % NB;
+    A[r][c] = c <= r ? g[t] : (T)0;
+  }
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int j = 0; j < NB; ++j) {
+    if (threadIdx.x == 0) {
+      T d = A[j][j];
+      if (!(d > (T)0)) {
+        bad = 1;
+        d = (T)1;
+      }
+      A[j][j] = sqrt(d);
+    }
+    __syncthreads();
+    const T piv = A[j][j];
+    for (int i = j + 1 + threadIdx.x; i < NB; i += blockDim.x) A[i][j] /= piv;
+    __syncthreads();
+    const int w = NB - 1 - j;
+    for (int t = threadIdx.x; t < w * w; t += blockDim.x) {
+      const int i = j + 1 + t / w, c = j + 1 + t % w;
+      if (c <= i) A[i][c] -= A[i][j] * A[c][j];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && bad) flag_breakdown(L.status, s);
+  // X = L^{-1} written to the diagonal-inverse store, one column per thread (each thread
+  // reads back only the entries of its own column)
+  T* dv = (T*)L.dinv + m.dinv_off + (int64_t)k * NB2;
+  if (threadIdx.x < NB) {
+    const int c = threadIdx.x;
+    for (int r = 0; r < c; ++r) dv[r * NB + c] = (T)0;
+    dv[c * NB + c] = (T)1 / A[c][c];
+    for (int i = c + 1; i < NB; ++i) {
+      T sacc = (T)0;
+      for (int q = c; q < i; ++q) sacc += A[i][q] * dv[q * NB + c];
+      dv[i * NB + c] = -sacc / A[i][i];
+    }
+  }
+  for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) g[t] = A[t / NB][t % NB];
+}
+
+// ---- step k, part 2: panel L(i,k) = A(i,k) L_kk^{-T} for i = k+1 .. R-1 --------------------
+template <typename T>
+__global__ void k_trsm_panel(LevelDev L, int k) {
+  const int s = blockIdx.y;
+  const SubMeta m = L.meta[s];
+  const int i = k + 1 + blockIdx.x;
+  if (k >= m.Bc || i >= m.R) return;
+  extern __shared__ unsigned char smem_raw[];
+  T* As = (T*)smem_raw;
+  T* Xs = As + NB * LDS;
+  T* g = tile_ptr<T>(m, L.tiles, i, k);
+  load_kmajor(As, g);
+  load_kmajor(Xs, (const T*)L.dinv + m.dinv_off + (int64_t)k * NB2);
+  __syncthreads();
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  T acc[4][4] = {};
+  gemm_nt_4x4(As, Xs, acc, tx, ty);
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) g[(4 * ty + a) * NB + 4 * tx + b] = acc[a][b];
+}
+
+// ---- step k, part 3: trailing update A(i,j) -= L(i,k) L(j,k)^T, k < j <= i, j < Bc --------
+template <typename T>
+__global__ void k_syrk_update(LevelDev L, int k) {
+  const int s = blockIdx.y;
+  const SubMeta m = L.meta[s];
+  if (k >= m.Bc) return;
+  int t = blockIdx.x, j = k + 1, i = -1;
+  for (; j < m.Bc; ++j) {
+    const int cnt = m.R - j;
+    if (t < cnt) {
+      i = j + t;
+      break;
+    }
+    t -= cnt;
+  }
+  if (i < 0) return;
+  extern __shared__ unsigned char smem_raw[];
+  T* As = (T*)smem_raw;
+  T* Bs = As + NB * LDS;
+  load_kmajor(As, tile_ptr<T>(m, L.tiles, i, k));
+  load_kmajor(Bs, tile_ptr<T>(m, L.tiles, j, k));
+  __syncthreads();
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  T acc[4][4] = {};
+  gemm_nt_4x4(As, Bs, acc, tx, ty);
+  T* c = tile_ptr<T>(m, L.tiles, i, j);
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) c[(4 * ty + a) * NB + 4 * tx + b] -= acc[a][b];
+}
+
+// ---- G = Y_G Y_G^T in FP64, Cholesky, inverse; K_C = G^{-1} - rho I ----------------------
+template <typename T>
+__global__ void k_gram(LevelDev L) {
+  const int s = blockIdx.x;
+  const SubMeta m = L.meta[s];
+  const int nc = m.nc;
+  if (nc == 0) return;
+  double* G = L.Ginv + m.g_off;
+  const int npair = nc * nc;
+  for (int p = threadIdx.x; p < npair; p += blockDim.x) {
+    const int a = p / nc, b = p % nc;
+    if (b > a) continue;
+    const T* ya = tile_ptr<T>(m, L.tiles, m.Bc + a / NB, 0) + (a % NB) * NB;
+    const T* yb = tile_ptr<T>(m, L.tiles, m.Bc + b / NB, 0) + (b % NB) * NB;
+    double acc = 0.0;
+    for (int j = m.nIb; j < m.Bc; ++j)
+      for (int c = 0; c < NB; ++c) acc += (double)ya[(int64_t)j * NB2 + c] * (double)yb[(int64_t)j * NB2 + c];
+    G[a * nc + b] = acc;
+    G[b * nc + a] = acc;
+  }
+}
+
+__global__ void k_small_chol_inv(LevelDev L) {
+  const int s = blockIdx.x;
+  const SubMeta m = L.meta[s];
+  const int n = m.nc;
+  if (n == 0) return;
+  double* G = L.Ginv + m.g_off;   // in: G (full), out: G^{-1}
+  double* W = L.KC + m.g_off;     // scratch for L^{-1}, then K_C
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) {
+      double d = G[j * n + j];
+      if (!(d > 0.0)) {
+        bad = 1;
+        d = 1.0;
+      }
+      G[j * n + j] = sqrt(d);
+    }
+    __syncthreads();
+    const double piv = G[j * n + j];
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) G[i * n + j] /= piv;
+    __syncthreads();
+    const int w = n - 1 - j;
+    for (int t = threadIdx.x; t < w * w; t += blockDim.x) {
+      const int i = j + 1 + t / w, c = j + 1 + t % w;
+      if (c <= i) G[i * n + c] -= G[i * n + j] * G[c * n + j];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && bad) flag_breakdown(L.status, s);
+  // W = L^{-1} (lower), one column per thread
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    for (int r = 0; r < c; ++r) W[r * n + c] = 0.0;
+    W[c * n + c] = 1.0 / G[c * n + c];
+    for (int i = c + 1; i < n; ++i) {
+      double acc = 0.0;
+      for (int q = c; q < i; ++q) acc += G[i * n + q] * W[q * n + c];
+      W[i * n + c] = -acc / G[i * n + i];
+    }
+  }
+  __syncthreads();
+  // G^{-1} = W^T W
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    const int a = t / n, b = t % n;
+    double acc = 0.0;
+    for (int q = (a > b ? a : b); q < n; ++q) acc += W[q * n + a] * W[q * n + b];
+    G[t] = acc;   // safe: G's lower part (the factor) is no longer read
+  }
+  __syncthreads();
+  const double rho = L.rho[s];
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    const int a = t / n, b = t % n;
+    W[t] = G[t] - (a == b ? rho : 0.0);
+  }
+}
+
+// Z = Y_G^T G^{-1}, written into the Psi buffer (rows: interface padded positions)
+template <typename T>
+__global__ void k_psi_rhs(LevelDev L) {
+  const int s = blockIdx.y;
+  const SubMeta m = L.meta[s];
+  const int nc = m.nc;
+  if (nc == 0) return;
+  const int rows = m.nGb * NB;
+  const int64_t total = (int64_t)rows * nc;
+  const double* Gi = L.Ginv + m.g_off;
+  T* Z = (T*)L.psi + m.psi_off;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(t / nc), q = (int)(t % nc);
+    const int jb = m.nIb + c / NB, cc = c % NB;
+    double acc = 0.0;
+    for (int p = 0; p < nc; ++p) {
+      const T y = tile_ptr<T>(m, L.tiles, m.Bc + p / NB, jb)[(p % NB) * NB + cc];
+      acc += (double)y * Gi[p * nc + q];
+    }
+    Z[t] = (T)acc;
+  }
+}
+
+// Psi_G = L_GG^{-T} Z, backward block sweep; one block per (column chunk of 16, subdomain)
+template <typename T>
+__global__ void k_trsm_back_psi(LevelDev L) {
+  const int s = blockIdx.y;
+  const SubMeta m = L.meta[s];
+  const int nc = m.nc;
+  const int c0 = blockIdx.x * 16;
+  if (c0 >= nc) return;
+  const int ncols = min(16, nc - c0);
+  T* Z = (T*)L.psi + m.psi_off;
+  __shared__ T part[4][NB][16];
+  __shared__ T rhs[NB][16];
+  const int c = threadIdx.x % NB;      // tile column
+  const int rq = threadIdx.x / NB;     // row quarter (16 rows)
+  for (int i = m.Bc - 1; i >= m.nIb; --i) {
+    T acc[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = (T)0;
+    for (int j = i + 1; j < m.Bc; ++j) {
+      const T* Lt = tile_ptr<T>(m, L.tiles, j, i);
+      const T* Xj = Z + (int64_t)(j - m.nIb) * NB * nc + c0;
+      for (int r = rq * 16; r < rq * 16 + 16; ++r) {
+        const T l = Lt[r * NB + c];
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+          if (q < ncols) acc[q] += l * Xj[(int64_t)r * nc + q];
+      }
+    }
+    for (int q = 0; q < 16; ++q) part[rq][c][q] = acc[q];
+    __syncthreads();
+    T* Zi = Z + (int64_t)(i - m.nIb) * NB * nc + c0;
+    for (int t = threadIdx.x; t < NB * 16; t += blockDim.x) {
+      const int cc = t / 16, q = t % 16;
+      if (q < ncols)
+        rhs[cc][q] = Zi[(int64_t)cc * nc + q] - (part[0][cc][q] + part[1][cc][q] + part[2][cc][q] + part[3][cc][q]);
+    }
+    __syncthreads();
+    const T* Dv = (const T*)L.dinv + m.dinv_off + (int64_t)i * NB2;
+    for (int t = threadIdx.x; t < NB * 16; t += blockDim.x) {
+      const int cc = t / 16, q = t % 16;
+      if (q >= ncols) continue;
+      T acc2 = (T)0;
+      for (int mm = cc; mm < NB; ++mm) acc2 += Dv[mm * NB + cc] * rhs[mm][q];   // (L_ii^{-1})^T
+      Zi[(int64_t)cc * nc + q] = acc2;
+    }
+    __syncthreads();
+  }
+}
+
+// ---- streaming triangular solves, one block per subdomain -------------------------------
+// part 0: interior block rows [0, nIb); part 1: interface block rows [nIb, Bc).
+template <typename T>
+__global__ void __launch_bounds__(256) k_trsv_fwd(LevelDev L, T* __restrict__ vec, int part) {
+  const int s = blockIdx.x;
+  const SubMeta m = L.meta[s];
+  const int B0 = part == 0 ? 0 : m.nIb, B1 = part == 0 ? m.nIb : m.Bc;
+  T* v = vec + m.vec_off;
+  __shared__ T rhs[NB];
+  const int row = threadIdx.x >> 2, q = threadIdx.x & 3;
+  for (int i = B0; i < B1; ++i) {
+    T acc = (T)0;
+    const T* Lrow = tile_ptr<T>(m, L.tiles, i, B0) + row * NB + q * 16;
+    for (int j = B0; j < i; ++j) {
+      const T* Lt = Lrow + (int64_t)(j - B0) * NB2;
+      const T* yj = v + j * NB + q * 16;
+      if (sizeof(T) == 4) {
+        const float4* L4 = (const float4*)Lt;
+        const float4* y4 = (const float4*)yj;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float4 a = __ldg(L4 + u), b = y4[u];
+          acc += (T)(a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w);
+        }
+      } else {
+        const double2* L2 = (const double2*)Lt;
+        const double2* y2 = (const double2*)yj;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const double2 a = __ldg(L2 + u), b = y2[u];
+          acc += (T)(a.x * b.x + a.y * b.y);
+        }
+      }
+    }
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    if (q == 0) rhs[row] = v[i * NB + row] - acc;
+    __syncthreads();
+    const T* Dv = (const T*)L.dinv + m.dinv_off + (int64_t)i * NB2 + row * NB + q * 16;
+    T y = (T)0;
+#pragma unroll
+    for (int u = 0; u < 16; ++u) y += Dv[u] * rhs[q * 16 + u];
+    y += __shfl_xor_sync(0xffffffffu, y, 1);
+    y += __shfl_xor_sync(0xffffffffu, y, 2);
+    if (q == 0) v[i * NB + row] = y;
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_trsv_bwd(LevelDev L, T* __restrict__ vec, int part) {
+  const int s = blockIdx.x;
+  const SubMeta m = L.meta[s];
+  const int B0 = part == 0 ? 0 : m.nIb, B1 = part == 0 ? m.nIb : m.Bc;
+  T* v = vec + m.vec_off;
+  __shared__ T red[16][NB];
+  __shared__ T rhs[NB];
+  const int c4 = threadIdx.x & 15, rg = threadIdx.x >> 4;   // columns 4*c4..+3, rows 4*rg..+3
+  for (int i = B1 - 1; i >= B0; --i) {
+    T acc[4] = {(T)0, (T)0, (T)0, (T)0};
+    for (int j = i + 1; j < B1; ++j) {
+      const T* Lt = tile_ptr<T>(m, L.tiles, j, i);
+      const T* xj = v + j * NB + 4 * rg;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const T x = xj[u];
+        const T* lr = Lt + (4 * rg + u) * NB + 4 * c4;
+        if (sizeof(T) == 4) {
+          const float4 a = __ldg((const float4*)lr);
+          acc[0] += (T)a.x * x;
+          acc[1] += (T)a.y * x;
+          acc[2] += (T)a.z * x;
+          acc[3] += (T)a.w * x;
+        } else {
+          const double2 a = __ldg((const double2*)lr), b = __ldg((const double2*)lr + 1);
+          acc[0] += (T)a.x * x;
+          acc[1] += (T)a.y * x;
+          acc[2] += (T)b.x * x;
+          acc[3] += (T)b.y * x;
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) red[rg][4 * c4 + u] = acc[u];
+    __syncthreads();
+    if (threadIdx.x < NB) {
+      T t = (T)0;
+      for (int g = 0; g < 16; ++g) t += red[g][threadIdx.x];
+      rhs[threadIdx.x] = v[i * NB + threadIdx.x] - t;
+    }
+    __syncthreads();
+    if (threadIdx.x < NB) {
+      const int c = threadIdx.x;
+      const T* Dv = (const T*)L.dinv + m.dinv_off + (int64_t)i * NB2;
+      T x = (T)0;
+      for (int mm = c; mm < NB; ++mm) x += Dv[mm * NB + c] * rhs[mm];
+      v[i * NB + c] = x;
+    }
+    __syncthreads();
+  }
+}
+
+// v_G -= Y_G^T G^{-1} Y_G v_G  (the constraint part of Eq. sub_cor), one block per subdomain
+template <typename T>
+__global__ void k_constraint_corr(LevelDev L, T* __restrict__ vec) {
+  const int s = blockIdx.x;
+  const SubMeta m = L.meta[s];
+  const int nc = m.nc;
+  if (nc == 0) return;
+  extern __shared__ double sh[];
+  double* t = sh;          // [nc]
+  double* mu = sh + nc;    // [nc]
+  T* v = vec + m.vec_off + m.nIb * NB;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int ncolG = m.nGb * NB;
+  for (int p = warp; p < nc; p += nw) {
+    T acc = (T)0;
+    for (int c = lane; c < ncolG; c += 32) {
+      const T y = tile_ptr<T>(m, L.tiles, m.Bc + p / NB, m.nIb + c / NB)[(p % NB) * NB + (c % NB)];
+      acc += y * v[c];
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) t[p] = (double)acc;
+  }
+  __syncthreads();
+  const double* Gi = L.Ginv + m.g_off;
+  for (int p = threadIdx.x; p < nc; p += blockDim.x) {
+    double acc = 0.0;
+    for (int q = 0; q < nc; ++q) acc += Gi[p * nc + q] * t[q];
+    mu[p] = acc;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < ncolG; c += blockDim.x) {
+    T acc = (T)0;
+    for (int p = 0; p < nc; ++p)
+      acc += tile_ptr<T>(m, L.tiles, m.Bc + p / NB, m.nIb + c / NB)[(p % NB) * NB + (c % NB)] * (T)mu[p];
+    v[c] = v[c] - acc;
+  }
+}
+
+// rc_sub = Psi_G^T v_G (FP64), one block per subdomain
+template <typename T>
+__global__ void k_psi_t_apply(LevelDev L, const T* __restrict__ vec, double* __restrict__ rc_sub) {
+  const int s = blockIdx.x;
+  const SubMeta m = L.meta[s];
+  const int nc = m.nc;
+  const T* v = vec + m.vec_off + m.nIb * NB;
+  const T* P = (const T*)L.psi + m.psi_off;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int q = warp; q < nc; q += nw) {
+    T acc = (T)0;
+    for (int c = lane; c < m.nG; c += 32) acc += P[(int64_t)c * nc + q] * v[c];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) rc_sub[m.c_off + q] = (double)acc;
+  }
+}
+
+// v_G += Psi_G zc_sub
+template <typename T>
+__global__ void k_psi_apply_add(LevelDev L, const double* __restrict__ zc_sub, T* __restrict__ vec) {
+  const int s = blockIdx.y;
+  const SubMeta m = L.meta[s];
+  const int nc = m.nc;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= m.nG) return;
+  const T* P = (const T*)L.psi + m.psi_off + (int64_t)c * nc;
+  const double* z = zc_sub + m.c_off;
+  T acc = (T)0;
+  for (int q = 0; q < nc; ++q) acc += P[q] * (T)z[q];
+  T* v = vec + m.vec_off + m.nIb * NB;
+  v[c] = v[c] + acc;
+}
+
+}  // namespace
+
+template <typename T>
+void launch_potrf_step(const LevelDev& L, int k, int max_R, int max_tiles, cudaStream_t st) {
+  const unsigned ns = (unsigned)L.n_sub;
+  const size_t sm = 2 * NB * LDS * sizeof(T);
+  static bool attr = false;   // opt in to more than 48 KB of dynamic shared memory once
+  if (!attr) {
+    cudaFuncSetAttribute(k_trsm_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_syrk_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    attr = true;
+  }
+  { note_launch(); k_potrf_diag<T><<<ns, 256, 0, st>>>(L, k); }
+  const int panel = max_R - k - 1;
+  if (panel > 0) { note_launch(); k_trsm_panel<T><<<dim3((unsigned)panel, ns), 256, sm, st>>>(L, k); }
+  if (max_tiles > 0) { note_launch(); k_syrk_update<T><<<dim3((unsigned)max_tiles, ns), 256, sm, st>>>(L, k); }
+}
+
+template <typename T>
+void launch_gram_chol_t(const LevelDev& L, cudaStream_t st) {
+  const unsigned ns = (unsigned)L.n_sub;
+  { note_launch(); k_gram<T><<<ns, 256, 0, st>>>(L); }
+  { note_launch(); k_small_chol_inv<<<ns, 256, 0, st>>>(L); }
+}
+
+void launch_gram_chol(const LevelDev& L, int precision_fp32, int, cudaStream_t st) {
+  if (precision_fp32)
+    launch_gram_chol_t<float>(L, st);
+  else
+    launch_gram_chol_t<double>(L, st);
+}
+
+template <typename T>
+void launch_psi(const LevelDev& L, int max_nGb, int max_nc, cudaStream_t st) {
+  const unsigned ns = (unsigned)L.n_sub;
+  if (max_nc <= 0 || max_nGb <= 0) return;
+  { note_launch(); k_psi_rhs<T><<<dim3(16, ns), 256, 0, st>>>(L); }
+  { note_launch(); k_trsm_back_psi<T><<<dim3((unsigned)((max_nc + 15) / 16), ns), 256, 0, st>>>(L); }
+}
+
+template <typename T>
+void launch_trsv(const LevelDev& L, T* vec, int part, int backward, cudaStream_t st) {
+  if (backward)
+    { note_launch(); k_trsv_bwd<T><<<(unsigned)L.n_sub, 256, 0, st>>>(L, vec, part); }
+  else
+    { note_launch(); k_trsv_fwd<T><<<(unsigned)L.n_sub, 256, 0, st>>>(L, vec, part); }
+}
+
+template <typename T>
+void launch_constraint_corr(const LevelDev& L, T* vec, int max_nc, cudaStream_t st) {
+  if (max_nc <= 0) return;
+  { note_launch(); k_constraint_corr<T><<<(unsigned)L.n_sub, 256, 2 * max_nc * sizeof(double), st>>>(L, vec); }
+}
+
+template <typename T>
+void launch_psi_t_apply(const LevelDev& L, const T* vec, double* rc_sub, cudaStream_t st) {
+  { note_launch(); k_psi_t_apply<T><<<(unsigned)L.n_sub, 256, 0, st>>>(L, vec, rc_sub); }
+}
+
+template <typename T>
+void launch_psi_apply_add(const LevelDev& L, const double* zc_sub, T* vec, int max_nG, cudaStream_t st) {
+  if (max_nG <= 0) return;
+  { note_launch(); k_psi_apply_add<T><<<dim3((unsigned)((max_nG + 255) / 256), (unsigned)L.n_sub), 256, 0, st>>>(L, zc_sub, vec); }
+}
+
+#define INST(T)                                                                                 \
+  template void launch_potrf_step<T>(const LevelDev&, int, int, int, cudaStream_t);              \
+  template void launch_psi<T>(const LevelDev&, int, int, cudaStream_t);                          \
+  template void launch_trsv<T>(const LevelDev&, T*, int, int, cudaStream_t);                     \
+  template void launch_constraint_corr<T>(const LevelDev&, T*, int, cudaStream_t);               \
+  template void launch_psi_t_apply<T>(const LevelDev&, const T*, double*, cudaStream_t);         \
+  template void launch_psi_apply_add<T>(const LevelDev&, const double*, T*, int, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace bddc

@@ -1,0 +1,148 @@
+// Internal declarations shared by the host orchestration (capi.cpp) and the kernels.
+//
+// Device layout of one BDDC level (all subdomains of a level are batched in every launch):
+//   * A subdomain's local DOFs live in a padded local vector of Bc*NB entries:
+//       [interior (nI) | pad to nIb*NB | interface (nG) | pad to Bc*NB],  Bc = nIb + nGb.
+//     The identity padding decouples, so the leading nIb block rows of the factor are the
+//     Cholesky factor of K_II and the trailing nGb block rows hold the factor of the
+//     Schur complement plus rho C^T C.
+//   * The augmented matrix [K_i + rho C_i^T C_i ; C_i] is stored as NB x NB tiles, row-major
+//     inside a tile, tiles ordered block row after block row; block row i holds tiles
+//     j = 0 .. min(i, Bc-1).  Block rows Bc .. Bc+ncb-1 hold the constraint rows; after the
+//     partial Cholesky they hold Y = C L^{-T} (nonzero only in interface columns).
+//   * The inverses of the Bc diagonal factor tiles are kept next to the factor.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace bddc {
+
+constexpr int NB = 64;            // tile edge
+constexpr int64_t NB2 = NB * NB;
+
+struct SubMeta {
+  int32_t n, nI, nG, nc;          // local sizes
+  int32_t nIb, nGb, ncb, Bc;      // block counts; Bc = nIb + nGb
+  int32_t R;                      // block rows = Bc + ncb
+  int32_t pad0;
+  int64_t tile_off;               // element offset of the tiles in the level's tile buffer
+  int64_t dinv_off;               // element offset of the Bc diagonal inverses
+  int64_t vec_off;                // offset of the padded local vector
+  int64_t row_off;                // offset into the level's CSR row pointer (Bc*NB + 1 entries)
+  int64_t c_off;                  // offset of the per-subdomain coarse vector (nc)
+  int64_t g_off;                  // offset of nc x nc matrices (G^{-1}, K_C)
+  int64_t psi_off;                // offset of Psi_G (nGb*NB rows x nc, row-major)
+};
+
+// Raw device pointers of one level, passed by value to kernels.
+struct LevelDev {
+  int64_t n_sub;
+  int64_t n_dof;                  // level DOFs (level 1: free DOFs; level l: coarse DOFs of l-1)
+  int64_t n_iface;
+  int64_t n_coarse;
+  int64_t n_vec;                  // total padded local length
+  const SubMeta* meta;
+  // CSR of K_i per subdomain over padded positions (FP64)
+  const int64_t* row_ptr;         // [sum (Bc*NB+1)], absolute offsets into col/val
+  const int32_t* col;             // padded local column
+  double* val;
+  // element -> padded local positions, element matrices
+  const int64_t* ke_off;          // [n_elems + 1] offsets into ke (ne_k^2 each)
+  const int64_t* ed_off;          // [n_elems + 1] offsets into eldof
+  const int32_t* eldof;           // padded local position, -1 prescribed
+  double* ke;                     // element matrices (row-major)
+  const int64_t* rc_ptr;          // row contributions: absolute offsets, per padded row
+  const int32_t* rc_elem;         // element slot
+  const int32_t* rc_a;            // row inside the element matrix
+  // constraint rows: per subdomain row list (CSR over padded positions)
+  const int64_t* c_ptr;           // [total rows + 1]
+  const int32_t* c_pos;           // padded local position
+  const double* c_val;
+  // maps
+  const int32_t* loc2iface;       // [n_vec] interface index or -1
+  const int32_t* loc2glob;        // [n_vec] level DOF id or -1
+  const int64_t* iface_ptr;       // [n_iface + 1] occurrences of an interface DOF
+  const int64_t* iface_occ;       //   flat padded positions, ascending subdomain
+  const int64_t* glob_occ_ptr;    // [n_dof + 1] occurrences of every level DOF
+  const int64_t* glob_occ;
+  const int32_t* sub_coarse;      // [sum nc] global coarse ids (R_Ci)
+  const int64_t* cinv_ptr;        // [n_coarse + 1] occurrences of a coarse DOF
+  const int64_t* cinv_occ;        //   flat indices into per-subdomain coarse vectors
+  double* w;                      // [n_vec] interface weights (0 elsewhere)
+  double* diag;                   // [n_vec] diagonal of K_i
+  double* rho;                    // [n_sub]
+  double* Ginv;                   // [sum nc*nc]
+  double* KC;                     // [sum nc*nc] local coarse matrices K_Ci
+  void* tiles;                    // factor tiles (float or double)
+  void* dinv;                     // diagonal inverses
+  void* psi;                      // Psi_G
+  int* status;                    // [4]: breakdown flag, level sub, timeout
+};
+
+// Counts every kernel launch of the library (defined in capi.cpp).
+void note_launch();
+
+// ---------------------------------------------------------------- assembly (assemble.cu)
+void launch_elem_q1(int physics, int dim, int64_t n_elems, const double* coords, const int32_t* conn,
+                    const double* coef, double nu, const int32_t* slot_elem, double* ke, cudaStream_t st);
+void launch_csr_values(const LevelDev& L, int64_t n_rows_total, const int32_t* row_sub, cudaStream_t st);
+template <typename T>
+void launch_densify_rows(const LevelDev& L, const int32_t* row_sub, cudaStream_t st);
+template <typename T>
+void launch_add_constraints(const LevelDev& L, cudaStream_t st);
+void launch_weights(const LevelDev& L, int multiplicity, const double* unused, cudaStream_t st);
+
+// ---------------------------------------------------------------- dense factor (dense.cu)
+template <typename T>
+void launch_potrf_step(const LevelDev& L, int k, int max_R, int max_tiles, cudaStream_t st);
+void launch_gram_chol(const LevelDev& L, int precision_fp32, int max_nc, cudaStream_t st);
+template <typename T>
+void launch_psi(const LevelDev& L, int max_nGb, int max_nc, cudaStream_t st);
+template <typename T>
+void launch_trsv(const LevelDev& L, T* vec, int part, int backward, cudaStream_t st);
+template <typename T>
+void launch_constraint_corr(const LevelDev& L, T* vec, int max_nc, cudaStream_t st);
+template <typename T>
+void launch_psi_t_apply(const LevelDev& L, const T* vec, double* rc_sub, cudaStream_t st);
+template <typename T>
+void launch_psi_apply_add(const LevelDev& L, const double* zc_sub, T* vec, int max_nG, cudaStream_t st);
+
+// ---------------------------------------------------------------- vectors (vector.cu)
+template <typename T>
+void launch_gather_iface(const LevelDev& L, const double* x, int weighted, T* loc, cudaStream_t st);
+template <typename T>
+void launch_scatter_iface(const LevelDev& L, const T* loc, int weighted, double* y, cudaStream_t st);
+template <typename T>
+void launch_gather_glob(const LevelDev& L, const double* x, int part, T* loc, cudaStream_t st);
+template <typename T>
+void launch_scatter_interior(const LevelDev& L, const T* loc, double* y, cudaStream_t st);
+void launch_spmv_rows(const LevelDev& L, int part, const double* x, double* y, double alpha, double beta,
+                      const int32_t* row_sub, cudaStream_t st);
+template <typename Tin, typename Tout>
+void launch_convert(const Tin* in, Tout* out, int64_t n, cudaStream_t st);
+void launch_axpy_loc(double* y, const double* x, double a, int64_t n, cudaStream_t st);
+template <typename T>
+void launch_add_to_double(double* y, const T* x, int64_t n, cudaStream_t st);
+void launch_coarse_gather(const LevelDev& L, const double* rc_sub, double* rC, cudaStream_t st);
+void launch_coarse_scatter_n(const int32_t* sub_coarse, int64_t total, const double* zC, double* zc_sub,
+                             cudaStream_t st);
+void launch_dot(const double* a, const double* b, int64_t n, double* partial, int nblk, double* out,
+                cudaStream_t st);
+void launch_pcg_update_x_r(double* x, double* r, const double* p, const double* q, const double* scal,
+                           int64_t n, cudaStream_t st);
+void launch_pcg_update_p(double* p, const double* z, const double* scal, int64_t n, cudaStream_t st);
+void launch_pcg_scalars(double* scal, int stage, int flexible, cudaStream_t st);
+void launch_grad_contract_slots(int64_t n_elems, int ne, const double* ke, const int32_t* slot_elem,
+                                const double* coef, const int64_t* edof, const double* lam, const double* u,
+                                int nrhs, int64_t n_full, double* grad, cudaStream_t st);
+void launch_expand_free(const double* xf, const int64_t* free_of_full, int64_t n_full, int nrhs,
+                        int64_t n_free, double* xfull, cudaStream_t st);
+void launch_copy_segments(const double* src, const int64_t* src_off, double* dst, const int64_t* dst_off,
+                          const int64_t* len, int64_t n, cudaStream_t st);
+void launch_iface_rhs(double* g, const double* f, const int64_t* idx, const double* t, int64_t n,
+                      cudaStream_t st);
+void launch_put_indexed(double* u, const int64_t* idx, const double* v, int64_t n, cudaStream_t st);
+
+}  // namespace bddc

@@ -1,0 +1,320 @@
+// Vector kernels of the solve phase: interface gather/scatter with weights (r_i = E_i^T r,
+// z = sum E_i z_i, Sec. 2), FP64 sparse products with K_i, coarse gather/scatter with R_Ci,
+// deterministic FP64 reductions and the device-side PCG recurrences, and the element
+// contraction of the adjoint gradient.
+//
+// All sums run in a fixed order (ascending subdomain for the interface / coarse sums, a
+// fixed grid and tree for the dot products), so results are bit-reproducible.
+#include "internal.h"
+
+namespace bddc {
+
+namespace {
+
+template <typename T>
+__global__ void k_gather_iface(LevelDev L, const double* __restrict__ x, int weighted, T* __restrict__ loc) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= L.n_vec) return;
+  const int32_t g = L.loc2iface[p];
+  double v = 0.0;
+  if (g >= 0) v = weighted ? L.w[p] * x[g] : x[g];
+  loc[p] = (T)v;
+}
+
+template <typename T>
+__global__ void k_scatter_iface(LevelDev L, const T* __restrict__ loc, int weighted, double* __restrict__ y) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= L.n_iface) return;
+  double s = 0.0;
+  for (int64_t o = L.iface_ptr[g]; o < L.iface_ptr[g + 1]; ++o) {
+    const int64_t p = L.iface_occ[o];
+    s += weighted ? L.w[p] * (double)loc[p] : (double)loc[p];
+  }
+  y[g] = s;
+}
+
+// part: 0 interior positions only, 1 interface only, 2 all
+template <typename T>
+__global__ void k_gather_glob(LevelDev L, const double* __restrict__ x, int part, T* __restrict__ loc) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= L.n_vec) return;
+  const int32_t g = L.loc2glob[p];
+  const bool is_if = L.loc2iface[p] >= 0;
+  double v = 0.0;
+  if (g >= 0 && (part == 2 || (part == 0 && !is_if) || (part == 1 && is_if))) v = x[g];
+  loc[p] = (T)v;
+}
+
+template <typename T>
+__global__ void k_scatter_interior(LevelDev L, const T* __restrict__ loc, double* __restrict__ y) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= L.n_vec) return;
+  const int32_t g = L.loc2glob[p];
+  if (g >= 0 && L.loc2iface[p] < 0) y[g] = (double)loc[p];
+}
+
+// y[row] = beta*y[row] + alpha * (K_i x)[row] over rows of the selected part; one warp per row.
+__global__ void k_spmv(LevelDev L, int part, const double* __restrict__ x, double* __restrict__ y, double alpha,
+                       double beta, const int32_t* __restrict__ row_sub) {
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= L.n_vec) return;
+  const int s = row_sub[row];
+  const SubMeta& m = L.meta[s];
+  const int r = (int)(row - m.vec_off);
+  const bool interior = r < m.nI;
+  const bool iface = r >= m.nIb * NB && r < m.nIb * NB + m.nG;
+  if (!((part == 0 && interior) || (part == 1 && iface) || (part == 2 && (interior || iface)))) return;
+  double acc = 0.0;
+  const double* xs = x + m.vec_off;
+  for (int64_t q = L.row_ptr[row] + lane; q < L.row_ptr[row + 1]; q += 32) acc += L.val[q] * xs[L.col[q]];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) y[row] = (beta == 0.0 ? 0.0 : beta * y[row]) + alpha * acc;
+}
+
+template <typename Tin, typename Tout>
+__global__ void k_convert(const Tin* __restrict__ in, Tout* __restrict__ out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (Tout)in[i];
+}
+
+template <typename T>
+__global__ void k_add_to_double(double* __restrict__ y, const T* __restrict__ x, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] += (double)x[i];
+}
+
+__global__ void k_axpy(double* __restrict__ y, const double* __restrict__ x, double a, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] += a * x[i];
+}
+
+__global__ void k_coarse_gather(LevelDev L, const double* __restrict__ rc_sub, double* __restrict__ rC) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= L.n_coarse) return;
+  double s = 0.0;
+  for (int64_t o = L.cinv_ptr[g]; o < L.cinv_ptr[g + 1]; ++o) s += rc_sub[L.cinv_occ[o]];
+  rC[g] = s;
+}
+
+__global__ void k_coarse_scatter(const int32_t* __restrict__ sub_coarse, int64_t total, const double* __restrict__ zC,
+                                 double* __restrict__ zc_sub) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < total) zc_sub[t] = zC[sub_coarse[t]];
+}
+
+// deterministic dot: fixed grid, per-block tree, then a single block over the partials
+__global__ void k_dot_partial(const double* __restrict__ a, const double* __restrict__ b, int64_t n,
+                              double* __restrict__ partial) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s += a[i] * b[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void k_dot_final(const double* __restrict__ partial, int nblk, double* __restrict__ out) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nblk; i += 256) s += partial[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+// scal layout (see capi.cpp): 0 rz, 1 pq, 2 alpha, 3 beta, 4 rz_new, 5 rr, 6 gg, 7 z.r_old, 8 frozen
+__global__ void k_pcg_scalars(double* scal, int stage, int flexible) {
+  if (threadIdx.x != 0) return;
+  if (scal[8] != 0.0) {   // converged column: freeze the iterate
+    scal[2] = 0.0;
+    scal[3] = 0.0;
+    return;
+  }
+  if (stage == 0) {
+    const double pq = scal[1];
+    scal[2] = pq != 0.0 ? scal[0] / pq : 0.0;
+  } else {
+    const double rz_old = scal[0];
+    const double num = flexible ? (scal[4] - scal[7]) : scal[4];
+    scal[3] = rz_old != 0.0 ? num / rz_old : 0.0;
+    scal[0] = scal[4];
+  }
+}
+
+__global__ void k_pcg_xr(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
+                         const double* __restrict__ q, const double* __restrict__ scal, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double a = scal[2];
+  x[i] += a * p[i];
+  r[i] -= a * q[i];
+}
+
+__global__ void k_pcg_p(double* __restrict__ p, const double* __restrict__ z, const double* __restrict__ scal,
+                        int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  p[i] = z[i] + scal[3] * p[i];
+}
+
+// grad[e] = -(1/coef_e) * sum_k lam_k,e^T K_e u_k,e ; one warp per element
+__global__ void k_grad_contract(int64_t n_elems, int ne, const double* __restrict__ ke,
+                                const int32_t* __restrict__ slot_elem, const double* __restrict__ coef,
+                                const int64_t* __restrict__ edof, const double* __restrict__ lam,
+                                const double* __restrict__ u, int nrhs, int64_t n_full, double* __restrict__ grad) {
+  const int64_t slot = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (slot >= n_elems) return;
+  const int64_t e = slot_elem[slot];
+  const double* K = ke + slot * (int64_t)ne * ne;
+  const int64_t* d = edof + e * ne;
+  double acc = 0.0;
+  for (int k = 0; k < nrhs; ++k) {
+    const double* lk = lam + (int64_t)k * n_full;
+    const double* uk = u + (int64_t)k * n_full;
+    for (int a = lane; a < ne; a += 32) {
+      double t = 0.0;
+      for (int b = 0; b < ne; ++b) t += K[a * ne + b] * uk[d[b]];
+      acc += lk[d[a]] * t;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) grad[e] = -acc / coef[e];
+}
+
+__global__ void k_expand_free(const double* __restrict__ xf, const int64_t* __restrict__ free_of_full,
+                              int64_t n_full, int nrhs, int64_t n_free, double* __restrict__ xfull) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_full * nrhs) return;
+  const int64_t k = i / n_full, j = i % n_full;
+  const int64_t f = free_of_full[j];
+  xfull[i] = f >= 0 ? xf[k * n_free + f] : 0.0;
+}
+
+// dst[dst_off[k] + t] = src[src_off[k] + t], t < len[k]; one block per segment
+__global__ void k_copy_segments(const double* __restrict__ src, const int64_t* __restrict__ src_off,
+                                double* __restrict__ dst, const int64_t* __restrict__ dst_off,
+                                const int64_t* __restrict__ len, int64_t n) {
+  const int64_t k = blockIdx.x;
+  if (k >= n) return;
+  for (int64_t t = threadIdx.x; t < len[k]; t += blockDim.x) dst[dst_off[k] + t] = src[src_off[k] + t];
+}
+
+// g[k] = f[idx[k]] - t[k]
+__global__ void k_iface_rhs(double* __restrict__ g, const double* __restrict__ f, const int64_t* __restrict__ idx,
+                            const double* __restrict__ t, int64_t n) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) g[k] = f[idx[k]] - t[k];
+}
+
+// u[idx[k]] = v[k]
+__global__ void k_put_indexed(double* __restrict__ u, const int64_t* __restrict__ idx, const double* __restrict__ v,
+                              int64_t n) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) u[idx[k]] = v[k];
+}
+
+inline unsigned nblocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+template <typename T>
+void launch_gather_iface(const LevelDev& L, const double* x, int weighted, T* loc, cudaStream_t st) {
+  if (L.n_vec > 0) { note_launch(); k_gather_iface<T><<<nblocks(L.n_vec, 256), 256, 0, st>>>(L, x, weighted, loc); }
+}
+template <typename T>
+void launch_scatter_iface(const LevelDev& L, const T* loc, int weighted, double* y, cudaStream_t st) {
+  if (L.n_iface > 0) { note_launch(); k_scatter_iface<T><<<nblocks(L.n_iface, 256), 256, 0, st>>>(L, loc, weighted, y); }
+}
+template <typename T>
+void launch_gather_glob(const LevelDev& L, const double* x, int part, T* loc, cudaStream_t st) {
+  if (L.n_vec > 0) { note_launch(); k_gather_glob<T><<<nblocks(L.n_vec, 256), 256, 0, st>>>(L, x, part, loc); }
+}
+template <typename T>
+void launch_scatter_interior(const LevelDev& L, const T* loc, double* y, cudaStream_t st) {
+  if (L.n_vec > 0) { note_launch(); k_scatter_interior<T><<<nblocks(L.n_vec, 256), 256, 0, st>>>(L, loc, y); }
+}
+void launch_spmv_rows(const LevelDev& L, int part, const double* x, double* y, double alpha, double beta,
+                      const int32_t* row_sub, cudaStream_t st) {
+  if (L.n_vec > 0) { note_launch(); k_spmv<<<nblocks(L.n_vec, 8), 256, 0, st>>>(L, part, x, y, alpha, beta, row_sub); }
+}
+template <typename Tin, typename Tout>
+void launch_convert(const Tin* in, Tout* out, int64_t n, cudaStream_t st) {
+  if (n > 0) { note_launch(); k_convert<Tin, Tout><<<nblocks(n, 256), 256, 0, st>>>(in, out, n); }
+}
+template <typename T>
+void launch_add_to_double(double* y, const T* x, int64_t n, cudaStream_t st) {
+  if (n > 0) { note_launch(); k_add_to_double<T><<<nblocks(n, 256), 256, 0, st>>>(y, x, n); }
+}
+void launch_axpy_loc(double* y, const double* x, double a, int64_t n, cudaStream_t st) {
+  if (n > 0) { note_launch(); k_axpy<<<nblocks(n, 256), 256, 0, st>>>(y, x, a, n); }
+}
+void launch_coarse_gather(const LevelDev& L, const double* rc_sub, double* rC, cudaStream_t st) {
+  if (L.n_coarse > 0) { note_launch(); k_coarse_gather<<<nblocks(L.n_coarse, 256), 256, 0, st>>>(L, rc_sub, rC); }
+}
+void launch_coarse_scatter_n(const int32_t* sub_coarse, int64_t total, const double* zC, double* zc_sub,
+                             cudaStream_t st) {
+  if (total > 0) { note_launch(); k_coarse_scatter<<<nblocks(total, 256), 256, 0, st>>>(sub_coarse, total, zC, zc_sub); }
+}
+void launch_dot(const double* a, const double* b, int64_t n, double* partial, int nblk, double* out, cudaStream_t st) {
+  { note_launch(); k_dot_partial<<<nblk, 256, 0, st>>>(a, b, n, partial); }
+  { note_launch(); k_dot_final<<<1, 256, 0, st>>>(partial, nblk, out); }
+}
+void launch_pcg_update_x_r(double* x, double* r, const double* p, const double* q, const double* scal, int64_t n,
+                           cudaStream_t st) {
+  if (n > 0) { note_launch(); k_pcg_xr<<<nblocks(n, 256), 256, 0, st>>>(x, r, p, q, scal, n); }
+}
+void launch_pcg_update_p(double* p, const double* z, const double* scal, int64_t n, cudaStream_t st) {
+  if (n > 0) { note_launch(); k_pcg_p<<<nblocks(n, 256), 256, 0, st>>>(p, z, scal, n); }
+}
+void launch_pcg_scalars(double* scal, int stage, int flexible, cudaStream_t st) {
+  { note_launch(); k_pcg_scalars<<<1, 32, 0, st>>>(scal, stage, flexible); }
+}
+void launch_grad_contract_slots(int64_t n_elems, int ne, const double* ke, const int32_t* slot_elem, const double* coef,
+                                const int64_t* edof, const double* lam, const double* u, int nrhs, int64_t n_full,
+                                double* grad, cudaStream_t st) {
+  if (n_elems > 0)
+    { note_launch(); k_grad_contract<<<nblocks(n_elems, 8), 256, 0, st>>>(n_elems, ne, ke, slot_elem, coef, edof, lam, u, nrhs, n_full,
+                                                          grad); }
+}
+void launch_expand_free(const double* xf, const int64_t* free_of_full, int64_t n_full, int nrhs, int64_t n_free,
+                        double* xfull, cudaStream_t st) {
+  if (n_full > 0)
+    { note_launch(); k_expand_free<<<nblocks(n_full * nrhs, 256), 256, 0, st>>>(xf, free_of_full, n_full, nrhs, n_free, xfull); }
+}
+
+void launch_copy_segments(const double* src, const int64_t* src_off, double* dst, const int64_t* dst_off,
+                          const int64_t* len, int64_t n, cudaStream_t st) {
+  if (n > 0) { note_launch(); k_copy_segments<<<(unsigned)n, 256, 0, st>>>(src, src_off, dst, dst_off, len, n); }
+}
+void launch_iface_rhs(double* g, const double* f, const int64_t* idx, const double* t, int64_t n, cudaStream_t st) {
+  if (n > 0) { note_launch(); k_iface_rhs<<<nblocks(n, 256), 256, 0, st>>>(g, f, idx, t, n); }
+}
+void launch_put_indexed(double* u, const int64_t* idx, const double* v, int64_t n, cudaStream_t st) {
+  if (n > 0) { note_launch(); k_put_indexed<<<nblocks(n, 256), 256, 0, st>>>(u, idx, v, n); }
+}
+
+#define INST(T)                                                                             \
+  template void launch_gather_iface<T>(const LevelDev&, const double*, int, T*, cudaStream_t); \
+  template void launch_scatter_iface<T>(const LevelDev&, const T*, int, double*, cudaStream_t); \
+  template void launch_gather_glob<T>(const LevelDev&, const double*, int, T*, cudaStream_t);  \
+  template void launch_scatter_interior<T>(const LevelDev&, const T*, double*, cudaStream_t);  \
+  template void launch_add_to_double<T>(double*, const T*, int64_t, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+template void launch_convert<double, float>(const double*, float*, int64_t, cudaStream_t);
+template void launch_convert<float, double>(const float*, double*, int64_t, cudaStream_t);
+template void launch_convert<double, double>(const double*, double*, int64_t, cudaStream_t);
+
+}  // namespace bddc

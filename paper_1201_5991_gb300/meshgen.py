@@ -344,6 +344,8 @@ def config(name: str) -> Problem:
         return poisson2d(32, 4)
     if name == "elasticity3d_48":
         return elasticity3d(48, 4, seed=2)
+    if name == "elasticity3d_24":            # same 12^3 subdomains, 2^3 of them (profiling case)
+        return elasticity3d(24, 2, seed=2)
     if name == "elasticity3d_96_kmeans":
         return elasticity3d_kmeans(96, 512, 8, seed=3, seed2=33)
     if name == "elasticity3d_64_16rhs":

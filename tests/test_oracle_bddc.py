@@ -52,6 +52,19 @@ def test_schur_and_condensed_rhs_vs_global_elimination(name):
     np.testing.assert_allclose(b.condensed_rhs(p.f[:, 0]), g_ref, atol=1e-12 * np.abs(g_ref).max())
 
 
+def test_promoted_corners_solve():
+    # a floating subdomain with corners only: three promoted corners make A_i nonsingular
+    p = meshgen.elasticity3d(4, 1, seed=0, constraints=meshgen.CORNERS)
+    cent = p.coords[p.conn].mean(axis=1)
+    p.parts = [(cent[:, 0] > 0.5).astype(np.int32)]
+    p.n_parts = [2]
+    b = Bddc(p)
+    assert b.l1.maps.n_promoted == 3
+    u, info = b.solve(p.f[:, 0], tol=1e-12)
+    u_ref = fem.direct_solve(p)[:, 0]
+    assert np.linalg.norm(u - u_ref) / np.linalg.norm(u_ref) < 1e-10
+
+
 def test_one_subdomain_is_exact():
     p = meshgen.elasticity3d(4, 1, seed=3)
     b = Bddc(p)
