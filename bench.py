@@ -125,17 +125,18 @@ class ClockSampler:
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def traffic_per_launch():
-    """DRAM bytes per launch of the streaming sweep from the committed ncu summary, or None
-    when the kernel source changed since the counters were taken."""
+def traffic_ratio():
+    """DRAM bytes / algorithmic bytes of the streaming sweep from the committed ncu summary
+    (profiles/trsv_sweep_traffic.json), or None when the kernel source changed since the
+    counters were taken."""
     path = os.path.join(ROOT, "profiles", "trsv_sweep_traffic.json")
     try:
         with open(path) as fh:
             rec = json.load(fh)
-        src = open(os.path.join(ROOT, "paper_1201_5991_gb300", "csrc", "dense.cu"), "rb").read()
-        if hashlib.sha256(src).hexdigest() != rec.get("dense_cu_sha256"):
+        src = open(os.path.join(ROOT, "paper_1201_5991_gb300", "csrc", "sweep.cu"), "rb").read()
+        if hashlib.sha256(src).hexdigest() != rec.get("sweep_cu_sha256"):
             return None
-        return float(rec["dram_bytes_per_launch"])
+        return float(rec["traffic_over_algorithmic"])
     except Exception:
         return None
 
@@ -303,9 +304,10 @@ def run_gpu(args, rank, world, local_rank):
 
     hbm, _, peak_kind = load_peaks()
     achieved = prof[2] / (prof[0] * 1e-3) / 1e9 if prof[0] > 0 else 0.0
-    traffic = traffic_per_launch()
+    ratio = traffic_ratio()
+    traffic = ratio * prof[2] / max(prof[1], 1) if ratio is not None else None
     roofline = {
-        "kernel": "k_trsv_fwd/k_trsv_bwd<float> (streaming triangular sweeps)",
+        "kernel": "k_sweep<float> forward/backward (streaming triangular sweeps, TMA-staged tiles)",
         "bound": "hbm",
         "achieved": round(achieved, 1),
         "peak": hbm,
@@ -391,6 +393,7 @@ def run_reference(args, rank, world):
 
 
 def main():
+    global WORKLOAD
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -402,7 +405,6 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 form (profiling runs)")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
     args = ap.parse_args()
-    global WORKLOAD
     WORKLOAD = args.workload
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -90,6 +90,11 @@ struct Level {
   std::vector<int> max_tiles;  // per factor step k
   std::vector<double> step_flops;  // tile flops of factor step k (all subdomains)
   double trsv_bytes[2] = {0, 0};   // algorithmic bytes of one sweep over part 0 / part 1
+  // sweep task lists [part][direction] in dependency order and their control words
+  int2* tasks[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  int ntasks[2][2] = {{0, 0}, {0, 0}};
+  int* ctrl = nullptr;
+  int n_ctrl = 0;
   int ne_uniform = 0;          // level 1: entries per element row
   // device
   LevelDev d{};
@@ -155,6 +160,7 @@ struct bddc_handle_s {
   double* ucol = nullptr;
   double *full_a = nullptr, *full_b = nullptr;
   int refine_steps = 0;
+  int grid_max = 304;                  // persistent sweep grid: 2 CTAs per SM
   bddc_stats stats{};
   bool factored = false;
   // optional per-class CUDA-event timing
@@ -538,6 +544,28 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
   }
   (void)ts;
   d.status = h->d_status;
+  // sweep tasks: block rows of all subdomains, interleaved by depth so that every task's
+  // dependencies come earlier in the list
+  for (int part = 0; part < 2; ++part)
+    for (int dir = 0; dir < 2; ++dir) {
+      std::vector<int2> tl;
+      int depth = 0;
+      for (bool more = true; more; ++depth) {
+        more = false;
+        for (int64_t s = 0; s < ns; ++s) {
+          const SubMeta& m = L.meta[s];
+          const int B0 = part == 0 ? 0 : m.nIb, B1 = part == 0 ? m.nIb : m.Bc;
+          if (B0 + depth < B1) {
+            more = true;
+            tl.push_back(make_int2((int)s, dir == 0 ? B0 + depth : B1 - 1 - depth));
+          }
+        }
+      }
+      L.ntasks[part][dir] = (int)tl.size();
+      L.tasks[part][dir] = A.upload(tl, st);
+    }
+  L.n_ctrl = (int)(1 + L.dinv_elems / NB2);
+  L.ctrl = A.alloc<int>(L.n_ctrl);
   L.row_sub = A.upload(row_sub, st);
   L.slot_elem = A.upload(slot_elem, st);
   L.iface_dofs = A.upload(mp.iface_dofs, st);
@@ -595,6 +623,7 @@ void check_status(bddc_handle_s* h, int level) {
   int st[4];
   ck(cudaMemcpyAsync(st, h->d_status, sizeof(st), cudaMemcpyDeviceToHost, h->st), "status");
   ck(cudaStreamSynchronize(h->st), "sync");
+  if (st[2]) fail(BDDC_ERR_TIMEOUT, "a bounded device-side wait gave up (code " + std::to_string(st[2]) + ")");
   if (st[0]) {
     h->stats.breakdown_level = level;
     h->stats.breakdown_sub = st[1];
@@ -612,7 +641,8 @@ void reset_status(bddc_handle_s* h) {
 template <typename T>
 void trsv_one(bddc_handle_s* h, Level& L, T* v, int part, int backward, cudaStream_t st) {
   ProfScope ps(h, BDDC_PROF_TRSV, L.trsv_bytes[part], 0.0);
-  launch_trsv<T>(L.d, v, part, backward, st);
+  launch_sweep<T>(L.d, v, L.tasks[part][backward], L.ntasks[part][backward], part, backward, L.ctrl, L.n_ctrl,
+                  h->grid_max, st);
 }
 
 template <typename T>
@@ -788,8 +818,9 @@ void choose_refinement(bddc_handle_s* h) {
     ck(cudaMemcpyAsync(L.dl3, v, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
     launch_spmv_rows(L.d, 0, w, L.dl3, -1.0, 1.0, L.row_sub, st);
     const double rel = nv > 0 ? std::sqrt(dot_host(h, L.dl3, L.dl3, n)) / nv : 0.0;
+    if (rel > 0.5 * prev) break;          // stagnated at round-off: the previous count suffices
     best = steps;
-    if (rel < 4e-16 || rel > 0.5 * prev) break;
+    if (rel < 4e-16) break;
     prev = rel;
   }
   h->refine_steps = best;
@@ -894,6 +925,12 @@ void analysis(bddc_handle_s* h, const bddc_mesh* mesh, const bddc_partition* par
 void device_setup(bddc_handle_s* h) {
   cudaStream_t st = h->st;
   DevArena& A = h->arena;
+  {
+    int dev = 0, sms = 0;
+    ck(cudaGetDevice(&dev), "cudaGetDevice");
+    ck(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
+    h->grid_max = 2 * std::max(1, sms);
+  }
   h->d_status = A.alloc<int>(4);
   h->d_coords = A.upload(h->coords, st);
   h->d_conn = A.upload(h->conn, st);
@@ -1066,7 +1103,7 @@ int solve_impl(bddc_handle_s* h, const double* rhs, double* x, int nrhs, double 
     worst = std::max(worst, r.rel);
     if (k == 0) first = r;
   }
-  ck(cudaStreamSynchronize(st), "sync");
+  check_status(h, 0);
   h->stats.iterations = maxits;
   h->stats.converged = all_conv ? 1 : 0;
   h->stats.rel_residual = worst;

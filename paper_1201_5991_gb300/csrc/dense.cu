@@ -8,7 +8,6 @@
 //  * G_i = Y_i Y_i^T = C_i A_i^{-1} C_i^T (FP64), its Cholesky factor and inverse;
 //    Psi_i = A_i^{-1} C_i^T G_i^{-1} (so C_i Psi_i = I and K_i Psi_i = -C_i^T Lambda_i with
 //    Lambda_i = rho I - G_i^{-1}), K_Ci = Psi_i^T K_i Psi_i = -Lambda_i = G_i^{-1} - rho I.
-//  * Streaming forward / backward triangular solves with the tiles (per Krylov iteration).
 #include "internal.h"
 
 namespace bddc {
@@ -317,108 +316,6 @@ __global__ void k_trsm_back_psi(LevelDev L) {
   }
 }
 
-// ---- streaming triangular solves, one block per subdomain -------------------------------
-// part 0: interior block rows [0, nIb); part 1: interface block rows [nIb, Bc).
-template <typename T>
-__global__ void __launch_bounds__(256) k_trsv_fwd(LevelDev L, T* __restrict__ vec, int part) {
-  const int s = blockIdx.x;
-  const SubMeta m = L.meta[s];
-  const int B0 = part == 0 ? 0 : m.nIb, B1 = part == 0 ? m.nIb : m.Bc;
-  T* v = vec + m.vec_off;
-  __shared__ T rhs[NB];
-  const int row = threadIdx.x >> 2, q = threadIdx.x & 3;
-  for (int i = B0; i < B1; ++i) {
-    T acc = (T)0;
-    const T* Lrow = tile_ptr<T>(m, L.tiles, i, B0) + row * NB + q * 16;
-    for (int j = B0; j < i; ++j) {
-      const T* Lt = Lrow + (int64_t)(j - B0) * NB2;
-      const T* yj = v + j * NB + q * 16;
-      if (sizeof(T) == 4) {
-        const float4* L4 = (const float4*)Lt;
-        const float4* y4 = (const float4*)yj;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const float4 a = __ldg(L4 + u), b = y4[u];
-          acc += (T)(a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w);
-        }
-      } else {
-        const double2* L2 = (const double2*)Lt;
-        const double2* y2 = (const double2*)yj;
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const double2 a = __ldg(L2 + u), b = y2[u];
-          acc += (T)(a.x * b.x + a.y * b.y);
-        }
-      }
-    }
-    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-    if (q == 0) rhs[row] = v[i * NB + row] - acc;
-    __syncthreads();
-    const T* Dv = (const T*)L.dinv + m.dinv_off + (int64_t)i * NB2 + row * NB + q * 16;
-    T y = (T)0;
-#pragma unroll
-    for (int u = 0; u < 16; ++u) y += Dv[u] * rhs[q * 16 + u];
-    y += __shfl_xor_sync(0xffffffffu, y, 1);
-    y += __shfl_xor_sync(0xffffffffu, y, 2);
-    if (q == 0) v[i * NB + row] = y;
-    __syncthreads();
-  }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256) k_trsv_bwd(LevelDev L, T* __restrict__ vec, int part) {
-  const int s = blockIdx.x;
-  const SubMeta m = L.meta[s];
-  const int B0 = part == 0 ? 0 : m.nIb, B1 = part == 0 ? m.nIb : m.Bc;
-  T* v = vec + m.vec_off;
-  __shared__ T red[16][NB];
-  __shared__ T rhs[NB];
-  const int c4 = threadIdx.x & 15, rg = threadIdx.x >> 4;   // columns 4*c4..+3, rows 4*rg..+3
-  for (int i = B1 - 1; i >= B0; --i) {
-    T acc[4] = {(T)0, (T)0, (T)0, (T)0};
-    for (int j = i + 1; j < B1; ++j) {
-      const T* Lt = tile_ptr<T>(m, L.tiles, j, i);
-      const T* xj = v + j * NB + 4 * rg;
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const T x = xj[u];
-        const T* lr = Lt + (4 * rg + u) * NB + 4 * c4;
-        if (sizeof(T) == 4) {
-          const float4 a = __ldg((const float4*)lr);
-          acc[0] += (T)a.x * x;
-          acc[1] += (T)a.y * x;
-          acc[2] += (T)a.z * x;
-          acc[3] += (T)a.w * x;
-        } else {
-          const double2 a = __ldg((const double2*)lr), b = __ldg((const double2*)lr + 1);
-          acc[0] += (T)a.x * x;
-          acc[1] += (T)a.y * x;
-          acc[2] += (T)b.x * x;
-          acc[3] += (T)b.y * x;
-        }
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) red[rg][4 * c4 + u] = acc[u];
-    __syncthreads();
-    if (threadIdx.x < NB) {
-      T t = (T)0;
-      for (int g = 0; g < 16; ++g) t += red[g][threadIdx.x];
-      rhs[threadIdx.x] = v[i * NB + threadIdx.x] - t;
-    }
-    __syncthreads();
-    if (threadIdx.x < NB) {
-      const int c = threadIdx.x;
-      const T* Dv = (const T*)L.dinv + m.dinv_off + (int64_t)i * NB2;
-      T x = (T)0;
-      for (int mm = c; mm < NB; ++mm) x += Dv[mm * NB + c] * rhs[mm];
-      v[i * NB + c] = x;
-    }
-    __syncthreads();
-  }
-}
-
 // v_G -= Y_G^T G^{-1} Y_G v_G  (the constraint part of Eq. sub_cor), one block per subdomain
 template <typename T>
 __global__ void k_constraint_corr(LevelDev L, T* __restrict__ vec) {
@@ -531,14 +428,6 @@ void launch_psi(const LevelDev& L, int max_nGb, int max_nc, cudaStream_t st) {
 }
 
 template <typename T>
-void launch_trsv(const LevelDev& L, T* vec, int part, int backward, cudaStream_t st) {
-  if (backward)
-    { note_launch(); k_trsv_bwd<T><<<(unsigned)L.n_sub, 256, 0, st>>>(L, vec, part); }
-  else
-    { note_launch(); k_trsv_fwd<T><<<(unsigned)L.n_sub, 256, 0, st>>>(L, vec, part); }
-}
-
-template <typename T>
 void launch_constraint_corr(const LevelDev& L, T* vec, int max_nc, cudaStream_t st) {
   if (max_nc <= 0) return;
   { note_launch(); k_constraint_corr<T><<<(unsigned)L.n_sub, 256, 2 * max_nc * sizeof(double), st>>>(L, vec); }
@@ -558,7 +447,6 @@ void launch_psi_apply_add(const LevelDev& L, const double* zc_sub, T* vec, int m
 #define INST(T)                                                                                 \
   template void launch_potrf_step<T>(const LevelDev&, int, int, int, cudaStream_t);              \
   template void launch_psi<T>(const LevelDev&, int, int, cudaStream_t);                          \
-  template void launch_trsv<T>(const LevelDev&, T*, int, int, cudaStream_t);                     \
   template void launch_constraint_corr<T>(const LevelDev&, T*, int, cudaStream_t);               \
   template void launch_psi_t_apply<T>(const LevelDev&, const T*, double*, cudaStream_t);         \
   template void launch_psi_apply_add<T>(const LevelDev&, const double*, T*, int, cudaStream_t);

@@ -100,8 +100,11 @@ void launch_potrf_step(const LevelDev& L, int k, int max_R, int max_tiles, cudaS
 void launch_gram_chol(const LevelDev& L, int precision_fp32, int max_nc, cudaStream_t st);
 template <typename T>
 void launch_psi(const LevelDev& L, int max_nGb, int max_nc, cudaStream_t st);
+// sweep.cu: forward (backward = 0) or backward triangular sweep over part 0 (interior
+// block rows) or part 1 (interface block rows) of every subdomain; ctrl has n_ctrl ints.
 template <typename T>
-void launch_trsv(const LevelDev& L, T* vec, int part, int backward, cudaStream_t st);
+void launch_sweep(const LevelDev& L, T* vec, const int2* tasks, int ntasks, int part, int backward, int* ctrl,
+                  int n_ctrl, int grid_max, cudaStream_t st);
 template <typename T>
 void launch_constraint_corr(const LevelDev& L, T* vec, int max_nc, cudaStream_t st);
 template <typename T>

@@ -1,0 +1,319 @@
+// Streaming triangular sweeps with the tiled factors, batched over all subdomains of a level:
+// forward L y = b and backward L^T x = y over the interior block rows (the discrete
+// Dirichlet problems of the Schur operator, Sec. 2) or over the interface block rows (the
+// constrained Neumann problem of Eq. sub_cor, restricted to the interface).
+//
+// Design (GB300): the sweep is bound by reading the factor from HBM once.  A persistent grid
+// of 2 CTAs per SM takes block-row tasks (subdomain s, block row i) from a global counter in
+// dependency order (all subdomains' first rows, then their second rows, ...).  A task
+// streams its row of NB x NB tiles (forward) or its column of tiles (backward) into a ring of
+// shared-memory stages with cp.async.bulk, completion tracked by mbarriers, while the solution
+// blocks it depends on are published by other CTAs through per-row ready flags
+// (release/acquire).  A task only waits for tasks handed out before it, so the scheme cannot
+// deadlock whatever the residency.  Every wait is bounded; a timeout sets status[2] and the
+// kernel finishes without waiting further (the host reports BDDC_ERR_TIMEOUT).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "internal.h"
+
+namespace bddc {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kYSlots = 16;          // solution blocks staged in shared memory at a time
+constexpr long long kSpinLimit = 1ll << 24;
+
+__device__ __forceinline__ int64_t tile_index(int i, int j, int Bc) {
+  return i < Bc ? ((int64_t)i * (i + 1) / 2 + j) : ((int64_t)Bc * (Bc + 1) / 2 + (int64_t)(i - Bc) * Bc + j);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+template <typename T>
+struct Vec2;
+template <>
+struct Vec2<float> {
+  using type = float2;
+};
+template <>
+struct Vec2<double> {
+  using type = double2;
+};
+
+// One task: (subdomain, block row).  Forward consumes tiles (i, B0..i-1) then D_i^{-1};
+// backward consumes tiles (B1-1..i+1, i) then D_i^{-1}.
+template <typename T, int S, bool BWD>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_sweep(LevelDev L, T* __restrict__ vec, const int2* __restrict__ tasks, int ntasks, int part,
+            int* __restrict__ ctrl) {
+  using V2 = typename Vec2<T>::type;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T* stage = (T*)smem_raw;                       // S tiles of NB*NB
+  __shared__ __align__(8) uint64_t full[S];
+  __shared__ __align__(16) T ybuf[kYSlots][NB];
+  __shared__ T red[kThreads / 32][NB];
+  __shared__ __align__(16) T rhs[NB];
+  __shared__ int s_task, s_ready;
+  int* counter = ctrl;
+  int* flags = ctrl + 1;
+  int* status = L.status;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int k = 0; k < S; ++k) mbar_init(&full[k], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  uint32_t cons = 0;     // tiles consumed by this CTA (ring position and phase)
+  uint32_t issued = 0;   // tiles issued (thread 0)
+  bool lost = false;     // a tile wait gave up: drain before exit
+  for (;;) {
+    if (tid == 0) s_task = atomicAdd(counter, 1);
+    __syncthreads();
+    const int t = s_task;
+    if (t >= ntasks) break;
+    const int sub = tasks[t].x, i = tasks[t].y;
+    const SubMeta m = L.meta[sub];
+    const int B0 = part == 0 ? 0 : m.nIb, B1 = part == 0 ? m.nIb : m.Bc;
+    const int nL = BWD ? (B1 - 1 - i) : (i - B0);   // factor tiles before D_i^{-1}
+    const int ntile = nL + 1;
+    const T* tiles = (const T*)L.tiles + m.tile_off;
+    const T* dinv = (const T*)L.dinv + m.dinv_off + (int64_t)i * NB2;
+    const int fbase = (int)(m.dinv_off / NB2);   // flags of this subdomain's block rows
+    T* v = vec + m.vec_off;
+    auto tile_src = [&](int k) -> const T* {
+      if (k == nL) return dinv;
+      const int j = BWD ? (B1 - 1 - k) : (B0 + k);
+      return BWD ? tiles + tile_index(j, i, m.Bc) * NB2 : tiles + tile_index(i, j, m.Bc) * NB2;
+    };
+    // prologue: fill the ring
+    if (tid == 0) {
+      const int pre = ntile < S ? ntile : S;
+      for (int k = 0; k < pre; ++k) {
+        const uint32_t slot = (cons + k) % S;
+        mbar_expect_tx(&full[slot], (uint32_t)(NB2 * sizeof(T)));
+        bulk_g2s(stage + slot * NB2, tile_src(k), (uint32_t)(NB2 * sizeof(T)), &full[slot]);
+      }
+      issued += pre;
+    }
+    T acc[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) acc[r] = (T)0;
+    T accc0 = (T)0, accc1 = (T)0;
+    int staged_end = 0;   // tiles [staged_begin, staged_end) have their solution block in ybuf
+    for (int k = 0; k < ntile; ++k) {
+      if (k < nL && k >= staged_end) {
+        // wait until the next solution blocks are published, then stage up to kYSlots of them
+        if (warp == 0) {
+          int ready = 0;
+          long long spins = 0;
+          for (;;) {
+            // tile k+q needs block j(k+q); poll 32 of them at once
+            const int q = lane;
+            int ok = 1;
+            if (k + q < nL) {
+              const int j = BWD ? (B1 - 1 - (k + q)) : (B0 + k + q);
+              ok = ld_acquire(flags + fbase + j) != 0;
+            } else {
+              ok = 0;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, ok);
+            ready = __ffs(~bal) - 1;          // consecutive ready tiles from k
+            if (bal == 0xffffffffu) ready = 32;
+            if (ready > 0) break;
+            if (++spins > kSpinLimit) {
+              if (lane == 0) atomicExch(status + 2, 1);
+              ready = 1;
+              break;
+            }
+            __nanosleep(64);
+          }
+          if (lane == 0) s_ready = ready < kYSlots ? ready : kYSlots;
+        }
+        __syncthreads();
+        const int cnt = s_ready;
+        for (int e = tid; e < cnt * NB; e += kThreads) {
+          const int kk = k + e / NB;
+          const int j = BWD ? (B1 - 1 - kk) : (B0 + kk);
+          ybuf[kk % kYSlots][e % NB] = __ldcg(v + j * NB + e % NB);
+        }
+        __syncthreads();
+        staged_end = k + cnt;
+      }
+      // wait for the tile
+      const uint32_t slot = cons % S, parity = (cons / S) & 1u;
+      {
+        long long spins = 0;
+        while (!mbar_try_wait(&full[slot], parity)) {
+          if (++spins > kSpinLimit) {
+            if (tid == 0) atomicExch(status + 2, 2);
+            lost = true;
+            break;
+          }
+        }
+      }
+      const T* tl = stage + slot * NB2;
+      if (k < nL) {
+        const T* y = ybuf[k % kYSlots];
+        if (!BWD) {
+          const V2 yv = *(const V2*)(y + 2 * lane);
+#pragma unroll
+          for (int r = 0; r < 8; ++r) {
+            const V2 a = *(const V2*)(tl + (warp + 8 * r) * NB + 2 * lane);
+            acc[r] += a.x * yv.x + a.y * yv.y;
+          }
+        } else {
+#pragma unroll
+          for (int r = 0; r < 8; ++r) {
+            const int row = warp + 8 * r;
+            const V2 a = *(const V2*)(tl + row * NB + 2 * lane);
+            const T x = y[row];
+            accc0 += a.x * x;
+            accc1 += a.y * x;
+          }
+        }
+      } else {
+        // diagonal block: right-hand side, then D_i^{-1} (forward) or D_i^{-T} (backward)
+        if (!BWD) {
+#pragma unroll
+          for (int r = 0; r < 8; ++r) {
+            T a = acc[r];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            if (lane == 0) rhs[warp + 8 * r] = __ldcg(v + i * NB + warp + 8 * r) - a;
+          }
+          __syncthreads();
+          const V2 rv = *(const V2*)(rhs + 2 * lane);
+#pragma unroll
+          for (int r = 0; r < 8; ++r) {
+            const V2 a = *(const V2*)(tl + (warp + 8 * r) * NB + 2 * lane);
+            T yv = a.x * rv.x + a.y * rv.y;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) yv += __shfl_xor_sync(0xffffffffu, yv, o);
+            if (lane == 0) v[i * NB + warp + 8 * r] = yv;
+          }
+          if (lane == 0) __threadfence();
+        } else {
+          red[warp][2 * lane] = accc0;
+          red[warp][2 * lane + 1] = accc1;
+          __syncthreads();
+          if (tid < NB) {
+            T a = (T)0;
+#pragma unroll
+            for (int w = 0; w < kThreads / 32; ++w) a += red[w][tid];
+            rhs[tid] = __ldcg(v + i * NB + tid) - a;
+          }
+          __syncthreads();
+          T p0 = (T)0, p1 = (T)0;
+#pragma unroll
+          for (int r = 0; r < 8; ++r) {
+            const int row = warp + 8 * r;
+            const V2 a = *(const V2*)(tl + row * NB + 2 * lane);
+            p0 += a.x * rhs[row];
+            p1 += a.y * rhs[row];
+          }
+          __syncthreads();
+          red[warp][2 * lane] = p0;
+          red[warp][2 * lane + 1] = p1;
+          __syncthreads();
+          if (tid < NB) {
+            T a = (T)0;
+#pragma unroll
+            for (int w = 0; w < kThreads / 32; ++w) a += red[w][tid];
+            v[i * NB + tid] = a;
+            __threadfence();
+          }
+        }
+      }
+      __syncthreads();   // every thread is done with this stage
+      ++cons;
+      if (tid == 0 && k + S < ntile) {
+        const uint32_t ns = (cons + S - 1) % S;   // the slot just released
+        mbar_expect_tx(&full[ns], (uint32_t)(NB2 * sizeof(T)));
+        bulk_g2s(stage + ns * NB2, tile_src(k + S), (uint32_t)(NB2 * sizeof(T)), &full[ns]);
+        ++issued;
+      }
+    }
+    // publish the solution block of row i
+    if (tid == 0) {
+      __threadfence();
+      st_release(flags + fbase + i, 1);
+    }
+  }
+  // After a lost tile wait, copies may still be in flight into this CTA's shared memory:
+  // wait (bounded) for the last phase issued on every slot before the CTA exits.
+  if (tid == 0 && lost) {
+    for (uint32_t c = (issued > (uint32_t)S ? issued - S : 0u); c < issued; ++c) {
+      long long spins = 0;
+      while (!mbar_try_wait(&full[c % S], (c / S) & 1u) && ++spins < kSpinLimit) {
+      }
+    }
+  }
+}
+
+}  // namespace
+
+// Task lists and control words live in the level (see capi.cpp); this entry launches one
+// sweep.  ctrl = [counter, flags...] must be zeroed before the launch (memset in the stream).
+template <typename T>
+void launch_sweep(const LevelDev& L, T* vec, const int2* tasks, int ntasks, int part, int backward, int* ctrl,
+                  int n_ctrl, int grid_max, cudaStream_t st) {
+  if (ntasks <= 0) return;
+  constexpr int S = sizeof(T) == 4 ? 6 : 3;
+  const size_t dyn = (size_t)S * NB2 * sizeof(T);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_sweep<T, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    cudaFuncSetAttribute(k_sweep<T, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    attr = true;
+  }
+  cudaMemsetAsync(ctrl, 0, sizeof(int) * (size_t)n_ctrl, st);
+  const int grid = ntasks < grid_max ? ntasks : grid_max;
+  note_launch();
+  if (backward)
+    k_sweep<T, S, true><<<grid, kThreads, dyn, st>>>(L, vec, tasks, ntasks, part, ctrl);
+  else
+    k_sweep<T, S, false><<<grid, kThreads, dyn, st>>>(L, vec, tasks, ntasks, part, ctrl);
+}
+
+template void launch_sweep<float>(const LevelDev&, float*, const int2*, int, int, int, int*, int, int, cudaStream_t);
+template void launch_sweep<double>(const LevelDev&, double*, const int2*, int, int, int, int*, int, int, cudaStream_t);
+
+}  // namespace bddc
