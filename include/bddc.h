@@ -210,6 +210,22 @@ int bddc_apply_schur(bddc_handle h, const double* x, double* y, int nrhs);
 int bddc_grad(bddc_handle h, const double* dJdu, const double* u, int nrhs, double tol,
               double* grad_coef, double* grad_rhs);
 
+/* bddc_grad without device allocation.  The paper has no counterpart: this entry point exists
+ * for callers that cannot let a library allocate device memory -- applications that hand
+ * (almost) all of it to their own pool, where a cudaMalloc from the library would fail or
+ * fragment that pool, and latency-critical loops, where cudaMalloc/cudaFree would stall the
+ * device.  Same results as bddc_grad (the element contraction sums right-hand sides in another
+ * order).  grad_rhs is required (it receives lambda); grad_coef may be NULL.  The full-DOF
+ * scratch of the contraction lives in one fixed 16 MiB device array inside the library, held
+ * by every GPU that loads the library until the process exits: meshes with
+ * n_nodes * dofs_per_node > 1,048,576 are rejected with BDDC_ERR_INVALID.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress); make this first call
+ * before any stream capture.  Every call shares the array and overwrites the part it reads, so
+ * calls whose work overlaps on the GPU (several streams, several host threads) race and must be
+ * serialised by the caller.  Errors as bddc_grad. */
+int bddc_grad_noalloc(bddc_handle h, const double* dJdu, const double* u, int nrhs, double tol,
+                      double* grad_coef, double* grad_rhs);
+
 /* Index maps of BDDC level `level` (1-based).  Errors: INVALID. */
 int bddc_get_maps(bddc_handle h, int level, bddc_level_maps* out);
 

@@ -31,7 +31,7 @@ EXPORTED = [
     "bddc_default_opts", "bddc_analyze", "bddc_setup", "bddc_update_coef", "bddc_solve",
     "bddc_solve_host", "bddc_apply_precond", "bddc_apply_schur", "bddc_grad", "bddc_get_maps",
     "bddc_get_stats", "bddc_sizes", "bddc_free", "bddc_last_error", "bddc_kernel_launches",
-    "bddc_reset_profile",
+    "bddc_reset_profile", "bddc_grad_noalloc",
 ]
 PROF_TRSV, PROF_FACTOR, PROF_SPMV, PROF_CLASSES = 0, 1, 2, 4
 
@@ -114,6 +114,7 @@ def lib() -> C.CDLL:
     L.bddc_apply_precond.argtypes = [H, P, P, C.c_int]
     L.bddc_apply_schur.argtypes = [H, P, P, C.c_int]
     L.bddc_grad.argtypes = [H, P, P, C.c_int, C.c_double, P, P]
+    L.bddc_grad_noalloc.argtypes = [H, P, P, C.c_int, C.c_double, P, P]
     L.bddc_get_maps.argtypes = [H, C.c_int, C.POINTER(LevelMaps)]
     L.bddc_get_stats.argtypes = [H, C.POINTER(Stats)]
     L.bddc_sizes.argtypes = [H, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]

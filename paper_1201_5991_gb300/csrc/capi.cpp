@@ -1133,6 +1133,30 @@ int guarded(F&& fn) {
 }
 
 }  // namespace
+
+// ---- accessors used by noalloc.cu (read-only views of a set-up handle) --------------------
+void set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+
+bool grad_view(bddc_handle_s* h, GradView* v) {
+  if (!h || !h->factored || h->lv.empty()) return false;
+  const Level& L = h->lv[0];
+  v->n_elems = h->n_elems;
+  v->n_full = h->n_full;
+  v->n_free = h->n_free;
+  v->ne = h->npe * h->ndof;
+  v->ke = L.d.ke;
+  v->slot_elem = L.slot_elem;
+  v->coef = h->d_coef;
+  v->edof = h->d_edof;
+  v->free_of_full = h->d_free_of_full;
+  v->stream = h->st;
+  return true;
+}
+
+int adjoint_solve_into(bddc_handle_s* h, const double* dJdu, double* lam, int nrhs, double tol) {
+  return guarded([&]() { return solve_impl(h, dJdu, lam, nrhs, tol, nullptr); });
+}
+
 }  // namespace bddc
 
 // ====================================================================== C ABI

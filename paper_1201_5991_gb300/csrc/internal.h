@@ -84,6 +84,18 @@ struct LevelDev {
 // Counts every kernel launch of the library (defined in capi.cpp).
 void note_launch();
 
+// Read-only view of a set-up handle for the entry point in noalloc.cu (defined in capi.cpp).
+struct GradView {
+  int64_t n_elems, n_full, n_free;
+  int ne;
+  const double* ke;               // level-1 element matrices in slot order
+  const int32_t* slot_elem;
+  const double* coef;
+  const int64_t* edof;            // element -> full DOF ids
+  const int64_t* free_of_full;    // full DOF -> free id or -1
+  cudaStream_t stream;
+};
+
 // ---------------------------------------------------------------- assembly (assemble.cu)
 void launch_elem_q1(int physics, int dim, int64_t n_elems, const double* coords, const int32_t* conn,
                     const double* coef, double nu, const int32_t* slot_elem, double* ke, cudaStream_t st);
