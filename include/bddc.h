@@ -99,6 +99,8 @@ typedef struct {
   int use_graph;            /* 1: capture one Krylov iteration in a CUDA graph */
   int verbose;
   int profile;              /* 1: time kernel classes with CUDA events (bddc_stats.prof_*) */
+  int tensor_cores;         /* mixed: 1 = FP32 trailing updates on tcgen05 tensor cores (3xBF16 split,
+                               256-wide panels); 0 = FP32 CUDA cores */
 } bddc_opts;
 
 /* kernel classes timed when bddc_opts.profile = 1 */

@@ -57,7 +57,7 @@ class Opts(C.Structure):
     _fields_ = [
         ("precision", C.c_int), ("weights", C.c_int), ("all_corners", C.c_uint), ("maxit", C.c_int),
         ("refine_steps", C.c_int), ("flexible", C.c_int), ("use_graph", C.c_int), ("verbose", C.c_int),
-        ("profile", C.c_int),
+        ("profile", C.c_int), ("tensor_cores", C.c_int),
     ]
 
 

@@ -89,6 +89,8 @@ struct Level {
   int max_R = 0, max_Bc = 0, max_nc = 0, max_nG = 0, max_nGb = 0;
   std::vector<int> max_tiles;  // per factor step k
   std::vector<double> step_flops;  // tile flops of factor step k (all subdomains)
+  std::vector<int> narrow_tiles;   // per step k: in-panel update tiles (256-wide panels)
+  std::vector<int> wide_items;     // per super-step: tensor-core work items
   double trsv_bytes[2] = {0, 0};   // algorithmic bytes of one sweep over part 0 / part 1
   // sweep task lists [part][direction] in dependency order and their control words
   int2* tasks[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
@@ -121,6 +123,8 @@ struct Level {
 };
 
 int64_t pad_pos(const SubMeta& m, int64_t r) { return r < m.nI ? r : (int64_t)m.nIb * NB + (r - m.nI); }
+
+constexpr int kPanel = 4;   // tile columns per tensor-core super-panel (256)
 
 }  // namespace
 }  // namespace bddc
@@ -345,6 +349,8 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
   L.sum_nc = coff;
   L.max_tiles.assign(L.max_Bc, 0);
   L.step_flops.assign(L.max_Bc, 0.0);
+  L.narrow_tiles.assign(L.max_Bc, 0);
+  L.wide_items.assign((L.max_Bc + kPanel - 1) / kPanel + 1, 0);
   const double nb3 = (double)NB * NB * NB;
   const double wsz = L.fp32 ? 4.0 : 8.0;
   L.trsv_bytes[0] = L.trsv_bytes[1] = 0.0;
@@ -355,6 +361,17 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
       for (int j = k + 1; j < m.Bc; ++j) cnt += m.R - j;
       L.max_tiles[k] = std::max(L.max_tiles[k], (int)cnt);
       L.step_flops[k] += nb3 / 3.0 + nb3 * (double)(m.R - k - 1) + 2.0 * nb3 * (double)cnt;
+    }
+    for (int k = 0; k < m.Bc; ++k) {
+      const int kb1 = (k / kPanel + 1) * kPanel;
+      int64_t cnt = 0;
+      for (int j = k + 1; j < std::min(kb1, (int)m.Bc); ++j) cnt += m.R - j;
+      L.narrow_tiles[k] = std::max(L.narrow_tiles[k], (int)cnt);
+    }
+    for (int kb0 = 0; kb0 < m.Bc; kb0 += kPanel) {
+      int64_t cnt = 0;
+      for (int j = kb0 + kPanel; j < m.Bc; ++j) cnt += (m.R - j + 1) / 2;
+      L.wide_items[kb0 / kPanel] = std::max(L.wide_items[kb0 / kPanel], (int)cnt);
     }
     // a sweep reads the stored triangle once and the vector in and out
     L.trsv_bytes[0] += wsz * (0.5 * (double)m.nI * (m.nI + 1) + 2.0 * m.nI);
@@ -608,9 +625,22 @@ void factor_level(bddc_handle_s* h, Level& L, cudaStream_t st) {
   ck(cudaMemsetAsync(d.tiles, 0, sizeof(T) * (size_t)std::max<int64_t>(L.tile_elems, 1), st), "memset tiles");
   launch_densify_rows<T>(d, L.row_sub, st);
   launch_add_constraints<T>(d, st);
-  for (int k = 0; k < L.max_Bc; ++k) {
-    ProfScope ps(h, BDDC_PROF_FACTOR, 0.0, L.step_flops[k]);
-    launch_potrf_step<T>(d, k, L.max_R, L.max_tiles[k], st);
+  if (sizeof(T) == 4 && h->opts.tensor_cores) {
+    // 256-wide panels: in-panel steps on CUDA cores, the rank-256 trailing update on tcgen05
+    for (int kb0 = 0; kb0 < L.max_Bc; kb0 += kPanel) {
+      const int kb1 = kb0 + kPanel;
+      double fl = 0.0;
+      for (int k = kb0; k < std::min(kb1, L.max_Bc); ++k) fl += L.step_flops[k];
+      ProfScope ps(h, BDDC_PROF_FACTOR, 0.0, fl);
+      for (int k = kb0; k < std::min(kb1, L.max_Bc); ++k)
+        launch_potrf_step<T>(d, k, L.max_R, L.narrow_tiles[k], kb1, st);
+      launch_update_tc(d, kb0, kb1, L.wide_items[kb0 / kPanel], st);
+    }
+  } else {
+    for (int k = 0; k < L.max_Bc; ++k) {
+      ProfScope ps(h, BDDC_PROF_FACTOR, 0.0, L.step_flops[k]);
+      launch_potrf_step<T>(d, k, L.max_R, L.max_tiles[k], 1 << 30, st);
+    }
   }
   if (L.max_nc > 0) {
     launch_gram_chol(d, L.fp32 ? 1 : 0, L.max_nc, st);
@@ -1173,6 +1203,8 @@ void bddc_default_opts(bddc_opts* o) {
   o->flexible = -1;
   o->use_graph = 1;
   o->verbose = 0;
+  o->profile = 0;
+  o->tensor_cores = 1;
 }
 
 int bddc_analyze(const bddc_mesh* mesh, const bddc_partition* part, unsigned constraints, const bddc_opts* opts,

@@ -133,14 +133,15 @@ __global__ void k_trsm_panel(LevelDev L, int k) {
     for (int b = 0; b < 4; ++b) g[(4 * ty + a) * NB + 4 * tx + b] = acc[a][b];
 }
 
-// ---- step k, part 3: trailing update A(i,j) -= L(i,k) L(j,k)^T, k < j <= i, j < Bc --------
+// ---- step k, part 3: trailing update A(i,j) -= L(i,k) L(j,k)^T, k < j <= i, j < min(Bc, jmax) --
 template <typename T>
-__global__ void k_syrk_update(LevelDev L, int k) {
+__global__ void k_syrk_update(LevelDev L, int k, int jmax) {
   const int s = blockIdx.y;
   const SubMeta m = L.meta[s];
   if (k >= m.Bc) return;
+  const int jend = jmax < m.Bc ? jmax : m.Bc;
   int t = blockIdx.x, j = k + 1, i = -1;
-  for (; j < m.Bc; ++j) {
+  for (; j < jend; ++j) {
     const int cnt = m.R - j;
     if (t < cnt) {
       i = j + t;
@@ -390,7 +391,7 @@ __global__ void k_psi_apply_add(LevelDev L, const double* __restrict__ zc_sub, T
 }  // namespace
 
 template <typename T>
-void launch_potrf_step(const LevelDev& L, int k, int max_R, int max_tiles, cudaStream_t st) {
+void launch_potrf_step(const LevelDev& L, int k, int max_R, int max_tiles, int jmax, cudaStream_t st) {
   const unsigned ns = (unsigned)L.n_sub;
   const size_t sm = 2 * NB * LDS * sizeof(T);
   static bool attr = false;   // opt in to more than 48 KB of dynamic shared memory once
@@ -402,7 +403,7 @@ void launch_potrf_step(const LevelDev& L, int k, int max_R, int max_tiles, cudaS
   { note_launch(); k_potrf_diag<T><<<ns, 256, 0, st>>>(L, k); }
   const int panel = max_R - k - 1;
   if (panel > 0) { note_launch(); k_trsm_panel<T><<<dim3((unsigned)panel, ns), 256, sm, st>>>(L, k); }
-  if (max_tiles > 0) { note_launch(); k_syrk_update<T><<<dim3((unsigned)max_tiles, ns), 256, sm, st>>>(L, k); }
+  if (max_tiles > 0) { note_launch(); k_syrk_update<T><<<dim3((unsigned)max_tiles, ns), 256, sm, st>>>(L, k, jmax); }
 }
 
 template <typename T>
@@ -445,7 +446,7 @@ void launch_psi_apply_add(const LevelDev& L, const double* zc_sub, T* vec, int m
 }
 
 #define INST(T)                                                                                 \
-  template void launch_potrf_step<T>(const LevelDev&, int, int, int, cudaStream_t);              \
+  template void launch_potrf_step<T>(const LevelDev&, int, int, int, int, cudaStream_t);         \
   template void launch_psi<T>(const LevelDev&, int, int, cudaStream_t);                          \
   template void launch_constraint_corr<T>(const LevelDev&, T*, int, cudaStream_t);               \
   template void launch_psi_t_apply<T>(const LevelDev&, const T*, double*, cudaStream_t);         \

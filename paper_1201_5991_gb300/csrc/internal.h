@@ -107,8 +107,11 @@ void launch_add_constraints(const LevelDev& L, cudaStream_t st);
 void launch_weights(const LevelDev& L, int multiplicity, const double* unused, cudaStream_t st);
 
 // ---------------------------------------------------------------- dense factor (dense.cu)
+// one block column k: diagonal tile + inverse, panel, trailing update of columns (k, jmax)
 template <typename T>
-void launch_potrf_step(const LevelDev& L, int k, int max_R, int max_tiles, cudaStream_t st);
+void launch_potrf_step(const LevelDev& L, int k, int max_R, int max_tiles, int jmax, cudaStream_t st);
+// update_tc.cu: rank-(64 (kb1-kb0)) trailing update of columns >= kb1 on the tensor cores (FP32 tiles)
+void launch_update_tc(const LevelDev& L, int kb0, int kb1, int max_items, cudaStream_t st);
 void launch_gram_chol(const LevelDev& L, int precision_fp32, int max_nc, cudaStream_t st);
 template <typename T>
 void launch_psi(const LevelDev& L, int max_nGb, int max_nc, cudaStream_t st);

@@ -44,7 +44,7 @@ def host_mesh(prob, n_levels: Optional[int] = None) -> _HostMesh:
 
 
 def make_opts(precision="mixed", weights="stiffness", all_corners=0, maxit=500, refine_steps=0, flexible=-1,
-              use_graph=1, profile=0) -> capi.Opts:
+              use_graph=1, profile=0, tensor_cores=1) -> capi.Opts:
     o = capi.Opts()
     capi.lib().bddc_default_opts(C.byref(o))
     o.precision = capi.PREC_MIXED if precision == "mixed" else capi.PREC_FP64
@@ -55,6 +55,7 @@ def make_opts(precision="mixed", weights="stiffness", all_corners=0, maxit=500, 
     o.flexible = int(flexible)
     o.use_graph = int(use_graph)
     o.profile = int(profile)
+    o.tensor_cores = int(tensor_cores)
     return o
 
 

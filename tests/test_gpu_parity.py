@@ -137,3 +137,28 @@ def test_error_codes():
     with pytest.raises(capi.BddcError) as ei:
         s.solve(_dev(f), tol=1e-8)
     assert ei.value.code == capi.ERR_NAN
+
+
+def test_tensor_core_factor_matches_cuda_core_factor():
+    # 12^3-element subdomains (n ~ 6k, 25 super-panels of 256).  Both FP32 factorisations (the
+    # tcgen05 3xBF16 trailing update and the CUDA-core update) carry FP32 rounding amplified by
+    # kappa(A_i) ~ 1e4.  Against the FP64 preconditioner (itself pinned to the oracle at 1e-10)
+    # the tensor-core error may exceed the CUDA-core one by the bf16x3 scheme's extra rounding:
+    # the dropped products a1 b2 + a2 b1 + a2 b2 add ~2^-23 relative per product, about one
+    # FP32 rounding more than an FMA, so at most 4x; a misplaced tile or wrong sign gives O(1).
+    # The tensor-core path must still solve to 1e-8.
+    p = meshgen.elasticity3d(24, 2, seed=2)
+    ref = fem.direct_solve(p)[:, 0]
+    s_tc = BddcSolver(p, precision="mixed", tensor_cores=1)
+    s_cc = BddcSolver(p, precision="mixed", tensor_cores=0)
+    s_64 = BddcSolver(p, precision="fp64")
+    r = torch.tensor(np.random.default_rng(6).standard_normal(s_tc.n_iface), dtype=torch.float64, device="cuda")
+    z_tc = s_tc.apply_precond(r).cpu().numpy()
+    z_cc = s_cc.apply_precond(r).cpu().numpy()
+    z_64 = s_64.apply_precond(r).cpu().numpy()
+    e_tc, e_cc = _rel(z_tc, z_64), _rel(z_cc, z_64)
+    print(f"FP32 preconditioner error vs FP64: tensor cores {e_tc:.3e}, CUDA cores {e_cc:.3e}")
+    assert e_tc < 4.0 * e_cc + 1e-7
+    assert e_tc < 1e-2
+    u = s_tc.solve(_dev(p.f[:, 0]), tol=1e-12).cpu().numpy()
+    assert _rel(u, ref) < 1e-8
