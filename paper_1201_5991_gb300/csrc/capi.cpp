@@ -97,6 +97,11 @@ struct Level {
   int ntasks[2][2] = {{0, 0}, {0, 0}};
   int* ctrl = nullptr;
   int n_ctrl = 0;
+  int64_t* rows[3] = {nullptr, nullptr, nullptr};   // interior rows, interface rows, all rows
+  int64_t nrows[3] = {0, 0, 0};
+  int32_t* crow_sub = nullptr;                      // subdomain of every constraint row
+  double* cc_t = nullptr;                           // [sum_nc] scratch of the constraint correction
+  double* cc_mu = nullptr;
   int ne_uniform = 0;          // level 1: entries per element row
   // device
   LevelDev d{};
@@ -583,6 +588,25 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
     }
   L.n_ctrl = (int)(1 + L.dinv_elems / NB2);
   L.ctrl = A.alloc<int>(L.n_ctrl);
+  {
+    std::vector<int64_t> rl[3];
+    std::vector<int32_t> cs;
+    for (int64_t s = 0; s < ns; ++s) {
+      const SubMeta& m = L.meta[s];
+      for (int r = 0; r < m.nI; ++r) rl[0].push_back(m.vec_off + r);
+      for (int r = 0; r < m.nG; ++r) rl[1].push_back(m.vec_off + (int64_t)m.nIb * NB + r);
+      for (int q = 0; q < m.nc; ++q) cs.push_back((int32_t)s);
+    }
+    rl[2] = rl[0];
+    rl[2].insert(rl[2].end(), rl[1].begin(), rl[1].end());
+    for (int k = 0; k < 3; ++k) {
+      L.nrows[k] = (int64_t)rl[k].size();
+      L.rows[k] = A.upload(rl[k], st);
+    }
+    L.crow_sub = A.upload(cs, st);
+    L.cc_t = A.alloc<double>(L.sum_nc);
+    L.cc_mu = A.alloc<double>(L.sum_nc);
+  }
   L.row_sub = A.upload(row_sub, st);
   L.slot_elem = A.upload(slot_elem, st);
   L.iface_dofs = A.upload(mp.iface_dofs, st);
@@ -700,7 +724,7 @@ void interior_solve_l1(bddc_handle_s* h, Level& L, const double* v, double* w, c
     launch_add_to_double<float>(w, t, n, st);
     if (it + 1 < steps) {
       ck(cudaMemcpyAsync(r, v, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
-      launch_spmv_rows(L.d, 0, w, r, -1.0, 1.0, L.row_sub, st);
+      launch_spmv_rows(L.d, L.rows[0], L.nrows[0], w, r, -1.0, 1.0, L.row_sub, st);
     }
   }
 }
@@ -711,10 +735,10 @@ void schur_apply(bddc_handle_s* h, const double* x, double* y, cudaStream_t st) 
   const int64_t n = L.n_vec;
   launch_gather_iface<double>(L.d, x, 0, L.dl0, st);                 // x_i = R_i x
   ck(cudaMemsetAsync(L.dl1, 0, sizeof(double) * n, st), "memset");
-  launch_spmv_rows(L.d, 0, L.dl0, L.dl1, 1.0, 0.0, L.row_sub, st);  // v = K_IG x_i
+  launch_spmv_rows(L.d, L.rows[0], L.nrows[0], L.dl0, L.dl1, 1.0, 0.0, L.row_sub, st);  // v = K_IG x_i
   interior_solve_l1(h, L, L.dl1, L.dl2, st);                        // w = K_II^{-1} v
   launch_axpy_loc(L.dl0, L.dl2, -1.0, n, st);                       // t = [-w ; x_i]
-  launch_spmv_rows(L.d, 1, L.dl0, L.dl1, 1.0, 0.0, L.row_sub, st);  // y_i = K_GG x_i - K_GI w
+  launch_spmv_rows(L.d, L.rows[1], L.nrows[1], L.dl0, L.dl1, 1.0, 0.0, L.row_sub, st);  // y_i = K_GG x_i - K_GI w
   launch_scatter_iface<double>(L.d, L.dl1, 0, y, st);                // y = sum R_i^T y_i
 }
 
@@ -723,7 +747,7 @@ void condensed_rhs(bddc_handle_s* h, const double* f, double* g, cudaStream_t st
   Level& L = h->lv[0];
   launch_gather_glob<double>(L.d, f, 0, L.dl1, st);
   interior_solve_l1(h, L, L.dl1, L.dl2, st);
-  launch_spmv_rows(L.d, 1, L.dl2, L.dl0, 1.0, 0.0, L.row_sub, st);
+  launch_spmv_rows(L.d, L.rows[1], L.nrows[1], L.dl2, L.dl0, 1.0, 0.0, L.row_sub, st);
   launch_scatter_iface<double>(L.d, L.dl0, 0, L.gi0, st);
   launch_iface_rhs(g, f, L.iface_dofs, L.gi0, L.d.n_iface, st);
 }
@@ -733,7 +757,7 @@ void recover(bddc_handle_s* h, const double* f, const double* uG, double* u, cud
   Level& L = h->lv[0];
   launch_gather_iface<double>(L.d, uG, 0, L.dl0, st);
   launch_gather_glob<double>(L.d, f, 0, L.dl1, st);
-  launch_spmv_rows(L.d, 0, L.dl0, L.dl1, -1.0, 1.0, L.row_sub, st);
+  launch_spmv_rows(L.d, L.rows[0], L.nrows[0], L.dl0, L.dl1, -1.0, 1.0, L.row_sub, st);
   interior_solve_l1(h, L, L.dl1, L.dl2, st);
   ck(cudaMemsetAsync(u, 0, sizeof(double) * h->n_free, st), "memset");
   launch_scatter_interior<double>(L.d, L.dl2, u, st);
@@ -760,7 +784,7 @@ void interface_step_t(bddc_handle_s* h, int l, const double* rhat, double* zhat,
   launch_psi_t_apply<T>(L.d, v, L.rc_sub, st);          // Psi_i^T r_i
   launch_coarse_gather(L.d, L.rc_sub, L.rC, st);        // r_C = sum R_Ci^T Psi_i^T r_i
   trsv_one<T>(h, L, v, 1, 0, st);                       // Eq. sub_cor via the trailing factor
-  launch_constraint_corr<T>(L.d, v, L.max_nc, st);
+  launch_constraint_corr<T>(L.d, v, L.crow_sub, L.sum_nc, L.cc_t, L.cc_mu, L.max_nGb, st);
   trsv_one<T>(h, L, v, 1, 1, st);
   const bool last = l + 2 == (int)h->lv.size();
   if (last)
@@ -788,13 +812,13 @@ void full_step_t(bddc_handle_s* h, int l, const double* r, double* z, cudaStream
   launch_gather_glob<T>(L.d, r, 0, v, st);                  // r_I
   trsv_pair<T>(h, L, v, 0, st);                                // u1 = A_II^{-1} r_I
   launch_convert<T, double>(v, L.dl0, n, st);
-  launch_spmv_rows(L.d, 1, L.dl0, L.dl1, 1.0, 0.0, L.row_sub, st);   // (A_GI u1)_i
+  launch_spmv_rows(L.d, L.rows[1], L.nrows[1], L.dl0, L.dl1, 1.0, 0.0, L.row_sub, st);   // (A_GI u1)_i
   launch_scatter_iface<double>(L.d, L.dl1, 0, L.gi0, st);
   launch_iface_rhs(L.gi1, r, L.iface_dofs, L.gi0, L.d.n_iface, st); // r'_G = r_G - A_GI u1
   interface_step(h, l, L.gi1, L.gi2, st);                             // z_G
   launch_gather_iface<double>(L.d, L.gi2, 0, L.dl0, st);
   launch_gather_glob<double>(L.d, r, 0, L.dl1, st);
-  launch_spmv_rows(L.d, 0, L.dl0, L.dl1, -1.0, 1.0, L.row_sub, st);  // r_I - A_IG z_G
+  launch_spmv_rows(L.d, L.rows[0], L.nrows[0], L.dl0, L.dl1, -1.0, 1.0, L.row_sub, st);  // r_I - A_IG z_G
   launch_convert<double, T>(L.dl1, v, n, st);
   trsv_pair<T>(h, L, v, 0, st);                                           // z_I
   ck(cudaMemsetAsync(z, 0, sizeof(double) * L.d.n_dof, st), "memset");
@@ -838,7 +862,7 @@ void choose_refinement(bddc_handle_s* h) {
   double* v = h->full_a;   // n_vec-sized scratch allocated for this purpose
   double* w = h->full_b;
   ck(cudaMemsetAsync(v, 0, sizeof(double) * n, st), "memset");
-  launch_spmv_rows(L.d, 0, L.dl0, v, 1.0, 0.0, L.row_sub, st);
+  launch_spmv_rows(L.d, L.rows[0], L.nrows[0], L.dl0, v, 1.0, 0.0, L.row_sub, st);
   const double nv = std::sqrt(dot_host(h, v, v, n));
   int best = 1;
   double prev = 1e300;
@@ -846,7 +870,7 @@ void choose_refinement(bddc_handle_s* h) {
     h->refine_steps = steps;
     interior_solve_l1(h, L, v, w, st);
     ck(cudaMemcpyAsync(L.dl3, v, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
-    launch_spmv_rows(L.d, 0, w, L.dl3, -1.0, 1.0, L.row_sub, st);
+    launch_spmv_rows(L.d, L.rows[0], L.nrows[0], w, L.dl3, -1.0, 1.0, L.row_sub, st);
     const double rel = nv > 0 ? std::sqrt(dot_host(h, L.dl3, L.dl3, n)) / nv : 0.0;
     if (rel > 0.5 * prev) break;          // stagnated at round-off: the previous count suffices
     best = steps;

@@ -29,6 +29,7 @@ __device__ __forceinline__ void flag_breakdown(int* status, int sub) {
 }
 
 constexpr int LDS = NB + 4;   // k-major shared tile stride (multiple of 4 for vector loads)
+constexpr int kMaxCoarseLocal = 256;   // coarse DOFs of one subdomain handled by k_psi_t_apply
 
 template <typename T>
 __device__ __forceinline__ void load_kmajor(T* s, const T* __restrict__ g) {
@@ -167,22 +168,28 @@ __global__ void k_syrk_update(LevelDev L, int k, int jmax) {
 }
 
 // ---- G = Y_G Y_G^T in FP64, Cholesky, inverse; K_C = G^{-1} - rho I ----------------------
+// one warp per entry (a, b), a >= b, of one subdomain's G; lanes stride over the interface
+// columns (contiguous inside a tile row), FP64 products, fixed-order warp reduction
 template <typename T>
 __global__ void k_gram(LevelDev L) {
-  const int s = blockIdx.x;
+  const int s = blockIdx.y;
   const SubMeta m = L.meta[s];
   const int nc = m.nc;
-  if (nc == 0) return;
-  double* G = L.Ginv + m.g_off;
-  const int npair = nc * nc;
-  for (int p = threadIdx.x; p < npair; p += blockDim.x) {
-    const int a = p / nc, b = p % nc;
-    if (b > a) continue;
-    const T* ya = tile_ptr<T>(m, L.tiles, m.Bc + a / NB, 0) + (a % NB) * NB;
-    const T* yb = tile_ptr<T>(m, L.tiles, m.Bc + b / NB, 0) + (b % NB) * NB;
-    double acc = 0.0;
-    for (int j = m.nIb; j < m.Bc; ++j)
-      for (int c = 0; c < NB; ++c) acc += (double)ya[(int64_t)j * NB2 + c] * (double)yb[(int64_t)j * NB2 + c];
+  const int pair = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (pair >= nc * nc) return;
+  const int a = pair / nc, b = pair % nc;
+  if (b > a) return;
+  const T* ya = tile_ptr<T>(m, L.tiles, m.Bc + a / NB, m.nIb) + (a % NB) * NB;
+  const T* yb = tile_ptr<T>(m, L.tiles, m.Bc + b / NB, m.nIb) + (b % NB) * NB;
+  double acc = 0.0;
+  for (int c = lane; c < m.nGb * NB; c += 32) {
+    const int64_t o = (int64_t)(c / NB) * NB2 + (c % NB);
+    acc += (double)ya[o] * (double)yb[o];
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) {
+    double* G = L.Ginv + m.g_off;
     G[a * nc + b] = acc;
     G[b * nc + a] = acc;
   }
@@ -317,45 +324,57 @@ __global__ void k_trsm_back_psi(LevelDev L) {
   }
 }
 
-// v_G -= Y_G^T G^{-1} Y_G v_G  (the constraint part of Eq. sub_cor), one block per subdomain
+// v_G -= Y_G^T G^{-1} Y_G v_G  (the constraint part of Eq. sub_cor), in three launches with
+// all subdomains' rows in flight: t = Y_G v (one warp per constraint row), mu = G^{-1} t (one
+// warp per row of G^{-1}), v -= Y_G^T mu (one thread per interface column).
 template <typename T>
-__global__ void k_constraint_corr(LevelDev L, T* __restrict__ vec) {
-  const int s = blockIdx.x;
+__global__ void k_cc_yv(LevelDev L, const T* __restrict__ vec, const int32_t* __restrict__ crow_sub,
+                        int64_t total_rows, double* __restrict__ t) {
+  const int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (g >= total_rows) return;
+  const int s = crow_sub[g];
   const SubMeta m = L.meta[s];
-  const int nc = m.nc;
-  if (nc == 0) return;
-  extern __shared__ double sh[];
-  double* t = sh;          // [nc]
-  double* mu = sh + nc;    // [nc]
-  T* v = vec + m.vec_off + m.nIb * NB;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const int ncolG = m.nGb * NB;
-  for (int p = warp; p < nc; p += nw) {
-    T acc = (T)0;
-    for (int c = lane; c < ncolG; c += 32) {
-      const T y = tile_ptr<T>(m, L.tiles, m.Bc + p / NB, m.nIb + c / NB)[(p % NB) * NB + (c % NB)];
-      acc += y * v[c];
-    }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) t[p] = (double)acc;
-  }
-  __syncthreads();
-  const double* Gi = L.Ginv + m.g_off;
-  for (int p = threadIdx.x; p < nc; p += blockDim.x) {
-    double acc = 0.0;
-    for (int q = 0; q < nc; ++q) acc += Gi[p * nc + q] * t[q];
-    mu[p] = acc;
-  }
-  __syncthreads();
-  for (int c = threadIdx.x; c < ncolG; c += blockDim.x) {
-    T acc = (T)0;
-    for (int p = 0; p < nc; ++p)
-      acc += tile_ptr<T>(m, L.tiles, m.Bc + p / NB, m.nIb + c / NB)[(p % NB) * NB + (c % NB)] * (T)mu[p];
-    v[c] = v[c] - acc;
-  }
+  const int p = (int)(g - m.c_off);
+  const T* v = vec + m.vec_off + m.nIb * NB;
+  const T* yrow = tile_ptr<T>(m, L.tiles, m.Bc + p / NB, m.nIb) + (p % NB) * NB;
+  T acc = (T)0;
+  for (int c = lane; c < m.nGb * NB; c += 32) acc += yrow[(int64_t)(c / NB) * NB2 + (c % NB)] * v[c];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) t[g] = (double)acc;
 }
 
-// rc_sub = Psi_G^T v_G (FP64), one block per subdomain
+__global__ void k_cc_mu(LevelDev L, const int32_t* __restrict__ crow_sub, int64_t total_rows,
+                        const double* __restrict__ t, double* __restrict__ mu) {
+  const int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (g >= total_rows) return;
+  const int s = crow_sub[g];
+  const SubMeta m = L.meta[s];
+  const int p = (int)(g - m.c_off);
+  const double* Gi = L.Ginv + m.g_off + (int64_t)p * m.nc;
+  double acc = 0.0;
+  for (int q = lane; q < m.nc; q += 32) acc += Gi[q] * t[m.c_off + q];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) mu[g] = acc;
+}
+
+template <typename T>
+__global__ void k_cc_update(LevelDev L, T* __restrict__ vec, const double* __restrict__ mu) {
+  const int s = blockIdx.y;
+  const SubMeta m = L.meta[s];
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= m.nGb * NB || m.nc == 0) return;
+  T acc = (T)0;
+  for (int p = 0; p < m.nc; ++p)
+    acc += tile_ptr<T>(m, L.tiles, m.Bc + p / NB, m.nIb + c / NB)[(p % NB) * NB + (c % NB)] * (T)mu[m.c_off + p];
+  T* v = vec + m.vec_off + m.nIb * NB;
+  v[c] = v[c] - acc;
+}
+
+// rc_sub = Psi_G^T v_G (FP64 result), one block per subdomain: warp w takes interface rows
+// w, w+8, ..., lane l the coarse DOFs l, l+32, ... (coalesced reads of Psi's rows); the eight
+// warps' partial sums are added in a fixed order.
 template <typename T>
 __global__ void k_psi_t_apply(LevelDev L, const T* __restrict__ vec, double* __restrict__ rc_sub) {
   const int s = blockIdx.x;
@@ -363,12 +382,31 @@ __global__ void k_psi_t_apply(LevelDev L, const T* __restrict__ vec, double* __r
   const int nc = m.nc;
   const T* v = vec + m.vec_off + m.nIb * NB;
   const T* P = (const T*)L.psi + m.psi_off;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int q = warp; q < nc; q += nw) {
-    T acc = (T)0;
-    for (int c = lane; c < m.nG; c += 32) acc += P[(int64_t)c * nc + q] * v[c];
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) rc_sub[m.c_off + q] = (double)acc;
+  __shared__ T part[8][kMaxCoarseLocal];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int q0 = 0; q0 < nc; q0 += kMaxCoarseLocal) {   // coarse DOFs in chunks of 256
+    T acc[kMaxCoarseLocal / 32];
+#pragma unroll
+    for (int u = 0; u < kMaxCoarseLocal / 32; ++u) acc[u] = (T)0;
+    for (int c = warp; c < m.nG; c += 8) {
+      const T x = v[c];
+      const T* row = P + (int64_t)c * nc + q0;
+#pragma unroll
+      for (int u = 0; u < kMaxCoarseLocal / 32; ++u) {
+        const int q = lane + 32 * u;
+        if (q0 + q < nc) acc[u] += row[q] * x;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kMaxCoarseLocal / 32; ++u) part[warp][lane + 32 * u] = acc[u];
+    __syncthreads();
+    for (int q = threadIdx.x; q < kMaxCoarseLocal && q0 + q < nc; q += blockDim.x) {
+      T t = (T)0;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) t += part[w][q];
+      rc_sub[m.c_off + q0 + q] = (double)t;
+    }
+    __syncthreads();
   }
 }
 
@@ -407,17 +445,18 @@ void launch_potrf_step(const LevelDev& L, int k, int max_R, int max_tiles, int j
 }
 
 template <typename T>
-void launch_gram_chol_t(const LevelDev& L, cudaStream_t st) {
+void launch_gram_chol_t(const LevelDev& L, int max_nc, cudaStream_t st) {
   const unsigned ns = (unsigned)L.n_sub;
-  { note_launch(); k_gram<T><<<ns, 256, 0, st>>>(L); }
+  const unsigned gx = (unsigned)(((int64_t)max_nc * max_nc + 7) / 8);
+  { note_launch(); k_gram<T><<<dim3(gx, ns), 256, 0, st>>>(L); }
   { note_launch(); k_small_chol_inv<<<ns, 256, 0, st>>>(L); }
 }
 
-void launch_gram_chol(const LevelDev& L, int precision_fp32, int, cudaStream_t st) {
+void launch_gram_chol(const LevelDev& L, int precision_fp32, int max_nc, cudaStream_t st) {
   if (precision_fp32)
-    launch_gram_chol_t<float>(L, st);
+    launch_gram_chol_t<float>(L, max_nc, st);
   else
-    launch_gram_chol_t<double>(L, st);
+    launch_gram_chol_t<double>(L, max_nc, st);
 }
 
 template <typename T>
@@ -429,9 +468,13 @@ void launch_psi(const LevelDev& L, int max_nGb, int max_nc, cudaStream_t st) {
 }
 
 template <typename T>
-void launch_constraint_corr(const LevelDev& L, T* vec, int max_nc, cudaStream_t st) {
-  if (max_nc <= 0) return;
-  { note_launch(); k_constraint_corr<T><<<(unsigned)L.n_sub, 256, 2 * max_nc * sizeof(double), st>>>(L, vec); }
+void launch_constraint_corr(const LevelDev& L, T* vec, const int32_t* crow_sub, int64_t total_rows, double* t,
+                            double* mu, int max_nGb, cudaStream_t st) {
+  if (total_rows <= 0) return;
+  const unsigned g = (unsigned)((total_rows + 7) / 8);
+  { note_launch(); k_cc_yv<T><<<g, 256, 0, st>>>(L, vec, crow_sub, total_rows, t); }
+  { note_launch(); k_cc_mu<<<g, 256, 0, st>>>(L, crow_sub, total_rows, t, mu); }
+  { note_launch(); k_cc_update<T><<<dim3((unsigned)((max_nGb * NB + 255) / 256), (unsigned)L.n_sub), 256, 0, st>>>(L, vec, mu); }
 }
 
 template <typename T>
@@ -448,7 +491,8 @@ void launch_psi_apply_add(const LevelDev& L, const double* zc_sub, T* vec, int m
 #define INST(T)                                                                                 \
   template void launch_potrf_step<T>(const LevelDev&, int, int, int, int, cudaStream_t);         \
   template void launch_psi<T>(const LevelDev&, int, int, cudaStream_t);                          \
-  template void launch_constraint_corr<T>(const LevelDev&, T*, int, cudaStream_t);               \
+  template void launch_constraint_corr<T>(const LevelDev&, T*, const int32_t*, int64_t, double*, double*, int, \
+                                         cudaStream_t);                                                   \
   template void launch_psi_t_apply<T>(const LevelDev&, const T*, double*, cudaStream_t);         \
   template void launch_psi_apply_add<T>(const LevelDev&, const double*, T*, int, cudaStream_t);
 INST(float)

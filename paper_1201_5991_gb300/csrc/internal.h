@@ -120,8 +120,10 @@ void launch_psi(const LevelDev& L, int max_nGb, int max_nc, cudaStream_t st);
 template <typename T>
 void launch_sweep(const LevelDev& L, T* vec, const int2* tasks, int ntasks, int part, int backward, int* ctrl,
                   int n_ctrl, int grid_max, cudaStream_t st);
+// crow_sub: subdomain of every constraint row (flat over the level); t, mu: scratch [total_rows]
 template <typename T>
-void launch_constraint_corr(const LevelDev& L, T* vec, int max_nc, cudaStream_t st);
+void launch_constraint_corr(const LevelDev& L, T* vec, const int32_t* crow_sub, int64_t total_rows, double* t,
+                            double* mu, int max_nGb, cudaStream_t st);
 template <typename T>
 void launch_psi_t_apply(const LevelDev& L, const T* vec, double* rc_sub, cudaStream_t st);
 template <typename T>
@@ -136,8 +138,9 @@ template <typename T>
 void launch_gather_glob(const LevelDev& L, const double* x, int part, T* loc, cudaStream_t st);
 template <typename T>
 void launch_scatter_interior(const LevelDev& L, const T* loc, double* y, cudaStream_t st);
-void launch_spmv_rows(const LevelDev& L, int part, const double* x, double* y, double alpha, double beta,
-                      const int32_t* row_sub, cudaStream_t st);
+// rows: flat padded row indices (interior rows, interface rows or both, of every subdomain)
+void launch_spmv_rows(const LevelDev& L, const int64_t* rows, int64_t nrows, const double* x, double* y, double alpha,
+                      double beta, const int32_t* row_sub, cudaStream_t st);
 template <typename Tin, typename Tout>
 void launch_convert(const Tin* in, Tout* out, int64_t n, cudaStream_t st);
 void launch_axpy_loc(double* y, const double* x, double a, int64_t n, cudaStream_t st);

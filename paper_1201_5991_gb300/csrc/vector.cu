@@ -53,23 +53,21 @@ __global__ void k_scatter_interior(LevelDev L, const T* __restrict__ loc, double
   if (g >= 0 && L.loc2iface[p] < 0) y[g] = (double)loc[p];
 }
 
-// y[row] = beta*y[row] + alpha * (K_i x)[row] over rows of the selected part; one warp per row.
-__global__ void k_spmv(LevelDev L, int part, const double* __restrict__ x, double* __restrict__ y, double alpha,
-                       double beta, const int32_t* __restrict__ row_sub) {
-  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (row >= L.n_vec) return;
+// y[row] = beta*y[row] + alpha * (K_i x)[row] for the rows of a list (interior rows, interface
+// rows or all rows of every subdomain); 16 lanes per row, two rows per warp.
+__global__ void k_spmv(LevelDev L, const int64_t* __restrict__ rows, int64_t nrows, const double* __restrict__ x,
+                       double* __restrict__ y, double alpha, double beta, const int32_t* __restrict__ row_sub) {
+  const int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 4) + (threadIdx.x >> 4);
+  const int l = threadIdx.x & 15;
+  const bool valid = g < nrows;
+  const int64_t row = rows[valid ? g : 0];
   const int s = row_sub[row];
-  const SubMeta& m = L.meta[s];
-  const int r = (int)(row - m.vec_off);
-  const bool interior = r < m.nI;
-  const bool iface = r >= m.nIb * NB && r < m.nIb * NB + m.nG;
-  if (!((part == 0 && interior) || (part == 1 && iface) || (part == 2 && (interior || iface)))) return;
+  const double* xs = x + L.meta[s].vec_off;
   double acc = 0.0;
-  const double* xs = x + m.vec_off;
-  for (int64_t q = L.row_ptr[row] + lane; q < L.row_ptr[row + 1]; q += 32) acc += L.val[q] * xs[L.col[q]];
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) y[row] = (beta == 0.0 ? 0.0 : beta * y[row]) + alpha * acc;
+  if (valid)
+    for (int64_t q = L.row_ptr[row] + l; q < L.row_ptr[row + 1]; q += 16) acc += L.val[q] * xs[L.col[q]];
+  for (int o = 8; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (valid && l == 0) y[row] = (beta == 0.0 ? 0.0 : beta * y[row]) + alpha * acc;
 }
 
 template <typename Tin, typename Tout>
@@ -244,9 +242,9 @@ template <typename T>
 void launch_scatter_interior(const LevelDev& L, const T* loc, double* y, cudaStream_t st) {
   if (L.n_vec > 0) { note_launch(); k_scatter_interior<T><<<nblocks(L.n_vec, 256), 256, 0, st>>>(L, loc, y); }
 }
-void launch_spmv_rows(const LevelDev& L, int part, const double* x, double* y, double alpha, double beta,
-                      const int32_t* row_sub, cudaStream_t st) {
-  if (L.n_vec > 0) { note_launch(); k_spmv<<<nblocks(L.n_vec, 8), 256, 0, st>>>(L, part, x, y, alpha, beta, row_sub); }
+void launch_spmv_rows(const LevelDev& L, const int64_t* rows, int64_t nrows, const double* x, double* y, double alpha,
+                      double beta, const int32_t* row_sub, cudaStream_t st) {
+  if (nrows > 0) { note_launch(); k_spmv<<<nblocks(nrows, 16), 256, 0, st>>>(L, rows, nrows, x, y, alpha, beta, row_sub); }
 }
 template <typename Tin, typename Tout>
 void launch_convert(const Tin* in, Tout* out, int64_t n, cudaStream_t st) {
