@@ -113,6 +113,7 @@ typedef struct {
   int iterations;           /* Krylov iterations of the last solve (max over right-hand sides) */
   int converged;            /* 1 when every right-hand side met the tolerance */
   double rel_residual;      /* max over right-hand sides of ||g - S u|| / ||g|| at exit */
+  double rhs_norm;          /* ||g|| (condensed right-hand side) of the first right-hand side */
   double lambda_min, lambda_max;  /* Lanczos estimate from PCG (first right-hand side) */
   int n_levels;
   int64_t n_sub[BDDC_MAX_LEVELS];     /* subdomains of BDDC level l (index l-1) */

@@ -63,7 +63,7 @@ class Opts(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [
-        ("iterations", C.c_int), ("converged", C.c_int), ("rel_residual", C.c_double),
+        ("iterations", C.c_int), ("converged", C.c_int), ("rel_residual", C.c_double), ("rhs_norm", C.c_double),
         ("lambda_min", C.c_double), ("lambda_max", C.c_double), ("n_levels", C.c_int),
         ("n_sub", C.c_int64 * MAX_LEVELS), ("n_dof", C.c_int64 * MAX_LEVELS),
         ("n_iface", C.c_int64 * MAX_LEVELS), ("n_coarse", C.c_int64 * MAX_LEVELS),

@@ -170,6 +170,10 @@ struct bddc_handle_s {
   double *full_a = nullptr, *full_b = nullptr;
   int refine_steps = 0;
   int grid_max = 304;                  // persistent sweep grid: 2 CTAs per SM
+  cudaStream_t cap_st = nullptr;       // private stream for graph capture
+  cudaGraphExec_t iter_graph = nullptr;  // one captured PCG iteration
+  int iter_graph_flexible = -1;
+  int64_t graph_kernels = 0;           // kernel nodes in iter_graph
   bddc_stats stats{};
   bool factored = false;
   // optional per-class CUDA-event timing
@@ -179,9 +183,16 @@ struct bddc_handle_s {
     double bytes, flops;
   };
   std::vector<ProfRec> prof_pending;
+  std::vector<ProfRec> graph_prof;     // event pairs recorded by every replay of iter_graph
   std::vector<cudaEvent_t> event_pool;
   ~bddc_handle_s() {
+    if (iter_graph) cudaGraphExecDestroy(iter_graph);
+    if (cap_st) cudaStreamDestroy(cap_st);
     for (auto& r : prof_pending) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+    for (auto& r : graph_prof) {
       cudaEventDestroy(r.a);
       cudaEventDestroy(r.b);
     }
@@ -193,6 +204,17 @@ namespace bddc {
 namespace {
 
 constexpr int kDotBlocks = 304;   // 2 x SM count of a GB300; fixed for reproducible sums
+
+// Event record that also works inside stream capture (there it becomes an event-record node of
+// the graph instead of a capture-internal dependency).
+void record_event(cudaEvent_t e, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  ck(cudaStreamIsCapturing(st, &cs), "cudaStreamIsCapturing");
+  if (cs == cudaStreamCaptureStatusActive)
+    ck(cudaEventRecordWithFlags(e, st, cudaEventRecordExternal), "cudaEventRecordWithFlags");
+  else
+    ck(cudaEventRecord(e, st), "cudaEventRecord");
+}
 
 cudaEvent_t take_event(bddc_handle_s* h) {
   if (!h->event_pool.empty()) {
@@ -211,11 +233,13 @@ struct ProfScope {
   bddc_handle_s* h;
   int cls;
   double bytes, flops;
+  cudaStream_t st;
   cudaEvent_t a = nullptr;
-  ProfScope(bddc_handle_s* h_, int cls_, double bytes_, double flops_) : h(h_), cls(cls_), bytes(bytes_), flops(flops_) {
+  ProfScope(bddc_handle_s* h_, int cls_, double bytes_, double flops_, cudaStream_t st_)
+      : h(h_), cls(cls_), bytes(bytes_), flops(flops_), st(st_) {
     if (h->opts.profile) {
       a = take_event(h);
-      ck(cudaEventRecord(a, h->st), "cudaEventRecord");
+      record_event(a, st);
     }
   }
   ~ProfScope() {
@@ -226,10 +250,26 @@ struct ProfScope {
     } catch (...) {
       return;
     }
-    cudaEventRecord(b, h->st);
+    try {
+      record_event(b, st);
+    } catch (...) {
+      return;
+    }
     h->prof_pending.push_back({a, b, cls, bytes, flops});
   }
 };
+
+// After a replay of iter_graph has completed: add the durations of its captured event pairs.
+void accumulate_graph_profile(bddc_handle_s* h) {
+  for (auto& r : h->graph_prof) {
+    float ms = 0.f;
+    ck(cudaEventElapsedTime(&ms, r.a, r.b), "cudaEventElapsedTime");
+    h->stats.prof_ms[r.cls] += ms;
+    h->stats.prof_launches[r.cls] += 1;
+    h->stats.prof_bytes[r.cls] += r.bytes;
+    h->stats.prof_flops[r.cls] += r.flops;
+  }
+}
 
 void flush_profile(bddc_handle_s* h) {
   if (h->prof_pending.empty()) return;
@@ -655,14 +695,14 @@ void factor_level(bddc_handle_s* h, Level& L, cudaStream_t st) {
       const int kb1 = kb0 + kPanel;
       double fl = 0.0;
       for (int k = kb0; k < std::min(kb1, L.max_Bc); ++k) fl += L.step_flops[k];
-      ProfScope ps(h, BDDC_PROF_FACTOR, 0.0, fl);
+      ProfScope ps(h, BDDC_PROF_FACTOR, 0.0, fl, st);
       for (int k = kb0; k < std::min(kb1, L.max_Bc); ++k)
         launch_potrf_step<T>(d, k, L.max_R, L.narrow_tiles[k], kb1, st);
       launch_update_tc(d, kb0, kb1, L.wide_items[kb0 / kPanel], st);
     }
   } else {
     for (int k = 0; k < L.max_Bc; ++k) {
-      ProfScope ps(h, BDDC_PROF_FACTOR, 0.0, L.step_flops[k]);
+      ProfScope ps(h, BDDC_PROF_FACTOR, 0.0, L.step_flops[k], st);
       launch_potrf_step<T>(d, k, L.max_R, L.max_tiles[k], 1 << 30, st);
     }
   }
@@ -694,7 +734,7 @@ void reset_status(bddc_handle_s* h) {
 // ------------------------------------------------------------------ solve-phase building blocks
 template <typename T>
 void trsv_one(bddc_handle_s* h, Level& L, T* v, int part, int backward, cudaStream_t st) {
-  ProfScope ps(h, BDDC_PROF_TRSV, L.trsv_bytes[part], 0.0);
+  ProfScope ps(h, BDDC_PROF_TRSV, L.trsv_bytes[part], 0.0, st);
   launch_sweep<T>(L.d, v, L.tasks[part][backward], L.ntasks[part][backward], part, backward, L.ctrl, L.n_ctrl,
                   h->grid_max, st);
 }
@@ -1027,8 +1067,70 @@ struct PcgResult {
   int iterations = 0;
   bool converged = false;
   double rel = 0.0;
+  double gnorm = 0.0;
   std::vector<double> alpha, beta;
 };
+
+// One full PCG iteration (Sec. 4) on the level-1 interface, all on the device:
+// q = S p, alpha = r.z / p.q, x += alpha p, r -= alpha q, ||r||^2, z = M^{-1} r (Algorithm 2),
+// beta (Fletcher-Reeves or flexible), p = z + beta p.  Scalars stay in device memory.
+void pcg_body(bddc_handle_s* h, double* x, int flexible, cudaStream_t st) {
+  const int64_t n = h->lv[0].d.n_iface;
+  double* S = h->scal;
+  schur_apply(h, h->vp, h->vq, st);
+  launch_dot(h->vp, h->vq, n, h->partial, kDotBlocks, S + 1, st);
+  launch_pcg_scalars(S, 0, flexible, st);
+  if (flexible) ck(cudaMemcpyAsync(h->vrold, h->vr, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
+  launch_pcg_update_x_r(x, h->vr, h->vp, h->vq, S, n, st);
+  launch_dot(h->vr, h->vr, n, h->partial, kDotBlocks, S + 5, st);
+  precond(h, h->vr, h->vz, st);
+  launch_dot(h->vr, h->vz, n, h->partial, kDotBlocks, S + 4, st);
+  if (flexible) launch_dot(h->vz, h->vrold, n, h->partial, kDotBlocks, S + 7, st);
+  launch_pcg_scalars(S, 1, flexible, st);
+  launch_pcg_update_p(h->vp, h->vz, S, n, st);
+}
+
+// Capture pcg_body into a CUDA graph (once per handle; the buffers never move).
+void capture_iteration(bddc_handle_s* h, int flexible) {
+  if (!h->cap_st) ck(cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking), "cudaStreamCreate");
+  cudaGraph_t g = nullptr;
+  flush_profile(h);   // events recorded so far belong to eager launches
+  const int64_t launches0 = g_launches.load();
+  ck(cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+  try {
+    pcg_body(h, h->vx, flexible, h->cap_st);
+  } catch (...) {
+    cudaStreamEndCapture(h->cap_st, &g);
+    if (g) cudaGraphDestroy(g);
+    throw;
+  }
+  ck(cudaStreamEndCapture(h->cap_st, &g), "cudaStreamEndCapture");
+  // captured kernels did not run: count them once per replay instead
+  h->graph_kernels = g_launches.load() - launches0;
+  g_launches.fetch_sub(h->graph_kernels);
+  h->graph_prof.insert(h->graph_prof.end(), h->prof_pending.begin(), h->prof_pending.end());
+  h->prof_pending.clear();
+  cudaGraphExec_t ex = nullptr;
+  const cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  ck(e, "cudaGraphInstantiate");
+  h->iter_graph = ex;
+  h->iter_graph_flexible = flexible;
+}
+
+// r = g - S x, z = M^{-1} r, p = z, rz = r.z  (start, or restart after a failed true-residual check)
+void pcg_start(bddc_handle_s* h, const double* g, double* x, bool x_zero, cudaStream_t st) {
+  const int64_t n = h->lv[0].d.n_iface;
+  double* S = h->scal;
+  ck(cudaMemcpyAsync(h->vr, g, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
+  if (!x_zero) {
+    schur_apply(h, x, h->vq, st);
+    launch_axpy_loc(h->vr, h->vq, -1.0, n, st);
+  }
+  precond(h, h->vr, h->vz, st);
+  ck(cudaMemcpyAsync(h->vp, h->vz, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
+  launch_dot(h->vr, h->vz, n, h->partial, kDotBlocks, S + 0, st);
+}
 
 PcgResult pcg(bddc_handle_s* h, const double* g, double* x, double tol, int maxit) {
   cudaStream_t st = h->st;
@@ -1043,57 +1145,62 @@ PcgResult pcg(bddc_handle_s* h, const double* g, double* x, double tol, int maxi
   double* S = h->scal;
   ck(cudaMemsetAsync(S, 0, sizeof(double) * 16, st), "memset");
   launch_dot(g, g, n, h->partial, kDotBlocks, S + 6, st);
-  ck(cudaMemcpyAsync(h->vr, g, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
-  precond(h, h->vr, h->vz, st);
-  ck(cudaMemcpyAsync(h->vp, h->vz, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
-  launch_dot(h->vr, h->vz, n, h->partial, kDotBlocks, S + 0, st);
+  pcg_start(h, g, x, true, st);
   ck(cudaMemcpyAsync(h->h_scal, S, sizeof(double) * 16, cudaMemcpyDeviceToHost, st), "d2h");
   ck(cudaStreamSynchronize(st), "sync");
   const double gg = h->h_scal[6];
   if (!std::isfinite(gg)) fail(BDDC_ERR_NAN, "NaN in the condensed right-hand side");
+  res.gnorm = std::sqrt(gg);
   if (gg == 0.0) {
     res.converged = true;
     return res;
   }
+  const bool graphs = h->opts.use_graph && x == h->vx;
+  if (h->iter_graph && h->iter_graph_flexible != flexible) {
+    cudaGraphExecDestroy(h->iter_graph);
+    h->iter_graph = nullptr;
+    for (auto& r : h->graph_prof) {
+      h->event_pool.push_back(r.a);
+      h->event_pool.push_back(r.b);
+    }
+    h->graph_prof.clear();
+  }
   bool checked = false;
   for (int it = 1; it <= maxit; ++it) {
-    schur_apply(h, h->vp, h->vq, st);                               // q = S p
-    launch_dot(h->vp, h->vq, n, h->partial, kDotBlocks, S + 1, st);
-    launch_pcg_scalars(S, 0, flexible, st);                          // alpha = rz / pq
-    if (flexible) ck(cudaMemcpyAsync(h->vrold, h->vr, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
-    launch_pcg_update_x_r(x, h->vr, h->vp, h->vq, S, n, st);
-    launch_dot(h->vr, h->vr, n, h->partial, kDotBlocks, S + 5, st);
+    bool replayed = false;
+    if (graphs && h->iter_graph) {
+      ck(cudaGraphLaunch(h->iter_graph, st), "cudaGraphLaunch");
+      g_launches.fetch_add(h->graph_kernels);
+      replayed = true;
+    } else {
+      pcg_body(h, x, flexible, st);   // the first iteration runs eagerly, then it is captured
+      if (graphs) capture_iteration(h, flexible);
+    }
     ck(cudaMemcpyAsync(h->h_scal, S, sizeof(double) * 16, cudaMemcpyDeviceToHost, st), "d2h");
     ck(cudaStreamSynchronize(st), "sync");
+    if (replayed && !h->graph_prof.empty()) accumulate_graph_profile(h);
     res.iterations = it;
     res.alpha.push_back(h->h_scal[2]);
+    res.beta.push_back(h->h_scal[3]);
     double rel = std::sqrt(h->h_scal[5] / gg);
     if (!std::isfinite(rel)) fail(BDDC_ERR_NAN, "NaN in the Krylov recurrence");
+    res.rel = rel;
     if (rel <= tol) {
       schur_apply(h, x, h->vq, st);                                 // true residual g - S x
-      ck(cudaMemcpyAsync(h->vr, g, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
-      launch_axpy_loc(h->vr, h->vq, -1.0, n, st);
-      launch_dot(h->vr, h->vr, n, h->partial, kDotBlocks, S + 5, st);
-      ck(cudaMemcpyAsync(h->h_scal + 5, S + 5, sizeof(double), cudaMemcpyDeviceToHost, st), "d2h");
+      ck(cudaMemcpyAsync(h->vrold, g, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
+      launch_axpy_loc(h->vrold, h->vq, -1.0, n, st);
+      launch_dot(h->vrold, h->vrold, n, h->partial, kDotBlocks, S + 9, st);
+      ck(cudaMemcpyAsync(h->h_scal + 9, S + 9, sizeof(double), cudaMemcpyDeviceToHost, st), "d2h");
       ck(cudaStreamSynchronize(st), "sync");
-      const double rel_true = std::sqrt(h->h_scal[5] / gg);
+      const double rel_true = std::sqrt(h->h_scal[9] / gg);
       if (rel_true <= tol || checked) {
         res.rel = rel_true;
         res.converged = rel_true <= tol;
         return res;
       }
       checked = true;
-      rel = rel_true;
+      pcg_start(h, g, x, false, st);   // restart from the current iterate with the true residual
     }
-    res.rel = rel;
-    precond(h, h->vr, h->vz, st);                                    // z = M^{-1} r
-    launch_dot(h->vr, h->vz, n, h->partial, kDotBlocks, S + 4, st);
-    if (flexible) launch_dot(h->vz, h->vrold, n, h->partial, kDotBlocks, S + 7, st);
-    launch_pcg_scalars(S, 1, flexible, st);                          // beta
-    launch_pcg_update_p(h->vp, h->vz, S, n, st);
-    ck(cudaMemcpyAsync(h->h_scal + 3, S + 3, sizeof(double), cudaMemcpyDeviceToHost, st), "d2h");
-    ck(cudaStreamSynchronize(st), "sync");
-    res.beta.push_back(h->h_scal[3]);
   }
   return res;
 }
@@ -1161,6 +1268,7 @@ int solve_impl(bddc_handle_s* h, const double* rhs, double* x, int nrhs, double 
   h->stats.iterations = maxits;
   h->stats.converged = all_conv ? 1 : 0;
   h->stats.rel_residual = worst;
+  h->stats.rhs_norm = first.gnorm;
   lanczos(first, &h->stats.lambda_min, &h->stats.lambda_max);
   h->stats.solve_ms = now_ms() - t0;
   h->stats.factor_bytes = h->arena.bytes;

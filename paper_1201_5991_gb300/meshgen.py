@@ -188,82 +188,74 @@ def block_grouping(dim: int, nsub: int, group: int) -> np.ndarray:
 
 def kmeans(points: np.ndarray, k: int, seed: int, iters: int = 5) -> np.ndarray:
     """Lloyd's k-means: default_rng(seed) uniform initial centres inside the points' bounding
-    box, exactly ``iters`` update steps, nearest centre with ties to the lower index."""
+    box, exactly ``iters`` update steps (empty clusters keep their centre), nearest centre by
+    |c|^2 - 2 p.c with ties to the lower index."""
     rng = np.random.default_rng(seed)
     lo, hi = points.min(axis=0), points.max(axis=0)
     centres = lo + (hi - lo) * rng.random((k, points.shape[1]))
     lab = _nearest(points, centres)
     for _ in range(iters):
-        for j in range(k):
-            sel = lab == j
-            if sel.any():
-                centres[j] = points[sel].mean(axis=0)
+        cnt = np.bincount(lab, minlength=k)
+        sums = np.stack([np.bincount(lab, weights=points[:, d], minlength=k) for d in range(points.shape[1])], axis=1)
+        keep = cnt > 0
+        centres[keep] = sums[keep] / cnt[keep, None]
         lab = _nearest(points, centres)
     return lab.astype(np.int32)
 
 
-def _nearest(points, centres, chunk=65536):
+def _nearest(points, centres, chunk=131072):
     out = np.empty(points.shape[0], dtype=np.int64)
+    cc = (centres * centres).sum(axis=1)
     for s in range(0, points.shape[0], chunk):
         p = points[s:s + chunk]
-        d = ((p[:, None, :] - centres[None, :, :]) ** 2).sum(axis=2)
+        d = cc[None, :] - 2.0 * (p @ centres.T)
         out[s:s + chunk] = np.argmin(d, axis=1)
     return out
 
 
 def face_connected_fix(conn: np.ndarray, part: np.ndarray, dim: int) -> np.ndarray:
-    """Make every subdomain face-connected: each face-connected component other than the
-    largest one (ties: the one holding the smallest element id) moves to the face-adjacent
-    subdomain with the smallest id.  Repeats until stable; empty labels are then compacted.
-
-    Only structured Q1 meshes (lexicographic local order) are handled.
-    """
-    part = part.copy()
+    """Make every subdomain of a structured box mesh face-connected: each face-connected
+    component other than the largest (ties: the one holding the smallest element id) moves to
+    the face-adjacent subdomain with the smallest id.  Repeats until stable; empty labels are
+    then compacted.  Elements are lexicographic in an n^dim grid (as built by box_mesh)."""
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import connected_components
+    part = part.astype(np.int64).copy()
     nel = conn.shape[0]
-    if dim == 2:
-        faces = [(0, 1), (2, 3), (0, 2), (1, 3)]
-    else:
-        faces = [(0, 1, 2, 3), (4, 5, 6, 7), (0, 1, 4, 5), (2, 3, 6, 7), (0, 2, 4, 6), (1, 3, 5, 7)]
-    keys = {}
-    nbr = [[] for _ in range(nel)]
-    for e in range(nel):
-        for f in faces:
-            key = tuple(sorted(int(conn[e, a]) for a in f))
-            o = keys.get(key)
-            if o is None:
-                keys[key] = e
-            else:
-                nbr[e].append(o)
-                nbr[o].append(e)
+    n = int(round(nel ** (1.0 / dim)))
+    idx = np.arange(nel).reshape((n,) * dim)
+    pairs = []
+    for ax in range(dim):
+        a = np.take(idx, np.arange(n - 1), axis=ax).ravel()
+        b = np.take(idx, np.arange(1, n), axis=ax).ravel()
+        pairs.append((a, b))
+    ea = np.concatenate([p[0] for p in pairs])
+    eb = np.concatenate([p[1] for p in pairs])
     for _ in range(100):
-        changed = False
-        seen = np.full(nel, -1, dtype=np.int64)
-        comps = {}
-        for e in range(nel):
-            if seen[e] >= 0:
-                continue
-            stack = [e]
-            seen[e] = e
-            members = []
-            while stack:
-                x = stack.pop()
-                members.append(x)
-                for y in nbr[x]:
-                    if seen[y] < 0 and part[y] == part[e]:
-                        seen[y] = e
-                        stack.append(y)
-            comps.setdefault(int(part[e]), []).append(sorted(members))
-        for p, cl in comps.items():
-            if len(cl) < 2:
-                continue
-            cl.sort(key=lambda m: (-len(m), m[0]))
-            for m in cl[1:]:
-                adj = sorted({int(part[y]) for x in m for y in nbr[x] if part[y] != p})
-                if adj:
-                    part[np.array(m)] = adj[0]
-                    changed = True
-        if not changed:
+        same = part[ea] == part[eb]
+        g = sp.coo_matrix((np.ones(int(same.sum())), (ea[same], eb[same])), shape=(nel, nel))
+        ncomp, comp = connected_components(g, directed=False)
+        # component sizes and first element; the kept component per part is the largest
+        size = np.bincount(comp, minlength=ncomp)
+        first = np.full(ncomp, nel, dtype=np.int64)
+        np.minimum.at(first, comp, np.arange(nel))
+        cpart = part[first]
+        order = np.lexsort((first, -size, cpart))          # by part, then size desc, then first
+        keep = np.zeros(ncomp, dtype=bool)
+        _, start = np.unique(cpart[order], return_index=True)
+        keep[order[start]] = True
+        if keep.all():
             break
+        # move each dropped component to its smallest face-adjacent other part
+        diff = ~same
+        cand = np.full(ncomp, np.iinfo(np.int64).max)
+        for x, y in ((ea[diff], eb[diff]), (eb[diff], ea[diff])):
+            np.minimum.at(cand, comp[x], part[y])
+        move = (~keep) & (cand < np.iinfo(np.int64).max)
+        if not move.any():
+            break
+        sel = move[comp]
+        part[sel] = cand[comp[sel]]
     _, part = np.unique(part, return_inverse=True)
     return part.astype(np.int32)
 
@@ -315,7 +307,7 @@ def elasticity3d(n: int, nsub: int, seed: int, nrhs: int = 1, group: int = 0,
         f_full=f, parts=parts, n_parts=n_parts, n_levels=levels, constraints=constraints)
 
 
-def elasticity3d_kmeans(n: int, nsub: int, ngroup: int, seed: int, seed2: int) -> Problem:
+def elasticity3d_kmeans(n: int, nsub: int, ngroup: int, seed: int, seed2: int, kmeans_iters: int = 5) -> Problem:
     """Elasticity as ``elasticity3d`` with a seeded k-means split of element centroids into
     nsub subdomains (made face-connected), grouped by k-means of subdomain centroids into
     ngroup level-2 subdomains; three levels."""
@@ -324,7 +316,7 @@ def elasticity3d_kmeans(n: int, nsub: int, ngroup: int, seed: int, seed2: int) -
     dirichlet = mask_face_x0(coords, 3)
     g = box_body_load(coords, conn, 3, [0.0, 0.0, -1.0])
     cent = coords[conn].mean(axis=1)
-    p1 = kmeans(cent, nsub, seed)
+    p1 = kmeans(cent, nsub, seed, iters=kmeans_iters)
     p1 = face_connected_fix(conn, p1, 3)
     ns = int(p1.max()) + 1
     scent = np.stack([np.bincount(p1, weights=cent[:, d], minlength=ns) for d in range(3)], axis=1)
@@ -347,7 +339,7 @@ def config(name: str) -> Problem:
     if name == "elasticity3d_24":            # same 12^3 subdomains, 2^3 of them (profiling case)
         return elasticity3d(24, 2, seed=2)
     if name == "elasticity3d_96_kmeans":
-        return elasticity3d_kmeans(96, 512, 8, seed=3, seed2=33)
+        return elasticity3d_kmeans(96, 512, 8, seed=3, seed2=33, kmeans_iters=20)
     if name == "elasticity3d_64_16rhs":
         return elasticity3d(64, 8, seed=5, nrhs=16)
     raise KeyError(name)

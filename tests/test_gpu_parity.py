@@ -162,3 +162,19 @@ def test_tensor_core_factor_matches_cuda_core_factor():
     assert e_tc < 1e-2
     u = s_tc.solve(_dev(p.f[:, 0]), tol=1e-12).cpu().numpy()
     assert _rel(u, ref) < 1e-8
+
+
+def test_graph_iteration_matches_eager_and_profiles():
+    # the captured PCG iteration replays exactly the eager kernels: bit-identical iterates
+    p = PROBLEMS["elast8_4"]()
+    f = _dev(p.f[:, 0])
+    a = BddcSolver(p, precision="mixed", use_graph=1).solve(f, tol=1e-10).cpu().numpy()
+    b = BddcSolver(p, precision="mixed", use_graph=0).solve(f, tol=1e-10).cpu().numpy()
+    np.testing.assert_array_equal(a, b)
+    s = BddcSolver(p, precision="mixed", use_graph=1, profile=1)
+    s.reset_profile()
+    s.solve(f, tol=1e-10)
+    st = s.stats()
+    # every iteration sweeps: interior (refinement) and interface rows, forward and backward
+    assert st.prof_launches[capi.PROF_TRSV] >= 4 * st.iterations
+    assert st.prof_ms[capi.PROF_TRSV] > 0
