@@ -47,6 +47,9 @@ extern "C" {
 /* physics */
 #define BDDC_POISSON 0      /* -div(coef grad u) = f, 1 DOF per node */
 #define BDDC_ELASTICITY 1   /* isotropic linear elasticity, coef = Young's modulus, nu = Poisson ratio */
+#define BDDC_STOKES 2       /* Stokes flow, Taylor-Hood Q2-Q1 hexes (27 nodes, 4 DOF slots u,v,w,p per
+                               node; the pressure slot exists on the 8 vertex nodes only, the others
+                               must be marked prescribed), coef = viscosity */
 
 /* constraint classes (Sec. 2: corners, averages over edges and faces) */
 #define BDDC_CORNERS 1u
@@ -63,20 +66,23 @@ extern "C" {
 
 typedef struct bddc_handle_s* bddc_handle;
 
-/* Mesh of the first level (host pointers). Element-local node order is lexicographic:
- * local node a sits at reference position xi_d = 2*((a >> d) & 1) - 1 (Q1: 2**dim nodes). */
+/* Mesh of the first level (host pointers).  Element-local node order is lexicographic:
+ * Q1: local node a at reference position xi_d = 2*((a >> d) & 1) - 1 (2**dim nodes);
+ * Q2 (Stokes): a = ix + 3 iy + 9 iz at xi = (ix-1, iy-1, iz-1). */
 typedef struct {
   int dim;                  /* 2 or 3 */
-  int nodes_per_elem;       /* 4 (2D Q1) or 8 (3D Q1) */
-  int dofs_per_node;        /* 1 (Poisson) or dim (elasticity) */
-  int physics;              /* BDDC_POISSON | BDDC_ELASTICITY */
+  int nodes_per_elem;       /* 4 (2D Q1), 8 (3D Q1) or 27 (Q2-Q1 Stokes) */
+  int dofs_per_node;        /* 1 (Poisson), dim (elasticity) or 4 (Stokes) */
+  int physics;              /* BDDC_POISSON | BDDC_ELASTICITY | BDDC_STOKES */
   int64_t n_nodes;
   int64_t n_elems;
   const double* coords;     /* [n_nodes * dim] */
   const int32_t* conn;      /* [n_elems * nodes_per_elem] node ids */
   const double* coef;       /* [n_elems] coefficient (Young's modulus / conductivity), > 0 */
   double nu;                /* Poisson ratio (elasticity) */
-  const uint8_t* dirichlet; /* [n_nodes * dofs_per_node], 1 = prescribed (value 0) */
+  const uint8_t* dirichlet; /* [n_nodes * dofs_per_node], 1 = prescribed */
+  const double* dir_values; /* [n_nodes * dofs_per_node] prescribed values, or NULL (all zero);
+                               bddc_solve then solves K_ff u = f - K_fd u_d */
 } bddc_mesh;
 
 /* Division into subdomains per level (Algorithm 1 takes it as an input: ParMETIS/METIS in
@@ -101,7 +107,16 @@ typedef struct {
   int profile;              /* 1: time kernel classes with CUDA events (bddc_stats.prof_*) */
   int tensor_cores;         /* mixed: 1 = FP32 trailing updates on tcgen05 tensor cores (3xBF16 split,
                                256-wide panels); 0 = FP32 CUDA cores */
+  int krylov;               /* BDDC_KRYLOV_*; 0 = automatic: PCG for the SPD problems; for Stokes
+                               BiCGstab (FP64) or flexible GMRES (mixed: FP32 factors of the
+                               saddle points make the preconditioner inexact beyond what
+                               BiCGstab's short recurrences tolerate) */
 } bddc_opts;
+
+#define BDDC_KRYLOV_AUTO 0
+#define BDDC_KRYLOV_PCG 1        /* preconditioned CG (Sec. 4), SPD problems */
+#define BDDC_KRYLOV_BICGSTAB 2   /* right-preconditioned BiCGstab (Sec. 4, Stokes) */
+#define BDDC_KRYLOV_FGMRES 3     /* right-preconditioned flexible GMRES(50) */
 
 /* kernel classes timed when bddc_opts.profile = 1 */
 #define BDDC_PROF_TRSV 0    /* streaming triangular sweeps (Schur operator and preconditioner) */
@@ -184,7 +199,8 @@ int bddc_setup(const bddc_mesh* mesh, const bddc_partition* part, unsigned const
 int bddc_update_coef(bddc_handle h, const double* coef);
 
 /* Solve K u = f for nrhs right-hand sides (Sec. 2): condensed right-hand side
- * g = f_G - sum R_i^T K_GI K_II^{-1} f_I,i, PCG on S u_G = g preconditioned by Algorithm 2,
+ * g = f_G - sum R_i^T K_GI K_II^{-1} f_I,i, PCG (BiCGstab for Stokes, Sec. 4) on S u_G = g
+ * preconditioned by Algorithm 2,
  * stop when ||r|| / ||g|| <= tol (confirmed on the true residual), then interior recovery
  * u_I = K_II^{-1} (f_I - K_IG u_G).  rhs: device [nrhs][n_free] FP64.  x: device
  * [nrhs][n_free] FP64, output (the initial guess is zero).  stats: host, may be NULL.

@@ -22,12 +22,17 @@ per subdomain:
     residual, confirmed once with the true residual.  The condition number is estimated
     from the Lanczos tridiagonal T_jj = 1/alpha_j + beta_{j-1}/alpha_{j-1},
     T_{j,j+1} = sqrt(beta_j)/alpha_j.
+  * BiCGstab (Sec. 4, the Stokes experiments): right preconditioned, van der Vorst's
+    recurrences; flexible GMRES (Saad) as the alternative for an inexact preconditioner.
 
-Weights: diagonal-stiffness D_i(j) = K_i(jj) / sum_k K_k(jj) (default) or multiplicity.
+Weights: diagonal-stiffness D_i(j) = K_i(jj) / sum_k K_k(jj) (default) or multiplicity; DOFs
+whose diagonal sum is zero (Stokes pressures) take the multiplicity weight.
 
 Parity: pinned in ``tests/test_oracle_bddc.py`` against the direct solve, an explicitly
 formed Schur complement, one-subdomain exactness, the all-interface-corners case, K_Ci =
--Lambda_i = Psi_i^T K_i Psi_i, C_i Psi_i = I, and lambda_min(M^{-1} S) >= 1.
+-Lambda_i = Psi_i^T K_i Psi_i, C_i Psi_i = I, and lambda_min(M^{-1} S) >= 1; the Krylov
+methods against LAPACK solves; the Stokes cavity against the direct solve and the discrete
+divergence-free condition.
 """
 from __future__ import annotations
 
@@ -46,7 +51,7 @@ from .maps import LevelMaps, LevelMesh, analyze, mesh_level1, next_level_mesh
 class LevelData:
     maps: LevelMaps
     K: List[np.ndarray]            # dense local matrices, local order (interior, interface)
-    KII: List[object]              # Cholesky factors of the interior blocks
+    KII: List[object]              # LU factors of the interior blocks
     saddle: List[object]           # LU factors of [[K_i, C_i^T], [C_i, 0]]
     Psi: List[np.ndarray]          # [n_local, n_c]
     Lam: List[np.ndarray]          # [n_c, n_c]
@@ -102,7 +107,7 @@ def setup_level(mesh: LevelMesh, Ke, constraints: int, weights: str, assembled: 
         Ks = K[s]
         nI = maps.sub_nI[s]
         n = Ks.shape[0]
-        KII.append(sla.cho_factor(Ks[:nI, :nI], lower=True) if nI else None)
+        KII.append(sla.lu_factor(Ks[:nI, :nI]) if nI else None)
         C = maps.sub_C[s]
         nc = C.shape[0]
         Sd = np.zeros((n + nc, n + nc))
@@ -120,7 +125,10 @@ def setup_level(mesh: LevelMesh, Ke, constraints: int, weights: str, assembled: 
         if weights == "multiplicity":
             w.append(maps.sub_wmult[s].copy())
         else:
-            w.append(np.diag(Ks)[nI:] / diag_sum[maps.sub_iface[s]])
+            ds = diag_sum[maps.sub_iface[s]]
+            dw = np.diag(Ks)[nI:]
+            # DOFs with a zero diagonal (Stokes pressures) fall back to multiplicity weights
+            w.append(np.where(ds > 0, dw / np.where(ds > 0, ds, 1.0), maps.sub_wmult[s]))
     A = _assemble_level(mesh, Ke) if assembled else None
     return LevelData(maps, K, KII, saddle, Psi, Lam, KC, w, A)
 
@@ -151,7 +159,7 @@ class Bddc:
         for s, rc in enumerate(last.maps.sub_coarse):   # K_C = sum R_Ci^T K_Ci R_Ci
             KC[np.ix_(rc, rc)] += last.KC[s]
         self.KC = KC
-        self.KC_chol = sla.cho_factor(KC, lower=True) if nC else None
+        self.KC_chol = sla.lu_factor(KC) if nC else None
 
     # ------------------------------------------------------------------ level-1 operators
     @property
@@ -172,7 +180,7 @@ class Bddc:
             xi = x[d.maps.sub_iface[s]]
             yi = K[nI:, nI:] @ xi
             if nI:
-                yi -= K[nI:, :nI] @ sla.cho_solve(d.KII[s], K[:nI, nI:] @ xi)
+                yi -= K[nI:, :nI] @ sla.lu_solve(d.KII[s], K[:nI, nI:] @ xi)
             np.add.at(y, d.maps.sub_iface[s], yi)
         return y
 
@@ -184,7 +192,7 @@ class Bddc:
             nI = d.maps.sub_nI[s]
             if nI:
                 fI = f[d.maps.sub_dofs[s][:nI]]
-                np.add.at(g, d.maps.sub_iface[s], -(d.K[s][nI:, :nI] @ sla.cho_solve(d.KII[s], fI)))
+                np.add.at(g, d.maps.sub_iface[s], -(d.K[s][nI:, :nI] @ sla.lu_solve(d.KII[s], fI)))
         return g
 
     def recover(self, f: np.ndarray, uG: np.ndarray) -> np.ndarray:
@@ -197,7 +205,7 @@ class Bddc:
             if nI:
                 dofs = d.maps.sub_dofs[s]
                 rhs = f[dofs[:nI]] - d.K[s][:nI, nI:] @ uG[d.maps.sub_iface[s]]
-                u[dofs[:nI]] = sla.cho_solve(d.KII[s], rhs)
+                u[dofs[:nI]] = sla.lu_solve(d.KII[s], rhs)
         return u
 
     # ------------------------------------------------------------------ Algorithm 2
@@ -217,7 +225,7 @@ class Bddc:
             z_loc.append(sol[:n])                                     # Eq. sub_cor
             np.add.at(r_C, m.sub_coarse[s], d.Psi[s].T @ r_i)         # r_C
         if lev == len(self.levels) - 1:
-            z_C = sla.cho_solve(self.KC_chol, r_C) if nC else r_C
+            z_C = sla.lu_solve(self.KC_chol, r_C) if nC else r_C
         else:
             z_C = self._full_step(lev + 1, r_C)
         z_hat = np.zeros_like(r_hat)
@@ -236,7 +244,7 @@ class Bddc:
             nI = m.sub_nI[s]
             if nI:
                 I = m.sub_dofs[s][:nI]
-                u1[I] = sla.cho_solve(d.KII[s], r[I])
+                u1[I] = sla.lu_solve(d.KII[s], r[I])
         rp = r - d.A @ u1
         zG = self._interface_step(lev, rp[m.iface_dofs])
         z = u1.copy()
@@ -245,7 +253,7 @@ class Bddc:
             nI = m.sub_nI[s]
             if nI:
                 I = m.sub_dofs[s][:nI]
-                z[I] -= sla.cho_solve(d.KII[s], d.K[s][:nI, nI:] @ zG[m.sub_iface[s]])
+                z[I] -= sla.lu_solve(d.KII[s], d.K[s][:nI, nI:] @ zG[m.sub_iface[s]])
         return z
 
     def precond(self, r_hat: np.ndarray) -> np.ndarray:
@@ -254,10 +262,16 @@ class Bddc:
 
     # ------------------------------------------------------------------ solve
     def solve(self, f: Optional[np.ndarray] = None, tol: float = 1e-12, maxit: int = 1000,
-              flexible: bool = False):
-        """PCG on S u_hat = g_hat for each right-hand side column; returns (u, info)."""
+              flexible: bool = False, krylov: Optional[str] = None):
+        """Krylov solve of S u_hat = g_hat for each right-hand side column; returns (u, info).
+
+        PCG (Sec. 4) for the SPD problems, BiCGstab (Sec. 4, Stokes) for the indefinite one;
+        ``krylov="fgmres"`` selects flexible GMRES.
+        """
         if f is None:
             f = self.prob.f
+        if krylov is None:
+            krylov = "bicgstab" if self.prob.physics == 2 else "pcg"
         f = np.asarray(f, dtype=np.float64)
         squeeze = f.ndim == 1
         F = f[:, None] if squeeze else f
@@ -265,7 +279,12 @@ class Bddc:
         infos = []
         for k in range(F.shape[1]):
             g = self.condensed_rhs(F[:, k])
-            uG, info = pcg(self.schur, self.precond, g, tol, maxit, flexible)
+            if krylov == "pcg":
+                uG, info = pcg(self.schur, self.precond, g, tol, maxit, flexible)
+            elif krylov == "fgmres":
+                uG, info = fgmres(self.schur, self.precond, g, tol, maxit)
+            else:
+                uG, info = bicgstab(self.schur, self.precond, g, tol, maxit)
             U[:, k] = self.recover(F[:, k], uG)
             infos.append(info)
         return (U[:, 0] if squeeze else U), infos
@@ -325,6 +344,85 @@ def pcg(A, M, b, tol: float, maxit: int, flexible: bool = False):
         p = z_new + beta * p
         r = r_new
     return x, PcgInfo(it, float(rel), np.array(alphas), np.array(betas), converged)
+
+
+def bicgstab(A, M, b, tol: float, maxit: int):
+    """Right-preconditioned BiCGstab (van der Vorst); stops on ||r|| / ||b|| <= tol, confirmed
+    with the true residual."""
+    x = np.zeros_like(b)
+    nb = np.linalg.norm(b)
+    if nb == 0.0:
+        return x, PcgInfo(0, 0.0, np.zeros(0), np.zeros(0), True)
+    r = b.copy()
+    rh = r.copy()
+    rho = alpha = omega = 1.0
+    v = np.zeros_like(b)
+    p = np.zeros_like(b)
+    rel = 1.0
+    it = 0
+    converged = False
+    while it < maxit:
+        it += 1
+        rho_new = float(rh @ r)
+        beta = (rho_new / rho) * (alpha / omega)
+        p = r + beta * (p - omega * v)
+        ph = M(p)
+        v = A(ph)
+        alpha = rho_new / float(rh @ v)
+        s = r - alpha * v
+        sh = M(s)
+        t = A(sh)
+        omega = float(t @ s) / float(t @ t)
+        x = x + alpha * ph + omega * sh
+        r = s - omega * t
+        rho = rho_new
+        rel = np.linalg.norm(r) / nb
+        if rel <= tol:
+            rel = np.linalg.norm(b - A(x)) / nb
+            if rel <= tol:
+                converged = True
+                break
+    return x, PcgInfo(it, float(rel), np.zeros(0), np.zeros(0), converged)
+
+
+def fgmres(A, M, b, tol: float, maxit: int, restart: int = 50):
+    """Flexible GMRES(restart) with right preconditioning (Saad 1993): the preconditioned
+    vectors z_j = M(v_j) are stored and x is updated with Z y, so M may change between calls.
+    Modified Gram-Schmidt; stops when the true residual ||b - A x|| / ||b|| <= tol."""
+    x = np.zeros_like(b)
+    nb = np.linalg.norm(b)
+    if nb == 0.0:
+        return x, PcgInfo(0, 0.0, np.zeros(0), np.zeros(0), True)
+    it = 0
+    rel = 1.0
+    while it < maxit:
+        r = b - A(x)
+        beta = np.linalg.norm(r)
+        rel = beta / nb
+        if rel <= tol:
+            return x, PcgInfo(it, float(rel), np.zeros(0), np.zeros(0), True)
+        V = [r / beta]
+        Z = []
+        H = np.zeros((restart + 1, restart))
+        k = 0
+        while k < restart and it < maxit:
+            Z.append(M(V[k]))
+            w = A(Z[k])
+            for i in range(k + 1):
+                H[i, k] = float(V[i] @ w)
+                w = w - H[i, k] * V[i]
+            H[k + 1, k] = np.linalg.norm(w)
+            V.append(w / H[k + 1, k] if H[k + 1, k] > 0 else w)
+            k += 1
+            it += 1
+            e1 = np.zeros(k + 1)
+            e1[0] = beta
+            y = np.linalg.lstsq(H[:k + 1, :k], e1, rcond=None)[0]
+            if np.linalg.norm(H[:k + 1, :k] @ y - e1) / nb <= tol or H[k, k - 1] == 0:
+                break
+        x = x + np.column_stack(Z) @ y
+    rel = np.linalg.norm(b - A(x)) / nb
+    return x, PcgInfo(it, float(rel), np.zeros(0), np.zeros(0), rel <= tol)
 
 
 def lanczos_extremes(alphas: np.ndarray, betas: np.ndarray):

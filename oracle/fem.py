@@ -107,6 +107,56 @@ def element_elasticity(X: np.ndarray, E: float, nu: float) -> np.ndarray:
     return K
 
 
+GAUSS3 = (np.array([-np.sqrt(0.6), 0.0, np.sqrt(0.6)]), np.array([5.0, 8.0, 5.0]) / 9.0)
+
+
+def q2_1d(x: float):
+    """Quadratic Lagrange functions on nodes -1, 0, 1 and their derivatives."""
+    return (np.array([0.5 * x * (x - 1.0), 1.0 - x * x, 0.5 * x * (x + 1.0)]),
+            np.array([x - 0.5, -2.0 * x, x + 0.5]))
+
+
+def element_stokes(X: np.ndarray, nu: float = 1.0) -> np.ndarray:
+    """Taylor-Hood Q2-Q1 hex, DOF slots (node a of 27, component c of 4) -> 4a + c.
+
+    Velocity (c = 0, 1, 2) on all 27 nodes, pressure (c = 3) on the 8 vertex nodes; the
+    pressure slots of the other 19 nodes carry zero rows and columns.  Blocks:
+    A[(a,i),(b,j)] = nu delta_ij int grad phi_a . grad phi_b  (vector Laplacian form),
+    B[(p,3),(b,j)] = -int psi_p d phi_b / dx_j  and its transpose; 3x3x3 Gauss rule,
+    isoparametric Q2 geometry.  Local node a = ix + 3 iy + 9 iz.
+    """
+    K = np.zeros((108, 108))
+    vert = [ix + 3 * iy + 9 * iz for iz in (0, 2) for iy in (0, 2) for ix in (0, 2)]
+    pts, wts = GAUSS3
+    for gz, wz in zip(pts, wts):
+        for gy, wy in zip(pts, wts):
+            for gx, wx in zip(pts, wts):
+                fx, dx = q2_1d(gx)
+                fy, dy = q2_1d(gy)
+                fz, dz = q2_1d(gz)
+                G = np.zeros((27, 3))
+                for a in range(27):
+                    ix, iy, iz = a % 3, (a // 3) % 3, a // 9
+                    G[a] = [dx[ix] * fy[iy] * fz[iz], fx[ix] * dy[iy] * fz[iz], fx[ix] * fy[iy] * dz[iz]]
+                J = X.T @ G
+                detJ = np.linalg.det(J)
+                Gx = G @ np.linalg.inv(J)
+                w = wx * wy * wz * detJ
+                Lap = nu * w * (Gx @ Gx.T)
+                for i in range(3):
+                    K[i:108:4, i:108:4][:27, :27] += Lap
+                xi = np.array([gx, gy, gz])
+                for k, a in enumerate(vert):
+                    c = np.array([-1.0 if (k >> d) & 1 == 0 else 1.0 for d in range(3)])
+                    psi = np.prod((1.0 + c * xi) / 2.0)
+                    for b in range(27):
+                        for j in range(3):
+                            v = -w * psi * Gx[b, j]
+                            K[4 * a + 3, 4 * b + j] += v
+                            K[4 * b + j, 4 * a + 3] += v
+    return K
+
+
 def element_matrices(prob) -> np.ndarray:
     """All element matrices of a Problem, [n_elems, ne, ne], each scaled by its coefficient.
 
@@ -124,6 +174,8 @@ def element_matrices(prob) -> np.ndarray:
             unit.append(element_laplace(X[e], 1.0))
         elif prob.physics == 1:
             unit.append(element_elasticity(X[e], 1.0, prob.nu))
+        elif prob.physics == 2:
+            unit.append(element_stokes(X[e], 1.0))
         else:
             raise NotImplementedError("physics")
     unit = np.stack(unit)

@@ -31,7 +31,10 @@ selection; this oracle takes the following readings (the CUDA library takes the 
     one coarse DOF; its row averages (weight 1/count) that component over the glob's free
     DOFs.  Coarse DOFs are numbered by (glob order, component).
   * local DOF order of a subdomain: interior DOFs ascending by global id, then interface
-    DOFs ascending.  The global interface numbers the interface DOFs ascending.
+    DOFs ascending; for Stokes the pressure DOFs follow the velocity DOFs inside each of the
+    two groups.  The global interface numbers the interface DOFs ascending.
+  * rigid-body test for Stokes: the floating modes are the constant velocities, so one point
+    constrained in the three velocity components suffices.
   * multiplicity weight of an interface DOF: 1 / |sharing set of its node|.
   * pseudo-mesh of the next level: one pseudo-node per glob carrying coarse DOFs (in glob
     order) with coordinates at the centroid of the glob's nodes that carry a free DOF; one
@@ -63,6 +66,9 @@ class LevelMesh:
     part: np.ndarray                   # [n_elems] -> subdomain
     n_sub: int
     n_dof: int                         # number of free DOFs of this level
+    rigid_comps: Tuple[int, ...] = ()  # components carrying the floating (rigid) modes
+    rigid_points: int = 1              # constrained points needed: 1, 2 (2D elast.) or 3 (3D elast.)
+    last_comp: int = -1                # component ordered after the others in local orders (-1: none)
 
 
 @dataclasses.dataclass
@@ -105,8 +111,14 @@ def mesh_level1(prob) -> LevelMesh:
                  for p in range(prob.n_nodes)]
     elem_nodes = [np.asarray(r, dtype=np.int64) for r in prob.conn]
     elem_dofs = [dof_id[(r[:, None].astype(np.int64) * nd + np.arange(nd)).ravel()] for r in prob.conn]
+    if prob.physics == 2:          # Stokes: constant velocities float; pressures ordered last
+        rc, rp, last = (0, 1, 2), 1, 3
+    elif prob.physics == 1:
+        rc, rp, last = tuple(range(nd)), (3 if prob.dim == 3 else 2), -1
+    else:
+        rc, rp, last = (0,), 1, -1
     return LevelMesh(prob.dim, nd, prob.coords, node_dofs, elem_nodes, elem_dofs,
-                     np.asarray(prob.parts[0]), int(prob.n_parts[0]), int(free.sum()))
+                     np.asarray(prob.parts[0]), int(prob.n_parts[0]), int(free.sum()), rc, rp, last)
 
 
 def _seqmean(X: np.ndarray) -> np.ndarray:
@@ -203,26 +215,34 @@ def analyze(mesh: LevelMesh, constraints: int, all_corners: bool = False) -> Lev
     diam = np.linalg.norm(mesh.coords.max(axis=0) - mesh.coords.min(axis=0))
     tol = 1e-12 * diam * diam
 
+    rigid = set(mesh.rigid_comps)
+
+    def node_rigid_state(p):
+        """(all rigid-mode DOFs prescribed, all rigid-mode DOFs present and free)"""
+        nd = [(int(c), int(d)) for c, d in mesh.node_dofs[int(p)] if int(c) in rigid]
+        present = {c for c, _ in nd}
+        return (len(nd) > 0 and all(d < 0 for _, d in nd),
+                present == rigid and all(d >= 0 for _, d in nd))
+
     def points_of(s):
         pts = []
         for g in globs:
             if s in g.subs and glob_is_constrained(g):
-                if len(glob_free_comps(g)) == mesh.ncomp:
+                if rigid.issubset(glob_free_comps(g)):
                     pts.append(glob_centroid(g))
         for p in sub_nodes[s]:
-            nd = mesh.node_dofs[int(p)]
-            if len(nd) and all(int(d) < 0 for _, d in nd):
+            if node_rigid_state(p)[0]:
                 pts.append(mesh.coords[int(p)])
         return np.array(pts).reshape(-1, mesh.dim)
 
     def sufficient(pts):
-        if mesh.ncomp == 1:
+        if mesh.rigid_points == 1:
             return pts.shape[0] >= 1
         if pts.shape[0] == 0:
             return False
         d0 = np.linalg.norm(pts - pts[0], axis=1)
         j = int(np.argmax(d0))
-        if mesh.dim == 2:
+        if mesh.rigid_points == 2:
             return d0[j] * d0[j] > tol
         if d0[j] * d0[j] <= tol:
             return False
@@ -238,8 +258,7 @@ def analyze(mesh: LevelMesh, constraints: int, all_corners: bool = False) -> Lev
             if sufficient(pts):
                 break
             cand = [int(p) for p in sub_nodes[s] if iface[p] and int(p) not in corner_nodes
-                    and len(mesh.node_dofs[int(p)]) == mesh.ncomp
-                    and all(int(d) >= 0 for _, d in mesh.node_dofs[int(p)])]
+                    and node_rigid_state(p)[1]]
             if not cand:
                 raise ValueError(f"subdomain {s}: no candidate corner")
             cand = np.array(cand, dtype=np.int64)
@@ -249,7 +268,7 @@ def analyze(mesh: LevelMesh, constraints: int, all_corners: bool = False) -> Lev
             else:
                 d0 = np.linalg.norm(pts - pts[0], axis=1)
                 j = int(np.argmax(d0))
-                if d0[j] * d0[j] <= tol or mesh.dim == 2:
+                if d0[j] * d0[j] <= tol or mesh.rigid_points <= 2:
                     dist = np.linalg.norm(X - pts[0], axis=1)
                 else:
                     u = (pts[j] - pts[0]) / d0[j]
@@ -280,11 +299,12 @@ def analyze(mesh: LevelMesh, constraints: int, all_corners: bool = False) -> Lev
     for s in range(nsub):
         interior, inter = [], []
         for p in sub_nodes[s]:
-            for _, d in mesh.node_dofs[int(p)]:
+            for c, d in mesh.node_dofs[int(p)]:
                 if d >= 0:
-                    (inter if iface[p] else interior).append(int(d))
-        interior.sort()
-        inter.sort()
+                    key = (1 if int(c) == mesh.last_comp else 0, int(d))
+                    (inter if iface[p] else interior).append(key)
+        interior = [d for _, d in sorted(interior)]
+        inter = [d for _, d in sorted(inter)]
         dofs = np.array(interior + inter, dtype=np.int64)
         loc = {d: k for k, d in enumerate(dofs)}
         sub_dofs.append(dofs)
@@ -331,4 +351,5 @@ def next_level_mesh(maps: LevelMaps, part_next: np.ndarray, n_sub_next: int) -> 
         elem_nodes.append(np.array([node_of_glob[g] for g in gl], dtype=np.int64))
         elem_dofs.append(maps.sub_coarse[s].copy())
     return LevelMesh(mesh.dim, mesh.ncomp, np.array(coords), node_dofs, elem_nodes, elem_dofs,
-                     np.asarray(part_next), int(n_sub_next), maps.n_coarse)
+                     np.asarray(part_next), int(n_sub_next), maps.n_coarse, mesh.rigid_comps,
+                     mesh.rigid_points, mesh.last_comp)

@@ -23,9 +23,11 @@ ERR_TIMEOUT = -7
 
 POISSON = 0
 ELASTICITY = 1
+STOKES = 2
 CORNERS, EDGES, FACES = 1, 2, 4
 PREC_FP64, PREC_MIXED = 0, 1
 WEIGHTS_STIFFNESS, WEIGHTS_MULTIPLICITY = 0, 1
+KRYLOV_AUTO, KRYLOV_PCG, KRYLOV_BICGSTAB, KRYLOV_FGMRES = 0, 1, 2, 3
 
 EXPORTED = [
     "bddc_default_opts", "bddc_analyze", "bddc_setup", "bddc_update_coef", "bddc_solve",
@@ -41,7 +43,7 @@ class Mesh(C.Structure):
         ("dim", C.c_int), ("nodes_per_elem", C.c_int), ("dofs_per_node", C.c_int), ("physics", C.c_int),
         ("n_nodes", C.c_int64), ("n_elems", C.c_int64),
         ("coords", C.POINTER(C.c_double)), ("conn", C.POINTER(C.c_int32)), ("coef", C.POINTER(C.c_double)),
-        ("nu", C.c_double), ("dirichlet", C.POINTER(C.c_uint8)),
+        ("nu", C.c_double), ("dirichlet", C.POINTER(C.c_uint8)), ("dir_values", C.POINTER(C.c_double)),
     ]
 
 
@@ -57,7 +59,7 @@ class Opts(C.Structure):
     _fields_ = [
         ("precision", C.c_int), ("weights", C.c_int), ("all_corners", C.c_uint), ("maxit", C.c_int),
         ("refine_steps", C.c_int), ("flexible", C.c_int), ("use_graph", C.c_int), ("verbose", C.c_int),
-        ("profile", C.c_int), ("tensor_cores", C.c_int),
+        ("profile", C.c_int), ("tensor_cores", C.c_int), ("krylov", C.c_int),
     ]
 
 

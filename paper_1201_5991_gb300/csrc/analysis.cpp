@@ -191,17 +191,25 @@ bool analyze_level(const LevelMesh& mesh, unsigned constraints, bool all_corners
       if (mesh.nd_id[q] >= 0) return true;
     return false;
   };
+  const uint32_t rmask = mesh.rigid_mask;
+  // a node's rigid-mode DOFs: all prescribed (a constrained point) / all present and free
   auto node_all_prescribed = [&](int64_t p) {
-    if (mesh.nd_ptr[p + 1] == mesh.nd_ptr[p]) return false;
-    for (int64_t q = mesh.nd_ptr[p]; q < mesh.nd_ptr[p + 1]; ++q)
+    bool any = false;
+    for (int64_t q = mesh.nd_ptr[p]; q < mesh.nd_ptr[p + 1]; ++q) {
+      if (!((rmask >> mesh.nd_comp[q]) & 1u)) continue;
+      any = true;
       if (mesh.nd_id[q] >= 0) return false;
-    return true;
+    }
+    return any;
   };
   auto node_all_free_full = [&](int64_t p) {
-    if (mesh.nd_ptr[p + 1] - mesh.nd_ptr[p] != nc) return false;
-    for (int64_t q = mesh.nd_ptr[p]; q < mesh.nd_ptr[p + 1]; ++q)
+    uint32_t present = 0;
+    for (int64_t q = mesh.nd_ptr[p]; q < mesh.nd_ptr[p + 1]; ++q) {
+      if (!((rmask >> mesh.nd_comp[q]) & 1u)) continue;
       if (mesh.nd_id[q] < 0) return false;
-    return true;
+      present |= 1u << mesh.nd_comp[q];
+    }
+    return present == rmask;
   };
   auto constrained = [&](int64_t g) -> bool {
     if (m.glob_promoted[g]) return true;
@@ -252,13 +260,12 @@ bool analyze_level(const LevelMesh& mesh, unsigned constraints, bool all_corners
   double diam2 = 0.0;
   for (int d = 0; d < dim; ++d) diam2 = diam2 + (hi[d] - lo[d]) * (hi[d] - lo[d]);
   const double tol = 1e-12 * diam2;
-  const uint32_t full = nc >= 32 ? 0xffffffffu : ((1u << nc) - 1u);
 
   std::vector<Pt> pts;
   auto gather_points = [&](int64_t s) {
     pts.clear();
     for (int64_t g : sub_globs[s]) {
-      if (!constrained(g) || glob_comps[g] != full) continue;
+      if (!constrained(g) || (glob_comps[g] & rmask) != rmask) continue;
       Pt q{{0, 0, 0}};
       for (int d = 0; d < dim; ++d) q.x[d] = m.glob_centroid[g * dim + d];
       pts.push_back(q);
@@ -271,7 +278,7 @@ bool analyze_level(const LevelMesh& mesh, unsigned constraints, bool all_corners
     }
   };
   auto sufficient = [&]() -> bool {
-    if (nc == 1) return !pts.empty();
+    if (mesh.rigid_points == 1) return !pts.empty();
     if (pts.empty()) return false;
     size_t j = 0;
     double best = -1.0;
@@ -282,7 +289,7 @@ bool analyze_level(const LevelMesh& mesh, unsigned constraints, bool all_corners
         j = k;
       }
     }
-    if (dim == 2) return best * best > tol;
+    if (mesh.rigid_points == 2) return best * best > tol;
     if (best * best <= tol) return false;
     double u[3] = {pts[j].x[0] - pts[0].x[0], pts[j].x[1] - pts[0].x[1], pts[j].x[2] - pts[0].x[2]};
     double mx = 0.0;
@@ -320,7 +327,7 @@ bool analyze_level(const LevelMesh& mesh, unsigned constraints, bool all_corners
           }
         }
         double u[3] = {0, 0, 0};
-        bool use_line = !(best * best <= tol || dim == 2);
+        bool use_line = !(best * best <= tol || mesh.rigid_points <= 2);
         if (use_line)
           for (int d = 0; d < 3; ++d) u[d] = (pts[j].x[d] - pts[0].x[d]) / best;
         double bd = -1.0;
@@ -381,19 +388,24 @@ bool analyze_level(const LevelMesh& mesh, unsigned constraints, bool all_corners
   for (int64_t s = 0; s < ns; ++s) {
     interior.clear();
     inter.clear();
+    // sort key: DOFs of the last component (Stokes pressures) after the others, then id
+    const int64_t shift = (int64_t)1 << 40;
     for (int64_t p : sub_nodes[s])
       for (int64_t q = mesh.nd_ptr[p]; q < mesh.nd_ptr[p + 1]; ++q) {
         int64_t d = mesh.nd_id[q];
         if (d < 0) continue;
+        const int64_t key = d + (mesh.nd_comp[q] == mesh.last_comp ? shift : 0);
         if (iface[p]) {
-          inter.push_back(d);
+          inter.push_back(key);
           mult[d] = 1.0 / (double)nsh(p);
         } else {
-          interior.push_back(d);
+          interior.push_back(key);
         }
       }
     std::sort(interior.begin(), interior.end());
     std::sort(inter.begin(), inter.end());
+    for (auto& k : interior) k %= shift;
+    for (auto& k : inter) k %= shift;
     int64_t base = (int64_t)m.sub_dofs.size();
     for (int64_t d : interior) {
       loc[d] = (int64_t)m.sub_dofs.size() - base;
@@ -475,6 +487,9 @@ void next_level_mesh(const LevelMesh& mesh, const LevelMaps& maps, const int32_t
   n.part.assign(part, part + ns);
   n.n_sub = n_sub_next;
   n.n_dof = maps.n_coarse;
+  n.rigid_mask = mesh.rigid_mask;
+  n.rigid_points = mesh.rigid_points;
+  n.last_comp = mesh.last_comp;
 }
 
 }  // namespace bddc

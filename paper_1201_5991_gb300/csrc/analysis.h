@@ -27,6 +27,9 @@ struct LevelMesh {
   std::vector<int64_t> en_ptr, en;     // element -> nodes
   std::vector<int64_t> ed_ptr, ed;     // element -> DOF ids of its matrix (-1 = prescribed)
   std::vector<int32_t> part;           // element -> subdomain
+  uint32_t rigid_mask = 1u;            // components that carry the floating (rigid) modes
+  int rigid_points = 1;                // constrained points needed: 1, 2 (2D elasticity), 3 (3D elasticity)
+  int last_comp = -1;                  // component ordered after the others in local orders (-1: none)
 };
 
 struct LevelMaps {

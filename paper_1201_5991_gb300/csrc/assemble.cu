@@ -110,6 +110,130 @@ __global__ void k_elem_q1(int physics, int64_t n_elems, const double* __restrict
   }
 }
 
+// Taylor-Hood Q2-Q1 hex (Stokes, Sec. 4), one block per element, DOF slot 4a + c (node a of 27,
+// component c: u, v, w, p).  A[(a,i),(b,j)] = coef delta_ij int grad phi_a . grad phi_b,
+// B[(p,3),(b,j)] = -coef int psi_p d phi_b / dx_j (psi_p: Q1 function of vertex p) and its
+// transpose; 3x3x3 Gauss rule, isoparametric Q2 geometry; pressure slots of non-vertex nodes
+// stay zero.  Thread t accumulates entries t, t+256, ... of the 27x27 Laplacian and the 8x81 B.
+__global__ void __launch_bounds__(256) k_elem_q2q1(int64_t n_elems, const double* __restrict__ coords,
+                                                   const int32_t* __restrict__ conn, const double* __restrict__ coef,
+                                                   const int32_t* __restrict__ slot_elem, double* __restrict__ ke) {
+  constexpr int NE = 108, NLAP = 27 * 27, NB_ = 8 * 81, NACC = (NLAP + NB_ + 255) / 256;
+  const int64_t slot = blockIdx.x;
+  if (slot >= n_elems) return;
+  const int64_t e = slot_elem[slot];
+  __shared__ double X[27][3], Gr[27][3], Gx[27][3], psi[8], Ji[3][3], wd;
+  const int tid = threadIdx.x;
+  if (tid < 81) X[tid / 3][tid % 3] = coords[(int64_t)conn[e * 27 + tid / 3] * 3 + tid % 3];
+  double acc[NACC];
+#pragma unroll
+  for (int u = 0; u < NACC; ++u) acc[u] = 0.0;
+  const double gq[3] = {-0.77459666924148337704, 0.0, 0.77459666924148337704};   // +-sqrt(3/5), 0
+  const double gw[3] = {5.0 / 9.0, 8.0 / 9.0, 5.0 / 9.0};
+  __syncthreads();
+  for (int g = 0; g < 27; ++g) {
+    const double xi[3] = {gq[g % 3], gq[(g / 3) % 3], gq[g / 9]};
+    if (tid < 27) {
+      const int ix[3] = {tid % 3, (tid / 3) % 3, tid / 9};
+      double f[3], d[3];
+      for (int k = 0; k < 3; ++k) {
+        const double x = xi[k];
+        f[k] = ix[k] == 0 ? 0.5 * x * (x - 1.0) : (ix[k] == 1 ? 1.0 - x * x : 0.5 * x * (x + 1.0));
+        d[k] = ix[k] == 0 ? x - 0.5 : (ix[k] == 1 ? -2.0 * x : x + 0.5);
+      }
+      Gr[tid][0] = d[0] * f[1] * f[2];
+      Gr[tid][1] = f[0] * d[1] * f[2];
+      Gr[tid][2] = f[0] * f[1] * d[2];
+    }
+    if (tid >= 32 && tid < 40) {
+      const int p = tid - 32;
+      double v = 1.0;
+      for (int k = 0; k < 3; ++k) v *= 0.5 * (1.0 + (((p >> k) & 1) ? 1.0 : -1.0) * xi[k]);
+      psi[p] = v;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double J[3][3];
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+          double sacc = 0.0;
+          for (int n = 0; n < 27; ++n) sacc += X[n][a] * Gr[n][b];
+          J[a][b] = sacc;
+        }
+      const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+      const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+      const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+      const double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+      Ji[0][0] = c00 / det;
+      Ji[1][0] = c01 / det;
+      Ji[2][0] = c02 / det;
+      Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+      Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+      Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+      Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+      Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+      Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+      wd = gw[g % 3] * gw[(g / 3) % 3] * gw[g / 9] * det;
+    }
+    __syncthreads();
+    if (tid < 81) {
+      const int a = tid / 3, k = tid % 3;
+      Gx[a][k] = Gr[a][0] * Ji[0][k] + Gr[a][1] * Ji[1][k] + Gr[a][2] * Ji[2][k];
+    }
+    __syncthreads();
+    const double w = wd;
+#pragma unroll
+    for (int u = 0; u < NACC; ++u) {
+      const int t = tid + 256 * u;
+      if (t < NLAP) {
+        const int a = t / 27, b = t % 27;
+        acc[u] += w * (Gx[a][0] * Gx[b][0] + Gx[a][1] * Gx[b][1] + Gx[a][2] * Gx[b][2]);
+      } else if (t < NLAP + NB_) {
+        const int q = t - NLAP, p = q / 81, r = q % 81;
+        acc[u] -= w * psi[p] * Gx[r / 3][r % 3];
+      }
+    }
+    __syncthreads();
+  }
+  double* K = ke + slot * (int64_t)NE * NE;
+  for (int t = tid; t < NE * NE; t += 256) K[t] = 0.0;
+  __syncthreads();
+  const double cf = coef[e];
+#pragma unroll
+  for (int u = 0; u < NACC; ++u) {
+    const int t = tid + 256 * u;
+    if (t < NLAP) {
+      const int a = t / 27, b = t % 27;
+      for (int i = 0; i < 3; ++i) K[(4 * a + i) * NE + 4 * b + i] = cf * acc[u];
+    } else if (t < NLAP + NB_) {
+      const int q = t - NLAP, p = q / 81, r = q % 81, b = r / 3, j = r % 3;
+      const int a = 2 * (p & 1) + 6 * ((p >> 1) & 1) + 18 * ((p >> 2) & 1);   // vertex node of pressure p
+      K[(4 * a + 3) * NE + 4 * b + j] = cf * acc[u];
+      K[(4 * b + j) * NE + 4 * a + 3] = cf * acc[u];
+    }
+  }
+}
+
+// Dirichlet lifting: lift[g] = - sum over the element rows (slot, a) holding free DOF g of
+// sum_b K_e[a][b] u_d[b] (u_d: prescribed values of the element's slots, 0 on free slots).
+// One warp per free DOF, element rows in a fixed order.
+__global__ void k_lift(int64_t n_free, int ne, const int64_t* __restrict__ lptr, const int32_t* __restrict__ lslot,
+                       const int32_t* __restrict__ la, const double* __restrict__ ke, const double* __restrict__ ud,
+                       double* __restrict__ lift) {
+  const int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (g >= n_free) return;
+  double acc = 0.0;
+  for (int64_t c = lptr[g]; c < lptr[g + 1]; ++c) {
+    const int64_t k = lslot[c];
+    const double* row = ke + k * (int64_t)ne * ne + (int64_t)la[c] * ne;
+    const double* u = ud + k * (int64_t)ne;
+    for (int b = lane; b < ne; b += 32) acc += row[b] * u[b];
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) lift[g] = -acc;
+}
+
 // One warp per padded local row: CSR values of K_i from the element matrices containing the
 // row's DOF, in ascending element order.
 __global__ void k_csr_values(LevelDev L, const int32_t* __restrict__ row_sub) {
@@ -172,7 +296,8 @@ __global__ void k_densify(LevelDev L, const int32_t* __restrict__ row_sub) {
   }
 }
 
-// One block per subdomain: rho = mean diag K_i, A += rho C^T C (rows one after another),
+// One block per subdomain: rho = mean diag K_i, A += C^T R C with R = diag(rho c_rho) (rows one
+// after another; c_rho = 0 leaves a row unaugmented),
 // then the constraint rows into block rows Bc .. Bc+ncb-1.
 template <typename T>
 __global__ void k_add_constraints(LevelDev L) {
@@ -194,12 +319,13 @@ __global__ void k_add_constraints(LevelDev L) {
   for (int q = 0; q < m.nc; ++q) {
     const int64_t e0 = L.c_ptr[m.c_off + q], e1 = L.c_ptr[m.c_off + q + 1];
     const int cnt = (int)(e1 - e0);
-    for (int t = threadIdx.x; t < cnt * cnt; t += blockDim.x) {
+    const double rq = rho * L.c_rho[m.c_off + q];   // 0 for rows that are not augmented (Stokes pressures)
+    for (int t = threadIdx.x; t < cnt * cnt && rq != 0.0; t += blockDim.x) {
       const int x = t / cnt, y = t % cnt;
       const int pa = L.c_pos[e0 + x], pb = L.c_pos[e0 + y];
       if (pb > pa) continue;
       T* p = tiles + m.tile_off + tile_index(pa / NB, pb / NB, m.Bc) * NB2 + (pa % NB) * NB + (pb % NB);
-      *p = (T)((double)*p + rho * L.c_val[e0 + x] * L.c_val[e0 + y]);
+      *p = (T)((double)*p + rq * L.c_val[e0 + x] * L.c_val[e0 + y]);
     }
     __syncthreads();
     for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
@@ -211,7 +337,8 @@ __global__ void k_add_constraints(LevelDev L) {
   }
 }
 
-// Interface weights: stiffness D_i(j) = K_i(jj) / sum_k K_k(jj), or multiplicity 1/count.
+// Interface weights: stiffness D_i(j) = K_i(jj) / sum_k K_k(jj), or multiplicity 1/count (also
+// used where the diagonal sum is zero, as for Stokes pressures).
 __global__ void k_weights(LevelDev L, int multiplicity) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= L.n_iface) return;
@@ -223,6 +350,11 @@ __global__ void k_weights(LevelDev L, int multiplicity) {
   }
   double s = 0.0;
   for (int64_t o = o0; o < o1; ++o) s += L.diag[L.iface_occ[o]];
+  if (!(s > 0.0)) {   // zero diagonal (Stokes pressures): multiplicity weights
+    const double w = 1.0 / (double)(o1 - o0);
+    for (int64_t o = o0; o < o1; ++o) L.w[L.iface_occ[o]] = w;
+    return;
+  }
   for (int64_t o = o0; o < o1; ++o) L.w[L.iface_occ[o]] = L.diag[L.iface_occ[o]] / s;
 }
 
@@ -236,6 +368,20 @@ void launch_elem_q1(int physics, int dim, int64_t n_elems, const double* coords,
     { note_launch(); k_elem_q1<2><<<blocks, 128, 0, st>>>(physics, n_elems, coords, conn, coef, nu, slot_elem, ke); }
   else
     { note_launch(); k_elem_q1<3><<<blocks, 128, 0, st>>>(physics, n_elems, coords, conn, coef, nu, slot_elem, ke); }
+}
+
+void launch_elem_q2q1(int64_t n_elems, const double* coords, const int32_t* conn, const double* coef,
+                      const int32_t* slot_elem, double* ke, cudaStream_t st) {
+  if (n_elems <= 0) return;
+  note_launch();
+  k_elem_q2q1<<<(unsigned)n_elems, 256, 0, st>>>(n_elems, coords, conn, coef, slot_elem, ke);
+}
+
+void launch_lift(int64_t n_free, int ne, const int64_t* lptr, const int32_t* lslot, const int32_t* la,
+                 const double* ke, const double* ud, double* lift, cudaStream_t st) {
+  if (n_free <= 0) return;
+  note_launch();
+  k_lift<<<(unsigned)((n_free + 7) / 8), 256, 0, st>>>(n_free, ne, lptr, lslot, la, ke, ud, lift);
 }
 
 void launch_csr_values(const LevelDev& L, int64_t n_rows_total, const int32_t* row_sub, cudaStream_t st) {

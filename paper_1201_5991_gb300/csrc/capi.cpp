@@ -160,19 +160,32 @@ struct bddc_handle_s {
   int64_t* d_edof = nullptr;           // element -> full DOF ids
   int64_t* d_free_of_full = nullptr;
   int* d_status = nullptr;
+  // non-zero prescribed values: lift = -K_fd u_d, added to every right-hand side
+  bool has_lift = false;
+  std::vector<double> dir_full;        // [n_full] prescribed values, 0 on free DOFs
+  double* d_dir_full = nullptr;
+  double* d_lift = nullptr;            // [n_free]
+  double* d_lift_ud = nullptr;         // [n_elems * ne] prescribed values of each element slot
+  int64_t* d_lift_ptr = nullptr;       // free DOF -> its (slot, row) occurrences in lifting elements
+  int32_t* d_lift_slot = nullptr;
+  int32_t* d_lift_a = nullptr;
   // PCG
   double* scal = nullptr;              // [16]
   double* partial = nullptr;           // [kDotBlocks]
   double* h_scal = nullptr;            // pinned [16]
   double *vx = nullptr, *vr = nullptr, *vz = nullptr, *vp = nullptr, *vq = nullptr, *vrold = nullptr, *vg = nullptr;
+  double *vs = nullptr, *vsh = nullptr, *vt = nullptr;   // BiCGstab s, M^{-1} s, S M^{-1} s
+  // flexible GMRES(kRestart): Krylov basis V, preconditioned basis Z, Arnoldi column scratch
+  double *gm_V = nullptr, *gm_Z = nullptr, *gm_w = nullptr, *gm_h = nullptr, *gm_partial = nullptr;
+  double* h_gm = nullptr;              // pinned: Arnoldi column (two passes + norm) and y
   double* fcol = nullptr;              // [n_free] work
   double* ucol = nullptr;
   double *full_a = nullptr, *full_b = nullptr;
   int refine_steps = 0;
   int grid_max = 304;                  // persistent sweep grid: 2 CTAs per SM
   cudaStream_t cap_st = nullptr;       // private stream for graph capture
-  cudaGraphExec_t iter_graph = nullptr;  // one captured PCG iteration
-  int iter_graph_flexible = -1;
+  cudaGraphExec_t iter_graph = nullptr;  // one captured Krylov iteration
+  int iter_graph_flexible = -1;          // 0/1: PCG (Fletcher-Reeves / flexible), 2: BiCGstab
   int64_t graph_kernels = 0;           // kernel nodes in iter_graph
   bddc_stats stats{};
   bool factored = false;
@@ -197,6 +210,7 @@ struct bddc_handle_s {
       cudaEventDestroy(r.b);
     }
     for (auto e : event_pool) cudaEventDestroy(e);
+    if (h_gm) cudaFreeHost(h_gm);
   }
 };
 
@@ -204,6 +218,15 @@ namespace bddc {
 namespace {
 
 constexpr int kDotBlocks = 304;   // 2 x SM count of a GB300; fixed for reproducible sums
+
+constexpr int kRestart = 50;   // flexible GMRES restart length
+
+int krylov_kind(const bddc_handle_s* h) {
+  if (h->opts.krylov != 0) return h->opts.krylov;
+  if (h->physics != BDDC_STOKES) return BDDC_KRYLOV_PCG;
+  return h->opts.precision == BDDC_PREC_MIXED ? BDDC_KRYLOV_FGMRES : BDDC_KRYLOV_BICGSTAB;
+}
+
 
 // Event record that also works inside stream capture (there it becomes an event-record node of
 // the graph instead of a capture-internal dependency).
@@ -320,6 +343,17 @@ void build_level1_mesh(bddc_handle_s* h, LevelMesh* out) {
     }
   m.part = h->parts[0];
   m.n_dof = h->n_free;
+  if (h->physics == BDDC_STOKES) {          // constant velocities float; pressures ordered last
+    m.rigid_mask = 7u;
+    m.rigid_points = 1;
+    m.last_comp = 3;
+  } else if (h->physics == BDDC_ELASTICITY) {
+    m.rigid_mask = (1u << h->ndof) - 1u;
+    m.rigid_points = h->dim == 3 ? 3 : 2;
+  } else {
+    m.rigid_mask = 1u;
+    m.rigid_points = 1;
+  }
 }
 
 // Single-subdomain "level" holding the coarsest problem: all DOFs interior.
@@ -585,6 +619,16 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
   d.sub_coarse = A.upload(sub_coarse, st);
   d.cinv_ptr = A.upload(cinv_ptr, st);
   d.cinv_occ = A.upload(cinv_occ, st);
+  {
+    // constraint rows that augment A_i (Sec. 2 saddle point, Eq. psi_def): the rows of the
+    // components carrying the floating modes; Stokes pressure averages stay in the saddle point
+    std::vector<double> c_rho(L.sum_nc, 0.0);
+    for (int64_t t = 0; t < L.sum_nc; ++t)
+      c_rho[t] = ((ms.rigid_mask >> mp.coarse_comp[mp.sub_coarse[t]]) & 1u) ? 1.0 : 0.0;
+    d.c_rho = A.upload(c_rho, st);
+  }
+  d.indefinite = h->physics == BDDC_STOKES ? 1 : 0;
+  d.sgn = L.fp32 ? (void*)A.alloc<float>(L.n_vec) : (void*)A.alloc<double>(L.n_vec);
   d.w = A.alloc<double>(L.n_vec);
   d.diag = A.alloc<double>(L.n_vec);
   d.rho = A.alloc<double>(ns);
@@ -928,8 +972,14 @@ void numeric_setup(bddc_handle_s* h) {
   for (size_t l = 0; l < h->lv.size(); ++l) {
     Level& L = h->lv[l];
     if (l == 0) {
-      launch_elem_q1(h->physics, h->dim, h->n_elems, h->d_coords, h->d_conn, h->d_coef, h->nu, L.slot_elem,
-                     L.d.ke, st);
+      if (h->physics == BDDC_STOKES)
+        launch_elem_q2q1(h->n_elems, h->d_coords, h->d_conn, h->d_coef, L.slot_elem, L.d.ke, st);
+      else
+        launch_elem_q1(h->physics, h->dim, h->n_elems, h->d_coords, h->d_conn, h->d_coef, h->nu, L.slot_elem,
+                       L.d.ke, st);
+      if (h->has_lift)
+        launch_lift(h->n_free, h->npe * h->ndof, h->d_lift_ptr, h->d_lift_slot, h->d_lift_a, L.d.ke, h->d_lift_ud,
+                    h->d_lift, st);
     } else {
       const Level& P = h->lv[l - 1];
       std::vector<int64_t> dummy;
@@ -952,12 +1002,19 @@ void numeric_setup(bddc_handle_s* h) {
 void analysis(bddc_handle_s* h, const bddc_mesh* mesh, const bddc_partition* part) {
   const double t0 = now_ms();
   if (!mesh || !part) fail(BDDC_ERR_INVALID, "null mesh or partition");
+  if (h->opts.krylov < BDDC_KRYLOV_AUTO || h->opts.krylov > BDDC_KRYLOV_FGMRES) fail(BDDC_ERR_INVALID, "unknown Krylov method");
   if (mesh->dim != 2 && mesh->dim != 3) fail(BDDC_ERR_INVALID, "dim must be 2 or 3");
-  if (mesh->nodes_per_elem != (1 << mesh->dim)) fail(BDDC_ERR_INVALID, "only Q1 elements (2**dim nodes)");
+  if (mesh->physics != BDDC_POISSON && mesh->physics != BDDC_ELASTICITY && mesh->physics != BDDC_STOKES)
+    fail(BDDC_ERR_INVALID, "unknown physics");
+  if (mesh->physics == BDDC_STOKES) {
+    if (mesh->dim != 3 || mesh->nodes_per_elem != 27 || mesh->dofs_per_node != 4)
+      fail(BDDC_ERR_INVALID, "Stokes needs Q2-Q1 hexahedra: dim 3, 27 nodes per element, 4 DOFs per node");
+  } else if (mesh->nodes_per_elem != (1 << mesh->dim)) {
+    fail(BDDC_ERR_INVALID, "only Q1 elements (2**dim nodes)");
+  }
   if (mesh->physics == BDDC_ELASTICITY && (mesh->dim != 3 || mesh->dofs_per_node != 3))
     fail(BDDC_ERR_INVALID, "elasticity needs dim 3 and 3 DOFs per node");
   if (mesh->physics == BDDC_POISSON && mesh->dofs_per_node != 1) fail(BDDC_ERR_INVALID, "Poisson needs 1 DOF per node");
-  if (mesh->physics != BDDC_POISSON && mesh->physics != BDDC_ELASTICITY) fail(BDDC_ERR_INVALID, "unknown physics");
   if (part->n_levels < 2 || part->n_levels > BDDC_MAX_LEVELS) fail(BDDC_ERR_INVALID, "n_levels out of range");
   if (mesh->n_nodes <= 0 || mesh->n_elems <= 0 || !mesh->coords || !mesh->conn || !mesh->coef || !mesh->dirichlet)
     fail(BDDC_ERR_INVALID, "empty mesh or null array");
@@ -980,6 +1037,16 @@ void analysis(bddc_handle_s* h, const bddc_mesh* mesh, const bddc_partition* par
   h->n_free = 0;
   for (int64_t q = 0; q < h->n_full; ++q)
     if (!mesh->dirichlet[q]) h->free_of_full[q] = h->n_free++;
+  h->dir_full.assign(h->n_full, 0.0);
+  h->has_lift = false;
+  if (mesh->dir_values)
+    for (int64_t q = 0; q < h->n_full; ++q)
+      if (mesh->dirichlet[q] && mesh->dir_values[q] != 0.0) {
+        if (!std::isfinite(mesh->dir_values[q])) fail(BDDC_ERR_INVALID, "non-finite prescribed value");
+        h->dir_full[q] = mesh->dir_values[q];
+        h->has_lift = true;
+      }
+  if (!h->has_lift) h->dir_full.clear();
   h->n_levels = part->n_levels;
   h->parts.clear();
   h->n_parts.clear();
@@ -1043,6 +1110,56 @@ void device_setup(bddc_handle_s* h) {
     prepare_level(h, h->lv[l], A, st);
     if (l > 0) prepare_level_segments(h->lv[l], h->lv[l - 1], A, st);
   }
+  if (h->has_lift) {
+    // occurrences (slot, element row) of every free DOF in elements that touch a non-zero
+    // prescribed value, in slot order; u_d of every slot
+    const Level& L = h->lv[0];
+    const int ne = h->npe * h->ndof;
+    const int64_t nel = h->n_elems;
+    std::vector<int32_t> slot_elem(nel);
+    for (int64_t s = 0; s < L.maps.n_sub(); ++s)
+      for (int64_t k = L.maps.sub_elem_ptr[s]; k < L.maps.sub_elem_ptr[s + 1]; ++k)
+        slot_elem[k] = (int32_t)L.maps.sub_elems[k];
+    std::vector<double> ud((size_t)nel * ne, 0.0);
+    std::vector<int64_t> ptr(h->n_free + 1, 0);
+    std::vector<char> lifting(nel, 0);
+    auto full_dof = [&](int64_t e, int a) {
+      return (int64_t)h->conn[e * h->npe + a / h->ndof] * h->ndof + a % h->ndof;
+    };
+    for (int64_t k = 0; k < nel; ++k) {
+      const int64_t e = slot_elem[k];
+      for (int a = 0; a < ne; ++a) {
+        const double v = h->dir_full[full_dof(e, a)];
+        ud[(size_t)k * ne + a] = v;
+        if (v != 0.0) lifting[k] = 1;
+      }
+      if (lifting[k])
+        for (int a = 0; a < ne; ++a) {
+          const int64_t g = h->free_of_full[full_dof(e, a)];
+          if (g >= 0) ptr[g + 1]++;
+        }
+    }
+    for (int64_t g = 0; g < h->n_free; ++g) ptr[g + 1] += ptr[g];
+    std::vector<int32_t> lslot(ptr[h->n_free]), la(ptr[h->n_free]);
+    std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
+    for (int64_t k = 0; k < nel; ++k) {
+      if (!lifting[k]) continue;
+      const int64_t e = slot_elem[k];
+      for (int a = 0; a < ne; ++a) {
+        const int64_t g = h->free_of_full[full_dof(e, a)];
+        if (g < 0) continue;
+        lslot[fill[g]] = (int32_t)k;
+        la[fill[g]] = a;
+        fill[g]++;
+      }
+    }
+    h->d_dir_full = A.upload(h->dir_full, st);
+    h->d_lift_ud = A.upload(ud, st);
+    h->d_lift_ptr = A.upload(ptr, st);
+    h->d_lift_slot = A.upload(lslot, st);
+    h->d_lift_a = A.upload(la, st);
+    h->d_lift = A.alloc<double>(h->n_free);
+  }
   h->scal = A.alloc<double>(16);
   h->partial = A.alloc<double>(kDotBlocks);
   ck(cudaMallocHost(&h->h_scal, sizeof(double) * 16), "cudaMallocHost");
@@ -1054,6 +1171,17 @@ void device_setup(bddc_handle_s* h) {
   h->vq = A.alloc<double>(ni);
   h->vrold = A.alloc<double>(ni);
   h->vg = A.alloc<double>(ni);
+  h->vs = A.alloc<double>(ni);
+  h->vsh = A.alloc<double>(ni);
+  h->vt = A.alloc<double>(ni);
+  if (krylov_kind(h) == BDDC_KRYLOV_FGMRES) {
+    h->gm_V = A.alloc<double>(ni * (kRestart + 1));
+    h->gm_Z = A.alloc<double>(ni * kRestart);
+    h->gm_w = A.alloc<double>(ni);
+    h->gm_h = A.alloc<double>(3 * (kRestart + 1) + 2);
+    h->gm_partial = A.alloc<double>((int64_t)kDotBlocks * (kRestart + 1));
+    ck(cudaMallocHost(&h->h_gm, sizeof(double) * (3 * (kRestart + 1) + 2)), "cudaMallocHost");
+  }
   h->fcol = A.alloc<double>(h->n_free);
   h->ucol = A.alloc<double>(h->n_free);
   const int64_t nbig = std::max<int64_t>(h->n_full, h->lv[0].n_vec);
@@ -1090,7 +1218,39 @@ void pcg_body(bddc_handle_s* h, double* x, int flexible, cudaStream_t st) {
   launch_pcg_update_p(h->vp, h->vz, S, n, st);
 }
 
-// Capture pcg_body into a CUDA graph (once per handle; the buffers never move).
+// One right-preconditioned BiCGstab iteration (van der Vorst; the Krylov method of the Stokes
+// experiments of Sec. 4), all on the device.  Vectors: x, r = vr, rh = vrold (fixed shadow
+// residual), p = vp, ph = M^{-1} p = vz, v = S ph = vq, s = vs, sh = M^{-1} s = vsh, t = S sh = vt.
+// Scalars: 0 rho, 1 alpha, 2 omega, 3 rho_new, 4 rh.v, 5 t.s, 6 t.t, 7 beta, 8 r.r.
+void bicg_body(bddc_handle_s* h, double* x, cudaStream_t st) {
+  const int64_t n = h->lv[0].d.n_iface;
+  double* S = h->scal;
+  launch_dot(h->vrold, h->vr, n, h->partial, kDotBlocks, S + 3, st);
+  launch_bicg_scalars(S, 0, st);
+  launch_bicg_p(h->vp, h->vr, h->vq, S, n, st);
+  precond(h, h->vp, h->vz, st);
+  schur_apply(h, h->vz, h->vq, st);
+  launch_dot(h->vrold, h->vq, n, h->partial, kDotBlocks, S + 4, st);
+  launch_bicg_scalars(S, 1, st);
+  launch_bicg_s(h->vs, h->vr, h->vq, S, n, st);
+  precond(h, h->vs, h->vsh, st);
+  schur_apply(h, h->vsh, h->vt, st);
+  launch_dot(h->vt, h->vs, n, h->partial, kDotBlocks, S + 5, st);
+  launch_dot(h->vt, h->vt, n, h->partial, kDotBlocks, S + 6, st);
+  launch_bicg_scalars(S, 2, st);
+  launch_bicg_xr(x, h->vr, h->vz, h->vsh, h->vs, h->vt, S, n, st);
+  launch_dot(h->vr, h->vr, n, h->partial, kDotBlocks, S + 8, st);
+}
+
+// kind 0/1: PCG with Fletcher-Reeves / flexible beta; 2: BiCGstab
+void iteration_body(bddc_handle_s* h, double* x, int kind, cudaStream_t st) {
+  if (kind == 2)
+    bicg_body(h, x, st);
+  else
+    pcg_body(h, x, kind, st);
+}
+
+// Capture one Krylov iteration into a CUDA graph (once per handle; the buffers never move).
 void capture_iteration(bddc_handle_s* h, int flexible) {
   if (!h->cap_st) ck(cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking), "cudaStreamCreate");
   cudaGraph_t g = nullptr;
@@ -1098,7 +1258,7 @@ void capture_iteration(bddc_handle_s* h, int flexible) {
   const int64_t launches0 = g_launches.load();
   ck(cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
   try {
-    pcg_body(h, h->vx, flexible, h->cap_st);
+    iteration_body(h, h->vx, flexible, h->cap_st);
   } catch (...) {
     cudaStreamEndCapture(h->cap_st, &g);
     if (g) cudaGraphDestroy(g);
@@ -1116,6 +1276,17 @@ void capture_iteration(bddc_handle_s* h, int flexible) {
   ck(e, "cudaGraphInstantiate");
   h->iter_graph = ex;
   h->iter_graph_flexible = flexible;
+}
+
+void drop_graph_if_kind_differs(bddc_handle_s* h, int kind) {
+  if (!h->iter_graph || h->iter_graph_flexible == kind) return;
+  cudaGraphExecDestroy(h->iter_graph);
+  h->iter_graph = nullptr;
+  for (auto& r : h->graph_prof) {
+    h->event_pool.push_back(r.a);
+    h->event_pool.push_back(r.b);
+  }
+  h->graph_prof.clear();
 }
 
 // r = g - S x, z = M^{-1} r, p = z, rz = r.z  (start, or restart after a failed true-residual check)
@@ -1156,15 +1327,7 @@ PcgResult pcg(bddc_handle_s* h, const double* g, double* x, double tol, int maxi
     return res;
   }
   const bool graphs = h->opts.use_graph && x == h->vx;
-  if (h->iter_graph && h->iter_graph_flexible != flexible) {
-    cudaGraphExecDestroy(h->iter_graph);
-    h->iter_graph = nullptr;
-    for (auto& r : h->graph_prof) {
-      h->event_pool.push_back(r.a);
-      h->event_pool.push_back(r.b);
-    }
-    h->graph_prof.clear();
-  }
+  drop_graph_if_kind_differs(h, flexible);
   bool checked = false;
   for (int it = 1; it <= maxit; ++it) {
     bool replayed = false;
@@ -1200,6 +1363,71 @@ PcgResult pcg(bddc_handle_s* h, const double* g, double* x, double tol, int maxi
       }
       checked = true;
       pcg_start(h, g, x, false, st);   // restart from the current iterate with the true residual
+    }
+  }
+  return res;
+}
+
+// Right-preconditioned BiCGstab on the level-1 interface; stops on ||r|| / ||g|| <= tol once
+// the true residual g - S x confirms it (the recurrence continues otherwise).
+PcgResult bicgstab(bddc_handle_s* h, const double* g, double* x, double tol, int maxit) {
+  cudaStream_t st = h->st;
+  const int64_t n = h->lv[0].d.n_iface;
+  PcgResult res;
+  ck(cudaMemsetAsync(x, 0, sizeof(double) * n, st), "memset");
+  if (n == 0) {
+    res.converged = true;
+    return res;
+  }
+  double* S = h->scal;
+  ck(cudaMemsetAsync(S, 0, sizeof(double) * 16, st), "memset");
+  launch_dot(g, g, n, h->partial, kDotBlocks, S + 10, st);
+  ck(cudaMemcpyAsync(h->vr, g, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
+  ck(cudaMemcpyAsync(h->vrold, g, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
+  ck(cudaMemsetAsync(h->vp, 0, sizeof(double) * n, st), "memset");
+  ck(cudaMemsetAsync(h->vq, 0, sizeof(double) * n, st), "memset");
+  launch_bicg_scalars(S, 3, st);
+  ck(cudaMemcpyAsync(h->h_scal, S, sizeof(double) * 16, cudaMemcpyDeviceToHost, st), "d2h");
+  ck(cudaStreamSynchronize(st), "sync");
+  const double gg = h->h_scal[10];
+  if (!std::isfinite(gg)) fail(BDDC_ERR_NAN, "NaN in the condensed right-hand side");
+  res.gnorm = std::sqrt(gg);
+  if (gg == 0.0) {
+    res.converged = true;
+    return res;
+  }
+  const bool graphs = h->opts.use_graph && x == h->vx;
+  drop_graph_if_kind_differs(h, 2);
+  for (int it = 1; it <= maxit; ++it) {
+    bool replayed = false;
+    if (graphs && h->iter_graph) {
+      ck(cudaGraphLaunch(h->iter_graph, st), "cudaGraphLaunch");
+      g_launches.fetch_add(h->graph_kernels);
+      replayed = true;
+    } else {
+      bicg_body(h, x, st);
+      if (graphs) capture_iteration(h, 2);
+    }
+    ck(cudaMemcpyAsync(h->h_scal, S, sizeof(double) * 16, cudaMemcpyDeviceToHost, st), "d2h");
+    ck(cudaStreamSynchronize(st), "sync");
+    if (replayed && !h->graph_prof.empty()) accumulate_graph_profile(h);
+    res.iterations = it;
+    const double rel = std::sqrt(h->h_scal[8] / gg);
+    if (!std::isfinite(rel)) fail(BDDC_ERR_NAN, "NaN in the Krylov recurrence");
+    res.rel = rel;
+    if (rel <= tol) {
+      schur_apply(h, x, h->vq, st);
+      ck(cudaMemcpyAsync(h->vs, g, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
+      launch_axpy_loc(h->vs, h->vq, -1.0, n, st);
+      launch_dot(h->vs, h->vs, n, h->partial, kDotBlocks, S + 9, st);
+      ck(cudaMemcpyAsync(h->h_scal + 9, S + 9, sizeof(double), cudaMemcpyDeviceToHost, st), "d2h");
+      ck(cudaStreamSynchronize(st), "sync");
+      const double rel_true = std::sqrt(h->h_scal[9] / gg);
+      res.rel = rel_true;
+      if (rel_true <= tol) {
+        res.converged = true;
+        return res;
+      }
     }
   }
   return res;
@@ -1243,7 +1471,127 @@ void lanczos(const PcgResult& r, double* lmin, double* lmax) {
   *lmax = kth(k - 1);
 }
 
-int solve_impl(bddc_handle_s* h, const double* rhs, double* x, int nrhs, double tol, bddc_stats* stats) {
+// Flexible GMRES(kRestart) with right preconditioning (Saad): the Krylov basis V is built from
+// S z_j with z_j = M^{-1} v_j kept in Z, so the update x += Z y stays exact for a preconditioner
+// that is not a fixed linear operator (FP32 factors of an indefinite saddle point: their rounding
+// error, ~kappa * 2^-24, breaks BiCGstab's short recurrences).  Classical Gram-Schmidt applied
+// twice; Givens rotations and the small triangular solve on the host.
+PcgResult fgmres(bddc_handle_s* h, const double* g, double* x, double tol, int maxit) {
+  cudaStream_t st = h->st;
+  const int64_t n = h->lv[0].d.n_iface;
+  const int m = kRestart;
+  PcgResult res;
+  ck(cudaMemsetAsync(x, 0, sizeof(double) * n, st), "memset");
+  if (n == 0) {
+    res.converged = true;
+    return res;
+  }
+  double* S = h->scal;
+  double* hd0 = h->gm_h;              // [m + 1] first Gram-Schmidt pass
+  double* hd1 = h->gm_h + (m + 1);    // [m + 1] second pass
+  double* hnrm = h->gm_h + 2 * (m + 1);
+  double* yd = h->gm_h + 2 * (m + 1) + 2;   // [m]
+  double* hh = h->h_gm;               // pinned mirror of gm_h
+  launch_dot(g, g, n, h->partial, kDotBlocks, S + 0, st);
+  ck(cudaMemcpyAsync(h->h_scal, S, sizeof(double), cudaMemcpyDeviceToHost, st), "d2h");
+  ck(cudaStreamSynchronize(st), "sync");
+  const double gg = h->h_scal[0];
+  if (!std::isfinite(gg)) fail(BDDC_ERR_NAN, "NaN in the condensed right-hand side");
+  res.gnorm = std::sqrt(gg);
+  if (gg == 0.0) {
+    res.converged = true;
+    return res;
+  }
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
+  int it = 0;
+  bool first = true;
+  while (it < maxit) {
+    // r = g - S x (x = 0 on the first cycle), v_0 = r / ||r||
+    ck(cudaMemcpyAsync(h->gm_w, g, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
+    if (!first) {
+      schur_apply(h, x, h->vq, st);
+      launch_axpy_loc(h->gm_w, h->vq, -1.0, n, st);
+    }
+    launch_dot(h->gm_w, h->gm_w, n, h->partial, kDotBlocks, hnrm, st);
+    launch_scale_by_norm(h->gm_V, h->gm_w, hnrm, n, st);
+    ck(cudaMemcpyAsync(hh + 2 * (m + 1), hnrm, sizeof(double), cudaMemcpyDeviceToHost, st), "d2h");
+    ck(cudaStreamSynchronize(st), "sync");
+    const double beta = std::sqrt(hh[2 * (m + 1)]);
+    if (!std::isfinite(beta)) fail(BDDC_ERR_NAN, "NaN in the Krylov recurrence");
+    res.rel = beta / res.gnorm;
+    if (res.rel <= tol) {   // the true residual of the current iterate meets the tolerance
+      res.converged = true;
+      return res;
+    }
+    first = false;
+    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(gv.begin(), gv.end(), 0.0);
+    gv[0] = beta;
+    int k = 0;   // Arnoldi steps of this cycle
+    while (k < m && it < maxit) {
+      const int j = k;
+      double* Vj = h->gm_V + (int64_t)j * n;
+      double* Zj = h->gm_Z + (int64_t)j * n;
+      precond(h, Vj, Zj, st);
+      schur_apply(h, Zj, h->gm_w, st);
+      launch_multidot(h->gm_V, n, j + 1, h->gm_w, n, h->gm_partial, kDotBlocks, hd0, st);
+      launch_combine(h->gm_w, h->gm_V, n, j + 1, hd0, -1.0, n, st);
+      launch_multidot(h->gm_V, n, j + 1, h->gm_w, n, h->gm_partial, kDotBlocks, hd1, st);
+      launch_combine(h->gm_w, h->gm_V, n, j + 1, hd1, -1.0, n, st);
+      launch_dot(h->gm_w, h->gm_w, n, h->partial, kDotBlocks, hnrm, st);
+      launch_scale_by_norm(h->gm_V + (int64_t)(j + 1) * n, h->gm_w, hnrm, n, st);
+      ck(cudaMemcpyAsync(hh, h->gm_h, sizeof(double) * (2 * (m + 1) + 1), cudaMemcpyDeviceToHost, st), "d2h");
+      ck(cudaStreamSynchronize(st), "sync");
+      double* col = &H[(size_t)j * (m + 1)];   // column j of the Hessenberg matrix
+      for (int i = 0; i <= j; ++i) col[i] = hh[i] + hh[(m + 1) + i];
+      col[j + 1] = std::sqrt(std::max(hh[2 * (m + 1)], 0.0));
+      for (int i = 0; i < j; ++i) {   // earlier rotations
+        const double a = col[i], b = col[i + 1];
+        col[i] = cs[i] * a + sn[i] * b;
+        col[i + 1] = -sn[i] * a + cs[i] * b;
+      }
+      const double a = col[j], b = col[j + 1];
+      const double rr = std::hypot(a, b);
+      cs[j] = rr > 0.0 ? a / rr : 1.0;
+      sn[j] = rr > 0.0 ? b / rr : 0.0;
+      col[j] = rr;
+      col[j + 1] = 0.0;
+      gv[j + 1] = -sn[j] * gv[j];
+      gv[j] = cs[j] * gv[j];
+      ++k;
+      ++it;
+      res.iterations = it;
+      res.rel = std::fabs(gv[j + 1]) / res.gnorm;
+      if (!std::isfinite(res.rel)) fail(BDDC_ERR_NAN, "NaN in the Krylov recurrence");
+      if (res.rel <= tol || rr == 0.0) break;
+    }
+    // y = R^{-1} g (upper triangular after the rotations), x += Z y
+    for (int i = k - 1; i >= 0; --i) {
+      double sacc = gv[i];
+      for (int l = i + 1; l < k; ++l) sacc -= H[(size_t)l * (m + 1) + i] * y[l];
+      const double d = H[(size_t)i * (m + 1) + i];
+      y[i] = d != 0.0 ? sacc / d : 0.0;
+    }
+    std::copy(y.begin(), y.begin() + k, hh + 2 * (m + 1) + 2);
+    ck(cudaMemcpyAsync(yd, hh + 2 * (m + 1) + 2, sizeof(double) * k, cudaMemcpyHostToDevice, st), "h2d");
+    launch_combine(x, h->gm_Z, n, k, yd, 1.0, n, st);
+    ck(cudaStreamSynchronize(st), "sync");
+    // the next cycle starts from the true residual and stops there if it meets the tolerance
+  }
+  // iteration cap: report the true residual
+  schur_apply(h, x, h->vq, st);
+  ck(cudaMemcpyAsync(h->gm_w, g, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
+  launch_axpy_loc(h->gm_w, h->vq, -1.0, n, st);
+  launch_dot(h->gm_w, h->gm_w, n, h->partial, kDotBlocks, S + 9, st);
+  ck(cudaMemcpyAsync(h->h_scal + 9, S + 9, sizeof(double), cudaMemcpyDeviceToHost, st), "d2h");
+  ck(cudaStreamSynchronize(st), "sync");
+  res.rel = std::sqrt(h->h_scal[9] / gg);
+  res.converged = res.rel <= tol;
+  return res;
+}
+
+int solve_impl(bddc_handle_s* h, const double* rhs, double* x, int nrhs, double tol, bddc_stats* stats,
+               bool with_lift) {
   if (!h->factored) fail(BDDC_ERR_INVALID, "handle has no numeric set-up");
   if (nrhs < 1) fail(BDDC_ERR_INVALID, "nrhs must be >= 1");
   if (!(tol > 0.0)) fail(BDDC_ERR_INVALID, "tol must be positive");
@@ -1253,11 +1601,19 @@ int solve_impl(bddc_handle_s* h, const double* rhs, double* x, int nrhs, double 
   bool all_conv = true;
   double worst = 0.0;
   PcgResult first;
+  const int kind = krylov_kind(h);
   for (int k = 0; k < nrhs; ++k) {
     const double* f = rhs + (int64_t)k * h->n_free;
     double* u = x + (int64_t)k * h->n_free;
+    if (with_lift && h->has_lift) {   // f - K_fd u_d
+      ck(cudaMemcpyAsync(h->fcol, f, sizeof(double) * h->n_free, cudaMemcpyDeviceToDevice, st), "copy");
+      launch_axpy_loc(h->fcol, h->d_lift, 1.0, h->n_free, st);
+      f = h->fcol;
+    }
     condensed_rhs(h, f, h->vg, st);
-    PcgResult r = pcg(h, h->vg, h->vx, tol, h->opts.maxit);
+    PcgResult r = kind == BDDC_KRYLOV_BICGSTAB ? bicgstab(h, h->vg, h->vx, tol, h->opts.maxit)
+                  : kind == BDDC_KRYLOV_FGMRES ? fgmres(h, h->vg, h->vx, tol, h->opts.maxit)
+                                               : pcg(h, h->vg, h->vx, tol, h->opts.maxit);
     recover(h, f, h->vx, u, st);
     maxits = std::max(maxits, r.iterations);
     all_conv = all_conv && r.converged;
@@ -1311,12 +1667,13 @@ bool grad_view(bddc_handle_s* h, GradView* v) {
   v->coef = h->d_coef;
   v->edof = h->d_edof;
   v->free_of_full = h->d_free_of_full;
+  v->dir_full = h->has_lift ? h->d_dir_full : nullptr;
   v->stream = h->st;
   return true;
 }
 
 int adjoint_solve_into(bddc_handle_s* h, const double* dJdu, double* lam, int nrhs, double tol) {
-  return guarded([&]() { return solve_impl(h, dJdu, lam, nrhs, tol, nullptr); });
+  return guarded([&]() { return solve_impl(h, dJdu, lam, nrhs, tol, nullptr, false); });
 }
 
 }  // namespace bddc
@@ -1399,7 +1756,7 @@ int bddc_update_coef(bddc_handle h, const double* coef) {
 int bddc_solve(bddc_handle h, const double* rhs, double* x, int nrhs, double tol, bddc_stats* stats) {
   return guarded([&]() {
     if (!h || h->analysis_only || !rhs || !x) fail(BDDC_ERR_INVALID, "bad handle or vectors");
-    return solve_impl(h, rhs, x, nrhs, tol, stats);
+    return solve_impl(h, rhs, x, nrhs, tol, stats, true);
   });
 }
 
@@ -1413,7 +1770,7 @@ int bddc_solve_host(bddc_handle h, const double* rhs_host, double* x_host, int n
     int rc;
     try {
       ck(cudaMemcpyAsync(dr, rhs_host, bytes, cudaMemcpyHostToDevice, h->st), "h2d");
-      rc = solve_impl(h, dr, dx, nrhs, tol, stats);
+      rc = solve_impl(h, dr, dx, nrhs, tol, stats, true);
       ck(cudaMemcpyAsync(x_host, dx, bytes, cudaMemcpyDeviceToHost, h->st), "d2h");
       ck(cudaStreamSynchronize(h->st), "sync");
     } catch (...) {
@@ -1461,7 +1818,7 @@ int bddc_grad(bddc_handle h, const double* dJdu, const double* u, int nrhs, doub
     }
     int rc;
     try {
-      rc = solve_impl(h, dJdu, lam, nrhs, tol, nullptr);   // K lambda = dJ/du (K symmetric)
+      rc = solve_impl(h, dJdu, lam, nrhs, tol, nullptr, false);   // K lambda = dJ/du (K symmetric)
       if (grad_coef && (rc == BDDC_OK || rc == BDDC_ERR_NOT_CONVERGED)) {
         double *lf = nullptr, *uf = nullptr;
         const size_t fb = sizeof(double) * (size_t)h->n_full * nrhs;
@@ -1469,6 +1826,8 @@ int bddc_grad(bddc_handle h, const double* dJdu, const double* u, int nrhs, doub
         ck(cudaMallocAsync(&uf, fb, st), "cudaMallocAsync");
         launch_expand_free(lam, h->d_free_of_full, h->n_full, nrhs, h->n_free, lf, st);
         launch_expand_free(u, h->d_free_of_full, h->n_full, nrhs, h->n_free, uf, st);
+        if (h->has_lift)   // prescribed values enter K_e u_e
+          for (int k = 0; k < nrhs; ++k) launch_axpy_loc(uf + (int64_t)k * h->n_full, h->d_dir_full, 1.0, h->n_full, st);
         const Level& L = h->lv[0];
         launch_grad_contract_slots(h->n_elems, h->npe * h->ndof, L.d.ke, L.slot_elem, h->d_coef, h->d_edof, lf, uf,
                                    nrhs, h->n_full, grad_coef, st);

@@ -7,7 +7,8 @@
 //    constrained Neumann problem of Eq. psi_def / Eq. sub_cor restricted to the interface.
 //  * G_i = Y_i Y_i^T = C_i A_i^{-1} C_i^T (FP64), its Cholesky factor and inverse;
 //    Psi_i = A_i^{-1} C_i^T G_i^{-1} (so C_i Psi_i = I and K_i Psi_i = -C_i^T Lambda_i with
-//    Lambda_i = rho I - G_i^{-1}), K_Ci = Psi_i^T K_i Psi_i = -Lambda_i = G_i^{-1} - rho I.
+//    Lambda_i = R - G_i^{-1}), K_Ci = Psi_i^T K_i Psi_i = -Lambda_i = G_i^{-1} - R, where
+//    R = diag(rho c_rho) (rho on the rows that augment A_i, 0 on Stokes pressure rows).
 #include "internal.h"
 
 namespace bddc {
@@ -73,26 +74,40 @@ __global__ void k_potrf_diag(LevelDev L, int k) {
   }
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
+  __shared__ T sg[NB];
   for (int j = 0; j < NB; ++j) {
     if (threadIdx.x == 0) {
       T d = A[j][j];
-      if (!(d > (T)0)) {
+      T sj = (T)1;
+      if (L.indefinite) {
+        if (!(fabs(d) > (T)1e-30)) {
+          bad = 1;
+          d = (T)1;
+        }
+        if (d < (T)0) {
+          sj = (T)-1;
+          d = -d;
+        }
+      } else if (!(d > (T)0)) {
         bad = 1;
         d = (T)1;
       }
       A[j][j] = sqrt(d);
+      sg[j] = sj;
     }
     __syncthreads();
-    const T piv = A[j][j];
+    const T piv = A[j][j] * sg[j];   // l_ij = a_ij / (s_j l_jj)
     for (int i = j + 1 + threadIdx.x; i < NB; i += blockDim.x) A[i][j] /= piv;
     __syncthreads();
     const int w = NB - 1 - j;
+    const T sj = sg[j];
     for (int t = threadIdx.x; t < w * w; t += blockDim.x) {
       const int i = j + 1 + t / w, c = j + 1 + t % w;
-      if (c <= i) A[i][c] -= A[i][j] * A[c][j];
+      if (c <= i) A[i][c] -= A[i][j] * sj * A[c][j];
     }
     __syncthreads();
   }
+  if (threadIdx.x < NB) ((T*)L.sgn)[m.vec_off + (int64_t)k * NB + threadIdx.x] = sg[threadIdx.x];
   if (threadIdx.x == 0 && bad) flag_breakdown(L.status, s);
   // X = L^{-1} written to the diagonal-inverse store, one column per thread (each thread
   // reads back only the entries of its own column)
@@ -128,10 +143,11 @@ __global__ void k_trsm_panel(LevelDev L, int k) {
   T acc[4][4] = {};
   gemm_nt_4x4(As, Xs, acc, tx, ty);
   __syncthreads();
+  const T* sk = (const T*)L.sgn + m.vec_off + (int64_t)k * NB;   // L(i,k) = A(i,k) L_kk^{-T} S_k
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) g[(4 * ty + a) * NB + 4 * tx + b] = acc[a][b];
+    for (int b = 0; b < 4; ++b) g[(4 * ty + a) * NB + 4 * tx + b] = acc[a][b] * sk[4 * tx + b];
 }
 
 // ---- step k, part 3: trailing update A(i,j) -= L(i,k) L(j,k)^T, k < j <= i, j < min(Bc, jmax) --
@@ -157,6 +173,11 @@ __global__ void k_syrk_update(LevelDev L, int k, int jmax) {
   load_kmajor(As, tile_ptr<T>(m, L.tiles, i, k));
   load_kmajor(Bs, tile_ptr<T>(m, L.tiles, j, k));
   __syncthreads();
+  if (L.indefinite) {   // A(i,j) -= L(i,k) S_k L(j,k)^T: fold S_k into the k-major B operand
+    const T* sk = (const T*)L.sgn + m.vec_off + (int64_t)k * NB;
+    for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) Bs[(t / NB) * LDS + (t % NB)] *= sk[t / NB];
+    __syncthreads();
+  }
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   T acc[4][4] = {};
   gemm_nt_4x4(As, Bs, acc, tx, ty);
@@ -182,10 +203,11 @@ __global__ void k_gram(LevelDev L) {
   if (b > a) return;
   const T* ya = tile_ptr<T>(m, L.tiles, m.Bc + a / NB, m.nIb) + (a % NB) * NB;
   const T* yb = tile_ptr<T>(m, L.tiles, m.Bc + b / NB, m.nIb) + (b % NB) * NB;
+  const T* sG = (const T*)L.sgn + m.vec_off + (int64_t)m.nIb * NB;   // G = Y S Y^T
   double acc = 0.0;
   for (int c = lane; c < m.nGb * NB; c += 32) {
     const int64_t o = (int64_t)(c / NB) * NB2 + (c % NB);
-    acc += (double)ya[o] * (double)yb[o];
+    acc += (double)ya[o] * (double)sG[c] * (double)yb[o];
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane == 0) {
@@ -195,11 +217,82 @@ __global__ void k_gram(LevelDev L) {
   }
 }
 
+// G^{-1} by Gauss-Jordan elimination with partial pivoting (indefinite levels), FP64, one block
+// per subdomain; W (the K_C buffer) holds the eliminated copy of G.
+__device__ void gauss_jordan_inverse(double* G, double* W, int n, int* bad) {
+  __shared__ int piv_row;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    W[t] = G[t];
+    G[t] = (t / n == t % n) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) {
+      int best = j;
+      double bv = fabs(W[j * n + j]);
+      for (int i = j + 1; i < n; ++i)
+        if (fabs(W[i * n + j]) > bv) {
+          bv = fabs(W[i * n + j]);
+          best = i;
+        }
+      if (!(bv > 0.0)) *bad = 1;
+      piv_row = best;
+    }
+    __syncthreads();
+    const int pr = piv_row;
+    if (pr != j)
+      for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        double a = W[j * n + c], b = W[pr * n + c];
+        W[j * n + c] = b;
+        W[pr * n + c] = a;
+        a = G[j * n + c];
+        b = G[pr * n + c];
+        G[j * n + c] = b;
+        G[pr * n + c] = a;
+      }
+    __syncthreads();
+    const double inv = W[j * n + j] != 0.0 ? 1.0 / W[j * n + j] : 0.0;
+    __syncthreads();
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+      W[j * n + c] *= inv;
+      G[j * n + c] *= inv;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+      const int i = t / n, c = t % n;
+      if (i == j) continue;
+      const double f = W[i * n + j];
+      if (c != j) W[i * n + c] -= f * W[j * n + c];
+      G[i * n + c] -= f * G[j * n + c];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+      if (i != j) W[i * n + j] = 0.0;
+    __syncthreads();
+  }
+}
+
 __global__ void k_small_chol_inv(LevelDev L) {
   const int s = blockIdx.x;
   const SubMeta m = L.meta[s];
   const int n = m.nc;
   if (n == 0) return;
+  if (L.indefinite) {
+    __shared__ int badi;
+    if (threadIdx.x == 0) badi = 0;
+    __syncthreads();
+    double* G = L.Ginv + m.g_off;
+    double* W = L.KC + m.g_off;
+    gauss_jordan_inverse(G, W, n, &badi);
+    __syncthreads();
+    if (threadIdx.x == 0 && badi) flag_breakdown(L.status, s);
+    const double rho = L.rho[s];
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+      const int a = t / n, b = t % n;
+      W[t] = G[t] - (a == b ? rho * L.c_rho[m.c_off + a] : 0.0);   // K_C = G^{-1} - R
+    }
+    return;
+  }
   double* G = L.Ginv + m.g_off;   // in: G (full), out: G^{-1}
   double* W = L.KC + m.g_off;     // scratch for L^{-1}, then K_C
   __shared__ int bad;
@@ -248,7 +341,7 @@ __global__ void k_small_chol_inv(LevelDev L) {
   const double rho = L.rho[s];
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
     const int a = t / n, b = t % n;
-    W[t] = G[t] - (a == b ? rho : 0.0);
+    W[t] = G[t] - (a == b ? rho * L.c_rho[m.c_off + a] : 0.0);   // K_C = G^{-1} - R
   }
 }
 
@@ -271,7 +364,7 @@ __global__ void k_psi_rhs(LevelDev L) {
       const T y = tile_ptr<T>(m, L.tiles, m.Bc + p / NB, jb)[(p % NB) * NB + cc];
       acc += (double)y * Gi[p * nc + q];
     }
-    Z[t] = (T)acc;
+    Z[t] = (T)acc;   // Z = Y^T G^{-1}
   }
 }
 
@@ -337,9 +430,10 @@ __global__ void k_cc_yv(LevelDev L, const T* __restrict__ vec, const int32_t* __
   const SubMeta m = L.meta[s];
   const int p = (int)(g - m.c_off);
   const T* v = vec + m.vec_off + m.nIb * NB;
+  const T* sg = (const T*)L.sgn + m.vec_off + m.nIb * NB;   // the sweep left S L^{-1} r: undo S
   const T* yrow = tile_ptr<T>(m, L.tiles, m.Bc + p / NB, m.nIb) + (p % NB) * NB;
   T acc = (T)0;
-  for (int c = lane; c < m.nGb * NB; c += 32) acc += yrow[(int64_t)(c / NB) * NB2 + (c % NB)] * v[c];
+  for (int c = lane; c < m.nGb * NB; c += 32) acc += yrow[(int64_t)(c / NB) * NB2 + (c % NB)] * (v[c] * sg[c]);
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane == 0) t[g] = (double)acc;
 }
@@ -369,7 +463,7 @@ __global__ void k_cc_update(LevelDev L, T* __restrict__ vec, const double* __res
   for (int p = 0; p < m.nc; ++p)
     acc += tile_ptr<T>(m, L.tiles, m.Bc + p / NB, m.nIb + c / NB)[(p % NB) * NB + (c % NB)] * (T)mu[m.c_off + p];
   T* v = vec + m.vec_off + m.nIb * NB;
-  v[c] = v[c] - acc;
+  v[c] = v[c] - acc;   // S L^{-1} r - Y^T mu
 }
 
 // rc_sub = Psi_G^T v_G (FP64 result), one block per subdomain: warp w takes interface rows

@@ -11,6 +11,10 @@
 //     j = 0 .. min(i, Bc-1).  Block rows Bc .. Bc+ncb-1 hold the constraint rows; after the
 //     partial Cholesky they hold Y = C L^{-T} (nonzero only in interface columns).
 //   * The inverses of the Bc diagonal factor tiles are kept next to the factor.
+//   * Symmetric indefinite levels (Stokes) use a signed Cholesky A = L S L^T with S = diag(+-1)
+//     and no pivoting (velocities precede pressures in both blocks); SPD levels have S = I.
+//     Then the constraint block rows hold Y S (Y = C L^{-T}), G = C A^{-1} C^T = (Y S) S (Y S)^T,
+//     Psi = L^{-T} (Y S)^T G^{-1}, and the forward sweep leaves S L^{-1} r.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -78,6 +82,9 @@ struct LevelDev {
   void* tiles;                    // factor tiles (float or double)
   void* dinv;                     // diagonal inverses
   void* psi;                      // Psi_G
+  void* sgn;                      // [n_vec] pivot signs of the signed Cholesky (T; +1 for SPD levels)
+  const double* c_rho;            // [sum nc] 1 where a constraint row is augmented by rho, else 0
+  int indefinite;                 // 1: negative pivots allowed (Stokes), 0: SPD
   int* status;                    // [4]: breakdown flag, level sub, timeout
 };
 
@@ -93,12 +100,17 @@ struct GradView {
   const double* coef;
   const int64_t* edof;            // element -> full DOF ids
   const int64_t* free_of_full;    // full DOF -> free id or -1
+  const double* dir_full;         // [n_full] prescribed values (0 on free DOFs), or null when all zero
   cudaStream_t stream;
 };
 
 // ---------------------------------------------------------------- assembly (assemble.cu)
 void launch_elem_q1(int physics, int dim, int64_t n_elems, const double* coords, const int32_t* conn,
                     const double* coef, double nu, const int32_t* slot_elem, double* ke, cudaStream_t st);
+void launch_elem_q2q1(int64_t n_elems, const double* coords, const int32_t* conn, const double* coef,
+                      const int32_t* slot_elem, double* ke, cudaStream_t st);
+void launch_lift(int64_t n_free, int ne, const int64_t* lptr, const int32_t* lslot, const int32_t* la,
+                 const double* ke, const double* ud, double* lift, cudaStream_t st);
 void launch_csr_values(const LevelDev& L, int64_t n_rows_total, const int32_t* row_sub, cudaStream_t st);
 template <typename T>
 void launch_densify_rows(const LevelDev& L, const int32_t* row_sub, cudaStream_t st);
@@ -165,5 +177,18 @@ void launch_copy_segments(const double* src, const int64_t* src_off, double* dst
 void launch_iface_rhs(double* g, const double* f, const int64_t* idx, const double* t, int64_t n,
                       cudaStream_t st);
 void launch_put_indexed(double* u, const int64_t* idx, const double* v, int64_t n, cudaStream_t st);
+// flexible GMRES (vector.cu): out[i] = V_i . w (i < nv, partial holds nv * nblk doubles);
+// w += alpha sum_i c_i V_i; dst = src / sqrt(*nrm2)
+void launch_multidot(const double* V, int64_t ldv, int nv, const double* w, int64_t n, double* partial, int nblk,
+                     double* out, cudaStream_t st);
+void launch_combine(double* w, const double* V, int64_t ldv, int nv, const double* c, double alpha, int64_t n,
+                    cudaStream_t st);
+void launch_scale_by_norm(double* dst, const double* src, const double* nrm2, int64_t n, cudaStream_t st);
+// BiCGstab (vector.cu)
+void launch_bicg_scalars(double* S, int stage, cudaStream_t st);
+void launch_bicg_p(double* p, const double* r, const double* v, const double* S, int64_t n, cudaStream_t st);
+void launch_bicg_s(double* sv, const double* r, const double* v, const double* S, int64_t n, cudaStream_t st);
+void launch_bicg_xr(double* x, double* r, const double* ph, const double* sh, const double* sv, const double* t,
+                    const double* S, int64_t n, cudaStream_t st);
 
 }  // namespace bddc

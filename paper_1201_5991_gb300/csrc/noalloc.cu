@@ -57,13 +57,13 @@ cudaError_t scratch_address(void** out) {
 
 // out_l / out_u: full-DOF copies (zero on prescribed DOFs) of one right-hand side
 __global__ void k_expand_pair(const double* __restrict__ lam, const double* __restrict__ u,
-                              const int64_t* __restrict__ free_of_full, int64_t n_full, double* __restrict__ out_l,
-                              double* __restrict__ out_u) {
+                              const int64_t* __restrict__ free_of_full, const double* __restrict__ dir_full,
+                              int64_t n_full, double* __restrict__ out_l, double* __restrict__ out_u) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n_full) return;
   const int64_t f = free_of_full[j];
   out_l[j] = f >= 0 ? lam[f] : 0.0;
-  out_u[j] = f >= 0 ? u[f] : 0.0;
+  out_u[j] = f >= 0 ? u[f] : (dir_full ? dir_full[j] : 0.0);   // prescribed values enter K_e u_e
 }
 
 // grad[e] += -(1/coef_e) lam_e^T K_e u_e for one right-hand side; one warp per element
@@ -122,7 +122,7 @@ extern "C" int bddc_grad_noalloc(bddc_handle h, const double* dJdu, const double
     for (int k = 0; k < nrhs && ce == cudaSuccess; ++k) {
       note_launch();
       k_expand_pair<<<(unsigned)((v.n_full + 255) / 256), 256, 0, st>>>(
-          grad_rhs + (int64_t)k * v.n_free, u + (int64_t)k * v.n_free, v.free_of_full, v.n_full, lf, uf);
+          grad_rhs + (int64_t)k * v.n_free, u + (int64_t)k * v.n_free, v.free_of_full, v.dir_full, v.n_full, lf, uf);
       note_launch();
       k_grad_contract_accum<<<(unsigned)((v.n_elems + 7) / 8), 256, 0, st>>>(v.n_elems, v.ne, v.ke, v.slot_elem,
                                                                               v.coef, v.edof, lf, uf, grad_coef);

@@ -1,7 +1,8 @@
 // Streaming triangular sweeps with the tiled factors, batched over all subdomains of a level:
-// forward L y = b and backward L^T x = y over the interior block rows (the discrete
+// forward y = S L^{-1} b and backward L^T x = y over the interior block rows (the discrete
 // Dirichlet problems of the Schur operator, Sec. 2) or over the interface block rows (the
-// constrained Neumann problem of Eq. sub_cor, restricted to the interface).
+// constrained Neumann problem of Eq. sub_cor, restricted to the interface).  S holds the pivot
+// signs of the signed Cholesky (identity for SPD levels), so the pair solves L S L^T x = b.
 //
 // Design (GB300): the sweep is bound by reading the factor from HBM once.  A persistent grid
 // of 2 CTAs per SM takes block-row tasks (subdomain s, block row i) from a global counter in
@@ -172,7 +173,10 @@ __global__ void __launch_bounds__(kThreads, 2)
         for (int e = tid; e < cnt * NB; e += kThreads) {
           const int kk = k + e / NB;
           const int j = BWD ? (B1 - 1 - kk) : (B0 + kk);
-          ybuf[kk % kYSlots][e % NB] = __ldcg(v + j * NB + e % NB);
+          T yj = __ldcg(v + j * NB + e % NB);
+          if (!BWD && L.indefinite)   // solved rows hold S_j y_j: the update needs y_j
+            yj *= ((const T*)L.sgn)[m.vec_off + (int64_t)j * NB + e % NB];
+          ybuf[kk % kYSlots][e % NB] = yj;
         }
         __syncthreads();
         staged_end = k + cnt;
@@ -221,13 +225,14 @@ __global__ void __launch_bounds__(kThreads, 2)
           }
           __syncthreads();
           const V2 rv = *(const V2*)(rhs + 2 * lane);
+          const T* sg = (const T*)L.sgn + m.vec_off + (int64_t)i * NB;   // forward output is S L^{-1} b
 #pragma unroll
           for (int r = 0; r < 8; ++r) {
             const V2 a = *(const V2*)(tl + (warp + 8 * r) * NB + 2 * lane);
             T yv = a.x * rv.x + a.y * rv.y;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) yv += __shfl_xor_sync(0xffffffffu, yv, o);
-            if (lane == 0) v[i * NB + warp + 8 * r] = yv;
+            if (lane == 0) v[i * NB + warp + 8 * r] = yv * sg[warp + 8 * r];
           }
           if (lane == 0) __threadfence();
         } else {

@@ -1,6 +1,7 @@
 // Trailing update of the blocked Cholesky on the 5th-generation tensor cores (tcgen05), FP32
 // factors (mixed mode): for one super-panel of up to W = 4 tile columns q in [kb0, kb1),
-//     A(i, j) -= sum_q L(i, q) L(j, q)^T       for kb1 <= j < Bc, j <= i < R,
+//     A(i, j) -= sum_q L(i, q) S_q L(j, q)^T       for kb1 <= j < Bc, j <= i < R,
+// (S_q: pivot signs of the signed Cholesky, identity for SPD levels)
 // batched over all subdomains of a level.  This is the rank-256 update that follows the
 // factorisation of a 256-wide panel (Algorithm 1, "factorize the matrices of local saddle
 // point problems").
@@ -186,10 +187,17 @@ __global__ void __launch_bounds__(kThreads, 2)
   load_chunk(kb0);
   for (int q = kb0; q < qend; ++q) {
     if (q > kb0) promote();   // also frees the shared-memory stage and the accumulators
+    const float* sq = (const float*)L.sgn + m.vec_off + (int64_t)q * NB;   // pivot signs of column q
 #pragma unroll
     for (int u = 0; u < 12; ++u) {
       const int f = tid + 256 * (u & 3);        // float4 index inside the tile
       const int r = (f * 4) / NB, k = (f * 4) % NB;
+      if (u >= 8 && L.indefinite) {             // B = L(j,q) S_q
+        rg[u].x *= sq[k];
+        rg[u].y *= sq[k + 1];
+        rg[u].z *= sq[k + 2];
+        rg[u].w *= sq[k + 3];
+      }
       __nv_bfloat16 p0[4], p1[4], p2[4];
       split3(rg[u].x, p0[0], p1[0], p2[0]);
       split3(rg[u].y, p0[1], p1[1], p2[1]);

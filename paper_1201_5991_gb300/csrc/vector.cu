@@ -222,6 +222,99 @@ __global__ void k_put_indexed(double* __restrict__ u, const int64_t* __restrict_
   if (k < n) u[idx[k]] = v[k];
 }
 
+// BiCGstab (right preconditioned) device scalars; layout: 0 rho, 1 alpha, 2 omega, 3 rho_new,
+// 4 rh.v, 5 t.s, 6 t.t, 7 beta.  A zero denominator (breakdown) yields 0, which the host sees as
+// a stalled residual.
+__global__ void k_bicg_scalars(double* S, int stage) {
+  if (threadIdx.x != 0) return;
+  if (stage == 3) {          // start: rho = alpha = omega = 1
+    S[0] = S[1] = S[2] = 1.0;
+  } else if (stage == 0) {   // beta = (rho_new / rho) (alpha / omega)
+    S[7] = (S[0] != 0.0 && S[2] != 0.0) ? (S[3] / S[0]) * (S[1] / S[2]) : 0.0;
+    S[0] = S[3];
+  } else if (stage == 1) {   // alpha = rho / (rh . v)
+    S[1] = S[4] != 0.0 ? S[0] / S[4] : 0.0;
+  } else {                   // omega = (t . s) / (t . t)
+    S[2] = S[6] != 0.0 ? S[5] / S[6] : 0.0;
+  }
+}
+
+// p = r + beta (p - omega v)
+__global__ void k_bicg_p(double* __restrict__ p, const double* __restrict__ r, const double* __restrict__ v,
+                         const double* __restrict__ S, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = r[i] + S[7] * (p[i] - S[2] * v[i]);
+}
+
+// s = r - alpha v
+__global__ void k_bicg_s(double* __restrict__ sv, const double* __restrict__ r, const double* __restrict__ v,
+                         const double* __restrict__ S, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) sv[i] = r[i] - S[1] * v[i];
+}
+
+// x += alpha ph + omega sh ; r = s - omega t
+__global__ void k_bicg_xr(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ ph,
+                          const double* __restrict__ sh, const double* __restrict__ sv, const double* __restrict__ t,
+                          const double* __restrict__ S, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  x[i] += S[1] * ph[i] + S[2] * sh[i];
+  r[i] = sv[i] - S[2] * t[i];
+}
+
+// ---- flexible GMRES building blocks (fixed-order, reproducible) ----
+// partial[i * nblk + b] = sum over the grid-stride slice b of V_i . w, for i < nv (grid nblk x nv)
+__global__ void k_multidot_partial(const double* __restrict__ V, int64_t ldv, const double* __restrict__ w, int64_t n,
+                                   double* __restrict__ partial) {
+  __shared__ double red[256];
+  const double* v = V + (int64_t)blockIdx.y * ldv;
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s += v[i] * w[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = red[0];
+}
+
+// out[i] = sum_b partial[i * nblk + b]; one block per i
+__global__ void k_multidot_final(const double* __restrict__ partial, int nblk, double* __restrict__ out) {
+  __shared__ double red[256];
+  const double* p = partial + (int64_t)blockIdx.x * nblk;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nblk; i += 256) s += p[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = red[0];
+}
+
+// w += alpha sum_{i < nv} c_i V_i, i ascending
+__global__ void k_combine(double* __restrict__ w, const double* __restrict__ V, int64_t ldv, int nv,
+                          const double* __restrict__ c, double alpha, int64_t n) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  double acc = 0.0;
+  for (int i = 0; i < nv; ++i) acc += c[i] * V[(int64_t)i * ldv + k];
+  w[k] += alpha * acc;
+}
+
+// dst = src / sqrt(*nrm2) (dst = 0 when the norm vanishes: lucky breakdown)
+__global__ void k_scale_by_norm(double* __restrict__ dst, const double* __restrict__ src,
+                                const double* __restrict__ nrm2, int64_t n) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const double s = *nrm2 > 0.0 ? 1.0 / sqrt(*nrm2) : 0.0;
+  dst[k] = src[k] * s;
+}
+
 inline unsigned nblocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
@@ -300,6 +393,37 @@ void launch_iface_rhs(double* g, const double* f, const int64_t* idx, const doub
 }
 void launch_put_indexed(double* u, const int64_t* idx, const double* v, int64_t n, cudaStream_t st) {
   if (n > 0) { note_launch(); k_put_indexed<<<nblocks(n, 256), 256, 0, st>>>(u, idx, v, n); }
+}
+
+void launch_multidot(const double* V, int64_t ldv, int nv, const double* w, int64_t n, double* partial, int nblk,
+                     double* out, cudaStream_t st) {
+  if (nv <= 0) return;
+  note_launch();
+  k_multidot_partial<<<dim3(nblk, nv), 256, 0, st>>>(V, ldv, w, n, partial);
+  note_launch();
+  k_multidot_final<<<nv, 256, 0, st>>>(partial, nblk, out);
+}
+void launch_combine(double* w, const double* V, int64_t ldv, int nv, const double* c, double alpha, int64_t n,
+                    cudaStream_t st) {
+  if (n > 0 && nv > 0) { note_launch(); k_combine<<<nblocks(n, 256), 256, 0, st>>>(w, V, ldv, nv, c, alpha, n); }
+}
+void launch_scale_by_norm(double* dst, const double* src, const double* nrm2, int64_t n, cudaStream_t st) {
+  if (n > 0) { note_launch(); k_scale_by_norm<<<nblocks(n, 256), 256, 0, st>>>(dst, src, nrm2, n); }
+}
+
+void launch_bicg_scalars(double* S, int stage, cudaStream_t st) {
+  note_launch();
+  k_bicg_scalars<<<1, 32, 0, st>>>(S, stage);
+}
+void launch_bicg_p(double* p, const double* r, const double* v, const double* S, int64_t n, cudaStream_t st) {
+  if (n > 0) { note_launch(); k_bicg_p<<<nblocks(n, 256), 256, 0, st>>>(p, r, v, S, n); }
+}
+void launch_bicg_s(double* sv, const double* r, const double* v, const double* S, int64_t n, cudaStream_t st) {
+  if (n > 0) { note_launch(); k_bicg_s<<<nblocks(n, 256), 256, 0, st>>>(sv, r, v, S, n); }
+}
+void launch_bicg_xr(double* x, double* r, const double* ph, const double* sh, const double* sv, const double* t,
+                    const double* S, int64_t n, cudaStream_t st) {
+  if (n > 0) { note_launch(); k_bicg_xr<<<nblocks(n, 256), 256, 0, st>>>(x, r, ph, sh, sv, t, S, n); }
 }
 
 #define INST(T)                                                                             \

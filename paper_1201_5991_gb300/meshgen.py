@@ -330,6 +330,45 @@ def elasticity3d_kmeans(n: int, nsub: int, ngroup: int, seed: int, seed2: int, k
         n_levels=3, constraints=CORNERS | EDGES | FACES)
 
 
+def stokes_cavity(n: int, nsub: int, groups=(), lid=(1.0 / math.sqrt(3.0), math.sqrt(2.0 / 3.0), 0.0)) -> Problem:
+    """3D lid-driven cavity (Sec. 4): Taylor-Hood Q2-Q1 hexes n^3 on the unit cube, viscosity 1,
+    zero velocity on every face except z = 1, where the lid velocity is prescribed on all its
+    nodes (its edges included), no body force; nsub^3 cubic subdomains.
+
+    Every lattice node has 4 DOF slots (u, v, w, p); the pressure slots of nodes that are not
+    element vertices do not exist and are masked as prescribed (value 0); the pressure at node 0
+    is pinned to 0 to remove the constant.  ``groups`` lists the level groupings (g -> g^3
+    subdomains of the previous level per subdomain of the next).
+    """
+    coords, conn = box_mesh_q2(n)
+    m = 2 * n + 1
+    nn = coords.shape[0]
+    iz, iy, ix = np.meshgrid(np.arange(m), np.arange(m), np.arange(m), indexing="ij")
+    ix, iy, iz = ix.ravel(), iy.ravel(), iz.ravel()
+    vertex = (ix % 2 == 0) & (iy % 2 == 0) & (iz % 2 == 0)
+    bnd = (ix == 0) | (ix == m - 1) | (iy == 0) | (iy == m - 1) | (iz == 0) | (iz == m - 1)
+    top = iz == m - 1
+    dirichlet = np.zeros(nn * 4, dtype=np.uint8)
+    values = np.zeros(nn * 4)
+    for c in range(3):
+        dirichlet[np.nonzero(bnd)[0] * 4 + c] = 1
+        values[np.nonzero(top)[0] * 4 + c] = lid[c]
+    dirichlet[np.nonzero(~vertex)[0] * 4 + 3] = 1
+    dirichlet[3] = 1
+    parts = [cubic_partition(3, n, nsub)]
+    n_parts = [nsub ** 3]
+    cur = nsub
+    for g in groups:
+        parts.append(block_grouping(3, cur, g))
+        cur //= g
+        n_parts.append(cur ** 3)
+    return Problem(
+        name=f"stokes_cavity_{n}_{nsub}", dim=3, nodes_per_elem=27, dofs_per_node=4, physics=STOKES,
+        coords=coords, conn=conn, coef=np.ones(conn.shape[0]), nu=1.0, dirichlet=dirichlet,
+        f_full=np.zeros((nn * 4, 1)), parts=parts, n_parts=n_parts, n_levels=len(parts) + 1,
+        constraints=CORNERS | EDGES | FACES, dir_values=values)
+
+
 def config(name: str) -> Problem:
     """The named workloads: the paper's problem classes (Sec. 4) at synthetic sizes."""
     if name == "poisson2d_32":
@@ -342,4 +381,10 @@ def config(name: str) -> Problem:
         return elasticity3d_kmeans(96, 512, 8, seed=3, seed2=33, kmeans_iters=20)
     if name == "elasticity3d_64_16rhs":
         return elasticity3d(64, 8, seed=5, nrhs=16)
+    if name == "stokes_cavity_32":             # 512 subdomains of 4^3, two levels
+        return stokes_cavity(32, 8)
+    if name == "stokes_cavity_32_3lev":        # 512 / 64 / 1
+        return stokes_cavity(32, 8, groups=(2,))
+    if name == "stokes_cavity_32_4lev":        # 512 / 64 / 8 / 1
+        return stokes_cavity(32, 8, groups=(2, 2))
     raise KeyError(name)

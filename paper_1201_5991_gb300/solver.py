@@ -21,15 +21,17 @@ class _HostMesh:
     """Keeps the host arrays of a mesh / partition alive while the C structs point at them."""
 
     def __init__(self, dim, nodes_per_elem, dofs_per_node, physics, coords, conn, coef, nu, dirichlet, parts,
-                 n_parts, n_levels):
+                 n_parts, n_levels, dir_values=None):
         self.coords = np.ascontiguousarray(coords, dtype=np.float64)
         self.conn = np.ascontiguousarray(conn, dtype=np.int32)
         self.coef = np.ascontiguousarray(coef, dtype=np.float64)
         self.dirichlet = np.ascontiguousarray(dirichlet, dtype=np.uint8)
+        self.dir_values = None if dir_values is None else np.ascontiguousarray(dir_values, dtype=np.float64)
         self.parts = [np.ascontiguousarray(p, dtype=np.int32) for p in parts]
+        dv = _ptr(self.dir_values, C.c_double) if self.dir_values is not None else None
         self.mesh = capi.Mesh(dim, nodes_per_elem, dofs_per_node, physics, self.coords.shape[0], self.conn.shape[0],
                               _ptr(self.coords, C.c_double), _ptr(self.conn, C.c_int32), _ptr(self.coef, C.c_double),
-                              float(nu), _ptr(self.dirichlet, C.c_uint8))
+                              float(nu), _ptr(self.dirichlet, C.c_uint8), dv)
         self.part = capi.Partition()
         self.part.n_levels = int(n_levels)
         for l, p in enumerate(self.parts):
@@ -40,11 +42,12 @@ class _HostMesh:
 def host_mesh(prob, n_levels: Optional[int] = None) -> _HostMesh:
     L = int(n_levels or prob.n_levels)
     return _HostMesh(prob.dim, prob.nodes_per_elem, prob.dofs_per_node, prob.physics, prob.coords, prob.conn,
-                     prob.coef, prob.nu, prob.dirichlet, prob.parts[:L - 1], prob.n_parts[:L - 1], L)
+                     prob.coef, prob.nu, prob.dirichlet, prob.parts[:L - 1], prob.n_parts[:L - 1], L,
+                     getattr(prob, "dir_values", None))
 
 
 def make_opts(precision="mixed", weights="stiffness", all_corners=0, maxit=500, refine_steps=0, flexible=-1,
-              use_graph=1, profile=0, tensor_cores=1) -> capi.Opts:
+              use_graph=1, profile=0, tensor_cores=1, krylov=0) -> capi.Opts:
     o = capi.Opts()
     capi.lib().bddc_default_opts(C.byref(o))
     o.precision = capi.PREC_MIXED if precision == "mixed" else capi.PREC_FP64
@@ -56,6 +59,7 @@ def make_opts(precision="mixed", weights="stiffness", all_corners=0, maxit=500, 
     o.use_graph = int(use_graph)
     o.profile = int(profile)
     o.tensor_cores = int(tensor_cores)
+    o.krylov = int(krylov)
     return o
 
 

@@ -79,6 +79,8 @@ CASES = {
     "elast8_3lev": (lambda: meshgen.elasticity3d(8, 4, seed=0, group=2), 3),
     "elast6_corners": (lambda: meshgen.elasticity3d(6, 2, seed=1, constraints=meshgen.CORNERS), 2),
     "kmeans_small": (lambda: meshgen.elasticity3d_kmeans(12, 24, 3, seed=3, seed2=33), 3),
+    "stokes6": (lambda: meshgen.stokes_cavity(6, 3), 2),              # velocities before pressures
+    "stokes8_3lev": (lambda: meshgen.stokes_cavity(8, 4, (2,)), 3),
 }
 
 
@@ -120,6 +122,30 @@ def test_invalid_partition_is_rejected():
     assert ei.value.code == capi.ERR_INVALID
     p = meshgen.poisson2d(8, 2)
     p.n_parts = [5]                          # subdomain 4 is empty
+    with pytest.raises(capi.BddcError) as ei:
+        solver.analyze(p)
+    assert ei.value.code == capi.ERR_INVALID
+
+
+def test_stokes_local_order_puts_pressures_last():
+    p = meshgen.stokes_cavity(6, 3)
+    lib = solver.analyze(p)[0]
+    full = np.nonzero(p.free)[0]
+    comp = full % 4
+    sp = lib["sub_dof_ptr"]
+    for s in range(lib["n_sub"]):
+        nI = lib["sub_nI"][s]
+        dofs = lib["sub_dofs"][sp[s]:sp[s + 1]]
+        for seg in (dofs[:nI], dofs[nI:]):
+            c = comp[seg]
+            k = np.argmax(c == 3) if np.any(c == 3) else c.size
+            assert np.all(c[:k] < 3) and np.all(c[k:] == 3)
+
+
+def test_stokes_mesh_validation():
+    p = meshgen.stokes_cavity(2, 1)
+    p.nodes_per_elem = 8
+    p.conn = p.conn[:, :8]
     with pytest.raises(capi.BddcError) as ei:
         solver.analyze(p)
     assert ei.value.code == capi.ERR_INVALID

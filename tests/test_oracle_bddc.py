@@ -4,7 +4,7 @@ import pytest
 import scipy.sparse.linalg as spla
 
 from oracle import fem, maps
-from oracle.bddc import Bddc, lanczos_extremes, pcg
+from oracle.bddc import Bddc, bicgstab, fgmres, lanczos_extremes, pcg
 from paper_1201_5991_gb300 import meshgen
 
 SMALL = {
@@ -161,9 +161,88 @@ def test_planted_dropped_coarse_term_is_caught():
     p = SMALL["elast"]()
     b = Bddc(p)
     n = b.KC.shape[0]
-    b.KC_chol = (np.eye(n) * 1e30, True)
+    b.KC_chol = (np.eye(n) * 1e30, np.arange(n))
     E = np.eye(b.n_iface)
     S = np.stack([b.schur(e) for e in E], axis=1)
     M = np.stack([b.precond(e) for e in E], axis=1)
     ev = np.sort(np.linalg.eigvals(M @ S).real)
     assert ev[0] < 0.5
+
+
+# ---------------------------------------------------------------- Stokes (indefinite, Sec. 4)
+def test_bicgstab_solves_a_nonsymmetric_system():
+    # right-preconditioned BiCGstab against a dense LAPACK solve, with a diagonal preconditioner
+    rng = np.random.default_rng(5)
+    n = 60
+    A = np.eye(n) * 4.0 + rng.standard_normal((n, n)) / np.sqrt(n)
+    b = rng.standard_normal(n)
+    d = np.diag(A).copy()
+    x, info = bicgstab(lambda v: A @ v, lambda v: v / d, b, 1e-13, 200)
+    assert info.converged
+    np.testing.assert_allclose(x, np.linalg.solve(A, b), rtol=0, atol=1e-11)
+
+
+def test_fgmres_with_a_changing_preconditioner():
+    # a preconditioner that differs on every call (a few Jacobi sweeps with a call-dependent
+    # count) is allowed in flexible GMRES; the answer must still be LAPACK's
+    rng = np.random.default_rng(6)
+    n = 80
+    A = np.eye(n) * 3.0 + rng.standard_normal((n, n)) / np.sqrt(n)
+    b = rng.standard_normal(n)
+    d = np.diag(A).copy()
+    calls = [0]
+
+    def M(v):
+        calls[0] += 1
+        z = v / d
+        for _ in range(calls[0] % 3):
+            z = z + (v - A @ z) / d
+        return z
+
+    x, info = fgmres(lambda v: A @ v, M, b, 1e-12, 300, restart=10)
+    assert info.converged and calls[0] > 10       # restarted at least once
+    np.testing.assert_allclose(x, np.linalg.solve(A, b), rtol=0, atol=1e-10)
+
+
+def test_stokes_fgmres_matches_direct_solve():
+    p = meshgen.stokes_cavity(4, 2)
+    _, feff = fem.free_system(p)
+    u_ref = fem.direct_solve(p)[:, 0]
+    u, info = Bddc(p).solve(feff[:, 0], tol=1e-13, maxit=200, krylov="fgmres")
+    assert info[0].converged
+    assert np.abs(u - u_ref).max() < 1e-8 * np.abs(u_ref).max()
+
+
+STOKES = {
+    "two_level": lambda: meshgen.stokes_cavity(4, 2),
+    "two_level_27": lambda: meshgen.stokes_cavity(6, 3),
+    "three_level": lambda: meshgen.stokes_cavity(8, 4, (2,)),
+}
+
+
+@pytest.mark.parametrize("name", list(STOKES))
+def test_stokes_bicgstab_matches_direct_solve(name):
+    # the lid-driven cavity: prescribed lid velocities are lifted to the right-hand side
+    p = STOKES[name]()
+    _, feff = fem.free_system(p)
+    u_ref = fem.direct_solve(p)[:, 0]
+    u, info = Bddc(p).solve(feff[:, 0], tol=1e-13, maxit=200)
+    assert info[0].converged
+    assert np.abs(u - u_ref).max() < 1e-8 * np.abs(u_ref).max()
+    # the discrete velocity is divergence free: the pressure rows of K_ff u = f hold
+    Kff, _ = fem.free_system(p)
+    full = np.nonzero(p.free)[0]
+    isp = (full % p.dofs_per_node) == 3
+    res = (Kff @ u - feff[:, 0])[isp]
+    assert np.abs(res).max() < 1e-9 * np.abs(feff).max()
+
+
+def test_stokes_weights_are_a_partition_of_unity():
+    # pressure interface DOFs have a zero diagonal: their weights fall back to multiplicity
+    p = STOKES["two_level_27"]()
+    b = Bddc(p)
+    m = b.l1.maps
+    acc = np.zeros(m.iface_dofs.size)
+    for s in range(len(m.sub_dofs)):
+        np.add.at(acc, m.sub_iface[s], b.l1.w[s])
+    np.testing.assert_allclose(acc, 1.0, rtol=0, atol=1e-14)

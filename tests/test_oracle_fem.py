@@ -95,3 +95,77 @@ def test_body_load_sums_to_total_force():
     p = meshgen.elasticity3d(6, 2, seed=0)
     tot = p.f_full[:, 0].reshape(-1, 3).sum(axis=0)
     np.testing.assert_allclose(tot, [0, 0, -1.0], atol=1e-14)   # unit cube, b = (0,0,-1)
+
+
+# ---------------------------------------------------------------- Taylor-Hood Q2-Q1 (Stokes)
+def _q2_hex(a=1.0, b=1.0, c=1.0):
+    # 27 nodes, local a = ix + 3 iy + 9 iz at (ix a/2, iy b/2, iz c/2)
+    return np.array([[ix * a / 2, iy * b / 2, iz * c / 2]
+                     for iz in range(3) for iy in range(3) for ix in range(3)], float)
+
+
+def _vel(X, fn):
+    """Velocity slots (4a + c, c < 3) filled with fn(x) = (u, v, w); pressure slots 0."""
+    u = np.zeros(108)
+    for a in range(27):
+        u[4 * a:4 * a + 3] = fn(X[a])
+    return u
+
+
+def test_q2q1_stokes_structure_and_null_spaces():
+    X = _q2_hex(0.5, 1.0, 2.0)
+    K = fem.element_stokes(X, 1.0)
+    assert np.allclose(K, K.T, atol=1e-14)
+    vert = [0, 2, 6, 8, 18, 20, 24, 26]
+    pres = [4 * a + 3 for a in range(27)]
+    nonvert = [4 * a + 3 for a in range(27) if a not in vert]
+    assert np.all(K[nonvert] == 0.0) and np.all(K[:, nonvert] == 0.0)
+    assert np.all(K[np.ix_(pres, pres)] == 0.0)           # no pressure-pressure block
+    # constant velocities lie in the null space of the viscous block and are divergence free
+    for t in np.eye(3):
+        assert np.abs(K @ _vel(X, lambda x: t)).max() < 1e-13
+    # a constant pressure only sees the boundary: B^T 1 = -int grad phi_b, whose sum over the
+    # (partition-of-unity) velocity basis vanishes
+    p1 = np.zeros(108)
+    p1[[4 * a + 3 for a in vert]] = 1.0
+    f = K @ p1
+    for j in range(3):
+        assert abs(f[j::4][:27].sum()) < 1e-13
+
+
+def test_q2q1_stokes_closed_forms_on_a_box():
+    a, b, c = 0.5, 1.0, 2.0
+    X = _q2_hex(a, b, c)
+    K = fem.element_stokes(X, 1.0)
+    vol = a * b * c
+    vert = [0, 2, 6, 8, 18, 20, 24, 26]
+    # viscous energy of u = (y, 0, 0): int |grad u|^2 = vol
+    u = _vel(X, lambda x: (x[1], 0.0, 0.0))
+    assert abs(u @ K @ u - vol) < 1e-13
+    # u = (x^2, 0, 0) is exact in Q2: int |grad u|^2 = int 4 x^2 = 4 a^3 b c / 3
+    u = _vel(X, lambda x: (x[0] ** 2, 0.0, 0.0))
+    assert abs(u @ K @ u - 4.0 * a ** 3 * b * c / 3.0) < 1e-13
+    # divergence rows: (B u)_p = -int psi_p div u.  div (x, 0, 0) = 1: -vol / 8 at every vertex
+    Bu = (K @ _vel(X, lambda x: (x[0], 0.0, 0.0)))[[4 * v + 3 for v in vert]]
+    np.testing.assert_allclose(Bu, -vol / 8.0, rtol=0, atol=1e-14)
+    # div (0, 0, z^2) = 2z: -int psi_p 2 z = -(a/2)(b/2) 2 int_0^c z l(z) dz with l = 1 - z/c or z/c
+    Bu = (K @ _vel(X, lambda x: (0.0, 0.0, x[2] ** 2)))[[4 * v + 3 for v in vert]]
+    lo = -(a / 2) * (b / 2) * 2 * (c ** 2 / 6.0)
+    hi = -(a / 2) * (b / 2) * 2 * (c ** 2 / 3.0)
+    np.testing.assert_allclose(Bu, [lo] * 4 + [hi] * 4, rtol=0, atol=1e-14)
+
+
+def test_q2q1_stokes_inf_sup_on_two_elements():
+    # the assembled pressure Schur complement B A^{-1} B^T of a small Dirichlet cavity is
+    # positive definite on the pressures once one pressure is pinned (Taylor-Hood is stable)
+    prob = meshgen.stokes_cavity(2, 1)
+    Kff, _ = fem.free_system(prob)
+    Kff = Kff.toarray()
+    ndof = prob.dofs_per_node
+    full = np.nonzero(prob.free)[0]
+    isp = (full % ndof) == 3
+    A = Kff[np.ix_(~isp, ~isp)]
+    B = Kff[np.ix_(isp, ~isp)]
+    assert np.linalg.eigvalsh(A).min() > 0
+    ev = np.linalg.eigvalsh(B @ np.linalg.solve(A, B.T))
+    assert ev.min() > 1e-6 * ev.max()
