@@ -37,6 +37,13 @@ WORKLOADS = {
                        "corners+edges+faces, two-level BDDC, PCG to 1e-8",
     "elasticity3d_24": "3D elasticity, 24^3 Q1 hexes, 8 cubic subdomains of 12^3 (profiling case), "
                        "corners+edges+faces, two-level BDDC, PCG to 1e-8",
+    "stokes_cavity_32": "3D lid-driven cavity Stokes, 32^3 Taylor-Hood Q2-Q1 hexes, 786,077 free DOFs, "
+                        "512 cubic subdomains of 4^3, corners+edges+faces, two-level BDDC, "
+                        "FGMRES (mixed) / BiCGstab (FP64) to 1e-8",
+    "stokes_cavity_32_3lev": "3D lid-driven cavity Stokes, 32^3 Q2-Q1, 512/64/1 subdomains, three-level BDDC, "
+                             "FGMRES (mixed) / BiCGstab (FP64) to 1e-8",
+    "stokes_cavity_32_4lev": "3D lid-driven cavity Stokes, 32^3 Q2-Q1, 512/64/8/1 subdomains, four-level BDDC, "
+                             "FGMRES (mixed) / BiCGstab (FP64) to 1e-8",
 }
 WORKLOAD = "elasticity3d_48"
 TOL = 1e-8
@@ -175,7 +182,7 @@ def oracle_sample(prob, iterations: int):
         Ks = K[k]
         C = mp.sub_C[s]
         n, nc = Ks.shape[0], C.shape[0]
-        kii = sla.cho_factor(Ks[:nI, :nI], lower=True)
+        kii = sla.lu_factor(Ks[:nI, :nI]) if prob.physics == 2 else sla.cho_factor(Ks[:nI, :nI], lower=True)
         Sd = np.zeros((n + nc, n + nc))
         Sd[:n, :n] = Ks
         Sd[:n, n:] = C.T
@@ -189,18 +196,19 @@ def oracle_sample(prob, iterations: int):
     t2 = time.perf_counter()
     for kii, lu, Ks, nI, n, nc in facts:
         x = np.ones(n - nI)
-        w = sla.cho_solve(kii, Ks[:nI, nI:] @ x)
+        w = sla.lu_solve(kii, Ks[:nI, nI:] @ x) if prob.physics == 2 else sla.cho_solve(kii, Ks[:nI, nI:] @ x)
         _ = Ks[nI:, nI:] @ x - Ks[nI:, :nI] @ w
         r = np.zeros(n + nc)
         r[nI:n] = 1.0
         sla.lu_solve(lu, r)
     t_iter = (time.perf_counter() - t2) / len(sample)
     ns = prob.n_parts[0]
-    est = t_analysis + ns * t_setup + iterations * ns * t_iter
+    per_it = 2 if prob.physics == 2 else 1   # BiCGstab: two operator and preconditioner applications
+    est = t_analysis + ns * t_setup + per_it * iterations * ns * t_iter
     sample_s = time.perf_counter() - t0
     desc = (f"index analysis of all {ns} subdomains + set-up of {len(sample)} of {ns} subdomains + one "
             f"iteration's subdomain solves for the same {len(sample)}, extrapolated to {ns} subdomains x "
-            f"{iterations} PCG iterations ({sample_s:.1f} s of CPU work)")
+            f"{iterations} Krylov iterations x {per_it} applications ({sample_s:.1f} s of CPU work)")
     return est, desc
 
 
@@ -347,9 +355,12 @@ def run_gpu(args, rank, world, local_rank):
         "iterations": st0.iterations,
         "rel_residual": st0.rel_residual,
         "setup_ms": st0.analysis_ms + st0.factor_ms,
+        "analysis_ms": st0.analysis_ms,
+        "factor_ms": st0.factor_ms,
         "solve_ms": st0.solve_ms,
         "refine_steps": st0.refine_steps,
-        "kappa_estimate": st0.lambda_max / st0.lambda_min if st0.lambda_min > 0 else None,
+        "kappa_estimate": (st0.lambda_max / st0.lambda_min if st0.lambda_min > 0 and prob.physics != 2
+                           else None),
         "plain_fp64": None if st64 is None else {
             "value": prob.n_free * world / (ms64 * 1e-3), "ms_per_step": ms64, "steps": pk,
             "iterations": st64.iterations, "setup_ms": st64.analysis_ms + st64.factor_ms,

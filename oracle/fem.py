@@ -182,6 +182,35 @@ def element_matrices(prob) -> np.ndarray:
     return unit[inv] * prob.coef[:, None, None]
 
 
+def apply_K(prob, u_full: np.ndarray, chunk: int = 4096) -> np.ndarray:
+    """K u over all DOFs without forming K: sum_e P_e^T (coef_e K_e^unit) P_e u, elements with
+    identical geometry sharing one unit matrix (as in element_matrices).  For meshes too large
+    for the assembled matrix; u_full is [n_nodes * ndof] or [n_nodes * ndof, k]."""
+    X = prob.coords[prob.conn]
+    shape_key = np.round(X - X[:, :1, :], 14).reshape(X.shape[0], -1)
+    uniq, inv = np.unique(shape_key, axis=0, return_inverse=True)
+    inv = inv.ravel()
+    ed = element_dofs(prob)
+    U = u_full if u_full.ndim == 2 else u_full[:, None]
+    out = np.zeros_like(U)
+    for u in range(uniq.shape[0]):
+        els = np.nonzero(inv == u)[0]
+        e0 = int(els[0])
+        if prob.physics == 0:
+            K1 = element_laplace(X[e0], 1.0)
+        elif prob.physics == 1:
+            K1 = element_elasticity(X[e0], 1.0, prob.nu)
+        else:
+            K1 = element_stokes(X[e0], 1.0)
+        for c0 in range(0, els.size, chunk):
+            ec = els[c0:c0 + chunk]
+            ue = U[ed[ec]]                                   # [ne_chunk, ne, k]
+            ye = np.einsum("ab,ebk->eak", K1, ue) * prob.coef[ec][:, None, None]
+            for k in range(U.shape[1]):
+                out[:, k] += np.bincount(ed[ec].ravel(), weights=ye[:, :, k].ravel(), minlength=U.shape[0])
+    return out if u_full.ndim == 2 else out[:, 0]
+
+
 def element_dofs(prob) -> np.ndarray:
     """Global DOF ids (node * ndof + comp) of every element, [n_elems, nn * ndof]."""
     nd = prob.dofs_per_node

@@ -92,6 +92,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   __shared__ __align__(16) T ybuf[kYSlots][NB];
   __shared__ T red[kThreads / 32][NB];
   __shared__ __align__(16) T rhs[NB];
+  __shared__ T s_sg[NB];                         // pivot signs of the task's block row (indefinite)
   __shared__ int s_task, s_ready;
   int* counter = ctrl;
   int* flags = ctrl + 1;
@@ -112,6 +113,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     if (t >= ntasks) break;
     const int sub = tasks[t].x, i = tasks[t].y;
     const SubMeta m = L.meta[sub];
+    if (!BWD && L.indefinite && tid < NB) s_sg[tid] = ((const T*)L.sgn)[m.vec_off + (int64_t)i * NB + tid];
     const int B0 = part == 0 ? 0 : m.nIb, B1 = part == 0 ? m.nIb : m.Bc;
     const int nL = BWD ? (B1 - 1 - i) : (i - B0);   // factor tiles before D_i^{-1}
     const int ntile = nL + 1;
@@ -225,14 +227,14 @@ __global__ void __launch_bounds__(kThreads, 2)
           }
           __syncthreads();
           const V2 rv = *(const V2*)(rhs + 2 * lane);
-          const T* sg = (const T*)L.sgn + m.vec_off + (int64_t)i * NB;   // forward output is S L^{-1} b
+          const bool signed_rows = L.indefinite != 0;   // forward output is S L^{-1} b
 #pragma unroll
           for (int r = 0; r < 8; ++r) {
             const V2 a = *(const V2*)(tl + (warp + 8 * r) * NB + 2 * lane);
             T yv = a.x * rv.x + a.y * rv.y;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) yv += __shfl_xor_sync(0xffffffffu, yv, o);
-            if (lane == 0) v[i * NB + warp + 8 * r] = yv * sg[warp + 8 * r];
+            if (lane == 0) v[i * NB + warp + 8 * r] = signed_rows ? yv * s_sg[warp + 8 * r] : yv;
           }
           if (lane == 0) __threadfence();
         } else {

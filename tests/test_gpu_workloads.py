@@ -104,3 +104,27 @@ def test_adjoint_gradient_64_16_load_cases():
         fd = -float(np.einsum("ak,ab,bk->", up, k_e, um))
         g2 = -float(np.einsum("ak,ab,bk->", ue[list(sample).index(e)][:, :2], k_e, ue[list(sample).index(e)][:, :2]))
         assert abs(fd - g2) <= 1e-5 * abs(g2)
+
+
+def _stokes_residual(p, u):
+    """f_f - K_ff u_f - K_fd u_d over the free DOFs, by the oracle's matrix-free product."""
+    full = np.array(p.dir_values, dtype=np.float64)
+    full[p.free] = u
+    return (p.f_full[:, 0] - fem.apply_K(p, full))[p.free]
+
+
+@pytest.mark.parametrize("name", ["stokes_cavity_32", "stokes_cavity_32_3lev", "stokes_cavity_32_4lev"])
+def test_stokes_cavity32_full_size(name):
+    # 32^3 Taylor-Hood cavity, 512 subdomains of 4^3, 2 / 3 / 4 levels, mixed precision
+    # (FGMRES outer iteration): the oracle's FP64 residual of the full system must meet the
+    # stopping test and match the library's true interface residual
+    p = meshgen.config(name)
+    s = BddcSolver(p, precision="mixed")
+    u = s.solve(_dev(p.f[:, 0]), tol=1e-8).cpu().numpy()
+    st = s.last_stats
+    assert st.converged == 1 and st.n_levels == p.n_levels
+    r = np.linalg.norm(_stokes_residual(p, u))
+    assert r <= 1e-8 * st.rhs_norm * 1.0001
+    assert abs(r - st.rel_residual * st.rhs_norm) <= 0.02 * r + 1e-13 * st.rhs_norm
+    # the lid drives a circulation: the velocity field is not trivial
+    assert np.abs(u).max() > 0.1

@@ -169,3 +169,11 @@ def test_q2q1_stokes_inf_sup_on_two_elements():
     assert np.linalg.eigvalsh(A).min() > 0
     ev = np.linalg.eigvalsh(B @ np.linalg.solve(A, B.T))
     assert ev.min() > 1e-6 * ev.max()
+
+
+@pytest.mark.parametrize("mk", [lambda: meshgen.stokes_cavity(3, 1), lambda: meshgen.elasticity3d(4, 2, seed=3),
+                                lambda: meshgen.poisson2d(8, 2)])
+def test_matrix_free_apply_equals_assembled_product(mk):
+    p = mk()
+    u = np.random.default_rng(2).standard_normal(p.n_nodes * p.dofs_per_node)
+    np.testing.assert_allclose(fem.apply_K(p, u, chunk=7), fem.assemble(p) @ u, rtol=0, atol=1e-12)
