@@ -132,16 +132,19 @@ class ClockSampler:
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def traffic_ratio():
-    """DRAM bytes / algorithmic bytes of the streaming sweep from the committed ncu summary
-    (profiles/trsv_sweep_traffic.json), or None when the kernel source changed since the
-    counters were taken."""
-    path = os.path.join(ROOT, "profiles", "trsv_sweep_traffic.json")
+def traffic_ratio(cls):
+    """DRAM bytes / algorithmic bytes of the roofline kernel class from the committed ncu summary
+    (profiles/trsv_sweep_traffic.json for the sweeps, profiles/trmv_schur_traffic.json for the
+    factor products), or None when the kernel source changed since the counters were taken."""
+    from paper_1201_5991_gb300 import capi
+    fname, src_name = (("trsv_sweep_traffic.json", "sweep.cu") if cls == capi.PROF_TRSV
+                       else ("trmv_schur_traffic.json", "trmv.cu"))
+    path = os.path.join(ROOT, "profiles", fname)
     try:
         with open(path) as fh:
             rec = json.load(fh)
-        src = open(os.path.join(ROOT, "paper_1201_5991_gb300", "csrc", "sweep.cu"), "rb").read()
-        if hashlib.sha256(src).hexdigest() != rec.get("sweep_cu_sha256"):
+        src = open(os.path.join(ROOT, "paper_1201_5991_gb300", "csrc", src_name), "rb").read()
+        if hashlib.sha256(src).hexdigest() != rec.get("source_sha256", rec.get("sweep_cu_sha256")):
             return None
         return float(rec["traffic_over_algorithmic"])
     except Exception:
@@ -253,6 +256,7 @@ def run_gpu(args, rank, world, local_rank):
         times, stats = [], []
         launches0 = L.bddc_kernel_launches()
         prof = [0.0, 0, 0.0]
+        cls = {c: [0.0, 0, 0.0, 0.0] for c in (capi.PROF_TRSV, capi.PROF_FACTOR, capi.PROF_SPMV, capi.PROF_TRMV)}
         for _ in range(steps):
             flush.fill_(1.0)
             torch.cuda.synchronize()
@@ -265,11 +269,16 @@ def run_gpu(args, rank, world, local_rank):
             times.append(e0.elapsed_time(e1))
             st = s.stats()
             stats.append(st)
-            prof[0] += st.prof_ms[capi.PROF_TRSV]
-            prof[1] += st.prof_launches[capi.PROF_TRSV]
-            prof[2] += st.prof_bytes[capi.PROF_TRSV]
+            for c, acc in cls.items():
+                acc[0] += st.prof_ms[c]
+                acc[1] += st.prof_launches[c]
+                acc[2] += st.prof_bytes[c]
+                acc[3] += st.prof_flops[c]
             del s, u
         launches = (L.bddc_kernel_launches() - launches0) / max(steps, 1)
+        # the roofline kernel: the streaming kernel class with the largest share of the step
+        dom = max((capi.PROF_TRSV, capi.PROF_TRMV), key=lambda c: cls[c][0])
+        prof = [cls[dom][0], cls[dom][1], cls[dom][2], dom, cls]
         torch.cuda.synchronize()
         barrier()
         clk = sampler.stop() if sampler else None
@@ -312,10 +321,28 @@ def run_gpu(args, rank, world, local_rank):
 
     hbm, _, peak_kind = load_peaks()
     achieved = prof[2] / (prof[0] * 1e-3) / 1e9 if prof[0] > 0 else 0.0
-    ratio = traffic_ratio()
+    dom, cls = prof[3], prof[4]
+    ratio = traffic_ratio(dom)
     traffic = ratio * prof[2] / max(prof[1], 1) if ratio is not None else None
+    names = {capi.PROF_TRSV: "k_sweep<float> forward/backward (streaming triangular sweeps, TMA-staged tiles)",
+             capi.PROF_TRMV: "k_trmv_t + k_trmv_n (inner Schur operator: products with the stored interface factor)",
+             capi.PROF_SPMV: "k_spmv (FP64 CSR products with K_i)",
+             capi.PROF_FACTOR: "batched tiled factorisation (k_potrf_diag, k_trsm_panel, k_update_tc)"}
+    kernel_classes = {}
+    for c, (cms, cl, cb, cf) in cls.items():
+        if cl == 0:
+            continue
+        e = {"kernel": names[c], "ms_per_step": round(cms / args.steps, 3), "launches_per_step": cl / args.steps,
+             "share_of_step": round(cms / args.steps / ms, 4) if ms > 0 else None}
+        if cb > 0:
+            e["achieved_GBps"] = round(cb / (cms * 1e-3) / 1e9, 1)
+            e["frac_of_hbm"] = round(cb / (cms * 1e-3) / 1e9 / hbm, 4)
+        if cf > 0:
+            e["achieved_TFLOPs_fp32"] = round(cf / (cms * 1e-3) / 1e12, 2)
+        kernel_classes[{capi.PROF_TRSV: "trsv", capi.PROF_TRMV: "trmv", capi.PROF_SPMV: "spmv",
+                        capi.PROF_FACTOR: "factor"}[c]] = e
     roofline = {
-        "kernel": "k_sweep<float> forward/backward (streaming triangular sweeps, TMA-staged tiles)",
+        "kernel": names[dom],
         "bound": "hbm",
         "achieved": round(achieved, 1),
         "peak": hbm,
@@ -327,6 +354,7 @@ def run_gpu(args, rank, world, local_rank):
         "algorithmic_bytes_per_launch": prof[2] / max(prof[1], 1),
         "avg_launch_ms": prof[0] / max(prof[1], 1),
         "share_of_step": round(prof[0] / args.steps / ms, 4) if ms > 0 else None,
+        "classes": kernel_classes,
     }
 
     if rank != 0:
@@ -359,6 +387,8 @@ def run_gpu(args, rank, world, local_rank):
         "factor_ms": st0.factor_ms,
         "solve_ms": st0.solve_ms,
         "refine_steps": st0.refine_steps,
+        "inner_steps": st0.inner_steps,
+        "outer_iterations": st0.outer_iterations,
         "kappa_estimate": (st0.lambda_max / st0.lambda_min if st0.lambda_min > 0 and prob.physics != 2
                            else None),
         "plain_fp64": None if st64 is None else {

@@ -107,6 +107,13 @@ typedef struct {
   int profile;              /* 1: time kernel classes with CUDA events (bddc_stats.prof_*) */
   int tensor_cores;         /* mixed: 1 = FP32 trailing updates on tcgen05 tensor cores (3xBF16 split,
                                256-wide panels); 0 = FP32 CUDA cores */
+  int inner_steps;          /* mixed PCG: FP64 outer refinement x += S~^{-1}(g - S x) (residual with the
+                               FP64 operator S) around an inner PCG with a cheaper operator S~:
+                               0 = S~ from the stored interface factor (L_GG S L_GG^T - C^T R C, no
+                               interior solve), k >= 1 = S with k interior-solve steps,
+                               -1 = no outer loop (every PCG iteration applies the FP64 operator) */
+  double inner_tol;         /* first inner residual reduction of the outer refinement (later ones adapt to
+                               the observed outer reduction); 0 = automatic (1e-2) */
   int krylov;               /* BDDC_KRYLOV_*; 0 = automatic: PCG for the SPD problems; for Stokes
                                BiCGstab (FP64) or flexible GMRES (mixed: FP32 factors of the
                                saddle points make the preconditioner inexact beyond what
@@ -122,6 +129,7 @@ typedef struct {
 #define BDDC_PROF_TRSV 0    /* streaming triangular sweeps (Schur operator and preconditioner) */
 #define BDDC_PROF_FACTOR 1  /* one step of the batched blocked Cholesky (diagonal, panel, update) */
 #define BDDC_PROF_SPMV 2    /* FP64 sparse products with K_i */
+#define BDDC_PROF_TRMV 3    /* inner Schur operator: products with the stored interface factor */
 #define BDDC_PROF_CLASSES 4
 
 typedef struct {
@@ -138,6 +146,8 @@ typedef struct {
   int64_t n_promoted[BDDC_MAX_LEVELS];/* corners added by the rigid-body test */
   int breakdown_level, breakdown_sub; /* set with BDDC_ERR_BREAKDOWN */
   int refine_steps;                   /* refinement steps in use (mixed) */
+  int inner_steps;                    /* inner operator in use: -1 none, 0 factor products, k steps */
+  int outer_iterations;               /* FP64 outer refinement steps of the last solve (max over rhs) */
   double analysis_ms, factor_ms, solve_ms;
   int64_t factor_bytes;               /* device bytes held by factors */
   double prof_ms[BDDC_PROF_CLASSES];          /* summed CUDA-event durations per class */

@@ -35,7 +35,7 @@ EXPORTED = [
     "bddc_get_stats", "bddc_sizes", "bddc_free", "bddc_last_error", "bddc_kernel_launches",
     "bddc_reset_profile", "bddc_grad_noalloc",
 ]
-PROF_TRSV, PROF_FACTOR, PROF_SPMV, PROF_CLASSES = 0, 1, 2, 4
+PROF_TRSV, PROF_FACTOR, PROF_SPMV, PROF_TRMV, PROF_CLASSES = 0, 1, 2, 3, 4
 
 
 class Mesh(C.Structure):
@@ -59,7 +59,8 @@ class Opts(C.Structure):
     _fields_ = [
         ("precision", C.c_int), ("weights", C.c_int), ("all_corners", C.c_uint), ("maxit", C.c_int),
         ("refine_steps", C.c_int), ("flexible", C.c_int), ("use_graph", C.c_int), ("verbose", C.c_int),
-        ("profile", C.c_int), ("tensor_cores", C.c_int), ("krylov", C.c_int),
+        ("profile", C.c_int), ("tensor_cores", C.c_int), ("inner_steps", C.c_int), ("inner_tol", C.c_double),
+        ("krylov", C.c_int),
     ]
 
 
@@ -70,7 +71,8 @@ class Stats(C.Structure):
         ("n_sub", C.c_int64 * MAX_LEVELS), ("n_dof", C.c_int64 * MAX_LEVELS),
         ("n_iface", C.c_int64 * MAX_LEVELS), ("n_coarse", C.c_int64 * MAX_LEVELS),
         ("n_promoted", C.c_int64 * MAX_LEVELS), ("breakdown_level", C.c_int), ("breakdown_sub", C.c_int),
-        ("refine_steps", C.c_int), ("analysis_ms", C.c_double), ("factor_ms", C.c_double),
+        ("refine_steps", C.c_int), ("inner_steps", C.c_int), ("outer_iterations", C.c_int),
+        ("analysis_ms", C.c_double), ("factor_ms", C.c_double),
         ("solve_ms", C.c_double), ("factor_bytes", C.c_int64),
         ("prof_ms", C.c_double * 4), ("prof_launches", C.c_int64 * 4), ("prof_bytes", C.c_double * 4),
         ("prof_flops", C.c_double * 4),

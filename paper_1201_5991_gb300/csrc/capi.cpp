@@ -92,6 +92,7 @@ struct Level {
   std::vector<int> narrow_tiles;   // per step k: in-panel update tiles (256-wide panels)
   std::vector<int> wide_items;     // per super-step: tensor-core work items
   double trsv_bytes[2] = {0, 0};   // algorithmic bytes of one sweep over part 0 / part 1
+  double trmv_bytes = 0;           // algorithmic bytes of one factor-based inner Schur product
   // sweep task lists [part][direction] in dependency order and their control words
   int2* tasks[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   int ntasks[2][2] = {{0, 0}, {0, 0}};
@@ -181,11 +182,14 @@ struct bddc_handle_s {
   double* fcol = nullptr;              // [n_free] work
   double* ucol = nullptr;
   double *full_a = nullptr, *full_b = nullptr;
-  int refine_steps = 0;
+  int refine_steps = 0;                // interior-solve steps of the FP64 Schur operator
+  bool use_outer = false;              // mixed PCG: FP64 outer refinement around an inner PCG
+  int inner_steps = 0;                 // inner operator: 0 = from the stored factor, k = k interior-solve steps
+  int cur_steps = 0;                   // steps used by the next interior solves
   int grid_max = 304;                  // persistent sweep grid: 2 CTAs per SM
   cudaStream_t cap_st = nullptr;       // private stream for graph capture
   cudaGraphExec_t iter_graph = nullptr;  // one captured Krylov iteration
-  int iter_graph_flexible = -1;          // 0/1: PCG (Fletcher-Reeves / flexible), 2: BiCGstab
+  int iter_graph_key = -1;               // graph_key() of the captured iteration
   int64_t graph_kernels = 0;           // kernel nodes in iter_graph
   bddc_stats stats{};
   bool factored = false;
@@ -433,6 +437,7 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
   const double nb3 = (double)NB * NB * NB;
   const double wsz = L.fp32 ? 4.0 : 8.0;
   L.trsv_bytes[0] = L.trsv_bytes[1] = 0.0;
+  L.trmv_bytes = 0.0;
   for (int64_t s = 0; s < ns; ++s) {
     const SubMeta& m = L.meta[s];
     for (int k = 0; k < m.Bc; ++k) {
@@ -455,6 +460,7 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
     // a sweep reads the stored triangle once and the vector in and out
     L.trsv_bytes[0] += wsz * (0.5 * (double)m.nI * (m.nI + 1) + 2.0 * m.nI);
     L.trsv_bytes[1] += wsz * (0.5 * (double)m.nG * (m.nG + 1) + 2.0 * m.nG);
+    L.trmv_bytes += wsz * ((double)m.nG * (m.nG + 1) + 4.0 * m.nG);   // the triangle twice, vectors
   }
 
   // element slots (subdomain order) and their padded local DOF positions
@@ -801,7 +807,7 @@ void interior_solve_l1(bddc_handle_s* h, Level& L, const double* v, double* w, c
   float* t = (float*)L.locB;
   double* r = L.dl3;
   ck(cudaMemsetAsync(w, 0, sizeof(double) * n, st), "memset");
-  const int steps = std::max(1, h->refine_steps);
+  const int steps = std::max(1, h->cur_steps);
   for (int it = 0; it < steps; ++it) {
     launch_convert<double, float>(it == 0 ? v : r, t, n, st);
     trsv_pair<float>(h, L, t, 0, st);
@@ -813,10 +819,24 @@ void interior_solve_l1(bddc_handle_s* h, Level& L, const double* v, double* w, c
   }
 }
 
-// y = S x on the level-1 interface (Sec. 2, discrete Dirichlet problems)
+// y = S x on the level-1 interface (Sec. 2, discrete Dirichlet problems).  With cur_steps = 0
+// on an FP32 level: the inner operator S~ = sum R_i^T (L_GG S L_GG^T - C_i^T R C_i) R_i from the
+// stored factor (no interior solves).
 void schur_apply(bddc_handle_s* h, const double* x, double* y, cudaStream_t st) {
   Level& L = h->lv[0];
   const int64_t n = L.n_vec;
+  if (L.fp32 && h->cur_steps == 0) {
+    launch_gather_iface<double>(L.d, x, 0, L.dl0, st);
+    launch_convert<double, float>(L.dl0, (float*)L.locA, n, st);
+    {
+      ProfScope ps(h, BDDC_PROF_TRMV, L.trmv_bytes, 0.0, st);
+      launch_trmv_schur(L.d, L.max_nGb, (const float*)L.locA, (float*)L.locB, (float*)L.locA, st);
+    }
+    launch_convert<float, double>((const float*)L.locA, L.dl1, n, st);
+    launch_sub_ctrc(L.d, L.crow_sub, L.sum_nc, L.dl0, L.dl1, st);
+    launch_scatter_iface<double>(L.d, L.dl1, 0, y, st);
+    return;
+  }
   launch_gather_iface<double>(L.d, x, 0, L.dl0, st);                 // x_i = R_i x
   ck(cudaMemsetAsync(L.dl1, 0, sizeof(double) * n, st), "memset");
   launch_spmv_rows(L.d, L.rows[0], L.nrows[0], L.dl0, L.dl1, 1.0, 0.0, L.row_sub, st);  // v = K_IG x_i
@@ -931,11 +951,11 @@ double dot_host(bddc_handle_s* h, const double* a, const double* b, int64_t n) {
 void choose_refinement(bddc_handle_s* h) {
   Level& L = h->lv[0];
   if (!L.fp32) {
-    h->refine_steps = 0;
+    h->refine_steps = h->cur_steps = 0;
     return;
   }
   if (h->opts.refine_steps > 0) {
-    h->refine_steps = h->opts.refine_steps;
+    h->refine_steps = h->cur_steps = h->opts.refine_steps;
     return;
   }
   cudaStream_t st = h->st;
@@ -951,7 +971,7 @@ void choose_refinement(bddc_handle_s* h) {
   int best = 1;
   double prev = 1e300;
   for (int steps = 1; steps <= 8; ++steps) {
-    h->refine_steps = steps;
+    h->refine_steps = h->cur_steps = steps;
     interior_solve_l1(h, L, v, w, st);
     ck(cudaMemcpyAsync(L.dl3, v, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
     launch_spmv_rows(L.d, L.rows[0], L.nrows[0], w, L.dl3, -1.0, 1.0, L.row_sub, st);
@@ -961,7 +981,7 @@ void choose_refinement(bddc_handle_s* h) {
     if (rel < 4e-16) break;
     prev = rel;
   }
-  h->refine_steps = best;
+  h->refine_steps = h->cur_steps = best;
 }
 
 void numeric_setup(bddc_handle_s* h) {
@@ -996,6 +1016,15 @@ void numeric_setup(bddc_handle_s* h) {
   h->stats.factor_ms = now_ms() - t0;
   flush_profile(h);
   h->stats.refine_steps = h->refine_steps;
+  h->cur_steps = h->refine_steps;
+  h->use_outer = false;
+  h->inner_steps = 0;
+  if (h->lv[0].fp32 && krylov_kind(h) == BDDC_KRYLOV_PCG && h->opts.inner_steps >= 0 &&
+      h->opts.inner_steps < h->refine_steps) {
+    h->use_outer = true;
+    h->inner_steps = h->opts.inner_steps;
+  }
+  h->stats.inner_steps = h->use_outer ? h->inner_steps : -1;
   h->factored = true;
 }
 
@@ -1193,6 +1222,7 @@ void device_setup(bddc_handle_s* h) {
 // ------------------------------------------------------------------ PCG (Sec. 4)
 struct PcgResult {
   int iterations = 0;
+  int outer = 0;              // FP64 outer refinement steps (pcg_refined)
   bool converged = false;
   double rel = 0.0;
   double gnorm = 0.0;
@@ -1251,6 +1281,10 @@ void iteration_body(bddc_handle_s* h, double* x, int kind, cudaStream_t st) {
 }
 
 // Capture one Krylov iteration into a CUDA graph (once per handle; the buffers never move).
+// A captured iteration depends on the method (0/1: PCG with Fletcher-Reeves / flexible beta,
+// 2: BiCGstab) and on the interior-solve steps of the Schur operator.
+int graph_key(const bddc_handle_s* h, int kind) { return kind | (h->cur_steps << 3); }
+
 void capture_iteration(bddc_handle_s* h, int flexible) {
   if (!h->cap_st) ck(cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking), "cudaStreamCreate");
   cudaGraph_t g = nullptr;
@@ -1275,11 +1309,11 @@ void capture_iteration(bddc_handle_s* h, int flexible) {
   cudaGraphDestroy(g);
   ck(e, "cudaGraphInstantiate");
   h->iter_graph = ex;
-  h->iter_graph_flexible = flexible;
+  h->iter_graph_key = graph_key(h, flexible);
 }
 
 void drop_graph_if_kind_differs(bddc_handle_s* h, int kind) {
-  if (!h->iter_graph || h->iter_graph_flexible == kind) return;
+  if (!h->iter_graph || h->iter_graph_key == graph_key(h, kind)) return;
   cudaGraphExecDestroy(h->iter_graph);
   h->iter_graph = nullptr;
   for (auto& r : h->graph_prof) {
@@ -1590,6 +1624,75 @@ PcgResult fgmres(bddc_handle_s* h, const double* g, double* x, double tol, int m
   return res;
 }
 
+// Mixed-precision iterative refinement around PCG (the outer iteration that restores FP64
+// accuracy): x += S~^{-1} r with r = g - S x, where S is the FP64 Schur operator (interior solves
+// refined to FP64 accuracy) and S~ the same operator with h->inner_steps interior-solve steps
+// (0: products with the stored interface factor, no interior solve; k >= 1: k interior-solve
+// steps).  Each inner PCG reduces its residual by eta (never below what the outer tolerance
+// needs), starting from opts.inner_tol and adapted to the observed outer reduction within the
+// solve (so repeated solves are bitwise identical); an outer step that fails to halve the
+// residual switches the inner operator to the FP64 one.
+// The solution is left in h->vs; h->vt holds the outer residual.
+PcgResult pcg_refined(bddc_handle_s* h, const double* g, double tol, int maxit) {
+  constexpr int kMaxOuter = 40;
+  cudaStream_t st = h->st;
+  const int64_t n = h->lv[0].d.n_iface;
+  double* xo = h->vs;
+  double* ro = h->vt;
+  PcgResult res;
+  ck(cudaMemsetAsync(xo, 0, sizeof(double) * std::max<int64_t>(n, 1), st), "memset");
+  if (n == 0) {
+    res.converged = true;
+    return res;
+  }
+  ck(cudaMemcpyAsync(ro, g, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
+  const double gnorm = std::sqrt(dot_host(h, g, g, n));
+  if (!std::isfinite(gnorm)) fail(BDDC_ERR_NAN, "NaN in the condensed right-hand side");
+  res.gnorm = gnorm;
+  if (gnorm == 0.0) {
+    res.converged = true;
+    return res;
+  }
+  double rnorm = gnorm;
+  int inner = h->inner_steps;
+  double eta = h->opts.inner_tol > 0.0 ? std::min(h->opts.inner_tol, 0.5) : 1e-2;
+  for (int outer = 0; outer < kMaxOuter && res.iterations < maxit; ++outer) {
+    const double tin = std::max(eta, 0.5 * tol * gnorm / rnorm);
+    h->cur_steps = inner;
+    PcgResult in = pcg(h, ro, h->vx, tin, maxit - res.iterations);
+    h->cur_steps = h->refine_steps;
+    res.iterations += in.iterations;
+    res.outer = outer + 1;
+    if (outer == 0) {
+      res.alpha = in.alpha;
+      res.beta = in.beta;
+    }
+    launch_axpy_loc(xo, h->vx, 1.0, n, st);
+    schur_apply(h, xo, h->vq, st);                        // r = g - S x with the FP64 operator
+    ck(cudaMemcpyAsync(ro, g, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
+    launch_axpy_loc(ro, h->vq, -1.0, n, st);
+    const double rn = std::sqrt(dot_host(h, ro, ro, n));
+    if (!std::isfinite(rn)) fail(BDDC_ERR_NAN, "NaN in the outer refinement");
+    res.rel = rn / gnorm;
+    if (res.rel <= tol) {
+      res.converged = true;
+      return res;
+    }
+    // the outer reduction shows how accurate the inner operator is: ask the next inner solve for
+    // about that much (solving further is lost at the restart), unless the inner solve itself
+    // was the limit
+    const double ratio = rn / rnorm;
+    if (ratio > 0.5)
+      inner = h->refine_steps;                          // stagnation: inner operator = FP64 one
+    else if (ratio > 2.0 * tin)
+      eta = std::min(0.1, std::max(1e-4, ratio));
+    else
+      eta = std::max(1e-4, 0.5 * eta);
+    rnorm = rn;
+  }
+  return res;
+}
+
 int solve_impl(bddc_handle_s* h, const double* rhs, double* x, int nrhs, double tol, bddc_stats* stats,
                bool with_lift) {
   if (!h->factored) fail(BDDC_ERR_INVALID, "handle has no numeric set-up");
@@ -1597,7 +1700,8 @@ int solve_impl(bddc_handle_s* h, const double* rhs, double* x, int nrhs, double 
   if (!(tol > 0.0)) fail(BDDC_ERR_INVALID, "tol must be positive");
   cudaStream_t st = h->st;
   const double t0 = now_ms();
-  int maxits = 0;
+  h->cur_steps = h->refine_steps;
+  int maxits = 0, max_outer = 0;
   bool all_conv = true;
   double worst = 0.0;
   PcgResult first;
@@ -1611,17 +1715,21 @@ int solve_impl(bddc_handle_s* h, const double* rhs, double* x, int nrhs, double 
       f = h->fcol;
     }
     condensed_rhs(h, f, h->vg, st);
+    const bool refined = kind == BDDC_KRYLOV_PCG && h->use_outer;
     PcgResult r = kind == BDDC_KRYLOV_BICGSTAB ? bicgstab(h, h->vg, h->vx, tol, h->opts.maxit)
                   : kind == BDDC_KRYLOV_FGMRES ? fgmres(h, h->vg, h->vx, tol, h->opts.maxit)
+                  : refined                    ? pcg_refined(h, h->vg, tol, h->opts.maxit)
                                                : pcg(h, h->vg, h->vx, tol, h->opts.maxit);
-    recover(h, f, h->vx, u, st);
+    recover(h, f, refined ? h->vs : h->vx, u, st);
     maxits = std::max(maxits, r.iterations);
+    max_outer = std::max(max_outer, r.outer);
     all_conv = all_conv && r.converged;
     worst = std::max(worst, r.rel);
     if (k == 0) first = r;
   }
   check_status(h, 0);
   h->stats.iterations = maxits;
+  h->stats.outer_iterations = max_outer;
   h->stats.converged = all_conv ? 1 : 0;
   h->stats.rel_residual = worst;
   h->stats.rhs_norm = first.gnorm;

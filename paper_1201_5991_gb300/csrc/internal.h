@@ -177,6 +177,11 @@ void launch_copy_segments(const double* src, const int64_t* src_off, double* dst
 void launch_iface_rhs(double* g, const double* f, const int64_t* idx, const double* t, int64_t n,
                       cudaStream_t st);
 void launch_put_indexed(double* u, const int64_t* idx, const double* v, int64_t n, cudaStream_t st);
+// inner Schur operator from the stored factor (trmv.cu): y = L_GG S L_GG^T x over the
+// interface block rows of an FP32 level (y1 scratch), and y -= C^T R C x (FP64, local vectors)
+void launch_trmv_schur(const LevelDev& L, int max_nGb, const float* x, float* y1, float* y, cudaStream_t st);
+void launch_sub_ctrc(const LevelDev& L, const int32_t* crow_sub, int64_t total_rows, const double* x, double* y,
+                     cudaStream_t st);
 // flexible GMRES (vector.cu): out[i] = V_i . w (i < nv, partial holds nv * nblk doubles);
 // w += alpha sum_i c_i V_i; dst = src / sqrt(*nrm2)
 void launch_multidot(const double* V, int64_t ldv, int nv, const double* w, int64_t n, double* partial, int nblk,

@@ -1,0 +1,139 @@
+// Inner Schur operator from the stored factor (mixed precision only).
+//
+// The trailing block of the partial factorisation of A_i = K_i + C_i^T R C_i is the factor of
+// the augmented local Schur complement: L_GG S L_GG^T = S_i + C_i^T R C_i, S_i = K_GG -
+// K_GI K_II^{-1} K_IG (Sec. 2).  So S~_i x = L_GG S (L_GG^T x) - C_i^T R C_i x reproduces S_i up to
+// the FP32 rounding of the factorisation, with two triangular matrix-vector PRODUCTS over the
+// interface block rows: unlike the triangular solves they carry no dependency chain, so every
+// (subdomain, block row) is an independent CTA and the pass streams the interface triangle at
+// full bandwidth.  It serves as the cheap operator of the inner iteration of the mixed solver;
+// the outer iteration applies the FP64 operator.
+#include "internal.h"
+
+namespace bddc {
+
+namespace {
+
+__device__ __forceinline__ int64_t tile_index_t(int i, int j, int Bc) {
+  return i < Bc ? ((int64_t)i * (i + 1) / 2 + j) : ((int64_t)Bc * (Bc + 1) / 2 + (int64_t)(i - Bc) * Bc + j);
+}
+
+// y1_j = sum_{i >= j} L(i,j)^T x_i over the interface block rows; block (o, s) makes output
+// block j = nIb + o.  Warp w takes the tile rows w, w+8, ..., lane l the columns 2l, 2l+1, so
+// every row is one coalesced 256-byte read; the eight warps' column sums are added at the end
+// in a fixed order (no barrier inside the tile loop).
+__global__ void __launch_bounds__(256) k_trmv_t(LevelDev L, const float* __restrict__ x, float* __restrict__ y1) {
+  const int s = blockIdx.y;
+  const SubMeta m = L.meta[s];
+  const int o = blockIdx.x;
+  if (o >= m.nGb) return;
+  const int j = m.nIb + o;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ float part[8][64];
+  const float* tiles = (const float*)L.tiles + m.tile_off;
+  const float* xv = x + m.vec_off;
+  const int nGrow = m.nIb * NB + m.nG;   // padded rows beyond the interface hold no data
+  float ax = 0.f, ay = 0.f;
+#pragma unroll 2
+  for (int i = j; i < m.Bc; ++i) {
+    const float* t = tiles + tile_index_t(i, j, m.Bc) * NB2 + 2 * lane;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int row = warp + 8 * r;
+      const int grow = i * NB + row;
+      const float xr = grow < nGrow ? __ldg(xv + grow) : 0.f;
+      const float2 a = __ldg((const float2*)(t + row * NB));
+      ax += a.x * xr;
+      ay += a.y * xr;
+    }
+  }
+  part[warp][2 * lane] = ax;
+  part[warp][2 * lane + 1] = ay;
+  __syncthreads();
+  if (threadIdx.x < 64) {
+    const int c = threadIdx.x;
+    float v = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) v += part[w][c];
+    y1[m.vec_off + (int64_t)j * NB + c] = v;
+  }
+}
+
+// y_i = sum_{nIb <= j <= i} L(i,j) S_j y1_j; block (o, s) makes output block i = nIb + o.
+// Warp w takes rows w, w+8, ..., lane l the columns 2l, 2l+1.
+__global__ void __launch_bounds__(256) k_trmv_n(LevelDev L, const float* __restrict__ y1, float* __restrict__ y) {
+  const int s = blockIdx.y;
+  const SubMeta m = L.meta[s];
+  const int o = blockIdx.x;
+  if (o >= m.nGb) return;
+  const int i = m.nIb + o;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float* tiles = (const float*)L.tiles + m.tile_off;
+  const float* yv = y1 + m.vec_off;
+  const float* sg = (const float*)L.sgn + m.vec_off;
+  float acc[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) acc[r] = 0.f;
+#pragma unroll 2
+  for (int j = m.nIb; j <= i; ++j) {
+    float2 b = *(const float2*)(yv + (int64_t)j * NB + 2 * lane);
+    if (L.indefinite) {
+      const float2 sj = *(const float2*)(sg + (int64_t)j * NB + 2 * lane);
+      b.x *= sj.x;
+      b.y *= sj.y;
+    }
+    const float* t = tiles + tile_index_t(i, j, m.Bc) * NB2 + 2 * lane;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const float2 a = __ldg((const float2*)(t + (warp + 8 * r) * NB));
+      acc[r] += a.x * b.x + a.y * b.y;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    float v = acc[r];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0) y[m.vec_off + (int64_t)i * NB + warp + 8 * r] = v;
+  }
+}
+
+// y -= C^T R C x over the padded local interface vectors (FP64); one warp per constraint row.
+// Distinct rows touch disjoint positions (each local DOF lies in one glob and has one
+// component), so the update needs no atomics.
+__global__ void k_sub_ctrc(LevelDev L, const int32_t* __restrict__ crow_sub, int64_t total_rows,
+                           const double* __restrict__ x, double* __restrict__ y) {
+  const int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (g >= total_rows) return;
+  const int s = crow_sub[g];
+  const SubMeta m = L.meta[s];
+  const double rq = L.rho[s] * L.c_rho[g];
+  if (rq == 0.0) return;
+  const int64_t a = L.c_ptr[g], b = L.c_ptr[g + 1];
+  double t = 0.0;
+  for (int64_t e = a + lane; e < b; e += 32) t += L.c_val[e] * x[m.vec_off + L.c_pos[e]];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+  for (int64_t e = a + lane; e < b; e += 32) y[m.vec_off + L.c_pos[e]] -= rq * t * L.c_val[e];
+}
+
+}  // namespace
+
+void launch_trmv_schur(const LevelDev& L, int max_nGb, const float* x, float* y1, float* y, cudaStream_t st) {
+  if (max_nGb <= 0 || L.n_sub <= 0) return;
+  const dim3 grid((unsigned)max_nGb, (unsigned)L.n_sub);
+  note_launch();
+  k_trmv_t<<<grid, 256, 0, st>>>(L, x, y1);
+  note_launch();
+  k_trmv_n<<<grid, 256, 0, st>>>(L, y1, y);
+}
+
+void launch_sub_ctrc(const LevelDev& L, const int32_t* crow_sub, int64_t total_rows, const double* x, double* y,
+                     cudaStream_t st) {
+  if (total_rows <= 0) return;
+  note_launch();
+  k_sub_ctrc<<<(unsigned)((total_rows + 7) / 8), 256, 0, st>>>(L, crow_sub, total_rows, x, y);
+}
+
+}  // namespace bddc
