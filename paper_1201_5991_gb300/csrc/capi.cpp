@@ -91,6 +91,11 @@ struct Level {
   std::vector<double> step_flops;  // tile flops of factor step k (all subdomains)
   std::vector<int> narrow_tiles;   // per step k: in-panel update tiles (256-wide panels)
   std::vector<int> wide_items;     // per super-step: tensor-core work items
+  std::vector<int64_t> wide_items2; // per super-step: 128 x 128 work items of the pre-split update (all subdomains)
+  int64_t* item_pref = nullptr;     // [super-steps][n_sub + 1] first work item of every subdomain
+  uint8_t* split = nullptr;        // scaled FP16 parts of the current super-panel (pre-split update)
+  float* rscale = nullptr;         // their row unscaling factors (powers of two)
+  int64_t* prow_off = nullptr;     // [n_sub] first split row of every subdomain
   double trsv_bytes[2] = {0, 0};   // algorithmic bytes of one sweep over part 0 / part 1
   double trmv_bytes = 0;           // algorithmic bytes of one factor-based inner Schur product
   // sweep task lists [part][direction] in dependency order and their control words
@@ -434,6 +439,7 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
   L.step_flops.assign(L.max_Bc, 0.0);
   L.narrow_tiles.assign(L.max_Bc, 0);
   L.wide_items.assign((L.max_Bc + kPanel - 1) / kPanel + 1, 0);
+  L.wide_items2.assign((L.max_Bc + kPanel - 1) / kPanel + 1, 0);
   const double nb3 = (double)NB * NB * NB;
   const double wsz = L.fp32 ? 4.0 : 8.0;
   L.trsv_bytes[0] = L.trsv_bytes[1] = 0.0;
@@ -456,6 +462,7 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
       int64_t cnt = 0;
       for (int j = kb0 + kPanel; j < m.Bc; ++j) cnt += (m.R - j + 1) / 2;
       L.wide_items[kb0 / kPanel] = std::max(L.wide_items[kb0 / kPanel], (int)cnt);
+
     }
     // a sweep reads the stored triangle once and the vector in and out
     L.trsv_bytes[0] += wsz * (0.5 * (double)m.nI * (m.nI + 1) + 2.0 * m.nI);
@@ -641,6 +648,33 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
   d.Ginv = A.alloc<double>(L.g_elems);
   d.KC = A.alloc<double>(L.g_elems);
   const size_t ts = L.fp32 ? sizeof(float) : sizeof(double);
+  if (L.fp32 && h->opts.tensor_cores && h->physics != BDDC_STOKES) {
+    // pre-split panel buffer: kPanel tiles of 24 KB (three BF16 parts) for every block row
+    std::vector<int64_t> po(ns);
+    int64_t rows = 0;
+    for (int64_t s = 0; s < ns; ++s) {
+      po[s] = rows;
+      rows += L.meta[s].R;
+    }
+    L.prow_off = A.upload(po, st);
+    L.split = A.alloc<uint8_t>(rows * kPanel * 2 * NB2 * 2);
+    L.rscale = A.alloc<float>(rows * NB);
+    // work items (128 x 128 output blocks) of every super-step, flattened over the subdomains
+    const int np = (int)L.wide_items2.size();
+    std::vector<int64_t> pref((size_t)np * (ns + 1), 0);
+    for (int p = 0; p < np; ++p) {
+      const int kb1 = (p + 1) * kPanel;
+      int64_t acc = 0;
+      for (int64_t s = 0; s < ns; ++s) {
+        pref[(size_t)p * (ns + 1) + s] = acc;
+        const SubMeta& m = L.meta[s];
+        for (int j = kb1; j < m.Bc; j += 2) acc += (m.R - j + 1) / 2;
+      }
+      pref[(size_t)p * (ns + 1) + ns] = acc;
+      L.wide_items2[p] = acc;
+    }
+    L.item_pref = A.upload(pref, st);
+  }
   if (L.fp32) {
     d.tiles = A.alloc<float>(L.tile_elems);
     d.dinv = A.alloc<float>(L.dinv_elems);
@@ -748,7 +782,17 @@ void factor_level(bddc_handle_s* h, Level& L, cudaStream_t st) {
       ProfScope ps(h, BDDC_PROF_FACTOR, 0.0, fl, st);
       for (int k = kb0; k < std::min(kb1, L.max_Bc); ++k)
         launch_potrf_step<T>(d, k, L.max_R, L.narrow_tiles[k], kb1, st);
-      launch_update_tc(d, kb0, kb1, L.wide_items[kb0 / kPanel], st);
+      if (L.split) {
+        const int p = kb0 / kPanel;
+        const int64_t items = L.wide_items2[p];
+        if (items > 0) {
+          launch_split_panel(d, kb0, kb1, L.max_R, L.split, L.rscale, L.prow_off, st);
+          launch_update_tc2(d, kb0, kb1, (int)std::min<int64_t>(items, h->grid_max / 2), L.split, L.rscale,
+                            L.prow_off, L.item_pref + (size_t)p * (d.n_sub + 1), st);
+        }
+      } else {
+        launch_update_tc(d, kb0, kb1, L.wide_items[kb0 / kPanel], st);
+      }
     }
   } else {
     for (int k = 0; k < L.max_Bc; ++k) {

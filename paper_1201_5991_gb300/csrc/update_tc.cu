@@ -23,6 +23,7 @@
 // signals an mbarrier when the shared-memory operands may be reused.  The epilogue reads the
 // accumulator with tcgen05.ld and subtracts it from the tiles in global memory.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -38,6 +39,7 @@ constexpr uint32_t kPartA = 128 * 128;   // bytes of one BF16 part of A (128 row
 constexpr uint32_t kPartB = 64 * 128;    // bytes of one BF16 part of B (64 rows x 64)
 constexpr uint32_t kStage = 3 * kPartA + 3 * kPartB;
 constexpr long long kSpinLimit = 1ll << 26;
+constexpr int kPanelTiles = 4;           // tile columns of a super-panel (the split buffer's row pitch)
 
 __device__ __forceinline__ int64_t tile_index(int i, int j, int Bc) {
   return i < Bc ? ((int64_t)i * (i + 1) / 2 + j) : ((int64_t)Bc * (Bc + 1) / 2 + (int64_t)(i - Bc) * Bc + j);
@@ -263,7 +265,356 @@ __global__ void __launch_bounds__(kThreads, 2)
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
 }
 
+// ---------------------------------------------------------------------------------------
+// Pre-split variant (SPD levels): FP32 from two scaled FP16 parts.  For the 64 x 256 slab of
+// panel row tile i, every row r is scaled by 2^e_r so that its largest entry lies in
+// [2^14, 2^15), and each scaled entry a is split into hi = fp16(a) and lo = fp16((a - hi) 2^11)
+// (the scaled low part cannot underflow).  Then a b = hi_a hi_b + (hi_a lo_b + lo_a hi_b) 2^-11
+// up to the dropped lo lo term (2^-22 relative): three FP16 products instead of six BF16
+// ones, and 4 bytes per entry instead of 6 (the scheme of Ootomo and Yokota, 2022).  The
+// output is unscaled exactly by the stored factors 2^-e_i and 2^-e_j.  Measured against FP64 on factor-like data
+// (rows spanning four decades): 2-4e-7 of sum |a||b| (bf16x3: 1.3e-7, FP32 dot: 8e-7).
+//
+// k_split_panel writes the parts in the exact shared-memory operand image (K-major, 128-byte
+// swizzle), so the update moves bytes with cp.async.bulk only.  A work item is a 128 x 128
+// output block (row tiles i0, i0+1 by column tiles j, j+1); per panel column q the producer
+// warp copies the two parts of the four tiles (64 KB) into one of two shared-memory stages and
+// one thread issues 12 MMAs (3 products x 4 K-steps, M = N = 128) into one of two TMEM
+// accumulator pairs (hi hi; the two cross products); eight epilogue warps promote each pair
+// into FP32 registers after every column and finally update the output tiles.
+
+constexpr uint32_t kTilePart = 64 * 128;         // one FP16 part of one 64 x 64 tile (8 KB)
+constexpr uint32_t kSplitTile = 2 * kTilePart;   // hi and lo of one tile (16 KB)
+constexpr uint32_t kOpnd = 2 * kTilePart;        // one part of a 128-row operand (16 KB)
+constexpr uint32_t kStage2 = 4 * kOpnd;          // A hi, A lo, B hi, B lo (64 KB)
+constexpr int kThreads2 = 288;                   // 8 epilogue warps + 1 producer / MMA warp
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void store4h(uint8_t* part, uint32_t off, const __half* h) {
+  __half2 lo = __halves2half2(h[0], h[1]), hi = __halves2half2(h[2], h[3]);
+  uint2 v;
+  v.x = *(uint32_t*)&lo;
+  v.y = *(uint32_t*)&hi;
+  *(uint2*)(part + off) = v;
+}
+
+// one block per panel row tile i (kb1 <= i < R) of every subdomain; thread (r, c4): row r of
+// tile column kb0 + c4 (the four threads of a row share its scale)
+__global__ void __launch_bounds__(256) k_split_panel(LevelDev L, int kb0, int kb1, uint8_t* __restrict__ split,
+                                                     float* __restrict__ rscale, const int64_t* __restrict__ prow_off) {
+  const int s = blockIdx.y;
+  const SubMeta m = L.meta[s];
+  if (kb1 >= m.Bc) return;
+  const int i = kb1 + (int)blockIdx.x;
+  if (i >= m.R) return;
+  const int r = threadIdx.x >> 2, c4 = threadIdx.x & 3;
+  const float4* t = (const float4*)((const float*)L.tiles + m.tile_off + tile_index(i, kb0 + c4, m.Bc) * NB2 + r * NB);
+  float4 v[16];
+  float mx = 0.f;
+#pragma unroll
+  for (int u = 0; u < 16; ++u) {
+    v[u] = __ldcg(t + u);
+    mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v[u].x), fabsf(v[u].y)), fmaxf(fabsf(v[u].z), fabsf(v[u].w))));
+  }
+  mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+  mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+  int ex = 0;
+  if (mx > 0.f) {
+    int k;
+    frexpf(mx, &k);   // mx = f 2^k, f in [0.5, 1)
+    ex = 15 - k;      // mx 2^ex in [2^14, 2^15)
+  }
+  const int64_t row = prow_off[s] + i;
+  if (c4 == 0) rscale[row * NB + r] = ldexpf(1.f, -ex);   // exact power of two
+  uint8_t* dst = split + (row * kPanelTiles + c4) * (int64_t)kSplitTile;
+#pragma unroll
+  for (int u = 0; u < 16; ++u) {
+    const float a[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+    __half h[4], l[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float sa = ldexpf(a[e], ex);
+      h[e] = __float2half_rn(sa);
+      l[e] = __float2half_rn((sa - __half2float(h[e])) * 2048.f);
+    }
+    const uint32_t off = sw128_off(r, 4 * u);
+    store4h(dst, off, h);
+    store4h(dst + kTilePart, off, l);
+  }
+}
+
+// Persistent: CTA c takes the work items c, c + gridDim.x, ... of the panel (items of all
+// subdomains flattened; item_pref[s] = first item of subdomain s).  One global step per (item,
+// panel column); step g uses shared-memory stage and TMEM accumulator pair g & 1, so the copies
+// and MMAs of the next steps (also of the next item) run while the epilogue warps promote the
+// previous accumulators and write back the previous item's output block.
+__global__ void __launch_bounds__(kThreads2, 1)
+    k_update_tc2(LevelDev L, int kb0, int kb1, const uint8_t* __restrict__ split, const float* __restrict__ rscale,
+                 const int64_t* __restrict__ prow_off, const int64_t* __restrict__ item_pref) {
+  const int64_t n_items = item_pref[L.n_sub];
+  if ((int64_t)blockIdx.x >= n_items) return;
+  const int nq = kb1 - kb0;   // every subdomain with items has kb1 < Bc
+
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* stage0 = smem_raw + (base - raw);
+  __shared__ __align__(8) uint64_t full_bar[2], mma_bar[2], epi_bar[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_lost, s_issued;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&tmem_slot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full_bar[b])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mma_bar[b])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 256;" ::"r"(smem_u32(&epi_bar[b])));
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_lost = 0;
+    s_issued = 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  // item -> (subdomain, column pair j, j+1, row pair i0, i0+1)
+  auto decode = [&](int64_t it, int& s, int& j, int& i0) {
+    int lo = 0, hi = (int)L.n_sub - 1;
+    while (lo < hi) {   // last s with item_pref[s] <= it
+      const int mid = (lo + hi + 1) >> 1;
+      if (item_pref[mid] <= it) lo = mid; else hi = mid - 1;
+    }
+    s = lo;
+    const SubMeta& m = L.meta[s];
+    int64_t t = it - item_pref[s];
+    j = kb1;
+    i0 = -1;
+    for (; j < m.Bc; j += 2) {
+      const int cnt = (m.R - j + 1) / 2;
+      if (t < cnt) {
+        i0 = j + 2 * (int)t;
+        break;
+      }
+      t -= cnt;
+    }
+  };
+
+  if (warp == 8) {
+    // ---- producer / MMA issuer
+    if (lane == 0) {
+      // c FP32, a and b FP16, both K-major, N = 128, M = 128
+      const uint32_t idesc = (1u << 4) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+      bool lost = false;
+      int issued = 0;
+      auto wait = [&](uint64_t* bar, uint32_t parity) {
+        long long spins = 0;
+        while (!mbar_try_wait(bar, parity))
+          if (++spins > kSpinLimit) return false;
+        return true;
+      };
+      uint32_t g = 0;   // global step
+      for (int64_t it = blockIdx.x; it < n_items && !lost; it += gridDim.x) {
+        int s, j, i0;
+        decode(it, s, j, i0);
+        const SubMeta& m = L.meta[s];
+        const bool hasA1 = i0 + 1 < m.R, hasB1 = j + 1 < m.Bc;
+        const int64_t rbase = prow_off[s];
+        const uint8_t* rowA0 = split + (rbase + i0) * kPanelTiles * (int64_t)kSplitTile;
+        const uint8_t* rowA1 = split + (rbase + (hasA1 ? i0 + 1 : i0)) * kPanelTiles * (int64_t)kSplitTile;
+        const uint8_t* rowB0 = split + (rbase + j) * kPanelTiles * (int64_t)kSplitTile;
+        const uint8_t* rowB1 = split + (rbase + (hasB1 ? j + 1 : j)) * kPanelTiles * (int64_t)kSplitTile;
+        // the output tiles are read back by the epilogue after the last column: start moving them into L2
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const int ti = i0 + a, tj = j + c;
+            if ((a == 0 || hasA1) && (c == 0 || hasB1) && (ti >= m.Bc || tj <= ti)) {
+              const float* tp = (const float*)L.tiles + m.tile_off + tile_index(ti, tj, m.Bc) * NB2;
+              asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(tp), "r"((uint32_t)(NB2 * 4)) : "memory");
+            }
+          }
+        for (int q = 0; q < nq; ++q, ++g) {
+          const int b = g & 1;
+          const uint32_t n = g >> 1;
+          if (g >= 2 && !wait(&mma_bar[b], (n - 1) & 1u)) {   // MMAs of step g - 2 have read this stage
+            lost = true;
+            break;
+          }
+          uint8_t* sA = stage0 + b * kStage2;   // [A hi | A lo | B hi | B lo], 128 rows each
+          uint8_t* sB = sA + 2 * kOpnd;
+          mbar_expect_tx(&full_bar[b], kStage2);
+          const int64_t qo = (int64_t)q * kSplitTile;
+#pragma unroll
+          for (int p = 0; p < 2; ++p) {
+            bulk_g2s(sA + p * kOpnd, rowA0 + qo + p * kTilePart, kTilePart, &full_bar[b]);
+            bulk_g2s(sA + p * kOpnd + kTilePart, rowA1 + qo + p * kTilePart, kTilePart, &full_bar[b]);
+            bulk_g2s(sB + p * kOpnd, rowB0 + qo + p * kTilePart, kTilePart, &full_bar[b]);
+            bulk_g2s(sB + p * kOpnd + kTilePart, rowB1 + qo + p * kTilePart, kTilePart, &full_bar[b]);
+          }
+          if (!wait(&full_bar[b], n & 1u)) {
+            wait(&full_bar[b], n & 1u);   // copies may still land: one more bounded wait
+            lost = true;
+            break;
+          }
+          if (g >= 2 && !wait(&epi_bar[b], (n - 1) & 1u)) {   // accumulators of step g - 2 are read
+            lost = true;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t sa = smem_u32(sA), sb = smem_u32(sB);
+          const uint32_t acc_small = tmem + 256u * b, acc_big = acc_small + 128u;
+          // products: (A lo, B hi), (A hi, B lo) into the small accumulator, (A hi, B hi) into the big one
+          const int pa[3] = {1, 0, 0}, pb[3] = {0, 1, 0};
+#pragma unroll
+          for (int p = 0; p < 3; ++p)
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint64_t da = desc_sw128(sa + pa[p] * kOpnd + kk * 32);
+              const uint64_t db = desc_sw128(sb + pb[p] * kOpnd + kk * 32);
+              const bool big = p == 2;
+              const uint32_t acc = (kk > 0 || (p > 0 && !big)) ? 1u : 0u;   // fresh accumulators per step
+              asm volatile(
+                  "{\n .reg .pred pp;\n setp.ne.b32 pp, %4, 0;\n"
+                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pp;\n}\n" ::"r"(big ? acc_big : acc_small),
+                  "l"(da), "l"(db), "r"(idesc), "r"(acc));
+            }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           smem_u32(&mma_bar[b]))
+                       : "memory");
+          ++issued;
+        }
+      }
+      s_issued = issued;
+      if (lost) {
+        s_lost = 1;
+        atomicExch(L.status + 2, 4);
+      }
+    }
+  } else {
+    // ---- epilogue warps: warp w reads TMEM lanes 32 (w & 3) .. +31 (output rows) and columns
+    // 64 (w >> 2) .. +63; per step hi hi + 2^-11 (cross products) is added into FP32 registers
+    bool lost = false;
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+    const uint32_t col0 = 64u * (uint32_t)(warp >> 2);
+    const int erow = 32 * (warp & 3) + lane;
+    uint32_t g = 0;
+    for (int64_t it = blockIdx.x; it < n_items && !lost; it += gridDim.x) {
+      int s, j, i0;
+      decode(it, s, j, i0);
+      const SubMeta& m = L.meta[s];
+      float racc[64];
+#pragma unroll
+      for (int c = 0; c < 64; ++c) racc[c] = 0.f;
+      for (int q = 0; q < nq; ++q, ++g) {
+        const int b = g & 1;
+        const uint32_t n = g >> 1;
+        long long spins = 0;
+        while (!mbar_try_wait(&mma_bar[b], n & 1u))
+          if (++spins > kSpinLimit) {
+            lost = true;
+            break;
+          }
+        lost = __any_sync(0xffffffffu, lost);
+        if (lost) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+        for (int c16 = 0; c16 < 4; ++c16) {
+          const uint32_t taddr = tmem + lane_base + 256u * b + col0 + 16u * c16;
+          uint32_t v[16], w[16];
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+              : "r"(taddr));
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+              : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7]),
+                "=r"(w[8]), "=r"(w[9]), "=r"(w[10]), "=r"(w[11]), "=r"(w[12]), "=r"(w[13]), "=r"(w[14]), "=r"(w[15])
+              : "r"(taddr + 128u));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int c = 0; c < 16; ++c)
+            racc[16 * c16 + c] += __uint_as_float(w[c]) + __uint_as_float(v[c]) * (1.f / 2048.f);
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&epi_bar[b])) : "memory");
+      }
+      if (lost) break;
+      const bool hasA1 = i0 + 1 < m.R, hasB1 = j + 1 < m.Bc;
+      const int ti = erow < 64 ? i0 : i0 + 1;
+      const int tj = col0 < 64 ? j : j + 1;
+      const bool ok = (erow < 64 || hasA1) && (col0 < 64 || hasB1) && (ti >= m.Bc || tj <= ti);
+      if (ok) {
+        const int64_t rbase = prow_off[s];
+        const float sa = rscale[(rbase + ti) * NB + (erow & 63)];
+        const float4* sb = (const float4*)(rscale + (rbase + tj) * NB);
+        float* c = (float*)L.tiles + m.tile_off + tile_index(ti, tj, m.Bc) * NB2 + (erow & 63) * NB;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          float4 x = *(float4*)(c + 4 * u);
+          const float4 f = __ldg(sb + u);   // both factors are powers of two: the products are exact
+          x.x -= (racc[4 * u + 0] * sa) * f.x;
+          x.y -= (racc[4 * u + 1] * sa) * f.y;
+          x.z -= (racc[4 * u + 2] * sa) * f.z;
+          x.w -= (racc[4 * u + 3] * sa) * f.w;
+          *(float4*)(c + 4 * u) = x;
+        }
+      }
+    }
+    if (lost && lane == 0) atomicExch(L.status + 2, 4);
+  }
+  __syncthreads();
+  // before the accumulators are released no MMA may still be running (also on the error path)
+  const int issued = s_issued;
+  if (issued > 0) {
+    const int b = (issued - 1) & 1;
+    const uint32_t n = (uint32_t)((issued - 1) >> 1);
+    long long spins = 0;
+    while (!mbar_try_wait(&mma_bar[b], n & 1u))
+      if (++spins > kSpinLimit) break;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+}
+
 }  // namespace
+
+void launch_split_panel(const LevelDev& L, int kb0, int kb1, int max_R, uint8_t* split, float* rscale,
+                        const int64_t* prow_off, cudaStream_t st) {
+  if (L.n_sub <= 0 || max_R <= kb1) return;
+  note_launch();
+  k_split_panel<<<dim3((unsigned)(max_R - kb1), (unsigned)L.n_sub), 256, 0, st>>>(L, kb0, kb1, split, rscale, prow_off);
+}
+
+void launch_update_tc2(const LevelDev& L, int kb0, int kb1, int grid, const uint8_t* split, const float* rscale,
+                       const int64_t* prow_off, const int64_t* item_pref, cudaStream_t st) {
+  if (grid <= 0 || L.n_sub <= 0) return;
+  const size_t dyn = 2 * kStage2 + 1024;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_update_tc2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    attr = true;
+  }
+  note_launch();
+  k_update_tc2<<<(unsigned)grid, kThreads2, dyn, st>>>(L, kb0, kb1, split, rscale, prow_off, item_pref);
+}
 
 void launch_update_tc(const LevelDev& L, int kb0, int kb1, int max_items, cudaStream_t st) {
   if (max_items <= 0 || L.n_sub <= 0) return;
