@@ -124,6 +124,7 @@ struct Level {
   double* dl2 = nullptr;
   double* dl3 = nullptr;
   double* rc_sub = nullptr;    // [sum_nc]
+  double* psi_part = nullptr;  // [sum_nc * kPsiSlices] partial sums of Psi^T r
   double* zc_sub = nullptr;
   double* rC = nullptr;        // [n_coarse]
   double* zC = nullptr;
@@ -739,6 +740,7 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
   L.dl2 = A.alloc<double>(L.n_vec);
   L.dl3 = A.alloc<double>(L.n_vec);
   L.rc_sub = A.alloc<double>(L.sum_nc);
+  L.psi_part = A.alloc<double>(L.sum_nc * kPsiSlices);
   L.zc_sub = A.alloc<double>(L.sum_nc);
   L.rC = A.alloc<double>(mp.n_coarse);
   L.zC = A.alloc<double>(mp.n_coarse);
@@ -929,7 +931,7 @@ void interface_step_t(bddc_handle_s* h, int l, const double* rhat, double* zhat,
   Level& L = h->lv[l];
   T* v = (T*)L.locA;
   launch_gather_iface<T>(L.d, rhat, 1, v, st);          // r_i = E_i^T r_hat
-  launch_psi_t_apply<T>(L.d, v, L.rc_sub, st);          // Psi_i^T r_i
+  launch_psi_t_apply<T>(L.d, v, L.psi_part, L.sum_nc, L.rc_sub, st);   // Psi_i^T r_i
   launch_coarse_gather(L.d, L.rc_sub, L.rC, st);        // r_C = sum R_Ci^T Psi_i^T r_i
   trsv_one<T>(h, L, v, 1, 0, st);                       // Eq. sub_cor via the trailing factor
   launch_constraint_corr<T>(L.d, v, L.crow_sub, L.sum_nc, L.cc_t, L.cc_mu, L.max_nGb, st);

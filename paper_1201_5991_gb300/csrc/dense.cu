@@ -30,7 +30,7 @@ __device__ __forceinline__ void flag_breakdown(int* status, int sub) {
 }
 
 constexpr int LDS = NB + 4;   // k-major shared tile stride (multiple of 4 for vector loads)
-constexpr int kMaxCoarseLocal = 256;   // coarse DOFs of one subdomain handled by k_psi_t_apply
+constexpr int kMaxCoarseLocal = 256;   // coarse DOFs of one subdomain handled per pass of k_psi_t_part
 
 template <typename T>
 __device__ __forceinline__ void load_kmajor(T* s, const T* __restrict__ g) {
@@ -466,23 +466,27 @@ __global__ void k_cc_update(LevelDev L, T* __restrict__ vec, const double* __res
   v[c] = v[c] - acc;   // S L^{-1} r - Y^T mu
 }
 
-// rc_sub = Psi_G^T v_G (FP64 result), one block per subdomain: warp w takes interface rows
-// w, w+8, ..., lane l the coarse DOFs l, l+32, ... (coalesced reads of Psi's rows); the eight
-// warps' partial sums are added in a fixed order.
+// rc_sub = Psi_G^T v_G (FP64 result).  The interface rows of a subdomain are cut into
+// kPsiSlices slices, one block each (so the pass runs on n_sub x kPsiSlices blocks): warp w takes
+// rows w, w+8, ... of the slice, lane l the coarse DOFs l, l+32, ... (coalesced reads of Psi's
+// rows); the eight warps' sums and then the slices' sums are added in a fixed order.
 template <typename T>
-__global__ void k_psi_t_apply(LevelDev L, const T* __restrict__ vec, double* __restrict__ rc_sub) {
-  const int s = blockIdx.x;
+__global__ void k_psi_t_part(LevelDev L, const T* __restrict__ vec, double* __restrict__ part) {
+  const int s = blockIdx.y, z = blockIdx.x;
   const SubMeta m = L.meta[s];
   const int nc = m.nc;
+  const int chunk = (m.nG + kPsiSlices - 1) / kPsiSlices;
+  const int r0 = z * chunk, r1 = min(m.nG, r0 + chunk);
   const T* v = vec + m.vec_off + m.nIb * NB;
   const T* P = (const T*)L.psi + m.psi_off;
-  __shared__ T part[8][kMaxCoarseLocal];
+  __shared__ T red[8][kMaxCoarseLocal];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int q0 = 0; q0 < nc; q0 += kMaxCoarseLocal) {   // coarse DOFs in chunks of 256
     T acc[kMaxCoarseLocal / 32];
 #pragma unroll
     for (int u = 0; u < kMaxCoarseLocal / 32; ++u) acc[u] = (T)0;
-    for (int c = warp; c < m.nG; c += 8) {
+#pragma unroll 4
+    for (int c = r0 + warp; c < r1; c += 8) {
       const T x = v[c];
       const T* row = P + (int64_t)c * nc + q0;
 #pragma unroll
@@ -492,16 +496,25 @@ __global__ void k_psi_t_apply(LevelDev L, const T* __restrict__ vec, double* __r
       }
     }
 #pragma unroll
-    for (int u = 0; u < kMaxCoarseLocal / 32; ++u) part[warp][lane + 32 * u] = acc[u];
+    for (int u = 0; u < kMaxCoarseLocal / 32; ++u) red[warp][lane + 32 * u] = acc[u];
     __syncthreads();
     for (int q = threadIdx.x; q < kMaxCoarseLocal && q0 + q < nc; q += blockDim.x) {
-      T t = (T)0;
+      double t = 0.0;
 #pragma unroll
-      for (int w = 0; w < 8; ++w) t += part[w][q];
-      rc_sub[m.c_off + q0 + q] = (double)t;
+      for (int w = 0; w < 8; ++w) t += (double)red[w][q];
+      part[(m.c_off + q0 + q) * kPsiSlices + z] = t;
     }
     __syncthreads();
   }
+}
+
+__global__ void k_psi_t_final(const double* __restrict__ part, int64_t total, double* __restrict__ rc_sub) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= total) return;
+  double t = 0.0;
+#pragma unroll
+  for (int z = 0; z < kPsiSlices; ++z) t += part[g * kPsiSlices + z];
+  rc_sub[g] = t;
 }
 
 // v_G += Psi_G zc_sub
@@ -572,8 +585,11 @@ void launch_constraint_corr(const LevelDev& L, T* vec, const int32_t* crow_sub, 
 }
 
 template <typename T>
-void launch_psi_t_apply(const LevelDev& L, const T* vec, double* rc_sub, cudaStream_t st) {
-  { note_launch(); k_psi_t_apply<T><<<(unsigned)L.n_sub, 256, 0, st>>>(L, vec, rc_sub); }
+void launch_psi_t_apply(const LevelDev& L, const T* vec, double* part, int64_t sum_nc, double* rc_sub,
+                        cudaStream_t st) {
+  if (sum_nc <= 0) return;
+  { note_launch(); k_psi_t_part<T><<<dim3(kPsiSlices, (unsigned)L.n_sub), 256, 0, st>>>(L, vec, part); }
+  { note_launch(); k_psi_t_final<<<(unsigned)((sum_nc + 255) / 256), 256, 0, st>>>(part, sum_nc, rc_sub); }
 }
 
 template <typename T>
@@ -587,7 +603,7 @@ void launch_psi_apply_add(const LevelDev& L, const double* zc_sub, T* vec, int m
   template void launch_psi<T>(const LevelDev&, int, int, cudaStream_t);                          \
   template void launch_constraint_corr<T>(const LevelDev&, T*, const int32_t*, int64_t, double*, double*, int, \
                                          cudaStream_t);                                                   \
-  template void launch_psi_t_apply<T>(const LevelDev&, const T*, double*, cudaStream_t);         \
+  template void launch_psi_t_apply<T>(const LevelDev&, const T*, double*, int64_t, double*, cudaStream_t); \
   template void launch_psi_apply_add<T>(const LevelDev&, const double*, T*, int, cudaStream_t);
 INST(float)
 INST(double)

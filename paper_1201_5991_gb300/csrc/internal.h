@@ -24,6 +24,7 @@
 namespace bddc {
 
 constexpr int NB = 64;            // tile edge
+constexpr int kPsiSlices = 8;     // interface-row slices per subdomain in the Psi^T product
 constexpr int64_t NB2 = NB * NB;
 
 struct SubMeta {
@@ -146,7 +147,8 @@ template <typename T>
 void launch_constraint_corr(const LevelDev& L, T* vec, const int32_t* crow_sub, int64_t total_rows, double* t,
                             double* mu, int max_nGb, cudaStream_t st);
 template <typename T>
-void launch_psi_t_apply(const LevelDev& L, const T* vec, double* rc_sub, cudaStream_t st);
+void launch_psi_t_apply(const LevelDev& L, const T* vec, double* part, int64_t sum_nc, double* rc_sub,
+                        cudaStream_t st);
 template <typename T>
 void launch_psi_apply_add(const LevelDev& L, const double* zc_sub, T* vec, int max_nG, cudaStream_t st);
 
