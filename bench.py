@@ -137,7 +137,7 @@ def traffic_ratio(cls):
     (profiles/trsv_sweep_traffic.json for the sweeps, profiles/trmv_schur_traffic.json for the
     factor products), or None when the kernel source changed since the counters were taken."""
     from paper_1201_5991_gb300 import capi
-    fname, src_name = (("trsv_sweep_traffic.json", "sweep.cu") if cls == capi.PROF_TRSV
+    fname, src_name = (("trsv_sweep_traffic.json", "sweep.cu") if cls in (capi.PROF_TRSV, capi.PROF_TRSV_IFACE)
                        else ("trmv_schur_traffic.json", "trmv.cu"))
     path = os.path.join(ROOT, "profiles", fname)
     try:
@@ -256,7 +256,7 @@ def run_gpu(args, rank, world, local_rank):
         times, stats = [], []
         launches0 = L.bddc_kernel_launches()
         prof = [0.0, 0, 0.0]
-        cls = {c: [0.0, 0, 0.0, 0.0] for c in (capi.PROF_TRSV, capi.PROF_FACTOR, capi.PROF_SPMV, capi.PROF_TRMV)}
+        cls = {c: [0.0, 0, 0.0, 0.0] for c in range(capi.PROF_CLASSES)}
         for _ in range(steps):
             flush.fill_(1.0)
             torch.cuda.synchronize()
@@ -277,7 +277,7 @@ def run_gpu(args, rank, world, local_rank):
             del s, u
         launches = (L.bddc_kernel_launches() - launches0) / max(steps, 1)
         # the roofline kernel: the streaming kernel class with the largest share of the step
-        dom = max((capi.PROF_TRSV, capi.PROF_TRMV), key=lambda c: cls[c][0])
+        dom = max((capi.PROF_TRSV, capi.PROF_TRSV_IFACE, capi.PROF_TRMV), key=lambda c: cls[c][0])
         prof = [cls[dom][0], cls[dom][1], cls[dom][2], dom, cls]
         torch.cuda.synchronize()
         barrier()
@@ -324,7 +324,10 @@ def run_gpu(args, rank, world, local_rank):
     dom, cls = prof[3], prof[4]
     ratio = traffic_ratio(dom)
     traffic = ratio * prof[2] / max(prof[1], 1) if ratio is not None else None
-    names = {capi.PROF_TRSV: "k_sweep<float> forward/backward (streaming triangular sweeps, TMA-staged tiles)",
+    names = {capi.PROF_TRSV: "k_sweep<float> forward/backward over interior block rows (Schur operator; "
+                             "streaming triangular sweeps, TMA-staged tiles)",
+             capi.PROF_TRSV_IFACE: "k_sweep<float> forward/backward over interface block rows (subdomain corrections)",
+             capi.PROF_COARSE: "k_sweep<double> forward/backward of the coarsest FP64 factor",
              capi.PROF_TRMV: "k_trmv_t + k_trmv_n (inner Schur operator: products with the stored interface factor)",
              capi.PROF_SPMV: "k_spmv (FP64 CSR products with K_i)",
              capi.PROF_FACTOR: "batched tiled factorisation (k_potrf_diag, k_trsm_panel, k_update_tc)"}
@@ -339,7 +342,8 @@ def run_gpu(args, rank, world, local_rank):
             e["frac_of_hbm"] = round(cb / (cms * 1e-3) / 1e9 / hbm, 4)
         if cf > 0:
             e["achieved_TFLOPs_fp32"] = round(cf / (cms * 1e-3) / 1e12, 2)
-        kernel_classes[{capi.PROF_TRSV: "trsv", capi.PROF_TRMV: "trmv", capi.PROF_SPMV: "spmv",
+        kernel_classes[{capi.PROF_TRSV: "trsv_interior", capi.PROF_TRSV_IFACE: "trsv_interface",
+                        capi.PROF_COARSE: "trsv_coarsest", capi.PROF_TRMV: "trmv", capi.PROF_SPMV: "spmv",
                         capi.PROF_FACTOR: "factor"}[c]] = e
     roofline = {
         "kernel": names[dom],
@@ -388,6 +392,10 @@ def run_gpu(args, rank, world, local_rank):
         "solve_ms": st0.solve_ms,
         "refine_steps": st0.refine_steps,
         "inner_steps": st0.inner_steps,
+        "autotuned_sweeps": {f"level{l + 1}_{'interior' if part == 0 else 'interface'}":
+                             {"ctas_per_sm": st0.sweep_ctas[2 * l + part], "deep_ring": st0.sweep_deep[2 * l + part],
+                              "longest_first": st0.sweep_order[2 * l + part]}
+                             for l in range(st0.n_levels) for part in range(2)},
         "outer_iterations": st0.outer_iterations,
         "kappa_estimate": (st0.lambda_max / st0.lambda_min if st0.lambda_min > 0 and prob.physics != 2
                            else None),

@@ -118,6 +118,9 @@ typedef struct {
                                BiCGstab (FP64) or flexible GMRES (mixed: FP32 factors of the
                                saddle points make the preconditioner inexact beyond what
                                BiCGstab's short recurrences tolerate) */
+  int autotune;             /* 1: time the sweep launch variants (CTAs per SM, tile-ring depth, task order)
+                               on every level at set-up and keep the fastest; results are cached per level
+                               shape for the life of the process.  0: fixed defaults */
 } bddc_opts;
 
 #define BDDC_KRYLOV_AUTO 0
@@ -126,11 +129,13 @@ typedef struct {
 #define BDDC_KRYLOV_FGMRES 3     /* right-preconditioned flexible GMRES(50) */
 
 /* kernel classes timed when bddc_opts.profile = 1 */
-#define BDDC_PROF_TRSV 0    /* streaming triangular sweeps (Schur operator and preconditioner) */
+#define BDDC_PROF_TRSV 0    /* streaming triangular sweeps over interior block rows (Schur operator) */
 #define BDDC_PROF_FACTOR 1  /* one step of the batched blocked Cholesky (diagonal, panel, update) */
 #define BDDC_PROF_SPMV 2    /* FP64 sparse products with K_i */
 #define BDDC_PROF_TRMV 3    /* inner Schur operator: products with the stored interface factor */
-#define BDDC_PROF_CLASSES 4
+#define BDDC_PROF_TRSV_IFACE 4   /* sweeps over interface block rows (subdomain corrections) */
+#define BDDC_PROF_COARSE 5  /* sweeps of the coarsest level's FP64 factor */
+#define BDDC_PROF_CLASSES 6
 
 typedef struct {
   int iterations;           /* Krylov iterations of the last solve (max over right-hand sides) */
@@ -154,6 +159,11 @@ typedef struct {
   int64_t prof_launches[BDDC_PROF_CLASSES];   /* launches per class */
   double prof_bytes[BDDC_PROF_CLASSES];       /* algorithmic bytes moved (TRSV, SPMV) */
   double prof_flops[BDDC_PROF_CLASSES];       /* algorithmic flops (FACTOR) */
+  /* sweep launch configuration per level l (index 2 (l-1) + part; part 0 interior, 1 interface) */
+  int sweep_ctas[2 * BDDC_MAX_LEVELS];        /* CTAs per SM of the persistent grid (1 or 2) */
+  int sweep_deep[2 * BDDC_MAX_LEVELS];        /* 1: deep tile ring (FP32 6 / FP64 3 stages), 0: shallow (4 / 2) */
+  int sweep_order[2 * BDDC_MAX_LEVELS];       /* 0: subdomain order, 1: longest chains first within each depth */
+  double tune_ms;                              /* time spent autotuning in the last set-up (0 when cached) */
 } bddc_stats;
 
 /* Index maps of one level, library-owned, valid until bddc_free (for bit-exact checks).

@@ -35,7 +35,7 @@ EXPORTED = [
     "bddc_get_stats", "bddc_sizes", "bddc_free", "bddc_last_error", "bddc_kernel_launches",
     "bddc_reset_profile", "bddc_grad_noalloc",
 ]
-PROF_TRSV, PROF_FACTOR, PROF_SPMV, PROF_TRMV, PROF_CLASSES = 0, 1, 2, 3, 4
+PROF_TRSV, PROF_FACTOR, PROF_SPMV, PROF_TRMV, PROF_TRSV_IFACE, PROF_COARSE, PROF_CLASSES = 0, 1, 2, 3, 4, 5, 6
 
 
 class Mesh(C.Structure):
@@ -60,7 +60,7 @@ class Opts(C.Structure):
         ("precision", C.c_int), ("weights", C.c_int), ("all_corners", C.c_uint), ("maxit", C.c_int),
         ("refine_steps", C.c_int), ("flexible", C.c_int), ("use_graph", C.c_int), ("verbose", C.c_int),
         ("profile", C.c_int), ("tensor_cores", C.c_int), ("inner_steps", C.c_int), ("inner_tol", C.c_double),
-        ("krylov", C.c_int),
+        ("krylov", C.c_int), ("autotune", C.c_int),
     ]
 
 
@@ -74,8 +74,10 @@ class Stats(C.Structure):
         ("refine_steps", C.c_int), ("inner_steps", C.c_int), ("outer_iterations", C.c_int),
         ("analysis_ms", C.c_double), ("factor_ms", C.c_double),
         ("solve_ms", C.c_double), ("factor_bytes", C.c_int64),
-        ("prof_ms", C.c_double * 4), ("prof_launches", C.c_int64 * 4), ("prof_bytes", C.c_double * 4),
-        ("prof_flops", C.c_double * 4),
+        ("prof_ms", C.c_double * PROF_CLASSES), ("prof_launches", C.c_int64 * PROF_CLASSES),
+        ("prof_bytes", C.c_double * PROF_CLASSES), ("prof_flops", C.c_double * PROF_CLASSES),
+        ("sweep_ctas", C.c_int * (2 * MAX_LEVELS)), ("sweep_deep", C.c_int * (2 * MAX_LEVELS)),
+        ("sweep_order", C.c_int * (2 * MAX_LEVELS)), ("tune_ms", C.c_double),
     ]
 
 

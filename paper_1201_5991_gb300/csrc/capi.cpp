@@ -5,11 +5,14 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
 #include <functional>
+#include <map>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <unordered_map>
@@ -99,8 +102,17 @@ struct Level {
   double trsv_bytes[2] = {0, 0};   // algorithmic bytes of one sweep over part 0 / part 1
   double trmv_bytes = 0;           // algorithmic bytes of one factor-based inner Schur product
   // sweep task lists [part][direction] in dependency order and their control words
-  int2* tasks[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  int2* tasks[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};       // [part][dir], subdomain order
+  int2* tasks_big[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [part][dir], longest chains first
   int ntasks[2][2] = {{0, 0}, {0, 0}};
+  // coarsest level of the mixed form: FP32 copy of the FP64 factor for the preconditioner's solves
+  bool solve32 = false;
+  LevelDev d32{};
+  float* v32 = nullptr;
+  // sweep launch configuration per part (autotuned): CTAs per SM, deep tile ring, task order
+  int sweep_ctas[2] = {2, 2};
+  int sweep_deep[2] = {1, 1};
+  int sweep_order[2] = {0, 0};
   int* ctrl = nullptr;
   int n_ctrl = 0;
   int64_t* rows[3] = {nullptr, nullptr, nullptr};   // interior rows, interface rows, all rows
@@ -693,24 +705,35 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
   d.status = h->d_status;
   // sweep tasks: block rows of all subdomains, interleaved by depth so that every task's
   // dependencies come earlier in the list
-  for (int part = 0; part < 2; ++part)
-    for (int dir = 0; dir < 2; ++dir) {
-      std::vector<int2> tl;
-      int depth = 0;
-      for (bool more = true; more; ++depth) {
-        more = false;
-        for (int64_t s = 0; s < ns; ++s) {
-          const SubMeta& m = L.meta[s];
-          const int B0 = part == 0 ? 0 : m.nIb, B1 = part == 0 ? m.nIb : m.Bc;
-          if (B0 + depth < B1) {
-            more = true;
-            tl.push_back(make_int2((int)s, dir == 0 ? B0 + depth : B1 - 1 - depth));
+  // (bucketing variant: within every depth the subdomains with the longest chains come first, so
+  // uneven subdomains start their critical paths earliest)
+  for (int part = 0; part < 2; ++part) {
+    std::vector<int64_t> by_len(ns);
+    for (int64_t s = 0; s < ns; ++s) by_len[s] = s;
+    std::stable_sort(by_len.begin(), by_len.end(), [&](int64_t a, int64_t b) {
+      const int la = part == 0 ? L.meta[a].nIb : L.meta[a].nGb, lb = part == 0 ? L.meta[b].nIb : L.meta[b].nGb;
+      return la > lb;
+    });
+    for (int order = 0; order < 2; ++order)
+      for (int dir = 0; dir < 2; ++dir) {
+        std::vector<int2> tl;
+        int depth = 0;
+        for (bool more = true; more; ++depth) {
+          more = false;
+          for (int64_t k = 0; k < ns; ++k) {
+            const int64_t s = order == 0 ? k : by_len[k];
+            const SubMeta& m = L.meta[s];
+            const int B0 = part == 0 ? 0 : m.nIb, B1 = part == 0 ? m.nIb : m.Bc;
+            if (B0 + depth < B1) {
+              more = true;
+              tl.push_back(make_int2((int)s, dir == 0 ? B0 + depth : B1 - 1 - depth));
+            }
           }
         }
+        L.ntasks[part][dir] = (int)tl.size();
+        (order == 0 ? L.tasks : L.tasks_big)[part][dir] = A.upload(tl, st);
       }
-      L.ntasks[part][dir] = (int)tl.size();
-      L.tasks[part][dir] = A.upload(tl, st);
-    }
+  }
   L.n_ctrl = (int)(1 + L.dinv_elems / NB2);
   L.ctrl = A.alloc<int>(L.n_ctrl);
   {
@@ -830,9 +853,11 @@ void reset_status(bddc_handle_s* h) {
 // ------------------------------------------------------------------ solve-phase building blocks
 template <typename T>
 void trsv_one(bddc_handle_s* h, Level& L, T* v, int part, int backward, cudaStream_t st) {
-  ProfScope ps(h, BDDC_PROF_TRSV, L.trsv_bytes[part], 0.0, st);
-  launch_sweep<T>(L.d, v, L.tasks[part][backward], L.ntasks[part][backward], part, backward, L.ctrl, L.n_ctrl,
-                  h->grid_max, st);
+  const bool copy32 = sizeof(T) == 4 && L.solve32;   // FP32 copy of an FP64 factor
+  ProfScope ps(h, L.coarsest ? BDDC_PROF_COARSE : part == 0 ? BDDC_PROF_TRSV : BDDC_PROF_TRSV_IFACE,
+               copy32 ? 0.5 * L.trsv_bytes[part] : L.trsv_bytes[part], 0.0, st);
+  launch_sweep<T>(copy32 ? L.d32 : L.d, v, (L.sweep_order[part] ? L.tasks_big : L.tasks)[part][backward], L.ntasks[part][backward],
+                  part, backward, L.ctrl, L.n_ctrl, h->grid_max / 2 * L.sweep_ctas[part], L.sweep_deep[part], st);
 }
 
 template <typename T>
@@ -916,6 +941,12 @@ void recover(bddc_handle_s* h, const double* f, const double* uG, double* u, cud
 
 void coarsest_solve(bddc_handle_s* h, const double* rC, double* zC, cudaStream_t st) {
   Level& C = h->lv.back();
+  if (C.solve32) {   // mixed form: the preconditioner's coarse solve with the FP32 copy of the factor
+    launch_gather_glob<float>(C.d32, rC, 2, C.v32, st);
+    trsv_pair<float>(h, C, C.v32, 0, st);
+    launch_scatter_interior<float>(C.d32, C.v32, zC, st);
+    return;
+  }
   double* v = (double*)C.locA;
   launch_gather_glob<double>(C.d, rC, 2, v, st);
   trsv_pair<double>(h, C, v, 0, st);
@@ -1030,10 +1061,86 @@ void choose_refinement(bddc_handle_s* h) {
   h->refine_steps = h->cur_steps = best;
 }
 
+// ------------------------------------------------------------------ autotuner
+// Launch variants of the streaming sweeps, timed with CUDA events on the level's own factors:
+// CTAs per SM of the persistent grid (1, 2), tile-ring depth (shallow, deep), task order (subdomain
+// order, longest chains first).  The sweeps compute the same result bit for bit in every variant
+// (each block row adds its tile contributions in a fixed order), so the choice only moves time.
+// Results are cached per level shape (precision, subdomain count, block-row histogram).
+std::mutex g_tune_mu;
+std::map<std::string, std::array<int, 6>> g_tune_cache;
+
+std::string level_shape_key(const Level& L) {
+  std::string k = (L.fp32 || L.solve32 ? "f" : "d") + std::to_string(L.meta.size()) + ":";
+  for (const SubMeta& m : L.meta) k += std::to_string(m.nIb) + "," + std::to_string(m.nGb) + ";";
+  return k;
+}
+
+template <typename T>
+void tune_sweeps(bddc_handle_s* h, Level& L, cudaStream_t st) {
+  const std::string key = level_shape_key(L);
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      for (int p = 0; p < 2; ++p) {
+        L.sweep_ctas[p] = it->second[3 * p];
+        L.sweep_deep[p] = it->second[3 * p + 1];
+        L.sweep_order[p] = it->second[3 * p + 2];
+      }
+      return;
+    }
+  }
+  const double t0 = now_ms();
+  const int saved_profile = h->opts.profile;
+  h->opts.profile = 0;
+  T* v = (sizeof(T) == 4 && L.solve32) ? (T*)L.v32 : (T*)L.locA;
+  ck(cudaMemsetAsync(v, 0, sizeof(T) * (size_t)L.n_vec, st), "memset");
+  cudaEvent_t a, b;
+  ck(cudaEventCreate(&a), "cudaEventCreate");
+  ck(cudaEventCreate(&b), "cudaEventCreate");
+  for (int p = 0; p < 2; ++p) {
+    if (L.ntasks[p][0] == 0) continue;
+    float best = 1e30f;
+    int bc = 2, bd = 1, bo = 0;
+    for (int order = 0; order < 2; ++order)
+      for (int deep = 1; deep >= 0; --deep)
+        for (int ctas = 2; ctas >= 1; --ctas) {
+          L.sweep_ctas[p] = ctas;
+          L.sweep_deep[p] = deep;
+          L.sweep_order[p] = order;
+          trsv_pair<T>(h, L, v, p, st);   // warm-up
+          ck(cudaEventRecord(a, st), "cudaEventRecord");
+          for (int r = 0; r < 2; ++r) trsv_pair<T>(h, L, v, p, st);
+          ck(cudaEventRecord(b, st), "cudaEventRecord");
+          ck(cudaEventSynchronize(b), "cudaEventSynchronize");
+          float ms = 0.f;
+          ck(cudaEventElapsedTime(&ms, a, b), "cudaEventElapsedTime");
+          if (ms < 0.97f * best) {   // a variant must win clearly to replace an earlier one
+            best = ms;
+            bc = ctas;
+            bd = deep;
+            bo = order;
+          }
+        }
+    L.sweep_ctas[p] = bc;
+    L.sweep_deep[p] = bd;
+    L.sweep_order[p] = bo;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  h->opts.profile = saved_profile;
+  h->stats.tune_ms += now_ms() - t0;
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  g_tune_cache[key] = {L.sweep_ctas[0], L.sweep_deep[0], L.sweep_order[0], L.sweep_ctas[1], L.sweep_deep[1],
+                       L.sweep_order[1]};
+}
+
 void numeric_setup(bddc_handle_s* h) {
   cudaStream_t st = h->st;
   const double t0 = now_ms();
   reset_status(h);
+  h->stats.tune_ms = 0.0;
   ck(cudaMemcpyAsync(h->d_coef, h->coef.data(), sizeof(double) * h->n_elems, cudaMemcpyHostToDevice, st), "coef");
   for (size_t l = 0; l < h->lv.size(); ++l) {
     Level& L = h->lv[l];
@@ -1056,6 +1163,33 @@ void numeric_setup(bddc_handle_s* h) {
     else
       factor_level<double>(h, L, st);
     check_status(h, (int)l + 1);
+    if (L.coarsest && h->opts.precision == BDDC_PREC_MIXED) {
+      // the coarsest factorisation stays FP64; its solves inside the FP32 preconditioner use an FP32
+      // copy (FP64 arithmetic on GB300 runs at 1/64 of FP32 and made these short sweeps compute-bound)
+      if (!L.solve32) {
+        L.d32 = L.d;
+        L.d32.tiles = h->arena.alloc<float>(L.tile_elems);
+        L.d32.dinv = h->arena.alloc<float>(L.dinv_elems);
+        L.d32.sgn = h->arena.alloc<float>(L.n_vec);
+        L.v32 = h->arena.alloc<float>(L.n_vec);
+        L.solve32 = true;
+      }
+      launch_convert<double, float>((const double*)L.d.tiles, (float*)L.d32.tiles, L.tile_elems, st);
+      launch_convert<double, float>((const double*)L.d.dinv, (float*)L.d32.dinv, L.dinv_elems, st);
+      launch_convert<double, float>((const double*)L.d.sgn, (float*)L.d32.sgn, L.n_vec, st);
+    }
+    if (h->opts.autotune) {
+      if (L.fp32 || L.solve32)
+        tune_sweeps<float>(h, L, st);
+      else
+        tune_sweeps<double>(h, L, st);
+      check_status(h, (int)l + 1);
+    }
+    for (int p = 0; p < 2; ++p) {
+      h->stats.sweep_ctas[2 * l + p] = L.sweep_ctas[p];
+      h->stats.sweep_deep[2 * l + p] = L.sweep_deep[p];
+      h->stats.sweep_order[2 * l + p] = L.sweep_order[p];
+    }
   }
   choose_refinement(h);
   ck(cudaStreamSynchronize(st), "sync");
@@ -1848,6 +1982,7 @@ void bddc_default_opts(bddc_opts* o) {
   o->verbose = 0;
   o->profile = 0;
   o->tensor_cores = 1;
+  o->autotune = 1;
 }
 
 int bddc_analyze(const bddc_mesh* mesh, const bddc_partition* part, unsigned constraints, const bddc_opts* opts,

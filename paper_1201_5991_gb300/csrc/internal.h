@@ -141,7 +141,7 @@ void launch_psi(const LevelDev& L, int max_nGb, int max_nc, cudaStream_t st);
 // block rows) or part 1 (interface block rows) of every subdomain; ctrl has n_ctrl ints.
 template <typename T>
 void launch_sweep(const LevelDev& L, T* vec, const int2* tasks, int ntasks, int part, int backward, int* ctrl,
-                  int n_ctrl, int grid_max, cudaStream_t st);
+                  int n_ctrl, int grid_max, int deep, cudaStream_t st);
 // crow_sub: subdomain of every constraint row (flat over the level); t, mu: scratch [total_rows]
 template <typename T>
 void launch_constraint_corr(const LevelDev& L, T* vec, const int32_t* crow_sub, int64_t total_rows, double* t,

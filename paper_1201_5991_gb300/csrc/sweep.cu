@@ -299,11 +299,9 @@ __global__ void __launch_bounds__(kThreads, 2)
 
 // Task lists and control words live in the level (see capi.cpp); this entry launches one
 // sweep.  ctrl = [counter, flags...] must be zeroed before the launch (memset in the stream).
-template <typename T>
-void launch_sweep(const LevelDev& L, T* vec, const int2* tasks, int ntasks, int part, int backward, int* ctrl,
-                  int n_ctrl, int grid_max, cudaStream_t st) {
-  if (ntasks <= 0) return;
-  constexpr int S = sizeof(T) == 4 ? 6 : 3;
+template <typename T, int S>
+void launch_sweep_s(const LevelDev& L, T* vec, const int2* tasks, int ntasks, int part, int backward, int* ctrl,
+                    int grid, cudaStream_t st) {
   const size_t dyn = (size_t)S * NB2 * sizeof(T);
   static bool attr = false;
   if (!attr) {
@@ -311,8 +309,6 @@ void launch_sweep(const LevelDev& L, T* vec, const int2* tasks, int ntasks, int 
     cudaFuncSetAttribute(k_sweep<T, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     attr = true;
   }
-  cudaMemsetAsync(ctrl, 0, sizeof(int) * (size_t)n_ctrl, st);
-  const int grid = ntasks < grid_max ? ntasks : grid_max;
   note_launch();
   if (backward)
     k_sweep<T, S, true><<<grid, kThreads, dyn, st>>>(L, vec, tasks, ntasks, part, ctrl);
@@ -320,7 +316,29 @@ void launch_sweep(const LevelDev& L, T* vec, const int2* tasks, int ntasks, int 
     k_sweep<T, S, false><<<grid, kThreads, dyn, st>>>(L, vec, tasks, ntasks, part, ctrl);
 }
 
-template void launch_sweep<float>(const LevelDev&, float*, const int2*, int, int, int, int*, int, int, cudaStream_t);
-template void launch_sweep<double>(const LevelDev&, double*, const int2*, int, int, int, int*, int, int, cudaStream_t);
+// deep: the longer tile ring (FP32: 6 stages, FP64: 3); shallow: FP32 4, FP64 2
+template <typename T>
+void launch_sweep(const LevelDev& L, T* vec, const int2* tasks, int ntasks, int part, int backward, int* ctrl,
+                  int n_ctrl, int grid_max, int deep, cudaStream_t st) {
+  if (ntasks <= 0) return;
+  cudaMemsetAsync(ctrl, 0, sizeof(int) * (size_t)n_ctrl, st);
+  const int grid = ntasks < grid_max ? ntasks : grid_max;
+  if (sizeof(T) == 4) {
+    if (deep)
+      launch_sweep_s<T, 6>(L, vec, tasks, ntasks, part, backward, ctrl, grid, st);
+    else
+      launch_sweep_s<T, 4>(L, vec, tasks, ntasks, part, backward, ctrl, grid, st);
+  } else {
+    if (deep)
+      launch_sweep_s<T, 3>(L, vec, tasks, ntasks, part, backward, ctrl, grid, st);
+    else
+      launch_sweep_s<T, 2>(L, vec, tasks, ntasks, part, backward, ctrl, grid, st);
+  }
+}
+
+template void launch_sweep<float>(const LevelDev&, float*, const int2*, int, int, int, int*, int, int, int,
+                                  cudaStream_t);
+template void launch_sweep<double>(const LevelDev&, double*, const int2*, int, int, int, int*, int, int, int,
+                                   cudaStream_t);
 
 }  // namespace bddc

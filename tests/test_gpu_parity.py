@@ -177,9 +177,11 @@ def test_graph_iteration_matches_eager_and_profiles():
     st = s.stats()
     # every inner iteration sweeps the interface rows forward and backward (preconditioner)
     # and applies the factor-based Schur operator once
-    assert st.prof_launches[capi.PROF_TRSV] >= 2 * st.iterations
+    assert st.prof_launches[capi.PROF_TRSV_IFACE] >= 2 * st.iterations
     assert st.prof_launches[capi.PROF_TRMV] >= st.iterations
-    assert st.prof_ms[capi.PROF_TRSV] > 0 and st.prof_ms[capi.PROF_TRMV] > 0
+    assert st.prof_launches[capi.PROF_COARSE] >= 2 * st.iterations
+    assert st.prof_launches[capi.PROF_TRSV] > 0   # FP64 operator of the outer iteration
+    assert st.prof_ms[capi.PROF_TRSV_IFACE] > 0 and st.prof_ms[capi.PROF_TRMV] > 0
 
 
 @pytest.mark.parametrize("inner", [-1, 0, 1, 2])
@@ -198,3 +200,21 @@ def test_outer_refinement_variants_match_direct_solve(inner):
         assert st.outer_iterations == 0 and st.inner_steps == -1
     elif inner < st.refine_steps:
         assert st.outer_iterations >= 2 and st.inner_steps == inner
+
+
+def test_autotuned_sweeps_are_bitwise_equal_to_defaults():
+    # the tuner only picks launch variants (CTAs per SM, tile-ring depth, task order) of sweeps
+    # whose per-row summation order is fixed, so the solution must not change in any bit
+    p = meshgen.elasticity3d_kmeans(12, 20, 4, seed=3, seed2=33)   # uneven subdomains, 3 levels
+    f = _dev(p.f[:, 0])
+    a = BddcSolver(p, precision="mixed", autotune=0)
+    ua = a.solve(f, tol=1e-10).cpu().numpy()
+    b = BddcSolver(p, precision="mixed", autotune=1)
+    ub = b.solve(f, tol=1e-10).cpu().numpy()
+    np.testing.assert_array_equal(ua, ub)
+    st = b.last_stats
+    for l in range(st.n_levels):
+        for part in range(2):
+            k = 2 * l + part
+            assert st.sweep_ctas[k] in (1, 2) and st.sweep_deep[k] in (0, 1) and st.sweep_order[k] in (0, 1)
+    assert all(a.last_stats.sweep_ctas[k] == 2 and a.last_stats.sweep_deep[k] == 1 for k in range(2 * st.n_levels))
