@@ -386,8 +386,9 @@ def run_gpu(args, rank, world, local_rank):
         "time_to_1e-8_ms": ms,
         "iterations": st0.iterations,
         "rel_residual": st0.rel_residual,
-        "setup_ms": st0.analysis_ms + st0.factor_ms,
+        "setup_ms": st0.analysis_ms + st0.prepare_ms + st0.factor_ms,
         "analysis_ms": st0.analysis_ms,
+        "prepare_ms": st0.prepare_ms,
         "factor_ms": st0.factor_ms,
         "solve_ms": st0.solve_ms,
         "refine_steps": st0.refine_steps,
@@ -401,7 +402,7 @@ def run_gpu(args, rank, world, local_rank):
                            else None),
         "plain_fp64": None if st64 is None else {
             "value": prob.n_free * world / (ms64 * 1e-3), "ms_per_step": ms64, "steps": pk,
-            "iterations": st64.iterations, "setup_ms": st64.analysis_ms + st64.factor_ms,
+            "iterations": st64.iterations, "setup_ms": st64.analysis_ms + st64.prepare_ms + st64.factor_ms,
             "solve_ms": st64.solve_ms, "speedup_mixed_vs_plain": ms64 / ms},
         "e2e": {"value": prob.n_free * world / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": int(prob.n_free * 8 + mesh_bytes), "d2h_bytes_per_step": int(prob.n_free * 8)},

@@ -164,6 +164,8 @@ typedef struct {
   int sweep_deep[2 * BDDC_MAX_LEVELS];        /* 1: deep tile ring (FP32 6 / FP64 3 stages), 0: shallow (4 / 2) */
   int sweep_order[2 * BDDC_MAX_LEVELS];       /* 0: subdomain order, 1: longest chains first within each depth */
   double tune_ms;                              /* time spent autotuning in the last set-up (0 when cached) */
+  double prepare_ms;                           /* device set-up of the last bddc_setup: level layouts, maps,
+                                                  allocations and uploads (between analysis and factor) */
 } bddc_stats;
 
 /* Index maps of one level, library-owned, valid until bddc_free (for bit-exact checks).

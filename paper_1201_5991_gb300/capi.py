@@ -77,7 +77,7 @@ class Stats(C.Structure):
         ("prof_ms", C.c_double * PROF_CLASSES), ("prof_launches", C.c_int64 * PROF_CLASSES),
         ("prof_bytes", C.c_double * PROF_CLASSES), ("prof_flops", C.c_double * PROF_CLASSES),
         ("sweep_ctas", C.c_int * (2 * MAX_LEVELS)), ("sweep_deep", C.c_int * (2 * MAX_LEVELS)),
-        ("sweep_order", C.c_int * (2 * MAX_LEVELS)), ("tune_ms", C.c_double),
+        ("sweep_order", C.c_int * (2 * MAX_LEVELS)), ("tune_ms", C.c_double), ("prepare_ms", C.c_double),
     ]
 
 

@@ -384,6 +384,70 @@ void launch_lift(int64_t n_free, int ne, const int64_t* lptr, const int32_t* lsl
   k_lift<<<(unsigned)((n_free + 7) / 8), 256, 0, st>>>(n_free, ne, lptr, lslot, la, ke, ud, lift);
 }
 
+// CSR pattern of K_i on the device: one warp per padded local row marks, in a per-warp bitmap
+// over the subdomain's padded positions, the positions of every element containing the row;
+// the set bits, read in ascending order, are the row's columns.  Pass 1 (cnt != null) counts,
+// pass 2 (col != null) writes at row_ptr.
+__global__ void k_csr_pattern(LevelDev L, int64_t n_rows, const int32_t* __restrict__ row_sub, int words,
+                              int32_t* __restrict__ cnt, const int64_t* __restrict__ row_ptr, int32_t* __restrict__ col) {
+  extern __shared__ uint32_t bm_all[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (row >= n_rows) return;
+  uint32_t* bm = bm_all + (size_t)warp * words;
+  const SubMeta m = L.meta[row_sub[row]];
+  const int nw = (m.Bc * NB + 31) >> 5;
+  for (int w = lane; w < nw; w += 32) bm[w] = 0u;
+  __syncwarp();
+  for (int64_t c = L.rc_ptr[row]; c < L.rc_ptr[row + 1]; ++c) {
+    const int64_t k = L.rc_elem[c];
+    for (int64_t t = L.ed_off[k] + lane; t < L.ed_off[k + 1]; t += 32) {
+      const int32_t p = L.eldof[t];
+      if (p >= 0) atomicOr(&bm[p >> 5], 1u << (p & 31));
+    }
+  }
+  __syncwarp();
+  if (cnt) {
+    int tot = 0;
+    for (int w = lane; w < nw; w += 32) tot += __popc(bm[w]);
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    if (lane == 0) cnt[row] = tot;
+    return;
+  }
+  int64_t out = row_ptr[row];
+  for (int w0 = 0; w0 < nw; w0 += 32) {
+    const int w = w0 + lane;
+    uint32_t bits = w < nw ? bm[w] : 0u;
+    const int pc = __popc(bits);
+    int pre = pc;   // inclusive prefix over the lanes
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, pre, o);
+      if (lane >= o) pre += v;
+    }
+    int64_t dst = out + (pre - pc);
+    while (bits) {
+      const int b = __ffs(bits) - 1;
+      col[dst++] = (int32_t)(w * 32 + b);
+      bits &= bits - 1;
+    }
+    out += __shfl_sync(0xffffffffu, pre, 31);
+  }
+}
+
+void launch_csr_pattern(const LevelDev& L, int64_t n_rows, const int32_t* row_sub, int max_len, int32_t* cnt,
+                        const int64_t* row_ptr, int32_t* col, cudaStream_t st) {
+  if (n_rows <= 0) return;
+  const int words = (max_len + 31) / 32;
+  const size_t sm = (size_t)8 * words * sizeof(uint32_t);
+  static size_t attr = 0;
+  if (sm > 48 * 1024 && sm > attr) {
+    cudaFuncSetAttribute(k_csr_pattern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    attr = sm;
+  }
+  note_launch();
+  k_csr_pattern<<<(unsigned)((n_rows + 7) / 8), 256, sm, st>>>(L, n_rows, row_sub, words, cnt, row_ptr, col);
+}
+
 void launch_csr_values(const LevelDev& L, int64_t n_rows_total, const int32_t* row_sub, cudaStream_t st) {
   (void)n_rows_total;
   if (L.n_vec <= 0) return;

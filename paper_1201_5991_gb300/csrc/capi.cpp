@@ -55,14 +55,40 @@ double now_ms() {
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 // ------------------------------------------------------------------ device memory helpers
+// The library's device memory comes from one private stream-ordered pool per device whose
+// release threshold keeps freed blocks cached: a handle set up after another one was freed (a
+// new mesh, new coefficients through a fresh set-up) reuses them instead of paying for
+// cudaMalloc of several GB again.  The device's default pool is left untouched.
+cudaMemPool_t library_pool() {
+  static std::mutex mu;
+  static std::unordered_map<int, cudaMemPool_t> pools;
+  int dev = 0;
+  ck(cudaGetDevice(&dev), "cudaGetDevice");
+  std::lock_guard<std::mutex> g(mu);
+  auto it = pools.find(dev);
+  if (it != pools.end()) return it->second;
+  cudaMemPoolProps props{};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.handleTypes = cudaMemHandleTypeNone;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t pool = nullptr;
+  ck(cudaMemPoolCreate(&pool, &props), "cudaMemPoolCreate");
+  uint64_t keep = ~0ull;
+  ck(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep), "cudaMemPoolSetAttribute");
+  pools[dev] = pool;
+  return pool;
+}
+
 struct DevArena {
   std::vector<void*> ptrs;
   int64_t bytes = 0;
+  cudaStream_t st = nullptr;   // allocations and frees are ordered on the handle's stream
   template <typename T>
   T* alloc(int64_t n) {
     if (n <= 0) n = 1;
     void* p = nullptr;
-    ck(cudaMalloc(&p, sizeof(T) * (size_t)n), "cudaMalloc");
+    ck(cudaMallocFromPoolAsync(&p, sizeof(T) * (size_t)n, library_pool(), st), "cudaMallocFromPoolAsync");
     ptrs.push_back(p);
     bytes += (int64_t)sizeof(T) * n;
     return (T*)p;
@@ -74,7 +100,8 @@ struct DevArena {
     return p;
   }
   void release() {
-    for (void* p : ptrs) cudaFree(p);
+    for (void* p : ptrs) cudaFreeAsync(p, st);
+    if (!ptrs.empty()) cudaStreamSynchronize(st);
     ptrs.clear();
     bytes = 0;
   }
@@ -543,46 +570,6 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
         }
     }
   }
-  std::vector<std::vector<int32_t>> sub_cols(ns);
-  std::vector<std::vector<int64_t>> sub_rowlen(ns);
-  parallel_for(ns, [&](int64_t s) {
-    const SubMeta& m = L.meta[s];
-    const int64_t nr = (int64_t)m.Bc * NB;
-    std::vector<int64_t> stamp(nr, -1);
-    std::vector<int32_t> cols;
-    auto& out = sub_cols[s];
-    auto& len = sub_rowlen[s];
-    len.assign(nr, 0);
-    for (int64_t r = 0; r < nr; ++r) {
-      cols.clear();
-      const int64_t row = m.vec_off + r;
-      for (int64_t c = rc_ptr[row]; c < rc_ptr[row + 1]; ++c) {
-        int64_t k = rc_elem[c];
-        for (int64_t t = ed_off[k]; t < ed_off[k + 1]; ++t) {
-          int32_t col = eldof[t];
-          if (col >= 0 && stamp[col] != r) {
-            stamp[col] = r;
-            cols.push_back(col);
-          }
-        }
-      }
-      std::sort(cols.begin(), cols.end());
-      len[r] = (int64_t)cols.size();
-      out.insert(out.end(), cols.begin(), cols.end());
-    }
-  });
-  std::vector<int64_t> row_ptr(L.n_vec + 1, 0);
-  for (int64_t s = 0; s < ns; ++s) {
-    const SubMeta& m = L.meta[s];
-    for (int64_t r = 0; r < (int64_t)m.Bc * NB; ++r) row_ptr[m.vec_off + r + 1] = sub_rowlen[s][r];
-  }
-  for (int64_t r = 0; r < L.n_vec; ++r) row_ptr[r + 1] += row_ptr[r];
-  std::vector<int32_t> col(row_ptr[L.n_vec]);
-  for (int64_t s = 0; s < ns; ++s) {
-    const SubMeta& m = L.meta[s];
-    std::copy(sub_cols[s].begin(), sub_cols[s].end(), col.begin() + row_ptr[m.vec_off]);
-  }
-  sub_cols.clear();
   // constraint rows over padded positions
   std::vector<int64_t> c_ptr(mp.c_ptr.size());
   std::vector<int32_t> c_pos(mp.c_col.size());
@@ -623,9 +610,6 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
   d.n_coarse = mp.n_coarse;
   d.n_vec = L.n_vec;
   d.meta = A.upload(L.meta, st);
-  d.row_ptr = A.upload(row_ptr, st);
-  d.col = A.upload(col, st);
-  d.val = A.alloc<double>(row_ptr[L.n_vec]);
   d.ke_off = A.upload(ke_off, st);
   d.ed_off = A.upload(ed_off, st);
   d.eldof = A.upload(eldof, st);
@@ -633,6 +617,26 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
   d.rc_ptr = A.upload(rc_ptr, st);
   d.rc_elem = A.upload(rc_elem, st);
   d.rc_a = A.upload(rc_a, st);
+  {
+    // CSR pattern of every K_i over padded positions, built on the device: per row the union of
+    // the local positions of the elements containing it (ascending)
+    int max_len = 0;
+    for (const SubMeta& m : L.meta) max_len = std::max(max_len, m.Bc * NB);
+    if ((size_t)8 * ((max_len + 31) / 32) * 4 > 227 * 1024)
+      fail(BDDC_ERR_INVALID, "a subdomain has more than 58,000 local DOFs (dense local factors are not built for that)");
+    L.row_sub = A.upload(row_sub, st);
+    int32_t* cnt = A.alloc<int32_t>(L.n_vec);
+    launch_csr_pattern(d, L.n_vec, L.row_sub, max_len, cnt, nullptr, nullptr, st);
+    std::vector<int32_t> hc(L.n_vec);
+    if (L.n_vec > 0) ck(cudaMemcpyAsync(hc.data(), cnt, sizeof(int32_t) * L.n_vec, cudaMemcpyDeviceToHost, st), "d2h");
+    ck(cudaStreamSynchronize(st), "sync");
+    std::vector<int64_t> row_ptr(L.n_vec + 1, 0);
+    for (int64_t r = 0; r < L.n_vec; ++r) row_ptr[r + 1] = row_ptr[r] + hc[r];
+    d.row_ptr = A.upload(row_ptr, st);
+    d.col = A.alloc<int32_t>(row_ptr[L.n_vec]);
+    d.val = A.alloc<double>(row_ptr[L.n_vec]);
+    launch_csr_pattern(d, L.n_vec, L.row_sub, max_len, nullptr, d.row_ptr, (int32_t*)d.col, st);
+  }
   d.c_ptr = A.upload(c_ptr, st);
   d.c_pos = A.upload(c_pos, st);
   d.c_val = A.upload(mp.c_val, st);
@@ -755,7 +759,6 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
     L.cc_t = A.alloc<double>(L.sum_nc);
     L.cc_mu = A.alloc<double>(L.sum_nc);
   }
-  L.row_sub = A.upload(row_sub, st);
   L.slot_elem = A.upload(slot_elem, st);
   L.iface_dofs = A.upload(mp.iface_dofs, st);
   L.dl0 = A.alloc<double>(L.n_vec);
@@ -1293,6 +1296,7 @@ void analysis(bddc_handle_s* h, const bddc_mesh* mesh, const bddc_partition* par
 }
 
 void device_setup(bddc_handle_s* h) {
+  const double t0 = now_ms();
   cudaStream_t st = h->st;
   DevArena& A = h->arena;
   {
@@ -1397,6 +1401,7 @@ void device_setup(bddc_handle_s* h) {
   h->full_a = A.alloc<double>(nbig);
   h->full_b = A.alloc<double>(nbig);
   ck(cudaStreamSynchronize(st), "sync");
+  h->stats.prepare_ms = now_ms() - t0;
 }
 
 // ------------------------------------------------------------------ PCG (Sec. 4)
@@ -2015,6 +2020,7 @@ int bddc_setup(const bddc_mesh* mesh, const bddc_partition* part, unsigned const
     if (h->opts.maxit <= 0) h->opts.maxit = 500;
     h->constraints = constraints;
     h->st = (cudaStream_t)stream;
+    h->arena.st = h->st;
     try {
       analysis(h, mesh, part);
       device_setup(h);

@@ -112,6 +112,9 @@ void launch_elem_q2q1(int64_t n_elems, const double* coords, const int32_t* conn
                       const int32_t* slot_elem, double* ke, cudaStream_t st);
 void launch_lift(int64_t n_free, int ne, const int64_t* lptr, const int32_t* lslot, const int32_t* la,
                  const double* ke, const double* ud, double* lift, cudaStream_t st);
+// CSR pattern of K_i (pass 1: cnt[row] = row length; pass 2: col at row_ptr)
+void launch_csr_pattern(const LevelDev& L, int64_t n_rows, const int32_t* row_sub, int max_len, int32_t* cnt,
+                        const int64_t* row_ptr, int32_t* col, cudaStream_t st);
 void launch_csr_values(const LevelDev& L, int64_t n_rows_total, const int32_t* row_sub, cudaStream_t st);
 template <typename T>
 void launch_densify_rows(const LevelDev& L, const int32_t* row_sub, cudaStream_t st);
