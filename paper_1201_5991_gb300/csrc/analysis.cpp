@@ -15,8 +15,11 @@
 #include "analysis.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <functional>
 #include <numeric>
+#include <thread>
 #include <unordered_map>
 
 namespace bddc {
@@ -61,6 +64,22 @@ double cross_norm(const Pt& p, const Pt& o, const double* u) {
   return std::sqrt(c0 * c0 + c1 * c1 + c2 * c2);
 }
 
+// fn(i) for i in [0, n) on up to 16 host threads (independent iterations)
+void parallel_range(int64_t n, const std::function<void(int64_t)>& fn) {
+  const unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  if (n < 4 || nt == 1) {
+    for (int64_t i = 0; i < n; ++i) fn(i);
+    return;
+  }
+  std::atomic<int64_t> next{0};
+  std::vector<std::thread> th;
+  for (unsigned t = 0; t < nt; ++t)
+    th.emplace_back([&]() {
+      for (int64_t i; (i = next.fetch_add(1)) < n;) fn(i);
+    });
+  for (auto& t : th) t.join();
+}
+
 }  // namespace
 
 bool analyze_level(const LevelMesh& mesh, unsigned constraints, bool all_corners, LevelMaps* out,
@@ -96,23 +115,21 @@ bool analyze_level(const LevelMesh& mesh, unsigned constraints, bool all_corners
     for (int64_t e = 0; e < ne; ++e) m.sub_elems[fill[mesh.part[e]]++] = e;
   }
   // subdomain -> nodes (sorted unique)
+  for (int64_t q = 0; q < (int64_t)mesh.en.size(); ++q)
+    if (mesh.en[q] < 0 || mesh.en[q] >= nn) {
+      *err = "node id out of range in element connectivity entry " + std::to_string(q);
+      return false;
+    }
   std::vector<std::vector<int64_t>> sub_nodes(ns);
-  for (int64_t s = 0; s < ns; ++s) {
+  parallel_range(ns, [&](int64_t s) {
     auto& v = sub_nodes[s];
     for (int64_t k = m.sub_elem_ptr[s]; k < m.sub_elem_ptr[s + 1]; ++k) {
       int64_t e = m.sub_elems[k];
-      for (int64_t q = mesh.en_ptr[e]; q < mesh.en_ptr[e + 1]; ++q) {
-        int64_t p = mesh.en[q];
-        if (p < 0 || p >= nn) {
-          *err = "node id out of range in element " + std::to_string(e);
-          return false;
-        }
-        v.push_back(p);
-      }
+      for (int64_t q = mesh.en_ptr[e]; q < mesh.en_ptr[e + 1]; ++q) v.push_back(mesh.en[q]);
     }
     std::sort(v.begin(), v.end());
     v.erase(std::unique(v.begin(), v.end()), v.end());
-  }
+  });
   // node -> sharing set (ascending subdomain ids)
   m.node_sub_ptr.assign(nn + 1, 0);
   for (int64_t s = 0; s < ns; ++s)
@@ -378,71 +395,96 @@ bool analyze_level(const LevelMesh& mesh, unsigned constraints, bool all_corners
   std::vector<int64_t> iface_pos(mesh.n_dof, -1);
   for (int64_t k = 0; k < m.n_iface; ++k) iface_pos[m.iface_dofs[k]] = k;
 
-  // per-subdomain local orderings, weights, constraint rows
-  std::vector<int64_t> loc(mesh.n_dof, -1);
-  std::vector<double> mult(mesh.n_dof, 0.0);
-  m.sub_dof_ptr.assign(1, 0);
-  m.sub_coarse_ptr.assign(1, 0);
-  m.c_ptr.assign(1, 0);
-  std::vector<int64_t> interior, inter;
-  for (int64_t s = 0; s < ns; ++s) {
-    interior.clear();
-    inter.clear();
-    // sort key: DOFs of the last component (Stokes pressures) after the others, then id
-    const int64_t shift = (int64_t)1 << 40;
+  // per-subdomain local orderings, weights, constraint rows (computed per subdomain in
+  // parallel, then concatenated in subdomain order)
+  std::vector<int64_t> dof_node(mesh.n_dof, -1);
+  for (int64_t p = 0; p < nn; ++p)
+    for (int64_t q = mesh.nd_ptr[p]; q < mesh.nd_ptr[p + 1]; ++q)
+      if (mesh.nd_id[q] >= 0) dof_node[mesh.nd_id[q]] = p;
+  struct SubOut {
+    std::vector<int64_t> interior, inter, coarse, crow_len, ccol;
+  };
+  std::vector<SubOut> so(ns);
+  // sort key: DOFs of the last component (Stokes pressures) after the others, then id
+  const int64_t shift = (int64_t)1 << 40;
+  auto key_of = [&](int64_t q) { return mesh.nd_id[q] + (mesh.nd_comp[q] == mesh.last_comp ? shift : 0); };
+  parallel_range(ns, [&](int64_t s) {
+    SubOut& o = so[s];
     for (int64_t p : sub_nodes[s])
       for (int64_t q = mesh.nd_ptr[p]; q < mesh.nd_ptr[p + 1]; ++q) {
-        int64_t d = mesh.nd_id[q];
-        if (d < 0) continue;
-        const int64_t key = d + (mesh.nd_comp[q] == mesh.last_comp ? shift : 0);
-        if (iface[p]) {
-          inter.push_back(key);
-          mult[d] = 1.0 / (double)nsh(p);
-        } else {
-          interior.push_back(key);
-        }
+        if (mesh.nd_id[q] < 0) continue;
+        (iface[p] ? o.inter : o.interior).push_back(key_of(q));
       }
-    std::sort(interior.begin(), interior.end());
-    std::sort(inter.begin(), inter.end());
-    for (auto& k : interior) k %= shift;
-    for (auto& k : inter) k %= shift;
-    int64_t base = (int64_t)m.sub_dofs.size();
-    for (int64_t d : interior) {
-      loc[d] = (int64_t)m.sub_dofs.size() - base;
-      m.sub_dofs.push_back(d);
-      m.sub_iface.push_back(-1);
-      m.sub_wmult.push_back(0.0);
-    }
-    for (int64_t d : inter) {
-      loc[d] = (int64_t)m.sub_dofs.size() - base;
-      m.sub_dofs.push_back(d);
-      m.sub_iface.push_back(iface_pos[d]);
-      m.sub_wmult.push_back(mult[d]);
-    }
-    m.sub_nI.push_back((int64_t)interior.size());
-    m.sub_dof_ptr.push_back((int64_t)m.sub_dofs.size());
-    // constraint rows: globs touching s in glob order -> ascending coarse ids
+    std::sort(o.interior.begin(), o.interior.end());
+    std::sort(o.inter.begin(), o.inter.end());
+    const int64_t nI = (int64_t)o.interior.size();
+    // constraint rows: globs touching s in glob order -> ascending coarse ids; their DOFs are
+    // interface DOFs, found in the sorted interface keys
     std::vector<int64_t> gl = sub_globs[s];
     std::sort(gl.begin(), gl.end());
-    for (int64_t g : gl) {
+    for (int64_t g : gl)
       for (int64_t k = m.glob_coarse_ptr[g]; k < m.glob_coarse_ptr[g + 1]; ++k) {
-        int c = m.coarse_comp[k];
-        m.sub_coarse.push_back(k);
-        int64_t first = (int64_t)m.c_col.size();
+        const int c = m.coarse_comp[k];
+        o.coarse.push_back(k);
+        const int64_t first = (int64_t)o.ccol.size();
         for (int64_t t = m.glob_ptr[g]; t < m.glob_ptr[g + 1]; ++t) {
-          int64_t p = m.glob_nodes[t];
+          const int64_t p = m.glob_nodes[t];
           for (int64_t q = mesh.nd_ptr[p]; q < mesh.nd_ptr[p + 1]; ++q)
-            if (mesh.nd_comp[q] == c && mesh.nd_id[q] >= 0) m.c_col.push_back(loc[mesh.nd_id[q]]);
+            if (mesh.nd_comp[q] == c && mesh.nd_id[q] >= 0) {
+              const int64_t key = key_of(q);
+              const int64_t pos = std::lower_bound(o.inter.begin(), o.inter.end(), key) - o.inter.begin();
+              o.ccol.push_back(nI + pos);
+            }
         }
-        int64_t cnt = (int64_t)m.c_col.size() - first;
-        for (int64_t t = 0; t < cnt; ++t) m.c_val.push_back(1.0 / (double)cnt);
-        m.c_ptr.push_back((int64_t)m.c_col.size());
+        o.crow_len.push_back((int64_t)o.ccol.size() - first);
       }
-    }
-    m.sub_coarse_ptr.push_back((int64_t)m.sub_coarse.size());
-    for (int64_t d : interior) loc[d] = -1;
-    for (int64_t d : inter) loc[d] = -1;
+    for (auto& k : o.interior) k %= shift;
+    for (auto& k : o.inter) k %= shift;
+  });
+  // offsets, then every subdomain's block filled in parallel
+  m.sub_dof_ptr.assign(ns + 1, 0);
+  m.sub_coarse_ptr.assign(ns + 1, 0);
+  std::vector<int64_t> ccol_off(ns + 1, 0);
+  m.sub_nI.resize(ns);
+  for (int64_t s = 0; s < ns; ++s) {
+    m.sub_dof_ptr[s + 1] = m.sub_dof_ptr[s] + (int64_t)(so[s].interior.size() + so[s].inter.size());
+    m.sub_coarse_ptr[s + 1] = m.sub_coarse_ptr[s] + (int64_t)so[s].coarse.size();
+    ccol_off[s + 1] = ccol_off[s] + (int64_t)so[s].ccol.size();
+    m.sub_nI[s] = (int64_t)so[s].interior.size();
   }
+  m.sub_dofs.resize(m.sub_dof_ptr[ns]);
+  m.sub_iface.resize(m.sub_dof_ptr[ns]);
+  m.sub_wmult.resize(m.sub_dof_ptr[ns]);
+  m.sub_coarse.resize(m.sub_coarse_ptr[ns]);
+  m.c_ptr.resize(m.sub_coarse_ptr[ns] + 1);
+  m.c_col.resize(ccol_off[ns]);
+  m.c_val.resize(ccol_off[ns]);
+  m.c_ptr[0] = 0;
+  parallel_range(ns, [&](int64_t s) {
+    const SubOut& o = so[s];
+    int64_t w = m.sub_dof_ptr[s];
+    for (int64_t d : o.interior) {
+      m.sub_dofs[w] = d;
+      m.sub_iface[w] = -1;
+      m.sub_wmult[w++] = 0.0;
+    }
+    for (int64_t d : o.inter) {
+      m.sub_dofs[w] = d;
+      m.sub_iface[w] = iface_pos[d];
+      m.sub_wmult[w++] = 1.0 / (double)nsh(dof_node[d]);
+    }
+    int64_t t = ccol_off[s];
+    for (size_t r = 0; r < o.coarse.size(); ++r) {
+      const int64_t row = m.sub_coarse_ptr[s] + (int64_t)r;
+      m.sub_coarse[row] = o.coarse[r];
+      const int64_t cnt = o.crow_len[r];
+      for (int64_t u = 0; u < cnt; ++u, ++t) {
+        m.c_col[t] = o.ccol[t - ccol_off[s]];
+        m.c_val[t] = 1.0 / (double)cnt;
+      }
+      m.c_ptr[row + 1] = t;
+    }
+  });
   return true;
 }
 

@@ -9,6 +9,7 @@
 #include <atomic>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <functional>
 #include <map>
@@ -359,6 +360,25 @@ void flush_profile(bddc_handle_s* h) {
   h->prof_pending.clear();
 }
 
+void parallel_for(int64_t n, const std::function<void(int64_t)>& fn) {
+  unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  if (n < 4 || nt == 1) {
+    for (int64_t i = 0; i < n; ++i) fn(i);
+    return;
+  }
+  std::vector<std::thread> th;
+  std::atomic<int64_t> next{0};
+  for (unsigned t = 0; t < nt; ++t)
+    th.emplace_back([&]() {
+      for (;;) {
+        int64_t i = next.fetch_add(1);
+        if (i >= n) break;
+        fn(i);
+      }
+    });
+  for (auto& t : th) t.join();
+}
+
 // ------------------------------------------------------------------ level preparation
 void build_level1_mesh(bddc_handle_s* h, LevelMesh* out) {
   LevelMesh& m = *out;
@@ -384,12 +404,15 @@ void build_level1_mesh(bddc_handle_s* h, LevelMesh* out) {
     m.en_ptr[e] = e * h->npe;
     m.ed_ptr[e] = e * h->npe * h->ndof;
   }
-  for (int64_t e = 0; e < h->n_elems; ++e)
-    for (int a = 0; a < h->npe; ++a) {
-      int64_t p = h->conn[e * h->npe + a];
-      m.en[e * h->npe + a] = p;
-      for (int c = 0; c < h->ndof; ++c) m.ed[(e * h->npe + a) * h->ndof + c] = h->free_of_full[p * h->ndof + c];
-    }
+  const int64_t chunk = 4096;
+  parallel_for((h->n_elems + chunk - 1) / chunk, [&](int64_t b) {
+    for (int64_t e = b * chunk; e < std::min(h->n_elems, (b + 1) * chunk); ++e)
+      for (int a = 0; a < h->npe; ++a) {
+        const int64_t p = h->conn[e * h->npe + a];
+        m.en[e * h->npe + a] = p;
+        for (int c = 0; c < h->ndof; ++c) m.ed[(e * h->npe + a) * h->ndof + c] = h->free_of_full[p * h->ndof + c];
+      }
+  });
   m.part = h->parts[0];
   m.n_dof = h->n_free;
   if (h->physics == BDDC_STOKES) {          // constant velocities float; pressures ordered last
@@ -411,24 +434,6 @@ void build_coarsest_mesh(const Level& prev, LevelMesh* out) {
   next_level_mesh(prev.mesh, prev.maps, part.data(), 1, out);
 }
 
-void parallel_for(int64_t n, const std::function<void(int64_t)>& fn) {
-  unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-  if (n < 4 || nt == 1) {
-    for (int64_t i = 0; i < n; ++i) fn(i);
-    return;
-  }
-  std::vector<std::thread> th;
-  std::atomic<int64_t> next{0};
-  for (unsigned t = 0; t < nt; ++t)
-    th.emplace_back([&]() {
-      for (;;) {
-        int64_t i = next.fetch_add(1);
-        if (i >= n) break;
-        fn(i);
-      }
-    });
-  for (auto& t : th) t.join();
-}
 
 // Host arrays of one level, built from its mesh and maps, then uploaded.
 void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
@@ -1271,14 +1276,23 @@ void analysis(bddc_handle_s* h, const bddc_mesh* mesh, const bddc_partition* par
   h->lv.clear();
   h->lv.resize(h->n_levels);   // L-1 BDDC levels + coarsest
   std::string err;
+  double tp = t0;
+  auto phase = [&](const char* what, int level) {   // opts.verbose >= 2: host phase times on stderr
+    const double t = now_ms();
+    if (h->opts.verbose >= 2) fprintf(stderr, "bddc analysis: %-16s level %d %8.2f ms\n", what, level, t - tp);
+    tp = t;
+  };
+  phase("input", 0);
   for (int l = 0; l + 1 < h->n_levels; ++l) {
     Level& L = h->lv[l];
     if (l == 0)
       build_level1_mesh(h, &L.mesh);
     else
       next_level_mesh(h->lv[l - 1].mesh, h->lv[l - 1].maps, h->parts[l].data(), h->n_parts[l], &L.mesh);
+    phase("mesh", l + 1);
     const bool allc = (h->opts.all_corners >> l) & 1u;
     if (!analyze_level(L.mesh, h->constraints, allc, &L.maps, &err)) fail(BDDC_ERR_INVALID, "level " + std::to_string(l + 1) + ": " + err);
+    phase("analyze", l + 1);
     L.fp32 = h->opts.precision == BDDC_PREC_MIXED;
     h->stats.n_sub[l] = L.maps.n_sub();
     h->stats.n_dof[l] = L.mesh.n_dof;
@@ -1290,7 +1304,9 @@ void analysis(bddc_handle_s* h, const bddc_mesh* mesh, const bddc_partition* par
   C.coarsest = true;
   C.fp32 = false;
   build_coarsest_mesh(h->lv[h->n_levels - 2], &C.mesh);
+  phase("mesh", h->n_levels);
   if (!analyze_level(C.mesh, 0u, false, &C.maps, &err)) fail(BDDC_ERR_INVALID, "coarsest level: " + err);
+  phase("analyze", h->n_levels);
   h->stats.n_levels = h->n_levels;
   h->stats.analysis_ms = now_ms() - t0;
 }

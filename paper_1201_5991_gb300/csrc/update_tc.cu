@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(kThreads2, 1)
   uint8_t* stage0 = smem_raw + (base - raw);
   __shared__ __align__(8) uint64_t full_bar[2], mma_bar[2], epi_bar[2];
   __shared__ uint32_t tmem_slot;
-  __shared__ int s_lost, s_issued;
+  __shared__ int s_issued;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&tmem_slot)));
@@ -384,7 +384,6 @@ __global__ void __launch_bounds__(kThreads2, 1)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 256;" ::"r"(smem_u32(&epi_bar[b])));
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    s_lost = 0;
     s_issued = 0;
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -501,10 +500,7 @@ __global__ void __launch_bounds__(kThreads2, 1)
         }
       }
       s_issued = issued;
-      if (lost) {
-        s_lost = 1;
-        atomicExch(L.status + 2, 4);
-      }
+      if (lost) atomicExch(L.status + 2, 4);
     }
   } else {
     // ---- epilogue warps: warp w reads TMEM lanes 32 (w & 3) .. +31 (output rows) and columns
