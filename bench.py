@@ -69,9 +69,10 @@ def load_peaks():
     try:
         with open(path) as fh:
             pk = json.load(fh)
-        return float(pk["hbm_gbs"]), float(pk.get("bf16_tflops", 1896.2)), "measured"
+        return (float(pk["hbm_gbs"]), float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1692.8))),
+                "measured")
     except Exception:
-        return 6800.0, 1900.0, "fallback"
+        return 6800.0, 1700.0, "fallback"
 
 
 class ClockSampler:
@@ -276,8 +277,9 @@ def run_gpu(args, rank, world, local_rank):
                 acc[3] += st.prof_flops[c]
             del s, u
         launches = (L.bddc_kernel_launches() - launches0) / max(steps, 1)
-        # the roofline kernel: the streaming kernel class with the largest share of the step
-        dom = max((capi.PROF_TRSV, capi.PROF_TRSV_IFACE, capi.PROF_TRMV), key=lambda c: cls[c][0])
+        # the roofline kernel: the single kernel class with the largest share of the step
+        dom = max((capi.PROF_TRSV, capi.PROF_TRSV_IFACE, capi.PROF_TRMV, capi.PROF_TC_UPDATE),
+                  key=lambda c: cls[c][0])
         prof = [cls[dom][0], cls[dom][1], cls[dom][2], dom, cls]
         torch.cuda.synchronize()
         barrier()
@@ -319,10 +321,15 @@ def run_gpu(args, rank, world, local_rank):
         e2e_s = float(t.item())
     mesh_bytes = prob.coords.nbytes + prob.conn.nbytes + prob.coef.nbytes + prob.dirichlet.nbytes
 
-    hbm, _, peak_kind = load_peaks()
-    achieved = prof[2] / (prof[0] * 1e-3) / 1e9 if prof[0] > 0 else 0.0
+    hbm, tc_peak, peak_kind = load_peaks()
     dom, cls = prof[3], prof[4]
-    ratio = traffic_ratio(dom)
+    tensor = dom == capi.PROF_TC_UPDATE
+    if tensor:   # three FP16 tensor-core products per FP32-equivalent multiply-add (scaled hi/lo split)
+        achieved = 3.0 * cls[dom][3] / (prof[0] * 1e-3) / 1e12 if prof[0] > 0 else 0.0
+        ratio = None
+    else:
+        achieved = prof[2] / (prof[0] * 1e-3) / 1e9 if prof[0] > 0 else 0.0
+        ratio = traffic_ratio(dom)
     traffic = ratio * prof[2] / max(prof[1], 1) if ratio is not None else None
     names = {capi.PROF_TRSV: "k_sweep<float> forward/backward over interior block rows (Schur operator; "
                              "streaming triangular sweeps, TMA-staged tiles)",
@@ -330,7 +337,10 @@ def run_gpu(args, rank, world, local_rank):
              capi.PROF_COARSE: "k_sweep<double> forward/backward of the coarsest FP64 factor",
              capi.PROF_TRMV: "k_trmv_t + k_trmv_n (inner Schur operator: products with the stored interface factor)",
              capi.PROF_SPMV: "k_spmv (FP64 CSR products with K_i)",
-             capi.PROF_FACTOR: "batched tiled factorisation (k_potrf_diag, k_trsm_panel, k_update_tc)"}
+             capi.PROF_FACTOR: "factorisation steps on CUDA cores (k_potrf_diag, k_trsm_panel, in-panel "
+                               "k_syrk_update, k_split_panel)",
+             capi.PROF_TC_UPDATE: "k_update_tc2 (rank-256 trailing update on tcgen05, scaled two-part FP16 "
+                                  "products, persistent, TMEM double-buffered)"}
     kernel_classes = {}
     for c, (cms, cl, cb, cf) in cls.items():
         if cl == 0:
@@ -342,20 +352,25 @@ def run_gpu(args, rank, world, local_rank):
             e["frac_of_hbm"] = round(cb / (cms * 1e-3) / 1e9 / hbm, 4)
         if cf > 0:
             e["achieved_TFLOPs_fp32"] = round(cf / (cms * 1e-3) / 1e12, 2)
+        if c == capi.PROF_TC_UPDATE and cf > 0:
+            e["achieved_TFLOPs_fp16_mma"] = round(3.0 * cf / (cms * 1e-3) / 1e12, 1)
+            e["frac_of_tensor_peak"] = round(3.0 * cf / (cms * 1e-3) / 1e12 / tc_peak, 4)
         kernel_classes[{capi.PROF_TRSV: "trsv_interior", capi.PROF_TRSV_IFACE: "trsv_interface",
                         capi.PROF_COARSE: "trsv_coarsest", capi.PROF_TRMV: "trmv", capi.PROF_SPMV: "spmv",
-                        capi.PROF_FACTOR: "factor"}[c]] = e
+                        capi.PROF_FACTOR: "factor_cuda_cores", capi.PROF_TC_UPDATE: "tc_update"}[c]] = e
+    peak = tc_peak if tensor else hbm
     roofline = {
         "kernel": names[dom],
-        "bound": "hbm",
+        "bound": "tensor" if tensor else "hbm",
         "achieved": round(achieved, 1),
-        "peak": hbm,
-        "peak_kind": peak_kind,
-        "unit": "GB/s",
-        "frac": round(achieved / hbm, 4),
+        "peak": peak,
+        "peak_kind": (peak_kind + (" bf16 sustained (fp16 dense rate = bf16)" if tensor else " copy bandwidth")),
+        "unit": "TFLOP/s" if tensor else "GB/s",
+        "frac": round(achieved / peak, 4),
         "traffic": traffic,
         "launches_per_step": prof[1] / max(args.steps, 1),
-        "algorithmic_bytes_per_launch": prof[2] / max(prof[1], 1),
+        "algorithmic_bytes_per_launch": None if tensor else prof[2] / max(prof[1], 1),
+        "algorithmic_fp32_flops_per_launch": cls[dom][3] / max(prof[1], 1) if tensor else None,
         "avg_launch_ms": prof[0] / max(prof[1], 1),
         "share_of_step": round(prof[0] / args.steps / ms, 4) if ms > 0 else None,
         "classes": kernel_classes,

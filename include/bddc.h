@@ -130,12 +130,13 @@ typedef struct {
 
 /* kernel classes timed when bddc_opts.profile = 1 */
 #define BDDC_PROF_TRSV 0    /* streaming triangular sweeps over interior block rows (Schur operator) */
-#define BDDC_PROF_FACTOR 1  /* one step of the batched blocked Cholesky (diagonal, panel, update) */
+#define BDDC_PROF_FACTOR 1  /* batched blocked Cholesky steps on CUDA cores (diagonal, panel, in-panel update) */
 #define BDDC_PROF_SPMV 2    /* FP64 sparse products with K_i */
 #define BDDC_PROF_TRMV 3    /* inner Schur operator: products with the stored interface factor */
 #define BDDC_PROF_TRSV_IFACE 4   /* sweeps over interface block rows (subdomain corrections) */
 #define BDDC_PROF_COARSE 5  /* sweeps of the coarsest level's FP64 factor */
-#define BDDC_PROF_CLASSES 6
+#define BDDC_PROF_TC_UPDATE 6   /* tensor-core trailing updates of the factorisation (FP32-equivalent flops) */
+#define BDDC_PROF_CLASSES 7
 
 typedef struct {
   int iterations;           /* Krylov iterations of the last solve (max over right-hand sides) */

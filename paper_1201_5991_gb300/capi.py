@@ -35,7 +35,8 @@ EXPORTED = [
     "bddc_get_stats", "bddc_sizes", "bddc_free", "bddc_last_error", "bddc_kernel_launches",
     "bddc_reset_profile", "bddc_grad_noalloc",
 ]
-PROF_TRSV, PROF_FACTOR, PROF_SPMV, PROF_TRMV, PROF_TRSV_IFACE, PROF_COARSE, PROF_CLASSES = 0, 1, 2, 3, 4, 5, 6
+PROF_TRSV, PROF_FACTOR, PROF_SPMV, PROF_TRMV, PROF_TRSV_IFACE, PROF_COARSE, PROF_TC_UPDATE, PROF_CLASSES = (
+    0, 1, 2, 3, 4, 5, 6, 7)
 
 
 class Mesh(C.Structure):

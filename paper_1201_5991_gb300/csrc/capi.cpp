@@ -123,6 +123,7 @@ struct Level {
   std::vector<int> narrow_tiles;   // per step k: in-panel update tiles (256-wide panels)
   std::vector<int> wide_items;     // per super-step: tensor-core work items
   std::vector<int64_t> wide_items2; // per super-step: 128 x 128 work items of the pre-split update (all subdomains)
+  std::vector<double> tc_flops;     // per super-step: FP32-equivalent flops of the trailing update
   int64_t* item_pref = nullptr;     // [super-steps][n_sub + 1] first work item of every subdomain
   uint8_t* split = nullptr;        // scaled FP16 parts of the current super-panel (pre-split update)
   float* rscale = nullptr;         // their row unscaling factors (powers of two)
@@ -485,6 +486,7 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
   L.narrow_tiles.assign(L.max_Bc, 0);
   L.wide_items.assign((L.max_Bc + kPanel - 1) / kPanel + 1, 0);
   L.wide_items2.assign((L.max_Bc + kPanel - 1) / kPanel + 1, 0);
+  L.tc_flops.assign((L.max_Bc + kPanel - 1) / kPanel + 1, 0.0);
   const double nb3 = (double)NB * NB * NB;
   const double wsz = L.fp32 ? 4.0 : 8.0;
   L.trsv_bytes[0] = L.trsv_bytes[1] = 0.0;
@@ -504,9 +506,13 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
       L.narrow_tiles[k] = std::max(L.narrow_tiles[k], (int)cnt);
     }
     for (int kb0 = 0; kb0 < m.Bc; kb0 += kPanel) {
-      int64_t cnt = 0;
-      for (int j = kb0 + kPanel; j < m.Bc; ++j) cnt += (m.R - j + 1) / 2;
+      int64_t cnt = 0, tiles = 0;
+      for (int j = kb0 + kPanel; j < m.Bc; ++j) {
+        cnt += (m.R - j + 1) / 2;
+        tiles += m.R - j;
+      }
       L.wide_items[kb0 / kPanel] = std::max(L.wide_items[kb0 / kPanel], (int)cnt);
+      L.tc_flops[kb0 / kPanel] += 2.0 * nb3 * kPanel * (double)tiles;
 
     }
     // a sweep reads the stored triangle once and the vector in and out
@@ -810,19 +816,21 @@ void factor_level(bddc_handle_s* h, Level& L, cudaStream_t st) {
     // 256-wide panels: in-panel steps on CUDA cores, the rank-256 trailing update on tcgen05
     for (int kb0 = 0; kb0 < L.max_Bc; kb0 += kPanel) {
       const int kb1 = kb0 + kPanel;
+      const int p = kb0 / kPanel;
       double fl = 0.0;
       for (int k = kb0; k < std::min(kb1, L.max_Bc); ++k) fl += L.step_flops[k];
-      ProfScope ps(h, BDDC_PROF_FACTOR, 0.0, fl, st);
-      for (int k = kb0; k < std::min(kb1, L.max_Bc); ++k)
-        launch_potrf_step<T>(d, k, L.max_R, L.narrow_tiles[k], kb1, st);
+      {
+        ProfScope ps(h, BDDC_PROF_FACTOR, 0.0, std::max(0.0, fl - L.tc_flops[p]), st);
+        for (int k = kb0; k < std::min(kb1, L.max_Bc); ++k)
+          launch_potrf_step<T>(d, k, L.max_R, L.narrow_tiles[k], kb1, st);
+        if (L.split && L.wide_items2[p] > 0) launch_split_panel(d, kb0, kb1, L.max_R, L.split, L.rscale, L.prow_off, st);
+      }
+      ProfScope ps(h, BDDC_PROF_TC_UPDATE, 0.0, L.tc_flops[p], st);
       if (L.split) {
-        const int p = kb0 / kPanel;
         const int64_t items = L.wide_items2[p];
-        if (items > 0) {
-          launch_split_panel(d, kb0, kb1, L.max_R, L.split, L.rscale, L.prow_off, st);
+        if (items > 0)
           launch_update_tc2(d, kb0, kb1, (int)std::min<int64_t>(items, h->grid_max / 2), L.split, L.rscale,
                             L.prow_off, L.item_pref + (size_t)p * (d.n_sub + 1), st);
-        }
       } else {
         launch_update_tc(d, kb0, kb1, L.wide_items[kb0 / kPanel], st);
       }
