@@ -65,7 +65,9 @@ __global__ void k_potrf_diag(LevelDev L, int k) {
   const int s = blockIdx.x;
   const SubMeta m = L.meta[s];
   if (k >= m.Bc) return;
-  __shared__ T A[NB][NB + 1];
+  extern __shared__ unsigned char smem_raw[];
+  T(*A)[NB + 1] = (T(*)[NB + 1])smem_raw;                 // the tile, then its factor L
+  T(*X)[NB + 1] = (T(*)[NB + 1])(smem_raw + sizeof(T) * NB * (NB + 1));   // L^{-1}
   __shared__ int bad;
   T* g = tile_ptr<T>(m, L.tiles, k, k);
   for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
@@ -109,20 +111,30 @@ __global__ void k_potrf_diag(LevelDev L, int k) {
   }
   if (threadIdx.x < NB) ((T*)L.sgn)[m.vec_off + (int64_t)k * NB + threadIdx.x] = sg[threadIdx.x];
   if (threadIdx.x == 0 && bad) flag_breakdown(L.status, s);
-  // X = L^{-1} written to the diagonal-inverse store, one column per thread (each thread
-  // reads back only the entries of its own column)
-  T* dv = (T*)L.dinv + m.dinv_off + (int64_t)k * NB2;
-  if (threadIdx.x < NB) {
-    const int c = threadIdx.x;
-    for (int r = 0; r < c; ++r) dv[r * NB + c] = (T)0;
-    dv[c * NB + c] = (T)1 / A[c][c];
-    for (int i = c + 1; i < NB; ++i) {
-      T sacc = (T)0;
-      for (int q = c; q < i; ++q) sacc += A[i][q] * dv[q * NB + c];
-      dv[i * NB + c] = -sacc / A[i][i];
+  // X = L^{-1} by forward substitution on the columns, in shared memory: four threads per
+  // column c (thread t4 sums the terms q = t4 mod 4, and keeps the entries X[q][c] of that
+  // class, so no thread reads another's writes); the four partial sums meet by shuffles
+  {
+    const int c = threadIdx.x >> 2, t4 = threadIdx.x & 3;
+    const unsigned grp = 0xFu << (threadIdx.x & 28);
+    if (c < NB) {
+      if ((c & 3) == t4) X[c][c] = (T)1 / A[c][c];
+      for (int i = c + 1; i < NB; ++i) {
+        T part = (T)0;
+        for (int q = c + ((t4 - c) & 3); q < i; q += 4) part += A[i][q] * X[q][c];
+        part += __shfl_xor_sync(grp, part, 1);
+        part += __shfl_xor_sync(grp, part, 2);
+        if ((i & 3) == t4) X[i][c] = -part / A[i][i];
+      }
     }
   }
-  for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) g[t] = A[t / NB][t % NB];
+  __syncthreads();
+  T* dv = (T*)L.dinv + m.dinv_off + (int64_t)k * NB2;
+  for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
+    const int r = t / NB, c = t % NB;
+    dv[t] = c <= r ? X[r][c] : (T)0;
+    g[t] = A[r][c];
+  }
 }
 
 // ---- step k, part 2: panel L(i,k) = A(i,k) L_kk^{-T} for i = k+1 .. R-1 --------------------
@@ -539,13 +551,15 @@ template <typename T>
 void launch_potrf_step(const LevelDev& L, int k, int max_R, int max_tiles, int jmax, cudaStream_t st) {
   const unsigned ns = (unsigned)L.n_sub;
   const size_t sm = 2 * NB * LDS * sizeof(T);
+  const size_t sm_diag = 2 * NB * (NB + 1) * sizeof(T);
   static bool attr = false;   // opt in to more than 48 KB of dynamic shared memory once
   if (!attr) {
+    cudaFuncSetAttribute(k_potrf_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_diag);
     cudaFuncSetAttribute(k_trsm_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     cudaFuncSetAttribute(k_syrk_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     attr = true;
   }
-  { note_launch(); k_potrf_diag<T><<<ns, 256, 0, st>>>(L, k); }
+  { note_launch(); k_potrf_diag<T><<<ns, 256, sm_diag, st>>>(L, k); }
   const int panel = max_R - k - 1;
   if (panel > 0) { note_launch(); k_trsm_panel<T><<<dim3((unsigned)panel, ns), 256, sm, st>>>(L, k); }
   if (max_tiles > 0) { note_launch(); k_syrk_update<T><<<dim3((unsigned)max_tiles, ns), 256, sm, st>>>(L, k, jmax); }
