@@ -303,6 +303,15 @@ def run_gpu(args, rank, world, local_rank):
         ms64, stats64, _, _, _ = timed("fp64", pk, 1)
         st64 = stats64[-1]
 
+    # batching ablation (outside the timed region): level-1 sweeps and CUDA-core factorisation
+    # in one launch for all subdomains vs one launch per subdomain
+    try:
+        s_ab = BddcSolver(prob, precision="mixed", stream=stream)
+        ablation = {k: round(v, 3) for k, v in s_ab.batching_ablation().items()}
+        del s_ab
+    except capi.BddcError as e:
+        ablation = {"unavailable": str(e)}
+
     # end to end through the public host-buffer entry point
     fh = np.ascontiguousarray(prob.f[:, 0])
     e2e_times = []
@@ -422,6 +431,7 @@ def run_gpu(args, rank, world, local_rank):
         "e2e": {"value": prob.n_free * world / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": int(prob.n_free * 8 + mesh_bytes), "d2h_bytes_per_step": int(prob.n_free * 8)},
         "gpu_launches": int(round(launches)),
+        "batching_ablation": ablation,
         "roofline": roofline,
         "cpu_baseline": cpu,
         "clocks": clk,

@@ -286,6 +286,17 @@ int64_t bddc_kernel_launches(void);
 /* Reset the per-class timers of bddc_stats.prof_* on a handle. */
 int bddc_reset_profile(bddc_handle h);
 
+/* Batching ablation (measurement only; no counterpart in the paper): on level 1 of a set-up
+ * handle, times with CUDA events on the handle's stream
+ *   ms[0]  one forward + backward interior sweep pair, all subdomains in one launch each,
+ *   ms[1]  the same sweeps launched once per subdomain,
+ *   ms[2]  the CUDA-core tiled factorisation (no tensor cores) batched over all subdomains,
+ *   ms[3]  the same factorisation launched once per subdomain per step.
+ * The factorisation runs are repeated work: afterwards the handle's level-1 factors are
+ * recomputed by the normal path, so the handle stays valid and bit-identical.  Mixed-precision
+ * SPD handles only.  Errors: INVALID, CUDA. */
+int bddc_batching_ablation(bddc_handle h, double* ms);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char* bddc_last_error(void);
 

@@ -33,7 +33,7 @@ EXPORTED = [
     "bddc_default_opts", "bddc_analyze", "bddc_setup", "bddc_update_coef", "bddc_solve",
     "bddc_solve_host", "bddc_apply_precond", "bddc_apply_schur", "bddc_grad", "bddc_get_maps",
     "bddc_get_stats", "bddc_sizes", "bddc_free", "bddc_last_error", "bddc_kernel_launches",
-    "bddc_reset_profile", "bddc_grad_noalloc",
+    "bddc_reset_profile", "bddc_grad_noalloc", "bddc_batching_ablation",
 ]
 PROF_TRSV, PROF_FACTOR, PROF_SPMV, PROF_TRMV, PROF_TRSV_IFACE, PROF_COARSE, PROF_TC_UPDATE, PROF_CLASSES = (
     0, 1, 2, 3, 4, 5, 6, 7)
@@ -132,6 +132,7 @@ def lib() -> C.CDLL:
     L.bddc_kernel_launches.argtypes = []
     L.bddc_kernel_launches.restype = C.c_int64
     L.bddc_reset_profile.argtypes = [H]
+    L.bddc_batching_ablation.argtypes = [H, C.POINTER(C.c_double)]
     for name in EXPORTED:
         if name not in ("bddc_default_opts", "bddc_free", "bddc_last_error", "bddc_kernel_launches"):
             getattr(L, name).restype = C.c_int

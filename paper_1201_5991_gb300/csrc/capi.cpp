@@ -133,6 +133,8 @@ struct Level {
   // sweep task lists [part][direction] in dependency order and their control words
   int2* tasks[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};       // [part][dir], subdomain order
   int2* tasks_big[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [part][dir], longest chains first
+  int2* tasks_by_sub[2] = {nullptr, nullptr};     // interior tasks [dir] grouped per subdomain
+  std::vector<int> task_sub_off[2];               // their per-subdomain offsets
   int ntasks[2][2] = {{0, 0}, {0, 0}};
   // coarsest level of the mixed form: FP32 copy of the FP64 factor for the preconditioner's solves
   bool solve32 = false;
@@ -747,6 +749,16 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
         }
         L.ntasks[part][dir] = (int)tl.size();
         (order == 0 ? L.tasks : L.tasks_big)[part][dir] = A.upload(tl, st);
+        if (order == 0 && part == 0) {   // the same tasks grouped per subdomain (batching ablation)
+          std::vector<int2> bys(tl.size());
+          std::vector<int> off(ns + 1, 0);
+          for (const int2& t : tl) off[t.x + 1]++;
+          for (int64_t q = 0; q < ns; ++q) off[q + 1] += off[q];
+          std::vector<int> fill(off.begin(), off.end() - 1);
+          for (const int2& t : tl) bys[fill[t.x]++] = t;
+          L.tasks_by_sub[dir] = A.upload(bys, st);
+          L.task_sub_off[dir] = off;
+        }
       }
   }
   L.n_ctrl = (int)(1 + L.dinv_elems / NB2);
@@ -2200,6 +2212,81 @@ int bddc_get_stats(bddc_handle h, bddc_stats* out) {
     if (!h || !out) fail(BDDC_ERR_INVALID, "bad arguments");
     flush_profile(h);
     *out = h->stats;
+    return BDDC_OK;
+  });
+}
+
+int bddc_batching_ablation(bddc_handle h, double* ms) {
+  return guarded([&]() {
+    if (!h || !ms || !h->factored || h->lv.empty() || !h->lv[0].fp32 || h->physics == BDDC_STOKES)
+      fail(BDDC_ERR_INVALID, "the ablation needs a set-up mixed-precision SPD handle");
+    Level& L = h->lv[0];
+    cudaStream_t st = h->st;
+    const int saved_profile = h->opts.profile;
+    h->opts.profile = 0;
+    cudaEvent_t a, b;
+    ck(cudaEventCreate(&a), "cudaEventCreate");
+    ck(cudaEventCreate(&b), "cudaEventCreate");
+    auto elapsed = [&]() {
+      ck(cudaEventSynchronize(b), "cudaEventSynchronize");
+      float t = 0.f;
+      ck(cudaEventElapsedTime(&t, a, b), "cudaEventElapsedTime");
+      return (double)t;
+    };
+    float* v = (float*)L.locA;
+    ck(cudaMemsetAsync(v, 0, sizeof(float) * (size_t)L.n_vec, st), "memset");
+    // (1) interior sweep pair: one launch per direction vs one per subdomain and direction
+    const int grid = h->grid_max / 2 * L.sweep_ctas[0];
+    trsv_pair<float>(h, L, v, 0, st);
+    ck(cudaEventRecord(a, st), "cudaEventRecord");
+    trsv_pair<float>(h, L, v, 0, st);
+    ck(cudaEventRecord(b, st), "cudaEventRecord");
+    ms[0] = elapsed();
+    ck(cudaEventRecord(a, st), "cudaEventRecord");
+    for (int dir = 0; dir < 2; ++dir)
+      for (int64_t s = 0; s < (int64_t)L.meta.size(); ++s) {
+        const int o0 = L.task_sub_off[dir][s], o1 = L.task_sub_off[dir][s + 1];
+        launch_sweep<float>(L.d, v, L.tasks_by_sub[dir] + o0, o1 - o0, 0, dir, L.ctrl, L.n_ctrl, grid,
+                            L.sweep_deep[0], st);
+      }
+    ck(cudaEventRecord(b, st), "cudaEventRecord");
+    ms[1] = elapsed();
+    // (2) CUDA-core tiled factorisation of level 1 (every step: diagonal tile, panel, trailing
+    // update): batched over all subdomains vs launched per subdomain; both start from the
+    // assembled tiles
+    auto assemble_tiles = [&]() {
+      ck(cudaMemsetAsync(L.d.tiles, 0, sizeof(float) * (size_t)std::max<int64_t>(L.tile_elems, 1), st), "memset");
+      launch_densify_rows<float>(L.d, L.row_sub, st);
+      launch_add_constraints<float>(L.d, st);
+    };
+    assemble_tiles();
+    ck(cudaEventRecord(a, st), "cudaEventRecord");
+    for (int k = 0; k < L.max_Bc; ++k) launch_potrf_step<float>(L.d, k, L.max_R, L.max_tiles[k], 1 << 30, st);
+    ck(cudaEventRecord(b, st), "cudaEventRecord");
+    ms[2] = elapsed();
+    assemble_tiles();
+    ck(cudaEventRecord(a, st), "cudaEventRecord");
+    for (int64_t s = 0; s < (int64_t)L.meta.size(); ++s) {
+      LevelDev one = L.d;
+      one.meta = L.d.meta + s;
+      one.n_sub = 1;
+      const SubMeta& m = L.meta[s];
+      for (int k = 0; k < m.Bc; ++k) {
+        int64_t cnt = 0;
+        for (int j = k + 1; j < m.Bc; ++j) cnt += m.R - j;
+        launch_potrf_step<float>(one, k, m.R, (int)cnt, 1 << 30, st);
+      }
+    }
+    ck(cudaEventRecord(b, st), "cudaEventRecord");
+    ms[3] = elapsed();
+    // restore the level-1 factors of the handle's own path (deterministic: bit-identical)
+    reset_status(h);
+    factor_level<float>(h, L, st);
+    check_status(h, 1);
+    h->opts.profile = saved_profile;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    ck(cudaStreamSynchronize(st), "sync");
     return BDDC_OK;
   });
 }

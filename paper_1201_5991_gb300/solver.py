@@ -210,6 +210,13 @@ class BddcSolver:
     def reset_profile(self):
         capi.check(capi.lib().bddc_reset_profile(self.hd.h))
 
+    def batching_ablation(self) -> dict:
+        """Level-1 sweeps and CUDA-core factorisation, batched vs one launch per subdomain (ms)."""
+        ms = (C.c_double * 4)()
+        capi.check(capi.lib().bddc_batching_ablation(self.hd.h, ms))
+        return {"sweep_pair_batched_ms": ms[0], "sweep_pair_per_subdomain_ms": ms[1],
+                "cuda_core_factor_batched_ms": ms[2], "cuda_core_factor_per_subdomain_ms": ms[3]}
+
     def stats(self) -> capi.Stats:
         st = capi.Stats()
         capi.check(capi.lib().bddc_get_stats(self.hd.h, C.byref(st)))

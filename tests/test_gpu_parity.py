@@ -218,3 +218,14 @@ def test_autotuned_sweeps_are_bitwise_equal_to_defaults():
             k = 2 * l + part
             assert st.sweep_ctas[k] in (1, 2) and st.sweep_deep[k] in (0, 1) and st.sweep_order[k] in (0, 1)
     assert all(a.last_stats.sweep_ctas[k] == 2 and a.last_stats.sweep_deep[k] == 1 for k in range(2 * st.n_levels))
+
+
+def test_batching_ablation_leaves_the_handle_unchanged():
+    p = PROBLEMS["elast8_4"]()
+    f = _dev(p.f[:, 0])
+    s = BddcSolver(p, precision="mixed")
+    u0 = s.solve(f, tol=1e-10).cpu().numpy()
+    ab = s.batching_ablation()
+    assert all(v > 0 for v in ab.values())
+    u1 = s.solve(f, tol=1e-10).cpu().numpy()
+    np.testing.assert_array_equal(u0, u1)   # the factors were recomputed bit for bit
