@@ -1183,7 +1183,6 @@ void numeric_setup(bddc_handle_s* h) {
                     h->d_lift, st);
     } else {
       const Level& P = h->lv[l - 1];
-      std::vector<int64_t> dummy;
       launch_copy_segments(P.d.KC, L.seg_src, L.d.ke, L.d.ke_off, L.seg_len, L.mesh.n_elems, st);
     }
     if (L.fp32)

@@ -288,6 +288,7 @@ constexpr uint32_t kSplitTile = 2 * kTilePart;   // hi and lo of one tile (16 KB
 constexpr uint32_t kOpnd = 2 * kTilePart;        // one part of a 128-row operand (16 KB)
 constexpr uint32_t kStage2 = 4 * kOpnd;          // A hi, A lo, B hi, B lo (64 KB)
 constexpr int kThreads2 = 288;                   // 8 epilogue warps + 1 producer / MMA warp
+constexpr int kStages2 = 3;                      // shared-memory stages (copies run two steps ahead)
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
@@ -355,9 +356,10 @@ __global__ void __launch_bounds__(256) k_split_panel(LevelDev L, int kb0, int kb
 
 // Persistent: CTA c takes the work items c, c + gridDim.x, ... of the panel (items of all
 // subdomains flattened; item_pref[s] = first item of subdomain s).  One global step per (item,
-// panel column); step g uses shared-memory stage and TMEM accumulator pair g & 1, so the copies
-// and MMAs of the next steps (also of the next item) run while the epilogue warps promote the
-// previous accumulators and write back the previous item's output block.
+// panel column); step g uses shared-memory stage g % 3 (its copies are requested two steps
+// ahead) and TMEM accumulator pair g & 1, so the copies and MMAs of the next steps (also of the
+// next item) run while the epilogue warps promote the previous accumulators and write back the
+// previous item's output block.
 __global__ void __launch_bounds__(kThreads2, 1)
     k_update_tc2(LevelDev L, int kb0, int kb1, const uint8_t* __restrict__ split, const float* __restrict__ rscale,
                  const int64_t* __restrict__ prow_off, const int64_t* __restrict__ item_pref) {
@@ -369,7 +371,9 @@ __global__ void __launch_bounds__(kThreads2, 1)
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t* stage0 = smem_raw + (base - raw);
-  __shared__ __align__(8) uint64_t full_bar[2], mma_bar[2], epi_bar[2];
+  // full/free: shared-memory stage g % kStages2 loaded / read by its MMAs; mma/epi: TMEM
+  // accumulator pair g & 1 written by its MMAs / read by the epilogue
+  __shared__ __align__(8) uint64_t full_bar[kStages2], free_bar[kStages2], mma_bar[2], epi_bar[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int s_issued;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -378,8 +382,11 @@ __global__ void __launch_bounds__(kThreads2, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kStages2; ++b) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full_bar[b])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&free_bar[b])));
+    }
+    for (int b = 0; b < 2; ++b) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mma_bar[b])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 256;" ::"r"(smem_u32(&epi_bar[b])));
     }
@@ -426,77 +433,106 @@ __global__ void __launch_bounds__(kThreads2, 1)
           if (++spins > kSpinLimit) return false;
         return true;
       };
-      uint32_t g = 0;   // global step
-      for (int64_t it = blockIdx.x; it < n_items && !lost; it += gridDim.x) {
-        int s, j, i0;
-        decode(it, s, j, i0);
-        const SubMeta& m = L.meta[s];
-        const bool hasA1 = i0 + 1 < m.R, hasB1 = j + 1 < m.Bc;
-        const int64_t rbase = prow_off[s];
-        const uint8_t* rowA0 = split + (rbase + i0) * kPanelTiles * (int64_t)kSplitTile;
-        const uint8_t* rowA1 = split + (rbase + (hasA1 ? i0 + 1 : i0)) * kPanelTiles * (int64_t)kSplitTile;
-        const uint8_t* rowB0 = split + (rbase + j) * kPanelTiles * (int64_t)kSplitTile;
-        const uint8_t* rowB1 = split + (rbase + (hasB1 ? j + 1 : j)) * kPanelTiles * (int64_t)kSplitTile;
-        // the output tiles are read back by the epilogue after the last column: start moving them into L2
+      // steps of this CTA: its items in order, nq panel columns each
+      const int64_t my_items = (n_items - (int64_t)blockIdx.x + gridDim.x - 1) / gridDim.x;
+      const uint32_t total = (uint32_t)(my_items * nq);
+      int64_t cached_k = -1;
+      int cs = 0, cj = 0, ci0 = 0;
+      // request the B and A parts of step gc into stage gc % kStages2 (after the MMAs of step
+      // gc - kStages2 have read it)
+      auto request = [&](uint32_t gc) -> bool {
+        const int st = (int)(gc % kStages2);
+        if (gc >= (uint32_t)kStages2 && !wait(&free_bar[st], ((gc / kStages2) - 1) & 1u)) return false;
+        const int64_t k = gc / nq;
+        const int q = (int)(gc % nq);
+        if (k != cached_k) {
+          decode(blockIdx.x + k * gridDim.x, cs, cj, ci0);
+          cached_k = k;
+        }
+        const SubMeta& m = L.meta[cs];
+        const bool hasA1 = ci0 + 1 < m.R, hasB1 = cj + 1 < m.Bc;
+        const int64_t rbase = prow_off[cs];
+        if (q == 0) {   // the output tiles are read back by the epilogue after the last column
 #pragma unroll
-        for (int a = 0; a < 2; ++a)
+          for (int a = 0; a < 2; ++a)
 #pragma unroll
-          for (int c = 0; c < 2; ++c) {
-            const int ti = i0 + a, tj = j + c;
-            if ((a == 0 || hasA1) && (c == 0 || hasB1) && (ti >= m.Bc || tj <= ti)) {
-              const float* tp = (const float*)L.tiles + m.tile_off + tile_index(ti, tj, m.Bc) * NB2;
-              asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(tp), "r"((uint32_t)(NB2 * 4)) : "memory");
+            for (int c = 0; c < 2; ++c) {
+              const int ti = ci0 + a, tj = cj + c;
+              if ((a == 0 || hasA1) && (c == 0 || hasB1) && (ti >= m.Bc || tj <= ti)) {
+                const float* tp = (const float*)L.tiles + m.tile_off + tile_index(ti, tj, m.Bc) * NB2;
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(tp), "r"((uint32_t)(NB2 * 4))
+                             : "memory");
+              }
             }
+        }
+        const uint8_t* rowA0 = split + (rbase + ci0) * kPanelTiles * (int64_t)kSplitTile;
+        const uint8_t* rowA1 = split + (rbase + (hasA1 ? ci0 + 1 : ci0)) * kPanelTiles * (int64_t)kSplitTile;
+        const uint8_t* rowB0 = split + (rbase + cj) * kPanelTiles * (int64_t)kSplitTile;
+        const uint8_t* rowB1 = split + (rbase + (hasB1 ? cj + 1 : cj)) * kPanelTiles * (int64_t)kSplitTile;
+        uint8_t* sA = stage0 + st * kStage2;   // [A hi | A lo | B hi | B lo], 128 rows each
+        uint8_t* sB = sA + 2 * kOpnd;
+        mbar_expect_tx(&full_bar[st], kStage2);
+        const int64_t qo = (int64_t)q * kSplitTile;
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+          bulk_g2s(sA + p * kOpnd, rowA0 + qo + p * kTilePart, kTilePart, &full_bar[st]);
+          bulk_g2s(sA + p * kOpnd + kTilePart, rowA1 + qo + p * kTilePart, kTilePart, &full_bar[st]);
+          bulk_g2s(sB + p * kOpnd, rowB0 + qo + p * kTilePart, kTilePart, &full_bar[st]);
+          bulk_g2s(sB + p * kOpnd + kTilePart, rowB1 + qo + p * kTilePart, kTilePart, &full_bar[st]);
+        }
+        return true;
+      };
+      uint32_t requested = 0;
+      for (; requested < total && requested < (uint32_t)(kStages2 - 1); ++requested)
+        if (!request(requested)) {
+          lost = true;
+          break;
+        }
+      for (uint32_t g = 0; g < total && !lost; ++g) {
+        const int st = (int)(g % kStages2);
+        const int b = (int)(g & 1u);
+        if (!wait(&full_bar[st], (g / kStages2) & 1u)) {
+          wait(&full_bar[st], (g / kStages2) & 1u);   // copies may still land: one more bounded wait
+          lost = true;
+          break;
+        }
+        if (g >= 2 && !wait(&epi_bar[b], ((g >> 1) - 1) & 1u)) {   // accumulators of step g - 2 are read
+          lost = true;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t sa = smem_u32(stage0 + st * kStage2), sb = sa + 2 * kOpnd;
+        const uint32_t acc_small = tmem + 256u * b, acc_big = acc_small + 128u;
+        // products: (A lo, B hi), (A hi, B lo) into the small accumulator, (A hi, B hi) into the big one
+        const int pa[3] = {1, 0, 0}, pb[3] = {0, 1, 0};
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t da = desc_sw128(sa + pa[p] * kOpnd + kk * 32);
+            const uint64_t db = desc_sw128(sb + pb[p] * kOpnd + kk * 32);
+            const bool big = p == 2;
+            const uint32_t acc = (kk > 0 || (p > 0 && !big)) ? 1u : 0u;   // fresh accumulators per step
+            asm volatile(
+                "{\n .reg .pred pp;\n setp.ne.b32 pp, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pp;\n}\n" ::"r"(big ? acc_big : acc_small),
+                "l"(da), "l"(db), "r"(idesc), "r"(acc));
           }
-        for (int q = 0; q < nq; ++q, ++g) {
-          const int b = g & 1;
-          const uint32_t n = g >> 1;
-          if (g >= 2 && !wait(&mma_bar[b], (n - 1) & 1u)) {   // MMAs of step g - 2 have read this stage
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&mma_bar[b]))
+                     : "memory");
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&free_bar[st]))
+                     : "memory");
+        ++issued;
+        // refill: step g + kStages2 - 1 goes into the stage of step g - 1, whose MMAs run ahead
+        // of the ones just issued
+        if (requested < total) {
+          if (!request(requested)) {
             lost = true;
             break;
           }
-          uint8_t* sA = stage0 + b * kStage2;   // [A hi | A lo | B hi | B lo], 128 rows each
-          uint8_t* sB = sA + 2 * kOpnd;
-          mbar_expect_tx(&full_bar[b], kStage2);
-          const int64_t qo = (int64_t)q * kSplitTile;
-#pragma unroll
-          for (int p = 0; p < 2; ++p) {
-            bulk_g2s(sA + p * kOpnd, rowA0 + qo + p * kTilePart, kTilePart, &full_bar[b]);
-            bulk_g2s(sA + p * kOpnd + kTilePart, rowA1 + qo + p * kTilePart, kTilePart, &full_bar[b]);
-            bulk_g2s(sB + p * kOpnd, rowB0 + qo + p * kTilePart, kTilePart, &full_bar[b]);
-            bulk_g2s(sB + p * kOpnd + kTilePart, rowB1 + qo + p * kTilePart, kTilePart, &full_bar[b]);
-          }
-          if (!wait(&full_bar[b], n & 1u)) {
-            wait(&full_bar[b], n & 1u);   // copies may still land: one more bounded wait
-            lost = true;
-            break;
-          }
-          if (g >= 2 && !wait(&epi_bar[b], (n - 1) & 1u)) {   // accumulators of step g - 2 are read
-            lost = true;
-            break;
-          }
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t sa = smem_u32(sA), sb = smem_u32(sB);
-          const uint32_t acc_small = tmem + 256u * b, acc_big = acc_small + 128u;
-          // products: (A lo, B hi), (A hi, B lo) into the small accumulator, (A hi, B hi) into the big one
-          const int pa[3] = {1, 0, 0}, pb[3] = {0, 1, 0};
-#pragma unroll
-          for (int p = 0; p < 3; ++p)
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-              const uint64_t da = desc_sw128(sa + pa[p] * kOpnd + kk * 32);
-              const uint64_t db = desc_sw128(sb + pb[p] * kOpnd + kk * 32);
-              const bool big = p == 2;
-              const uint32_t acc = (kk > 0 || (p > 0 && !big)) ? 1u : 0u;   // fresh accumulators per step
-              asm volatile(
-                  "{\n .reg .pred pp;\n setp.ne.b32 pp, %4, 0;\n"
-                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pp;\n}\n" ::"r"(big ? acc_big : acc_small),
-                  "l"(da), "l"(db), "r"(idesc), "r"(acc));
-            }
-          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                           smem_u32(&mma_bar[b]))
-                       : "memory");
-          ++issued;
+          ++requested;
         }
       }
       s_issued = issued;
@@ -602,7 +638,7 @@ void launch_split_panel(const LevelDev& L, int kb0, int kb1, int max_R, uint8_t*
 void launch_update_tc2(const LevelDev& L, int kb0, int kb1, int grid, const uint8_t* split, const float* rscale,
                        const int64_t* prow_off, const int64_t* item_pref, cudaStream_t st) {
   if (grid <= 0 || L.n_sub <= 0) return;
-  const size_t dyn = 2 * kStage2 + 1024;
+  const size_t dyn = kStages2 * kStage2 + 1024;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_update_tc2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
