@@ -303,6 +303,16 @@ def run_gpu(args, rank, world, local_rank):
         ms64, stats64, _, _, _ = timed("fp64", pk, 1)
         st64 = stats64[-1]
 
+    # accuracy of the timed mixed form against the plain FP64 form on the same problem (both to
+    # 1e-8; outside the timed region)
+    err = None
+    if st64 is not None:
+        s_m, u_m = one_step("mixed")
+        s_p, u_p = one_step("fp64")
+        err = {"rel_l2_error_mixed_vs_plain_fp64": float(torch.linalg.norm(u_m - u_p) / torch.linalg.norm(u_p)),
+               "note": "both solved to ||g - S u|| / ||g|| <= 1e-8; parity with the FP64 oracle at 1e-12 is in tests/"}
+        del s_m, u_m, s_p, u_p
+
     # batching ablation (outside the timed region): level-1 sweeps and CUDA-core factorisation
     # in one launch for all subdomains vs one launch per subdomain
     try:
@@ -432,6 +442,7 @@ def run_gpu(args, rank, world, local_rank):
                 "h2d_bytes_per_step": int(prob.n_free * 8 + mesh_bytes), "d2h_bytes_per_step": int(prob.n_free * 8)},
         "gpu_launches": int(round(launches)),
         "batching_ablation": ablation,
+        "accuracy": err,
         "roofline": roofline,
         "cpu_baseline": cpu,
         "clocks": clk,
