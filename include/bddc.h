@@ -105,8 +105,10 @@ typedef struct {
   int use_graph;            /* 1: capture one Krylov iteration in a CUDA graph */
   int verbose;
   int profile;              /* 1: time kernel classes with CUDA events (bddc_stats.prof_*) */
-  int tensor_cores;         /* mixed: 1 = FP32 trailing updates on tcgen05 tensor cores (3xBF16 split,
-                               256-wide panels); 0 = FP32 CUDA cores */
+  int tensor_cores;         /* mixed: 1 = FP32 trailing updates of the factorisation on the tcgen05 tensor
+                               cores in 256-wide panels (SPD levels: two row-scaled FP16 parts, three
+                               products; Stokes levels: three BF16 parts, six products); 0 = FP32
+                               CUDA cores */
   int inner_steps;          /* mixed PCG: FP64 outer refinement x += S~^{-1}(g - S x) (residual with the
                                FP64 operator S) around an inner PCG with a cheaper operator S~:
                                0 = S~ from the stored interface factor (L_GG S L_GG^T - C^T R C, no

@@ -679,7 +679,7 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
   d.KC = A.alloc<double>(L.g_elems);
   const size_t ts = L.fp32 ? sizeof(float) : sizeof(double);
   if (L.fp32 && h->opts.tensor_cores && h->physics != BDDC_STOKES) {
-    // pre-split panel buffer: kPanel tiles of 24 KB (three BF16 parts) for every block row
+    // pre-split panel buffer: kPanel tiles of 16 KB (FP16 hi and lo parts) for every block row
     std::vector<int64_t> po(ns);
     int64_t rows = 0;
     for (int64_t s = 0; s < ns; ++s) {
