@@ -103,7 +103,7 @@ typedef struct {
   int refine_steps;         /* mixed: FP64 refinement steps of each interior solve in S; 0 = automatic */
   int flexible;             /* 1: Polak-Ribiere beta; 0: Fletcher-Reeves; -1: automatic (mixed -> 1) */
   int use_graph;            /* 1: capture one Krylov iteration in a CUDA graph */
-  int verbose;
+  int verbose;              /* >= 2: phase times of the host index analysis on stderr */
   int profile;              /* 1: time kernel classes with CUDA events (bddc_stats.prof_*) */
   int tensor_cores;         /* mixed: 1 = FP32 trailing updates of the factorisation on the tcgen05 tensor
                                cores in 256-wide panels (SPD levels: two row-scaled FP16 parts, three
@@ -224,10 +224,11 @@ int bddc_setup(const bddc_mesh* mesh, const bddc_partition* part, unsigned const
 int bddc_update_coef(bddc_handle h, const double* coef);
 
 /* Solve K u = f for nrhs right-hand sides (Sec. 2): condensed right-hand side
- * g = f_G - sum R_i^T K_GI K_II^{-1} f_I,i, PCG (BiCGstab for Stokes, Sec. 4) on S u_G = g
- * preconditioned by Algorithm 2,
- * stop when ||r|| / ||g|| <= tol (confirmed on the true residual), then interior recovery
- * u_I = K_II^{-1} (f_I - K_IG u_G).  rhs: device [nrhs][n_free] FP64.  x: device
+ * g = f_G - sum R_i^T K_GI K_II^{-1} f_I,i (minus K_fd u_d when prescribed values are non-zero),
+ * a Krylov method on S u_G = g preconditioned by Algorithm 2 (opts.krylov: PCG, BiCGstab for
+ * Stokes as in Sec. 4, flexible GMRES; in the mixed form PCG runs inside the FP64 outer
+ * refinement of opts.inner_steps), stop when ||g - S u_G|| / ||g|| <= tol on the true residual
+ * with the FP64 operator, then interior recovery u_I = K_II^{-1} (f_I - K_IG u_G).  rhs: device [nrhs][n_free] FP64.  x: device
  * [nrhs][n_free] FP64, output (the initial guess is zero).  stats: host, may be NULL.
  * Errors: NOT_CONVERGED (x holds the last iterate), NAN, CUDA, TIMEOUT. */
 int bddc_solve(bddc_handle h, const double* rhs, double* x, int nrhs, double tol, bddc_stats* stats);
