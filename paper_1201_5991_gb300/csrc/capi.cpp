@@ -126,6 +126,7 @@ struct Level {
   std::vector<double> tc_flops;     // per super-step: FP32-equivalent flops of the trailing update
   int64_t* item_pref = nullptr;     // [super-steps][n_sub + 1] first work item of every subdomain
   uint8_t* split = nullptr;        // scaled FP16 parts of the current super-panel (pre-split update)
+  uint8_t* split_signed = nullptr; // indefinite levels: the same with the pivot signs on the columns
   float* rscale = nullptr;         // their row unscaling factors (powers of two)
   int64_t* prow_off = nullptr;     // [n_sub] first split row of every subdomain
   double trsv_bytes[2] = {0, 0};   // algorithmic bytes of one sweep over part 0 / part 1
@@ -678,7 +679,7 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
   d.Ginv = A.alloc<double>(L.g_elems);
   d.KC = A.alloc<double>(L.g_elems);
   const size_t ts = L.fp32 ? sizeof(float) : sizeof(double);
-  if (L.fp32 && h->opts.tensor_cores && h->physics != BDDC_STOKES) {
+  if (L.fp32 && h->opts.tensor_cores) {
     // pre-split panel buffer: kPanel tiles of 16 KB (FP16 hi and lo parts) for every block row
     std::vector<int64_t> po(ns);
     int64_t rows = 0;
@@ -688,6 +689,7 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
     }
     L.prow_off = A.upload(po, st);
     L.split = A.alloc<uint8_t>(rows * kPanel * 2 * NB2 * 2);
+    if (h->physics == BDDC_STOKES) L.split_signed = A.alloc<uint8_t>(rows * kPanel * 2 * NB2 * 2);
     L.rscale = A.alloc<float>(rows * NB);
     // work items (128 x 128 output blocks) of every super-step, flattened over the subdomains
     const int np = (int)L.wide_items2.size();
@@ -835,13 +837,15 @@ void factor_level(bddc_handle_s* h, Level& L, cudaStream_t st) {
         ProfScope ps(h, BDDC_PROF_FACTOR, 0.0, std::max(0.0, fl - L.tc_flops[p]), st);
         for (int k = kb0; k < std::min(kb1, L.max_Bc); ++k)
           launch_potrf_step<T>(d, k, L.max_R, L.narrow_tiles[k], kb1, st);
-        if (L.split && L.wide_items2[p] > 0) launch_split_panel(d, kb0, kb1, L.max_R, L.split, L.rscale, L.prow_off, st);
+        if (L.split && L.wide_items2[p] > 0)
+          launch_split_panel(d, kb0, kb1, L.max_R, L.split, L.split_signed, L.rscale, L.prow_off, st);
       }
       ProfScope ps(h, BDDC_PROF_TC_UPDATE, 0.0, L.tc_flops[p], st);
       if (L.split) {
         const int64_t items = L.wide_items2[p];
         if (items > 0)
-          launch_update_tc2(d, kb0, kb1, (int)std::min<int64_t>(items, h->grid_max / 2), L.split, L.rscale,
+          launch_update_tc2(d, kb0, kb1, (int)std::min<int64_t>(items, h->grid_max / 2), L.split,
+                            L.split_signed ? L.split_signed : L.split, L.rscale,
                             L.prow_off, L.item_pref + (size_t)p * (d.n_sub + 1), st);
       } else {
         launch_update_tc(d, kb0, kb1, L.wide_items[kb0 / kPanel], st);

@@ -128,15 +128,15 @@ template <typename T>
 void launch_potrf_step(const LevelDev& L, int k, int max_R, int max_tiles, int jmax, cudaStream_t st);
 // update_tc.cu: rank-(64 (kb1-kb0)) trailing update of columns >= kb1 on the tensor cores (FP32 tiles)
 void launch_update_tc(const LevelDev& L, int kb0, int kb1, int max_items, cudaStream_t st);
-// pre-split variant (SPD FP32 levels): k_split_panel writes the two scaled FP16 parts of the
+// pre-split variant (FP32 levels): k_split_panel writes the two scaled FP16 parts of the
 // panel tiles L(i, kb0..kb1-1), i >= kb1, at split + ((prow_off[s] + i) * 4 + q - kb0) * 16 KB
 // and the row unscaling factors 2^-e_r at rscale[(prow_off[s] + i) * 64 + r]; the update makes 128 x 128
 // output blocks from them (persistent grid; item_pref[s] = first work item of subdomain s,
 // item_pref[n_sub] = number of items)
-void launch_split_panel(const LevelDev& L, int kb0, int kb1, int max_R, uint8_t* split, float* rscale,
-                        const int64_t* prow_off, cudaStream_t st);
-void launch_update_tc2(const LevelDev& L, int kb0, int kb1, int grid, const uint8_t* split, const float* rscale,
-                       const int64_t* prow_off, const int64_t* item_pref, cudaStream_t st);
+void launch_split_panel(const LevelDev& L, int kb0, int kb1, int max_R, uint8_t* split, uint8_t* split_signed,
+                        float* rscale, const int64_t* prow_off, cudaStream_t st);
+void launch_update_tc2(const LevelDev& L, int kb0, int kb1, int grid, const uint8_t* split, const uint8_t* split_b,
+                       const float* rscale, const int64_t* prow_off, const int64_t* item_pref, cudaStream_t st);
 void launch_gram_chol(const LevelDev& L, int precision_fp32, int max_nc, cudaStream_t st);
 template <typename T>
 void launch_psi(const LevelDev& L, int max_nGb, int max_nc, cudaStream_t st);

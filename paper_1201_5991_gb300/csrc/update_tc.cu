@@ -266,7 +266,8 @@ __global__ void __launch_bounds__(kThreads, 2)
 }
 
 // ---------------------------------------------------------------------------------------
-// Pre-split variant (SPD levels): FP32 from two scaled FP16 parts.  For the 64 x 256 slab of
+// Pre-split variant: FP32 from two scaled FP16 parts (indefinite levels also get a copy whose
+// columns carry the pivot signs, read as the B operand).  For the 64 x 256 slab of
 // panel row tile i, every row r is scaled by 2^e_r so that its largest entry lies in
 // [2^14, 2^15), and each scaled entry a is split into hi = fp16(a) and lo = fp16((a - hi) 2^11)
 // (the scaled low part cannot underflow).  Then a b = hi_a hi_b + (hi_a lo_b + lo_a hi_b) 2^-11
@@ -312,7 +313,8 @@ __device__ __forceinline__ void store4h(uint8_t* part, uint32_t off, const __hal
 // one block per panel row tile i (kb1 <= i < R) of every subdomain; thread (r, c4): row r of
 // tile column kb0 + c4 (the four threads of a row share its scale)
 __global__ void __launch_bounds__(256) k_split_panel(LevelDev L, int kb0, int kb1, uint8_t* __restrict__ split,
-                                                     float* __restrict__ rscale, const int64_t* __restrict__ prow_off) {
+                                                     uint8_t* __restrict__ split_signed, float* __restrict__ rscale,
+                                                     const int64_t* __restrict__ prow_off) {
   const int s = blockIdx.y;
   const SubMeta m = L.meta[s];
   if (kb1 >= m.Bc) return;
@@ -351,6 +353,18 @@ __global__ void __launch_bounds__(256) k_split_panel(LevelDev L, int kb0, int kb
     const uint32_t off = sw128_off(r, 4 * u);
     store4h(dst, off, h);
     store4h(dst + kTilePart, off, l);
+    if (split_signed) {   // indefinite levels: the B operand is L(j, q) S_q (pivot signs of column q)
+      const float* sq = (const float*)L.sgn + m.vec_off + (int64_t)(kb0 + c4) * NB + 4 * u;
+      uint8_t* dsg = split_signed + (row * kPanelTiles + c4) * (int64_t)kSplitTile;
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (sq[e] < 0.f) {
+          h[e] = __hneg(h[e]);
+          l[e] = __hneg(l[e]);
+        }
+      store4h(dsg, off, h);
+      store4h(dsg + kTilePart, off, l);
+    }
   }
 }
 
@@ -361,7 +375,8 @@ __global__ void __launch_bounds__(256) k_split_panel(LevelDev L, int kb0, int kb
 // next item) run while the epilogue warps promote the previous accumulators and write back the
 // previous item's output block.
 __global__ void __launch_bounds__(kThreads2, 1)
-    k_update_tc2(LevelDev L, int kb0, int kb1, const uint8_t* __restrict__ split, const float* __restrict__ rscale,
+    k_update_tc2(LevelDev L, int kb0, int kb1, const uint8_t* __restrict__ split,
+                 const uint8_t* __restrict__ split_b, const float* __restrict__ rscale,
                  const int64_t* __restrict__ prow_off, const int64_t* __restrict__ item_pref) {
   const int64_t n_items = item_pref[L.n_sub];
   if ((int64_t)blockIdx.x >= n_items) return;
@@ -467,8 +482,8 @@ __global__ void __launch_bounds__(kThreads2, 1)
         }
         const uint8_t* rowA0 = split + (rbase + ci0) * kPanelTiles * (int64_t)kSplitTile;
         const uint8_t* rowA1 = split + (rbase + (hasA1 ? ci0 + 1 : ci0)) * kPanelTiles * (int64_t)kSplitTile;
-        const uint8_t* rowB0 = split + (rbase + cj) * kPanelTiles * (int64_t)kSplitTile;
-        const uint8_t* rowB1 = split + (rbase + (hasB1 ? cj + 1 : cj)) * kPanelTiles * (int64_t)kSplitTile;
+        const uint8_t* rowB0 = split_b + (rbase + cj) * kPanelTiles * (int64_t)kSplitTile;
+        const uint8_t* rowB1 = split_b + (rbase + (hasB1 ? cj + 1 : cj)) * kPanelTiles * (int64_t)kSplitTile;
         uint8_t* sA = stage0 + st * kStage2;   // [A hi | A lo | B hi | B lo], 128 rows each
         uint8_t* sB = sA + 2 * kOpnd;
         mbar_expect_tx(&full_bar[st], kStage2);
@@ -628,14 +643,16 @@ __global__ void __launch_bounds__(kThreads2, 1)
 
 }  // namespace
 
-void launch_split_panel(const LevelDev& L, int kb0, int kb1, int max_R, uint8_t* split, float* rscale,
-                        const int64_t* prow_off, cudaStream_t st) {
+void launch_split_panel(const LevelDev& L, int kb0, int kb1, int max_R, uint8_t* split, uint8_t* split_signed,
+                        float* rscale, const int64_t* prow_off, cudaStream_t st) {
   if (L.n_sub <= 0 || max_R <= kb1) return;
   note_launch();
-  k_split_panel<<<dim3((unsigned)(max_R - kb1), (unsigned)L.n_sub), 256, 0, st>>>(L, kb0, kb1, split, rscale, prow_off);
+  k_split_panel<<<dim3((unsigned)(max_R - kb1), (unsigned)L.n_sub), 256, 0, st>>>(L, kb0, kb1, split, split_signed,
+                                                                                 rscale, prow_off);
 }
 
-void launch_update_tc2(const LevelDev& L, int kb0, int kb1, int grid, const uint8_t* split, const float* rscale,
+void launch_update_tc2(const LevelDev& L, int kb0, int kb1, int grid, const uint8_t* split, const uint8_t* split_b,
+                       const float* rscale,
                        const int64_t* prow_off, const int64_t* item_pref, cudaStream_t st) {
   if (grid <= 0 || L.n_sub <= 0) return;
   const size_t dyn = kStages2 * kStage2 + 1024;
@@ -645,7 +662,7 @@ void launch_update_tc2(const LevelDev& L, int kb0, int kb1, int grid, const uint
     attr = true;
   }
   note_launch();
-  k_update_tc2<<<(unsigned)grid, kThreads2, dyn, st>>>(L, kb0, kb1, split, rscale, prow_off, item_pref);
+  k_update_tc2<<<(unsigned)grid, kThreads2, dyn, st>>>(L, kb0, kb1, split, split_b, rscale, prow_off, item_pref);
 }
 
 void launch_update_tc(const LevelDev& L, int kb0, int kb1, int max_items, cudaStream_t st) {
