@@ -106,9 +106,9 @@ typedef struct {
   int verbose;              /* >= 2: phase times of the host index analysis on stderr */
   int profile;              /* 1: time kernel classes with CUDA events (bddc_stats.prof_*) */
   int tensor_cores;         /* mixed: 1 = FP32 trailing updates of the factorisation on the tcgen05 tensor
-                               cores in 256-wide panels (SPD levels: two row-scaled FP16 parts, three
-                               products; Stokes levels: three BF16 parts, six products); 0 = FP32
-                               CUDA cores */
+                               cores in 256-wide panels (two row-scaled FP16 parts, three products;
+                               Stokes levels read a copy with the pivot signs on the columns as the
+                               second operand); 0 = FP32 CUDA cores */
   int inner_steps;          /* mixed PCG: FP64 outer refinement x += S~^{-1}(g - S x) (residual with the
                                FP64 operator S) around an inner PCG with a cheaper operator S~:
                                0 = S~ from the stored interface factor (L_GG S L_GG^T - C^T R C, no

@@ -121,7 +121,6 @@ struct Level {
   std::vector<int> max_tiles;  // per factor step k
   std::vector<double> step_flops;  // tile flops of factor step k (all subdomains)
   std::vector<int> narrow_tiles;   // per step k: in-panel update tiles (256-wide panels)
-  std::vector<int> wide_items;     // per super-step: tensor-core work items
   std::vector<int64_t> wide_items2; // per super-step: 128 x 128 work items of the pre-split update (all subdomains)
   std::vector<double> tc_flops;     // per super-step: FP32-equivalent flops of the trailing update
   int64_t* item_pref = nullptr;     // [super-steps][n_sub + 1] first work item of every subdomain
@@ -487,7 +486,6 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
   L.max_tiles.assign(L.max_Bc, 0);
   L.step_flops.assign(L.max_Bc, 0.0);
   L.narrow_tiles.assign(L.max_Bc, 0);
-  L.wide_items.assign((L.max_Bc + kPanel - 1) / kPanel + 1, 0);
   L.wide_items2.assign((L.max_Bc + kPanel - 1) / kPanel + 1, 0);
   L.tc_flops.assign((L.max_Bc + kPanel - 1) / kPanel + 1, 0.0);
   const double nb3 = (double)NB * NB * NB;
@@ -509,14 +507,9 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
       L.narrow_tiles[k] = std::max(L.narrow_tiles[k], (int)cnt);
     }
     for (int kb0 = 0; kb0 < m.Bc; kb0 += kPanel) {
-      int64_t cnt = 0, tiles = 0;
-      for (int j = kb0 + kPanel; j < m.Bc; ++j) {
-        cnt += (m.R - j + 1) / 2;
-        tiles += m.R - j;
-      }
-      L.wide_items[kb0 / kPanel] = std::max(L.wide_items[kb0 / kPanel], (int)cnt);
+      int64_t tiles = 0;
+      for (int j = kb0 + kPanel; j < m.Bc; ++j) tiles += m.R - j;
       L.tc_flops[kb0 / kPanel] += 2.0 * nb3 * kPanel * (double)tiles;
-
     }
     // a sweep reads the stored triangle once and the vector in and out
     L.trsv_bytes[0] += wsz * (0.5 * (double)m.nI * (m.nI + 1) + 2.0 * m.nI);
@@ -841,15 +834,11 @@ void factor_level(bddc_handle_s* h, Level& L, cudaStream_t st) {
           launch_split_panel(d, kb0, kb1, L.max_R, L.split, L.split_signed, L.rscale, L.prow_off, st);
       }
       ProfScope ps(h, BDDC_PROF_TC_UPDATE, 0.0, L.tc_flops[p], st);
-      if (L.split) {
-        const int64_t items = L.wide_items2[p];
-        if (items > 0)
-          launch_update_tc2(d, kb0, kb1, (int)std::min<int64_t>(items, h->grid_max / 2), L.split,
-                            L.split_signed ? L.split_signed : L.split, L.rscale,
-                            L.prow_off, L.item_pref + (size_t)p * (d.n_sub + 1), st);
-      } else {
-        launch_update_tc(d, kb0, kb1, L.wide_items[kb0 / kPanel], st);
-      }
+      const int64_t items = L.wide_items2[p];
+      if (L.split && items > 0)
+        launch_update_tc2(d, kb0, kb1, (int)std::min<int64_t>(items, h->grid_max / 2), L.split,
+                          L.split_signed ? L.split_signed : L.split, L.rscale,
+                          L.prow_off, L.item_pref + (size_t)p * (d.n_sub + 1), st);
     }
   } else {
     for (int k = 0; k < L.max_Bc; ++k) {

@@ -126,13 +126,13 @@ void launch_weights(const LevelDev& L, int multiplicity, const double* unused, c
 // one block column k: diagonal tile + inverse, panel, trailing update of columns (k, jmax)
 template <typename T>
 void launch_potrf_step(const LevelDev& L, int k, int max_R, int max_tiles, int jmax, cudaStream_t st);
-// update_tc.cu: rank-(64 (kb1-kb0)) trailing update of columns >= kb1 on the tensor cores (FP32 tiles)
-void launch_update_tc(const LevelDev& L, int kb0, int kb1, int max_items, cudaStream_t st);
-// pre-split variant (FP32 levels): k_split_panel writes the two scaled FP16 parts of the
-// panel tiles L(i, kb0..kb1-1), i >= kb1, at split + ((prow_off[s] + i) * 4 + q - kb0) * 16 KB
-// and the row unscaling factors 2^-e_r at rscale[(prow_off[s] + i) * 64 + r]; the update makes 128 x 128
-// output blocks from them (persistent grid; item_pref[s] = first work item of subdomain s,
-// item_pref[n_sub] = number of items)
+// update_tc.cu, FP32 levels with tensor cores: rank-(64 (kb1-kb0)) trailing update of the columns
+// >= kb1.  k_split_panel writes the two scaled FP16 parts of the panel tiles L(i, kb0..kb1-1),
+// i >= kb1, at split + ((prow_off[s] + i) * 4 + q - kb0) * 16 KB (indefinite levels: also a copy
+// with the pivot signs on the columns at split_signed) and the row unscaling factors 2^-e_r at
+// rscale[(prow_off[s] + i) * 64 + r]; the update makes 128 x 128 output blocks from them
+// (persistent grid; item_pref[s] = first work item of subdomain s, item_pref[n_sub] = number of
+// items; split_b = split_signed on indefinite levels, else split)
 void launch_split_panel(const LevelDev& L, int kb0, int kb1, int max_R, uint8_t* split, uint8_t* split_signed,
                         float* rscale, const int64_t* prow_off, cudaStream_t st);
 void launch_update_tc2(const LevelDev& L, int kb0, int kb1, int grid, const uint8_t* split, const uint8_t* split_b,

@@ -141,11 +141,12 @@ def test_error_codes():
 
 def test_tensor_core_factor_matches_cuda_core_factor():
     # 12^3-element subdomains (n ~ 6k, 25 super-panels of 256).  Both FP32 factorisations (the
-    # tcgen05 3xBF16 trailing update and the CUDA-core update) carry FP32 rounding amplified by
-    # kappa(A_i) ~ 1e4.  Against the FP64 preconditioner (itself pinned to the oracle at 1e-10)
-    # the tensor-core error may exceed the CUDA-core one by the bf16x3 scheme's extra rounding:
-    # the dropped products a1 b2 + a2 b1 + a2 b2 add ~2^-23 relative per product, about one
-    # FP32 rounding more than an FMA, so at most 4x; a misplaced tile or wrong sign gives O(1).
+    # tcgen05 trailing update from two scaled FP16 parts and the CUDA-core update) carry FP32
+    # rounding amplified by kappa(A_i) ~ 1e4.  Against the FP64 preconditioner (itself pinned to
+    # the oracle at 1e-10) the tensor-core error may exceed the CUDA-core one by the split's extra
+    # rounding: the low parts keep 11 more bits than the high parts, so each product carries
+    # ~2^-22 relative (the dropped lo lo term and the rounding of lo), about one FP32 rounding more
+    # than an FMA, so at most 4x; a misplaced tile or wrong sign gives O(1).
     # The tensor-core path must still solve to 1e-8.
     p = meshgen.elasticity3d(24, 2, seed=2)
     ref = fem.direct_solve(p)[:, 0]
