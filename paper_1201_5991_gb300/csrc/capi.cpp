@@ -128,6 +128,7 @@ struct Level {
   uint8_t* split_signed = nullptr; // indefinite levels: the same with the pivot signs on the columns
   float* rscale = nullptr;         // their row unscaling factors (powers of two)
   int64_t* prow_off = nullptr;     // [n_sub] first split row of every subdomain
+  TensorMap128 tile_tmap{};        // the FP32 tiles as [rows][64] for the update's TMA reduce-adds
   double trsv_bytes[2] = {0, 0};   // algorithmic bytes of one sweep over part 0 / part 1
   double trmv_bytes = 0;           // algorithmic bytes of one factor-based inner Schur product
   // sweep task lists [part][direction] in dependency order and their control words
@@ -702,6 +703,10 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
   }
   if (L.fp32) {
     d.tiles = A.alloc<float>(L.tile_elems);
+    if (L.split) {
+      const int r = make_tile_tmap(&L.tile_tmap, (float*)d.tiles, L.tile_elems);
+      if (r) fail(BDDC_ERR_CUDA, "cuTensorMapEncodeTiled for the factor tiles failed (error " + std::to_string(r) + ")");
+    }
     d.dinv = A.alloc<float>(L.dinv_elems);
     d.psi = A.alloc<float>(L.psi_elems);
     L.locA = A.alloc<float>(L.n_vec);
@@ -838,7 +843,7 @@ void factor_level(bddc_handle_s* h, Level& L, cudaStream_t st) {
       if (L.split && items > 0)
         launch_update_tc2(d, kb0, kb1, (int)std::min<int64_t>(items, h->grid_max / 2), L.split,
                           L.split_signed ? L.split_signed : L.split, L.rscale,
-                          L.prow_off, L.item_pref + (size_t)p * (d.n_sub + 1), st);
+                          L.prow_off, L.item_pref + (size_t)p * (d.n_sub + 1), L.tile_tmap, st);
     }
   } else {
     for (int k = 0; k < L.max_Bc; ++k) {

@@ -135,8 +135,16 @@ void launch_potrf_step(const LevelDev& L, int k, int max_R, int max_tiles, int j
 // items; split_b = split_signed on indefinite levels, else split)
 void launch_split_panel(const LevelDev& L, int kb0, int kb1, int max_R, uint8_t* split, uint8_t* split_signed,
                         float* rscale, const int64_t* prow_off, cudaStream_t st);
+// The update adds its output into the tiles with TMA reduce-adds through this tensor map: the
+// FP32 tile buffer viewed as [tile_elems / 64 rows][64 columns], 32 x 32 boxes, 128-byte
+// swizzle.  make_tile_tmap returns 0 or the driver's error code.
+struct TensorMap128 {
+  alignas(64) uint64_t opaque[16];   // a CUtensorMap
+};
+int make_tile_tmap(TensorMap128* map, float* tiles, int64_t tile_elems);
 void launch_update_tc2(const LevelDev& L, int kb0, int kb1, int grid, const uint8_t* split, const uint8_t* split_b,
-                       const float* rscale, const int64_t* prow_off, const int64_t* item_pref, cudaStream_t st);
+                       const float* rscale, const int64_t* prow_off, const int64_t* item_pref,
+                       const TensorMap128& tmap, cudaStream_t st);
 void launch_gram_chol(const LevelDev& L, int precision_fp32, int max_nc, cudaStream_t st);
 template <typename T>
 void launch_psi(const LevelDev& L, int max_nGb, int max_nc, cudaStream_t st);

@@ -26,10 +26,12 @@
 // and one thread issues 12 MMAs (3 products x 4 K-steps, M = N = 128) into one of two TMEM
 // accumulator pairs (hi hi; the two cross products); eight epilogue warps promote each pair
 // into FP32 registers after every column and finally update the output tiles.
+#include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstring>
 
 #include "internal.h"
 
@@ -78,6 +80,7 @@ constexpr uint32_t kOpnd = 2 * kTilePart;        // one part of a 128-row operan
 constexpr uint32_t kStage2 = 4 * kOpnd;          // A hi, A lo, B hi, B lo (64 KB)
 constexpr int kThreads2 = 288;                   // 8 epilogue warps + 1 producer / MMA warp
 constexpr int kStages2 = 3;                      // shared-memory stages (copies run two steps ahead)
+constexpr uint32_t kEpiBox = 32 * 128;           // per epilogue warp: one 32 x 32 FP32 output box (4 KB)
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
@@ -161,11 +164,15 @@ __global__ void __launch_bounds__(256) k_split_panel(LevelDev L, int kb0, int kb
 // panel column); step g uses shared-memory stage g % 3 (its copies are requested two steps
 // ahead) and TMEM accumulator pair g & 1, so the copies and MMAs of the next steps (also of the
 // next item) run while the epilogue warps promote the previous accumulators and write back the
-// previous item's output block.
+// previous item's output block.  The write-back is a TMA reduce-add: each epilogue warp scales
+// its 32 x 64 part of the block into a swizzled shared-memory box, 32 columns at a time, and one
+// lane adds the box into the tiles in L2 (the output is never read into the SM; every element
+// receives exactly one add per launch, so the result does not depend on timing).
 __global__ void __launch_bounds__(kThreads2, 1)
     k_update_tc2(LevelDev L, int kb0, int kb1, const uint8_t* __restrict__ split,
                  const uint8_t* __restrict__ split_b, const float* __restrict__ rscale,
-                 const int64_t* __restrict__ prow_off, const int64_t* __restrict__ item_pref) {
+                 const int64_t* __restrict__ prow_off, const int64_t* __restrict__ item_pref,
+                 const __grid_constant__ CUtensorMap tmap) {
   const int64_t n_items = item_pref[L.n_sub];
   if ((int64_t)blockIdx.x >= n_items) return;
   const int nq = kb1 - kb0;   // every subdomain with items has kb1 < Bc
@@ -348,6 +355,7 @@ __global__ void __launch_bounds__(kThreads2, 1)
     const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
     const uint32_t col0 = 64u * (uint32_t)(warp >> 2);
     const int erow = 32 * (warp & 3) + lane;
+    uint8_t* box = stage0 + kStages2 * kStage2 + warp * kEpiBox;   // 1024-byte aligned
     uint32_t g = 0;
     for (int64_t it = blockIdx.x; it < n_items && !lost; it += gridDim.x) {
       int s, j, i0;
@@ -395,23 +403,45 @@ __global__ void __launch_bounds__(kThreads2, 1)
       const int ti = erow < 64 ? i0 : i0 + 1;
       const int tj = col0 < 64 ? j : j + 1;
       const bool ok = (erow < 64 || hasA1) && (col0 < 64 || hasB1) && (ti >= m.Bc || tj <= ti);
-      if (ok) {
+      if (ok) {   // warp-uniform: the warp's 32 rows and 64 columns lie in one output tile
         const int64_t rbase = prow_off[s];
-        const float sa = rscale[(rbase + ti) * NB + (erow & 63)];
+        // negated row factor: the tiles receive x + (-(acc sa) f), which equals x - (acc sa) f
+        const float sa = -rscale[(rbase + ti) * NB + (erow & 63)];
         const float4* sb = (const float4*)(rscale + (rbase + tj) * NB);
-        float* c = (float*)L.tiles + m.tile_off + tile_index(ti, tj, m.Bc) * NB2 + (erow & 63) * NB;
+        // row of the warp's first output row in the [rows][64] view of the tile buffer
+        const int y = (int)((m.tile_off + tile_index(ti, tj, m.Bc) * NB2) / NB) + (32 * (warp & 3) & 63);
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
-          float4 x = *(float4*)(c + 4 * u);
-          const float4 f = __ldg(sb + u);   // both factors are powers of two: the products are exact
-          x.x -= (racc[4 * u + 0] * sa) * f.x;
-          x.y -= (racc[4 * u + 1] * sa) * f.y;
-          x.z -= (racc[4 * u + 2] * sa) * f.z;
-          x.w -= (racc[4 * u + 3] * sa) * f.w;
-          *(float4*)(c + 4 * u) = x;
+        for (int hh = 0; hh < 2; ++hh) {
+          // the previous reduce-add out of this warp's box has read it
+          if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+          __syncwarp();
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const int u = 8 * hh + k;
+            const float4 f = __ldg(sb + u);   // both factors are powers of two: the products are exact
+            float4 x;
+            x.x = (racc[4 * u + 0] * sa) * f.x;
+            x.y = (racc[4 * u + 1] * sa) * f.y;
+            x.z = (racc[4 * u + 2] * sa) * f.z;
+            x.w = (racc[4 * u + 3] * sa) * f.w;
+            // 128-byte swizzle: 16-byte chunk k of box row r sits at chunk k ^ (r & 7)
+            *(float4*)(box + lane * 128 + ((k ^ (lane & 7)) << 4)) = x;
+          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) {
+            asm volatile(
+                "cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                    (uint64_t)&tmap),
+                "r"(32 * hh), "r"(y), "r"(smem_u32(box))
+                : "memory");
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+          }
         }
       }
     }
+    // the reduce-adds are complete (and the boxes free) before the CTA ends, also on the error path
+    if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     if (lost && lane == 0) atomicExch(L.status + 2, 4);
   }
   __syncthreads();
@@ -440,17 +470,48 @@ void launch_split_panel(const LevelDev& L, int kb0, int kb1, int max_R, uint8_t*
 }
 
 void launch_update_tc2(const LevelDev& L, int kb0, int kb1, int grid, const uint8_t* split, const uint8_t* split_b,
-                       const float* rscale,
-                       const int64_t* prow_off, const int64_t* item_pref, cudaStream_t st) {
+                       const float* rscale, const int64_t* prow_off, const int64_t* item_pref,
+                       const TensorMap128& tmap, cudaStream_t st) {
   if (grid <= 0 || L.n_sub <= 0) return;
-  const size_t dyn = kStages2 * kStage2 + 1024;
+  const size_t dyn = kStages2 * kStage2 + 8 * kEpiBox + 1024;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_update_tc2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     attr = true;
   }
   note_launch();
-  k_update_tc2<<<(unsigned)grid, kThreads2, dyn, st>>>(L, kb0, kb1, split, split_b, rscale, prow_off, item_pref);
+  CUtensorMap m;
+  static_assert(sizeof(CUtensorMap) == sizeof(TensorMap128), "tensor map size");
+  std::memcpy(&m, &tmap, sizeof(m));
+  k_update_tc2<<<(unsigned)grid, kThreads2, dyn, st>>>(L, kb0, kb1, split, split_b, rscale, prow_off, item_pref, m);
+}
+
+int make_tile_tmap(TensorMap128* map, float* tiles, int64_t tile_elems) {
+  using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static EncodeTiled encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return (int)CUDA_ERROR_NOT_FOUND;
+    encode = (EncodeTiled)fn;
+  }
+  const int64_t rows = tile_elems / NB;
+  if (rows <= 0 || rows >= ((int64_t)1 << 31)) return (int)CUDA_ERROR_INVALID_VALUE;   // int32 box coordinates
+  const cuuint64_t dims[2] = {(cuuint64_t)NB, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)NB * sizeof(float)};
+  const cuuint32_t box[2] = {32, 32};
+  const cuuint32_t estr[2] = {1, 1};
+  CUtensorMap m;
+  const CUresult r = encode(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, tiles, dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return (int)r;
+  std::memcpy(map, &m, sizeof(m));
+  return 0;
 }
 
 }  // namespace bddc
