@@ -315,12 +315,14 @@ def run_gpu(args, rank, world, local_rank):
 
     # batching ablation (outside the timed region): level-1 sweeps and CUDA-core factorisation
     # in one launch for all subdomains vs one launch per subdomain
-    try:
-        s_ab = BddcSolver(prob, precision="mixed", stream=stream)
-        ablation = {k: round(v, 3) for k, v in s_ab.batching_ablation().items()}
-        del s_ab
-    except capi.BddcError as e:
-        ablation = {"unavailable": str(e)}
+    ablation = None
+    if not args.no_ablation:
+        try:
+            s_ab = BddcSolver(prob, precision="mixed", stream=stream)
+            ablation = {k: round(v, 3) for k, v in s_ab.batching_ablation().items()}
+            del s_ab
+        except capi.BddcError as e:
+            ablation = {"unavailable": str(e)}
 
     # end to end through the public host-buffer entry point
     fh = np.ascontiguousarray(prob.f[:, 0])
@@ -489,6 +491,7 @@ def main():
     ap.add_argument("--ref-iterations", type=int, default=51)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 form (profiling runs)")
+    ap.add_argument("--no-ablation", action="store_true", help="skip the batching ablation (profiling runs)")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
     args = ap.parse_args()
     WORKLOAD = args.workload

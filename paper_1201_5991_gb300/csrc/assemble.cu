@@ -94,18 +94,53 @@ __global__ void k_elem_q1(int physics, int64_t n_elems, const double* __restrict
     const double lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
     const double mu = E / (2.0 * (1.0 + nu));
     constexpr int ND = NN * DIM;
-    for (int idx = lane; idx < ND * ND; idx += 32) {
-      int row = idx / ND, col = idx % ND;
-      int a = row / DIM, i = row % DIM, b = col / DIM, j = col % DIM;
-      double s = 0.0;
-      for (int g = 0; g < NN; ++g) {
-        double dd = 0.0;
-        for (int k = 0; k < DIM; ++k) dd += sG[w][g][a][k] * sG[w][g][b][k];
-        double v = lam * sG[w][g][a][i] * sG[w][g][b][j] + mu * sG[w][g][a][j] * sG[w][g][b][i];
-        if (i == j) v += mu * dd;
-        s += sW[w][g] * v;
+    // lane p takes the node pair (a, b), a <= b, and makes the DIM x DIM block
+    //   K_ab[i][j] = sum_g w_g (lam ga_i gb_j + mu ga_j gb_i + mu (ga . gb) delta_ij)
+    //             = lam P_ij + mu P_ji + mu tr(P) delta_ij,   P = sum_g w_g ga gb^T
+    // (ga, gb: physical gradients of the shape functions of nodes a, b at Gauss point g) and its
+    // mirror K_ba = K_ab^T: DIM^2 products per Gauss point and pair (FP64 is the scarce unit)
+    double* kout = ke + slot * ND * ND;
+    for (int p = lane; p < NN * (NN + 1) / 2; p += 32) {
+      int a = 0, r = p;
+      while (r >= NN - a) {
+        r -= NN - a;
+        ++a;
       }
-      ke[slot * ND * ND + idx] = s;
+      const int b = a + r;
+      double P[DIM][DIM];
+#pragma unroll
+      for (int i = 0; i < DIM; ++i)
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) P[i][j] = 0.0;
+#pragma unroll 2
+      for (int g = 0; g < NN; ++g) {
+        const double wg = sW[w][g];
+        double ga[DIM], gb[DIM];
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+          ga[k] = wg * sG[w][g][a][k];
+          gb[k] = sG[w][g][b][k];
+        }
+#pragma unroll
+        for (int i = 0; i < DIM; ++i)
+#pragma unroll
+          for (int j = 0; j < DIM; ++j) P[i][j] += ga[i] * gb[j];
+      }
+      double tr = 0.0;
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) tr += P[k][k];
+      double blk[DIM][DIM];
+#pragma unroll
+      for (int i = 0; i < DIM; ++i)
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) blk[i][j] = lam * P[i][j] + mu * P[j][i] + (i == j ? mu * tr : 0.0);
+#pragma unroll
+      for (int i = 0; i < DIM; ++i)
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) {
+          kout[(a * DIM + i) * ND + b * DIM + j] = blk[i][j];
+          if (a != b) kout[(b * DIM + j) * ND + a * DIM + i] = blk[i][j];
+        }
     }
   }
 }

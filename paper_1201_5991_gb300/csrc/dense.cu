@@ -41,17 +41,45 @@ __device__ __forceinline__ void load_kmajor(T* s, const T* __restrict__ g) {
   }
 }
 
+// 16-byte aligned vectors of four entries (global or shared memory)
+template <typename T>
+__device__ __forceinline__ void load4(T (&v)[4], const T* p);
+template <>
+__device__ __forceinline__ void load4<float>(float (&v)[4], const float* p) {
+  const float4 a = *(const float4*)p;
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = a.z;
+  v[3] = a.w;
+}
+template <>
+__device__ __forceinline__ void load4<double>(double (&v)[4], const double* p) {
+  const double2 a = *(const double2*)p, b = *(const double2*)(p + 2);
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = b.x;
+  v[3] = b.y;
+}
+template <typename T>
+__device__ __forceinline__ void store4(T* p, const T (&v)[4]);
+template <>
+__device__ __forceinline__ void store4<float>(float* p, const float (&v)[4]) {
+  *(float4*)p = make_float4(v[0], v[1], v[2], v[3]);
+}
+template <>
+__device__ __forceinline__ void store4<double>(double* p, const double (&v)[4]) {
+  *(double2*)p = make_double2(v[0], v[1]);
+  *(double2*)(p + 2) = make_double2(v[2], v[3]);
+}
+
 // acc[i][j] += sum_m A[4ty+i][m] * B[4tx+j][m] with both operands k-major in shared memory
 template <typename T>
 __device__ __forceinline__ void gemm_nt_4x4(const T* As, const T* Bs, T acc[4][4], int tx, int ty) {
 #pragma unroll 8
   for (int m = 0; m < NB; ++m) {
     T a[4], b[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      a[q] = As[m * LDS + 4 * ty + q];
-      b[q] = Bs[m * LDS + 4 * tx + q];
-    }
+    load4(a, As + m * LDS + 4 * ty);   // LDS and the tile offsets keep these 16-byte aligned
+    load4(b, Bs + m * LDS + 4 * tx);
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -65,7 +93,7 @@ __global__ void k_potrf_diag(LevelDev L, int k) {
   const int s = blockIdx.x;
   const SubMeta m = L.meta[s];
   if (k >= m.Bc) return;
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   T(*A)[NB + 1] = (T(*)[NB + 1])smem_raw;                 // the tile, then its factor L
   T(*X)[NB + 1] = (T(*)[NB + 1])(smem_raw + sizeof(T) * NB * (NB + 1));   // L^{-1}
   __shared__ int bad;
@@ -77,38 +105,56 @@ __global__ void k_potrf_diag(LevelDev L, int k) {
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
   __shared__ T sg[NB];
-  for (int j = 0; j < NB; ++j) {
-    if (threadIdx.x == 0) {
+  // Right-looking elimination on the unscaled columns, one barrier per column: at column j
+  // every entry below the pivot is updated as a_ic -= a_ij a_cj / d_j (d_j = a_jj after the
+  // updates of the columns before j), which equals l_ij s_j l_cj with l_ij = a_ij / (s_j
+  // sqrt|d_j|), s_j = sign d_j; the columns are scaled to L afterwards.  Thread t owns row
+  // i = t / 4 and the columns c = t % 4 (mod 4); column j is only read at step j and only
+  // columns > j are written, so no entry is read and written in the same step.
+  {
+    const int i = threadIdx.x >> 2, cls = threadIdx.x & 3;
+    for (int j = 0; j < NB - 1; ++j) {
       T d = A[j][j];
-      T sj = (T)1;
-      if (L.indefinite) {
-        if (!(fabs(d) > (T)1e-30)) {
-          bad = 1;
-          d = (T)1;
-        }
-        if (d < (T)0) {
-          sj = (T)-1;
-          d = -d;
-        }
-      } else if (!(d > (T)0)) {
-        bad = 1;
+      // a failed pivot (flagged below from the same value) continues as 1, as in the scaling
+      if (L.indefinite ? !(fabs(d) > (T)1e-30) : !(d > (T)0)) d = (T)1;
+      if (i > j) {
+        const T f = A[i][j] / d;
+        const int c1 = j + 1 + ((cls - j - 1) & 3);   // first column > j of this thread's class
+        for (int c = c1; c <= i; c += 4) A[i][c] -= f * A[c][j];
+      }
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x < NB) {
+    const int j = threadIdx.x;
+    T d = A[j][j];
+    T sj = (T)1;
+    bool b = false;
+    if (L.indefinite) {
+      if (!(fabs(d) > (T)1e-30)) {
+        b = true;
         d = (T)1;
       }
-      A[j][j] = sqrt(d);
-      sg[j] = sj;
+      if (d < (T)0) {
+        sj = (T)-1;
+        d = -d;
+      }
+    } else if (!(d > (T)0)) {
+      b = true;
+      d = (T)1;
     }
-    __syncthreads();
-    const T piv = A[j][j] * sg[j];   // l_ij = a_ij / (s_j l_jj)
-    for (int i = j + 1 + threadIdx.x; i < NB; i += blockDim.x) A[i][j] /= piv;
-    __syncthreads();
-    const int w = NB - 1 - j;
-    const T sj = sg[j];
-    for (int t = threadIdx.x; t < w * w; t += blockDim.x) {
-      const int i = j + 1 + t / w, c = j + 1 + t % w;
-      if (c <= i) A[i][c] -= A[i][j] * sj * A[c][j];
-    }
-    __syncthreads();
+    if (b) bad = 1;
+    sg[j] = sj;
+    X[0][j] = sqrt(d);   // pivots, kept in the first row of X until the inverse is formed
   }
+  __syncthreads();
+  for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
+    const int r = t / NB, c = t % NB;
+    if (r > c) A[r][c] /= X[0][c] * sg[c];
+  }
+  __syncthreads();
+  if (threadIdx.x < NB) A[threadIdx.x][threadIdx.x] = X[0][threadIdx.x];
+  __syncthreads();
   if (threadIdx.x < NB) ((T*)L.sgn)[m.vec_off + (int64_t)k * NB + threadIdx.x] = sg[threadIdx.x];
   if (threadIdx.x == 0 && bad) flag_breakdown(L.status, s);
   // X = L^{-1} by forward substitution on the columns, in shared memory: four threads per
@@ -144,7 +190,7 @@ __global__ void k_trsm_panel(LevelDev L, int k) {
   const SubMeta m = L.meta[s];
   const int i = k + 1 + blockIdx.x;
   if (k >= m.Bc || i >= m.R) return;
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* As = (T*)smem_raw;
   T* Xs = As + NB * LDS;
   T* g = tile_ptr<T>(m, L.tiles, i, k);
@@ -157,9 +203,12 @@ __global__ void k_trsm_panel(LevelDev L, int k) {
   __syncthreads();
   const T* sk = (const T*)L.sgn + m.vec_off + (int64_t)k * NB;   // L(i,k) = A(i,k) L_kk^{-T} S_k
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < 4; ++a) {
+    T v[4];
 #pragma unroll
-    for (int b = 0; b < 4; ++b) g[(4 * ty + a) * NB + 4 * tx + b] = acc[a][b] * sk[4 * tx + b];
+    for (int b = 0; b < 4; ++b) v[b] = acc[a][b] * sk[4 * tx + b];
+    store4(g + (4 * ty + a) * NB + 4 * tx, v);
+  }
 }
 
 // ---- step k, part 3: trailing update A(i,j) -= L(i,k) L(j,k)^T, k < j <= i, j < min(Bc, jmax) --
@@ -179,7 +228,7 @@ __global__ void k_syrk_update(LevelDev L, int k, int jmax) {
     t -= cnt;
   }
   if (i < 0) return;
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* As = (T*)smem_raw;
   T* Bs = As + NB * LDS;
   load_kmajor(As, tile_ptr<T>(m, L.tiles, i, k));
@@ -195,9 +244,13 @@ __global__ void k_syrk_update(LevelDev L, int k, int jmax) {
   gemm_nt_4x4(As, Bs, acc, tx, ty);
   T* c = tile_ptr<T>(m, L.tiles, i, j);
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < 4; ++a) {
+    T v[4];
+    load4(v, c + (4 * ty + a) * NB + 4 * tx);
 #pragma unroll
-    for (int b = 0; b < 4; ++b) c[(4 * ty + a) * NB + 4 * tx + b] -= acc[a][b];
+    for (int b = 0; b < 4; ++b) v[b] -= acc[a][b];
+    store4(c + (4 * ty + a) * NB + 4 * tx, v);
+  }
 }
 
 // ---- G = Y_G Y_G^T in FP64, Cholesky, inverse; K_C = G^{-1} - rho I ----------------------
@@ -380,9 +433,14 @@ __global__ void k_psi_rhs(LevelDev L) {
   }
 }
 
-// Psi_G = L_GG^{-T} Z, backward block sweep; one block per (column chunk of 16, subdomain)
+// Psi_G = L_GG^{-T} Z, backward block sweep; one block per (column chunk of 16, subdomain).
+// Block row i: rhs = Z_i - sum_{j > i} L(j,i)^T X_j, then X_i = L_ii^{-T} rhs.  Thread t sums the
+// rows 16 g .. 16 g + 15 (g = t / 64) of every tile L(j,i) for the columns 4 tc .. 4 tc + 3
+// (tc = t % 16) and the right-hand sides 4 tq .. 4 tq + 3 (tq = (t / 16) % 4): a 4 x 4 register
+// block, one vector load of L and four (broadcast) loads of X per 16 products; the four row
+// groups meet in shared memory in a fixed order.
 template <typename T>
-__global__ void k_trsm_back_psi(LevelDev L) {
+__global__ void __launch_bounds__(256) k_trsm_back_psi(LevelDev L) {
   const int s = blockIdx.y;
   const SubMeta m = L.meta[s];
   const int nc = m.nc;
@@ -390,25 +448,34 @@ __global__ void k_trsm_back_psi(LevelDev L) {
   if (c0 >= nc) return;
   const int ncols = min(16, nc - c0);
   T* Z = (T*)L.psi + m.psi_off;
-  __shared__ T part[4][NB][16];
+  __shared__ T part[4][NB][17];
   __shared__ T rhs[NB][16];
-  const int c = threadIdx.x % NB;      // tile column
-  const int rq = threadIdx.x / NB;     // row quarter (16 rows)
+  const int g = threadIdx.x >> 6, tc = threadIdx.x & 15, tq = (threadIdx.x >> 4) & 3;
   for (int i = m.Bc - 1; i >= m.nIb; --i) {
-    T acc[16];
+    T acc[4][4];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) acc[q] = (T)0;
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = (T)0;
     for (int j = i + 1; j < m.Bc; ++j) {
-      const T* Lt = tile_ptr<T>(m, L.tiles, j, i);
-      const T* Xj = Z + (int64_t)(j - m.nIb) * NB * nc + c0;
-      for (int r = rq * 16; r < rq * 16 + 16; ++r) {
-        const T l = Lt[r * NB + c];
+      const T* Lt = tile_ptr<T>(m, L.tiles, j, i) + 16 * g * NB + 4 * tc;
+      const T* Xj = Z + ((int64_t)(j - m.nIb) * NB + 16 * g) * nc + c0 + 4 * tq;
+#pragma unroll 4
+      for (int r = 0; r < 16; ++r) {
+        T l[4], x[4];
+        load4(l, Lt + r * NB);
 #pragma unroll
-        for (int q = 0; q < 16; ++q)
-          if (q < ncols) acc[q] += l * Xj[(int64_t)r * nc + q];
+        for (int b = 0; b < 4; ++b) x[b] = 4 * tq + b < ncols ? Xj[(int64_t)r * nc + b] : (T)0;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] += l[a] * x[b];
       }
     }
-    for (int q = 0; q < 16; ++q) part[rq][c][q] = acc[q];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) part[g][4 * tc + a][4 * tq + b] = acc[a][b];
     __syncthreads();
     T* Zi = Z + (int64_t)(i - m.nIb) * NB * nc + c0;
     for (int t = threadIdx.x; t < NB * 16; t += blockDim.x) {
