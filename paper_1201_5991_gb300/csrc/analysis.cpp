@@ -64,20 +64,27 @@ double cross_norm(const Pt& p, const Pt& o, const double* u) {
   return std::sqrt(c0 * c0 + c1 * c1 + c2 * c2);
 }
 
-// fn(i) for i in [0, n) on up to 16 host threads (independent iterations)
-void parallel_range(int64_t n, const std::function<void(int64_t)>& fn) {
-  const unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+constexpr unsigned kWorkers = 16;
+
+// fn(i, w) for i in [0, n) on up to kWorkers host threads (independent iterations); w < kWorkers
+// names the thread, so that per-thread scratch can be indexed by it
+void parallel_range_worker(int64_t n, const std::function<void(int64_t, int)>& fn) {
+  const unsigned nt = std::max(1u, std::min(kWorkers, std::thread::hardware_concurrency()));
   if (n < 4 || nt == 1) {
-    for (int64_t i = 0; i < n; ++i) fn(i);
+    for (int64_t i = 0; i < n; ++i) fn(i, 0);
     return;
   }
   std::atomic<int64_t> next{0};
   std::vector<std::thread> th;
   for (unsigned t = 0; t < nt; ++t)
-    th.emplace_back([&]() {
-      for (int64_t i; (i = next.fetch_add(1)) < n;) fn(i);
+    th.emplace_back([&, t]() {
+      for (int64_t i; (i = next.fetch_add(1)) < n;) fn(i, (int)t);
     });
   for (auto& t : th) t.join();
+}
+
+void parallel_range(int64_t n, const std::function<void(int64_t)>& fn) {
+  parallel_range_worker(n, [&](int64_t i, int) { fn(i); });
 }
 
 }  // namespace
@@ -121,14 +128,23 @@ bool analyze_level(const LevelMesh& mesh, unsigned constraints, bool all_corners
       return false;
     }
   std::vector<std::vector<int64_t>> sub_nodes(ns);
-  parallel_range(ns, [&](int64_t s) {
+  std::vector<std::vector<char>> seen(kWorkers);   // per worker: node already listed
+  parallel_range_worker(ns, [&](int64_t s, int w) {
     auto& v = sub_nodes[s];
+    std::vector<char>& mk = seen[w];
+    if ((int64_t)mk.size() < nn) mk.assign(nn, 0);
     for (int64_t k = m.sub_elem_ptr[s]; k < m.sub_elem_ptr[s + 1]; ++k) {
       int64_t e = m.sub_elems[k];
-      for (int64_t q = mesh.en_ptr[e]; q < mesh.en_ptr[e + 1]; ++q) v.push_back(mesh.en[q]);
+      for (int64_t q = mesh.en_ptr[e]; q < mesh.en_ptr[e + 1]; ++q) {
+        const int64_t p = mesh.en[q];
+        if (!mk[p]) {
+          mk[p] = 1;
+          v.push_back(p);
+        }
+      }
     }
+    for (int64_t p : v) mk[p] = 0;
     std::sort(v.begin(), v.end());
-    v.erase(std::unique(v.begin(), v.end()), v.end());
   });
   // node -> sharing set (ascending subdomain ids)
   m.node_sub_ptr.assign(nn + 1, 0);
@@ -511,20 +527,17 @@ void next_level_mesh(const LevelMesh& mesh, const LevelMaps& maps, const int32_t
   const int64_t ns = maps.n_sub();
   n.n_elems = ns;
   n.en_ptr.assign(1, 0);
-  n.ed_ptr.assign(1, 0);
   for (int64_t s = 0; s < ns; ++s) {
     int64_t last = -1;
     for (int64_t k = maps.sub_coarse_ptr[s]; k < maps.sub_coarse_ptr[s + 1]; ++k) {
       int64_t cd = maps.sub_coarse[k];
       int64_t g = maps.coarse_glob[cd];
-      if (g != last) {
+      if (g != last) {   // the subdomain's coarse DOFs come glob by glob, all components
         n.en.push_back(node_of_glob[g]);
         last = g;
       }
-      n.ed.push_back(cd);
     }
     n.en_ptr.push_back((int64_t)n.en.size());
-    n.ed_ptr.push_back((int64_t)n.ed.size());
   }
   n.part.assign(part, part + ns);
   n.n_sub = n_sub_next;

@@ -24,8 +24,8 @@ struct LevelMesh {
   std::vector<int64_t> nd_ptr;         // node -> its DOFs (CSR)
   std::vector<int32_t> nd_comp;        //   component of each node DOF
   std::vector<int64_t> nd_id;          //   level DOF id, -1 = prescribed
-  std::vector<int64_t> en_ptr, en;     // element -> nodes
-  std::vector<int64_t> ed_ptr, ed;     // element -> DOF ids of its matrix (-1 = prescribed)
+  std::vector<int64_t> en_ptr, en;     // element -> nodes; the element matrix's DOFs are the
+                                       // DOFs of its nodes in this order (nd_id, -1 = prescribed)
   std::vector<int32_t> part;           // element -> subdomain
   uint32_t rigid_mask = 1u;            // components that carry the floating (rigid) modes
   int rigid_points = 1;                // constrained points needed: 1, 2 (2D elasticity), 3 (3D elasticity)

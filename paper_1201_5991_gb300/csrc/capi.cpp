@@ -208,7 +208,6 @@ struct bddc_handle_s {
   double* d_coords = nullptr;
   int32_t* d_conn = nullptr;
   double* d_coef = nullptr;
-  int64_t* d_edof = nullptr;           // element -> full DOF ids
   int64_t* d_free_of_full = nullptr;
   int* d_status = nullptr;
   // non-zero prescribed values: lift = -K_fd u_d, added to every right-hand side
@@ -364,6 +363,29 @@ void flush_profile(bddc_handle_s* h) {
   h->prof_pending.clear();
 }
 
+constexpr int kHostWorkers = 16;
+
+// fn(i, w) for i in [0, n) on up to kHostWorkers host threads; w < kHostWorkers names the thread,
+// so that per-thread scratch can be indexed by it
+void parallel_for_worker(int64_t n, const std::function<void(int64_t, int)>& fn) {
+  const unsigned nt = std::max(1u, std::min((unsigned)kHostWorkers, std::thread::hardware_concurrency()));
+  if (n < 4 || nt == 1) {
+    for (int64_t i = 0; i < n; ++i) fn(i, 0);
+    return;
+  }
+  std::vector<std::thread> th;
+  std::atomic<int64_t> next{0};
+  for (unsigned t = 0; t < nt; ++t)
+    th.emplace_back([&, t]() {
+      for (;;) {
+        const int64_t i = next.fetch_add(1);
+        if (i >= n) break;
+        fn(i, (int)t);
+      }
+    });
+  for (auto& t : th) t.join();
+}
+
 void parallel_for(int64_t n, const std::function<void(int64_t)>& fn) {
   unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
   if (n < 4 || nt == 1) {
@@ -402,20 +424,11 @@ void build_level1_mesh(bddc_handle_s* h, LevelMesh* out) {
   }
   m.en_ptr.resize(h->n_elems + 1);
   m.en.resize(h->n_elems * h->npe);
-  m.ed_ptr.resize(h->n_elems + 1);
-  m.ed.resize(h->n_elems * h->npe * h->ndof);
-  for (int64_t e = 0; e <= h->n_elems; ++e) {
-    m.en_ptr[e] = e * h->npe;
-    m.ed_ptr[e] = e * h->npe * h->ndof;
-  }
+  for (int64_t e = 0; e <= h->n_elems; ++e) m.en_ptr[e] = e * h->npe;
   const int64_t chunk = 4096;
   parallel_for((h->n_elems + chunk - 1) / chunk, [&](int64_t b) {
-    for (int64_t e = b * chunk; e < std::min(h->n_elems, (b + 1) * chunk); ++e)
-      for (int a = 0; a < h->npe; ++a) {
-        const int64_t p = h->conn[e * h->npe + a];
-        m.en[e * h->npe + a] = p;
-        for (int c = 0; c < h->ndof; ++c) m.ed[(e * h->npe + a) * h->ndof + c] = h->free_of_full[p * h->ndof + c];
-      }
+    const int64_t e1 = std::min(h->n_elems, (b + 1) * chunk) * h->npe;
+    for (int64_t q = b * chunk * h->npe; q < e1; ++q) m.en[q] = h->conn[q];
   });
   m.part = h->parts[0];
   m.n_dof = h->n_free;
@@ -518,66 +531,74 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
     L.trmv_bytes += wsz * ((double)m.nG * (m.nG + 1) + 4.0 * m.nG);   // the triangle twice, vectors
   }
 
-  // element slots (subdomain order) and their padded local DOF positions
+  // element slots (subdomain order) and their padded local DOF positions; an element's matrix
+  // DOFs are the DOFs of its nodes in node order
   const int64_t nel = ms.n_elems;
-  std::vector<int32_t> slot_elem(nel), slot_sub(nel);
+  std::vector<int32_t> slot_elem(nel);
   std::vector<int64_t> ke_off(nel + 1), ed_off(nel + 1);
   for (int64_t s = 0; s < ns; ++s)
-    for (int64_t k = mp.sub_elem_ptr[s]; k < mp.sub_elem_ptr[s + 1]; ++k) {
-      slot_elem[k] = (int32_t)mp.sub_elems[k];
-      slot_sub[k] = (int32_t)s;
-    }
+    for (int64_t k = mp.sub_elem_ptr[s]; k < mp.sub_elem_ptr[s + 1]; ++k) slot_elem[k] = (int32_t)mp.sub_elems[k];
   ke_off[0] = ed_off[0] = 0;
   for (int64_t k = 0; k < nel; ++k) {
-    int64_t e = slot_elem[k];
-    int64_t nek = ms.ed_ptr[e + 1] - ms.ed_ptr[e];
+    const int64_t e = slot_elem[k];
+    int64_t nek = 0;
+    for (int64_t q = ms.en_ptr[e]; q < ms.en_ptr[e + 1]; ++q) nek += ms.nd_ptr[ms.en[q] + 1] - ms.nd_ptr[ms.en[q]];
     ed_off[k + 1] = ed_off[k] + nek;
     ke_off[k + 1] = ke_off[k] + nek * nek;
   }
   std::vector<int32_t> eldof(ed_off[nel]);
   std::vector<int32_t> loc2iface(L.n_vec, -1), loc2glob(L.n_vec, -1), row_sub(L.n_vec);
-  parallel_for(ns, [&](int64_t s) {
+  // row contributions (ascending element slot) per padded row: every row of subdomain s only
+  // receives contributions from the slots of s, so counts and lists are built per subdomain
+  std::vector<int64_t> rc_ptr(L.n_vec + 1, 0);
+  std::vector<std::vector<int32_t>> pos_of(kHostWorkers);   // per worker: level DOF -> padded position
+  std::atomic<bool> missing{false};
+  parallel_for_worker(ns, [&](int64_t s, int w) {
     const SubMeta& m = L.meta[s];
-    std::unordered_map<int64_t, int32_t> pos;
-    pos.reserve((size_t)m.n * 2);
+    std::vector<int32_t>& pos = pos_of[w];
+    if ((int64_t)pos.size() < ms.n_dof) pos.assign(ms.n_dof, -1);
     for (int64_t q = mp.sub_dof_ptr[s]; q < mp.sub_dof_ptr[s + 1]; ++q) {
-      int64_t r = q - mp.sub_dof_ptr[s];
-      int64_t pp = pad_pos(m, r);
+      const int64_t pp = pad_pos(m, q - mp.sub_dof_ptr[s]);
       pos[mp.sub_dofs[q]] = (int32_t)pp;
       loc2glob[m.vec_off + pp] = (int32_t)mp.sub_dofs[q];
       loc2iface[m.vec_off + pp] = (int32_t)mp.sub_iface[q];
     }
     for (int64_t p = 0; p < (int64_t)m.Bc * NB; ++p) row_sub[m.vec_off + p] = (int32_t)s;
     for (int64_t k = mp.sub_elem_ptr[s]; k < mp.sub_elem_ptr[s + 1]; ++k) {
-      int64_t e = slot_elem[k];
-      for (int64_t q = ms.ed_ptr[e], t = ed_off[k]; q < ms.ed_ptr[e + 1]; ++q, ++t) {
-        int64_t d = ms.ed[q];
-        eldof[t] = d < 0 ? -1 : pos.at(d);
-      }
+      const int64_t e = slot_elem[k];
+      int64_t t = ed_off[k];
+      for (int64_t a = ms.en_ptr[e]; a < ms.en_ptr[e + 1]; ++a)
+        for (int64_t q = ms.nd_ptr[ms.en[a]]; q < ms.nd_ptr[ms.en[a] + 1]; ++q, ++t) {
+          const int64_t d = ms.nd_id[q];
+          int32_t pp = -1;
+          if (d >= 0) {
+            pp = d < ms.n_dof ? pos[d] : -1;
+            if (pp < 0) {   // every DOF of a subdomain's element belongs to the subdomain
+              missing = true;
+              continue;
+            }
+            rc_ptr[m.vec_off + pp + 1]++;
+          }
+          eldof[t] = pp;
+        }
     }
+    for (int64_t q = mp.sub_dof_ptr[s]; q < mp.sub_dof_ptr[s + 1]; ++q) pos[mp.sub_dofs[q]] = -1;
   });
-  // row contributions (ascending element slot) and CSR pattern per padded row
-  std::vector<int64_t> rc_ptr(L.n_vec + 1, 0);
-  for (int64_t k = 0; k < nel; ++k) {
-    const SubMeta& m = L.meta[slot_sub[k]];
-    for (int64_t t = ed_off[k]; t < ed_off[k + 1]; ++t)
-      if (eldof[t] >= 0) rc_ptr[m.vec_off + eldof[t] + 1]++;
-  }
+  if (missing) fail(BDDC_ERR_INVALID, "an element DOF is missing from its subdomain's local numbering");
   for (int64_t r = 0; r < L.n_vec; ++r) rc_ptr[r + 1] += rc_ptr[r];
   std::vector<int32_t> rc_elem(rc_ptr[L.n_vec]), rc_a(rc_ptr[L.n_vec]);
-  {
-    std::vector<int64_t> fill(rc_ptr.begin(), rc_ptr.end() - 1);
-    for (int64_t k = 0; k < nel; ++k) {
-      const SubMeta& m = L.meta[slot_sub[k]];
+  parallel_for(ns, [&](int64_t s) {
+    const SubMeta& m = L.meta[s];
+    std::vector<int64_t> fill(rc_ptr.begin() + m.vec_off, rc_ptr.begin() + m.vec_off + (int64_t)m.Bc * NB);
+    for (int64_t k = mp.sub_elem_ptr[s]; k < mp.sub_elem_ptr[s + 1]; ++k)
       for (int64_t t = ed_off[k]; t < ed_off[k + 1]; ++t)
         if (eldof[t] >= 0) {
-          int64_t r = m.vec_off + eldof[t];
+          const int64_t r = eldof[t];
           rc_elem[fill[r]] = (int32_t)k;
           rc_a[fill[r]] = (int32_t)(t - ed_off[k]);
           fill[r]++;
         }
-    }
-  }
+  });
   // constraint rows over padded positions
   std::vector<int64_t> c_ptr(mp.c_ptr.size());
   std::vector<int32_t> c_pos(mp.c_col.size());
@@ -1343,15 +1364,6 @@ void device_setup(bddc_handle_s* h) {
   h->d_conn = A.upload(h->conn, st);
   h->d_coef = A.alloc<double>(h->n_elems);
   h->d_free_of_full = A.upload(h->free_of_full, st);
-  {
-    const int ne = h->npe * h->ndof;
-    std::vector<int64_t> edof((size_t)h->n_elems * ne);
-    for (int64_t e = 0; e < h->n_elems; ++e)
-      for (int a = 0; a < h->npe; ++a)
-        for (int c = 0; c < h->ndof; ++c)
-          edof[(size_t)e * ne + a * h->ndof + c] = (int64_t)h->conn[e * h->npe + a] * h->ndof + c;
-    h->d_edof = A.upload(edof, st);
-  }
   for (size_t l = 0; l < h->lv.size(); ++l) {
     prepare_level(h, h->lv[l], A, st);
     if (l > 0) prepare_level_segments(h->lv[l], h->lv[l - 1], A, st);
@@ -1991,7 +2003,8 @@ bool grad_view(bddc_handle_s* h, GradView* v) {
   v->ke = L.d.ke;
   v->slot_elem = L.slot_elem;
   v->coef = h->d_coef;
-  v->edof = h->d_edof;
+  v->conn = h->d_conn;
+  v->ndof = h->ndof;
   v->free_of_full = h->d_free_of_full;
   v->dir_full = h->has_lift ? h->d_dir_full : nullptr;
   v->stream = h->st;
@@ -2157,8 +2170,8 @@ int bddc_grad(bddc_handle h, const double* dJdu, const double* u, int nrhs, doub
         if (h->has_lift)   // prescribed values enter K_e u_e
           for (int k = 0; k < nrhs; ++k) launch_axpy_loc(uf + (int64_t)k * h->n_full, h->d_dir_full, 1.0, h->n_full, st);
         const Level& L = h->lv[0];
-        launch_grad_contract_slots(h->n_elems, h->npe * h->ndof, L.d.ke, L.slot_elem, h->d_coef, h->d_edof, lf, uf,
-                                   nrhs, h->n_full, grad_coef, st);
+        launch_grad_contract_slots(h->n_elems, h->npe * h->ndof, L.d.ke, L.slot_elem, h->d_coef, h->d_conn, h->ndof,
+                                   lf, uf, nrhs, h->n_full, grad_coef, st);
         cudaFreeAsync(lf, st);
         cudaFreeAsync(uf, st);
       }

@@ -99,7 +99,8 @@ struct GradView {
   const double* ke;               // level-1 element matrices in slot order
   const int32_t* slot_elem;
   const double* coef;
-  const int64_t* edof;            // element -> full DOF ids
+  const int32_t* conn;            // element -> nodes; full DOF of element slot a: conn[a / ndof] ndof + a % ndof
+  int ndof;                       // DOFs per node
   const int64_t* free_of_full;    // full DOF -> free id or -1
   const double* dir_full;         // [n_full] prescribed values (0 on free DOFs), or null when all zero
   cudaStream_t stream;
@@ -189,9 +190,11 @@ void launch_pcg_update_x_r(double* x, double* r, const double* p, const double* 
                            int64_t n, cudaStream_t st);
 void launch_pcg_update_p(double* p, const double* z, const double* scal, int64_t n, cudaStream_t st);
 void launch_pcg_scalars(double* scal, int stage, int flexible, cudaStream_t st);
+// conn: element -> nodes (ne / ndof per element); the full DOF of element slot a is
+// conn[a / ndof] * ndof + a % ndof
 void launch_grad_contract_slots(int64_t n_elems, int ne, const double* ke, const int32_t* slot_elem,
-                                const double* coef, const int64_t* edof, const double* lam, const double* u,
-                                int nrhs, int64_t n_full, double* grad, cudaStream_t st);
+                                const double* coef, const int32_t* conn, int ndof, const double* lam,
+                                const double* u, int nrhs, int64_t n_full, double* grad, cudaStream_t st);
 void launch_expand_free(const double* xf, const int64_t* free_of_full, int64_t n_full, int nrhs,
                         int64_t n_free, double* xfull, cudaStream_t st);
 void launch_copy_segments(const double* src, const int64_t* src_off, double* dst, const int64_t* dst_off,

@@ -69,19 +69,20 @@ __global__ void k_expand_pair(const double* __restrict__ lam, const double* __re
 // grad[e] += -(1/coef_e) lam_e^T K_e u_e for one right-hand side; one warp per element
 __global__ void k_grad_contract_accum(int64_t n_elems, int ne, const double* __restrict__ ke,
                                       const int32_t* __restrict__ slot_elem, const double* __restrict__ coef,
-                                      const int64_t* __restrict__ edof, const double* __restrict__ lamf,
+                                      const int32_t* __restrict__ conn, int ndof, const double* __restrict__ lamf,
                                       const double* __restrict__ uf, double* __restrict__ grad) {
   const int64_t slot = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (slot >= n_elems) return;
   const int64_t e = slot_elem[slot];
   const double* K = ke + slot * (int64_t)ne * ne;
-  const int64_t* d = edof + e * ne;
+  const int32_t* cn = conn + e * (int64_t)(ne / ndof);
+  auto dof = [&](int a) { return (int64_t)cn[a / ndof] * ndof + a % ndof; };
   double acc = 0.0;
   for (int a = lane; a < ne; a += 32) {
     double t = 0.0;
-    for (int b = 0; b < ne; ++b) t += K[a * ne + b] * uf[d[b]];
-    acc += lamf[d[a]] * t;
+    for (int b = 0; b < ne; ++b) t += K[a * ne + b] * uf[dof(b)];
+    acc += lamf[dof(a)] * t;
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane == 0) grad[e] += -acc / coef[e];
@@ -125,7 +126,7 @@ extern "C" int bddc_grad_noalloc(bddc_handle h, const double* dJdu, const double
           grad_rhs + (int64_t)k * v.n_free, u + (int64_t)k * v.n_free, v.free_of_full, v.dir_full, v.n_full, lf, uf);
       note_launch();
       k_grad_contract_accum<<<(unsigned)((v.n_elems + 7) / 8), 256, 0, st>>>(v.n_elems, v.ne, v.ke, v.slot_elem,
-                                                                              v.coef, v.edof, lf, uf, grad_coef);
+                                                                              v.coef, v.conn, v.ndof, lf, uf, grad_coef);
       ce = cudaGetLastError();
     }
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);

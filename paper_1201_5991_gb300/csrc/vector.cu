@@ -168,22 +168,23 @@ __global__ void k_pcg_p(double* __restrict__ p, const double* __restrict__ z, co
 // grad[e] = -(1/coef_e) * sum_k lam_k,e^T K_e u_k,e ; one warp per element
 __global__ void k_grad_contract(int64_t n_elems, int ne, const double* __restrict__ ke,
                                 const int32_t* __restrict__ slot_elem, const double* __restrict__ coef,
-                                const int64_t* __restrict__ edof, const double* __restrict__ lam,
+                                const int32_t* __restrict__ conn, int ndof, const double* __restrict__ lam,
                                 const double* __restrict__ u, int nrhs, int64_t n_full, double* __restrict__ grad) {
   const int64_t slot = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (slot >= n_elems) return;
   const int64_t e = slot_elem[slot];
   const double* K = ke + slot * (int64_t)ne * ne;
-  const int64_t* d = edof + e * ne;
+  const int32_t* cn = conn + e * (int64_t)(ne / ndof);
+  auto dof = [&](int a) { return (int64_t)cn[a / ndof] * ndof + a % ndof; };
   double acc = 0.0;
   for (int k = 0; k < nrhs; ++k) {
     const double* lk = lam + (int64_t)k * n_full;
     const double* uk = u + (int64_t)k * n_full;
     for (int a = lane; a < ne; a += 32) {
       double t = 0.0;
-      for (int b = 0; b < ne; ++b) t += K[a * ne + b] * uk[d[b]];
-      acc += lk[d[a]] * t;
+      for (int b = 0; b < ne; ++b) t += K[a * ne + b] * uk[dof(b)];
+      acc += lk[dof(a)] * t;
     }
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -372,11 +373,11 @@ void launch_pcg_scalars(double* scal, int stage, int flexible, cudaStream_t st) 
   { note_launch(); k_pcg_scalars<<<1, 32, 0, st>>>(scal, stage, flexible); }
 }
 void launch_grad_contract_slots(int64_t n_elems, int ne, const double* ke, const int32_t* slot_elem, const double* coef,
-                                const int64_t* edof, const double* lam, const double* u, int nrhs, int64_t n_full,
-                                double* grad, cudaStream_t st) {
+                                const int32_t* conn, int ndof, const double* lam, const double* u, int nrhs,
+                                int64_t n_full, double* grad, cudaStream_t st) {
   if (n_elems > 0)
-    { note_launch(); k_grad_contract<<<nblocks(n_elems, 8), 256, 0, st>>>(n_elems, ne, ke, slot_elem, coef, edof, lam, u, nrhs, n_full,
-                                                          grad); }
+    { note_launch(); k_grad_contract<<<nblocks(n_elems, 8), 256, 0, st>>>(n_elems, ne, ke, slot_elem, coef, conn, ndof, lam, u,
+                                                          nrhs, n_full, grad); }
 }
 void launch_expand_free(const double* xf, const int64_t* free_of_full, int64_t n_full, int nrhs, int64_t n_free,
                         double* xfull, cudaStream_t st) {

@@ -48,7 +48,7 @@ def host_mesh(prob, n_levels: Optional[int] = None) -> _HostMesh:
 
 def make_opts(precision="mixed", weights="stiffness", all_corners=0, maxit=500, refine_steps=0, flexible=-1,
               use_graph=1, profile=0, tensor_cores=1, inner_steps=0, inner_tol=0.0, krylov=0,
-              autotune=1) -> capi.Opts:
+              autotune=1, verbose=0) -> capi.Opts:
     o = capi.Opts()
     capi.lib().bddc_default_opts(C.byref(o))
     o.precision = capi.PREC_MIXED if precision == "mixed" else capi.PREC_FP64
@@ -64,6 +64,7 @@ def make_opts(precision="mixed", weights="stiffness", all_corners=0, maxit=500, 
     o.inner_tol = float(inner_tol)
     o.krylov = int(krylov)
     o.autotune = int(autotune)
+    o.verbose = int(verbose)
     return o
 
 
