@@ -49,6 +49,21 @@ WORKLOAD = "elasticity3d_48"
 TOL = 1e-8
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest x over all ranks (the slowest replica's time); x itself on one rank."""
+    if world <= 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(n_free: int, world: int, ms: float) -> float:
+    """Whole-job DOF/s: every rank solves its own replica of n_free DOFs in ms (max over ranks)."""
+    return n_free * world / (ms * 1e-3)
+
+
 def workload_config(prob, extra=None):
     cfg = {
         "workload": WORKLOADS[WORKLOAD],
@@ -284,15 +299,11 @@ def run_gpu(args, rank, world, local_rank):
         torch.cuda.synchronize()
         barrier()
         clk = sampler.stop() if sampler else None
-        ms = sum(times) / len(times)
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(sum(times) / len(times), world, dev)
         return ms, stats, launches, prof, clk
 
     ms, stats, launches, prof, clk = timed("mixed", args.steps, args.warmup, profile=1, clocks=True)
-    value = prob.n_free * world / (ms * 1e-3)
+    value = weak_scaling_value(prob.n_free, world, ms)
     st0 = stats[-1]
 
     # plain FP64 form, same workload (fewer steps: its set-up is FP64-ALU bound)
@@ -335,11 +346,7 @@ def run_gpu(args, rank, world, local_rank):
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
         del s
-    e2e_s = sum(e2e_times) / len(e2e_times)
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(sum(e2e_times) / len(e2e_times), world, dev)
     mesh_bytes = prob.coords.nbytes + prob.conn.nbytes + prob.coef.nbytes + prob.dirichlet.nbytes
 
     hbm, tc_peak, peak_kind = load_peaks()
