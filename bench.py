@@ -149,12 +149,18 @@ class ClockSampler:
 
 
 def traffic_ratio(cls):
-    """DRAM bytes / algorithmic bytes of the roofline kernel class from the committed ncu summary
-    (profiles/trsv_sweep_traffic.json for the sweeps, profiles/trmv_schur_traffic.json for the
-    factor products), or None when the kernel source changed since the counters were taken."""
+    """DRAM bytes per algorithmic unit of the roofline kernel class from the committed ncu summary:
+    per algorithmic byte for the sweeps (profiles/trsv_sweep_traffic.json) and the factor products
+    (profiles/trmv_schur_traffic.json), per FP32-equivalent flop for the tensor-core update
+    (profiles/update_tc2_traffic.json); None when the kernel source changed since the counters
+    were taken."""
     from paper_1201_5991_gb300 import capi
-    fname, src_name = (("trsv_sweep_traffic.json", "sweep.cu") if cls in (capi.PROF_TRSV, capi.PROF_TRSV_IFACE)
-                       else ("trmv_schur_traffic.json", "trmv.cu"))
+    if cls in (capi.PROF_TRSV, capi.PROF_TRSV_IFACE):
+        fname, src_name, key = "trsv_sweep_traffic.json", "sweep.cu", "traffic_over_algorithmic"
+    elif cls == capi.PROF_TC_UPDATE:
+        fname, src_name, key = "update_tc2_traffic.json", "update_tc.cu", "traffic_over_fp32_flop"
+    else:
+        fname, src_name, key = "trmv_schur_traffic.json", "trmv.cu", "traffic_over_algorithmic"
     path = os.path.join(ROOT, "profiles", fname)
     try:
         with open(path) as fh:
@@ -162,7 +168,7 @@ def traffic_ratio(cls):
         src = open(os.path.join(ROOT, "paper_1201_5991_gb300", "csrc", src_name), "rb").read()
         if hashlib.sha256(src).hexdigest() != rec.get("source_sha256", rec.get("sweep_cu_sha256")):
             return None
-        return float(rec["traffic_over_algorithmic"])
+        return float(rec[key])
     except Exception:
         return None
 
@@ -352,13 +358,14 @@ def run_gpu(args, rank, world, local_rank):
     hbm, tc_peak, peak_kind = load_peaks()
     dom, cls = prof[3], prof[4]
     tensor = dom == capi.PROF_TC_UPDATE
+    ratio = traffic_ratio(dom)
     if tensor:   # three FP16 tensor-core products per FP32-equivalent multiply-add (scaled hi/lo split)
         achieved = 3.0 * cls[dom][3] / (prof[0] * 1e-3) / 1e12 if prof[0] > 0 else 0.0
-        ratio = None
+        units = cls[dom][3]   # FP32-equivalent flops: the DRAM bytes are the output tiles, read and written once
     else:
         achieved = prof[2] / (prof[0] * 1e-3) / 1e9 if prof[0] > 0 else 0.0
-        ratio = traffic_ratio(dom)
-    traffic = ratio * prof[2] / max(prof[1], 1) if ratio is not None else None
+        units = prof[2]
+    traffic = ratio * units / max(prof[1], 1) if ratio is not None else None
     names = {capi.PROF_TRSV: "k_sweep<float> forward/backward over interior block rows (Schur operator; "
                              "streaming triangular sweeps, TMA-staged tiles)",
              capi.PROF_TRSV_IFACE: "k_sweep<float> forward/backward over interface block rows (subdomain corrections)",
