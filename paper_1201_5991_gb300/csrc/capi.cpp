@@ -859,12 +859,13 @@ void factor_level(bddc_handle_s* h, Level& L, cudaStream_t st) {
         if (L.split && L.wide_items2[p] > 0)
           launch_split_panel(d, kb0, kb1, L.max_R, L.split, L.split_signed, L.rscale, L.prow_off, st);
       }
-      ProfScope ps(h, BDDC_PROF_TC_UPDATE, 0.0, L.tc_flops[p], st);
       const int64_t items = L.wide_items2[p];
-      if (L.split && items > 0)
+      if (L.split && items > 0) {   // the last super-panel has no trailing columns: no launch
+        ProfScope ps(h, BDDC_PROF_TC_UPDATE, 0.0, L.tc_flops[p], st);
         launch_update_tc2(d, kb0, kb1, (int)std::min<int64_t>(items, h->grid_max / 2), L.split,
                           L.split_signed ? L.split_signed : L.split, L.rscale,
                           L.prow_off, L.item_pref + (size_t)p * (d.n_sub + 1), L.tile_tmap, st);
+      }
     }
   } else {
     for (int k = 0; k < L.max_Bc; ++k) {
