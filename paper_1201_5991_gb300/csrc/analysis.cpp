@@ -295,28 +295,29 @@ bool analyze_level(const LevelMesh& mesh, unsigned constraints, bool all_corners
   const double tol = 1e-12 * diam2;
 
   std::vector<Pt> pts;
-  auto gather_points = [&](int64_t s) {
-    pts.clear();
+  auto gather_points_into = [&](int64_t s, std::vector<Pt>& out) {
+    out.clear();
     for (int64_t g : sub_globs[s]) {
       if (!constrained(g) || (glob_comps[g] & rmask) != rmask) continue;
       Pt q{{0, 0, 0}};
       for (int d = 0; d < dim; ++d) q.x[d] = m.glob_centroid[g * dim + d];
-      pts.push_back(q);
+      out.push_back(q);
     }
     for (int64_t p : sub_nodes[s]) {
       if (!node_all_prescribed(p)) continue;
       Pt q{{0, 0, 0}};
       for (int d = 0; d < dim; ++d) q.x[d] = mesh.coords[p * dim + d];
-      pts.push_back(q);
+      out.push_back(q);
     }
   };
-  auto sufficient = [&]() -> bool {
-    if (mesh.rigid_points == 1) return !pts.empty();
-    if (pts.empty()) return false;
+  auto gather_points = [&](int64_t s) { gather_points_into(s, pts); };
+  auto sufficient_for = [&](const std::vector<Pt>& q) -> bool {
+    if (mesh.rigid_points == 1) return !q.empty();
+    if (q.empty()) return false;
     size_t j = 0;
     double best = -1.0;
-    for (size_t k = 0; k < pts.size(); ++k) {
-      double d = std::sqrt(dist2(pts[k], pts[0], dim));
+    for (size_t k = 0; k < q.size(); ++k) {
+      double d = std::sqrt(dist2(q[k], q[0], dim));
       if (d > best) {
         best = d;
         j = k;
@@ -324,15 +325,31 @@ bool analyze_level(const LevelMesh& mesh, unsigned constraints, bool all_corners
     }
     if (mesh.rigid_points == 2) return best * best > tol;
     if (best * best <= tol) return false;
-    double u[3] = {pts[j].x[0] - pts[0].x[0], pts[j].x[1] - pts[0].x[1], pts[j].x[2] - pts[0].x[2]};
+    double u[3] = {q[j].x[0] - q[0].x[0], q[j].x[1] - q[0].x[1], q[j].x[2] - q[0].x[2]};
     double mx = 0.0;
-    for (size_t k = 0; k < pts.size(); ++k) mx = std::max(mx, cross_norm(pts[k], pts[0], u));
+    for (size_t k = 0; k < q.size(); ++k) mx = std::max(mx, cross_norm(q[k], q[0], u));
     return mx > tol;
   };
-  for (int64_t s = 0; s < ns; ++s) {
+  auto sufficient = [&]() -> bool { return sufficient_for(pts); };
+  // the test of every subdomain on the initial constraints, in parallel (0: insufficient,
+  // 1: sufficient, 2: no interface node); the ordered pass below reuses it until the first
+  // promotion changes the constraints of later subdomains
+  std::vector<char> pre(ns, 0);
+  parallel_range(ns, [&](int64_t s) {
     bool has_iface = false;
     for (int64_t p : sub_nodes[s]) has_iface = has_iface || iface[p];
-    if (!has_iface) continue;   // the whole (connected) problem: nothing to constrain
+    if (!has_iface) {
+      pre[s] = 2;
+      return;
+    }
+    std::vector<Pt> local;
+    gather_points_into(s, local);
+    pre[s] = sufficient_for(local) ? 1 : 0;
+  });
+  bool promoted_any = false;
+  for (int64_t s = 0; s < ns; ++s) {
+    if (pre[s] == 2) continue;   // the whole (connected) problem: nothing to constrain
+    if (!promoted_any && pre[s] == 1) continue;
     int tries = 0;
     for (;;) {
       gather_points(s);
@@ -384,6 +401,7 @@ bool analyze_level(const LevelMesh& mesh, unsigned constraints, bool all_corners
       for (int64_t k = m.node_sub_ptr[pick]; k < m.node_sub_ptr[pick + 1]; ++k) sub_globs[m.node_sub[k]].push_back(g);
       is_corner[pick] = 1;
       m.n_promoted++;
+      promoted_any = true;
     }
   }
   n_globs = (int64_t)m.glob_kind.size();
@@ -406,7 +424,8 @@ bool analyze_level(const LevelMesh& mesh, unsigned constraints, bool all_corners
     if (iface[p])
       for (int64_t q = mesh.nd_ptr[p]; q < mesh.nd_ptr[p + 1]; ++q)
         if (mesh.nd_id[q] >= 0) m.iface_dofs.push_back(mesh.nd_id[q]);
-  std::sort(m.iface_dofs.begin(), m.iface_dofs.end());
+  if (!std::is_sorted(m.iface_dofs.begin(), m.iface_dofs.end()))   // level 1 numbers DOFs node by node
+    std::sort(m.iface_dofs.begin(), m.iface_dofs.end());
   m.n_iface = (int64_t)m.iface_dofs.size();
   std::vector<int64_t> iface_pos(mesh.n_dof, -1);
   for (int64_t k = 0; k < m.n_iface; ++k) iface_pos[m.iface_dofs[k]] = k;

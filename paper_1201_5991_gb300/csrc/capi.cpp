@@ -1293,16 +1293,16 @@ void analysis(bddc_handle_s* h, const bddc_mesh* mesh, const bddc_partition* par
   h->n_free = 0;
   for (int64_t q = 0; q < h->n_full; ++q)
     if (!mesh->dirichlet[q]) h->free_of_full[q] = h->n_free++;
-  h->dir_full.assign(h->n_full, 0.0);
+  h->dir_full.clear();   // kept only when a prescribed value is non-zero
   h->has_lift = false;
   if (mesh->dir_values)
     for (int64_t q = 0; q < h->n_full; ++q)
       if (mesh->dirichlet[q] && mesh->dir_values[q] != 0.0) {
         if (!std::isfinite(mesh->dir_values[q])) fail(BDDC_ERR_INVALID, "non-finite prescribed value");
+        if (!h->has_lift) h->dir_full.assign(h->n_full, 0.0);
         h->dir_full[q] = mesh->dir_values[q];
         h->has_lift = true;
       }
-  if (!h->has_lift) h->dir_full.clear();
   h->n_levels = part->n_levels;
   h->parts.clear();
   h->n_parts.clear();

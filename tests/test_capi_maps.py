@@ -105,6 +105,20 @@ def test_all_corners_maps_bit_exact():
     assert lib[0]["n_coarse"] == lib[0]["n_iface"]
 
 
+def test_promoted_corners_maps_bit_exact():
+    # corners only on slab partitions along x: the inner slabs float with too few corners, so
+    # corners are promoted subdomain after subdomain, and a promotion on one slab adds a
+    # constrained point to its neighbour (the order of the promotions matters)
+    p = meshgen.elasticity3d(12, 3, seed=2, constraints=meshgen.CORNERS)
+    cent = p.coords[p.conn].mean(axis=1)
+    p.parts = [np.minimum((cent[:, 0] * 4).astype(np.int32), 3)]
+    p.n_parts = [4]
+    lib = solver.analyze(p, n_levels=2)
+    orc = _oracle_levels(p, 2)
+    assert lib[0]["n_promoted"] == 7
+    _compare(lib[0], orc[0])
+
+
 @pytest.mark.slow
 def test_maps_bit_exact_elasticity_48():
     p = meshgen.config("elasticity3d_48")
