@@ -165,26 +165,35 @@ bool analyze_level(const LevelMesh& mesh, unsigned constraints, bool all_corners
   std::vector<int64_t> parent(nn);
   std::iota(parent.begin(), parent.end(), 0);
   if (!all_corners) {
-    std::vector<int64_t> firsts;
-    for (int64_t e = 0; e < ne; ++e) {
-      firsts.clear();
-      for (int64_t q = mesh.en_ptr[e]; q < mesh.en_ptr[e + 1]; ++q) {
-        int64_t p = mesh.en[q];
-        if (!iface[p]) continue;
-        int64_t rep = -1;
-        for (int64_t f : firsts)
-          if (same_set(m, f, p)) {
-            rep = f;
-            break;
-          }
-        if (rep < 0) {
-          firsts.push_back(p);
-          continue;
+    // the pairs to join are found per chunk of elements in parallel and joined afterwards: a
+    // component's root is always its smallest node, so the globs do not depend on the order
+    const int64_t chunk = 4096, nchunk = (ne + chunk - 1) / chunk;
+    std::vector<std::vector<std::pair<int64_t, int64_t>>> joins(nchunk);
+    parallel_range(nchunk, [&](int64_t b) {
+      std::vector<int64_t> firsts;
+      for (int64_t e = b * chunk; e < std::min(ne, (b + 1) * chunk); ++e) {
+        firsts.clear();
+        for (int64_t q = mesh.en_ptr[e]; q < mesh.en_ptr[e + 1]; ++q) {
+          int64_t p = mesh.en[q];
+          if (!iface[p]) continue;
+          int64_t rep = -1;
+          for (int64_t f : firsts)
+            if (same_set(m, f, p)) {
+              rep = f;
+              break;
+            }
+          if (rep < 0)
+            firsts.push_back(p);
+          else
+            joins[b].emplace_back(p, rep);
         }
-        int64_t a = find_root(parent, p), b = find_root(parent, rep);
+      }
+    });
+    for (const auto& jb : joins)
+      for (const auto& pr : jb) {
+        int64_t a = find_root(parent, pr.first), b = find_root(parent, pr.second);
         if (a != b) parent[std::max(a, b)] = std::min(a, b);
       }
-    }
   }
   // number globs by first (= smallest) node
   std::vector<int64_t> glob_of_root(nn, -1);
@@ -450,8 +459,10 @@ bool analyze_level(const LevelMesh& mesh, unsigned constraints, bool all_corners
         if (mesh.nd_id[q] < 0) continue;
         (iface[p] ? o.inter : o.interior).push_back(key_of(q));
       }
-    std::sort(o.interior.begin(), o.interior.end());
-    std::sort(o.inter.begin(), o.inter.end());
+    // nodes come in ascending order and DOF ids grow with (node, component), so the keys are
+    // usually ordered already (not when the last component is moved to the end)
+    if (!std::is_sorted(o.interior.begin(), o.interior.end())) std::sort(o.interior.begin(), o.interior.end());
+    if (!std::is_sorted(o.inter.begin(), o.inter.end())) std::sort(o.inter.begin(), o.inter.end());
     const int64_t nI = (int64_t)o.interior.size();
     // constraint rows: globs touching s in glob order -> ascending coarse ids; their DOFs are
     // interface DOFs, found in the sorted interface keys
