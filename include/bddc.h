@@ -92,7 +92,8 @@ typedef struct {
 typedef struct {
   int n_levels;                              /* 2 .. BDDC_MAX_LEVELS */
   const int32_t* part[BDDC_MAX_LEVELS - 1];  /* host arrays */
-  int64_t n_parts[BDDC_MAX_LEVELS - 1];      /* number of subdomains of level l+1 */
+  int64_t n_parts[BDDC_MAX_LEVELS - 1];      /* number of subdomains of level l+1 (at most 65,535:
+                                                batched launches index subdomains by gridDim.y) */
 } bddc_partition;
 
 typedef struct {

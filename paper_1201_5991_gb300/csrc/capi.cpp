@@ -364,6 +364,7 @@ void flush_profile(bddc_handle_s* h) {
 }
 
 constexpr int kHostWorkers = 16;
+constexpr int64_t kMaxSubdomains = 65535;   // CUDA's limit on gridDim.y
 
 // fn(i, w) for i in [0, n) on up to kHostWorkers host threads; w < kHostWorkers names the thread,
 // so that per-thread scratch can be indexed by it
@@ -1308,6 +1309,8 @@ void analysis(bddc_handle_s* h, const bddc_mesh* mesh, const bddc_partition* par
   h->n_parts.clear();
   for (int l = 0; l + 1 < h->n_levels; ++l) {
     if (!part->part[l] || part->n_parts[l] <= 0) fail(BDDC_ERR_INVALID, "missing partition of level " + std::to_string(l + 1));
+    if (part->n_parts[l] > kMaxSubdomains)   // batched launches put the subdomains on grid.y
+      fail(BDDC_ERR_INVALID, "level " + std::to_string(l + 1) + " has more than 65,535 subdomains");
     const int64_t n_items = l == 0 ? h->n_elems : h->n_parts[l - 1];
     h->parts.emplace_back(part->part[l], part->part[l] + n_items);
     h->n_parts.push_back(part->n_parts[l]);

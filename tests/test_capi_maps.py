@@ -139,6 +139,12 @@ def test_invalid_partition_is_rejected():
     with pytest.raises(capi.BddcError) as ei:
         solver.analyze(p)
     assert ei.value.code == capi.ERR_INVALID
+    p = meshgen.poisson2d(8, 2)
+    p.n_parts = [65536]                      # more subdomains than a launch grid's y extent
+    with pytest.raises(capi.BddcError) as ei:
+        solver.analyze(p)
+    assert ei.value.code == capi.ERR_INVALID
+    assert "65,535" in capi.lib().bddc_last_error().decode()
 
 
 def test_stokes_local_order_puts_pressures_last():
