@@ -417,12 +417,10 @@ void build_level1_mesh(bddc_handle_s* h, LevelMesh* out) {
   m.coords = h->coords;
   m.nd_ptr.resize(h->n_nodes + 1);
   m.nd_comp.resize(h->n_full);
-  m.nd_id.resize(h->n_full);
   for (int64_t p = 0; p <= h->n_nodes; ++p) m.nd_ptr[p] = p * h->ndof;
-  for (int64_t q = 0; q < h->n_full; ++q) {
-    m.nd_comp[q] = (int32_t)(q % h->ndof);
-    m.nd_id[q] = h->free_of_full[q];
-  }
+  for (int64_t p = 0; p < h->n_nodes; ++p)
+    for (int c = 0; c < h->ndof; ++c) m.nd_comp[p * h->ndof + c] = c;
+  m.nd_id = h->free_of_full;
   m.en_ptr.resize(h->n_elems + 1);
   m.en.resize(h->n_elems * h->npe);
   for (int64_t e = 0; e <= h->n_elems; ++e) m.en_ptr[e] = e * h->npe;
