@@ -124,6 +124,11 @@ typedef struct {
   int autotune;             /* 1: time the sweep launch variants (CTAs per SM, tile-ring depth, task order)
                                on every level at set-up and keep the fastest; results are cached per level
                                shape for the life of the process.  0: fixed defaults */
+  int wait_probe;           /* test only, default 0.  1: every row-flag wait of the streaming sweeps polls a
+                               device word that nothing sets, with a short limit, so that each sweep runs
+                               its bounded-wait error path and the call reports BDDC_ERR_TIMEOUT (the
+                               results of such a call are meaningless; the CUDA context stays usable).
+                               Tile-copy waits are not affected. */
 } bddc_opts;
 
 #define BDDC_KRYLOV_AUTO 0
@@ -249,10 +254,12 @@ int bddc_apply_schur(bddc_handle h, const double* x, double* y, int nrhs);
 
 /* Adjoint gradient of a scalar J(u) with u = K(coef)^{-1} f: solves K lambda_k = dJdu_k with
  * the same factors (K is symmetric), then grad_rhs = lambda and
- * grad_coef[e] = - sum_k lambda_k,e^T (dK_e/dcoef_e) u_k,e with dK_e/dcoef_e = K_e / coef_e.
+ * grad_coef[e] = - sum_k lambda_k,e^T (dK_e/dcoef_e) u_k,e with dK_e/dcoef_e = K_e / coef_e
+ * (Poisson and elasticity, whose element matrices are linear in the coefficient; for Stokes the
+ * viscosity scales only the viscous block, so grad_coef must be NULL there).
  * dJdu, u: device [nrhs][n_free].  grad_coef: device [n_elems] or NULL.  grad_rhs: device
  * [nrhs][n_free] or NULL.  tol: Krylov tolerance of the adjoint solve.
- * Errors as bddc_solve. */
+ * Errors as bddc_solve; INVALID for grad_coef on a Stokes handle. */
 int bddc_grad(bddc_handle h, const double* dJdu, const double* u, int nrhs, double tol,
               double* grad_coef, double* grad_rhs);
 
@@ -265,15 +272,30 @@ int bddc_grad(bddc_handle h, const double* dJdu, const double* u, int nrhs, doub
  * scratch of the contraction lives in one fixed 16 MiB device array inside the library, held
  * by every GPU that loads the library until the process exits: meshes with
  * n_nodes * dofs_per_node > 1,048,576 are rejected with BDDC_ERR_INVALID.  The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress); make this first call
- * before any stream capture.  Every call shares the array and overwrites the part it reads, so
- * calls whose work overlaps on the GPU (several streams, several host threads) race and must be
- * serialised by the caller.  Errors as bddc_grad. */
+ * device looks up that array's device address (cudaGetSymbolAddress).  The adjoint solve is the
+ * handle's own: the first solve on a handle, and the first after the Krylov method changes,
+ * builds the handle's cached CUDA graph of one iteration with its capture stream and events, so
+ * warm a handle with one bddc_solve (or one call of this entry point) before relying on
+ * allocation-free calls in a loop.  The call synchronises the handle's stream (it reads the
+ * Krylov scalars back every iteration), so it must not be made while that stream or the calling
+ * thread is capturing a CUDA graph.  Every call on a device shares the array and overwrites the
+ * part it reads, so calls whose work overlaps on the GPU (several streams, several host threads)
+ * race and must be serialised by the caller.  Errors as bddc_grad. */
 int bddc_grad_noalloc(bddc_handle h, const double* dJdu, const double* u, int nrhs, double tol,
                       double* grad_coef, double* grad_rhs);
 
 /* Index maps of BDDC level `level` (1-based).  Errors: INVALID. */
 int bddc_get_maps(bddc_handle h, int level, bddc_level_maps* out);
+
+/* Local coarse matrices K_Ci = Psi_i^T K_i Psi_i = -Lambda_i of BDDC level `level` (1-based) after
+ * set-up (Sec. 2, Eq. psi_def; on levels below the coarsest they are the element matrices of the
+ * next level).  kc: host FP64 buffer of n entries; receives, subdomain after subdomain, the
+ * nc_i x nc_i matrix of subdomain i row-major, rows and columns in the order of
+ * bddc_level_maps.sub_coarse (R_Ci), where nc_i = sub_coarse_ptr[i+1] - sub_coarse_ptr[i].  The
+ * entries needed are sum_i nc_i^2; a smaller n is rejected.  In both precisions the matrices are
+ * FP64, formed as G_i^{-1} - R with G_i = C_i A_i^{-1} C_i^T from the factor of A_i (FP32 factor in
+ * the mixed form).  Errors: INVALID (no numeric set-up, bad level, buffer too small), CUDA. */
+int bddc_get_coarse(bddc_handle h, int level, double* kc, int64_t n);
 
 /* Copy the statistics of the last set-up / solve into *out. */
 int bddc_get_stats(bddc_handle h, bddc_stats* out);
@@ -300,6 +322,19 @@ int bddc_reset_profile(bddc_handle h);
  * recomputed by the normal path, so the handle stays valid and bit-identical.  Mixed-precision
  * SPD handles only.  Errors: INVALID, CUDA. */
 int bddc_batching_ablation(bddc_handle h, double* ms);
+
+/* Test and measurement entry point for the tensor-core trailing update of the mixed factorisation
+ * (Algorithm 1, "factorize the matrices of local saddle point problems"; the FP32 block Cholesky's
+ * rank-256 update on tcgen05 from two row-scaled FP16 parts, three products).  a: host FP32 n x n
+ * row-major, n = 64 nb with nb >= 5.  The first 256 columns play the factored panel P and the rest
+ * the trailing matrix: on return a(i, j) -= sum_{q < 256} a(i, q) a(j, q) for every i, j >= 256
+ * whose 64 x 64 tiles satisfy tile(j) <= tile(i) (diagonal tiles are updated in full); the other
+ * entries are returned unchanged.  The data pass through the factor's tile layout and the same two
+ * kernels (panel split, persistent tcgen05 update) that bddc_setup launches.  ms: host, receives
+ * the update kernel's duration from CUDA events, or NULL.  Device buffers are allocated and freed
+ * by the call, on the default stream.  Errors: INVALID (n), CUDA, OOM, TIMEOUT (a bounded wait of
+ * the update kernel gave up). */
+int bddc_tc_update_check(int64_t n, float* a, double* ms);
 
 /* Message of the last failure on the calling thread ("" if none). */
 const char* bddc_last_error(void);

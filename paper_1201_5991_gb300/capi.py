@@ -33,7 +33,8 @@ EXPORTED = [
     "bddc_default_opts", "bddc_analyze", "bddc_setup", "bddc_update_coef", "bddc_solve",
     "bddc_solve_host", "bddc_apply_precond", "bddc_apply_schur", "bddc_grad", "bddc_get_maps",
     "bddc_get_stats", "bddc_sizes", "bddc_free", "bddc_last_error", "bddc_kernel_launches",
-    "bddc_reset_profile", "bddc_grad_noalloc", "bddc_batching_ablation",
+    "bddc_reset_profile", "bddc_grad_noalloc", "bddc_batching_ablation", "bddc_get_coarse",
+    "bddc_tc_update_check",
 ]
 PROF_TRSV, PROF_FACTOR, PROF_SPMV, PROF_TRMV, PROF_TRSV_IFACE, PROF_COARSE, PROF_TC_UPDATE, PROF_CLASSES = (
     0, 1, 2, 3, 4, 5, 6, 7)
@@ -61,7 +62,7 @@ class Opts(C.Structure):
         ("precision", C.c_int), ("weights", C.c_int), ("all_corners", C.c_uint), ("maxit", C.c_int),
         ("refine_steps", C.c_int), ("flexible", C.c_int), ("use_graph", C.c_int), ("verbose", C.c_int),
         ("profile", C.c_int), ("tensor_cores", C.c_int), ("inner_steps", C.c_int), ("inner_tol", C.c_double),
-        ("krylov", C.c_int), ("autotune", C.c_int),
+        ("krylov", C.c_int), ("autotune", C.c_int), ("wait_probe", C.c_int),
     ]
 
 
@@ -123,6 +124,8 @@ def lib() -> C.CDLL:
     L.bddc_grad.argtypes = [H, P, P, C.c_int, C.c_double, P, P]
     L.bddc_grad_noalloc.argtypes = [H, P, P, C.c_int, C.c_double, P, P]
     L.bddc_get_maps.argtypes = [H, C.c_int, C.POINTER(LevelMaps)]
+    L.bddc_get_coarse.argtypes = [H, C.c_int, C.POINTER(C.c_double), C.c_int64]
+    L.bddc_tc_update_check.argtypes = [C.c_int64, C.POINTER(C.c_float), C.POINTER(C.c_double)]
     L.bddc_get_stats.argtypes = [H, C.POINTER(Stats)]
     L.bddc_sizes.argtypes = [H, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     L.bddc_free.argtypes = [H]

@@ -686,6 +686,7 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
     d.c_rho = A.upload(c_rho, st);
   }
   d.indefinite = h->physics == BDDC_STOKES ? 1 : 0;
+  d.wait_probe = h->opts.wait_probe ? 1 : 0;
   d.sgn = L.fp32 ? (void*)A.alloc<float>(L.n_vec) : (void*)A.alloc<double>(L.n_vec);
   d.w = A.alloc<double>(L.n_vec);
   d.diag = A.alloc<double>(L.n_vec);
@@ -890,6 +891,15 @@ void check_status(bddc_handle_s* h, int level) {
     fail(BDDC_ERR_BREAKDOWN, "non-positive pivot on level " + std::to_string(level) + " subdomain " +
                                  std::to_string(st[1]));
   }
+}
+
+// A bounded wait that gave up explains whatever else went wrong in the same call (NaN, no
+// convergence): report it first.
+void throw_if_timeout(bddc_handle_s* h) {
+  int st[4];
+  if (cudaMemcpyAsync(st, h->d_status, sizeof(st), cudaMemcpyDeviceToHost, h->st) != cudaSuccess) return;
+  if (cudaStreamSynchronize(h->st) != cudaSuccess) return;
+  if (st[2]) fail(BDDC_ERR_TIMEOUT, "a bounded device-side wait gave up (code " + std::to_string(st[2]) + ")");
 }
 
 void reset_status(bddc_handle_s* h) {
@@ -1238,7 +1248,7 @@ void numeric_setup(bddc_handle_s* h) {
     }
   }
   choose_refinement(h);
-  ck(cudaStreamSynchronize(st), "sync");
+  check_status(h, 0);   // the refinement probe's sweeps
   h->stats.factor_ms = now_ms() - t0;
   flush_profile(h);
   h->stats.refine_steps = h->refine_steps;
@@ -1932,6 +1942,7 @@ int solve_impl(bddc_handle_s* h, const double* rhs, double* x, int nrhs, double 
   if (!(tol > 0.0)) fail(BDDC_ERR_INVALID, "tol must be positive");
   cudaStream_t st = h->st;
   const double t0 = now_ms();
+  ck(cudaMemsetAsync(h->d_status + 2, 0, sizeof(int), st), "status reset");   // timeout code of this call
   h->cur_steps = h->refine_steps;
   int maxits = 0, max_outer = 0;
   bool all_conv = true;
@@ -1946,12 +1957,18 @@ int solve_impl(bddc_handle_s* h, const double* rhs, double* x, int nrhs, double 
       launch_axpy_loc(h->fcol, h->d_lift, 1.0, h->n_free, st);
       f = h->fcol;
     }
-    condensed_rhs(h, f, h->vg, st);
     const bool refined = kind == BDDC_KRYLOV_PCG && h->use_outer;
-    PcgResult r = kind == BDDC_KRYLOV_BICGSTAB ? bicgstab(h, h->vg, h->vx, tol, h->opts.maxit)
-                  : kind == BDDC_KRYLOV_FGMRES ? fgmres(h, h->vg, h->vx, tol, h->opts.maxit)
-                  : refined                    ? pcg_refined(h, h->vg, tol, h->opts.maxit)
-                                               : pcg(h, h->vg, h->vx, tol, h->opts.maxit);
+    PcgResult r;
+    try {
+      condensed_rhs(h, f, h->vg, st);
+      r = kind == BDDC_KRYLOV_BICGSTAB ? bicgstab(h, h->vg, h->vx, tol, h->opts.maxit)
+          : kind == BDDC_KRYLOV_FGMRES ? fgmres(h, h->vg, h->vx, tol, h->opts.maxit)
+          : refined                    ? pcg_refined(h, h->vg, tol, h->opts.maxit)
+                                       : pcg(h, h->vg, h->vx, tol, h->opts.maxit);
+    } catch (const Fail& e) {
+      if (e.code != BDDC_ERR_TIMEOUT) throw_if_timeout(h);
+      throw;
+    }
     recover(h, f, refined ? h->vs : h->vx, u, st);
     maxits = std::max(maxits, r.iterations);
     max_outer = std::max(max_outer, r.outer);
@@ -2009,6 +2026,7 @@ bool grad_view(bddc_handle_s* h, GradView* v) {
   v->ndof = h->ndof;
   v->free_of_full = h->d_free_of_full;
   v->dir_full = h->has_lift ? h->d_dir_full : nullptr;
+  v->coef_linear = h->physics != BDDC_STOKES;
   v->stream = h->st;
   return true;
 }
@@ -2151,6 +2169,9 @@ int bddc_grad(bddc_handle h, const double* dJdu, const double* u, int nrhs, doub
               double* grad_rhs) {
   return guarded([&]() {
     if (!h || !h->factored || !dJdu || !u || nrhs < 1) fail(BDDC_ERR_INVALID, "bad arguments");
+    if (grad_coef && h->physics == BDDC_STOKES)
+      fail(BDDC_ERR_INVALID, "the coefficient gradient needs element matrices linear in the coefficient "
+                             "(Poisson, elasticity); the viscosity scales only the viscous block");
     cudaStream_t st = h->st;
     const size_t bytes = sizeof(double) * (size_t)h->n_free * nrhs;
     double* lam = grad_rhs;
@@ -2215,6 +2236,96 @@ int bddc_get_maps(bddc_handle h, int level, bddc_level_maps* out) {
     out->glob_promoted = m.glob_promoted.data();
     out->coarse_glob = m.coarse_glob.data();
     out->coarse_comp = m.coarse_comp.data();
+    return BDDC_OK;
+  });
+}
+
+int bddc_get_coarse(bddc_handle h, int level, double* kc, int64_t n) {
+  return guarded([&]() {
+    if (!h || !h->factored || !kc || level < 1 || level >= (int)h->lv.size())
+      fail(BDDC_ERR_INVALID, "bddc_get_coarse: needs a set-up handle, a BDDC level and a buffer");
+    const Level& L = h->lv[level - 1];
+    if (n < L.g_elems)
+      fail(BDDC_ERR_INVALID, "bddc_get_coarse: buffer of " + std::to_string(n) + " entries, needs " +
+                                 std::to_string(L.g_elems));
+    if (L.g_elems > 0)
+      ck(cudaMemcpyAsync(kc, L.d.KC, sizeof(double) * (size_t)L.g_elems, cudaMemcpyDeviceToHost, h->st), "d2h");
+    ck(cudaStreamSynchronize(h->st), "sync");
+    return BDDC_OK;
+  });
+}
+
+int bddc_tc_update_check(int64_t n, float* a, double* ms) {
+  return guarded([&]() {
+    if (!a || n < 5 * NB || n % NB != 0 || n > 64 * 1024)
+      fail(BDDC_ERR_INVALID, "bddc_tc_update_check: n must be a multiple of 64 in [320, 65536]");
+    const int nb = (int)(n / NB);
+    cudaStream_t st = nullptr;
+    DevArena A;
+    A.st = st;
+    try {
+      // one subdomain whose nb x nb block matrix is all "interior": tile (i, j), j <= i, holds a's block
+      SubMeta m{};
+      m.n = m.nI = (int32_t)n;
+      m.nIb = m.Bc = m.R = nb;
+      const int64_t tile_elems = (int64_t)nb * (nb + 1) / 2 * NB2;
+      std::vector<float> tiles((size_t)tile_elems);
+      for (int i = 0; i < nb; ++i)
+        for (int j = 0; j <= i; ++j) {
+          float* t = tiles.data() + ((int64_t)i * (i + 1) / 2 + j) * NB2;
+          for (int r = 0; r < NB; ++r)
+            std::memcpy(t + r * NB, a + ((int64_t)i * NB + r) * n + (int64_t)j * NB, sizeof(float) * NB);
+        }
+      LevelDev d{};
+      d.n_sub = 1;
+      d.n_vec = n;
+      std::vector<SubMeta> meta{m};
+      d.meta = A.upload(meta, st);
+      d.tiles = A.upload(tiles, st);
+      d.sgn = A.upload(std::vector<float>((size_t)n, 1.f), st);
+      d.status = A.upload(std::vector<int>{0, 0x7fffffff, 0, 0}, st);
+      const int64_t* prow_off = A.upload(std::vector<int64_t>{0}, st);
+      uint8_t* split = A.alloc<uint8_t>((int64_t)nb * kPanel * 2 * NB2 * 2);
+      float* rscale = A.alloc<float>((int64_t)nb * NB);
+      int64_t items = 0;
+      for (int j = kPanel; j < nb; j += 2) items += (nb - j + 1) / 2;
+      const int64_t* item_pref = A.upload(std::vector<int64_t>{0, items}, st);
+      TensorMap128 tmap{};
+      const int r = make_tile_tmap(&tmap, (float*)d.tiles, tile_elems);
+      if (r) fail(BDDC_ERR_CUDA, "cuTensorMapEncodeTiled failed (error " + std::to_string(r) + ")");
+      int dev = 0, sms = 0;
+      ck(cudaGetDevice(&dev), "cudaGetDevice");
+      ck(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
+      cudaEvent_t e0, e1;
+      ck(cudaEventCreate(&e0), "cudaEventCreate");
+      ck(cudaEventCreate(&e1), "cudaEventCreate");
+      launch_split_panel(d, 0, kPanel, nb, split, nullptr, rscale, prow_off, st);
+      ck(cudaEventRecord(e0, st), "cudaEventRecord");
+      launch_update_tc2(d, 0, kPanel, (int)std::min<int64_t>(items, std::max(1, sms)), split, split, rscale, prow_off,
+                        item_pref, tmap, st);
+      ck(cudaEventRecord(e1, st), "cudaEventRecord");
+      ck(cudaGetLastError(), "tensor-core update launch");
+      ck(cudaEventSynchronize(e1), "cudaEventSynchronize");
+      float t = 0.f;
+      ck(cudaEventElapsedTime(&t, e0, e1), "cudaEventElapsedTime");
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      if (ms) *ms = t;
+      int status[4];
+      ck(cudaMemcpy(status, d.status, sizeof(status), cudaMemcpyDeviceToHost), "d2h");
+      if (status[2]) fail(BDDC_ERR_TIMEOUT, "a bounded wait of the tensor-core update gave up");
+      ck(cudaMemcpy(tiles.data(), d.tiles, sizeof(float) * (size_t)tile_elems, cudaMemcpyDeviceToHost), "d2h");
+      for (int i = kPanel; i < nb; ++i)
+        for (int j = kPanel; j <= i; ++j) {
+          const float* t2 = tiles.data() + ((int64_t)i * (i + 1) / 2 + j) * NB2;
+          for (int r2 = 0; r2 < NB; ++r2)
+            std::memcpy(a + ((int64_t)i * NB + r2) * n + (int64_t)j * NB, t2 + r2 * NB, sizeof(float) * NB);
+        }
+    } catch (...) {
+      A.release();
+      throw;
+    }
+    A.release();
     return BDDC_OK;
   });
 }

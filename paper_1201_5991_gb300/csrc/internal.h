@@ -86,7 +86,9 @@ struct LevelDev {
   void* sgn;                      // [n_vec] pivot signs of the signed Cholesky (T; +1 for SPD levels)
   const double* c_rho;            // [sum nc] 1 where a constraint row is augmented by rho, else 0
   int indefinite;                 // 1: negative pivots allowed (Stokes), 0: SPD
-  int* status;                    // [4]: breakdown flag, level sub, timeout
+  int wait_probe;                 // test only: sweeps poll status[3] (never set) instead of their row flags
+  int* status;                    // [4]: breakdown flag, lowest breakdown subdomain, timeout code, a word
+                                  // nothing writes (the row-flag wait of the timeout probe)
 };
 
 // Counts every kernel launch of the library (defined in capi.cpp).
@@ -103,6 +105,7 @@ struct GradView {
   int ndof;                       // DOFs per node
   const int64_t* free_of_full;    // full DOF -> free id or -1
   const double* dir_full;         // [n_full] prescribed values (0 on free DOFs), or null when all zero
+  int coef_linear;                // 1: K_e is linear in coef_e (Poisson, elasticity), 0: Stokes
   cudaStream_t stream;
 };
 

@@ -10,7 +10,9 @@
 // one at a time, so the limit is 2 * n_full * 8 bytes <= 16 MiB, i.e. n_full <= 1,048,576
 // (n_full = nodes * DOFs per node, prescribed DOFs included); larger meshes are rejected with
 // BDDC_ERR_INVALID.  The adjoint solve itself uses only the buffers the handle allocated at
-// set-up.
+// set-up, once the handle is warm: its first solve (and the first after a change of Krylov
+// method) captures the CUDA graph of one iteration and creates that graph's stream and events.
+// The call synchronises the handle's stream, so it cannot run inside a stream capture.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -96,6 +98,11 @@ extern "C" int bddc_grad_noalloc(bddc_handle h, const double* dJdu, const double
   GradView v{};
   if (!h || !dJdu || !u || !grad_rhs || nrhs < 1 || !grad_view(h, &v)) {
     set_last_error("bddc_grad_noalloc: needs a set-up handle, dJdu, u, nrhs >= 1 and a grad_rhs buffer");
+    return BDDC_ERR_INVALID;
+  }
+  if (grad_coef && !v.coef_linear) {
+    set_last_error("bddc_grad_noalloc: the coefficient gradient needs element matrices linear in the coefficient "
+                   "(Poisson, elasticity)");
     return BDDC_ERR_INVALID;
   }
   if (2 * v.n_full > kScratchDoubles) {

@@ -12,7 +12,9 @@
 // blocks it depends on are published by other CTAs through per-row ready flags
 // (release/acquire).  A task only waits for tasks handed out before it, so the scheme cannot
 // deadlock whatever the residency.  Every wait is bounded; a timeout sets status[2] and the
-// kernel finishes without waiting further (the host reports BDDC_ERR_TIMEOUT).
+// kernel finishes without waiting further (the host reports BDDC_ERR_TIMEOUT).  A row-flag wait
+// that gives up stages the block as it is and goes on, so every tile copy is still consumed and
+// no access leaves the task's own rows; a tile wait that gives up drains the ring before exit.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -26,6 +28,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kYSlots = 16;          // solution blocks staged in shared memory at a time
 constexpr long long kSpinLimit = 1ll << 24;
+constexpr long long kProbeSpins = 32;   // row-flag wait limit of the timeout probe
 
 __device__ __forceinline__ int64_t tile_index(int i, int j, int Bc) {
   return i < Bc ? ((int64_t)i * (i + 1) / 2 + j) : ((int64_t)Bc * (Bc + 1) / 2 + (int64_t)(i - Bc) * Bc + j);
@@ -153,7 +156,8 @@ __global__ void __launch_bounds__(kThreads, 2)
             int ok = 1;
             if (k + q < nL) {
               const int j = BWD ? (B1 - 1 - (k + q)) : (B0 + k + q);
-              ok = ld_acquire(flags + fbase + j) != 0;
+              // the timeout probe polls a word that nothing sets (status[3]) instead of the row flag
+              ok = ld_acquire(L.wait_probe ? status + 3 : flags + fbase + j) != 0;
             } else {
               ok = 0;
             }
@@ -161,7 +165,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             ready = __ffs(~bal) - 1;          // consecutive ready tiles from k
             if (bal == 0xffffffffu) ready = 32;
             if (ready > 0) break;
-            if (++spins > kSpinLimit) {
+            if (++spins > (L.wait_probe ? kProbeSpins : kSpinLimit)) {
               if (lane == 0) atomicExch(status + 2, 1);
               ready = 1;
               break;

@@ -48,7 +48,7 @@ def host_mesh(prob, n_levels: Optional[int] = None) -> _HostMesh:
 
 def make_opts(precision="mixed", weights="stiffness", all_corners=0, maxit=500, refine_steps=0, flexible=-1,
               use_graph=1, profile=0, tensor_cores=1, inner_steps=0, inner_tol=0.0, krylov=0,
-              autotune=1, verbose=0) -> capi.Opts:
+              autotune=1, verbose=0, wait_probe=0) -> capi.Opts:
     o = capi.Opts()
     capi.lib().bddc_default_opts(C.byref(o))
     o.precision = capi.PREC_MIXED if precision == "mixed" else capi.PREC_FP64
@@ -65,6 +65,7 @@ def make_opts(precision="mixed", weights="stiffness", all_corners=0, maxit=500, 
     o.krylov = int(krylov)
     o.autotune = int(autotune)
     o.verbose = int(verbose)
+    o.wait_probe = int(wait_probe)
     return o
 
 
@@ -203,6 +204,18 @@ class BddcSolver:
         c = np.ascontiguousarray(coef, dtype=np.float64)
         capi.check(capi.lib().bddc_update_coef(self.hd.h, _ptr(c, C.c_double)))
 
+    def coarse_matrices(self, level: int = 1) -> list:
+        """Local coarse matrices K_Ci of every subdomain of a BDDC level (host numpy, FP64)."""
+        m = self.maps(level)
+        nc = np.diff(m["sub_coarse_ptr"])
+        buf = np.empty(int((nc * nc).sum()), dtype=np.float64)
+        capi.check(capi.lib().bddc_get_coarse(self.hd.h, level, _ptr(buf, C.c_double), buf.size))
+        out, off = [], 0
+        for k in nc:
+            out.append(buf[off:off + k * k].reshape(k, k).copy())
+            off += k * k
+        return out
+
     def maps(self, level: int = 1) -> dict:
         m = capi.LevelMaps()
         capi.check(capi.lib().bddc_get_maps(self.hd.h, level, C.byref(m)))
@@ -240,6 +253,7 @@ def _make_autograd():
             u = solver.solve(rhs.contiguous(), tol)
             ctx.solver = solver
             ctx.tol = tol
+            ctx.coef_device = coef.device
             ctx.save_for_backward(u)
             return u
 
@@ -249,7 +263,7 @@ def _make_autograd():
             gc, gr = ctx.solver.grad(grad_u.contiguous(), u, ctx.tol, want_coef=ctx.needs_input_grad[1],
                                      want_rhs=ctx.needs_input_grad[0])
             if gc is not None:
-                gc = gc.to(ctx.saved_tensors[0].device)
+                gc = gc.to(ctx.coef_device)   # the coefficients may live on the host
             return gr, gc, None, None
 
     return BddcSolve
@@ -264,3 +278,12 @@ def bddc_solve(rhs, coef, solver: BddcSolver, tol: float = 1e-10):
     if _autograd_fn is None:
         _autograd_fn = _make_autograd()
     return _autograd_fn.apply(rhs, coef, solver, tol)
+
+
+def tc_update_check(a: np.ndarray):
+    """a (n x n FP32) with a[i, j] -= sum_{q < 256} a[i, q] a[j, q] on the tile lower triangle of the
+    trailing part, through the tensor-core kernels of the factorisation.  Returns (result, ms)."""
+    a = np.ascontiguousarray(a, dtype=np.float32).copy()
+    ms = C.c_double()
+    capi.check(capi.lib().bddc_tc_update_check(a.shape[0], _ptr(a, C.c_float), C.byref(ms)))
+    return a, ms.value
