@@ -176,9 +176,42 @@ struct Level {
   double* gi1 = nullptr;
   double* gi2 = nullptr;
   double* gv0 = nullptr;       // [n_dof] (levels > 1)
+  int blk = 1;                 // right-hand sides the work vectors hold
 };
 
 int64_t pad_pos(const SubMeta& m, int64_t r) { return r < m.nI ? r : (int64_t)m.nIb * NB + (r - m.nI); }
+
+constexpr int kMaxBlock = 8;   // right-hand sides solved together (one pass over the factors)
+
+// Work vectors of the solve phase of one level for blocks of up to blk right-hand sides (every
+// column of a block has the vector kind's own length, see internal.h).
+void alloc_level_work(Level& L, DevArena& A, int blk) {
+  const int64_t nv = L.n_vec * blk;
+  if (L.fp32) {
+    L.locA = A.alloc<float>(nv);
+    L.locB = A.alloc<float>(nv);
+  } else {
+    L.locA = A.alloc<double>(nv);
+    L.locB = A.alloc<double>(nv);
+  }
+  L.dl0 = A.alloc<double>(nv);
+  L.dl1 = A.alloc<double>(nv);
+  L.dl2 = A.alloc<double>(nv);
+  L.dl3 = A.alloc<double>(nv);
+  L.cc_t = A.alloc<double>(L.sum_nc * blk);
+  L.cc_mu = A.alloc<double>(L.sum_nc * blk);
+  L.rc_sub = A.alloc<double>(L.sum_nc * blk);
+  L.psi_part = A.alloc<double>(L.sum_nc * kPsiSlices * blk);
+  L.zc_sub = A.alloc<double>(L.sum_nc * blk);
+  L.rC = A.alloc<double>(L.maps.n_coarse * blk);
+  L.zC = A.alloc<double>(L.maps.n_coarse * blk);
+  L.gi0 = A.alloc<double>(L.maps.n_iface * blk);
+  L.gi1 = A.alloc<double>(L.maps.n_iface * blk);
+  L.gi2 = A.alloc<double>(L.maps.n_iface * blk);
+  L.gv0 = A.alloc<double>(L.mesh.n_dof * blk);
+  if (L.solve32) L.v32 = A.alloc<float>(nv);
+  L.blk = blk;
+}
 
 constexpr int kPanel = 4;   // tile columns per tensor-core super-panel (256)
 
@@ -236,6 +269,7 @@ struct bddc_handle_s {
   int inner_steps = 0;                 // inner operator: 0 = from the stored factor, k = k interior-solve steps
   int cur_steps = 0;                   // steps used by the next interior solves
   int grid_max = 304;                  // persistent sweep grid: 2 CTAs per SM
+  int blk = 1;                         // right-hand sides the Krylov work vectors hold
   cudaStream_t cap_st = nullptr;       // private stream for graph capture
   cudaGraphExec_t iter_graph = nullptr;  // one captured Krylov iteration
   int iter_graph_key = -1;               // graph_key() of the captured iteration
@@ -730,14 +764,10 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
     }
     d.dinv = A.alloc<float>(L.dinv_elems);
     d.psi = A.alloc<float>(L.psi_elems);
-    L.locA = A.alloc<float>(L.n_vec);
-    L.locB = A.alloc<float>(L.n_vec);
   } else {
     d.tiles = A.alloc<double>(L.tile_elems);
     d.dinv = A.alloc<double>(L.dinv_elems);
     d.psi = A.alloc<double>(L.psi_elems);
-    L.locA = A.alloc<double>(L.n_vec);
-    L.locB = A.alloc<double>(L.n_vec);
   }
   (void)ts;
   d.status = h->d_status;
@@ -800,24 +830,10 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
       L.rows[k] = A.upload(rl[k], st);
     }
     L.crow_sub = A.upload(cs, st);
-    L.cc_t = A.alloc<double>(L.sum_nc);
-    L.cc_mu = A.alloc<double>(L.sum_nc);
   }
   L.slot_elem = A.upload(slot_elem, st);
   L.iface_dofs = A.upload(mp.iface_dofs, st);
-  L.dl0 = A.alloc<double>(L.n_vec);
-  L.dl1 = A.alloc<double>(L.n_vec);
-  L.dl2 = A.alloc<double>(L.n_vec);
-  L.dl3 = A.alloc<double>(L.n_vec);
-  L.rc_sub = A.alloc<double>(L.sum_nc);
-  L.psi_part = A.alloc<double>(L.sum_nc * kPsiSlices);
-  L.zc_sub = A.alloc<double>(L.sum_nc);
-  L.rC = A.alloc<double>(mp.n_coarse);
-  L.zC = A.alloc<double>(mp.n_coarse);
-  L.gi0 = A.alloc<double>(mp.n_iface);
-  L.gi1 = A.alloc<double>(mp.n_iface);
-  L.gi2 = A.alloc<double>(mp.n_iface);
-  L.gv0 = A.alloc<double>(ms.n_dof);
+  alloc_level_work(L, A, 1);
 }
 
 // Element matrices of levels > 1 come from the previous level's K_Ci: segment copies.
@@ -908,28 +924,42 @@ void reset_status(bddc_handle_s* h) {
 }
 
 // ------------------------------------------------------------------ solve-phase building blocks
-template <typename T>
-void trsv_one(bddc_handle_s* h, Level& L, T* v, int part, int backward, cudaStream_t st) {
-  const bool copy32 = sizeof(T) == 4 && L.solve32;   // FP32 copy of an FP64 factor
-  ProfScope ps(h, L.coarsest ? BDDC_PROF_COARSE : part == 0 ? BDDC_PROF_TRSV : BDDC_PROF_TRSV_IFACE,
-               copy32 ? 0.5 * L.trsv_bytes[part] : L.trsv_bytes[part], 0.0, st);
-  launch_sweep<T>(copy32 ? L.d32 : L.d, v, (L.sweep_order[part] ? L.tasks_big : L.tasks)[part][backward], L.ntasks[part][backward],
-                  part, backward, L.ctrl, L.n_ctrl, h->grid_max / 2 * L.sweep_ctas[part], L.sweep_deep[part], st);
+// Every building block acts on nb right-hand sides at once (nb <= the level's block capacity);
+// a block stores its columns one after another (see internal.h).
+
+// launches of a sweep or factor product over nb columns (groups of 8/4/2/1, or 4/2/1 in FP64)
+int column_groups(int nb, int max_nr) {
+  int n = 0;
+  for (int r = 0; r < nb; ++n) {
+    const int left = nb - r;
+    r += left >= max_nr ? max_nr : left >= 4 ? 4 : left >= 2 ? 2 : 1;
+  }
+  return n;
 }
 
 template <typename T>
-void trsv_pair(bddc_handle_s* h, Level& L, T* v, int part, cudaStream_t st) {
-  trsv_one<T>(h, L, v, part, 0, st);
-  trsv_one<T>(h, L, v, part, 1, st);
+void trsv_one(bddc_handle_s* h, Level& L, T* v, int part, int backward, cudaStream_t st, int nb = 1) {
+  const bool copy32 = sizeof(T) == 4 && L.solve32;   // FP32 copy of an FP64 factor
+  const double groups = column_groups(nb, sizeof(T) == 4 ? 8 : 4);
+  ProfScope ps(h, L.coarsest ? BDDC_PROF_COARSE : part == 0 ? BDDC_PROF_TRSV : BDDC_PROF_TRSV_IFACE,
+               groups * (copy32 ? 0.5 * L.trsv_bytes[part] : L.trsv_bytes[part]), 0.0, st);
+  launch_sweep<T>(copy32 ? L.d32 : L.d, v, (L.sweep_order[part] ? L.tasks_big : L.tasks)[part][backward], L.ntasks[part][backward],
+                  part, backward, L.ctrl, L.n_ctrl, h->grid_max / 2 * L.sweep_ctas[part], L.sweep_deep[part], st, nb);
+}
+
+template <typename T>
+void trsv_pair(bddc_handle_s* h, Level& L, T* v, int part, cudaStream_t st, int nb = 1) {
+  trsv_one<T>(h, L, v, part, 0, st, nb);
+  trsv_one<T>(h, L, v, part, 1, st, nb);
 }
 
 // w = K_II^{-1} v on level 1 (interior positions), FP64 accuracy.
 // FP64 factors: two sweeps.  FP32 factors: iterative refinement with the FP64 K_II.
-void interior_solve_l1(bddc_handle_s* h, Level& L, const double* v, double* w, cudaStream_t st) {
-  const int64_t n = L.n_vec;
+void interior_solve_l1(bddc_handle_s* h, Level& L, const double* v, double* w, cudaStream_t st, int nb = 1) {
+  const int64_t n = L.n_vec * nb;
   if (!L.fp32) {
     ck(cudaMemcpyAsync(w, v, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
-    trsv_pair<double>(h, L, w, 0, st);
+    trsv_pair<double>(h, L, w, 0, st, nb);
     return;
   }
   float* t = (float*)L.locB;
@@ -938,11 +968,11 @@ void interior_solve_l1(bddc_handle_s* h, Level& L, const double* v, double* w, c
   const int steps = std::max(1, h->cur_steps);
   for (int it = 0; it < steps; ++it) {
     launch_convert<double, float>(it == 0 ? v : r, t, n, st);
-    trsv_pair<float>(h, L, t, 0, st);
+    trsv_pair<float>(h, L, t, 0, st, nb);
     launch_add_to_double<float>(w, t, n, st);
     if (it + 1 < steps) {
       ck(cudaMemcpyAsync(r, v, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
-      launch_spmv_rows(L.d, L.rows[0], L.nrows[0], w, r, -1.0, 1.0, L.row_sub, st);
+      launch_spmv_rows(L.d, L.rows[0], L.nrows[0], w, r, -1.0, 1.0, L.row_sub, st, nb);
     }
   }
 }
@@ -950,128 +980,130 @@ void interior_solve_l1(bddc_handle_s* h, Level& L, const double* v, double* w, c
 // y = S x on the level-1 interface (Sec. 2, discrete Dirichlet problems).  With cur_steps = 0
 // on an FP32 level: the inner operator S~ = sum R_i^T (L_GG S L_GG^T - C_i^T R C_i) R_i from the
 // stored factor (no interior solves).
-void schur_apply(bddc_handle_s* h, const double* x, double* y, cudaStream_t st) {
+void schur_apply(bddc_handle_s* h, const double* x, double* y, cudaStream_t st, int nb = 1) {
   Level& L = h->lv[0];
-  const int64_t n = L.n_vec;
+  const int64_t n = L.n_vec * nb;
   if (L.fp32 && h->cur_steps == 0) {
-    launch_gather_iface<double>(L.d, x, 0, L.dl0, st);
+    launch_gather_iface<double>(L.d, x, 0, L.dl0, st, nb);
     launch_convert<double, float>(L.dl0, (float*)L.locA, n, st);
     {
-      ProfScope ps(h, BDDC_PROF_TRMV, L.trmv_bytes, 0.0, st);
-      launch_trmv_schur(L.d, L.max_nGb, (const float*)L.locA, (float*)L.locB, (float*)L.locA, st);
+      ProfScope ps(h, BDDC_PROF_TRMV, column_groups(nb, 8) * L.trmv_bytes, 0.0, st);
+      launch_trmv_schur(L.d, L.max_nGb, (const float*)L.locA, (float*)L.locB, (float*)L.locA, st, nb);
     }
     launch_convert<float, double>((const float*)L.locA, L.dl1, n, st);
-    launch_sub_ctrc(L.d, L.crow_sub, L.sum_nc, L.dl0, L.dl1, st);
-    launch_scatter_iface<double>(L.d, L.dl1, 0, y, st);
+    launch_sub_ctrc(L.d, L.crow_sub, L.sum_nc, L.dl0, L.dl1, st, nb);
+    launch_scatter_iface<double>(L.d, L.dl1, 0, y, st, nb);
     return;
   }
-  launch_gather_iface<double>(L.d, x, 0, L.dl0, st);                 // x_i = R_i x
+  launch_gather_iface<double>(L.d, x, 0, L.dl0, st, nb);                 // x_i = R_i x
   ck(cudaMemsetAsync(L.dl1, 0, sizeof(double) * n, st), "memset");
-  launch_spmv_rows(L.d, L.rows[0], L.nrows[0], L.dl0, L.dl1, 1.0, 0.0, L.row_sub, st);  // v = K_IG x_i
-  interior_solve_l1(h, L, L.dl1, L.dl2, st);                        // w = K_II^{-1} v
-  launch_axpy_loc(L.dl0, L.dl2, -1.0, n, st);                       // t = [-w ; x_i]
-  launch_spmv_rows(L.d, L.rows[1], L.nrows[1], L.dl0, L.dl1, 1.0, 0.0, L.row_sub, st);  // y_i = K_GG x_i - K_GI w
-  launch_scatter_iface<double>(L.d, L.dl1, 0, y, st);                // y = sum R_i^T y_i
+  launch_spmv_rows(L.d, L.rows[0], L.nrows[0], L.dl0, L.dl1, 1.0, 0.0, L.row_sub, st, nb);  // v = K_IG x_i
+  interior_solve_l1(h, L, L.dl1, L.dl2, st, nb);                        // w = K_II^{-1} v
+  launch_axpy_loc(L.dl0, L.dl2, -1.0, n, st);                           // t = [-w ; x_i]
+  launch_spmv_rows(L.d, L.rows[1], L.nrows[1], L.dl0, L.dl1, 1.0, 0.0, L.row_sub, st, nb);  // y_i = K_GG x_i - K_GI w
+  launch_scatter_iface<double>(L.d, L.dl1, 0, y, st, nb);                // y = sum R_i^T y_i
 }
 
-// g = f_G - sum R_i^T K_GI K_II^{-1} f_I
-void condensed_rhs(bddc_handle_s* h, const double* f, double* g, cudaStream_t st) {
+// g = f_G - sum R_i^T K_GI K_II^{-1} f_I   (f: nb columns of n_free)
+void condensed_rhs(bddc_handle_s* h, const double* f, double* g, cudaStream_t st, int nb = 1) {
   Level& L = h->lv[0];
-  launch_gather_glob<double>(L.d, f, 0, L.dl1, st);
-  interior_solve_l1(h, L, L.dl1, L.dl2, st);
-  launch_spmv_rows(L.d, L.rows[1], L.nrows[1], L.dl2, L.dl0, 1.0, 0.0, L.row_sub, st);
-  launch_scatter_iface<double>(L.d, L.dl0, 0, L.gi0, st);
-  launch_iface_rhs(g, f, L.iface_dofs, L.gi0, L.d.n_iface, st);
+  launch_gather_glob<double>(L.d, f, 0, L.dl1, st, nb);
+  interior_solve_l1(h, L, L.dl1, L.dl2, st, nb);
+  launch_spmv_rows(L.d, L.rows[1], L.nrows[1], L.dl2, L.dl0, 1.0, 0.0, L.row_sub, st, nb);
+  launch_scatter_iface<double>(L.d, L.dl0, 0, L.gi0, st, nb);
+  launch_iface_rhs(g, f, L.d.n_dof, L.iface_dofs, L.gi0, L.d.n_iface, st, nb);
 }
 
 // u_I = K_II^{-1} (f_I - K_IG u_G), u_G = u_hat
-void recover(bddc_handle_s* h, const double* f, const double* uG, double* u, cudaStream_t st) {
+void recover(bddc_handle_s* h, const double* f, const double* uG, double* u, cudaStream_t st, int nb = 1) {
   Level& L = h->lv[0];
-  launch_gather_iface<double>(L.d, uG, 0, L.dl0, st);
-  launch_gather_glob<double>(L.d, f, 0, L.dl1, st);
-  launch_spmv_rows(L.d, L.rows[0], L.nrows[0], L.dl0, L.dl1, -1.0, 1.0, L.row_sub, st);
-  interior_solve_l1(h, L, L.dl1, L.dl2, st);
-  ck(cudaMemsetAsync(u, 0, sizeof(double) * h->n_free, st), "memset");
-  launch_scatter_interior<double>(L.d, L.dl2, u, st);
-  launch_put_indexed(u, L.iface_dofs, uG, L.d.n_iface, st);
+  launch_gather_iface<double>(L.d, uG, 0, L.dl0, st, nb);
+  launch_gather_glob<double>(L.d, f, 0, L.dl1, st, nb);
+  launch_spmv_rows(L.d, L.rows[0], L.nrows[0], L.dl0, L.dl1, -1.0, 1.0, L.row_sub, st, nb);
+  interior_solve_l1(h, L, L.dl1, L.dl2, st, nb);
+  ck(cudaMemsetAsync(u, 0, sizeof(double) * h->n_free * nb, st), "memset");
+  launch_scatter_interior<double>(L.d, L.dl2, u, st, nb);
+  launch_put_indexed(u, h->n_free, L.iface_dofs, uG, L.d.n_iface, st, nb);
 }
 
-void coarsest_solve(bddc_handle_s* h, const double* rC, double* zC, cudaStream_t st) {
+void coarsest_solve(bddc_handle_s* h, const double* rC, double* zC, cudaStream_t st, int nb = 1) {
   Level& C = h->lv.back();
   if (C.solve32) {   // mixed form: the preconditioner's coarse solve with the FP32 copy of the factor
-    launch_gather_glob<float>(C.d32, rC, 2, C.v32, st);
-    trsv_pair<float>(h, C, C.v32, 0, st);
-    launch_scatter_interior<float>(C.d32, C.v32, zC, st);
+    launch_gather_glob<float>(C.d32, rC, 2, C.v32, st, nb);
+    trsv_pair<float>(h, C, C.v32, 0, st, nb);
+    launch_scatter_interior<float>(C.d32, C.v32, zC, st, nb);
     return;
   }
   double* v = (double*)C.locA;
-  launch_gather_glob<double>(C.d, rC, 2, v, st);
-  trsv_pair<double>(h, C, v, 0, st);
-  launch_scatter_interior<double>(C.d, v, zC, st);
+  launch_gather_glob<double>(C.d, rC, 2, v, st, nb);
+  trsv_pair<double>(h, C, v, 0, st, nb);
+  launch_scatter_interior<double>(C.d, v, zC, st, nb);
 }
 
-void full_step(bddc_handle_s* h, int l, const double* r, double* z, cudaStream_t st);
+void full_step(bddc_handle_s* h, int l, const double* r, double* z, cudaStream_t st, int nb);
 
 // One interface step of Algorithm 2 on BDDC level l: distribute, subdomain corrections,
 // coarse residual, coarse correction (coarsest solve or the next level), combine.
 template <typename T>
-void interface_step_t(bddc_handle_s* h, int l, const double* rhat, double* zhat, cudaStream_t st) {
+void interface_step_t(bddc_handle_s* h, int l, const double* rhat, double* zhat, cudaStream_t st, int nb) {
   Level& L = h->lv[l];
   T* v = (T*)L.locA;
-  launch_gather_iface<T>(L.d, rhat, 1, v, st);          // r_i = E_i^T r_hat
-  launch_psi_t_apply<T>(L.d, v, L.psi_part, L.sum_nc, L.rc_sub, st);   // Psi_i^T r_i
-  launch_coarse_gather(L.d, L.rc_sub, L.rC, st);        // r_C = sum R_Ci^T Psi_i^T r_i
-  trsv_one<T>(h, L, v, 1, 0, st);                       // Eq. sub_cor via the trailing factor
-  launch_constraint_corr<T>(L.d, v, L.crow_sub, L.sum_nc, L.cc_t, L.cc_mu, L.max_nGb, st);
-  trsv_one<T>(h, L, v, 1, 1, st);
+  launch_gather_iface<T>(L.d, rhat, 1, v, st, nb);          // r_i = E_i^T r_hat
+  launch_psi_t_apply<T>(L.d, v, L.psi_part, L.sum_nc, L.rc_sub, st, nb);   // Psi_i^T r_i
+  launch_coarse_gather(L.d, L.rc_sub, L.sum_nc, L.rC, st, nb);   // r_C = sum R_Ci^T Psi_i^T r_i
+  trsv_one<T>(h, L, v, 1, 0, st, nb);                       // Eq. sub_cor via the trailing factor
+  launch_constraint_corr<T>(L.d, v, L.crow_sub, L.sum_nc, L.cc_t, L.cc_mu, L.max_nGb, st, nb);
+  trsv_one<T>(h, L, v, 1, 1, st, nb);
   const bool last = l + 2 == (int)h->lv.size();
   if (last)
-    coarsest_solve(h, L.rC, L.zC, st);
+    coarsest_solve(h, L.rC, L.zC, st, nb);
   else
-    full_step(h, l + 1, L.rC, L.zC, st);
-  launch_coarse_scatter_n(L.d.sub_coarse, L.sum_nc, L.zC, L.zc_sub, st);
-  launch_psi_apply_add<T>(L.d, L.zc_sub, v, L.max_nG, st);   // Psi_i R_Ci z_C + z_i
-  launch_scatter_iface<T>(L.d, v, 1, zhat, st);            // z_hat = sum E_i (...)
+    full_step(h, l + 1, L.rC, L.zC, st, nb);
+  launch_coarse_scatter_n(L.d.sub_coarse, L.sum_nc, L.zC, L.d.n_coarse, L.zc_sub, st, nb);
+  launch_psi_apply_add<T>(L.d, L.zc_sub, L.sum_nc, v, L.max_nG, st, nb);   // Psi_i R_Ci z_C + z_i
+  launch_scatter_iface<T>(L.d, v, 1, zhat, st, nb);            // z_hat = sum E_i (...)
 }
 
-void interface_step(bddc_handle_s* h, int l, const double* rhat, double* zhat, cudaStream_t st) {
+void interface_step(bddc_handle_s* h, int l, const double* rhat, double* zhat, cudaStream_t st, int nb) {
   if (h->lv[l].fp32)
-    interface_step_t<float>(h, l, rhat, zhat, st);
+    interface_step_t<float>(h, l, rhat, zhat, st, nb);
   else
-    interface_step_t<double>(h, l, rhat, zhat, st);
+    interface_step_t<double>(h, l, rhat, zhat, st, nb);
 }
 
 // Levels l > 1: interior pre-correction, interface step, interior post-correction
 template <typename T>
-void full_step_t(bddc_handle_s* h, int l, const double* r, double* z, cudaStream_t st) {
+void full_step_t(bddc_handle_s* h, int l, const double* r, double* z, cudaStream_t st, int nb) {
   Level& L = h->lv[l];
-  const int64_t n = L.n_vec;
+  const int64_t n = L.n_vec * nb;
   T* v = (T*)L.locB;
-  launch_gather_glob<T>(L.d, r, 0, v, st);                  // r_I
-  trsv_pair<T>(h, L, v, 0, st);                                // u1 = A_II^{-1} r_I
+  launch_gather_glob<T>(L.d, r, 0, v, st, nb);                     // r_I
+  trsv_pair<T>(h, L, v, 0, st, nb);                                // u1 = A_II^{-1} r_I
   launch_convert<T, double>(v, L.dl0, n, st);
-  launch_spmv_rows(L.d, L.rows[1], L.nrows[1], L.dl0, L.dl1, 1.0, 0.0, L.row_sub, st);   // (A_GI u1)_i
-  launch_scatter_iface<double>(L.d, L.dl1, 0, L.gi0, st);
-  launch_iface_rhs(L.gi1, r, L.iface_dofs, L.gi0, L.d.n_iface, st); // r'_G = r_G - A_GI u1
-  interface_step(h, l, L.gi1, L.gi2, st);                             // z_G
-  launch_gather_iface<double>(L.d, L.gi2, 0, L.dl0, st);
-  launch_gather_glob<double>(L.d, r, 0, L.dl1, st);
-  launch_spmv_rows(L.d, L.rows[0], L.nrows[0], L.dl0, L.dl1, -1.0, 1.0, L.row_sub, st);  // r_I - A_IG z_G
+  launch_spmv_rows(L.d, L.rows[1], L.nrows[1], L.dl0, L.dl1, 1.0, 0.0, L.row_sub, st, nb);   // (A_GI u1)_i
+  launch_scatter_iface<double>(L.d, L.dl1, 0, L.gi0, st, nb);
+  launch_iface_rhs(L.gi1, r, L.d.n_dof, L.iface_dofs, L.gi0, L.d.n_iface, st, nb);   // r'_G = r_G - A_GI u1
+  interface_step(h, l, L.gi1, L.gi2, st, nb);                       // z_G
+  launch_gather_iface<double>(L.d, L.gi2, 0, L.dl0, st, nb);
+  launch_gather_glob<double>(L.d, r, 0, L.dl1, st, nb);
+  launch_spmv_rows(L.d, L.rows[0], L.nrows[0], L.dl0, L.dl1, -1.0, 1.0, L.row_sub, st, nb);  // r_I - A_IG z_G
   launch_convert<double, T>(L.dl1, v, n, st);
-  trsv_pair<T>(h, L, v, 0, st);                                           // z_I
-  ck(cudaMemsetAsync(z, 0, sizeof(double) * L.d.n_dof, st), "memset");
-  launch_scatter_interior<T>(L.d, v, z, st);
-  launch_put_indexed(z, L.iface_dofs, L.gi2, L.d.n_iface, st);
+  trsv_pair<T>(h, L, v, 0, st, nb);                                 // z_I
+  ck(cudaMemsetAsync(z, 0, sizeof(double) * L.d.n_dof * nb, st), "memset");
+  launch_scatter_interior<T>(L.d, v, z, st, nb);
+  launch_put_indexed(z, L.d.n_dof, L.iface_dofs, L.gi2, L.d.n_iface, st, nb);
 }
 
-void full_step(bddc_handle_s* h, int l, const double* r, double* z, cudaStream_t st) {
+void full_step(bddc_handle_s* h, int l, const double* r, double* z, cudaStream_t st, int nb) {
   if (h->lv[l].fp32)
-    full_step_t<float>(h, l, r, z, st);
+    full_step_t<float>(h, l, r, z, st, nb);
   else
-    full_step_t<double>(h, l, r, z, st);
+    full_step_t<double>(h, l, r, z, st, nb);
 }
 
-void precond(bddc_handle_s* h, const double* r, double* z, cudaStream_t st) { interface_step(h, 0, r, z, st); }
+void precond(bddc_handle_s* h, const double* r, double* z, cudaStream_t st, int nb = 1) {
+  interface_step(h, 0, r, z, st, nb);
+}
 
 double dot_host(bddc_handle_s* h, const double* a, const double* b, int64_t n) {
   launch_dot(a, b, n, h->partial, kDotBlocks, h->scal + 15, h->st);
@@ -1227,7 +1259,7 @@ void numeric_setup(bddc_handle_s* h) {
         L.d32.tiles = h->arena.alloc<float>(L.tile_elems);
         L.d32.dinv = h->arena.alloc<float>(L.dinv_elems);
         L.d32.sgn = h->arena.alloc<float>(L.n_vec);
-        L.v32 = h->arena.alloc<float>(L.n_vec);
+        L.v32 = h->arena.alloc<float>(L.n_vec * L.blk);
         L.solve32 = true;
       }
       launch_convert<double, float>((const double*)L.d.tiles, (float*)L.d32.tiles, L.tile_elems, st);
@@ -1471,23 +1503,24 @@ struct PcgResult {
   std::vector<double> alpha, beta;
 };
 
-// One full PCG iteration (Sec. 4) on the level-1 interface, all on the device:
-// q = S p, alpha = r.z / p.q, x += alpha p, r -= alpha q, ||r||^2, z = M^{-1} r (Algorithm 2),
-// beta (Fletcher-Reeves or flexible), p = z + beta p.  Scalars stay in device memory.
-void pcg_body(bddc_handle_s* h, double* x, int flexible, cudaStream_t st) {
+// One full PCG iteration (Sec. 4) on the level-1 interface for a block of nb right-hand sides,
+// all on the device: q = S p, alpha = r.z / p.q, x += alpha p, r -= alpha q, ||r||^2,
+// z = M^{-1} r (Algorithm 2), beta (Fletcher-Reeves or flexible), p = z + beta p.  Column k keeps
+// its scalars at scal[16 k ..]; a column whose flag scal[16 k + 8] is set stays frozen.
+void pcg_body(bddc_handle_s* h, double* x, int flexible, cudaStream_t st, int nb) {
   const int64_t n = h->lv[0].d.n_iface;
   double* S = h->scal;
-  schur_apply(h, h->vp, h->vq, st);
-  launch_dot(h->vp, h->vq, n, h->partial, kDotBlocks, S + 1, st);
-  launch_pcg_scalars(S, 0, flexible, st);
-  if (flexible) ck(cudaMemcpyAsync(h->vrold, h->vr, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
-  launch_pcg_update_x_r(x, h->vr, h->vp, h->vq, S, n, st);
-  launch_dot(h->vr, h->vr, n, h->partial, kDotBlocks, S + 5, st);
-  precond(h, h->vr, h->vz, st);
-  launch_dot(h->vr, h->vz, n, h->partial, kDotBlocks, S + 4, st);
-  if (flexible) launch_dot(h->vz, h->vrold, n, h->partial, kDotBlocks, S + 7, st);
-  launch_pcg_scalars(S, 1, flexible, st);
-  launch_pcg_update_p(h->vp, h->vz, S, n, st);
+  schur_apply(h, h->vp, h->vq, st, nb);
+  launch_dot(h->vp, h->vq, n, h->partial, kDotBlocks, S + 1, st, nb);
+  launch_pcg_scalars(S, 0, flexible, st, nb);
+  if (flexible) ck(cudaMemcpyAsync(h->vrold, h->vr, sizeof(double) * n * nb, cudaMemcpyDeviceToDevice, st), "copy");
+  launch_pcg_update_x_r(x, h->vr, h->vp, h->vq, S, n, st, nb);
+  launch_dot(h->vr, h->vr, n, h->partial, kDotBlocks, S + 5, st, nb);
+  precond(h, h->vr, h->vz, st, nb);
+  launch_dot(h->vr, h->vz, n, h->partial, kDotBlocks, S + 4, st, nb);
+  if (flexible) launch_dot(h->vz, h->vrold, n, h->partial, kDotBlocks, S + 7, st, nb);
+  launch_pcg_scalars(S, 1, flexible, st, nb);
+  launch_pcg_update_p(h->vp, h->vz, S, n, st, nb);
 }
 
 // One right-preconditioned BiCGstab iteration (van der Vorst; the Krylov method of the Stokes
@@ -1514,27 +1547,28 @@ void bicg_body(bddc_handle_s* h, double* x, cudaStream_t st) {
   launch_dot(h->vr, h->vr, n, h->partial, kDotBlocks, S + 8, st);
 }
 
-// kind 0/1: PCG with Fletcher-Reeves / flexible beta; 2: BiCGstab
-void iteration_body(bddc_handle_s* h, double* x, int kind, cudaStream_t st) {
+// kind 0/1: PCG with Fletcher-Reeves / flexible beta (nb columns); 2: BiCGstab (one column)
+void iteration_body(bddc_handle_s* h, double* x, int kind, cudaStream_t st, int nb) {
   if (kind == 2)
     bicg_body(h, x, st);
   else
-    pcg_body(h, x, kind, st);
+    pcg_body(h, x, kind, st, nb);
 }
 
-// Capture one Krylov iteration into a CUDA graph (once per handle; the buffers never move).
-// A captured iteration depends on the method (0/1: PCG with Fletcher-Reeves / flexible beta,
-// 2: BiCGstab) and on the interior-solve steps of the Schur operator.
-int graph_key(const bddc_handle_s* h, int kind) { return kind | (h->cur_steps << 3); }
+// Capture one Krylov iteration into a CUDA graph (once per handle and key; the buffers never
+// move while a graph is cached).  A captured iteration depends on the method (0/1: PCG with
+// Fletcher-Reeves / flexible beta, 2: BiCGstab), on the interior-solve steps of the Schur operator
+// and on the number of right-hand sides of the block.
+int graph_key(const bddc_handle_s* h, int kind, int nb) { return kind | (h->cur_steps << 3) | (nb << 8); }
 
-void capture_iteration(bddc_handle_s* h, int flexible) {
+void capture_iteration(bddc_handle_s* h, int kind, int nb) {
   if (!h->cap_st) ck(cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking), "cudaStreamCreate");
   cudaGraph_t g = nullptr;
   flush_profile(h);   // events recorded so far belong to eager launches
   const int64_t launches0 = g_launches.load();
   ck(cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
   try {
-    iteration_body(h, h->vx, flexible, h->cap_st);
+    iteration_body(h, h->vx, kind, h->cap_st, nb);
   } catch (...) {
     cudaStreamEndCapture(h->cap_st, &g);
     if (g) cudaGraphDestroy(g);
@@ -1551,13 +1585,14 @@ void capture_iteration(bddc_handle_s* h, int flexible) {
   cudaGraphDestroy(g);
   ck(e, "cudaGraphInstantiate");
   h->iter_graph = ex;
-  h->iter_graph_key = graph_key(h, flexible);
+  h->iter_graph_key = graph_key(h, kind, nb);
 }
 
-void drop_graph_if_kind_differs(bddc_handle_s* h, int kind) {
-  if (!h->iter_graph || h->iter_graph_key == graph_key(h, kind)) return;
+void drop_graph(bddc_handle_s* h) {
+  if (!h->iter_graph) return;
   cudaGraphExecDestroy(h->iter_graph);
   h->iter_graph = nullptr;
+  h->iter_graph_key = -1;
   for (auto& r : h->graph_prof) {
     h->event_pool.push_back(r.a);
     h->event_pool.push_back(r.b);
@@ -1565,46 +1600,103 @@ void drop_graph_if_kind_differs(bddc_handle_s* h, int kind) {
   h->graph_prof.clear();
 }
 
-// r = g - S x, z = M^{-1} r, p = z, rz = r.z  (start, or restart after a failed true-residual check)
-void pcg_start(bddc_handle_s* h, const double* g, double* x, bool x_zero, cudaStream_t st) {
-  const int64_t n = h->lv[0].d.n_iface;
-  double* S = h->scal;
-  ck(cudaMemcpyAsync(h->vr, g, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
-  if (!x_zero) {
-    schur_apply(h, x, h->vq, st);
-    launch_axpy_loc(h->vr, h->vq, -1.0, n, st);
-  }
-  precond(h, h->vr, h->vz, st);
-  ck(cudaMemcpyAsync(h->vp, h->vz, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
-  launch_dot(h->vr, h->vz, n, h->partial, kDotBlocks, S + 0, st);
+void drop_graph_if_kind_differs(bddc_handle_s* h, int kind, int nb) {
+  if (h->iter_graph && h->iter_graph_key != graph_key(h, kind, nb)) drop_graph(h);
 }
 
-PcgResult pcg(bddc_handle_s* h, const double* g, double* x, double tol, int maxit) {
+// Work vectors for blocks of up to kMaxBlock right-hand sides: allocated at the first solve with
+// more than one right-hand side (a set-up allocates for one); the cached iteration graph, which
+// refers to the old buffers, is dropped.
+void ensure_block(bddc_handle_s* h, int nb) {
+  if (h->blk >= nb) return;
+  const int blk = kMaxBlock;
+  ck(cudaStreamSynchronize(h->st), "sync");
+  drop_graph(h);
+  DevArena& A = h->arena;
+  for (Level& L : h->lv) alloc_level_work(L, A, blk);
+  const int64_t ni = std::max<int64_t>(h->lv[0].d.n_iface, 1) * blk;
+  h->vx = A.alloc<double>(ni);
+  h->vr = A.alloc<double>(ni);
+  h->vz = A.alloc<double>(ni);
+  h->vp = A.alloc<double>(ni);
+  h->vq = A.alloc<double>(ni);
+  h->vrold = A.alloc<double>(ni);
+  h->vg = A.alloc<double>(ni);
+  h->vs = A.alloc<double>(ni);
+  h->vsh = A.alloc<double>(ni);
+  h->vt = A.alloc<double>(ni);
+  h->scal = A.alloc<double>(16 * blk);
+  h->partial = A.alloc<double>((int64_t)kDotBlocks * blk);
+  if (h->h_scal) cudaFreeHost(h->h_scal);
+  h->h_scal = nullptr;
+  ck(cudaMallocHost(&h->h_scal, sizeof(double) * 16 * blk), "cudaMallocHost");
+  h->fcol = A.alloc<double>(h->n_free * blk);
+  h->ucol = A.alloc<double>(h->n_free * blk);
+  h->blk = blk;
+}
+
+// r = g - S x, z = M^{-1} r, p = z, rz = r.z  (start, or restart after a failed true-residual
+// check) for every column of the block
+void pcg_start(bddc_handle_s* h, const double* g, double* x, bool x_zero, cudaStream_t st, int nb) {
+  const int64_t n = h->lv[0].d.n_iface;
+  double* S = h->scal;
+  ck(cudaMemcpyAsync(h->vr, g, sizeof(double) * n * nb, cudaMemcpyDeviceToDevice, st), "copy");
+  if (!x_zero) {
+    schur_apply(h, x, h->vq, st, nb);
+    launch_axpy_loc(h->vr, h->vq, -1.0, n * nb, st);
+  }
+  precond(h, h->vr, h->vz, st, nb);
+  ck(cudaMemcpyAsync(h->vp, h->vz, sizeof(double) * n * nb, cudaMemcpyDeviceToDevice, st), "copy");
+  launch_dot(h->vr, h->vz, n, h->partial, kDotBlocks, S + 0, st, nb);
+}
+
+// Freeze column k of the running block PCG (its alpha and beta become 0 from the next kernel on).
+void freeze_column(bddc_handle_s* h, int k) {
+  h->h_scal[16 * k + 8] = 1.0;
+  ck(cudaMemcpyAsync(h->scal + 16 * k + 8, h->h_scal + 16 * k + 8, sizeof(double), cudaMemcpyHostToDevice, h->st),
+     "h2d");
+}
+
+// PCG on the level-1 interface (Sec. 4) for nb right-hand sides g (columns of n_iface) in
+// lockstep: every iteration applies S and the preconditioner to the whole block, so each factor
+// tile is read once for all columns.  Column k stops at ||r_k|| / ||g_k|| <= tol[k] once its true
+// residual confirms it (after one failed confirmation every column restarts from its iterate with
+// the true residual; after a second the column stops as not converged); stopped columns stay
+// frozen while the others continue.  x: nb columns.
+std::vector<PcgResult> pcg(bddc_handle_s* h, const double* g, double* x, const std::vector<double>& tol, int maxit,
+                           int nb) {
   cudaStream_t st = h->st;
   const int64_t n = h->lv[0].d.n_iface;
-  PcgResult res;
+  std::vector<PcgResult> res(nb);
   const int flexible = h->opts.flexible < 0 ? (h->opts.precision == BDDC_PREC_MIXED) : h->opts.flexible;
-  ck(cudaMemsetAsync(x, 0, sizeof(double) * n, st), "memset");
+  ck(cudaMemsetAsync(x, 0, sizeof(double) * n * nb, st), "memset");
   if (n == 0) {
-    res.converged = true;
+    for (auto& r : res) r.converged = true;
     return res;
   }
   double* S = h->scal;
-  ck(cudaMemsetAsync(S, 0, sizeof(double) * 16, st), "memset");
-  launch_dot(g, g, n, h->partial, kDotBlocks, S + 6, st);
-  pcg_start(h, g, x, true, st);
-  ck(cudaMemcpyAsync(h->h_scal, S, sizeof(double) * 16, cudaMemcpyDeviceToHost, st), "d2h");
+  ck(cudaMemsetAsync(S, 0, sizeof(double) * 16 * nb, st), "memset");
+  launch_dot(g, g, n, h->partial, kDotBlocks, S + 6, st, nb);
+  ck(cudaMemcpyAsync(h->h_scal, S, sizeof(double) * 16 * nb, cudaMemcpyDeviceToHost, st), "d2h");
   ck(cudaStreamSynchronize(st), "sync");
-  const double gg = h->h_scal[6];
-  if (!std::isfinite(gg)) fail(BDDC_ERR_NAN, "NaN in the condensed right-hand side");
-  res.gnorm = std::sqrt(gg);
-  if (gg == 0.0) {
-    res.converged = true;
-    return res;
+  std::vector<double> gg(nb);
+  std::vector<char> frozen(nb, 0), checked(nb, 0);
+  int active = nb;
+  for (int k = 0; k < nb; ++k) {
+    gg[k] = h->h_scal[16 * k + 6];
+    if (!std::isfinite(gg[k])) fail(BDDC_ERR_NAN, "NaN in the condensed right-hand side");
+    res[k].gnorm = std::sqrt(gg[k]);
+    if (gg[k] == 0.0) {
+      res[k].converged = true;
+      frozen[k] = 1;
+      --active;
+      freeze_column(h, k);
+    }
   }
+  if (active == 0) return res;
+  pcg_start(h, g, x, true, st, nb);
   const bool graphs = h->opts.use_graph && x == h->vx;
-  drop_graph_if_kind_differs(h, flexible);
-  bool checked = false;
+  drop_graph_if_kind_differs(h, flexible, nb);
   for (int it = 1; it <= maxit; ++it) {
     bool replayed = false;
     if (graphs && h->iter_graph) {
@@ -1612,34 +1704,48 @@ PcgResult pcg(bddc_handle_s* h, const double* g, double* x, double tol, int maxi
       g_launches.fetch_add(h->graph_kernels);
       replayed = true;
     } else {
-      pcg_body(h, x, flexible, st);   // the first iteration runs eagerly, then it is captured
-      if (graphs) capture_iteration(h, flexible);
+      pcg_body(h, x, flexible, st, nb);   // the first iteration runs eagerly, then it is captured
+      if (graphs) capture_iteration(h, flexible, nb);
     }
-    ck(cudaMemcpyAsync(h->h_scal, S, sizeof(double) * 16, cudaMemcpyDeviceToHost, st), "d2h");
+    ck(cudaMemcpyAsync(h->h_scal, S, sizeof(double) * 16 * nb, cudaMemcpyDeviceToHost, st), "d2h");
     ck(cudaStreamSynchronize(st), "sync");
     if (replayed && !h->graph_prof.empty()) accumulate_graph_profile(h);
-    res.iterations = it;
-    res.alpha.push_back(h->h_scal[2]);
-    res.beta.push_back(h->h_scal[3]);
-    double rel = std::sqrt(h->h_scal[5] / gg);
-    if (!std::isfinite(rel)) fail(BDDC_ERR_NAN, "NaN in the Krylov recurrence");
-    res.rel = rel;
-    if (rel <= tol) {
-      schur_apply(h, x, h->vq, st);                                 // true residual g - S x
-      ck(cudaMemcpyAsync(h->vrold, g, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
-      launch_axpy_loc(h->vrold, h->vq, -1.0, n, st);
-      launch_dot(h->vrold, h->vrold, n, h->partial, kDotBlocks, S + 9, st);
-      ck(cudaMemcpyAsync(h->h_scal + 9, S + 9, sizeof(double), cudaMemcpyDeviceToHost, st), "d2h");
-      ck(cudaStreamSynchronize(st), "sync");
-      const double rel_true = std::sqrt(h->h_scal[9] / gg);
-      if (rel_true <= tol || checked) {
-        res.rel = rel_true;
-        res.converged = rel_true <= tol;
-        return res;
-      }
-      checked = true;
-      pcg_start(h, g, x, false, st);   // restart from the current iterate with the true residual
+    std::vector<int> check;
+    for (int k = 0; k < nb; ++k) {
+      if (frozen[k]) continue;
+      const double* sk = h->h_scal + 16 * k;
+      res[k].iterations = it;
+      res[k].alpha.push_back(sk[2]);
+      res[k].beta.push_back(sk[3]);
+      const double rel = std::sqrt(sk[5] / gg[k]);
+      if (!std::isfinite(rel)) fail(BDDC_ERR_NAN, "NaN in the Krylov recurrence");
+      res[k].rel = rel;
+      if (rel <= tol[k]) check.push_back(k);
     }
+    if (check.empty()) continue;
+    schur_apply(h, x, h->vq, st, nb);                                 // true residuals g - S x
+    ck(cudaMemcpyAsync(h->vrold, g, sizeof(double) * n * nb, cudaMemcpyDeviceToDevice, st), "copy");
+    launch_axpy_loc(h->vrold, h->vq, -1.0, n * nb, st);
+    launch_dot(h->vrold, h->vrold, n, h->partial, kDotBlocks, S + 9, st, nb);
+    ck(cudaMemcpyAsync(h->h_scal, S, sizeof(double) * 16 * nb, cudaMemcpyDeviceToHost, st), "d2h");
+    ck(cudaStreamSynchronize(st), "sync");
+    bool restart = false;
+    for (int k : check) {
+      const double rel_true = std::sqrt(h->h_scal[16 * k + 9] / gg[k]);
+      if (rel_true <= tol[k] || checked[k]) {
+        res[k].rel = rel_true;
+        res[k].converged = rel_true <= tol[k];
+        frozen[k] = 1;
+        --active;
+      } else {
+        checked[k] = 1;
+        restart = true;
+      }
+    }
+    for (int k = 0; k < nb; ++k)   // the readback overwrote the host copies of the flags
+      if (frozen[k]) freeze_column(h, k);
+    if (active == 0) return res;
+    if (restart) pcg_start(h, g, x, false, st, nb);   // restart from the iterates with the true residuals
   }
   return res;
 }
@@ -1673,7 +1779,7 @@ PcgResult bicgstab(bddc_handle_s* h, const double* g, double* x, double tol, int
     return res;
   }
   const bool graphs = h->opts.use_graph && x == h->vx;
-  drop_graph_if_kind_differs(h, 2);
+  drop_graph_if_kind_differs(h, 2, 1);
   for (int it = 1; it <= maxit; ++it) {
     bool replayed = false;
     if (graphs && h->iter_graph) {
@@ -1682,7 +1788,7 @@ PcgResult bicgstab(bddc_handle_s* h, const double* g, double* x, double tol, int
       replayed = true;
     } else {
       bicg_body(h, x, st);
-      if (graphs) capture_iteration(h, 2);
+      if (graphs) capture_iteration(h, 2, 1);
     }
     ck(cudaMemcpyAsync(h->h_scal, S, sizeof(double) * 16, cudaMemcpyDeviceToHost, st), "d2h");
     ck(cudaStreamSynchronize(st), "sync");
@@ -1867,70 +1973,105 @@ PcgResult fgmres(bddc_handle_s* h, const double* g, double* x, double tol, int m
 }
 
 // Mixed-precision iterative refinement around PCG (the outer iteration that restores FP64
-// accuracy): x += S~^{-1} r with r = g - S x, where S is the FP64 Schur operator (interior solves
-// refined to FP64 accuracy) and S~ the same operator with h->inner_steps interior-solve steps
-// (0: products with the stored interface factor, no interior solve; k >= 1: k interior-solve
-// steps).  Each inner PCG reduces its residual by eta (never below what the outer tolerance
-// needs), starting from opts.inner_tol and adapted to the observed outer reduction within the
-// solve (so repeated solves are bitwise identical); an outer step that fails to halve the
-// residual switches the inner operator to the FP64 one.
+// accuracy), for a block of nb right-hand sides: x += S~^{-1} r with r = g - S x, where S is the
+// FP64 Schur operator (interior solves refined to FP64 accuracy) and S~ the same operator with
+// h->inner_steps interior-solve steps (0: products with the stored interface factor, no interior
+// solve; k >= 1: k interior-solve steps).  Each inner PCG reduces a column's residual by eta (never
+// below what the outer tolerance needs), starting from opts.inner_tol and adapted per column to its
+// observed outer reduction within the solve (so repeated solves are bitwise identical); an outer
+// step that fails to halve some column's residual switches the inner operator to the FP64 one.
+// Columns that meet the tolerance get a zero outer residual, so the inner PCG leaves them alone.
 // The solution is left in h->vs; h->vt holds the outer residual.
-PcgResult pcg_refined(bddc_handle_s* h, const double* g, double tol, int maxit) {
+std::vector<PcgResult> pcg_refined(bddc_handle_s* h, const double* g, double tol, int maxit, int nb) {
   constexpr int kMaxOuter = 40;
   cudaStream_t st = h->st;
   const int64_t n = h->lv[0].d.n_iface;
   double* xo = h->vs;
   double* ro = h->vt;
-  PcgResult res;
-  ck(cudaMemsetAsync(xo, 0, sizeof(double) * std::max<int64_t>(n, 1), st), "memset");
+  std::vector<PcgResult> res(nb);
+  ck(cudaMemsetAsync(xo, 0, sizeof(double) * std::max<int64_t>(n, 1) * nb, st), "memset");
   if (n == 0) {
-    res.converged = true;
+    for (auto& r : res) r.converged = true;
     return res;
   }
-  ck(cudaMemcpyAsync(ro, g, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
-  const double gnorm = std::sqrt(dot_host(h, g, g, n));
-  if (!std::isfinite(gnorm)) fail(BDDC_ERR_NAN, "NaN in the condensed right-hand side");
-  res.gnorm = gnorm;
-  if (gnorm == 0.0) {
-    res.converged = true;
-    return res;
+  auto norms = [&](const double* v) {   // ||v_k|| of every column
+    launch_dot(v, v, n, h->partial, kDotBlocks, h->scal, st, nb, 16);
+    ck(cudaMemcpyAsync(h->h_scal, h->scal, sizeof(double) * 16 * nb, cudaMemcpyDeviceToHost, st), "d2h");
+    ck(cudaStreamSynchronize(st), "sync");
+    std::vector<double> out(nb);
+    for (int k = 0; k < nb; ++k) out[k] = std::sqrt(h->h_scal[16 * k]);
+    return out;
+  };
+  ck(cudaMemcpyAsync(ro, g, sizeof(double) * n * nb, cudaMemcpyDeviceToDevice, st), "copy");
+  const std::vector<double> gnorm = norms(g);
+  std::vector<char> done(nb, 0);
+  int left = nb;
+  for (int k = 0; k < nb; ++k) {
+    if (!std::isfinite(gnorm[k])) fail(BDDC_ERR_NAN, "NaN in the condensed right-hand side");
+    res[k].gnorm = gnorm[k];
+    if (gnorm[k] == 0.0) {
+      res[k].converged = true;
+      done[k] = 1;
+      --left;
+    }
   }
-  double rnorm = gnorm;
+  std::vector<double> rnorm = gnorm, eta(nb, h->opts.inner_tol > 0.0 ? std::min(h->opts.inner_tol, 0.5) : 1e-2),
+                      tin(nb, 1.0);
   int inner = h->inner_steps;
-  double eta = h->opts.inner_tol > 0.0 ? std::min(h->opts.inner_tol, 0.5) : 1e-2;
-  for (int outer = 0; outer < kMaxOuter && res.iterations < maxit; ++outer) {
-    const double tin = std::max(eta, 0.5 * tol * gnorm / rnorm);
+  int its = 0;
+  for (int outer = 0; outer < kMaxOuter && its < maxit && left > 0; ++outer) {
+    for (int k = 0; k < nb; ++k) {
+      if (done[k]) {
+        ck(cudaMemsetAsync(ro + (int64_t)k * n, 0, sizeof(double) * n, st), "memset");
+        tin[k] = 1.0;
+      } else {
+        tin[k] = std::max(eta[k], 0.5 * tol * gnorm[k] / rnorm[k]);
+      }
+    }
     h->cur_steps = inner;
-    PcgResult in = pcg(h, ro, h->vx, tin, maxit - res.iterations);
+    std::vector<PcgResult> in = pcg(h, ro, h->vx, tin, maxit - its, nb);
     h->cur_steps = h->refine_steps;
-    res.iterations += in.iterations;
-    res.outer = outer + 1;
-    if (outer == 0) {
-      res.alpha = in.alpha;
-      res.beta = in.beta;
+    int most = 0;
+    for (int k = 0; k < nb; ++k) {
+      if (done[k]) continue;
+      res[k].iterations += in[k].iterations;
+      res[k].outer = outer + 1;
+      most = std::max(most, in[k].iterations);
+      if (outer == 0) {
+        res[k].alpha = in[k].alpha;
+        res[k].beta = in[k].beta;
+      }
     }
-    launch_axpy_loc(xo, h->vx, 1.0, n, st);
-    schur_apply(h, xo, h->vq, st);                        // r = g - S x with the FP64 operator
-    ck(cudaMemcpyAsync(ro, g, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
-    launch_axpy_loc(ro, h->vq, -1.0, n, st);
-    const double rn = std::sqrt(dot_host(h, ro, ro, n));
-    if (!std::isfinite(rn)) fail(BDDC_ERR_NAN, "NaN in the outer refinement");
-    res.rel = rn / gnorm;
-    if (res.rel <= tol) {
-      res.converged = true;
-      return res;
+    its += most;
+    launch_axpy_loc(xo, h->vx, 1.0, n * nb, st);
+    schur_apply(h, xo, h->vq, st, nb);                        // r = g - S x with the FP64 operator
+    ck(cudaMemcpyAsync(ro, g, sizeof(double) * n * nb, cudaMemcpyDeviceToDevice, st), "copy");
+    launch_axpy_loc(ro, h->vq, -1.0, n * nb, st);
+    const std::vector<double> rn = norms(ro);
+    bool stagnated = false;
+    for (int k = 0; k < nb; ++k) {
+      if (done[k]) continue;
+      if (!std::isfinite(rn[k])) fail(BDDC_ERR_NAN, "NaN in the outer refinement");
+      res[k].rel = rn[k] / gnorm[k];
+      if (res[k].rel <= tol) {
+        res[k].converged = true;
+        done[k] = 1;
+        --left;
+        continue;
+      }
+      // the outer reduction shows how accurate the inner operator is: ask the next inner solve for
+      // about that much (solving further is lost at the restart), unless the inner solve itself
+      // was the limit
+      const double ratio = rn[k] / rnorm[k];
+      if (ratio > 0.5)
+        stagnated = true;                                   // stagnation: inner operator = FP64 one
+      else if (ratio > 2.0 * tin[k])
+        eta[k] = std::min(0.1, std::max(1e-4, ratio));
+      else
+        eta[k] = std::max(1e-4, 0.5 * eta[k]);
+      rnorm[k] = rn[k];
     }
-    // the outer reduction shows how accurate the inner operator is: ask the next inner solve for
-    // about that much (solving further is lost at the restart), unless the inner solve itself
-    // was the limit
-    const double ratio = rn / rnorm;
-    if (ratio > 0.5)
-      inner = h->refine_steps;                          // stagnation: inner operator = FP64 one
-    else if (ratio > 2.0 * tin)
-      eta = std::min(0.1, std::max(1e-4, ratio));
-    else
-      eta = std::max(1e-4, 0.5 * eta);
-    rnorm = rn;
+    if (stagnated) inner = h->refine_steps;
   }
   return res;
 }
@@ -1949,32 +2090,45 @@ int solve_impl(bddc_handle_s* h, const double* rhs, double* x, int nrhs, double 
   double worst = 0.0;
   PcgResult first;
   const int kind = krylov_kind(h);
-  for (int k = 0; k < nrhs; ++k) {
-    const double* f = rhs + (int64_t)k * h->n_free;
-    double* u = x + (int64_t)k * h->n_free;
+  // PCG solves the right-hand sides in blocks of up to kMaxBlock (one pass over the factors per
+  // block and iteration); BiCGstab and flexible GMRES one at a time
+  const bool blocked = kind == BDDC_KRYLOV_PCG;
+  if (blocked && nrhs > 1) ensure_block(h, std::min(nrhs, kMaxBlock));
+  const int bmax = blocked ? h->blk : 1;
+  for (int k0 = 0; k0 < nrhs;) {
+    const int nb = std::min(bmax, nrhs - k0);
+    const double* f = rhs + (int64_t)k0 * h->n_free;
+    double* u = x + (int64_t)k0 * h->n_free;
     if (with_lift && h->has_lift) {   // f - K_fd u_d
-      ck(cudaMemcpyAsync(h->fcol, f, sizeof(double) * h->n_free, cudaMemcpyDeviceToDevice, st), "copy");
-      launch_axpy_loc(h->fcol, h->d_lift, 1.0, h->n_free, st);
+      ck(cudaMemcpyAsync(h->fcol, f, sizeof(double) * h->n_free * nb, cudaMemcpyDeviceToDevice, st), "copy");
+      for (int k = 0; k < nb; ++k) launch_axpy_loc(h->fcol + (int64_t)k * h->n_free, h->d_lift, 1.0, h->n_free, st);
       f = h->fcol;
     }
-    const bool refined = kind == BDDC_KRYLOV_PCG && h->use_outer;
-    PcgResult r;
+    const bool refined = blocked && h->use_outer;
+    std::vector<PcgResult> r;
     try {
-      condensed_rhs(h, f, h->vg, st);
-      r = kind == BDDC_KRYLOV_BICGSTAB ? bicgstab(h, h->vg, h->vx, tol, h->opts.maxit)
-          : kind == BDDC_KRYLOV_FGMRES ? fgmres(h, h->vg, h->vx, tol, h->opts.maxit)
-          : refined                    ? pcg_refined(h, h->vg, tol, h->opts.maxit)
-                                       : pcg(h, h->vg, h->vx, tol, h->opts.maxit);
+      condensed_rhs(h, f, h->vg, st, nb);
+      if (kind == BDDC_KRYLOV_BICGSTAB)
+        r.push_back(bicgstab(h, h->vg, h->vx, tol, h->opts.maxit));
+      else if (kind == BDDC_KRYLOV_FGMRES)
+        r.push_back(fgmres(h, h->vg, h->vx, tol, h->opts.maxit));
+      else if (refined)
+        r = pcg_refined(h, h->vg, tol, h->opts.maxit, nb);
+      else
+        r = pcg(h, h->vg, h->vx, std::vector<double>(nb, tol), h->opts.maxit, nb);
     } catch (const Fail& e) {
       if (e.code != BDDC_ERR_TIMEOUT) throw_if_timeout(h);
       throw;
     }
-    recover(h, f, refined ? h->vs : h->vx, u, st);
-    maxits = std::max(maxits, r.iterations);
-    max_outer = std::max(max_outer, r.outer);
-    all_conv = all_conv && r.converged;
-    worst = std::max(worst, r.rel);
-    if (k == 0) first = r;
+    recover(h, f, refined ? h->vs : h->vx, u, st, nb);
+    for (int k = 0; k < nb; ++k) {
+      maxits = std::max(maxits, r[k].iterations);
+      max_outer = std::max(max_outer, r[k].outer);
+      all_conv = all_conv && r[k].converged;
+      worst = std::max(worst, r[k].rel);
+    }
+    if (k0 == 0) first = r[0];
+    k0 += nb;
   }
   check_status(h, 0);
   h->stats.iterations = maxits;
@@ -2149,7 +2303,9 @@ int bddc_apply_precond(bddc_handle h, const double* r, double* z, int nrhs) {
   return guarded([&]() {
     if (!h || !h->factored || !r || !z || nrhs < 1) fail(BDDC_ERR_INVALID, "bad arguments");
     const int64_t n = h->lv[0].d.n_iface;
-    for (int k = 0; k < nrhs; ++k) precond(h, r + k * n, z + k * n, h->st);
+    if (nrhs > 1) ensure_block(h, std::min(nrhs, kMaxBlock));
+    for (int k0 = 0; k0 < nrhs; k0 += h->blk)
+      precond(h, r + k0 * n, z + k0 * n, h->st, std::min(h->blk, nrhs - k0));
     ck(cudaStreamSynchronize(h->st), "sync");
     return BDDC_OK;
   });
@@ -2159,7 +2315,9 @@ int bddc_apply_schur(bddc_handle h, const double* x, double* y, int nrhs) {
   return guarded([&]() {
     if (!h || !h->factored || !x || !y || nrhs < 1) fail(BDDC_ERR_INVALID, "bad arguments");
     const int64_t n = h->lv[0].d.n_iface;
-    for (int k = 0; k < nrhs; ++k) schur_apply(h, x + k * n, y + k * n, h->st);
+    if (nrhs > 1) ensure_block(h, std::min(nrhs, kMaxBlock));
+    for (int k0 = 0; k0 < nrhs; k0 += h->blk)
+      schur_apply(h, x + k0 * n, y + k0 * n, h->st, std::min(h->blk, nrhs - k0));
     ck(cudaStreamSynchronize(h->st), "sync");
     return BDDC_OK;
   });

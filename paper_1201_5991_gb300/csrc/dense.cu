@@ -505,6 +505,8 @@ __global__ void k_cc_yv(LevelDev L, const T* __restrict__ vec, const int32_t* __
   const int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (g >= total_rows) return;
+  vec += (int64_t)blockIdx.y * L.n_vec;   // column blockIdx.y of a block of right-hand sides
+  t += (int64_t)blockIdx.y * total_rows;
   const int s = crow_sub[g];
   const SubMeta m = L.meta[s];
   const int p = (int)(g - m.c_off);
@@ -522,6 +524,8 @@ __global__ void k_cc_mu(LevelDev L, const int32_t* __restrict__ crow_sub, int64_
   const int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (g >= total_rows) return;
+  t += (int64_t)blockIdx.y * total_rows;
+  mu += (int64_t)blockIdx.y * total_rows;
   const int s = crow_sub[g];
   const SubMeta m = L.meta[s];
   const int p = (int)(g - m.c_off);
@@ -533,11 +537,13 @@ __global__ void k_cc_mu(LevelDev L, const int32_t* __restrict__ crow_sub, int64_
 }
 
 template <typename T>
-__global__ void k_cc_update(LevelDev L, T* __restrict__ vec, const double* __restrict__ mu) {
+__global__ void k_cc_update(LevelDev L, T* __restrict__ vec, const double* __restrict__ mu, int64_t total_rows) {
   const int s = blockIdx.y;
   const SubMeta m = L.meta[s];
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= m.nGb * NB || m.nc == 0) return;
+  vec += (int64_t)blockIdx.z * L.n_vec;
+  mu += (int64_t)blockIdx.z * total_rows;
   T acc = (T)0;
   for (int p = 0; p < m.nc; ++p)
     acc += tile_ptr<T>(m, L.tiles, m.Bc + p / NB, m.nIb + c / NB)[(p % NB) * NB + (c % NB)] * (T)mu[m.c_off + p];
@@ -550,9 +556,11 @@ __global__ void k_cc_update(LevelDev L, T* __restrict__ vec, const double* __res
 // rows w, w+8, ... of the slice, lane l the coarse DOFs l, l+32, ... (coalesced reads of Psi's
 // rows); the eight warps' sums and then the slices' sums are added in a fixed order.
 template <typename T>
-__global__ void k_psi_t_part(LevelDev L, const T* __restrict__ vec, double* __restrict__ part) {
+__global__ void k_psi_t_part(LevelDev L, const T* __restrict__ vec, double* __restrict__ part, int64_t sum_nc) {
   const int s = blockIdx.y, z = blockIdx.x;
   const SubMeta m = L.meta[s];
+  vec += (int64_t)blockIdx.z * L.n_vec;
+  part += (int64_t)blockIdx.z * sum_nc * kPsiSlices;
   const int nc = m.nc;
   const int chunk = (m.nG + kPsiSlices - 1) / kPsiSlices;
   const int r0 = z * chunk, r1 = min(m.nG, r0 + chunk);
@@ -590,6 +598,8 @@ __global__ void k_psi_t_part(LevelDev L, const T* __restrict__ vec, double* __re
 __global__ void k_psi_t_final(const double* __restrict__ part, int64_t total, double* __restrict__ rc_sub) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= total) return;
+  part += (int64_t)blockIdx.y * total * kPsiSlices;
+  rc_sub += (int64_t)blockIdx.y * total;
   double t = 0.0;
 #pragma unroll
   for (int z = 0; z < kPsiSlices; ++z) t += part[g * kPsiSlices + z];
@@ -598,12 +608,14 @@ __global__ void k_psi_t_final(const double* __restrict__ part, int64_t total, do
 
 // v_G += Psi_G zc_sub
 template <typename T>
-__global__ void k_psi_apply_add(LevelDev L, const double* __restrict__ zc_sub, T* __restrict__ vec) {
+__global__ void k_psi_apply_add(LevelDev L, const double* __restrict__ zc_sub, int64_t sum_nc, T* __restrict__ vec) {
   const int s = blockIdx.y;
   const SubMeta m = L.meta[s];
   const int nc = m.nc;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= m.nG) return;
+  zc_sub += (int64_t)blockIdx.z * sum_nc;
+  vec += (int64_t)blockIdx.z * L.n_vec;
   const T* P = (const T*)L.psi + m.psi_off + (int64_t)c * nc;
   const double* z = zc_sub + m.c_off;
   T acc = (T)0;
@@ -655,37 +667,40 @@ void launch_psi(const LevelDev& L, int max_nGb, int max_nc, cudaStream_t st) {
   { note_launch(); k_trsm_back_psi<T><<<dim3((unsigned)((max_nc + 15) / 16), ns), 256, 0, st>>>(L); }
 }
 
+// The solve-phase launches below take nr right-hand sides: local vectors of n_vec, per-subdomain
+// coarse vectors of sum nc entries per column.
 template <typename T>
 void launch_constraint_corr(const LevelDev& L, T* vec, const int32_t* crow_sub, int64_t total_rows, double* t,
-                            double* mu, int max_nGb, cudaStream_t st) {
+                            double* mu, int max_nGb, cudaStream_t st, int nr) {
   if (total_rows <= 0) return;
   const unsigned g = (unsigned)((total_rows + 7) / 8);
-  { note_launch(); k_cc_yv<T><<<g, 256, 0, st>>>(L, vec, crow_sub, total_rows, t); }
-  { note_launch(); k_cc_mu<<<g, 256, 0, st>>>(L, crow_sub, total_rows, t, mu); }
-  { note_launch(); k_cc_update<T><<<dim3((unsigned)((max_nGb * NB + 255) / 256), (unsigned)L.n_sub), 256, 0, st>>>(L, vec, mu); }
+  { note_launch(); k_cc_yv<T><<<dim3(g, nr), 256, 0, st>>>(L, vec, crow_sub, total_rows, t); }
+  { note_launch(); k_cc_mu<<<dim3(g, nr), 256, 0, st>>>(L, crow_sub, total_rows, t, mu); }
+  { note_launch(); k_cc_update<T><<<dim3((unsigned)((max_nGb * NB + 255) / 256), (unsigned)L.n_sub, nr), 256, 0, st>>>(L, vec, mu, total_rows); }
 }
 
 template <typename T>
 void launch_psi_t_apply(const LevelDev& L, const T* vec, double* part, int64_t sum_nc, double* rc_sub,
-                        cudaStream_t st) {
+                        cudaStream_t st, int nr) {
   if (sum_nc <= 0) return;
-  { note_launch(); k_psi_t_part<T><<<dim3(kPsiSlices, (unsigned)L.n_sub), 256, 0, st>>>(L, vec, part); }
-  { note_launch(); k_psi_t_final<<<(unsigned)((sum_nc + 255) / 256), 256, 0, st>>>(part, sum_nc, rc_sub); }
+  { note_launch(); k_psi_t_part<T><<<dim3(kPsiSlices, (unsigned)L.n_sub, nr), 256, 0, st>>>(L, vec, part, sum_nc); }
+  { note_launch(); k_psi_t_final<<<dim3((unsigned)((sum_nc + 255) / 256), nr), 256, 0, st>>>(part, sum_nc, rc_sub); }
 }
 
 template <typename T>
-void launch_psi_apply_add(const LevelDev& L, const double* zc_sub, T* vec, int max_nG, cudaStream_t st) {
+void launch_psi_apply_add(const LevelDev& L, const double* zc_sub, int64_t sum_nc, T* vec, int max_nG,
+                          cudaStream_t st, int nr) {
   if (max_nG <= 0) return;
-  { note_launch(); k_psi_apply_add<T><<<dim3((unsigned)((max_nG + 255) / 256), (unsigned)L.n_sub), 256, 0, st>>>(L, zc_sub, vec); }
+  { note_launch(); k_psi_apply_add<T><<<dim3((unsigned)((max_nG + 255) / 256), (unsigned)L.n_sub, nr), 256, 0, st>>>(L, zc_sub, sum_nc, vec); }
 }
 
 #define INST(T)                                                                                 \
   template void launch_potrf_step<T>(const LevelDev&, int, int, int, int, cudaStream_t);         \
   template void launch_psi<T>(const LevelDev&, int, int, cudaStream_t);                          \
   template void launch_constraint_corr<T>(const LevelDev&, T*, const int32_t*, int64_t, double*, double*, int, \
-                                         cudaStream_t);                                                   \
-  template void launch_psi_t_apply<T>(const LevelDev&, const T*, double*, int64_t, double*, cudaStream_t); \
-  template void launch_psi_apply_add<T>(const LevelDev&, const double*, T*, int, cudaStream_t);
+                                         cudaStream_t, int);                                              \
+  template void launch_psi_t_apply<T>(const LevelDev&, const T*, double*, int64_t, double*, cudaStream_t, int); \
+  template void launch_psi_apply_add<T>(const LevelDev&, const double*, int64_t, T*, int, cudaStream_t, int);
 INST(float)
 INST(double)
 #undef INST

@@ -154,45 +154,53 @@ template <typename T>
 void launch_psi(const LevelDev& L, int max_nGb, int max_nc, cudaStream_t st);
 // sweep.cu: forward (backward = 0) or backward triangular sweep over part 0 (interior
 // block rows) or part 1 (interface block rows) of every subdomain; ctrl has n_ctrl ints.
+// Solve-phase launches take nr right-hand sides (default 1); a block of them stores its columns one
+// after another, each vector kind with its own length as the stride (local vectors n_vec,
+// interface vectors n_iface, level vectors n_dof, coarse vectors n_coarse, per-subdomain coarse
+// vectors sum nc).  The factor-streaming kernels read each factor tile once per group of columns.
 template <typename T>
 void launch_sweep(const LevelDev& L, T* vec, const int2* tasks, int ntasks, int part, int backward, int* ctrl,
-                  int n_ctrl, int grid_max, int deep, cudaStream_t st);
-// crow_sub: subdomain of every constraint row (flat over the level); t, mu: scratch [total_rows]
+                  int n_ctrl, int grid_max, int deep, cudaStream_t st, int nr = 1);
+// crow_sub: subdomain of every constraint row (flat over the level); t, mu: scratch [nr][total_rows]
 template <typename T>
 void launch_constraint_corr(const LevelDev& L, T* vec, const int32_t* crow_sub, int64_t total_rows, double* t,
-                            double* mu, int max_nGb, cudaStream_t st);
+                            double* mu, int max_nGb, cudaStream_t st, int nr = 1);
 template <typename T>
 void launch_psi_t_apply(const LevelDev& L, const T* vec, double* part, int64_t sum_nc, double* rc_sub,
-                        cudaStream_t st);
+                        cudaStream_t st, int nr = 1);
 template <typename T>
-void launch_psi_apply_add(const LevelDev& L, const double* zc_sub, T* vec, int max_nG, cudaStream_t st);
+void launch_psi_apply_add(const LevelDev& L, const double* zc_sub, int64_t sum_nc, T* vec, int max_nG,
+                          cudaStream_t st, int nr = 1);
 
 // ---------------------------------------------------------------- vectors (vector.cu)
 template <typename T>
-void launch_gather_iface(const LevelDev& L, const double* x, int weighted, T* loc, cudaStream_t st);
+void launch_gather_iface(const LevelDev& L, const double* x, int weighted, T* loc, cudaStream_t st, int nr = 1);
 template <typename T>
-void launch_scatter_iface(const LevelDev& L, const T* loc, int weighted, double* y, cudaStream_t st);
+void launch_scatter_iface(const LevelDev& L, const T* loc, int weighted, double* y, cudaStream_t st, int nr = 1);
 template <typename T>
-void launch_gather_glob(const LevelDev& L, const double* x, int part, T* loc, cudaStream_t st);
+void launch_gather_glob(const LevelDev& L, const double* x, int part, T* loc, cudaStream_t st, int nr = 1);
 template <typename T>
-void launch_scatter_interior(const LevelDev& L, const T* loc, double* y, cudaStream_t st);
+void launch_scatter_interior(const LevelDev& L, const T* loc, double* y, cudaStream_t st, int nr = 1);
 // rows: flat padded row indices (interior rows, interface rows or both, of every subdomain)
 void launch_spmv_rows(const LevelDev& L, const int64_t* rows, int64_t nrows, const double* x, double* y, double alpha,
-                      double beta, const int32_t* row_sub, cudaStream_t st);
+                      double beta, const int32_t* row_sub, cudaStream_t st, int nr = 1);
 template <typename Tin, typename Tout>
 void launch_convert(const Tin* in, Tout* out, int64_t n, cudaStream_t st);
 void launch_axpy_loc(double* y, const double* x, double a, int64_t n, cudaStream_t st);
 template <typename T>
 void launch_add_to_double(double* y, const T* x, int64_t n, cudaStream_t st);
-void launch_coarse_gather(const LevelDev& L, const double* rc_sub, double* rC, cudaStream_t st);
-void launch_coarse_scatter_n(const int32_t* sub_coarse, int64_t total, const double* zC, double* zc_sub,
-                             cudaStream_t st);
+void launch_coarse_gather(const LevelDev& L, const double* rc_sub, int64_t sum_nc, double* rC, cudaStream_t st,
+                          int nr = 1);
+void launch_coarse_scatter_n(const int32_t* sub_coarse, int64_t total, const double* zC, int64_t n_coarse,
+                             double* zc_sub, cudaStream_t st, int nr = 1);
+// nr dot products of the columns of a and b (length n each): out[k * ostride], partial [nr][nblk]
 void launch_dot(const double* a, const double* b, int64_t n, double* partial, int nblk, double* out,
-                cudaStream_t st);
+                cudaStream_t st, int nr = 1, int ostride = 16);
+// PCG of a block of right-hand sides: column k keeps its scalars at scal[16 k ..]
 void launch_pcg_update_x_r(double* x, double* r, const double* p, const double* q, const double* scal,
-                           int64_t n, cudaStream_t st);
-void launch_pcg_update_p(double* p, const double* z, const double* scal, int64_t n, cudaStream_t st);
-void launch_pcg_scalars(double* scal, int stage, int flexible, cudaStream_t st);
+                           int64_t n, cudaStream_t st, int nr = 1);
+void launch_pcg_update_p(double* p, const double* z, const double* scal, int64_t n, cudaStream_t st, int nr = 1);
+void launch_pcg_scalars(double* scal, int stage, int flexible, cudaStream_t st, int nr = 1);
 // conn: element -> nodes (ne / ndof per element); the full DOF of element slot a is
 // conn[a / ndof] * ndof + a % ndof
 void launch_grad_contract_slots(int64_t n_elems, int ne, const double* ke, const int32_t* slot_elem,
@@ -202,14 +210,17 @@ void launch_expand_free(const double* xf, const int64_t* free_of_full, int64_t n
                         int64_t n_free, double* xfull, cudaStream_t st);
 void launch_copy_segments(const double* src, const int64_t* src_off, double* dst, const int64_t* dst_off,
                           const int64_t* len, int64_t n, cudaStream_t st);
-void launch_iface_rhs(double* g, const double* f, const int64_t* idx, const double* t, int64_t n,
-                      cudaStream_t st);
-void launch_put_indexed(double* u, const int64_t* idx, const double* v, int64_t n, cudaStream_t st);
+// g = f[idx] - t per column (f columns of length fstride); u[idx] = v per column (u columns of ustride)
+void launch_iface_rhs(double* g, const double* f, int64_t fstride, const int64_t* idx, const double* t, int64_t n,
+                      cudaStream_t st, int nr = 1);
+void launch_put_indexed(double* u, int64_t ustride, const int64_t* idx, const double* v, int64_t n, cudaStream_t st,
+                        int nr = 1);
 // inner Schur operator from the stored factor (trmv.cu): y = L_GG S L_GG^T x over the
 // interface block rows of an FP32 level (y1 scratch), and y -= C^T R C x (FP64, local vectors)
-void launch_trmv_schur(const LevelDev& L, int max_nGb, const float* x, float* y1, float* y, cudaStream_t st);
+void launch_trmv_schur(const LevelDev& L, int max_nGb, const float* x, float* y1, float* y, cudaStream_t st,
+                       int nr = 1);
 void launch_sub_ctrc(const LevelDev& L, const int32_t* crow_sub, int64_t total_rows, const double* x, double* y,
-                     cudaStream_t st);
+                     cudaStream_t st, int nr = 1);
 // flexible GMRES (vector.cu): out[i] = V_i . w (i < nv, partial holds nv * nblk doubles);
 // w += alpha sum_i c_i V_i; dst = src / sqrt(*nrm2)
 void launch_multidot(const double* V, int64_t ldv, int nv, const double* w, int64_t n, double* partial, int nblk,

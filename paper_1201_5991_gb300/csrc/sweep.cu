@@ -83,18 +83,21 @@ struct Vec2<double> {
 };
 
 // One task: (subdomain, block row).  Forward consumes tiles (i, B0..i-1) then D_i^{-1};
-// backward consumes tiles (B1-1..i+1, i) then D_i^{-1}.
-template <typename T, int S, bool BWD>
+// backward consumes tiles (B1-1..i+1, i) then D_i^{-1}.  NR right-hand sides are solved together
+// (column r at vec + r * vstride): every factor tile is streamed from HBM once per task and
+// applied to all of them from shared memory.
+template <typename T, int S, bool BWD, int NR>
 __global__ void __launch_bounds__(kThreads, 2)
-    k_sweep(LevelDev L, T* __restrict__ vec, const int2* __restrict__ tasks, int ntasks, int part,
+    k_sweep(LevelDev L, T* __restrict__ vec, int64_t vstride, const int2* __restrict__ tasks, int ntasks, int part,
             int* __restrict__ ctrl) {
   using V2 = typename Vec2<T>::type;
+  constexpr int YS = NR == 1 ? kYSlots : (NR == 2 ? 8 : 4);   // solution blocks staged at a time
   extern __shared__ __align__(128) unsigned char smem_raw[];
   T* stage = (T*)smem_raw;                       // S tiles of NB*NB
   __shared__ __align__(8) uint64_t full[S];
-  __shared__ __align__(16) T ybuf[kYSlots][NB];
-  __shared__ T red[kThreads / 32][NB];
-  __shared__ __align__(16) T rhs[NB];
+  __shared__ __align__(16) T ybuf[YS][NR][NB];
+  __shared__ T red[kThreads / 32][NR][NB];
+  __shared__ __align__(16) T rhs[NR][NB];
   __shared__ T s_sg[NB];                         // pivot signs of the task's block row (indefinite)
   __shared__ int s_task, s_ready;
   int* counter = ctrl;
@@ -139,14 +142,18 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
       issued += pre;
     }
-    T acc[8];
+    T acc[8][NR];        // forward: rows warp + 8 r, this lane's two columns, every right-hand side
+    T accc[NR][2];       // backward: this lane's two columns, summed over the warp's rows
 #pragma unroll
-    for (int r = 0; r < 8; ++r) acc[r] = (T)0;
-    T accc0 = (T)0, accc1 = (T)0;
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int q = 0; q < NR; ++q) acc[r][q] = (T)0;
+#pragma unroll
+    for (int q = 0; q < NR; ++q) accc[q][0] = accc[q][1] = (T)0;
     int staged_end = 0;   // tiles [staged_begin, staged_end) have their solution block in ybuf
     for (int k = 0; k < ntile; ++k) {
       if (k < nL && k >= staged_end) {
-        // wait until the next solution blocks are published, then stage up to kYSlots of them
+        // wait until the next solution blocks are published, then stage up to YS of them
         if (warp == 0) {
           int ready = 0;
           long long spins = 0;
@@ -172,17 +179,18 @@ __global__ void __launch_bounds__(kThreads, 2)
             }
             __nanosleep(64);
           }
-          if (lane == 0) s_ready = ready < kYSlots ? ready : kYSlots;
+          if (lane == 0) s_ready = ready < YS ? ready : YS;
         }
         __syncthreads();
         const int cnt = s_ready;
-        for (int e = tid; e < cnt * NB; e += kThreads) {
-          const int kk = k + e / NB;
+        for (int e = tid; e < cnt * NR * NB; e += kThreads) {
+          const int kk = k + e / (NR * NB);
+          const int q = (e / NB) % NR, c = e % NB;
           const int j = BWD ? (B1 - 1 - kk) : (B0 + kk);
-          T yj = __ldcg(v + j * NB + e % NB);
+          T yj = __ldcg(v + q * vstride + j * NB + c);
           if (!BWD && L.indefinite)   // solved rows hold S_j y_j: the update needs y_j
-            yj *= ((const T*)L.sgn)[m.vec_off + (int64_t)j * NB + e % NB];
-          ybuf[kk % kYSlots][e % NB] = yj;
+            yj *= ((const T*)L.sgn)[m.vec_off + (int64_t)j * NB + c];
+          ybuf[kk % YS][q][c] = yj;
         }
         __syncthreads();
         staged_end = k + cnt;
@@ -201,76 +209,102 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
       const T* tl = stage + slot * NB2;
       if (k < nL) {
-        const T* y = ybuf[k % kYSlots];
+        const int ys = k % YS;
         if (!BWD) {
-          const V2 yv = *(const V2*)(y + 2 * lane);
+          V2 a[8];
 #pragma unroll
-          for (int r = 0; r < 8; ++r) {
-            const V2 a = *(const V2*)(tl + (warp + 8 * r) * NB + 2 * lane);
-            acc[r] += a.x * yv.x + a.y * yv.y;
+          for (int r = 0; r < 8; ++r) a[r] = *(const V2*)(tl + (warp + 8 * r) * NB + 2 * lane);
+#pragma unroll
+          for (int q = 0; q < NR; ++q) {
+            const V2 yv = *(const V2*)(&ybuf[ys][q][2 * lane]);
+#pragma unroll
+            for (int r = 0; r < 8; ++r) acc[r][q] += a[r].x * yv.x + a[r].y * yv.y;
           }
         } else {
 #pragma unroll
           for (int r = 0; r < 8; ++r) {
             const int row = warp + 8 * r;
             const V2 a = *(const V2*)(tl + row * NB + 2 * lane);
-            const T x = y[row];
-            accc0 += a.x * x;
-            accc1 += a.y * x;
+#pragma unroll
+            for (int q = 0; q < NR; ++q) {
+              const T x = ybuf[ys][q][row];
+              accc[q][0] += a.x * x;
+              accc[q][1] += a.y * x;
+            }
           }
         }
       } else {
         // diagonal block: right-hand side, then D_i^{-1} (forward) or D_i^{-T} (backward)
         if (!BWD) {
 #pragma unroll
-          for (int r = 0; r < 8; ++r) {
-            T a = acc[r];
+          for (int q = 0; q < NR; ++q)
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-            if (lane == 0) rhs[warp + 8 * r] = __ldcg(v + i * NB + warp + 8 * r) - a;
-          }
+            for (int r = 0; r < 8; ++r) {
+              T a = acc[r][q];
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+              if (lane == 0) rhs[q][warp + 8 * r] = __ldcg(v + q * vstride + i * NB + warp + 8 * r) - a;
+            }
           __syncthreads();
-          const V2 rv = *(const V2*)(rhs + 2 * lane);
           const bool signed_rows = L.indefinite != 0;   // forward output is S L^{-1} b
+          V2 a[8];
 #pragma unroll
-          for (int r = 0; r < 8; ++r) {
-            const V2 a = *(const V2*)(tl + (warp + 8 * r) * NB + 2 * lane);
-            T yv = a.x * rv.x + a.y * rv.y;
+          for (int r = 0; r < 8; ++r) a[r] = *(const V2*)(tl + (warp + 8 * r) * NB + 2 * lane);
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) yv += __shfl_xor_sync(0xffffffffu, yv, o);
-            if (lane == 0) v[i * NB + warp + 8 * r] = signed_rows ? yv * s_sg[warp + 8 * r] : yv;
+          for (int q = 0; q < NR; ++q) {
+            const V2 rv = *(const V2*)(&rhs[q][2 * lane]);
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+              T yv = a[r].x * rv.x + a[r].y * rv.y;
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1) yv += __shfl_xor_sync(0xffffffffu, yv, o);
+              if (lane == 0) v[q * vstride + i * NB + warp + 8 * r] = signed_rows ? yv * s_sg[warp + 8 * r] : yv;
+            }
           }
           if (lane == 0) __threadfence();
         } else {
-          red[warp][2 * lane] = accc0;
-          red[warp][2 * lane + 1] = accc1;
-          __syncthreads();
-          if (tid < NB) {
-            T a = (T)0;
 #pragma unroll
-            for (int w = 0; w < kThreads / 32; ++w) a += red[w][tid];
-            rhs[tid] = __ldcg(v + i * NB + tid) - a;
+          for (int q = 0; q < NR; ++q) {
+            red[warp][q][2 * lane] = accc[q][0];
+            red[warp][q][2 * lane + 1] = accc[q][1];
           }
           __syncthreads();
-          T p0 = (T)0, p1 = (T)0;
+          for (int e = tid; e < NR * NB; e += kThreads) {
+            const int q = e / NB, c = e % NB;
+            T a = (T)0;
+#pragma unroll
+            for (int w = 0; w < kThreads / 32; ++w) a += red[w][q][c];
+            rhs[q][c] = __ldcg(v + q * vstride + i * NB + c) - a;
+          }
+          __syncthreads();
+          T p[NR][2];
+#pragma unroll
+          for (int q = 0; q < NR; ++q) p[q][0] = p[q][1] = (T)0;
 #pragma unroll
           for (int r = 0; r < 8; ++r) {
             const int row = warp + 8 * r;
             const V2 a = *(const V2*)(tl + row * NB + 2 * lane);
-            p0 += a.x * rhs[row];
-            p1 += a.y * rhs[row];
+#pragma unroll
+            for (int q = 0; q < NR; ++q) {
+              p[q][0] += a.x * rhs[q][row];
+              p[q][1] += a.y * rhs[q][row];
+            }
           }
           __syncthreads();
-          red[warp][2 * lane] = p0;
-          red[warp][2 * lane + 1] = p1;
+#pragma unroll
+          for (int q = 0; q < NR; ++q) {
+            red[warp][q][2 * lane] = p[q][0];
+            red[warp][q][2 * lane + 1] = p[q][1];
+          }
           __syncthreads();
-          if (tid < NB) {
+          for (int e = tid; e < NR * NB; e += kThreads) {
+            const int q = e / NB, c = e % NB;
             T a = (T)0;
 #pragma unroll
-            for (int w = 0; w < kThreads / 32; ++w) a += red[w][tid];
-            v[i * NB + tid] = a;
-            __threadfence();
+            for (int w = 0; w < kThreads / 32; ++w) a += red[w][q][c];
+            v[q * vstride + i * NB + c] = a;
           }
+          __threadfence();
         }
       }
       __syncthreads();   // every thread is done with this stage
@@ -282,7 +316,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         ++issued;
       }
     }
-    // publish the solution block of row i
+    // publish the solution block of row i (every right-hand side)
     if (tid == 0) {
       __threadfence();
       st_release(flags + fbase + i, 1);
@@ -303,46 +337,69 @@ __global__ void __launch_bounds__(kThreads, 2)
 
 // Task lists and control words live in the level (see capi.cpp); this entry launches one
 // sweep.  ctrl = [counter, flags...] must be zeroed before the launch (memset in the stream).
-template <typename T, int S>
+template <typename T, int S, int NR>
 void launch_sweep_s(const LevelDev& L, T* vec, const int2* tasks, int ntasks, int part, int backward, int* ctrl,
                     int grid, cudaStream_t st) {
   const size_t dyn = (size_t)S * NB2 * sizeof(T);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_sweep<T, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-    cudaFuncSetAttribute(k_sweep<T, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    cudaFuncSetAttribute(k_sweep<T, S, false, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    cudaFuncSetAttribute(k_sweep<T, S, true, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     attr = true;
   }
   note_launch();
   if (backward)
-    k_sweep<T, S, true><<<grid, kThreads, dyn, st>>>(L, vec, tasks, ntasks, part, ctrl);
+    k_sweep<T, S, true, NR><<<grid, kThreads, dyn, st>>>(L, vec, L.n_vec, tasks, ntasks, part, ctrl);
   else
-    k_sweep<T, S, false><<<grid, kThreads, dyn, st>>>(L, vec, tasks, ntasks, part, ctrl);
+    k_sweep<T, S, false, NR><<<grid, kThreads, dyn, st>>>(L, vec, L.n_vec, tasks, ntasks, part, ctrl);
 }
 
-// deep: the longer tile ring (FP32: 6 stages, FP64: 3); shallow: FP32 4, FP64 2
+template <typename T, int S>
+void launch_sweep_nr(const LevelDev& L, T* vec, const int2* tasks, int ntasks, int part, int backward, int* ctrl,
+                     int n_ctrl, int grid, int nr, cudaStream_t st) {
+  // right-hand sides in groups of up to 8 (FP32) / 4 (FP64), each group one launch over the factor
+  constexpr int kMaxNR = sizeof(T) == 4 ? 8 : 4;
+  for (int r0 = 0; r0 < nr;) {
+    const int left = nr - r0;
+    const int g = left >= kMaxNR ? kMaxNR : left >= 4 ? 4 : left >= 2 ? 2 : 1;
+    if (r0 > 0) cudaMemsetAsync(ctrl, 0, sizeof(int) * (size_t)n_ctrl, st);
+    T* v = vec + (int64_t)r0 * L.n_vec;
+    if (g == 8)
+      launch_sweep_s<T, S, (sizeof(T) == 4 ? 8 : 4)>(L, v, tasks, ntasks, part, backward, ctrl, grid, st);
+    else if (g == 4)
+      launch_sweep_s<T, S, 4>(L, v, tasks, ntasks, part, backward, ctrl, grid, st);
+    else if (g == 2)
+      launch_sweep_s<T, S, 2>(L, v, tasks, ntasks, part, backward, ctrl, grid, st);
+    else
+      launch_sweep_s<T, S, 1>(L, v, tasks, ntasks, part, backward, ctrl, grid, st);
+    r0 += g;
+  }
+}
+
+// deep: the longer tile ring (FP32: 6 stages, FP64: 3); shallow: FP32 4, FP64 2.  nr columns of
+// length n_vec at vec.
 template <typename T>
 void launch_sweep(const LevelDev& L, T* vec, const int2* tasks, int ntasks, int part, int backward, int* ctrl,
-                  int n_ctrl, int grid_max, int deep, cudaStream_t st) {
-  if (ntasks <= 0) return;
+                  int n_ctrl, int grid_max, int deep, cudaStream_t st, int nr) {
+  if (ntasks <= 0 || nr <= 0) return;
   cudaMemsetAsync(ctrl, 0, sizeof(int) * (size_t)n_ctrl, st);
   const int grid = ntasks < grid_max ? ntasks : grid_max;
   if (sizeof(T) == 4) {
     if (deep)
-      launch_sweep_s<T, 6>(L, vec, tasks, ntasks, part, backward, ctrl, grid, st);
+      launch_sweep_nr<T, 6>(L, vec, tasks, ntasks, part, backward, ctrl, n_ctrl, grid, nr, st);
     else
-      launch_sweep_s<T, 4>(L, vec, tasks, ntasks, part, backward, ctrl, grid, st);
+      launch_sweep_nr<T, 4>(L, vec, tasks, ntasks, part, backward, ctrl, n_ctrl, grid, nr, st);
   } else {
     if (deep)
-      launch_sweep_s<T, 3>(L, vec, tasks, ntasks, part, backward, ctrl, grid, st);
+      launch_sweep_nr<T, 3>(L, vec, tasks, ntasks, part, backward, ctrl, n_ctrl, grid, nr, st);
     else
-      launch_sweep_s<T, 2>(L, vec, tasks, ntasks, part, backward, ctrl, grid, st);
+      launch_sweep_nr<T, 2>(L, vec, tasks, ntasks, part, backward, ctrl, n_ctrl, grid, nr, st);
   }
 }
 
 template void launch_sweep<float>(const LevelDev&, float*, const int2*, int, int, int, int*, int, int, int,
-                                  cudaStream_t);
+                                  cudaStream_t, int);
 template void launch_sweep<double>(const LevelDev&, double*, const int2*, int, int, int, int*, int, int, int,
-                                   cudaStream_t);
+                                   cudaStream_t, int);
 
 }  // namespace bddc

@@ -11,10 +11,15 @@ namespace bddc {
 
 namespace {
 
+// Several right-hand sides: blockIdx.y selects the column; every vector of a block stores its
+// columns one after another with its own length as the stride (local vectors n_vec, interface
+// vectors n_iface, level vectors n_dof, coarse vectors n_coarse, per-subdomain coarse vectors sum nc).
 template <typename T>
 __global__ void k_gather_iface(LevelDev L, const double* __restrict__ x, int weighted, T* __restrict__ loc) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= L.n_vec) return;
+  x += (int64_t)blockIdx.y * L.n_iface;
+  loc += (int64_t)blockIdx.y * L.n_vec;
   const int32_t g = L.loc2iface[p];
   double v = 0.0;
   if (g >= 0) v = weighted ? L.w[p] * x[g] : x[g];
@@ -25,6 +30,8 @@ template <typename T>
 __global__ void k_scatter_iface(LevelDev L, const T* __restrict__ loc, int weighted, double* __restrict__ y) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= L.n_iface) return;
+  loc += (int64_t)blockIdx.y * L.n_vec;
+  y += (int64_t)blockIdx.y * L.n_iface;
   double s = 0.0;
   for (int64_t o = L.iface_ptr[g]; o < L.iface_ptr[g + 1]; ++o) {
     const int64_t p = L.iface_occ[o];
@@ -38,6 +45,8 @@ template <typename T>
 __global__ void k_gather_glob(LevelDev L, const double* __restrict__ x, int part, T* __restrict__ loc) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= L.n_vec) return;
+  x += (int64_t)blockIdx.y * L.n_dof;
+  loc += (int64_t)blockIdx.y * L.n_vec;
   const int32_t g = L.loc2glob[p];
   const bool is_if = L.loc2iface[p] >= 0;
   double v = 0.0;
@@ -50,7 +59,7 @@ __global__ void k_scatter_interior(LevelDev L, const T* __restrict__ loc, double
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= L.n_vec) return;
   const int32_t g = L.loc2glob[p];
-  if (g >= 0 && L.loc2iface[p] < 0) y[g] = (double)loc[p];
+  if (g >= 0 && L.loc2iface[p] < 0) y[(int64_t)blockIdx.y * L.n_dof + g] = (double)loc[(int64_t)blockIdx.y * L.n_vec + p];
 }
 
 // y[row] = beta*y[row] + alpha * (K_i x)[row] for the rows of a list (interior rows, interface
@@ -62,6 +71,8 @@ __global__ void k_spmv(LevelDev L, const int64_t* __restrict__ rows, int64_t nro
   const bool valid = g < nrows;
   const int64_t row = rows[valid ? g : 0];
   const int s = row_sub[row];
+  x += (int64_t)blockIdx.y * L.n_vec;
+  y += (int64_t)blockIdx.y * L.n_vec;
   const double* xs = x + L.meta[s].vec_off;
   double acc = 0.0;
   if (valid)
@@ -87,24 +98,28 @@ __global__ void k_axpy(double* __restrict__ y, const double* __restrict__ x, dou
   if (i < n) y[i] += a * x[i];
 }
 
-__global__ void k_coarse_gather(LevelDev L, const double* __restrict__ rc_sub, double* __restrict__ rC) {
+__global__ void k_coarse_gather(LevelDev L, const double* __restrict__ rc_sub, int64_t sum_nc, double* __restrict__ rC) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= L.n_coarse) return;
+  rc_sub += (int64_t)blockIdx.y * sum_nc;
   double s = 0.0;
   for (int64_t o = L.cinv_ptr[g]; o < L.cinv_ptr[g + 1]; ++o) s += rc_sub[L.cinv_occ[o]];
-  rC[g] = s;
+  rC[(int64_t)blockIdx.y * L.n_coarse + g] = s;
 }
 
 __global__ void k_coarse_scatter(const int32_t* __restrict__ sub_coarse, int64_t total, const double* __restrict__ zC,
-                                 double* __restrict__ zc_sub) {
+                                 int64_t n_coarse, double* __restrict__ zc_sub) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < total) zc_sub[t] = zC[sub_coarse[t]];
+  if (t < total) zc_sub[(int64_t)blockIdx.y * total + t] = zC[(int64_t)blockIdx.y * n_coarse + sub_coarse[t]];
 }
 
 // deterministic dot: fixed grid, per-block tree, then a single block over the partials
 __global__ void k_dot_partial(const double* __restrict__ a, const double* __restrict__ b, int64_t n,
                               double* __restrict__ partial) {
   __shared__ double red[256];
+  a += (int64_t)blockIdx.y * n;
+  b += (int64_t)blockIdx.y * n;
+  partial += (int64_t)blockIdx.y * gridDim.x;
   double s = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     s += a[i] * b[i];
@@ -117,8 +132,10 @@ __global__ void k_dot_partial(const double* __restrict__ a, const double* __rest
   if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
 }
 
-__global__ void k_dot_final(const double* __restrict__ partial, int nblk, double* __restrict__ out) {
+__global__ void k_dot_final(const double* __restrict__ partial, int nblk, double* __restrict__ out, int ostride) {
   __shared__ double red[256];
+  partial += (int64_t)blockIdx.x * nblk;
+  out += (int64_t)blockIdx.x * ostride;
   double s = 0.0;
   for (int i = threadIdx.x; i < nblk; i += 256) s += partial[i];
   red[threadIdx.x] = s;
@@ -131,8 +148,9 @@ __global__ void k_dot_final(const double* __restrict__ partial, int nblk, double
 }
 
 // scal layout (see capi.cpp): 0 rz, 1 pq, 2 alpha, 3 beta, 4 rz_new, 5 rr, 6 gg, 7 z.r_old, 8 frozen
-__global__ void k_pcg_scalars(double* scal, int stage, int flexible) {
-  if (threadIdx.x != 0) return;
+__global__ void k_pcg_scalars(double* scal, int stage, int flexible, int nr) {
+  if ((int)threadIdx.x >= nr) return;
+  scal += 16 * threadIdx.x;   // column threadIdx.x of a block of right-hand sides
   if (scal[8] != 0.0) {   // converged column: freeze the iterate
     scal[2] = 0.0;
     scal[3] = 0.0;
@@ -153,16 +171,18 @@ __global__ void k_pcg_xr(double* __restrict__ x, double* __restrict__ r, const d
                          const double* __restrict__ q, const double* __restrict__ scal, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const double a = scal[2];
-  x[i] += a * p[i];
-  r[i] -= a * q[i];
+  const int64_t o = (int64_t)blockIdx.y * n;
+  const double a = scal[16 * blockIdx.y + 2];
+  x[o + i] += a * p[o + i];
+  r[o + i] -= a * q[o + i];
 }
 
 __global__ void k_pcg_p(double* __restrict__ p, const double* __restrict__ z, const double* __restrict__ scal,
                         int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  p[i] = z[i] + scal[3] * p[i];
+  const int64_t o = (int64_t)blockIdx.y * n;
+  p[o + i] = z[o + i] + scal[16 * blockIdx.y + 3] * p[o + i];
 }
 
 // grad[e] = -(1/coef_e) * sum_k lam_k,e^T K_e u_k,e ; one warp per element
@@ -209,18 +229,19 @@ __global__ void k_copy_segments(const double* __restrict__ src, const int64_t* _
   for (int64_t t = threadIdx.x; t < len[k]; t += blockDim.x) dst[dst_off[k] + t] = src[src_off[k] + t];
 }
 
-// g[k] = f[idx[k]] - t[k]
-__global__ void k_iface_rhs(double* __restrict__ g, const double* __restrict__ f, const int64_t* __restrict__ idx,
-                            const double* __restrict__ t, int64_t n) {
+// g[k] = f[idx[k]] - t[k] (column blockIdx.y; f has columns of length fstride)
+__global__ void k_iface_rhs(double* __restrict__ g, const double* __restrict__ f, int64_t fstride,
+                            const int64_t* __restrict__ idx, const double* __restrict__ t, int64_t n) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < n) g[k] = f[idx[k]] - t[k];
+  const int64_t o = (int64_t)blockIdx.y * n;
+  if (k < n) g[o + k] = f[(int64_t)blockIdx.y * fstride + idx[k]] - t[o + k];
 }
 
-// u[idx[k]] = v[k]
-__global__ void k_put_indexed(double* __restrict__ u, const int64_t* __restrict__ idx, const double* __restrict__ v,
-                              int64_t n) {
+// u[idx[k]] = v[k] (column blockIdx.y; u has columns of length ustride)
+__global__ void k_put_indexed(double* __restrict__ u, int64_t ustride, const int64_t* __restrict__ idx,
+                              const double* __restrict__ v, int64_t n) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < n) u[idx[k]] = v[k];
+  if (k < n) u[(int64_t)blockIdx.y * ustride + idx[k]] = v[(int64_t)blockIdx.y * n + k];
 }
 
 // BiCGstab (right preconditioned) device scalars; layout: 0 rho, 1 alpha, 2 omega, 3 rho_new,
@@ -321,24 +342,24 @@ inline unsigned nblocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); 
 }  // namespace
 
 template <typename T>
-void launch_gather_iface(const LevelDev& L, const double* x, int weighted, T* loc, cudaStream_t st) {
-  if (L.n_vec > 0) { note_launch(); k_gather_iface<T><<<nblocks(L.n_vec, 256), 256, 0, st>>>(L, x, weighted, loc); }
+void launch_gather_iface(const LevelDev& L, const double* x, int weighted, T* loc, cudaStream_t st, int nr) {
+  if (L.n_vec > 0) { note_launch(); k_gather_iface<T><<<dim3(nblocks(L.n_vec, 256), nr), 256, 0, st>>>(L, x, weighted, loc); }
 }
 template <typename T>
-void launch_scatter_iface(const LevelDev& L, const T* loc, int weighted, double* y, cudaStream_t st) {
-  if (L.n_iface > 0) { note_launch(); k_scatter_iface<T><<<nblocks(L.n_iface, 256), 256, 0, st>>>(L, loc, weighted, y); }
+void launch_scatter_iface(const LevelDev& L, const T* loc, int weighted, double* y, cudaStream_t st, int nr) {
+  if (L.n_iface > 0) { note_launch(); k_scatter_iface<T><<<dim3(nblocks(L.n_iface, 256), nr), 256, 0, st>>>(L, loc, weighted, y); }
 }
 template <typename T>
-void launch_gather_glob(const LevelDev& L, const double* x, int part, T* loc, cudaStream_t st) {
-  if (L.n_vec > 0) { note_launch(); k_gather_glob<T><<<nblocks(L.n_vec, 256), 256, 0, st>>>(L, x, part, loc); }
+void launch_gather_glob(const LevelDev& L, const double* x, int part, T* loc, cudaStream_t st, int nr) {
+  if (L.n_vec > 0) { note_launch(); k_gather_glob<T><<<dim3(nblocks(L.n_vec, 256), nr), 256, 0, st>>>(L, x, part, loc); }
 }
 template <typename T>
-void launch_scatter_interior(const LevelDev& L, const T* loc, double* y, cudaStream_t st) {
-  if (L.n_vec > 0) { note_launch(); k_scatter_interior<T><<<nblocks(L.n_vec, 256), 256, 0, st>>>(L, loc, y); }
+void launch_scatter_interior(const LevelDev& L, const T* loc, double* y, cudaStream_t st, int nr) {
+  if (L.n_vec > 0) { note_launch(); k_scatter_interior<T><<<dim3(nblocks(L.n_vec, 256), nr), 256, 0, st>>>(L, loc, y); }
 }
 void launch_spmv_rows(const LevelDev& L, const int64_t* rows, int64_t nrows, const double* x, double* y, double alpha,
-                      double beta, const int32_t* row_sub, cudaStream_t st) {
-  if (nrows > 0) { note_launch(); k_spmv<<<nblocks(nrows, 16), 256, 0, st>>>(L, rows, nrows, x, y, alpha, beta, row_sub); }
+                      double beta, const int32_t* row_sub, cudaStream_t st, int nr) {
+  if (nrows > 0) { note_launch(); k_spmv<<<dim3(nblocks(nrows, 16), nr), 256, 0, st>>>(L, rows, nrows, x, y, alpha, beta, row_sub); }
 }
 template <typename Tin, typename Tout>
 void launch_convert(const Tin* in, Tout* out, int64_t n, cudaStream_t st) {
@@ -351,26 +372,27 @@ void launch_add_to_double(double* y, const T* x, int64_t n, cudaStream_t st) {
 void launch_axpy_loc(double* y, const double* x, double a, int64_t n, cudaStream_t st) {
   if (n > 0) { note_launch(); k_axpy<<<nblocks(n, 256), 256, 0, st>>>(y, x, a, n); }
 }
-void launch_coarse_gather(const LevelDev& L, const double* rc_sub, double* rC, cudaStream_t st) {
-  if (L.n_coarse > 0) { note_launch(); k_coarse_gather<<<nblocks(L.n_coarse, 256), 256, 0, st>>>(L, rc_sub, rC); }
+void launch_coarse_gather(const LevelDev& L, const double* rc_sub, int64_t sum_nc, double* rC, cudaStream_t st, int nr) {
+  if (L.n_coarse > 0) { note_launch(); k_coarse_gather<<<dim3(nblocks(L.n_coarse, 256), nr), 256, 0, st>>>(L, rc_sub, sum_nc, rC); }
 }
-void launch_coarse_scatter_n(const int32_t* sub_coarse, int64_t total, const double* zC, double* zc_sub,
-                             cudaStream_t st) {
-  if (total > 0) { note_launch(); k_coarse_scatter<<<nblocks(total, 256), 256, 0, st>>>(sub_coarse, total, zC, zc_sub); }
+void launch_coarse_scatter_n(const int32_t* sub_coarse, int64_t total, const double* zC, int64_t n_coarse,
+                             double* zc_sub, cudaStream_t st, int nr) {
+  if (total > 0) { note_launch(); k_coarse_scatter<<<dim3(nblocks(total, 256), nr), 256, 0, st>>>(sub_coarse, total, zC, n_coarse, zc_sub); }
 }
-void launch_dot(const double* a, const double* b, int64_t n, double* partial, int nblk, double* out, cudaStream_t st) {
-  { note_launch(); k_dot_partial<<<nblk, 256, 0, st>>>(a, b, n, partial); }
-  { note_launch(); k_dot_final<<<1, 256, 0, st>>>(partial, nblk, out); }
+void launch_dot(const double* a, const double* b, int64_t n, double* partial, int nblk, double* out, cudaStream_t st,
+                int nr, int ostride) {
+  { note_launch(); k_dot_partial<<<dim3(nblk, nr), 256, 0, st>>>(a, b, n, partial); }
+  { note_launch(); k_dot_final<<<nr, 256, 0, st>>>(partial, nblk, out, ostride); }
 }
 void launch_pcg_update_x_r(double* x, double* r, const double* p, const double* q, const double* scal, int64_t n,
-                           cudaStream_t st) {
-  if (n > 0) { note_launch(); k_pcg_xr<<<nblocks(n, 256), 256, 0, st>>>(x, r, p, q, scal, n); }
+                           cudaStream_t st, int nr) {
+  if (n > 0) { note_launch(); k_pcg_xr<<<dim3(nblocks(n, 256), nr), 256, 0, st>>>(x, r, p, q, scal, n); }
 }
-void launch_pcg_update_p(double* p, const double* z, const double* scal, int64_t n, cudaStream_t st) {
-  if (n > 0) { note_launch(); k_pcg_p<<<nblocks(n, 256), 256, 0, st>>>(p, z, scal, n); }
+void launch_pcg_update_p(double* p, const double* z, const double* scal, int64_t n, cudaStream_t st, int nr) {
+  if (n > 0) { note_launch(); k_pcg_p<<<dim3(nblocks(n, 256), nr), 256, 0, st>>>(p, z, scal, n); }
 }
-void launch_pcg_scalars(double* scal, int stage, int flexible, cudaStream_t st) {
-  { note_launch(); k_pcg_scalars<<<1, 32, 0, st>>>(scal, stage, flexible); }
+void launch_pcg_scalars(double* scal, int stage, int flexible, cudaStream_t st, int nr) {
+  { note_launch(); k_pcg_scalars<<<1, 32, 0, st>>>(scal, stage, flexible, nr); }
 }
 void launch_grad_contract_slots(int64_t n_elems, int ne, const double* ke, const int32_t* slot_elem, const double* coef,
                                 const int32_t* conn, int ndof, const double* lam, const double* u, int nrhs,
@@ -389,11 +411,13 @@ void launch_copy_segments(const double* src, const int64_t* src_off, double* dst
                           const int64_t* len, int64_t n, cudaStream_t st) {
   if (n > 0) { note_launch(); k_copy_segments<<<(unsigned)n, 256, 0, st>>>(src, src_off, dst, dst_off, len, n); }
 }
-void launch_iface_rhs(double* g, const double* f, const int64_t* idx, const double* t, int64_t n, cudaStream_t st) {
-  if (n > 0) { note_launch(); k_iface_rhs<<<nblocks(n, 256), 256, 0, st>>>(g, f, idx, t, n); }
+void launch_iface_rhs(double* g, const double* f, int64_t fstride, const int64_t* idx, const double* t, int64_t n,
+                      cudaStream_t st, int nr) {
+  if (n > 0) { note_launch(); k_iface_rhs<<<dim3(nblocks(n, 256), nr), 256, 0, st>>>(g, f, fstride, idx, t, n); }
 }
-void launch_put_indexed(double* u, const int64_t* idx, const double* v, int64_t n, cudaStream_t st) {
-  if (n > 0) { note_launch(); k_put_indexed<<<nblocks(n, 256), 256, 0, st>>>(u, idx, v, n); }
+void launch_put_indexed(double* u, int64_t ustride, const int64_t* idx, const double* v, int64_t n, cudaStream_t st,
+                        int nr) {
+  if (n > 0) { note_launch(); k_put_indexed<<<dim3(nblocks(n, 256), nr), 256, 0, st>>>(u, ustride, idx, v, n); }
 }
 
 void launch_multidot(const double* V, int64_t ldv, int nv, const double* w, int64_t n, double* partial, int nblk,
@@ -428,10 +452,10 @@ void launch_bicg_xr(double* x, double* r, const double* ph, const double* sh, co
 }
 
 #define INST(T)                                                                             \
-  template void launch_gather_iface<T>(const LevelDev&, const double*, int, T*, cudaStream_t); \
-  template void launch_scatter_iface<T>(const LevelDev&, const T*, int, double*, cudaStream_t); \
-  template void launch_gather_glob<T>(const LevelDev&, const double*, int, T*, cudaStream_t);  \
-  template void launch_scatter_interior<T>(const LevelDev&, const T*, double*, cudaStream_t);  \
+  template void launch_gather_iface<T>(const LevelDev&, const double*, int, T*, cudaStream_t, int); \
+  template void launch_scatter_iface<T>(const LevelDev&, const T*, int, double*, cudaStream_t, int); \
+  template void launch_gather_glob<T>(const LevelDev&, const double*, int, T*, cudaStream_t, int);  \
+  template void launch_scatter_interior<T>(const LevelDev&, const T*, double*, cudaStream_t, int);  \
   template void launch_add_to_double<T>(double*, const T*, int64_t, cudaStream_t);
 INST(float)
 INST(double)
