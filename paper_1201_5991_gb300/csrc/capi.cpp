@@ -140,7 +140,9 @@ struct Level {
   // coarsest level of the mixed form: FP32 copy of the FP64 factor for the preconditioner's solves
   bool solve32 = false;
   LevelDev d32{};
-  float* v32 = nullptr;
+  float* v32 = nullptr;            // [blk][n_vec] FP32 input of the coarse solve
+  float* v32b = nullptr;           // [blk][n_vec] FP32 output of the explicit inverse
+  float* winv = nullptr;           // explicit inverse of the FP32 copy (n_vec x n_vec), or null
   // sweep launch configuration per part (autotuned): CTAs per SM, deep tile ring, task order
   int sweep_ctas[2] = {2, 2};
   int sweep_deep[2] = {1, 1};
@@ -182,6 +184,7 @@ struct Level {
 int64_t pad_pos(const SubMeta& m, int64_t r) { return r < m.nI ? r : (int64_t)m.nIb * NB + (r - m.nI); }
 
 constexpr int kMaxBlock = 8;   // right-hand sides solved together (one pass over the factors)
+constexpr int64_t kMaxCoarseInverse = 16384;   // padded coarse sizes with an explicit FP32 inverse (1 GiB)
 
 // Work vectors of the solve phase of one level for blocks of up to blk right-hand sides (every
 // column of a block has the vector kind's own length, see internal.h).
@@ -209,7 +212,10 @@ void alloc_level_work(Level& L, DevArena& A, int blk) {
   L.gi1 = A.alloc<double>(L.maps.n_iface * blk);
   L.gi2 = A.alloc<double>(L.maps.n_iface * blk);
   L.gv0 = A.alloc<double>(L.mesh.n_dof * blk);
-  if (L.solve32) L.v32 = A.alloc<float>(nv);
+  if (L.solve32) {
+    L.v32 = A.alloc<float>(nv);
+    L.v32b = A.alloc<float>(nv);
+  }
   L.blk = blk;
 }
 
@@ -1030,6 +1036,12 @@ void coarsest_solve(bddc_handle_s* h, const double* rC, double* zC, cudaStream_t
   Level& C = h->lv.back();
   if (C.solve32) {   // mixed form: the preconditioner's coarse solve with the FP32 copy of the factor
     launch_gather_glob<float>(C.d32, rC, 2, C.v32, st, nb);
+    if (C.winv) {     // explicit inverse of that copy: one product
+      ProfScope ps(h, BDDC_PROF_COARSE, 4.0 * (double)C.n_vec * C.n_vec * column_groups(nb, 8), 0.0, st);
+      launch_coarse_apply(C.winv, C.n_vec, C.v32, C.v32b, C.n_vec, nb, st);
+      launch_scatter_interior<float>(C.d32, C.v32b, zC, st, nb);
+      return;
+    }
     trsv_pair<float>(h, C, C.v32, 0, st, nb);
     launch_scatter_interior<float>(C.d32, C.v32, zC, st, nb);
     return;
@@ -1260,13 +1272,18 @@ void numeric_setup(bddc_handle_s* h) {
         L.d32.dinv = h->arena.alloc<float>(L.dinv_elems);
         L.d32.sgn = h->arena.alloc<float>(L.n_vec);
         L.v32 = h->arena.alloc<float>(L.n_vec * L.blk);
+        L.v32b = h->arena.alloc<float>(L.n_vec * L.blk);
+        if (L.n_vec <= kMaxCoarseInverse) L.winv = h->arena.alloc<float>(L.n_vec * L.n_vec);
         L.solve32 = true;
       }
       launch_convert<double, float>((const double*)L.d.tiles, (float*)L.d32.tiles, L.tile_elems, st);
       launch_convert<double, float>((const double*)L.d.dinv, (float*)L.d32.dinv, L.dinv_elems, st);
       launch_convert<double, float>((const double*)L.d.sgn, (float*)L.d32.sgn, L.n_vec, st);
+      // the preconditioner's coarse solves then are one product with the explicit inverse (a
+      // sweep pair over the coarse factor is a chain of dependent block rows: latency-bound)
+      if (L.winv) launch_coarse_inverse(L.d32, L.n_vec, L.winv, st);
     }
-    if (h->opts.autotune) {
+    if (h->opts.autotune && !L.winv) {   // the explicit inverse replaces the coarsest sweeps
       if (L.fp32 || L.solve32)
         tune_sweeps<float>(h, L, st);
       else

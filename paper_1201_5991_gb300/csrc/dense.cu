@@ -624,7 +624,189 @@ __global__ void k_psi_apply_add(LevelDev L, const double* __restrict__ zc_sub, i
   v[c] = v[c] + acc;
 }
 
+
+// ---- explicit inverse of the coarsest factor (FP32 copy, mixed form) ------------------------
+// W = A_C^{-1} = L^{-T} S L^{-1} of the single-subdomain coarsest level, whose block rows are all
+// "interior" (identity padding past the last DOF).  CTA c substitutes the identity columns
+// c CW .. c CW + CW - 1 through the tiled factor: forward y_i = D_i (e_i - sum_{j<i} L_ij y_j),
+// t = S y, backward x_i = D_i^T (t_i - sum_{j>i} L_ji^T x_j), with D_i the stored inverses of the
+// diagonal tiles (the same steps as the sweeps, in the same precision).  Column q of the result is
+// kept at W + (c CW + q) n_pad, so W is stored column after column; A_C is symmetric, so row q of
+// the stored matrix is row q of A_C^{-1} up to rounding.  Each product of a tile with a 64 x CW
+// block runs from shared memory, the tile k-major, every thread a block of CW/16 rows x 4 columns.
+template <int CW>
+__global__ void __launch_bounds__(256) k_coarse_inverse(LevelDev L, float* __restrict__ W) {
+  constexpr int RR = CW / 16;                 // rows per thread
+  constexpr int CG = CW / 4;                  // column groups of four
+  const SubMeta m = L.meta[0];
+  const int nb = m.Bc;
+  const int64_t npad = (int64_t)nb * NB;
+  const int c0 = blockIdx.x * CW;
+  if (c0 >= npad) return;
+  __shared__ __align__(16) float As[NB][NB + 4];   // tile, k-major: As[k][r]
+  __shared__ __align__(16) float Bs[NB][CW + 4];   // 64 x CW block: Bs[k][c]
+  const int tid = threadIdx.x;
+  const int cg = tid % CG, rg = tid / CG;          // columns 4 cg .. +3, rows RR rg .. +RR-1
+  float* Wc = W + (int64_t)c0 * npad;              // this CTA's columns, each of npad entries
+  const float* tiles = (const float*)L.tiles + m.tile_off;
+  const float* dinv = (const float*)L.dinv + m.dinv_off;
+  const float* sgn = (const float*)L.sgn + m.vec_off;
+  auto load_tile = [&](const float* t, bool transpose) {   // As[k][r] = t[r][k] (or t[k][r])
+    for (int e = tid; e < NB2; e += 256) {
+      const int a = e / NB, b = e % NB;
+      if (transpose) As[b][a] = t[e]; else As[a][b] = t[e];
+    }
+  };
+  auto load_block = [&](int blk) {                  // Bs[k][c] = W column c, rows of block blk
+    for (int e = tid; e < NB * CW; e += 256) {
+      const int c = e / NB, k = e % NB;
+      Bs[k][c] = Wc[(int64_t)c * npad + (int64_t)blk * NB + k];
+    }
+  };
+  auto mma = [&](float (&acc)[RR][4]) {
+#pragma unroll 8
+    for (int k = 0; k < NB; ++k) {
+      float a[RR], b[4];
+#pragma unroll
+      for (int r = 0; r < RR; ++r) a[r] = As[k][RR * rg + r];
+      const float4 bv = *(const float4*)&Bs[k][4 * cg];
+      b[0] = bv.x; b[1] = bv.y; b[2] = bv.z; b[3] = bv.w;
+#pragma unroll
+      for (int r = 0; r < RR; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[r][q] += a[r] * b[q];
+    }
+  };
+  auto store_block = [&](int blk, const float (&v)[RR][4]) {
+#pragma unroll
+    for (int r = 0; r < RR; ++r)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) Wc[(int64_t)(4 * cg + q) * npad + (int64_t)blk * NB + RR * rg + r] = v[r][q];
+  };
+  // forward: y_i = D_i (e_i - sum_{j<i} L_ij y_j)
+  for (int i = 0; i < nb; ++i) {
+    float acc[RR][4] = {};
+    for (int j = 0; j < i; ++j) {
+      __syncthreads();
+      load_tile(tiles + ((int64_t)i * (i + 1) / 2 + j) * NB2, true);
+      load_block(j);
+      __syncthreads();
+      mma(acc);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RR; ++r)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int64_t row = (int64_t)i * NB + RR * rg + r;
+        Bs[RR * rg + r][4 * cg + q] = (row == c0 + 4 * cg + q ? 1.f : 0.f) - acc[r][q];
+      }
+    load_tile(dinv + (int64_t)i * NB2, true);
+    __syncthreads();
+    float y[RR][4] = {};
+    mma(y);
+    store_block(i, y);
+  }
+  __syncthreads();
+  // t = S y (pivot signs of the signed factor; all +1 on SPD levels)
+  for (int e = tid; e < NB * CW; e += 256) {
+    const int c = e / NB;
+    for (int64_t row = e % NB; row < npad; row += NB) Wc[(int64_t)c * npad + row] *= sgn[row];
+  }
+  // backward: x_i = D_i^T (t_i - sum_{j>i} L_ji^T x_j)
+  for (int i = nb - 1; i >= 0; --i) {
+    float acc[RR][4] = {};
+    for (int j = i + 1; j < nb; ++j) {
+      __syncthreads();
+      load_tile(tiles + ((int64_t)j * (j + 1) / 2 + i) * NB2, false);
+      load_block(j);
+      __syncthreads();
+      mma(acc);
+    }
+    __syncthreads();
+    load_block(i);
+    __syncthreads();
+    float rhs[RR][4];
+#pragma unroll
+    for (int r = 0; r < RR; ++r)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) rhs[r][q] = Bs[RR * rg + r][4 * cg + q] - acc[r][q];
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RR; ++r)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) Bs[RR * rg + r][4 * cg + q] = rhs[r][q];
+    load_tile(dinv + (int64_t)i * NB2, false);
+    __syncthreads();
+    float x[RR][4] = {};
+    mma(x);
+    store_block(i, x);
+  }
+}
+
+// y = W x for nr columns (x, y: columns of n_vec, padded local positions 0 .. npad-1); one warp
+// per output row, lanes along the row (coalesced), FP32 sums in a fixed order.
+template <int NR>
+__global__ void k_coarse_apply(const float* __restrict__ W, int64_t npad, const float* __restrict__ x,
+                               float* __restrict__ y, int64_t n_vec) {
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= npad) return;
+  const int64_t c0 = (int64_t)blockIdx.y * NR;
+  const float* w = W + row * npad;
+  float acc[NR];
+#pragma unroll
+  for (int q = 0; q < NR; ++q) acc[q] = 0.f;
+  for (int64_t c = 4 * lane; c < npad; c += 128) {
+    const float4 a = *(const float4*)(w + c);
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+      const float4 b = *(const float4*)(x + (c0 + q) * n_vec + c);
+      acc[q] += a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NR; ++q) {
+    float v = acc[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) y[(c0 + q) * n_vec + row] = v;
+  }
+}
+
 }  // namespace
+
+void launch_coarse_inverse(const LevelDev& L, int64_t npad, float* W, cudaStream_t st) {
+  if (npad <= 0) return;
+  note_launch();
+  if (npad <= 2048)
+    k_coarse_inverse<16><<<(unsigned)((npad + 15) / 16), 256, 0, st>>>(L, W);
+  else
+    k_coarse_inverse<64><<<(unsigned)((npad + 63) / 64), 256, 0, st>>>(L, W);
+}
+
+void launch_coarse_apply(const float* W, int64_t npad, const float* x, float* y, int64_t n_vec, int nr,
+                         cudaStream_t st) {
+  if (npad <= 0 || nr <= 0) return;
+  const unsigned gx = (unsigned)((npad + 7) / 8);
+  for (int r0 = 0; r0 < nr;) {
+    const int left = nr - r0;
+    const int g = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
+    const int ng = left / g;
+    const float* xs = x + (int64_t)r0 * n_vec;
+    float* ys = y + (int64_t)r0 * n_vec;
+    note_launch();
+    if (g == 8)
+      k_coarse_apply<8><<<dim3(gx, ng), 256, 0, st>>>(W, npad, xs, ys, n_vec);
+    else if (g == 4)
+      k_coarse_apply<4><<<dim3(gx, ng), 256, 0, st>>>(W, npad, xs, ys, n_vec);
+    else if (g == 2)
+      k_coarse_apply<2><<<dim3(gx, ng), 256, 0, st>>>(W, npad, xs, ys, n_vec);
+    else
+      k_coarse_apply<1><<<dim3(gx, ng), 256, 0, st>>>(W, npad, xs, ys, n_vec);
+    r0 += ng * g;
+  }
+}
 
 template <typename T>
 void launch_potrf_step(const LevelDev& L, int k, int max_R, int max_tiles, int jmax, cudaStream_t st) {

@@ -152,6 +152,12 @@ void launch_update_tc2(const LevelDev& L, int kb0, int kb1, int grid, const uint
 void launch_gram_chol(const LevelDev& L, int precision_fp32, int max_nc, cudaStream_t st);
 template <typename T>
 void launch_psi(const LevelDev& L, int max_nGb, int max_nc, cudaStream_t st);
+// Explicit inverse W = A^{-1} of a single-subdomain level held in an FP32 factor (the coarsest
+// level's FP32 copy), npad x npad stored column after column; and y = W x for nr columns of n_vec
+// (padded local positions).
+void launch_coarse_inverse(const LevelDev& L, int64_t npad, float* W, cudaStream_t st);
+void launch_coarse_apply(const float* W, int64_t npad, const float* x, float* y, int64_t n_vec, int nr,
+                         cudaStream_t st);
 // sweep.cu: forward (backward = 0) or backward triangular sweep over part 0 (interior
 // block rows) or part 1 (interface block rows) of every subdomain; ctrl has n_ctrl ints.
 // Solve-phase launches take nr right-hand sides (default 1); a block of them stores its columns one
