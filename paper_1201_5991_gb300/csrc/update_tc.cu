@@ -78,7 +78,7 @@ constexpr uint32_t kTilePart = 64 * 128;         // one FP16 part of one 64 x 64
 constexpr uint32_t kSplitTile = 2 * kTilePart;   // hi and lo of one tile (16 KB)
 constexpr uint32_t kOpnd = 2 * kTilePart;        // one part of a 128-row operand (16 KB)
 constexpr uint32_t kStage2 = 4 * kOpnd;          // A hi, A lo, B hi, B lo (64 KB)
-constexpr int kThreads2 = 288;                   // 8 epilogue warps + 1 producer / MMA warp
+constexpr int kThreads2 = 320;                   // 8 epilogue warps + 1 MMA warp + 1 producer warp
 constexpr int kStages2 = 3;                      // shared-memory stages (copies run two steps ahead)
 constexpr uint32_t kEpiBox = 32 * 128;           // per epilogue warp: one 32 x 32 FP32 output box (4 KB)
 
@@ -161,10 +161,12 @@ __global__ void __launch_bounds__(256) k_split_panel(LevelDev L, int kb0, int kb
 
 // Persistent: CTA c takes the work items c, c + gridDim.x, ... of the panel (items of all
 // subdomains flattened; item_pref[s] = first item of subdomain s).  One global step per (item,
-// panel column); step g uses shared-memory stage g % 3 (its copies are requested two steps
-// ahead) and TMEM accumulator pair g & 1, so the copies and MMAs of the next steps (also of the
-// next item) run while the epilogue warps promote the previous accumulators and write back the
-// previous item's output block.  The write-back is a TMA reduce-add: each epilogue warp scales
+// panel column); step g uses shared-memory stage g % 3 and TMEM accumulator pair g & 1.  Three
+// roles run in their own warps: a producer thread requests the copies of each step as soon as its
+// stage is free, one thread issues the MMAs as soon as a stage is full and an accumulator pair
+// free (a single thread doing both waited, before every refill, for the MMAs of the previous step
+// to complete: 1.7 us per step, with the copies and the tensor pipe mostly idle), and the epilogue
+// warps promote the accumulators and write back each item's output block.  The write-back is a TMA reduce-add: each epilogue warp scales
 // its 32 x 64 part of the block into a swizzled shared-memory box, 32 columns at a time, and one
 // lane adds the box into the tiles in L2 (the output is never read into the SM; every element
 // receives exactly one add per launch, so the result does not depend on timing).
@@ -185,7 +187,7 @@ __global__ void __launch_bounds__(kThreads2, 1)
   // accumulator pair g & 1 written by its MMAs / read by the epilogue
   __shared__ __align__(8) uint64_t full_bar[kStages2], free_bar[kStages2], mma_bar[2], epi_bar[2];
   __shared__ uint32_t tmem_slot;
-  __shared__ int s_issued;
+  __shared__ int s_issued, s_requested;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&tmem_slot)));
@@ -202,6 +204,7 @@ __global__ void __launch_bounds__(kThreads2, 1)
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_issued = 0;
+    s_requested = 0;
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -230,29 +233,30 @@ __global__ void __launch_bounds__(kThreads2, 1)
     }
   };
 
-  if (warp == 8) {
-    // ---- producer / MMA issuer
+  // steps of this CTA: its items in order, nq panel columns each
+  const int64_t my_items = (n_items - (int64_t)blockIdx.x + gridDim.x - 1) / gridDim.x;
+  const uint32_t total = (uint32_t)(my_items * nq);
+  auto wait = [&](uint64_t* bar, uint32_t parity) {
+    long long spins = 0;
+    while (!mbar_try_wait(bar, parity))
+      if (++spins > kSpinLimit) return false;
+    return true;
+  };
+  if (warp == 9) {
+    // ---- producer: requests the B and A parts of step gc into stage gc % kStages2 once the MMAs
+    // of step gc - kStages2 have read that stage (its own thread, so that waiting for a stage
+    // never delays the issue of MMAs)
     if (lane == 0) {
-      // c FP32, a and b FP16, both K-major, N = 128, M = 128
-      const uint32_t idesc = (1u << 4) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
       bool lost = false;
-      int issued = 0;
-      auto wait = [&](uint64_t* bar, uint32_t parity) {
-        long long spins = 0;
-        while (!mbar_try_wait(bar, parity))
-          if (++spins > kSpinLimit) return false;
-        return true;
-      };
-      // steps of this CTA: its items in order, nq panel columns each
-      const int64_t my_items = (n_items - (int64_t)blockIdx.x + gridDim.x - 1) / gridDim.x;
-      const uint32_t total = (uint32_t)(my_items * nq);
       int64_t cached_k = -1;
       int cs = 0, cj = 0, ci0 = 0;
-      // request the B and A parts of step gc into stage gc % kStages2 (after the MMAs of step
-      // gc - kStages2 have read it)
-      auto request = [&](uint32_t gc) -> bool {
+      uint32_t gc = 0;
+      for (; gc < total; ++gc) {
         const int st = (int)(gc % kStages2);
-        if (gc >= (uint32_t)kStages2 && !wait(&free_bar[st], ((gc / kStages2) - 1) & 1u)) return false;
+        if (gc >= (uint32_t)kStages2 && !wait(&free_bar[st], ((gc / kStages2) - 1) & 1u)) {
+          lost = true;
+          break;
+        }
         const int64_t k = gc / nq;
         const int q = (int)(gc % nq);
         if (k != cached_k) {
@@ -290,19 +294,21 @@ __global__ void __launch_bounds__(kThreads2, 1)
           bulk_g2s(sB + p * kOpnd, rowB0 + qo + p * kTilePart, kTilePart, &full_bar[st]);
           bulk_g2s(sB + p * kOpnd + kTilePart, rowB1 + qo + p * kTilePart, kTilePart, &full_bar[st]);
         }
-        return true;
-      };
-      uint32_t requested = 0;
-      for (; requested < total && requested < (uint32_t)(kStages2 - 1); ++requested)
-        if (!request(requested)) {
-          lost = true;
-          break;
-        }
+      }
+      s_requested = (int)gc;
+      if (lost) atomicExch(L.status + 2, 4);
+    }
+  } else if (warp == 8) {
+    // ---- MMA issuer: one thread waits for the stage's data and for a free accumulator pair
+    if (lane == 0) {
+      // c FP32, a and b FP16, both K-major, N = 128, M = 128
+      const uint32_t idesc = (1u << 4) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+      bool lost = false;
+      int issued = 0;
       for (uint32_t g = 0; g < total && !lost; ++g) {
         const int st = (int)(g % kStages2);
         const int b = (int)(g & 1u);
         if (!wait(&full_bar[st], (g / kStages2) & 1u)) {
-          wait(&full_bar[st], (g / kStages2) & 1u);   // copies may still land: one more bounded wait
           lost = true;
           break;
         }
@@ -335,15 +341,6 @@ __global__ void __launch_bounds__(kThreads2, 1)
                          smem_u32(&free_bar[st]))
                      : "memory");
         ++issued;
-        // refill: step g + kStages2 - 1 goes into the stage of step g - 1, whose MMAs run ahead
-        // of the ones just issued
-        if (requested < total) {
-          if (!request(requested)) {
-            lost = true;
-            break;
-          }
-          ++requested;
-        }
       }
       s_issued = issued;
       if (lost) atomicExch(L.status + 2, 4);
@@ -445,6 +442,14 @@ __global__ void __launch_bounds__(kThreads2, 1)
     if (lost && lane == 0) atomicExch(L.status + 2, 4);
   }
   __syncthreads();
+  // copies requested but never consumed (a wait gave up) may still be landing in shared memory:
+  // wait (bounded) for them before the CTA exits
+  if (tid == 0)
+    for (int c = s_issued; c < s_requested; ++c) {
+      long long spins = 0;
+      while (!mbar_try_wait(&full_bar[c % kStages2], (uint32_t)(c / kStages2) & 1u) && ++spins < kSpinLimit) {
+      }
+    }
   // before the accumulators are released no MMA may still be running (also on the error path)
   const int issued = s_issued;
   if (issued > 0) {
