@@ -433,67 +433,68 @@ __global__ void k_psi_rhs(LevelDev L) {
   }
 }
 
-// Psi_G = L_GG^{-T} Z, backward block sweep; one block per (column chunk of 16, subdomain).
-// Block row i: rhs = Z_i - sum_{j > i} L(j,i)^T X_j, then X_i = L_ii^{-T} rhs.  Thread t sums the
-// rows 16 g .. 16 g + 15 (g = t / 64) of every tile L(j,i) for the columns 4 tc .. 4 tc + 3
-// (tc = t % 16) and the right-hand sides 4 tq .. 4 tq + 3 (tq = (t / 16) % 4): a 4 x 4 register
-// block, one vector load of L and four (broadcast) loads of X per 16 products; the four row
-// groups meet in shared memory in a fixed order.
+// Psi_G = L_GG^{-T} Z, right-looking over the interface block rows from the bottom: at step t,
+// block row i = Bc - 1 - t of every subdomain is final once X_i = D_i^T Z_i (D_i the stored inverse
+// of the diagonal tile), and every block row j < i above it receives Z_j -= L(i, j)^T X_i.  The
+// updates of a step are independent (one CTA per (j, subdomain, 16 columns)), so a step is one
+// wide launch instead of a per-CTA chain of dependent tiles.
 template <typename T>
-__global__ void __launch_bounds__(256) k_trsm_back_psi(LevelDev L) {
+__global__ void __launch_bounds__(256) k_psi_final(LevelDev L, int t) {
   const int s = blockIdx.y;
   const SubMeta m = L.meta[s];
-  const int nc = m.nc;
-  const int c0 = blockIdx.x * 16;
-  if (c0 >= nc) return;
-  const int ncols = min(16, nc - c0);
-  T* Z = (T*)L.psi + m.psi_off;
-  __shared__ T part[4][NB][17];
-  __shared__ T rhs[NB][16];
-  const int g = threadIdx.x >> 6, tc = threadIdx.x & 15, tq = (threadIdx.x >> 4) & 3;
-  for (int i = m.Bc - 1; i >= m.nIb; --i) {
-    T acc[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] = (T)0;
-    for (int j = i + 1; j < m.Bc; ++j) {
-      const T* Lt = tile_ptr<T>(m, L.tiles, j, i) + 16 * g * NB + 4 * tc;
-      const T* Xj = Z + ((int64_t)(j - m.nIb) * NB + 16 * g) * nc + c0 + 4 * tq;
-#pragma unroll 4
-      for (int r = 0; r < 16; ++r) {
-        T l[4], x[4];
-        load4(l, Lt + r * NB);
-#pragma unroll
-        for (int b = 0; b < 4; ++b) x[b] = 4 * tq + b < ncols ? Xj[(int64_t)r * nc + b] : (T)0;
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) acc[a][b] += l[a] * x[b];
-      }
-    }
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) part[g][4 * tc + a][4 * tq + b] = acc[a][b];
-    __syncthreads();
-    T* Zi = Z + (int64_t)(i - m.nIb) * NB * nc + c0;
-    for (int t = threadIdx.x; t < NB * 16; t += blockDim.x) {
-      const int cc = t / 16, q = t % 16;
-      if (q < ncols)
-        rhs[cc][q] = Zi[(int64_t)cc * nc + q] - (part[0][cc][q] + part[1][cc][q] + part[2][cc][q] + part[3][cc][q]);
-    }
-    __syncthreads();
-    const T* Dv = (const T*)L.dinv + m.dinv_off + (int64_t)i * NB2;
-    for (int t = threadIdx.x; t < NB * 16; t += blockDim.x) {
-      const int cc = t / 16, q = t % 16;
-      if (q >= ncols) continue;
-      T acc2 = (T)0;
-      for (int mm = cc; mm < NB; ++mm) acc2 += Dv[mm * NB + cc] * rhs[mm][q];   // (L_ii^{-1})^T
-      Zi[(int64_t)cc * nc + q] = acc2;
-    }
-    __syncthreads();
+  const int i = m.Bc - 1 - t, c0 = 16 * blockIdx.x, nc = m.nc;
+  if (i < m.nIb || c0 >= nc) return;
+  __shared__ T Ds[NB][NB + 1];
+  __shared__ __align__(16) T Zs[NB][16];
+  const T* dv = (const T*)L.dinv + m.dinv_off + (int64_t)i * NB2;
+  T* Zi = (T*)L.psi + m.psi_off + (int64_t)(i - m.nIb) * NB * nc;
+  for (int e = threadIdx.x; e < NB2; e += blockDim.x) Ds[e / NB][e % NB] = dv[e];
+  for (int e = threadIdx.x; e < NB * 16; e += blockDim.x) {
+    const int r = e / 16, q = e % 16;
+    Zs[r][q] = c0 + q < nc ? Zi[(int64_t)r * nc + c0 + q] : (T)0;
   }
+  __syncthreads();
+  const int r = threadIdx.x >> 2, q4 = 4 * (threadIdx.x & 3);
+  T x[4] = {};
+#pragma unroll 8
+  for (int mm = 0; mm < NB; ++mm) {   // X_i = D_i^T Z_i
+    const T d = Ds[mm][r];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) x[b] += d * Zs[mm][q4 + b];
+  }
+#pragma unroll
+  for (int b = 0; b < 4; ++b)
+    if (c0 + q4 + b < nc) Zi[(int64_t)r * nc + c0 + q4 + b] = x[b];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_psi_update(LevelDev L, int t) {
+  const int s = blockIdx.y;
+  const SubMeta m = L.meta[s];
+  const int i = m.Bc - 1 - t, j = m.nIb + (int)blockIdx.x, c0 = 16 * blockIdx.z, nc = m.nc;
+  if (j >= i || c0 >= nc) return;
+  __shared__ T Ls[NB][NB + 1];
+  __shared__ __align__(16) T Xs[NB][16];
+  const T* lt = (const T*)L.tiles + m.tile_off + tile_index(i, j, m.Bc) * NB2;
+  const T* Xi = (const T*)L.psi + m.psi_off + (int64_t)(i - m.nIb) * NB * nc;
+  T* Zj = (T*)L.psi + m.psi_off + (int64_t)(j - m.nIb) * NB * nc;
+  for (int e = threadIdx.x; e < NB2; e += blockDim.x) Ls[e / NB][e % NB] = lt[e];
+  for (int e = threadIdx.x; e < NB * 16; e += blockDim.x) {
+    const int r = e / 16, q = e % 16;
+    Xs[r][q] = c0 + q < nc ? Xi[(int64_t)r * nc + c0 + q] : (T)0;
+  }
+  __syncthreads();
+  const int c = threadIdx.x >> 2, q4 = 4 * (threadIdx.x & 3);
+  T acc[4] = {};
+#pragma unroll 8
+  for (int r = 0; r < NB; ++r) {   // (L(i, j)^T X_i)[c] = sum_r L(i, j)[r][c] X_i[r]
+    const T l = Ls[r][c];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[b] += l * Xs[r][q4 + b];
+  }
+#pragma unroll
+  for (int b = 0; b < 4; ++b)
+    if (c0 + q4 + b < nc) Zj[(int64_t)c * nc + c0 + q4 + b] -= acc[b];
 }
 
 // v_G -= Y_G^T G^{-1} Y_G v_G  (the constraint part of Eq. sub_cor), in three launches with
@@ -846,7 +847,12 @@ void launch_psi(const LevelDev& L, int max_nGb, int max_nc, cudaStream_t st) {
   const unsigned ns = (unsigned)L.n_sub;
   if (max_nc <= 0 || max_nGb <= 0) return;
   { note_launch(); k_psi_rhs<T><<<dim3(16, ns), 256, 0, st>>>(L); }
-  { note_launch(); k_trsm_back_psi<T><<<dim3((unsigned)((max_nc + 15) / 16), ns), 256, 0, st>>>(L); }
+  const unsigned chunks = (unsigned)((max_nc + 15) / 16);
+  for (int t = 0; t < max_nGb; ++t) {   // block row Bc - 1 - t of every subdomain, bottom up
+    { note_launch(); k_psi_final<T><<<dim3(chunks, ns), 256, 0, st>>>(L, t); }
+    if (max_nGb - 1 - t > 0)
+      { note_launch(); k_psi_update<T><<<dim3((unsigned)(max_nGb - 1 - t), ns, chunks), 256, 0, st>>>(L, t); }
+  }
 }
 
 // The solve-phase launches below take nr right-hand sides: local vectors of n_vec, per-subdomain

@@ -34,13 +34,13 @@
 #include <cstring>
 
 #include "internal.h"
+#include "split.cuh"
 
 namespace bddc {
 
 namespace {
 
 constexpr long long kSpinLimit = 1ll << 26;
-constexpr int kPanelTiles = 4;           // tile columns of a super-panel (the split buffer's row pitch)
 
 __device__ __forceinline__ int64_t tile_index(int i, int j, int Bc) {
   return i < Bc ? ((int64_t)i * (i + 1) / 2 + j) : ((int64_t)Bc * (Bc + 1) / 2 + (int64_t)(i - Bc) * Bc + j);
@@ -59,9 +59,6 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
   return d;
 }
 
-__device__ __forceinline__ uint32_t sw128_off(int r, int k) {
-  return (uint32_t)(r * 128 + (((k >> 3) ^ (r & 7)) << 4) + (k & 7) * 2);
-}
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
@@ -74,8 +71,6 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 
-constexpr uint32_t kTilePart = 64 * 128;         // one FP16 part of one 64 x 64 tile (8 KB)
-constexpr uint32_t kSplitTile = 2 * kTilePart;   // hi and lo of one tile (16 KB)
 constexpr uint32_t kOpnd = 2 * kTilePart;        // one part of a 128-row operand (16 KB)
 constexpr uint32_t kStage2 = 4 * kOpnd;          // A hi, A lo, B hi, B lo (64 KB)
 constexpr int kThreads2 = 320;                   // 8 epilogue warps + 1 MMA warp + 1 producer warp
@@ -93,16 +88,8 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                : "memory");
 }
 
-__device__ __forceinline__ void store4h(uint8_t* part, uint32_t off, const __half* h) {
-  __half2 lo = __halves2half2(h[0], h[1]), hi = __halves2half2(h[2], h[3]);
-  uint2 v;
-  v.x = *(uint32_t*)&lo;
-  v.y = *(uint32_t*)&hi;
-  *(uint2*)(part + off) = v;
-}
 
-// one block per panel row tile i (kb1 <= i < R) of every subdomain; thread (r, c4): row r of
-// tile column kb0 + c4 (the four threads of a row share its scale)
+// one block per panel row tile i (kb1 <= i < R) of every subdomain
 __global__ void __launch_bounds__(256) k_split_panel(LevelDev L, int kb0, int kb1, uint8_t* __restrict__ split,
                                                      uint8_t* __restrict__ split_signed, float* __restrict__ rscale,
                                                      const int64_t* __restrict__ prow_off) {
@@ -111,52 +98,7 @@ __global__ void __launch_bounds__(256) k_split_panel(LevelDev L, int kb0, int kb
   if (kb1 >= m.Bc) return;
   const int i = kb1 + (int)blockIdx.x;
   if (i >= m.R) return;
-  const int r = threadIdx.x >> 2, c4 = threadIdx.x & 3;
-  const float4* t = (const float4*)((const float*)L.tiles + m.tile_off + tile_index(i, kb0 + c4, m.Bc) * NB2 + r * NB);
-  float4 v[16];
-  float mx = 0.f;
-#pragma unroll
-  for (int u = 0; u < 16; ++u) {
-    v[u] = __ldcg(t + u);
-    mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v[u].x), fabsf(v[u].y)), fmaxf(fabsf(v[u].z), fabsf(v[u].w))));
-  }
-  mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-  mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
-  int ex = 0;
-  if (mx > 0.f) {
-    int k;
-    frexpf(mx, &k);   // mx = f 2^k, f in [0.5, 1)
-    ex = 15 - k;      // mx 2^ex in [2^14, 2^15)
-  }
-  const int64_t row = prow_off[s] + i;
-  if (c4 == 0) rscale[row * NB + r] = ldexpf(1.f, -ex);   // exact power of two
-  uint8_t* dst = split + (row * kPanelTiles + c4) * (int64_t)kSplitTile;
-#pragma unroll
-  for (int u = 0; u < 16; ++u) {
-    const float a[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
-    __half h[4], l[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const float sa = ldexpf(a[e], ex);
-      h[e] = __float2half_rn(sa);
-      l[e] = __float2half_rn((sa - __half2float(h[e])) * 2048.f);
-    }
-    const uint32_t off = sw128_off(r, 4 * u);
-    store4h(dst, off, h);
-    store4h(dst + kTilePart, off, l);
-    if (split_signed) {   // indefinite levels: the B operand is L(j, q) S_q (pivot signs of column q)
-      const float* sq = (const float*)L.sgn + m.vec_off + (int64_t)(kb0 + c4) * NB + 4 * u;
-      uint8_t* dsg = split_signed + (row * kPanelTiles + c4) * (int64_t)kSplitTile;
-#pragma unroll
-      for (int e = 0; e < 4; ++e)
-        if (sq[e] < 0.f) {
-          h[e] = __hneg(h[e]);
-          l[e] = __hneg(l[e]);
-        }
-      store4h(dsg, off, h);
-      store4h(dsg + kTilePart, off, l);
-    }
-  }
+  split_row_tile(L, s, m, i, kb0, split, split_signed, rscale, prow_off);
 }
 
 // Persistent: CTA c takes the work items c, c + gridDim.x, ... of the panel (items of all
@@ -249,40 +191,49 @@ __global__ void __launch_bounds__(kThreads2, 1)
     if (lane == 0) {
       bool lost = false;
       int64_t cached_k = -1;
-      int cs = 0, cj = 0, ci0 = 0;
+      // per item (read from global memory once, when the item changes): the four split rows and
+      // the output tiles to prefetch; per step only the panel-column offset changes
+      const uint8_t* rowA0 = nullptr;
+      const uint8_t* rowA1 = nullptr;
+      const uint8_t* rowB0 = nullptr;
+      const uint8_t* rowB1 = nullptr;
+      const float* pre[4] = {nullptr, nullptr, nullptr, nullptr};
       uint32_t gc = 0;
       for (; gc < total; ++gc) {
         const int st = (int)(gc % kStages2);
-        if (gc >= (uint32_t)kStages2 && !wait(&free_bar[st], ((gc / kStages2) - 1) & 1u)) {
-          lost = true;
-          break;
-        }
         const int64_t k = gc / nq;
         const int q = (int)(gc % nq);
-        if (k != cached_k) {
+        if (k != cached_k) {   // decode before waiting: the loads overlap the MMAs still reading the stage
+          int cs = 0, cj = 0, ci0 = 0;
           decode(blockIdx.x + k * gridDim.x, cs, cj, ci0);
           cached_k = k;
-        }
-        const SubMeta& m = L.meta[cs];
-        const bool hasA1 = ci0 + 1 < m.R, hasB1 = cj + 1 < m.Bc;
-        const int64_t rbase = prow_off[cs];
-        if (q == 0) {   // the output tiles are read back by the epilogue after the last column
+          const SubMeta m = L.meta[cs];
+          const bool hasA1 = ci0 + 1 < m.R, hasB1 = cj + 1 < m.Bc;
+          const int64_t rbase = prow_off[cs];
+          rowA0 = split + (rbase + ci0) * kPanelTiles * (int64_t)kSplitTile;
+          rowA1 = split + (rbase + (hasA1 ? ci0 + 1 : ci0)) * kPanelTiles * (int64_t)kSplitTile;
+          rowB0 = split_b + (rbase + cj) * kPanelTiles * (int64_t)kSplitTile;
+          rowB1 = split_b + (rbase + (hasB1 ? cj + 1 : cj)) * kPanelTiles * (int64_t)kSplitTile;
 #pragma unroll
           for (int a = 0; a < 2; ++a)
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
               const int ti = ci0 + a, tj = cj + c;
-              if ((a == 0 || hasA1) && (c == 0 || hasB1) && (ti >= m.Bc || tj <= ti)) {
-                const float* tp = (const float*)L.tiles + m.tile_off + tile_index(ti, tj, m.Bc) * NB2;
-                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(tp), "r"((uint32_t)(NB2 * 4))
-                             : "memory");
-              }
+              pre[2 * a + c] = ((a == 0 || hasA1) && (c == 0 || hasB1) && (ti >= m.Bc || tj <= ti))
+                                   ? (const float*)L.tiles + m.tile_off + tile_index(ti, tj, m.Bc) * NB2
+                                   : nullptr;
             }
         }
-        const uint8_t* rowA0 = split + (rbase + ci0) * kPanelTiles * (int64_t)kSplitTile;
-        const uint8_t* rowA1 = split + (rbase + (hasA1 ? ci0 + 1 : ci0)) * kPanelTiles * (int64_t)kSplitTile;
-        const uint8_t* rowB0 = split_b + (rbase + cj) * kPanelTiles * (int64_t)kSplitTile;
-        const uint8_t* rowB1 = split_b + (rbase + (hasB1 ? cj + 1 : cj)) * kPanelTiles * (int64_t)kSplitTile;
+        if (gc >= (uint32_t)kStages2 && !wait(&free_bar[st], ((gc / kStages2) - 1) & 1u)) {
+          lost = true;
+          break;
+        }
+        if (q == 0)   // the output tiles are read back by the epilogue after the last column
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+            if (pre[t])
+              asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(pre[t]), "r"((uint32_t)(NB2 * 4))
+                           : "memory");
         uint8_t* sA = stage0 + st * kStage2;   // [A hi | A lo | B hi | B lo], 128 rows each
         uint8_t* sB = sA + 2 * kOpnd;
         mbar_expect_tx(&full_bar[st], kStage2);
