@@ -66,12 +66,15 @@ extern "C" {
 
 typedef struct bddc_handle_s* bddc_handle;
 
-/* Mesh of the first level (host pointers).  Element-local node order is lexicographic:
+/* Mesh of the first level (host pointers).  Element types (Sec. 4: hexahedra for the Stokes
+ * cavity, linear tetrahedra for the geocomposite elasticity problem):
  * Q1: local node a at reference position xi_d = 2*((a >> d) & 1) - 1 (2**dim nodes);
+ * linear simplex (triangle, tetrahedron; dim + 1 nodes, Poisson and elasticity): any vertex
+ *   order, either orientation (the element uses |det J|); degenerate simplices are invalid input;
  * Q2 (Stokes): a = ix + 3 iy + 9 iz at xi = (ix-1, iy-1, iz-1). */
 typedef struct {
   int dim;                  /* 2 or 3 */
-  int nodes_per_elem;       /* 4 (2D Q1), 8 (3D Q1) or 27 (Q2-Q1 Stokes) */
+  int nodes_per_elem;       /* 4 (2D Q1), 8 (3D Q1), 3 (triangle), 4 in 3D (tetrahedron) or 27 (Q2-Q1 Stokes) */
   int dofs_per_node;        /* 1 (Poisson), dim (elasticity) or 4 (Stokes) */
   int physics;              /* BDDC_POISSON | BDDC_ELASTICITY | BDDC_STOKES */
   int64_t n_nodes;

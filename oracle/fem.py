@@ -8,14 +8,18 @@ matrices" (Sec. 2, Eq. psi_def context).  Element types (Sec. 4): linear elastic
 the scalar model problem of the first workload, the Laplace operator.
 
 Element conventions
+  * Linear simplices (triangles, tetrahedra; Sec. 4's geocomposite mesh is made of linear
+    tetrahedra): constant gradients from the inverse of the vertex matrix, exact one-term
+    integration.
   * Q1 element on 2**dim nodes, local node a has reference position xi_a[d] = 2*bit_d(a) - 1
     (lexicographic order, x fastest); 2-point Gauss rule per direction.
   * Elasticity DOF order inside an element is (node a, component c) -> 3a + c; strains use
     Voigt order [xx, yy, zz, yz, xz, xy] with engineering shears; isotropic D with
     lambda = E nu / ((1+nu)(1-2nu)), mu = E / (2(1+nu)).
 
-Parity: pinned (closed-form 2D Laplace element, rigid-body null space, constant-strain
-energies, Poisson and elasticity patch tests) in ``tests/test_oracle_fem.py``.
+Parity: pinned (closed-form 2D Laplace element, closed-form reference-tetrahedron Laplace
+element, rigid-body null spaces, constant-strain energies, Poisson and elasticity patch tests on
+boxes and on jittered tetrahedral meshes) in ``tests/test_oracle_fem.py``.
 """
 from __future__ import annotations
 
@@ -107,6 +111,31 @@ def element_elasticity(X: np.ndarray, E: float, nu: float) -> np.ndarray:
     return K
 
 
+def p1_gradients(X: np.ndarray):
+    """Linear simplex (triangle / tetrahedron) with vertices X [dim+1, dim]: the shape functions
+    N_a(x) = c_a + g_a . x are fixed by N_a(x_b) = delta_ab, i.e. the coefficient columns are the
+    inverse of the vertex matrix M = [1 x_b^T] (rows b).  Returns (g [dim+1, dim], volume), the
+    volume being |det M| / dim!."""
+    dim = X.shape[1]
+    M = np.hstack([np.ones((dim + 1, 1)), X])
+    Cinv = np.linalg.inv(M)               # column a holds (c_a, g_a)
+    vol = abs(np.linalg.det(M)) / float(np.prod(np.arange(1, dim + 1)))
+    return Cinv[1:, :].T.copy(), vol
+
+
+def element_laplace_p1(X: np.ndarray, coef: float = 1.0) -> np.ndarray:
+    """K_e[a, b] = coef * vol * g_a . g_b on a linear simplex (the gradients are constant)."""
+    g, vol = p1_gradients(X)
+    return coef * vol * (g @ g.T)
+
+
+def element_elasticity_p1(X: np.ndarray, E: float, nu: float) -> np.ndarray:
+    """K_e = vol B^T D B on a linear tetrahedron (constant strain), DOF order 3a + c."""
+    g, vol = p1_gradients(X)
+    B = elasticity_B(g)
+    return vol * (B.T @ elasticity_D(E, nu) @ B)
+
+
 GAUSS3 = (np.array([-np.sqrt(0.6), 0.0, np.sqrt(0.6)]), np.array([5.0, 8.0, 5.0]) / 9.0)
 
 
@@ -157,6 +186,19 @@ def element_stokes(X: np.ndarray, nu: float = 1.0) -> np.ndarray:
     return K
 
 
+def unit_element(prob, X: np.ndarray) -> np.ndarray:
+    """Element matrix with unit coefficient for the Problem's element type: Q1 boxes (2**dim
+    nodes), linear simplices (dim + 1 nodes) or the Q2-Q1 hexahedron (Stokes)."""
+    simplex = prob.nodes_per_elem == prob.dim + 1
+    if prob.physics == 0:
+        return element_laplace_p1(X, 1.0) if simplex else element_laplace(X, 1.0)
+    if prob.physics == 1:
+        return element_elasticity_p1(X, 1.0, prob.nu) if simplex else element_elasticity(X, 1.0, prob.nu)
+    if prob.physics == 2:
+        return element_stokes(X, 1.0)
+    raise NotImplementedError("physics")
+
+
 def element_matrices(prob) -> np.ndarray:
     """All element matrices of a Problem, [n_elems, ne, ne], each scaled by its coefficient.
 
@@ -167,18 +209,7 @@ def element_matrices(prob) -> np.ndarray:
     shape_key = np.round(X - X[:, :1, :], 14).reshape(X.shape[0], -1)
     uniq, inv = np.unique(shape_key, axis=0, return_inverse=True)
     inv = inv.ravel()
-    unit = []
-    for u in range(uniq.shape[0]):
-        e = int(np.nonzero(inv == u)[0][0])
-        if prob.physics == 0:
-            unit.append(element_laplace(X[e], 1.0))
-        elif prob.physics == 1:
-            unit.append(element_elasticity(X[e], 1.0, prob.nu))
-        elif prob.physics == 2:
-            unit.append(element_stokes(X[e], 1.0))
-        else:
-            raise NotImplementedError("physics")
-    unit = np.stack(unit)
+    unit = np.stack([unit_element(prob, X[int(np.nonzero(inv == u)[0][0])]) for u in range(uniq.shape[0])])
     return unit[inv] * prob.coef[:, None, None]
 
 
@@ -195,13 +226,7 @@ def apply_K(prob, u_full: np.ndarray, chunk: int = 4096) -> np.ndarray:
     out = np.zeros_like(U)
     for u in range(uniq.shape[0]):
         els = np.nonzero(inv == u)[0]
-        e0 = int(els[0])
-        if prob.physics == 0:
-            K1 = element_laplace(X[e0], 1.0)
-        elif prob.physics == 1:
-            K1 = element_elasticity(X[e0], 1.0, prob.nu)
-        else:
-            K1 = element_stokes(X[e0], 1.0)
+        K1 = unit_element(prob, X[int(els[0])])
         for c0 in range(0, els.size, chunk):
             ec = els[c0:c0 + chunk]
             ue = U[ed[ec]]                                   # [ne_chunk, ne, k]

@@ -14,32 +14,42 @@ __device__ __forceinline__ int64_t tile_index(int i, int j, int Bc) {
   return i < Bc ? ((int64_t)i * (i + 1) / 2 + j) : ((int64_t)Bc * (Bc + 1) / 2 + (int64_t)(i - Bc) * Bc + j);
 }
 
-// One warp per element.  Q1 element with lexicographic local nodes, 2-point Gauss rule per
-// direction; the Gauss point g has reference coordinates xi_d = (2 bit_d(g) - 1)/sqrt(3).
-template <int DIM>
-__global__ void k_elem_q1(int physics, int64_t n_elems, const double* __restrict__ coords,
+// One warp per element.  Q1 element (SIMPLEX = false): lexicographic local nodes, 2-point Gauss
+// rule per direction; the Gauss point g has reference coordinates xi_d = (2 bit_d(g) - 1)/sqrt(3).
+// Linear simplex (SIMPLEX = true; triangles, tetrahedra): the affine map from the reference
+// simplex, N_0 = 1 - sum_d xi_d and N_a = xi_{a-1}, has constant gradients, so one point with
+// weight 1/DIM! (the reference volume) integrates the constant integrand exactly; |det J| makes
+// the element independent of its vertex orientation.
+template <int DIM, bool SIMPLEX>
+__global__ void k_elem_q1p1(int physics, int64_t n_elems, const double* __restrict__ coords,
                           const int32_t* __restrict__ conn, const double* __restrict__ coef, double nu,
                           const int32_t* __restrict__ slot_elem, double* __restrict__ ke) {
-  constexpr int NN = 1 << DIM;   // nodes = Gauss points
+  constexpr int NN = SIMPLEX ? DIM + 1 : 1 << DIM;   // nodes
+  constexpr int NG = SIMPLEX ? 1 : NN;               // quadrature points
   constexpr int WARPS = 4;
-  __shared__ double sG[WARPS][NN][NN][DIM];   // [gp][node][d] physical gradients
-  __shared__ double sW[WARPS][NN];            // detJ * weight
+  __shared__ double sG[WARPS][NG][NN][DIM];   // [gp][node][d] physical gradients
+  __shared__ double sW[WARPS][NG];            // detJ * weight
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t slot = (int64_t)blockIdx.x * WARPS + w;
   if (slot >= n_elems) return;
   const int64_t e = slot_elem[slot];
   const double gq = 0.57735026918962576451;   // 1/sqrt(3)
-  if (lane < NN) {
-    double xi[DIM];
-    for (int d = 0; d < DIM; ++d) xi[d] = ((lane >> d) & 1) ? gq : -gq;
+  if (lane < NG) {
     double G[NN][DIM];
-    for (int a = 0; a < NN; ++a)
-      for (int d = 0; d < DIM; ++d) {
-        double v = (((a >> d) & 1) ? 1.0 : -1.0) * 0.5;
-        for (int d2 = 0; d2 < DIM; ++d2)
-          if (d2 != d) v *= (1.0 + (((a >> d2) & 1) ? 1.0 : -1.0) * xi[d2]) * 0.5;
-        G[a][d] = v;
-      }
+    if (SIMPLEX) {
+      for (int a = 0; a < NN; ++a)
+        for (int d = 0; d < DIM; ++d) G[a][d] = a == 0 ? -1.0 : (a - 1 == d ? 1.0 : 0.0);
+    } else {
+      double xi[DIM];
+      for (int d = 0; d < DIM; ++d) xi[d] = ((lane >> d) & 1) ? gq : -gq;
+      for (int a = 0; a < NN; ++a)
+        for (int d = 0; d < DIM; ++d) {
+          double v = (((a >> d) & 1) ? 1.0 : -1.0) * 0.5;
+          for (int d2 = 0; d2 < DIM; ++d2)
+            if (d2 != d) v *= (1.0 + (((a >> d2) & 1) ? 1.0 : -1.0) * xi[d2]) * 0.5;
+          G[a][d] = v;
+        }
+    }
     double J[DIM][DIM];
     for (int d = 0; d < DIM; ++d)
       for (int d2 = 0; d2 < DIM; ++d2) {
@@ -75,7 +85,7 @@ __global__ void k_elem_q1(int physics, int64_t n_elems, const double* __restrict
         for (int d2 = 0; d2 < DIM; ++d2) s += G[a][d2] * inv[d2][d];
         sG[w][lane][a][d] = s;
       }
-    sW[w][lane] = det;
+    sW[w][lane] = SIMPLEX ? fabs(det) / (DIM == 2 ? 2.0 : 6.0) : det;
   }
   __syncwarp();
   const double E = coef[e];
@@ -83,7 +93,7 @@ __global__ void k_elem_q1(int physics, int64_t n_elems, const double* __restrict
     for (int idx = lane; idx < NN * NN; idx += 32) {
       int a = idx / NN, b = idx % NN;
       double s = 0.0;
-      for (int g = 0; g < NN; ++g) {
+      for (int g = 0; g < NG; ++g) {
         double d = 0.0;
         for (int k = 0; k < DIM; ++k) d += sG[w][g][a][k] * sG[w][g][b][k];
         s += sW[w][g] * d;
@@ -113,7 +123,7 @@ __global__ void k_elem_q1(int physics, int64_t n_elems, const double* __restrict
 #pragma unroll
         for (int j = 0; j < DIM; ++j) P[i][j] = 0.0;
 #pragma unroll 2
-      for (int g = 0; g < NN; ++g) {
+      for (int g = 0; g < NG; ++g) {
         const double wg = sW[w][g];
         double ga[DIM], gb[DIM];
 #pragma unroll
@@ -395,14 +405,19 @@ __global__ void k_weights(LevelDev L, int multiplicity) {
 
 }  // namespace
 
-void launch_elem_q1(int physics, int dim, int64_t n_elems, const double* coords, const int32_t* conn,
+void launch_elem_q1p1(int physics, int dim, int simplex, int64_t n_elems, const double* coords, const int32_t* conn,
                     const double* coef, double nu, const int32_t* slot_elem, double* ke, cudaStream_t st) {
   if (n_elems <= 0) return;
   const int blocks = (int)((n_elems + 3) / 4);
-  if (dim == 2)
-    { note_launch(); k_elem_q1<2><<<blocks, 128, 0, st>>>(physics, n_elems, coords, conn, coef, nu, slot_elem, ke); }
+  note_launch();
+  if (dim == 2 && simplex)
+    k_elem_q1p1<2, true><<<blocks, 128, 0, st>>>(physics, n_elems, coords, conn, coef, nu, slot_elem, ke);
+  else if (dim == 2)
+    k_elem_q1p1<2, false><<<blocks, 128, 0, st>>>(physics, n_elems, coords, conn, coef, nu, slot_elem, ke);
+  else if (simplex)
+    k_elem_q1p1<3, true><<<blocks, 128, 0, st>>>(physics, n_elems, coords, conn, coef, nu, slot_elem, ke);
   else
-    { note_launch(); k_elem_q1<3><<<blocks, 128, 0, st>>>(physics, n_elems, coords, conn, coef, nu, slot_elem, ke); }
+    k_elem_q1p1<3, false><<<blocks, 128, 0, st>>>(physics, n_elems, coords, conn, coef, nu, slot_elem, ke);
 }
 
 void launch_elem_q2q1(int64_t n_elems, const double* coords, const int32_t* conn, const double* coef,

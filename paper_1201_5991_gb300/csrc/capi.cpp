@@ -1249,8 +1249,8 @@ void numeric_setup(bddc_handle_s* h) {
       if (h->physics == BDDC_STOKES)
         launch_elem_q2q1(h->n_elems, h->d_coords, h->d_conn, h->d_coef, L.slot_elem, L.d.ke, st);
       else
-        launch_elem_q1(h->physics, h->dim, h->n_elems, h->d_coords, h->d_conn, h->d_coef, h->nu, L.slot_elem,
-                       L.d.ke, st);
+        launch_elem_q1p1(h->physics, h->dim, h->npe == h->dim + 1, h->n_elems, h->d_coords, h->d_conn, h->d_coef,
+                         h->nu, L.slot_elem, L.d.ke, st);
       if (h->has_lift)
         launch_lift(h->n_free, h->npe * h->ndof, h->d_lift_ptr, h->d_lift_slot, h->d_lift_a, L.d.ke, h->d_lift_ud,
                     h->d_lift, st);
@@ -1323,8 +1323,8 @@ void analysis(bddc_handle_s* h, const bddc_mesh* mesh, const bddc_partition* par
   if (mesh->physics == BDDC_STOKES) {
     if (mesh->dim != 3 || mesh->nodes_per_elem != 27 || mesh->dofs_per_node != 4)
       fail(BDDC_ERR_INVALID, "Stokes needs Q2-Q1 hexahedra: dim 3, 27 nodes per element, 4 DOFs per node");
-  } else if (mesh->nodes_per_elem != (1 << mesh->dim)) {
-    fail(BDDC_ERR_INVALID, "only Q1 elements (2**dim nodes)");
+  } else if (mesh->nodes_per_elem != (1 << mesh->dim) && mesh->nodes_per_elem != mesh->dim + 1) {
+    fail(BDDC_ERR_INVALID, "Poisson and elasticity take Q1 boxes (2**dim nodes) or linear simplices (dim + 1 nodes)");
   }
   if (mesh->physics == BDDC_ELASTICITY && (mesh->dim != 3 || mesh->dofs_per_node != 3))
     fail(BDDC_ERR_INVALID, "elasticity needs dim 3 and 3 DOFs per node");
@@ -1347,6 +1347,24 @@ void analysis(bddc_handle_s* h, const bddc_mesh* mesh, const bddc_partition* par
     if (!(h->coef[e] > 0.0)) fail(BDDC_ERR_INVALID, "coefficient must be positive (element " + std::to_string(e) + ")");
   for (int32_t p : h->conn)
     if (p < 0 || p >= h->n_nodes) fail(BDDC_ERR_INVALID, "connectivity references a missing node");
+  if (h->npe == h->dim + 1)   // linear simplices: a flat element has no inverse Jacobian
+    for (int64_t e = 0; e < h->n_elems; ++e) {
+      double J[3][3] = {{0}}, h2 = 0.0;
+      const double* x0 = &h->coords[(int64_t)h->conn[e * h->npe] * h->dim];
+      for (int a = 1; a <= h->dim; ++a) {
+        const double* xa = &h->coords[(int64_t)h->conn[e * h->npe + a] * h->dim];
+        for (int d = 0; d < h->dim; ++d) {
+          J[a - 1][d] = xa[d] - x0[d];
+          h2 = std::max(h2, std::fabs(J[a - 1][d]));
+        }
+      }
+      const double det = h->dim == 2 ? J[0][0] * J[1][1] - J[0][1] * J[1][0]
+                                     : J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                                           J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                                           J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+      if (!(std::fabs(det) > 1e-12 * std::pow(h2, h->dim)))
+        fail(BDDC_ERR_INVALID, "degenerate simplex (element " + std::to_string(e) + ")");
+    }
   h->free_of_full.assign(h->n_full, -1);
   h->n_free = 0;
   for (int64_t q = 0; q < h->n_full; ++q)

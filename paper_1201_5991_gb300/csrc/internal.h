@@ -110,8 +110,9 @@ struct GradView {
 };
 
 // ---------------------------------------------------------------- assembly (assemble.cu)
-void launch_elem_q1(int physics, int dim, int64_t n_elems, const double* coords, const int32_t* conn,
-                    const double* coef, double nu, const int32_t* slot_elem, double* ke, cudaStream_t st);
+// Q1 boxes (simplex = 0, 2**dim nodes) or linear simplices (simplex = 1, dim + 1 nodes)
+void launch_elem_q1p1(int physics, int dim, int simplex, int64_t n_elems, const double* coords, const int32_t* conn,
+                      const double* coef, double nu, const int32_t* slot_elem, double* ke, cudaStream_t st);
 void launch_elem_q2q1(int64_t n_elems, const double* coords, const int32_t* conn, const double* coef,
                       const int32_t* slot_elem, double* ke, cudaStream_t st);
 void launch_lift(int64_t n_free, int ne, const int64_t* lptr, const int32_t* lslot, const int32_t* la,

@@ -8,6 +8,9 @@ It only lays out the problem data that the paper's workloads are made of (Sec. 4
                           lexicographic with x fastest; element ids likewise; the local node
                           order inside an element is lexicographic too (a = ix + 2 iy + 4 iz).
 * ``box_mesh_q2``      -- the 27-node Q2 hex mesh used by the Taylor--Hood cavity problem.
+* ``simplex_mesh``     -- linear triangles / tetrahedra (Kuhn's split of the box lattice) with
+                          seeded interior-node jitter: the element type of the paper's
+                          geocomposite problem on an irregular, non-congruent mesh.
 * ``loguniform_coef``  -- per-element Young's modulus E = 10**(3 U), U ~ U[0,1) (seeded).
 * masks                -- clamped face x = 0, or the whole boundary.
 * ``box_body_load``    -- nodal load of a constant body force on axis-aligned box elements
@@ -119,6 +122,67 @@ def box_mesh_q2(n: int, length: float = 1.0):
     return coords.astype(np.float64), conn
 
 
+# Kuhn's split of the unit cube into six tetrahedra along the diagonal from corner 0 to corner 7
+# (corner a at bits (x, y, z) of a): tetrahedron pi runs 0 -> e_pi0 -> e_pi0 + e_pi1 -> 7 for a
+# permutation pi of the axes.  Every cube of a lattice split the same way gives a conforming mesh
+# (each square face is cut along the diagonal through its lowest corner in both cubes).
+_KUHN = [(0, 1 << p0, (1 << p0) | (1 << p1), 7)
+         for p0, p1 in ((0, 1), (0, 2), (1, 0), (1, 2), (2, 0), (2, 1))]
+
+
+def simplex_mesh(dim: int, n: int, jitter: float = 0.0, seed: int = 0, length: float = 1.0):
+    """Linear simplices on [0, length]^dim: the n^dim box lattice with every square cut into two
+    triangles along the diagonal from its corner 0 (2D) or every cube into Kuhn's six tetrahedra
+    (3D); interior nodes moved by U(-jitter, jitter) h per coordinate from default_rng(seed)
+    (boundary nodes stay on the boundary planes).  Every element is numbered with positive
+    orientation.  jitter < 0.25 keeps every element valid (checked)."""
+    coords, hexes = box_mesh(dim, n, length)
+    h = length / n
+    if jitter > 0.0:
+        inner = np.all((coords > 0.0) & (coords < length), axis=1)
+        d = np.random.default_rng(seed).uniform(-jitter, jitter, size=coords.shape) * h
+        coords = coords + d * inner[:, None]
+    split = _KUHN if dim == 3 else [(0, 1, 3), (0, 3, 2)]
+    conn = np.concatenate([hexes[:, list(t)] for t in split], axis=0)
+    order = np.argsort(np.tile(np.arange(hexes.shape[0]), len(split)), kind="stable")
+    conn = conn[order]                                    # the simplices of box e are 6e.. (3D)
+    E = coords[conn[:, 1:]] - coords[conn[:, :1]]
+    det = np.linalg.det(E)
+    flip = det < 0.0
+    conn[flip, 1], conn[flip, 2] = conn[flip, 2].copy(), conn[flip, 1].copy()
+    det = np.abs(det)
+    if not np.all(det > 1e-3 * h ** dim):
+        raise ValueError("jitter produced a degenerate simplex")
+    return coords, conn.astype(np.int32)
+
+
+def simplex_body_load(coords: np.ndarray, conn: np.ndarray, ndof: int, b) -> np.ndarray:
+    """Nodal load of a constant body force b on linear simplices: each of the dim + 1 vertices
+    receives vol / (dim + 1) of the element's force."""
+    dim = coords.shape[1]
+    b = np.asarray(b, dtype=np.float64).reshape(ndof)
+    vol = np.abs(np.linalg.det(coords[conn[:, 1:]] - coords[conn[:, :1]])) / math.factorial(dim)
+    f = np.zeros(coords.shape[0] * ndof)
+    w = np.repeat(vol / (dim + 1), conn.shape[1])
+    for c in range(ndof):
+        np.add.at(f, conn.ravel() * ndof + c, w * b[c])
+    return f
+
+
+def simplex_face_pairs(conn: np.ndarray):
+    """Pairs (ea, eb), ea < eb, of simplices sharing a facet (dim of their dim + 1 nodes)."""
+    nn = conn.shape[1]
+    facets = np.concatenate([np.sort(np.delete(conn, k, axis=1), axis=1) for k in range(nn)], axis=0)
+    owner = np.tile(np.arange(conn.shape[0]), nn)
+    _, inv = np.unique(facets, axis=0, return_inverse=True)
+    inv = inv.ravel()
+    order = np.argsort(inv, kind="stable")
+    si, so = inv[order], owner[order]
+    twin = np.nonzero(si[1:] == si[:-1])[0]               # interior facets appear twice
+    a, b = so[twin], so[twin + 1]
+    return np.minimum(a, b), np.maximum(a, b)
+
+
 def loguniform_coef(n_elems: int, seed: int, decades: float = 3.0) -> np.ndarray:
     """E_e = 10**(decades * U_e), U_e ~ U[0, 1) from default_rng(seed)."""
     u = np.random.default_rng(seed).random(n_elems)
@@ -213,24 +277,23 @@ def _nearest(points, centres, chunk=131072):
     return out
 
 
-def face_connected_fix(conn: np.ndarray, part: np.ndarray, dim: int) -> np.ndarray:
-    """Make every subdomain of a structured box mesh face-connected: each face-connected
-    component other than the largest (ties: the one holding the smallest element id) moves to
-    the face-adjacent subdomain with the smallest id.  Repeats until stable; empty labels are
-    then compacted.  Elements are lexicographic in an n^dim grid (as built by box_mesh)."""
+def face_connected_fix(conn: np.ndarray, part: np.ndarray, dim: int, pairs=None) -> np.ndarray:
+    """Make every subdomain face-connected: each face-connected component other than the
+    largest (ties: the one holding the smallest element id) moves to the face-adjacent
+    subdomain with the smallest id.  Repeats until stable; empty labels are then compacted.
+    ``pairs`` = (ea, eb) lists the face-adjacent element pairs; by default the elements are
+    taken as lexicographic in an n^dim box grid (as built by box_mesh)."""
     import scipy.sparse as sp
     from scipy.sparse.csgraph import connected_components
     part = part.astype(np.int64).copy()
     nel = conn.shape[0]
-    n = int(round(nel ** (1.0 / dim)))
-    idx = np.arange(nel).reshape((n,) * dim)
-    pairs = []
-    for ax in range(dim):
-        a = np.take(idx, np.arange(n - 1), axis=ax).ravel()
-        b = np.take(idx, np.arange(1, n), axis=ax).ravel()
-        pairs.append((a, b))
-    ea = np.concatenate([p[0] for p in pairs])
-    eb = np.concatenate([p[1] for p in pairs])
+    if pairs is None:
+        n = int(round(nel ** (1.0 / dim)))
+        idx = np.arange(nel).reshape((n,) * dim)
+        ea = np.concatenate([np.take(idx, np.arange(n - 1), axis=ax).ravel() for ax in range(dim)])
+        eb = np.concatenate([np.take(idx, np.arange(1, n), axis=ax).ravel() for ax in range(dim)])
+    else:
+        ea, eb = (np.asarray(x, dtype=np.int64) for x in pairs)
     for _ in range(100):
         same = part[ea] == part[eb]
         g = sp.coo_matrix((np.ones(int(same.sum())), (ea[same], eb[same])), shape=(nel, nel))
@@ -330,6 +393,58 @@ def elasticity3d_kmeans(n: int, nsub: int, ngroup: int, seed: int, seed2: int, k
         n_levels=3, constraints=CORNERS | EDGES | FACES)
 
 
+def elasticity3d_tet(n: int, nsub: int, seed: int, jitter: float = 0.2, ngroup: int = 0,
+                     nrhs: int = 1, kmeans_iters: int = 10) -> Problem:
+    """Elasticity on linear tetrahedra (the element of Sec. 4's geocomposite problem): Kuhn's
+    six tetrahedra per cube of the n^3 lattice, interior nodes jittered by U(-jitter, jitter) h
+    (default_rng(seed)), E_e log-uniform in [1, 1e3] (default_rng(seed + 1)), clamped at x = 0,
+    gravity (0, 0, -1); subdomains by seeded k-means of element centroids (made face-connected),
+    optionally grouped by k-means of subdomain centroids into ngroup level-2 subdomains (three
+    levels); corners + edge and face averages.  Load cases beyond the first add noise as in
+    ``elasticity3d``."""
+    coords, conn = simplex_mesh(3, n, jitter, seed)
+    coef = loguniform_coef(conn.shape[0], seed + 1)
+    dirichlet = mask_face_x0(coords, 3)
+    g = simplex_body_load(coords, conn, 3, [0.0, 0.0, -1.0])
+    f = np.repeat(g[:, None], nrhs, axis=1)
+    if nrhs > 1:
+        free = dirichlet == 0
+        nf = int(free.sum())
+        for k in range(nrhs):
+            f[free, k] += np.random.default_rng(seed + k).standard_normal(nf) / math.sqrt(nf)
+    cent = coords[conn].mean(axis=1)
+    p1 = kmeans(cent, nsub, seed, iters=kmeans_iters)
+    p1 = face_connected_fix(conn, p1, 3, simplex_face_pairs(conn))
+    ns = int(p1.max()) + 1
+    parts, n_parts = [p1], [ns]
+    if ngroup:
+        scent = np.stack([np.bincount(p1, weights=cent[:, d], minlength=ns) for d in range(3)], axis=1)
+        scent /= np.bincount(p1, minlength=ns)[:, None]
+        _, p2 = np.unique(kmeans(scent, ngroup, seed + 2), return_inverse=True)
+        parts.append(p2.astype(np.int32))
+        n_parts.append(int(p2.max()) + 1)
+    return Problem(
+        name=f"elasticity3d_tet_{n}_{ns}", dim=3, nodes_per_elem=4, dofs_per_node=3,
+        physics=ELASTICITY, coords=coords, conn=conn, coef=coef, nu=0.3, dirichlet=dirichlet,
+        f_full=f, parts=parts, n_parts=n_parts, n_levels=len(parts) + 1,
+        constraints=CORNERS | EDGES | FACES)
+
+
+def poisson2d_tri(n: int, nsub: int, seed: int, jitter: float = 0.2) -> Problem:
+    """-Laplace u = 1 on the unit square with linear triangles (two per square of the n^2
+    lattice, interior nodes jittered), homogeneous Dirichlet, nsub k-means subdomains (made
+    edge-connected), corners only, two levels."""
+    coords, conn = simplex_mesh(2, n, jitter, seed)
+    cent = coords[conn].mean(axis=1)
+    p1 = face_connected_fix(conn, kmeans(cent, nsub, seed, iters=10), 2, simplex_face_pairs(conn))
+    ns = int(p1.max()) + 1
+    return Problem(
+        name=f"poisson2d_tri_{n}_{ns}", dim=2, nodes_per_elem=3, dofs_per_node=1, physics=POISSON,
+        coords=coords, conn=conn, coef=np.ones(conn.shape[0]), nu=0.0,
+        dirichlet=mask_boundary(coords, 1), f_full=simplex_body_load(coords, conn, 1, [1.0])[:, None],
+        parts=[p1], n_parts=[ns], n_levels=2, constraints=CORNERS)
+
+
 def stokes_cavity(n: int, nsub: int, groups=(), lid=(1.0 / math.sqrt(3.0), math.sqrt(2.0 / 3.0), 0.0)) -> Problem:
     """3D lid-driven cavity (Sec. 4): Taylor-Hood Q2-Q1 hexes n^3 on the unit cube, viscosity 1,
     zero velocity on every face except z = 1, where the lid velocity is prescribed on all its
@@ -381,6 +496,8 @@ def config(name: str) -> Problem:
         return elasticity3d_kmeans(96, 512, 8, seed=3, seed2=33, kmeans_iters=20)
     if name == "elasticity3d_64_16rhs":
         return elasticity3d(64, 8, seed=5, nrhs=16)
+    if name == "elasticity3d_tet_48":          # cfg2's node lattice as 663,552 jittered tetrahedra, 64 k-means subdomains
+        return elasticity3d_tet(48, 64, seed=2)
     if name == "stokes_cavity_32":             # 512 subdomains of 4^3, two levels
         return stokes_cavity(32, 8)
     if name == "stokes_cavity_32_3lev":        # 512 / 64 / 1

@@ -79,6 +79,9 @@ CASES = {
     "elast8_3lev": (lambda: meshgen.elasticity3d(8, 4, seed=0, group=2), 3),
     "elast6_corners": (lambda: meshgen.elasticity3d(6, 2, seed=1, constraints=meshgen.CORNERS), 2),
     "kmeans_small": (lambda: meshgen.elasticity3d_kmeans(12, 24, 3, seed=3, seed2=33), 3),
+    "tri_kmeans": (lambda: meshgen.poisson2d_tri(16, 6, seed=2), 2),   # linear triangles
+    "tet_kmeans": (lambda: meshgen.elasticity3d_tet(6, 10, seed=1), 2),   # jittered linear tetrahedra
+    "tet_3lev": (lambda: meshgen.elasticity3d_tet(8, 24, seed=3, ngroup=3), 3),
     "stokes6": (lambda: meshgen.stokes_cavity(6, 3), 2),              # velocities before pressures
     "stokes8_3lev": (lambda: meshgen.stokes_cavity(8, 4, (2,)), 3),
 }
@@ -166,6 +169,22 @@ def test_stokes_mesh_validation():
     p = meshgen.stokes_cavity(2, 1)
     p.nodes_per_elem = 8
     p.conn = p.conn[:, :8]
+    with pytest.raises(capi.BddcError) as ei:
+        solver.analyze(p)
+    assert ei.value.code == capi.ERR_INVALID
+
+
+def test_degenerate_simplex_is_rejected():
+    p = meshgen.elasticity3d_tet(2, 2, seed=0)
+    p.conn = p.conn.copy()
+    p.conn[5, 3] = p.conn[5, 2]              # two equal vertices: a flat tetrahedron
+    with pytest.raises(capi.BddcError) as ei:
+        solver.analyze(p)
+    assert ei.value.code == capi.ERR_INVALID
+    assert "element 5" in capi.lib().bddc_last_error().decode()
+    p = meshgen.elasticity3d_tet(2, 2, seed=0)
+    p.nodes_per_elem = 5                     # neither a box nor a simplex
+    p.conn = np.hstack([p.conn, p.conn[:, :1]])
     with pytest.raises(capi.BddcError) as ei:
         solver.analyze(p)
     assert ei.value.code == capi.ERR_INVALID

@@ -11,6 +11,8 @@ SMALL = {
     "poisson": lambda: meshgen.poisson2d(16, 4),
     "elast": lambda: meshgen.elasticity3d(6, 2, seed=1),
     "elast_corners": lambda: meshgen.elasticity3d(6, 2, seed=1, constraints=meshgen.CORNERS),
+    "tet": lambda: meshgen.elasticity3d_tet(5, 6, seed=1),
+    "tri": lambda: meshgen.poisson2d_tri(16, 6, seed=2),
 }
 
 

@@ -177,3 +177,105 @@ def test_matrix_free_apply_equals_assembled_product(mk):
     p = mk()
     u = np.random.default_rng(2).standard_normal(p.n_nodes * p.dofs_per_node)
     np.testing.assert_allclose(fem.apply_K(p, u, chunk=7), fem.assemble(p) @ u, rtol=0, atol=1e-12)
+
+
+# ---------------------------------------------------------------- linear simplices (Sec. 4's tetrahedra)
+def test_p1_laplace_reference_simplices_closed_form():
+    # Textbook element matrices of the reference triangle and tetrahedron: the gradients are
+    # (-1,-1), (1,0), (0,1) (resp. the 3D analogues) times the area 1/2 (volume 1/6).
+    K2 = fem.element_laplace_p1(np.array([[0, 0], [1, 0], [0, 1]], float))
+    np.testing.assert_allclose(K2, np.array([[2, -1, -1], [-1, 1, 0], [-1, 0, 1]]) / 2.0, atol=1e-15)
+    K3 = fem.element_laplace_p1(np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], float), 3.0)
+    ref = np.array([[3, -1, -1, -1], [-1, 1, 0, 0], [-1, 0, 1, 0], [-1, 0, 0, 1]]) / 6.0
+    np.testing.assert_allclose(K3, 3.0 * ref, atol=1e-15)
+    # an equilateral triangle of side s has K_ab = (2 delta_ab - 1 + delta_ab) / (2 sqrt 3)
+    # (cotangent formula: off-diagonal -cot(60)/2 = -1/(2 sqrt 3), diagonal 2 / (2 sqrt 3))
+    s = 1.7
+    T = np.array([[0, 0], [s, 0], [s / 2, s * np.sqrt(3) / 2]])
+    Ke = fem.element_laplace_p1(T)
+    np.testing.assert_allclose(Ke, (3 * np.eye(3) - 1) / (2 * np.sqrt(3)), atol=1e-14)
+    # node order and orientation do not matter
+    perm = [2, 0, 1]
+    np.testing.assert_allclose(fem.element_laplace_p1(T[perm]), Ke[np.ix_(perm, perm)], atol=1e-14)
+
+
+def _tet(rng):
+    X = rng.standard_normal((4, 3))
+    return X if np.linalg.det(X[1:] - X[0]) != 0 else _tet(rng)
+
+
+def test_p1_elasticity_rigid_null_space_and_rank():
+    X = _tet(np.random.default_rng(7))
+    K = fem.element_elasticity_p1(X, 2.0, 0.3)
+    np.testing.assert_allclose(K, K.T, atol=1e-12 * np.abs(K).max())
+    ev = np.linalg.eigvalsh(K)
+    assert np.sum(np.abs(ev) < 1e-10 * ev.max()) == 6      # 12 DOFs - 6 constant strains
+    assert ev.min() > -1e-10 * ev.max()
+    for t in np.eye(3):
+        assert np.linalg.norm(K @ np.tile(t, 4)) < 1e-10 * np.abs(K).max()
+    for w in np.eye(3):
+        assert np.linalg.norm(K @ np.cross(w, X).ravel()) < 1e-10 * np.abs(K).max()
+
+
+def test_p1_elasticity_constant_strain_energy():
+    # u = G x: strain eps = sym(G) is exact on a linear element, so
+    # 0.5 u^T K u = vol * (lam/2 tr(eps)^2 + mu eps:eps)
+    rng = np.random.default_rng(9)
+    X = _tet(rng)
+    vol = abs(np.linalg.det(X[1:] - X[0])) / 6.0
+    E, nu = 3.0, 0.25
+    lam, mu = E * nu / ((1 + nu) * (1 - 2 * nu)), E / (2 * (1 + nu))
+    G = rng.standard_normal((3, 3))
+    eps = 0.5 * (G + G.T)
+    u = (X @ G.T).ravel()
+    dens = 0.5 * lam * np.trace(eps) ** 2 + mu * np.sum(eps * eps)
+    K = fem.element_elasticity_p1(X, E, nu)
+    np.testing.assert_allclose(0.5 * u @ K @ u, vol * dens, rtol=1e-12)
+
+
+def test_simplex_meshes_are_conforming_and_fill_the_box():
+    for dim, n in ((2, 5), (3, 3)):
+        coords, conn = meshgen.simplex_mesh(dim, n, jitter=0.2, seed=4)
+        E = coords[conn[:, 1:]] - coords[conn[:, :1]]
+        vol = np.linalg.det(E) / (2.0 if dim == 2 else 6.0)
+        assert np.all(vol > 0)                                 # positively oriented
+        np.testing.assert_allclose(vol.sum(), 1.0, atol=1e-13)
+        ea, eb = meshgen.simplex_face_pairs(conn)
+        n_bnd = (dim + 1) * conn.shape[0] - 2 * ea.size        # facets with one owner
+        assert n_bnd == (2 * dim * n ** (dim - 1) * (2 if dim == 3 else 1))
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_p1_patch_tests_on_jittered_meshes(dim):
+    # homogeneous material, f = 0 and a linear field prescribed on the whole boundary: a
+    # linear-element solution on any valid mesh reproduces it exactly at the interior nodes
+    rng = np.random.default_rng(5)
+    if dim == 2:
+        p = meshgen.poisson2d_tri(6, 4, seed=3)
+        uex = 1.0 + p.coords @ rng.standard_normal(2)
+    else:
+        p = meshgen.elasticity3d_tet(3, 2, seed=3)
+        p.coef = np.full(p.n_elems, 2.5)            # homogeneous: the linear field is in equilibrium
+        p.dirichlet = meshgen.mask_boundary(p.coords, 3)
+        uex = (rng.standard_normal(3)[None, :] + p.coords @ rng.standard_normal((3, 3)).T).ravel()
+    p.f_full = np.zeros_like(p.f_full)
+    p.dir_values = uex.copy()
+    u = fem.direct_solve(p)[:, 0]
+    np.testing.assert_allclose(u, uex[p.free], atol=1e-11)
+
+
+def test_simplex_body_load_and_partition():
+    p = meshgen.elasticity3d_tet(4, 6, seed=2)
+    np.testing.assert_allclose(p.f_full[:, 0].reshape(-1, 3).sum(axis=0), [0, 0, -1.0], atol=1e-13)
+    # every subdomain face-connected (a facet-sharing chain joins its elements rigidly)
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import connected_components
+    ea, eb = meshgen.simplex_face_pairs(p.conn)
+    part = p.parts[0]
+    for s in range(p.n_parts[0]):
+        els = np.nonzero(part == s)[0]
+        loc = -np.ones(p.n_elems, dtype=np.int64)
+        loc[els] = np.arange(els.size)
+        keep = (part[ea] == s) & (part[eb] == s)
+        g = sp.coo_matrix((np.ones(int(keep.sum())), (loc[ea[keep]], loc[eb[keep]])), shape=(els.size,) * 2)
+        assert connected_components(g, directed=False)[0] == 1
