@@ -132,6 +132,10 @@ __global__ void __launch_bounds__(kThreads, 2)
       const int j = BWD ? (B1 - 1 - k) : (B0 + k);
       return BWD ? tiles + tile_index(j, i, m.Bc) * NB2 : tiles + tile_index(i, j, m.Bc) * NB2;
     };
+    // the task's own right-hand side block depends on no other task: read it into rhs now, off
+    // the chain of dependent rows (the diagonal step subtracts the updates in place)
+    for (int e = tid; e < NR * NB; e += kThreads) rhs[e / NB][e % NB] = __ldcg(v + (e / NB) * vstride + i * NB + e % NB);
+    __syncthreads();
     // prologue: fill the ring
     if (tid == 0) {
       const int pre = ntile < S ? ntile : S;
@@ -243,7 +247,7 @@ __global__ void __launch_bounds__(kThreads, 2)
               T a = acc[r][q];
 #pragma unroll
               for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-              if (lane == 0) rhs[q][warp + 8 * r] = __ldcg(v + q * vstride + i * NB + warp + 8 * r) - a;
+              if (lane == 0) rhs[q][warp + 8 * r] -= a;
             }
           __syncthreads();
           const bool signed_rows = L.indefinite != 0;   // forward output is S L^{-1} b
@@ -274,7 +278,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             T a = (T)0;
 #pragma unroll
             for (int w = 0; w < kThreads / 32; ++w) a += red[w][q][c];
-            rhs[q][c] = __ldcg(v + q * vstride + i * NB + c) - a;
+            rhs[q][c] -= a;
           }
           __syncthreads();
           T p[NR][2];
