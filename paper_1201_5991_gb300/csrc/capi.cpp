@@ -147,8 +147,8 @@ struct Level {
   int sweep_ctas[2] = {2, 2};
   int sweep_deep[2] = {1, 1};
   int sweep_order[2] = {0, 0};
-  int* ctrl = nullptr;
-  int n_ctrl = 0;
+  int* ctrl = nullptr;         // task counter of the sweeps
+  void* pub = nullptr;         // sweep publication buffer: n_vec x min(blk, 8) words of the factor's type
   int64_t* rows[3] = {nullptr, nullptr, nullptr};   // interior rows, interface rows, all rows
   int64_t nrows[3] = {0, 0, 0};
   int32_t* crow_sub = nullptr;                      // subdomain of every constraint row
@@ -197,6 +197,7 @@ void alloc_level_work(Level& L, DevArena& A, int blk) {
     L.locA = A.alloc<double>(nv);
     L.locB = A.alloc<double>(nv);
   }
+  L.pub = A.alloc<double>(L.n_vec * std::min(blk, 8));
   L.dl0 = A.alloc<double>(nv);
   L.dl1 = A.alloc<double>(nv);
   L.dl2 = A.alloc<double>(nv);
@@ -818,8 +819,7 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
         }
       }
   }
-  L.n_ctrl = (int)(1 + L.dinv_elems / NB2);
-  L.ctrl = A.alloc<int>(L.n_ctrl);
+  L.ctrl = A.alloc<int>(1);   // task counter of the sweeps
   {
     std::vector<int64_t> rl[3];
     std::vector<int32_t> cs;
@@ -950,7 +950,7 @@ void trsv_one(bddc_handle_s* h, Level& L, T* v, int part, int backward, cudaStre
   ProfScope ps(h, L.coarsest ? BDDC_PROF_COARSE : part == 0 ? BDDC_PROF_TRSV : BDDC_PROF_TRSV_IFACE,
                groups * (copy32 ? 0.5 * L.trsv_bytes[part] : L.trsv_bytes[part]), 0.0, st);
   launch_sweep<T>(copy32 ? L.d32 : L.d, v, (L.sweep_order[part] ? L.tasks_big : L.tasks)[part][backward], L.ntasks[part][backward],
-                  part, backward, L.ctrl, L.n_ctrl, h->grid_max / 2 * L.sweep_ctas[part], L.sweep_deep[part], st, nb);
+                  part, backward, L.ctrl, L.pub, h->grid_max / 2 * L.sweep_ctas[part], L.sweep_deep[part], st, nb);
 }
 
 template <typename T>
@@ -2562,7 +2562,7 @@ int bddc_batching_ablation(bddc_handle h, double* ms) {
     for (int dir = 0; dir < 2; ++dir)
       for (int64_t s = 0; s < (int64_t)L.meta.size(); ++s) {
         const int o0 = L.task_sub_off[dir][s], o1 = L.task_sub_off[dir][s + 1];
-        launch_sweep<float>(L.d, v, L.tasks_by_sub[dir] + o0, o1 - o0, 0, dir, L.ctrl, L.n_ctrl, grid,
+        launch_sweep<float>(L.d, v, L.tasks_by_sub[dir] + o0, o1 - o0, 0, dir, L.ctrl, L.pub, grid,
                             L.sweep_deep[0], st);
       }
     ck(cudaEventRecord(b, st), "cudaEventRecord");

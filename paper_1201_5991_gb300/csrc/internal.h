@@ -160,14 +160,15 @@ void launch_coarse_inverse(const LevelDev& L, int64_t npad, float* W, cudaStream
 void launch_coarse_apply(const float* W, int64_t npad, const float* x, float* y, int64_t n_vec, int nr,
                          cudaStream_t st);
 // sweep.cu: forward (backward = 0) or backward triangular sweep over part 0 (interior
-// block rows) or part 1 (interface block rows) of every subdomain; ctrl has n_ctrl ints.
+// block rows) or part 1 (interface block rows) of every subdomain; ctrl is the task counter and
+// pub a publication buffer of n_vec x min(nr, 8) words of T (both reset by the launch).
 // Solve-phase launches take nr right-hand sides (default 1); a block of them stores its columns one
 // after another, each vector kind with its own length as the stride (local vectors n_vec,
 // interface vectors n_iface, level vectors n_dof, coarse vectors n_coarse, per-subdomain coarse
 // vectors sum nc).  The factor-streaming kernels read each factor tile once per group of columns.
 template <typename T>
 void launch_sweep(const LevelDev& L, T* vec, const int2* tasks, int ntasks, int part, int backward, int* ctrl,
-                  int n_ctrl, int grid_max, int deep, cudaStream_t st, int nr = 1);
+                  void* pub, int grid_max, int deep, cudaStream_t st, int nr = 1);
 // crow_sub: subdomain of every constraint row (flat over the level); t, mu: scratch [nr][total_rows]
 template <typename T>
 void launch_constraint_corr(const LevelDev& L, T* vec, const int32_t* crow_sub, int64_t total_rows, double* t,

@@ -9,9 +9,13 @@
 // dependency order (all subdomains' first rows, then their second rows, ...).  A task
 // streams its row of NB x NB tiles (forward) or its column of tiles (backward) into a ring of
 // shared-memory stages with cp.async.bulk, completion tracked by mbarriers, while the solution
-// blocks it depends on are published by other CTAs through per-row ready flags
-// (release/acquire).  A task only waits for tasks handed out before it, so the scheme cannot
-// deadlock whatever the residency.  Every wait is bounded; a timeout sets status[2] and the
+// blocks it depends on are published by other CTAs in a publication buffer that is filled with
+// all-ones words before the launch: a block is ready when none of its words is all-ones any
+// more (every word is written once, atomically, and no arithmetic result has that NaN bit
+// pattern: NaN results are canonical, and a computed all-ones word is published as the
+// canonical NaN).  The consumer polls the data itself, one L2 round trip instead of a flag
+// acquire followed by the data load, and the producer needs no fence.  A task only waits for
+// tasks handed out before it, so the scheme cannot deadlock whatever the residency.  Every wait is bounded; a timeout sets status[2] and the
 // kernel finishes without waiting further (the host reports BDDC_ERR_TIMEOUT).  A row-flag wait
 // that gives up stages the block as it is and goes on, so every tile copy is still consumed and
 // no access leaves the task's own rows; a tile wait that gives up drains the ring before exit.
@@ -67,8 +71,28 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
   return v;
 }
 
-__device__ __forceinline__ void st_release(int* p, int v) {
-  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+// publication words: relaxed (coherent at L2) loads and stores; all-ones = not yet written
+__device__ __forceinline__ bool pub_ld2(const float* p, float2& v) {
+  uint32_t a, b;
+  asm volatile("ld.relaxed.gpu.global.v2.b32 {%0, %1}, [%2];" : "=r"(a), "=r"(b) : "l"(p) : "memory");
+  v = make_float2(__uint_as_float(a), __uint_as_float(b));
+  return a != 0xFFFFFFFFu && b != 0xFFFFFFFFu;
+}
+__device__ __forceinline__ bool pub_ld2(const double* p, double2& v) {
+  unsigned long long a, b;
+  asm volatile("ld.relaxed.gpu.global.v2.b64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
+  v = make_double2(__longlong_as_double((long long)a), __longlong_as_double((long long)b));
+  return a != ~0ull && b != ~0ull;
+}
+__device__ __forceinline__ void pub_st(float* p, float x) {
+  uint32_t a = __float_as_uint(x);
+  if (a == 0xFFFFFFFFu) a = 0x7FFFFFFFu;
+  asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(a) : "memory");
+}
+__device__ __forceinline__ void pub_st(double* p, double x) {
+  unsigned long long a = (unsigned long long)__double_as_longlong(x);
+  if (a == ~0ull) a = 0x7FFFFFFFFFFFFFFFull;
+  asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(a) : "memory");
 }
 
 template <typename T>
@@ -89,7 +113,7 @@ struct Vec2<double> {
 template <typename T, int S, bool BWD, int NR>
 __global__ void __launch_bounds__(kThreads, 2)
     k_sweep(LevelDev L, T* __restrict__ vec, int64_t vstride, const int2* __restrict__ tasks, int ntasks, int part,
-            int* __restrict__ ctrl) {
+            int* __restrict__ ctrl, T* pub) {
   using V2 = typename Vec2<T>::type;
   constexpr int YS = NR == 1 ? kYSlots : (NR == 2 ? 8 : 4);   // solution blocks staged at a time
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -99,9 +123,9 @@ __global__ void __launch_bounds__(kThreads, 2)
   __shared__ T red[kThreads / 32][NR][NB];
   __shared__ __align__(16) T rhs[NR][NB];
   __shared__ T s_sg[NB];                         // pivot signs of the task's block row (indefinite)
-  __shared__ int s_task, s_ready;
+  __shared__ int s_task;
+  __shared__ int s_rdy[kYSlots];                 // poll result per candidate block
   int* counter = ctrl;
-  int* flags = ctrl + 1;
   int* status = L.status;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
@@ -125,8 +149,8 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int ntile = nL + 1;
     const T* tiles = (const T*)L.tiles + m.tile_off;
     const T* dinv = (const T*)L.dinv + m.dinv_off + (int64_t)i * NB2;
-    const int fbase = (int)(m.dinv_off / NB2);   // flags of this subdomain's block rows
     T* v = vec + m.vec_off;
+    T* pv = pub + m.vec_off;   // this subdomain's published blocks (same layout as v)
     auto tile_src = [&](int k) -> const T* {
       if (k == nL) return dinv;
       const int j = BWD ? (B1 - 1 - k) : (B0 + k);
@@ -157,46 +181,47 @@ __global__ void __launch_bounds__(kThreads, 2)
     int staged_end = 0;   // tiles [staged_begin, staged_end) have their solution block in ybuf
     for (int k = 0; k < ntile; ++k) {
       if (k < nL && k >= staged_end) {
-        // wait until the next solution blocks are published, then stage up to YS of them
-        if (warp == 0) {
-          int ready = 0;
-          long long spins = 0;
-          for (;;) {
-            // tile k+q needs block j(k+q); poll 32 of them at once
-            const int q = lane;
-            int ok = 1;
-            if (k + q < nL) {
-              const int j = BWD ? (B1 - 1 - (k + q)) : (B0 + k + q);
-              // the timeout probe polls a word that nothing sets (status[3]) instead of the row flag
-              ok = ld_acquire(L.wait_probe ? status + 3 : flags + fbase + j) != 0;
-            } else {
-              ok = 0;
+        // wait until the next solution blocks are published, then stage up to YS of them: warp w
+        // polls blocks k + w and k + w + 8 (all their words at once), writes the ready ones into
+        // ybuf, and the consecutive ready blocks from k are staged
+        const int want = nL - k < YS ? nL - k : YS;
+        int cnt = 0;
+        long long spins = 0;
+        for (;;) {
+          __syncthreads();   // every thread has read s_rdy of the previous poll
+          for (int b = warp; b < want; b += kThreads / 32) {
+            const int j = BWD ? (B1 - 1 - (k + b)) : (B0 + k + b);
+            V2 y[NR];
+            bool ok = true;
+#pragma unroll
+            for (int q = 0; q < NR; ++q) ok &= pub_ld2(pv + q * vstride + j * NB + 2 * lane, y[q]);
+            // the timeout probe waits for a word that nothing sets (status[3]) instead
+            if (L.wait_probe) ok = ld_acquire(status + 3) != 0;
+            ok = __all_sync(0xffffffffu, ok);
+            if (ok) {
+              V2 sg = {(T)1, (T)1};
+              if (!BWD && L.indefinite)   // solved rows hold S_j y_j: the update needs y_j
+                sg = *(const V2*)((const T*)L.sgn + m.vec_off + (int64_t)j * NB + 2 * lane);
+#pragma unroll
+              for (int q = 0; q < NR; ++q) {
+                y[q].x *= sg.x;
+                y[q].y *= sg.y;
+                *(V2*)&ybuf[(k + b) % YS][q][2 * lane] = y[q];
+              }
             }
-            const unsigned bal = __ballot_sync(0xffffffffu, ok);
-            ready = __ffs(~bal) - 1;          // consecutive ready tiles from k
-            if (bal == 0xffffffffu) ready = 32;
-            if (ready > 0) break;
-            if (++spins > (L.wait_probe ? kProbeSpins : kSpinLimit)) {
-              if (lane == 0) atomicExch(status + 2, 1);
-              ready = 1;
-              break;
-            }
-            __nanosleep(64);
+            if (lane == 0) s_rdy[b] = ok ? 1 : 0;
           }
-          if (lane == 0) s_ready = ready < YS ? ready : YS;
+          __syncthreads();
+          cnt = 0;
+          while (cnt < want && s_rdy[cnt]) ++cnt;
+          if (cnt > 0) break;
+          if (++spins > (L.wait_probe ? kProbeSpins : kSpinLimit)) {
+            if (tid == 0) atomicExch(status + 2, 1);
+            cnt = 1;   // stage the block as it is and go on (error path)
+            break;
+          }
+          __nanosleep(64);
         }
-        __syncthreads();
-        const int cnt = s_ready;
-        for (int e = tid; e < cnt * NR * NB; e += kThreads) {
-          const int kk = k + e / (NR * NB);
-          const int q = (e / NB) % NR, c = e % NB;
-          const int j = BWD ? (B1 - 1 - kk) : (B0 + kk);
-          T yj = __ldcg(v + q * vstride + j * NB + c);
-          if (!BWD && L.indefinite)   // solved rows hold S_j y_j: the update needs y_j
-            yj *= ((const T*)L.sgn)[m.vec_off + (int64_t)j * NB + c];
-          ybuf[kk % YS][q][c] = yj;
-        }
-        __syncthreads();
         staged_end = k + cnt;
       }
       // wait for the tile
@@ -262,10 +287,13 @@ __global__ void __launch_bounds__(kThreads, 2)
               T yv = a[r].x * rv.x + a[r].y * rv.y;
 #pragma unroll
               for (int o = 16; o > 0; o >>= 1) yv += __shfl_xor_sync(0xffffffffu, yv, o);
-              if (lane == 0) v[q * vstride + i * NB + warp + 8 * r] = signed_rows ? yv * s_sg[warp + 8 * r] : yv;
+              if (lane == 0) {
+                const T out = signed_rows ? yv * s_sg[warp + 8 * r] : yv;
+                v[q * vstride + i * NB + warp + 8 * r] = out;
+                pub_st(pv + q * vstride + i * NB + warp + 8 * r, out);
+              }
             }
           }
-          if (lane == 0) __threadfence();
         } else {
 #pragma unroll
           for (int q = 0; q < NR; ++q) {
@@ -307,8 +335,8 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
             for (int w = 0; w < kThreads / 32; ++w) a += red[w][q][c];
             v[q * vstride + i * NB + c] = a;
+            pub_st(pv + q * vstride + i * NB + c, a);
           }
-          __threadfence();
         }
       }
       __syncthreads();   // every thread is done with this stage
@@ -319,11 +347,6 @@ __global__ void __launch_bounds__(kThreads, 2)
         bulk_g2s(stage + ns * NB2, tile_src(k + S), (uint32_t)(NB2 * sizeof(T)), &full[ns]);
         ++issued;
       }
-    }
-    // publish the solution block of row i (every right-hand side)
-    if (tid == 0) {
-      __threadfence();
-      st_release(flags + fbase + i, 1);
     }
   }
   // After a lost tile wait, copies may still be in flight into this CTA's shared memory:
@@ -339,11 +362,12 @@ __global__ void __launch_bounds__(kThreads, 2)
 
 }  // namespace
 
-// Task lists and control words live in the level (see capi.cpp); this entry launches one
-// sweep.  ctrl = [counter, flags...] must be zeroed before the launch (memset in the stream).
+// Task lists, control words and the publication buffer live in the level (see capi.cpp); this
+// entry launches one sweep.  ctrl[0] (the task counter) must be zero and pub all-ones over the
+// columns of the launch (memsets in the stream).
 template <typename T, int S, int NR>
 void launch_sweep_s(const LevelDev& L, T* vec, const int2* tasks, int ntasks, int part, int backward, int* ctrl,
-                    int grid, cudaStream_t st) {
+                    T* pub, int grid, cudaStream_t st) {
   const size_t dyn = (size_t)S * NB2 * sizeof(T);
   static bool attr = false;
   if (!attr) {
@@ -351,59 +375,60 @@ void launch_sweep_s(const LevelDev& L, T* vec, const int2* tasks, int ntasks, in
     cudaFuncSetAttribute(k_sweep<T, S, true, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     attr = true;
   }
+  cudaMemsetAsync(ctrl, 0, sizeof(int), st);
+  cudaMemsetAsync(pub, 0xFF, sizeof(T) * (size_t)L.n_vec * NR, st);
   note_launch();
   if (backward)
-    k_sweep<T, S, true, NR><<<grid, kThreads, dyn, st>>>(L, vec, L.n_vec, tasks, ntasks, part, ctrl);
+    k_sweep<T, S, true, NR><<<grid, kThreads, dyn, st>>>(L, vec, L.n_vec, tasks, ntasks, part, ctrl, pub);
   else
-    k_sweep<T, S, false, NR><<<grid, kThreads, dyn, st>>>(L, vec, L.n_vec, tasks, ntasks, part, ctrl);
+    k_sweep<T, S, false, NR><<<grid, kThreads, dyn, st>>>(L, vec, L.n_vec, tasks, ntasks, part, ctrl, pub);
 }
 
 template <typename T, int S>
 void launch_sweep_nr(const LevelDev& L, T* vec, const int2* tasks, int ntasks, int part, int backward, int* ctrl,
-                     int n_ctrl, int grid, int nr, cudaStream_t st) {
+                     T* pub, int grid, int nr, cudaStream_t st) {
   // right-hand sides in groups of up to 8 (FP32) / 4 (FP64), each group one launch over the factor
   constexpr int kMaxNR = sizeof(T) == 4 ? 8 : 4;
   for (int r0 = 0; r0 < nr;) {
     const int left = nr - r0;
     const int g = left >= kMaxNR ? kMaxNR : left >= 4 ? 4 : left >= 2 ? 2 : 1;
-    if (r0 > 0) cudaMemsetAsync(ctrl, 0, sizeof(int) * (size_t)n_ctrl, st);
     T* v = vec + (int64_t)r0 * L.n_vec;
     if (g == 8)
-      launch_sweep_s<T, S, (sizeof(T) == 4 ? 8 : 4)>(L, v, tasks, ntasks, part, backward, ctrl, grid, st);
+      launch_sweep_s<T, S, (sizeof(T) == 4 ? 8 : 4)>(L, v, tasks, ntasks, part, backward, ctrl, pub, grid, st);
     else if (g == 4)
-      launch_sweep_s<T, S, 4>(L, v, tasks, ntasks, part, backward, ctrl, grid, st);
+      launch_sweep_s<T, S, 4>(L, v, tasks, ntasks, part, backward, ctrl, pub, grid, st);
     else if (g == 2)
-      launch_sweep_s<T, S, 2>(L, v, tasks, ntasks, part, backward, ctrl, grid, st);
+      launch_sweep_s<T, S, 2>(L, v, tasks, ntasks, part, backward, ctrl, pub, grid, st);
     else
-      launch_sweep_s<T, S, 1>(L, v, tasks, ntasks, part, backward, ctrl, grid, st);
+      launch_sweep_s<T, S, 1>(L, v, tasks, ntasks, part, backward, ctrl, pub, grid, st);
     r0 += g;
   }
 }
 
 // deep: the longer tile ring (FP32: 6 stages, FP64: 3); shallow: FP32 4, FP64 2.  nr columns of
-// length n_vec at vec.
+// length n_vec at vec; pub holds min(nr, 8) such columns of T.
 template <typename T>
 void launch_sweep(const LevelDev& L, T* vec, const int2* tasks, int ntasks, int part, int backward, int* ctrl,
-                  int n_ctrl, int grid_max, int deep, cudaStream_t st, int nr) {
+                  void* pub, int grid_max, int deep, cudaStream_t st, int nr) {
   if (ntasks <= 0 || nr <= 0) return;
-  cudaMemsetAsync(ctrl, 0, sizeof(int) * (size_t)n_ctrl, st);
+  T* pb = (T*)pub;
   const int grid = ntasks < grid_max ? ntasks : grid_max;
   if (sizeof(T) == 4) {
     if (deep)
-      launch_sweep_nr<T, 6>(L, vec, tasks, ntasks, part, backward, ctrl, n_ctrl, grid, nr, st);
+      launch_sweep_nr<T, 6>(L, vec, tasks, ntasks, part, backward, ctrl, pb, grid, nr, st);
     else
-      launch_sweep_nr<T, 4>(L, vec, tasks, ntasks, part, backward, ctrl, n_ctrl, grid, nr, st);
+      launch_sweep_nr<T, 4>(L, vec, tasks, ntasks, part, backward, ctrl, pb, grid, nr, st);
   } else {
     if (deep)
-      launch_sweep_nr<T, 3>(L, vec, tasks, ntasks, part, backward, ctrl, n_ctrl, grid, nr, st);
+      launch_sweep_nr<T, 3>(L, vec, tasks, ntasks, part, backward, ctrl, pb, grid, nr, st);
     else
-      launch_sweep_nr<T, 2>(L, vec, tasks, ntasks, part, backward, ctrl, n_ctrl, grid, nr, st);
+      launch_sweep_nr<T, 2>(L, vec, tasks, ntasks, part, backward, ctrl, pb, grid, nr, st);
   }
 }
 
-template void launch_sweep<float>(const LevelDev&, float*, const int2*, int, int, int, int*, int, int, int,
+template void launch_sweep<float>(const LevelDev&, float*, const int2*, int, int, int, int*, void*, int, int,
                                   cudaStream_t, int);
-template void launch_sweep<double>(const LevelDev&, double*, const int2*, int, int, int, int*, int, int, int,
+template void launch_sweep<double>(const LevelDev&, double*, const int2*, int, int, int, int*, void*, int, int,
                                    cudaStream_t, int);
 
 }  // namespace bddc
