@@ -127,8 +127,9 @@ typedef struct {
   int autotune;             /* 1: time the sweep launch variants (CTAs per SM, tile-ring depth, task order)
                                on every level at set-up and keep the fastest; results are cached per level
                                shape for the life of the process.  0: fixed defaults */
-  int wait_probe;           /* test only, default 0.  1: every row-flag wait of the streaming sweeps polls a
-                               device word that nothing sets, with a short limit, so that each sweep runs
+  int wait_probe;           /* test only, default 0.  1: every wait of the streaming sweeps for a
+                               published solution block polls a device word that nothing sets, with
+                               a short limit, so that each sweep runs
                                its bounded-wait error path and the call reports BDDC_ERR_TIMEOUT (the
                                results of such a call are meaningless; the CUDA context stays usable).
                                Tile-copy waits are not affected. */

@@ -86,9 +86,9 @@ struct LevelDev {
   void* sgn;                      // [n_vec] pivot signs of the signed Cholesky (T; +1 for SPD levels)
   const double* c_rho;            // [sum nc] 1 where a constraint row is augmented by rho, else 0
   int indefinite;                 // 1: negative pivots allowed (Stokes), 0: SPD
-  int wait_probe;                 // test only: sweeps poll status[3] (never set) instead of their row flags
+  int wait_probe;                 // test only: sweeps poll status[3] (never set) instead of the published solution blocks
   int* status;                    // [4]: breakdown flag, lowest breakdown subdomain, timeout code, a word
-                                  // nothing writes (the row-flag wait of the timeout probe)
+                                  // nothing writes (the publication wait of the timeout probe)
 };
 
 // Counts every kernel launch of the library (defined in capi.cpp).

@@ -15,10 +15,11 @@
 // pattern: NaN results are canonical, and a computed all-ones word is published as the
 // canonical NaN).  The consumer polls the data itself, one L2 round trip instead of a flag
 // acquire followed by the data load, and the producer needs no fence.  A task only waits for
-// tasks handed out before it, so the scheme cannot deadlock whatever the residency.  Every wait is bounded; a timeout sets status[2] and the
-// kernel finishes without waiting further (the host reports BDDC_ERR_TIMEOUT).  A row-flag wait
-// that gives up stages the block as it is and goes on, so every tile copy is still consumed and
-// no access leaves the task's own rows; a tile wait that gives up drains the ring before exit.
+// tasks handed out before it, so the scheme cannot deadlock whatever the residency.  Every wait
+// is bounded; a timeout sets status[2] and the kernel finishes without waiting further (the host
+// reports BDDC_ERR_TIMEOUT).  A wait for a published block that gives up stages the block as it
+// is and goes on, so every tile copy is still consumed and no access leaves the task's own rows;
+// a tile wait that gives up drains the ring before exit.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -32,7 +33,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kYSlots = 16;          // solution blocks staged in shared memory at a time
 constexpr long long kSpinLimit = 1ll << 24;
-constexpr long long kProbeSpins = 32;   // row-flag wait limit of the timeout probe
+constexpr long long kProbeSpins = 32;   // publication wait limit of the timeout probe
 
 __device__ __forceinline__ int64_t tile_index(int i, int j, int Bc) {
   return i < Bc ? ((int64_t)i * (i + 1) / 2 + j) : ((int64_t)Bc * (Bc + 1) / 2 + (int64_t)(i - Bc) * Bc + j);

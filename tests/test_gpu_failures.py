@@ -7,8 +7,8 @@ subdomain factorisation and for a bounded device-side wait that gives up, made o
   the factorisation flags that subdomain (and only it: the other local matrices hold only their
   own elements).  The library must name the level and the subdomain, keep the CUDA context usable
   and, after bddc_update_coef with sane coefficients, solve again.
-* BDDC_ERR_TIMEOUT: the test-only option wait_probe makes every row-flag wait of the streaming
-  sweeps poll a device word that nothing sets, with a short limit.  Each wait then takes its
+* BDDC_ERR_TIMEOUT: the test-only option wait_probe makes every wait of the streaming sweeps for a
+  published solution block poll a device word that nothing sets, with a short limit.  Each wait then takes its
   error path (flag the timeout, stage the block as it is, go on), so every tile copy is still
   consumed and the sweep ends by itself; the host must report BDDC_ERR_TIMEOUT, and a later
   handle on the same context must solve correctly."""
