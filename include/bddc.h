@@ -329,16 +329,17 @@ int bddc_batching_ablation(bddc_handle h, double* ms);
 
 /* Test and measurement entry point for the tensor-core trailing update of the mixed factorisation
  * (Algorithm 1, "factorize the matrices of local saddle point problems"; the FP32 block Cholesky's
- * rank-256 update on tcgen05 from two row-scaled FP16 parts, three products).  a: host FP32 n x n
- * row-major, n = 64 nb with nb >= 5.  The first 256 columns play the factored panel P and the rest
- * the trailing matrix: on return a(i, j) -= sum_{q < 256} a(i, q) a(j, q) for every i, j >= 256
- * whose 64 x 64 tiles satisfy tile(j) <= tile(i) (diagonal tiles are updated in full); the other
- * entries are returned unchanged.  The data pass through the factor's tile layout and the same two
+ * rank-256 or rank-512 update on tcgen05 from two row-scaled FP16 parts, three products).
+ * rank: 256 or 512.  a: host FP32 n x n row-major, n = 64 nb with n >= rank + 64.  The first rank
+ * columns play the factored panel P and the rest the trailing matrix: on return
+ * a(i, j) -= sum_{q < rank} a(i, q) a(j, q) for every i, j >= rank whose 64 x 64 tiles satisfy
+ * tile(j) <= tile(i) (diagonal tiles are updated in full); the other entries are returned
+ * unchanged.  The data pass through the factor's tile layout and the same two
  * kernels (panel split, persistent tcgen05 update) that bddc_setup launches.  ms: host, receives
  * the update kernel's duration from CUDA events, or NULL.  Device buffers are allocated and freed
- * by the call, on the default stream.  Errors: INVALID (n), CUDA, OOM, TIMEOUT (a bounded wait of
- * the update kernel gave up). */
-int bddc_tc_update_check(int64_t n, float* a, double* ms);
+ * by the call, on the default stream.  Errors: INVALID (n, rank), CUDA, OOM, TIMEOUT (a bounded
+ * wait of the update kernel gave up). */
+int bddc_tc_update_check(int64_t n, int rank, float* a, double* ms);
 
 /* Message of the last failure on the calling thread ("" if none). */
 const char* bddc_last_error(void);

@@ -125,7 +125,7 @@ def lib() -> C.CDLL:
     L.bddc_grad_noalloc.argtypes = [H, P, P, C.c_int, C.c_double, P, P]
     L.bddc_get_maps.argtypes = [H, C.c_int, C.POINTER(LevelMaps)]
     L.bddc_get_coarse.argtypes = [H, C.c_int, C.POINTER(C.c_double), C.c_int64]
-    L.bddc_tc_update_check.argtypes = [C.c_int64, C.POINTER(C.c_float), C.POINTER(C.c_double)]
+    L.bddc_tc_update_check.argtypes = [C.c_int64, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_double)]
     L.bddc_get_stats.argtypes = [H, C.POINTER(Stats)]
     L.bddc_sizes.argtypes = [H, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     L.bddc_free.argtypes = [H]

@@ -120,10 +120,13 @@ struct Level {
   int max_R = 0, max_Bc = 0, max_nc = 0, max_nG = 0, max_nGb = 0;
   std::vector<int> max_tiles;  // per factor step k
   std::vector<double> step_flops;  // tile flops of factor step k (all subdomains)
-  std::vector<int> narrow_tiles;   // per step k: in-panel update tiles (256-wide panels)
-  std::vector<int64_t> wide_items2; // per super-step: 128 x 128 work items of the pre-split update (all subdomains)
-  std::vector<double> tc_flops;     // per super-step: FP32-equivalent flops of the trailing update
-  int64_t* item_pref = nullptr;     // [super-steps][n_sub + 1] first work item of every subdomain
+  std::vector<int> narrow_tiles;   // per step k: in-panel update tiles (256-wide sub-panels)
+  std::vector<double> panel_flops; // per step k: flops of the CUDA-core steps (tensor-core path)
+  // per 512-wide super-panel p and update u (0: rank-256 update of the second half's columns,
+  // 1: rank-512 update of the trailing columns): 128 x 128 work items and FP32-equivalent flops
+  std::vector<int64_t> tc_items;    // [2 p + u], all subdomains
+  std::vector<double> tc_flops;     // [2 p + u]
+  int64_t* item_pref = nullptr;     // [2 p + u][n_sub + 1] first work item of every subdomain
   uint8_t* split = nullptr;        // scaled FP16 parts of the current super-panel (pre-split update)
   uint8_t* split_signed = nullptr; // indefinite levels: the same with the pivot signs on the columns
   float* rscale = nullptr;         // their row unscaling factors (powers of two)
@@ -220,7 +223,8 @@ void alloc_level_work(Level& L, DevArena& A, int blk) {
   L.blk = blk;
 }
 
-constexpr int kPanel = 4;   // tile columns per tensor-core super-panel (256)
+constexpr int kSub = 4;     // tile columns of a CUDA-core sub-panel (256)
+constexpr int kPanel = 8;   // tile columns of a tensor-core super-panel (512, two sub-panels)
 
 }  // namespace
 }  // namespace bddc
@@ -540,8 +544,10 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
   L.max_tiles.assign(L.max_Bc, 0);
   L.step_flops.assign(L.max_Bc, 0.0);
   L.narrow_tiles.assign(L.max_Bc, 0);
-  L.wide_items2.assign((L.max_Bc + kPanel - 1) / kPanel + 1, 0);
-  L.tc_flops.assign((L.max_Bc + kPanel - 1) / kPanel + 1, 0.0);
+  L.panel_flops.assign(L.max_Bc, 0.0);
+  const int n_super = (L.max_Bc + kPanel - 1) / kPanel + 1;
+  L.tc_items.assign(2 * (size_t)n_super, 0);
+  L.tc_flops.assign(2 * (size_t)n_super, 0.0);
   const double nb3 = (double)NB * NB * NB;
   const double wsz = L.fp32 ? 4.0 : 8.0;
   L.trsv_bytes[0] = L.trsv_bytes[1] = 0.0;
@@ -555,15 +561,18 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
       L.step_flops[k] += nb3 / 3.0 + nb3 * (double)(m.R - k - 1) + 2.0 * nb3 * (double)cnt;
     }
     for (int k = 0; k < m.Bc; ++k) {
-      const int kb1 = (k / kPanel + 1) * kPanel;
+      const int kb1 = (k / kSub + 1) * kSub;
       int64_t cnt = 0;
       for (int j = k + 1; j < std::min(kb1, (int)m.Bc); ++j) cnt += m.R - j;
       L.narrow_tiles[k] = std::max(L.narrow_tiles[k], (int)cnt);
+      L.panel_flops[k] += nb3 / 3.0 + nb3 * (double)(m.R - k - 1) + 2.0 * nb3 * (double)cnt;
     }
     for (int kb0 = 0; kb0 < m.Bc; kb0 += kPanel) {
-      int64_t tiles = 0;
-      for (int j = kb0 + kPanel; j < m.Bc; ++j) tiles += m.R - j;
-      L.tc_flops[kb0 / kPanel] += 2.0 * nb3 * kPanel * (double)tiles;
+      int64_t tiles[2] = {0, 0};
+      for (int j = kb0 + kSub; j < std::min(kb0 + kPanel, (int)m.Bc); ++j) tiles[0] += m.R - j;
+      for (int j = kb0 + kPanel; j < m.Bc; ++j) tiles[1] += m.R - j;
+      L.tc_flops[2 * (kb0 / kPanel)] += 2.0 * nb3 * kSub * (double)tiles[0];
+      L.tc_flops[2 * (kb0 / kPanel) + 1] += 2.0 * nb3 * kPanel * (double)tiles[1];
     }
     // a sweep reads the stored triangle once and the vector in and out
     L.trsv_bytes[0] += wsz * (0.5 * (double)m.nI * (m.nI + 1) + 2.0 * m.nI);
@@ -747,19 +756,21 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
     L.split = A.alloc<uint8_t>(rows * kPanel * 2 * NB2 * 2);
     if (h->physics == BDDC_STOKES) L.split_signed = A.alloc<uint8_t>(rows * kPanel * 2 * NB2 * 2);
     L.rscale = A.alloc<float>(rows * NB);
-    // work items (128 x 128 output blocks) of every super-step, flattened over the subdomains
-    const int np = (int)L.wide_items2.size();
-    std::vector<int64_t> pref((size_t)np * (ns + 1), 0);
-    for (int p = 0; p < np; ++p) {
-      const int kb1 = (p + 1) * kPanel;
+    // work items (128 x 128 output blocks) of both updates of every super-panel, flattened over
+    // the subdomains; update 0 covers the columns [kb0 + kSub, kb0 + kPanel), update 1 the rest
+    const int nu = (int)L.tc_items.size();
+    std::vector<int64_t> pref((size_t)nu * (ns + 1), 0);
+    for (int u = 0; u < nu; ++u) {
+      const int kb0 = (u / 2) * kPanel;
+      const int jbeg = kb0 + (u % 2 ? kPanel : kSub), jend = u % 2 ? (1 << 30) : kb0 + kPanel;
       int64_t acc = 0;
       for (int64_t s = 0; s < ns; ++s) {
-        pref[(size_t)p * (ns + 1) + s] = acc;
+        pref[(size_t)u * (ns + 1) + s] = acc;
         const SubMeta& m = L.meta[s];
-        for (int j = kb1; j < m.Bc; j += 2) acc += (m.R - j + 1) / 2;
+        for (int j = jbeg; j < std::min((int)m.Bc, jend); j += 2) acc += (m.R - j + 1) / 2;
       }
-      pref[(size_t)p * (ns + 1) + ns] = acc;
-      L.wide_items2[p] = acc;
+      pref[(size_t)u * (ns + 1) + ns] = acc;
+      L.tc_items[u] = acc;
     }
     L.item_pref = A.upload(pref, st);
   }
@@ -868,25 +879,31 @@ void factor_level(bddc_handle_s* h, Level& L, cudaStream_t st) {
   launch_densify_rows<T>(d, L.row_sub, st);
   launch_add_constraints<T>(d, st);
   if (sizeof(T) == 4 && h->opts.tensor_cores) {
-    // 256-wide panels: in-panel steps on CUDA cores, the rank-256 trailing update on tcgen05
+    // 512-wide super-panels of two 256-wide sub-panels: in-sub-panel steps on CUDA cores; a
+    // rank-256 tcgen05 update of the second sub-panel's columns after the first, and one
+    // rank-512 update of every trailing column after the second
     for (int kb0 = 0; kb0 < L.max_Bc; kb0 += kPanel) {
-      const int kb1 = kb0 + kPanel;
       const int p = kb0 / kPanel;
-      double fl = 0.0;
-      for (int k = kb0; k < std::min(kb1, L.max_Bc); ++k) fl += L.step_flops[k];
-      {
-        ProfScope ps(h, BDDC_PROF_FACTOR, 0.0, std::max(0.0, fl - L.tc_flops[p]), st);
-        for (int k = kb0; k < std::min(kb1, L.max_Bc); ++k)
-          launch_potrf_step<T>(d, k, L.max_R, L.narrow_tiles[k], kb1, st);
-        if (L.split && L.wide_items2[p] > 0)
-          launch_split_panel(d, kb0, kb1, L.max_R, L.split, L.split_signed, L.rscale, L.prow_off, st);
-      }
-      const int64_t items = L.wide_items2[p];
-      if (L.split && items > 0) {   // the last super-panel has no trailing columns: no launch
-        ProfScope ps(h, BDDC_PROF_TC_UPDATE, 0.0, L.tc_flops[p], st);
-        launch_update_tc2(d, kb0, kb1, (int)std::min<int64_t>(items, h->grid_max / 2), L.split,
-                          L.split_signed ? L.split_signed : L.split, L.rscale,
-                          L.prow_off, L.item_pref + (size_t)p * (d.n_sub + 1), L.tile_tmap, st);
+      for (int half = 0; half < 2; ++half) {
+        const int k0 = kb0 + half * kSub, k1 = k0 + kSub;
+        const int u = 2 * p + half;
+        {
+          double fl = 0.0;
+          for (int k = k0; k < std::min(k1, L.max_Bc); ++k) fl += L.panel_flops[k];
+          ProfScope ps(h, BDDC_PROF_FACTOR, 0.0, fl, st);
+          for (int k = k0; k < std::min(k1, L.max_Bc); ++k) launch_potrf_step<T>(d, k, L.max_R, L.narrow_tiles[k], k1, st);
+          if (L.split && L.tc_items[u] > 0)
+            launch_split_panel(d, kb0, half ? kPanel : kSub, k1, L.max_R, L.split, L.split_signed, L.rscale,
+                               L.prow_off, st);
+        }
+        const int64_t items = L.tc_items[u];
+        if (L.split && items > 0) {   // no launch where no subdomain has columns left
+          ProfScope ps(h, BDDC_PROF_TC_UPDATE, 0.0, L.tc_flops[u], st);
+          launch_update_tc2(d, half ? kPanel : kSub, k1, half ? (1 << 30) : kb0 + kPanel,
+                            (int)std::min<int64_t>(items, h->grid_max / 2), L.split,
+                            L.split_signed ? L.split_signed : L.split, L.rscale, L.prow_off,
+                            L.item_pref + (size_t)u * (d.n_sub + 1), L.tile_tmap, st);
+        }
       }
     }
   } else {
@@ -2448,10 +2465,12 @@ int bddc_get_coarse(bddc_handle h, int level, double* kc, int64_t n) {
   });
 }
 
-int bddc_tc_update_check(int64_t n, float* a, double* ms) {
+int bddc_tc_update_check(int64_t n, int rank, float* a, double* ms) {
   return guarded([&]() {
-    if (!a || n < 5 * NB || n % NB != 0 || n > 64 * 1024)
-      fail(BDDC_ERR_INVALID, "bddc_tc_update_check: n must be a multiple of 64 in [320, 65536]");
+    if (rank != 256 && rank != 512) fail(BDDC_ERR_INVALID, "bddc_tc_update_check: rank must be 256 or 512");
+    const int nt = rank / NB;
+    if (!a || n < (int64_t)(nt + 1) * NB || n % NB != 0 || n > 64 * 1024)
+      fail(BDDC_ERR_INVALID, "bddc_tc_update_check: n must be a multiple of 64 in [rank + 64, 65536]");
     const int nb = (int)(n / NB);
     cudaStream_t st = nullptr;
     DevArena A;
@@ -2481,7 +2500,7 @@ int bddc_tc_update_check(int64_t n, float* a, double* ms) {
       uint8_t* split = A.alloc<uint8_t>((int64_t)nb * kPanel * 2 * NB2 * 2);
       float* rscale = A.alloc<float>((int64_t)nb * NB);
       int64_t items = 0;
-      for (int j = kPanel; j < nb; j += 2) items += (nb - j + 1) / 2;
+      for (int j = nt; j < nb; j += 2) items += (nb - j + 1) / 2;
       const int64_t* item_pref = A.upload(std::vector<int64_t>{0, items}, st);
       TensorMap128 tmap{};
       const int r = make_tile_tmap(&tmap, (float*)d.tiles, tile_elems);
@@ -2492,10 +2511,10 @@ int bddc_tc_update_check(int64_t n, float* a, double* ms) {
       cudaEvent_t e0, e1;
       ck(cudaEventCreate(&e0), "cudaEventCreate");
       ck(cudaEventCreate(&e1), "cudaEventCreate");
-      launch_split_panel(d, 0, kPanel, nb, split, nullptr, rscale, prow_off, st);
+      launch_split_panel(d, 0, nt, nt, nb, split, nullptr, rscale, prow_off, st);
       ck(cudaEventRecord(e0, st), "cudaEventRecord");
-      launch_update_tc2(d, 0, kPanel, (int)std::min<int64_t>(items, std::max(1, sms)), split, split, rscale, prow_off,
-                        item_pref, tmap, st);
+      launch_update_tc2(d, nt, nt, nb, (int)std::min<int64_t>(items, std::max(1, sms)), split, split, rscale,
+                        prow_off, item_pref, tmap, st);
       ck(cudaEventRecord(e1, st), "cudaEventRecord");
       ck(cudaGetLastError(), "tensor-core update launch");
       ck(cudaEventSynchronize(e1), "cudaEventSynchronize");
@@ -2508,8 +2527,8 @@ int bddc_tc_update_check(int64_t n, float* a, double* ms) {
       ck(cudaMemcpy(status, d.status, sizeof(status), cudaMemcpyDeviceToHost), "d2h");
       if (status[2]) fail(BDDC_ERR_TIMEOUT, "a bounded wait of the tensor-core update gave up");
       ck(cudaMemcpy(tiles.data(), d.tiles, sizeof(float) * (size_t)tile_elems, cudaMemcpyDeviceToHost), "d2h");
-      for (int i = kPanel; i < nb; ++i)
-        for (int j = kPanel; j <= i; ++j) {
+      for (int i = nt; i < nb; ++i)
+        for (int j = nt; j <= i; ++j) {
           const float* t2 = tiles.data() + ((int64_t)i * (i + 1) / 2 + j) * NB2;
           for (int r2 = 0; r2 < NB; ++r2)
             std::memcpy(a + ((int64_t)i * NB + r2) * n + (int64_t)j * NB, t2 + r2 * NB, sizeof(float) * NB);

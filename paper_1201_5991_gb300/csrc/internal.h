@@ -131,14 +131,15 @@ void launch_weights(const LevelDev& L, int multiplicity, const double* unused, c
 // one block column k: diagonal tile + inverse, panel, trailing update of columns (k, jmax)
 template <typename T>
 void launch_potrf_step(const LevelDev& L, int k, int max_R, int max_tiles, int jmax, cudaStream_t st);
-// update_tc.cu, FP32 levels with tensor cores: rank-(64 (kb1-kb0)) trailing update of the columns
-// >= kb1.  k_split_panel writes the two scaled FP16 parts of the panel tiles L(i, kb0..kb1-1),
-// i >= kb1, at split + ((prow_off[s] + i) * 4 + q - kb0) * 16 KB (indefinite levels: also a copy
-// with the pivot signs on the columns at split_signed) and the row unscaling factors 2^-e_r at
-// rscale[(prow_off[s] + i) * 64 + r]; the update makes 128 x 128 output blocks from them
-// (persistent grid; item_pref[s] = first work item of subdomain s, item_pref[n_sub] = number of
-// items; split_b = split_signed on indefinite levels, else split)
-void launch_split_panel(const LevelDev& L, int kb0, int kb1, int max_R, uint8_t* split, uint8_t* split_signed,
+// update_tc.cu, FP32 levels with tensor cores: rank-(64 nt) update of the output columns
+// ib <= j < jend from the nt panel tile columns kb0 .. kb0+nt-1 (nt = 4 or 8).  k_split_panel
+// writes the two scaled FP16 parts of the panel tiles L(i, kb0 + q), i >= ib, at
+// split + ((prow_off[s] + i) * 8 + q) * 16 KB (indefinite levels: also a copy with the pivot
+// signs on the columns at split_signed) and the row unscaling factors 2^-e_r at
+// rscale[(prow_off[s] + i) * 64 + r]; the update (nq = nt, jbeg = ib) makes 128 x 128 output
+// blocks from them (persistent grid; item_pref[s] = first work item of subdomain s,
+// item_pref[n_sub] = number of items; split_b = split_signed on indefinite levels, else split)
+void launch_split_panel(const LevelDev& L, int kb0, int nt, int ib, int max_R, uint8_t* split, uint8_t* split_signed,
                         float* rscale, const int64_t* prow_off, cudaStream_t st);
 // The update adds its output into the tiles with TMA reduce-adds through this tensor map: the
 // FP32 tile buffer viewed as [tile_elems / 64 rows][64 columns], 32 x 32 boxes, 128-byte
@@ -147,9 +148,9 @@ struct TensorMap128 {
   alignas(64) uint64_t opaque[16];   // a CUtensorMap
 };
 int make_tile_tmap(TensorMap128* map, float* tiles, int64_t tile_elems);
-void launch_update_tc2(const LevelDev& L, int kb0, int kb1, int grid, const uint8_t* split, const uint8_t* split_b,
-                       const float* rscale, const int64_t* prow_off, const int64_t* item_pref,
-                       const TensorMap128& tmap, cudaStream_t st);
+void launch_update_tc2(const LevelDev& L, int nq, int jbeg, int jend, int grid, const uint8_t* split,
+                       const uint8_t* split_b, const float* rscale, const int64_t* prow_off,
+                       const int64_t* item_pref, const TensorMap128& tmap, cudaStream_t st);
 void launch_gram_chol(const LevelDev& L, int precision_fp32, int max_nc, cudaStream_t st);
 template <typename T>
 void launch_psi(const LevelDev& L, int max_nGb, int max_nc, cudaStream_t st);

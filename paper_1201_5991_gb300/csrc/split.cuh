@@ -1,9 +1,9 @@
 // The scaled two-part FP16 split of the panel row tiles that feeds the tensor-core trailing
-// update (see update_tc.cu): for row tile i of a 256-wide super-panel, every row r is scaled by
-// 2^e_r so that its largest entry lies in [2^14, 2^15), and each scaled entry a is split into
-// hi = fp16(a) and lo = fp16((a - hi) 2^11), written in the shared-memory operand image of the
-// update (K-major, 128-byte swizzle).  Used by k_split_panel and by the panel-row kernel, which
-// splits the rows it has just computed.
+// update (see update_tc.cu): for row tile i and NT tile columns of a panel (NT = 4: a 256-wide
+// sub-panel, NT = 8: a 512-wide super-panel), every row r is scaled by 2^e_r so that its largest
+// entry lies in [2^14, 2^15), and each scaled entry a is split into hi = fp16(a) and
+// lo = fp16((a - hi) 2^11), written in the shared-memory operand image of the update (K-major,
+// 128-byte swizzle).
 #pragma once
 
 #include <cuda_fp16.h>
@@ -12,7 +12,7 @@
 
 namespace bddc {
 
-constexpr int kPanelTiles = 4;                  // tile columns of a super-panel (the split buffer's row pitch)
+constexpr int kPanelTiles = 8;                  // tile columns of a super-panel (the split buffer's row pitch)
 constexpr uint32_t kTilePart = 64 * 128;        // one FP16 part of one 64 x 64 tile (8 KB)
 constexpr uint32_t kSplitTile = 2 * kTilePart;  // hi and lo of one tile (16 KB)
 
@@ -32,12 +32,14 @@ __device__ __forceinline__ void store4h(uint8_t* part, uint32_t off, const __hal
   *(uint2*)(part + off) = v;
 }
 
-// Split the panel tiles L(i, kb0 .. kb0 + 3) of subdomain s; 256 threads, thread (r, c4) takes
-// row r of tile column kb0 + c4 (the four threads of a row share its scale).
+// Split the panel tiles L(i, kb0 .. kb0 + NT - 1) of subdomain s; 64 NT threads, thread (r, c4)
+// takes row r of tile column kb0 + c4 (the NT threads of a row, adjacent lanes, share its scale).
+template <int NT>
 __device__ __forceinline__ void split_row_tile(const LevelDev& L, int s, const SubMeta& m, int i, int kb0,
                                                uint8_t* __restrict__ split, uint8_t* __restrict__ split_signed,
                                                float* __restrict__ rscale, const int64_t* __restrict__ prow_off) {
-  const int r = threadIdx.x >> 2, c4 = threadIdx.x & 3;
+  static_assert(NT == 4 || NT == 8, "panel width");
+  const int r = threadIdx.x / NT, c4 = threadIdx.x % NT;
   const float4* t =
       (const float4*)((const float*)L.tiles + m.tile_off + split_tile_index(i, kb0 + c4, m.Bc) * NB2 + r * NB);
   float4 v[16];
@@ -47,8 +49,8 @@ __device__ __forceinline__ void split_row_tile(const LevelDev& L, int s, const S
     v[u] = __ldcg(t + u);
     mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v[u].x), fabsf(v[u].y)), fmaxf(fabsf(v[u].z), fabsf(v[u].w))));
   }
-  mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-  mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+#pragma unroll
+  for (int o = 1; o < NT; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   int ex = 0;
   if (mx > 0.f) {
     int k;

@@ -280,10 +280,11 @@ def bddc_solve(rhs, coef, solver: BddcSolver, tol: float = 1e-10):
     return _autograd_fn.apply(rhs, coef, solver, tol)
 
 
-def tc_update_check(a: np.ndarray):
-    """a (n x n FP32) with a[i, j] -= sum_{q < 256} a[i, q] a[j, q] on the tile lower triangle of the
-    trailing part, through the tensor-core kernels of the factorisation.  Returns (result, ms)."""
+def tc_update_check(a: np.ndarray, rank: int = 512):
+    """a (n x n FP32) with a[i, j] -= sum_{q < rank} a[i, q] a[j, q] on the tile lower triangle of the
+    trailing part (rank 256 or 512), through the tensor-core kernels of the factorisation.
+    Returns (result, ms)."""
     a = np.ascontiguousarray(a, dtype=np.float32).copy()
     ms = C.c_double()
-    capi.check(capi.lib().bddc_tc_update_check(a.shape[0], _ptr(a, C.c_float), C.byref(ms)))
+    capi.check(capi.lib().bddc_tc_update_check(a.shape[0], int(rank), _ptr(a, C.c_float), C.byref(ms)))
     return a, ms.value

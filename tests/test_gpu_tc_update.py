@@ -1,7 +1,8 @@
 """The tensor-core trailing update of the mixed factorisation (two row-scaled FP16 parts, three
 tcgen05 products, FP32 accumulation) against an FP64 product, through bddc_tc_update_check.
 
-Error bound of the scheme, entry by entry, for C - P P^T with K = 256 panel columns: each entry a
+Error bound of the scheme, entry by entry, for C - P P^T with K = 256 or 512 panel columns (the
+rank-256 update of a super-panel's second half and the rank-512 trailing update): each entry a
 of a row scaled into [2^14, 2^15) is split as a = hi + 2^-11 lo + r with |r| <= 2^-22 |a|, the
 dropped lo lo term is at most 2^-22 |a||b|, and the FP32 accumulation (tensor-core MMAs of K = 16,
 then FP32 adds of every 64-wide chunk) adds at most about 2 (K + 16) 2^-24 sum_q |a_q||b_q|.  So
@@ -20,26 +21,26 @@ from paper_1201_5991_gb300.solver import tc_update_check
 pytestmark = pytest.mark.gpu
 
 
-def _factor_like(n, seed):
+def _factor_like(n, K, seed):
     # panel rows spanning four decades (as factor rows of a stiffness matrix with E in [1, 1e3])
     rng = np.random.default_rng(seed)
     a = rng.standard_normal((n, n)).astype(np.float32)
     rows = (10.0 ** rng.uniform(-2, 2, size=n)).astype(np.float32)
-    a[:, :256] *= rows[:, None]
+    a[:, :K] *= rows[:, None]
     return a
 
 
-@pytest.mark.parametrize("n", [64 * 5, 64 * 12, 64 * 21])
-def test_split_update_error_bound(n):
-    a = _factor_like(n, seed=n)
-    out, ms = tc_update_check(a)
-    P = a[:, :256].astype(np.float64)
+@pytest.mark.parametrize("K,n", [(256, 64 * 5), (256, 64 * 12), (256, 64 * 21),
+                                 (512, 64 * 9), (512, 64 * 16), (512, 64 * 25)])
+def test_split_update_error_bound(K, n):
+    a = _factor_like(n, K, seed=n)
+    out, ms = tc_update_check(a, rank=K)
+    P = a[:, :K].astype(np.float64)
     exact = a.astype(np.float64) - P @ P.T
     absprod = np.abs(P) @ np.abs(P).T
-    K = 256
     gamma = 3 * 2.0 ** -22 + 2 * (K + 16) * 2.0 ** -24
     tiles = np.arange(n) // 64
-    upd = (tiles[:, None] >= tiles[None, :]) & (np.arange(n)[:, None] >= 256) & (np.arange(n)[None, :] >= 256)
+    upd = (tiles[:, None] >= tiles[None, :]) & (np.arange(n)[:, None] >= K) & (np.arange(n)[None, :] >= K)
     err = np.abs(out.astype(np.float64) - exact)
     bound = gamma * absprod + 2.0 ** -24 * np.abs(exact)
     assert np.all(err[upd] <= bound[upd]), float((err[upd] / bound[upd]).max())
@@ -47,9 +48,9 @@ def test_split_update_error_bound(n):
     rel = float((err[upd] / absprod[upd]).max())
     # norm-wise against an FP32 GEMM of the same panel (BLAS sgemm, FMA accumulation): the split
     # keeps about one FP32 rounding more per product, so at most a few times the FP32 error
-    P32 = a[:, :256]
+    P32 = a[:, :K]
     e32 = np.abs((a - P32 @ P32.T).astype(np.float64) - exact)
     ratio = float(np.linalg.norm(err[upd]) / np.linalg.norm(e32[upd]))
-    print(f"n={n}: max |error| / sum |p||p| = {rel:.2e} (bound {gamma:.2e}); "
+    print(f"K={K} n={n}: max |error| / sum |p||p| = {rel:.2e} (bound {gamma:.2e}); "
           f"||error|| / ||FP32 GEMM error|| = {ratio:.2f}; update {ms:.3f} ms")
     assert ratio < 4.0
