@@ -161,8 +161,10 @@ def traffic_ratio(cls):
     (profiles/update_tc2_traffic.json); None when the kernel source changed since the counters
     were taken."""
     from paper_1201_5991_gb300 import capi
-    if cls in (capi.PROF_TRSV, capi.PROF_TRSV_IFACE):
+    if cls == capi.PROF_TRSV:
         fname, src_name, key = "trsv_sweep_traffic.json", "sweep.cu", "traffic_over_algorithmic"
+    elif cls == capi.PROF_TRSV_IFACE:
+        fname, src_name, key = "trsv_sweep_traffic.json", "sweep.cu", "traffic_over_algorithmic_interface"
     elif cls == capi.PROF_TC_UPDATE:
         fname, src_name, key = "update_tc2_traffic.json", "update_tc.cu", "traffic_over_fp32_flop"
     else:
@@ -174,7 +176,7 @@ def traffic_ratio(cls):
         src = open(os.path.join(ROOT, "paper_1201_5991_gb300", "csrc", src_name), "rb").read()
         if hashlib.sha256(src).hexdigest() != rec.get("source_sha256", rec.get("sweep_cu_sha256")):
             return None
-        return float(rec[key])
+        return float(rec.get(key, rec.get("traffic_over_algorithmic")))
     except Exception:
         return None
 
@@ -441,13 +443,14 @@ def run_gpu(args, rank, world, local_rank):
     names = {capi.PROF_TRSV: "k_sweep<float> forward/backward over interior block rows (Schur operator; "
                              "streaming triangular sweeps, TMA-staged tiles)",
              capi.PROF_TRSV_IFACE: "k_sweep<float> forward/backward over interface block rows (subdomain corrections)",
-             capi.PROF_COARSE: "k_sweep<double> forward/backward of the coarsest FP64 factor",
+             capi.PROF_COARSE: "coarsest-level solves (k_coarse_apply with the explicit FP32 inverse of the "
+                               "FP64 coarse factor, else sweeps over it)",
              capi.PROF_TRMV: "k_trmv_t + k_trmv_n (inner Schur operator: products with the stored interface factor)",
              capi.PROF_SPMV: "k_spmv (FP64 CSR products with K_i)",
              capi.PROF_FACTOR: "factorisation steps on CUDA cores (k_potrf_diag, k_trsm_panel, in-panel "
                                "k_syrk_update, k_split_panel)",
-             capi.PROF_TC_UPDATE: "k_update_tc2 (rank-256 trailing update on tcgen05, scaled two-part FP16 "
-                                  "products, persistent, TMEM double-buffered)"}
+             capi.PROF_TC_UPDATE: "k_update_tc2 (rank-256 and rank-512 trailing updates of 512-wide super-panels "
+                                  "on tcgen05, scaled two-part FP16 products, persistent, TMEM double-buffered)"}
     kernel_classes = {}
     for c, (cms, cl, cb, cf) in cls.items():
         if cl == 0:
