@@ -117,7 +117,8 @@ struct Level {
   // host-side metadata
   std::vector<SubMeta> meta;
   int64_t n_vec = 0, tile_elems = 0, dinv_elems = 0, psi_elems = 0, g_elems = 0, sum_nc = 0;
-  int max_R = 0, max_Bc = 0, max_nc = 0, max_nG = 0, max_nGb = 0;
+  int max_R = 0, max_Bc = 0, max_nc = 0, max_nG = 0, max_nGb = 0, max_ncb = 0;
+  int64_t psiT_elems = 0;
   std::vector<int> max_tiles;  // per factor step k
   std::vector<double> step_flops;  // tile flops of factor step k (all subdomains)
   std::vector<int> narrow_tiles;   // per step k: in-panel update tiles (256-wide sub-panels)
@@ -173,7 +174,7 @@ struct Level {
   double* dl2 = nullptr;
   double* dl3 = nullptr;
   double* rc_sub = nullptr;    // [sum_nc]
-  double* psi_part = nullptr;  // [sum_nc * kPsiSlices] partial sums of Psi^T r
+  double* psi_part = nullptr;  // [sum_nc * rows_zmax(max_nGb)] partial sums of Psi^T r and Y r
   double* zc_sub = nullptr;
   double* rC = nullptr;        // [n_coarse]
   double* zC = nullptr;
@@ -208,7 +209,7 @@ void alloc_level_work(Level& L, DevArena& A, int blk) {
   L.cc_t = A.alloc<double>(L.sum_nc * blk);
   L.cc_mu = A.alloc<double>(L.sum_nc * blk);
   L.rc_sub = A.alloc<double>(L.sum_nc * blk);
-  L.psi_part = A.alloc<double>(L.sum_nc * kPsiSlices * blk);
+  L.psi_part = A.alloc<double>(L.sum_nc * rows_zmax(L.max_nGb) * blk);
   L.zc_sub = A.alloc<double>(L.sum_nc * blk);
   L.rC = A.alloc<double>(L.maps.n_coarse * blk);
   L.zC = A.alloc<double>(L.maps.n_coarse * blk);
@@ -502,8 +503,8 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
   const LevelMesh& ms = L.mesh;
   const int64_t ns = mp.n_sub();
   L.meta.resize(ns);
-  int64_t tile = 0, dinv = 0, vec = 0, coff = 0, goff = 0, psi = 0;
-  L.max_R = L.max_Bc = L.max_nc = L.max_nG = L.max_nGb = 0;
+  int64_t tile = 0, dinv = 0, vec = 0, coff = 0, goff = 0, psi = 0, psiT = 0;
+  L.max_R = L.max_Bc = L.max_nc = L.max_nG = L.max_nGb = L.max_ncb = 0;
   for (int64_t s = 0; s < ns; ++s) {
     SubMeta& m = L.meta[s];
     m.n = (int32_t)(mp.sub_dof_ptr[s + 1] - mp.sub_dof_ptr[s]);
@@ -529,16 +530,20 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
     goff += (int64_t)m.nc * m.nc;
     m.psi_off = psi;
     psi += (int64_t)m.nGb * NB * m.nc;
+    m.psiT_off = psiT;
+    psiT += (int64_t)m.ncb * m.nGb * NB2;
     L.max_R = std::max(L.max_R, (int)m.R);
     L.max_Bc = std::max(L.max_Bc, (int)m.Bc);
     L.max_nc = std::max(L.max_nc, (int)m.nc);
     L.max_nG = std::max(L.max_nG, (int)m.nG);
     L.max_nGb = std::max(L.max_nGb, (int)m.nGb);
+    L.max_ncb = std::max(L.max_ncb, (int)m.ncb);
   }
   L.n_vec = vec;
   L.tile_elems = tile;
   L.dinv_elems = dinv;
   L.psi_elems = psi;
+  L.psiT_elems = psiT;
   L.g_elems = goff;
   L.sum_nc = coff;
   L.max_tiles.assign(L.max_Bc, 0);
@@ -782,10 +787,12 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
     }
     d.dinv = A.alloc<float>(L.dinv_elems);
     d.psi = A.alloc<float>(L.psi_elems);
+    d.psiT = A.alloc<float>(L.psiT_elems);
   } else {
     d.tiles = A.alloc<double>(L.tile_elems);
     d.dinv = A.alloc<double>(L.dinv_elems);
     d.psi = A.alloc<double>(L.psi_elems);
+    d.psiT = A.alloc<double>(L.psiT_elems);
   }
   (void)ts;
   d.status = h->d_status;
@@ -891,7 +898,12 @@ void factor_level(bddc_handle_s* h, Level& L, cudaStream_t st) {
           double fl = 0.0;
           for (int k = k0; k < std::min(k1, L.max_Bc); ++k) fl += L.panel_flops[k];
           ProfScope ps(h, BDDC_PROF_FACTOR, 0.0, fl, st);
-          for (int k = k0; k < std::min(k1, L.max_Bc); ++k) launch_potrf_step<T>(d, k, L.max_R, L.narrow_tiles[k], k1, st);
+          bool fused = false;   // the previous step's update factored this step's diagonal tile
+          for (int k = k0; k < std::min(k1, L.max_Bc); ++k) {
+            const bool fuse = k + 1 < k1 && L.narrow_tiles[k] > 0;
+            launch_potrf_step<T>(d, k, L.max_R, L.narrow_tiles[k], k1, st, fused, fuse);
+            fused = fuse;
+          }
           if (L.split && L.tc_items[u] > 0)
             launch_split_panel(d, kb0, half ? kPanel : kSub, k1, L.max_R, L.split, L.split_signed, L.rscale,
                                L.prow_off, st);
@@ -907,14 +919,18 @@ void factor_level(bddc_handle_s* h, Level& L, cudaStream_t st) {
       }
     }
   } else {
+    bool fused = false;
     for (int k = 0; k < L.max_Bc; ++k) {
       ProfScope ps(h, BDDC_PROF_FACTOR, 0.0, L.step_flops[k], st);
-      launch_potrf_step<T>(d, k, L.max_R, L.max_tiles[k], 1 << 30, st);
+      const bool fuse = L.max_tiles[k] > 0;
+      launch_potrf_step<T>(d, k, L.max_R, L.max_tiles[k], 1 << 30, st, fused, fuse);
+      fused = fuse;
     }
   }
   if (L.max_nc > 0) {
     launch_gram_chol(d, L.fp32 ? 1 : 0, L.max_nc, st);
     launch_psi<T>(d, L.max_nGb, L.max_nc, st);
+    launch_psi_transpose<T>(d, L.max_nGb, L.max_ncb, st);   // the solve phase streams Psi_G^T by tiles
   }
   ck(cudaGetLastError(), "factor launch");
 }
@@ -1078,10 +1094,11 @@ void interface_step_t(bddc_handle_s* h, int l, const double* rhat, double* zhat,
   Level& L = h->lv[l];
   T* v = (T*)L.locA;
   launch_gather_iface<T>(L.d, rhat, 1, v, st, nb);          // r_i = E_i^T r_hat
-  launch_psi_t_apply<T>(L.d, v, L.psi_part, L.sum_nc, L.rc_sub, st, nb);   // Psi_i^T r_i
+  launch_psi_t_apply<T>(L.d, v, L.psi_part, L.sum_nc, L.rc_sub, L.max_nGb, L.max_ncb, st, nb);   // Psi_i^T r_i
   launch_coarse_gather(L.d, L.rc_sub, L.sum_nc, L.rC, st, nb);   // r_C = sum R_Ci^T Psi_i^T r_i
   trsv_one<T>(h, L, v, 1, 0, st, nb);                       // Eq. sub_cor via the trailing factor
-  launch_constraint_corr<T>(L.d, v, L.crow_sub, L.sum_nc, L.cc_t, L.cc_mu, L.max_nGb, st, nb);
+  launch_constraint_corr<T>(L.d, v, L.crow_sub, L.sum_nc, L.cc_t, L.cc_mu, L.psi_part, L.max_nGb, L.max_ncb, st,
+                            nb);
   trsv_one<T>(h, L, v, 1, 1, st, nb);
   const bool last = l + 2 == (int)h->lv.size();
   if (last)
@@ -1089,7 +1106,7 @@ void interface_step_t(bddc_handle_s* h, int l, const double* rhat, double* zhat,
   else
     full_step(h, l + 1, L.rC, L.zC, st, nb);
   launch_coarse_scatter_n(L.d.sub_coarse, L.sum_nc, L.zC, L.d.n_coarse, L.zc_sub, st, nb);
-  launch_psi_apply_add<T>(L.d, L.zc_sub, L.sum_nc, v, L.max_nG, st, nb);   // Psi_i R_Ci z_C + z_i
+  launch_psi_apply_add<T>(L.d, L.zc_sub, L.sum_nc, v, L.max_nGb, L.max_ncb, st, nb);   // Psi_i R_Ci z_C + z_i
   launch_scatter_iface<T>(L.d, v, 1, zhat, st, nb);            // z_hat = sum E_i (...)
 }
 
@@ -1163,14 +1180,22 @@ void choose_refinement(bddc_handle_s* h) {
   ck(cudaMemsetAsync(v, 0, sizeof(double) * n, st), "memset");
   launch_spmv_rows(L.d, L.rows[0], L.nrows[0], L.dl0, v, 1.0, 0.0, L.row_sub, st);
   const double nv = std::sqrt(dot_host(h, v, v, n));
+  // the refinement of interior_solve_l1 run step by step: after step s, w and the residual
+  // r = v - K_II w are exactly those of an interior solve with s steps (the same operations in
+  // the same order), so one pass measures every step count
   int best = 1;
   double prev = 1e300;
+  float* t = (float*)L.locB;
+  double* r = L.dl3;
+  ck(cudaMemsetAsync(w, 0, sizeof(double) * n, st), "memset");
   for (int steps = 1; steps <= 8; ++steps) {
     h->refine_steps = h->cur_steps = steps;
-    interior_solve_l1(h, L, v, w, st);
-    ck(cudaMemcpyAsync(L.dl3, v, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
-    launch_spmv_rows(L.d, L.rows[0], L.nrows[0], w, L.dl3, -1.0, 1.0, L.row_sub, st);
-    const double rel = nv > 0 ? std::sqrt(dot_host(h, L.dl3, L.dl3, n)) / nv : 0.0;
+    launch_convert<double, float>(steps == 1 ? v : r, t, n, st);
+    trsv_pair<float>(h, L, t, 0, st);
+    launch_add_to_double<float>(w, t, n, st);
+    ck(cudaMemcpyAsync(r, v, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
+    launch_spmv_rows(L.d, L.rows[0], L.nrows[0], w, r, -1.0, 1.0, L.row_sub, st);
+    const double rel = nv > 0 ? std::sqrt(dot_host(h, r, r, n)) / nv : 0.0;
     if (rel > 0.5 * prev) break;          // stagnated at round-off: the previous count suffices
     best = steps;
     if (rel < 4e-16) break;

@@ -30,7 +30,6 @@ __device__ __forceinline__ void flag_breakdown(int* status, int sub) {
 }
 
 constexpr int LDS = NB + 4;   // k-major shared tile stride (multiple of 4 for vector loads)
-constexpr int kMaxCoarseLocal = 256;   // coarse DOFs of one subdomain handled per pass of k_psi_t_part
 
 template <typename T>
 __device__ __forceinline__ void load_kmajor(T* s, const T* __restrict__ g) {
@@ -88,12 +87,12 @@ __device__ __forceinline__ void gemm_nt_4x4(const T* As, const T* Bs, T acc[4][4
 }
 
 // ---- step k, part 1: factor the diagonal tile and invert it -------------------------------
+// One CTA of 256 threads; smem_raw holds 2 NB (NB + 1) entries of T.  Called by k_potrf_diag and,
+// for the next block column of a panel, by the in-panel update kernel right after it has updated
+// that diagonal tile (so that the factorisation of a panel's later diagonal tiles overlaps the
+// rest of the previous step's update instead of taking a launch of its own).
 template <typename T>
-__global__ void k_potrf_diag(LevelDev L, int k) {
-  const int s = blockIdx.x;
-  const SubMeta m = L.meta[s];
-  if (k >= m.Bc) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ void factor_diag_tile(const LevelDev& L, const SubMeta& m, int s, int k, unsigned char* smem_raw) {
   T(*A)[NB + 1] = (T(*)[NB + 1])smem_raw;                 // the tile, then its factor L
   T(*X)[NB + 1] = (T(*)[NB + 1])(smem_raw + sizeof(T) * NB * (NB + 1));   // L^{-1}
   __shared__ int bad;
@@ -183,6 +182,15 @@ __global__ void k_potrf_diag(LevelDev L, int k) {
   }
 }
 
+template <typename T>
+__global__ void k_potrf_diag(LevelDev L, int k) {
+  const int s = blockIdx.x;
+  const SubMeta m = L.meta[s];
+  if (k >= m.Bc) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  factor_diag_tile<T>(L, m, s, k, smem_raw);
+}
+
 // ---- step k, part 2: panel L(i,k) = A(i,k) L_kk^{-T} for i = k+1 .. R-1 --------------------
 template <typename T>
 __global__ void k_trsm_panel(LevelDev L, int k) {
@@ -212,8 +220,10 @@ __global__ void k_trsm_panel(LevelDev L, int k) {
 }
 
 // ---- step k, part 3: trailing update A(i,j) -= L(i,k) L(j,k)^T, k < j <= i, j < min(Bc, jmax) --
+// fuse_next: the block that updates the next diagonal tile (k+1, k+1) (always block 0 of its
+// subdomain) factors and inverts it right away, and step k+1 launches no k_potrf_diag.
 template <typename T>
-__global__ void k_syrk_update(LevelDev L, int k, int jmax) {
+__global__ void k_syrk_update(LevelDev L, int k, int jmax, int fuse_next) {
   const int s = blockIdx.y;
   const SubMeta m = L.meta[s];
   if (k >= m.Bc) return;
@@ -250,6 +260,10 @@ __global__ void k_syrk_update(LevelDev L, int k, int jmax) {
 #pragma unroll
     for (int b = 0; b < 4; ++b) v[b] -= acc[a][b];
     store4(c + (4 * ty + a) * NB + 4 * tx, v);
+  }
+  if (fuse_next && i == k + 1 && j == k + 1) {   // block-uniform
+    __syncthreads();   // the updated tile is in global memory, visible to the whole block
+    factor_diag_tile<T>(L, m, s, k + 1, smem_raw);
   }
 }
 
@@ -497,29 +511,9 @@ __global__ void __launch_bounds__(256) k_psi_update(LevelDev L, int t) {
     if (c0 + q4 + b < nc) Zj[(int64_t)c * nc + c0 + q4 + b] -= acc[b];
 }
 
-// v_G -= Y_G^T G^{-1} Y_G v_G  (the constraint part of Eq. sub_cor), in three launches with
-// all subdomains' rows in flight: t = Y_G v (one warp per constraint row), mu = G^{-1} t (one
-// warp per row of G^{-1}), v -= Y_G^T mu (one thread per interface column).
-template <typename T>
-__global__ void k_cc_yv(LevelDev L, const T* __restrict__ vec, const int32_t* __restrict__ crow_sub,
-                        int64_t total_rows, double* __restrict__ t) {
-  const int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (g >= total_rows) return;
-  vec += (int64_t)blockIdx.y * L.n_vec;   // column blockIdx.y of a block of right-hand sides
-  t += (int64_t)blockIdx.y * total_rows;
-  const int s = crow_sub[g];
-  const SubMeta m = L.meta[s];
-  const int p = (int)(g - m.c_off);
-  const T* v = vec + m.vec_off + m.nIb * NB;
-  const T* sg = (const T*)L.sgn + m.vec_off + m.nIb * NB;   // the sweep left S L^{-1} r: undo S
-  const T* yrow = tile_ptr<T>(m, L.tiles, m.Bc + p / NB, m.nIb) + (p % NB) * NB;
-  T acc = (T)0;
-  for (int c = lane; c < m.nGb * NB; c += 32) acc += yrow[(int64_t)(c / NB) * NB2 + (c % NB)] * (v[c] * sg[c]);
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) t[g] = (double)acc;
-}
-
+// v_G -= Y_G^T G^{-1} Y_G v_G  (the constraint part of Eq. sub_cor): t = Y_G v and the final
+// update stream the constraint block rows of the factor (k_rows_matvec / k_cols_matvec below);
+// mu = G^{-1} t takes one warp per row of G^{-1}.
 __global__ void k_cc_mu(LevelDev L, const int32_t* __restrict__ crow_sub, int64_t total_rows,
                         const double* __restrict__ t, double* __restrict__ mu) {
   const int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -537,94 +531,173 @@ __global__ void k_cc_mu(LevelDev L, const int32_t* __restrict__ crow_sub, int64_
   if (lane == 0) mu[g] = acc;
 }
 
+// ---- products with Y_G and Psi_G^T, both held as ncb x nGb tiles of NB x NB per subdomain ----
+// MODE 0: M = Y_G, the constraint block rows of the factor (the forward sweep left S L^{-1} r in
+// the vector, so its entries are multiplied by the pivot signs S first); MODE 1: M = Psi_G^T
+// (psiT).  Row p of M belongs to coarse DOF p of the subdomain, column c to interface position c.
 template <typename T>
-__global__ void k_cc_update(LevelDev L, T* __restrict__ vec, const double* __restrict__ mu, int64_t total_rows) {
-  const int s = blockIdx.y;
-  const SubMeta m = L.meta[s];
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= m.nGb * NB || m.nc == 0) return;
-  vec += (int64_t)blockIdx.z * L.n_vec;
-  mu += (int64_t)blockIdx.z * total_rows;
-  T acc = (T)0;
-  for (int p = 0; p < m.nc; ++p)
-    acc += tile_ptr<T>(m, L.tiles, m.Bc + p / NB, m.nIb + c / NB)[(p % NB) * NB + (c % NB)] * (T)mu[m.c_off + p];
-  T* v = vec + m.vec_off + m.nIb * NB;
-  v[c] = v[c] - acc;   // S L^{-1} r - Y^T mu
+struct Pair;
+template <>
+struct Pair<float> {
+  using type = float2;
+};
+template <>
+struct Pair<double> {
+  using type = double2;
+};
+
+template <typename T, int MODE>
+__device__ __forceinline__ const T* m_tile(const LevelDev& L, const SubMeta& m, int rb, int j) {
+  if (MODE == 0) return tile_ptr<T>(m, L.tiles, m.Bc + rb, m.nIb + j);
+  return (const T*)L.psiT + m.psiT_off + ((int64_t)rb * m.nGb + j) * NB2;
 }
 
-// rc_sub = Psi_G^T v_G (FP64 result).  The interface rows of a subdomain are cut into
-// kPsiSlices slices, one block each (so the pass runs on n_sub x kPsiSlices blocks): warp w takes
-// rows w, w+8, ... of the slice, lane l the coarse DOFs l, l+32, ... (coalesced reads of Psi's
-// rows); the eight warps' sums and then the slices' sums are added in a fixed order.
-template <typename T>
-__global__ void k_psi_t_part(LevelDev L, const T* __restrict__ vec, double* __restrict__ part, int64_t sum_nc) {
-  const int s = blockIdx.y, z = blockIdx.x;
+// Row products over four tile columns: block (z, rb, s) adds the columns 4z .. 4z+3 of the
+// coarse rows rb NB .. rb NB + 63 of subdomain s for NR right-hand sides (column q at
+// vec + q n_vec) and writes part[(q sum_nc + c_off + p) zmax + z] (zero where the subdomain has
+// no such tile columns).  Warp w takes the rows w, w+8, .., lane l the columns 2l, 2l+1 of every
+// tile, so each tile row is one coalesced 256-byte read; rows past nc are not read.
+template <typename T, int NR, int MODE>
+__global__ void __launch_bounds__(256) k_rows_matvec(LevelDev L, const T* __restrict__ vec, double* __restrict__ part,
+                                                     int zmax, int64_t sum_nc) {
+  using V2 = typename Pair<T>::type;
+  const int z = blockIdx.x, rb = blockIdx.y, s = blockIdx.z;
   const SubMeta m = L.meta[s];
-  vec += (int64_t)blockIdx.z * L.n_vec;
-  part += (int64_t)blockIdx.z * sum_nc * kPsiSlices;
-  const int nc = m.nc;
-  const int chunk = (m.nG + kPsiSlices - 1) / kPsiSlices;
-  const int r0 = z * chunk, r1 = min(m.nG, r0 + chunk);
-  const T* v = vec + m.vec_off + m.nIb * NB;
-  const T* P = (const T*)L.psi + m.psi_off;
-  __shared__ T red[8][kMaxCoarseLocal];
+  if (rb >= m.ncb) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int q0 = 0; q0 < nc; q0 += kMaxCoarseLocal) {   // coarse DOFs in chunks of 256
-    T acc[kMaxCoarseLocal / 32];
+  const int j0 = 4 * z, j1 = min(m.nGb, j0 + 4);
+  __shared__ __align__(16) T xs[NR][4][NB];
+  const T* v = vec + m.vec_off + (int64_t)m.nIb * NB;
+  const T* sg = (const T*)L.sgn + m.vec_off + (int64_t)m.nIb * NB;
+  for (int e = threadIdx.x; e < NR * 4 * NB; e += blockDim.x) {
+    const int q = e / (4 * NB), jj = (e / NB) % 4, c = e % NB;
+    const int j = j0 + jj;
+    T x = (T)0;
+    if (j < j1) {
+      x = v[(int64_t)q * L.n_vec + (int64_t)j * NB + c];
+      if (MODE == 0 && L.indefinite) x *= sg[(int64_t)j * NB + c];
+    }
+    xs[q][jj][c] = x;
+  }
+  __syncthreads();
+  const int rows = min(NB, m.nc - rb * NB);
+  T acc[8][NR];
 #pragma unroll
-    for (int u = 0; u < kMaxCoarseLocal / 32; ++u) acc[u] = (T)0;
-#pragma unroll 4
-    for (int c = r0 + warp; c < r1; c += 8) {
-      const T x = v[c];
-      const T* row = P + (int64_t)c * nc + q0;
+  for (int r = 0; r < 8; ++r)
 #pragma unroll
-      for (int u = 0; u < kMaxCoarseLocal / 32; ++u) {
-        const int q = lane + 32 * u;
-        if (q0 + q < nc) acc[u] += row[q] * x;
+    for (int q = 0; q < NR; ++q) acc[r][q] = (T)0;
+  for (int j = j0; j < j1; ++j) {
+    const T* t = m_tile<T, MODE>(L, m, rb, j) + 2 * lane;
+    V2 xv[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) xv[q] = *(const V2*)&xs[q][j - j0][2 * lane];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int row = warp + 8 * r;
+      if (row < rows) {
+        const V2 a = __ldg((const V2*)(t + row * NB));
+#pragma unroll
+        for (int q = 0; q < NR; ++q) acc[r][q] += a.x * xv[q].x + a.y * xv[q].y;
       }
     }
+  }
 #pragma unroll
-    for (int u = 0; u < kMaxCoarseLocal / 32; ++u) red[warp][lane + 32 * u] = acc[u];
-    __syncthreads();
-    for (int q = threadIdx.x; q < kMaxCoarseLocal && q0 + q < nc; q += blockDim.x) {
-      double t = 0.0;
+  for (int r = 0; r < 8; ++r) {
+    const int row = warp + 8 * r;
+    if (row >= rows) continue;   // warp-uniform
 #pragma unroll
-      for (int w = 0; w < 8; ++w) t += (double)red[w][q];
-      part[(m.c_off + q0 + q) * kPsiSlices + z] = t;
+    for (int q = 0; q < NR; ++q) {
+      T a = acc[r][q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      if (lane == 0) part[((int64_t)q * sum_nc + m.c_off + rb * NB + row) * zmax + z] = (double)a;
     }
-    __syncthreads();
   }
 }
 
-__global__ void k_psi_t_final(const double* __restrict__ part, int64_t total, double* __restrict__ rc_sub) {
+// out[q sum_nc + g] = sum_{z < zmax} part[(q sum_nc + g) zmax + z], in order
+__global__ void k_sum_parts(const double* __restrict__ part, int zmax, int64_t total, double* __restrict__ out) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= total) return;
-  part += (int64_t)blockIdx.y * total * kPsiSlices;
-  rc_sub += (int64_t)blockIdx.y * total;
+  const int64_t o = (int64_t)blockIdx.y * total + g;
   double t = 0.0;
-#pragma unroll
-  for (int z = 0; z < kPsiSlices; ++z) t += part[g * kPsiSlices + z];
-  rc_sub[g] = t;
+  for (int z = 0; z < zmax; ++z) t += part[o * zmax + z];
+  out[o] = t;
 }
 
-// v_G += Psi_G zc_sub
-template <typename T>
-__global__ void k_psi_apply_add(LevelDev L, const double* __restrict__ zc_sub, int64_t sum_nc, T* __restrict__ vec) {
-  const int s = blockIdx.y;
+// Column products: block (j, s) makes v[nIb NB + j NB + c] += sign sum_p M[p][j NB + c] zsub_p
+// for the 64 positions of interface tile column j and NR right-hand sides (zsub column q at
+// zsub + q sum_nc, per-subdomain coarse vectors); the eight warps' partial sums are added in a
+// fixed order.
+template <typename T, int NR, int MODE>
+__global__ void __launch_bounds__(256) k_cols_matvec(LevelDev L, T* __restrict__ vec, const double* __restrict__ zsub,
+                                                     int64_t sum_nc, T sign) {
+  using V2 = typename Pair<T>::type;
+  const int j = blockIdx.x, s = blockIdx.y;
   const SubMeta m = L.meta[s];
-  const int nc = m.nc;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= m.nG) return;
-  zc_sub += (int64_t)blockIdx.z * sum_nc;
-  vec += (int64_t)blockIdx.z * L.n_vec;
-  const T* P = (const T*)L.psi + m.psi_off + (int64_t)c * nc;
-  const double* z = zc_sub + m.c_off;
-  T acc = (T)0;
-  for (int q = 0; q < nc; ++q) acc += P[q] * (T)z[q];
-  T* v = vec + m.vec_off + m.nIb * NB;
-  v[c] = v[c] + acc;
+  if (j >= m.nGb || m.nc == 0) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ T zs[NR][NB];
+  __shared__ T red[8][NR][NB];
+  T acc[NR][2];
+#pragma unroll
+  for (int q = 0; q < NR; ++q) acc[q][0] = acc[q][1] = (T)0;
+  for (int rb = 0; rb < m.ncb; ++rb) {
+    const int rows = min(NB, m.nc - rb * NB);
+    __syncthreads();
+    for (int e = threadIdx.x; e < NR * NB; e += blockDim.x) {
+      const int q = e / NB, p = e % NB;
+      zs[q][p] = p < rows ? (T)zsub[(int64_t)q * sum_nc + m.c_off + rb * NB + p] : (T)0;
+    }
+    __syncthreads();
+    const T* t = m_tile<T, MODE>(L, m, rb, j) + 2 * lane;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int row = warp + 8 * r;
+      if (row < rows) {
+        const V2 a = __ldg((const V2*)(t + row * NB));
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+          const T zq = zs[q][row];
+          acc[q][0] += a.x * zq;
+          acc[q][1] += a.y * zq;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NR; ++q) {
+    red[warp][q][2 * lane] = acc[q][0];
+    red[warp][q][2 * lane + 1] = acc[q][1];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < NR * NB; e += blockDim.x) {
+    const int q = e / NB, c = e % NB;
+    T a = (T)0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) a += red[w][q][c];
+    T* v = vec + (int64_t)q * L.n_vec + m.vec_off + (int64_t)m.nIb * NB + (int64_t)j * NB + c;
+    *v = *v + sign * a;
+  }
 }
 
+// psiT tile (rb, j)[p][c] = Psi_G[(j NB + c) nc + rb NB + p], zero outside nG x nc (set-up)
+template <typename T>
+__global__ void k_psi_transpose(LevelDev L) {
+  const int j = blockIdx.x, rb = blockIdx.y, s = blockIdx.z;
+  const SubMeta m = L.meta[s];
+  if (j >= m.nGb || rb >= m.ncb) return;
+  const T* P = (const T*)L.psi + m.psi_off;
+  T* out = (T*)L.psiT + m.psiT_off + ((int64_t)rb * m.nGb + j) * NB2;
+  __shared__ T ts[NB][NB + 1];
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int c = e / NB, p = e % NB;
+    const int gc = j * NB + c, gp = rb * NB + p;
+    ts[c][p] = (gc < m.nG && gp < m.nc) ? P[(int64_t)gc * m.nc + gp] : (T)0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) out[e] = ts[e % NB][e / NB];
+}
 
 // ---- explicit inverse of the coarsest factor (FP32 copy, mixed form) ------------------------
 // W = A_C^{-1} = L^{-T} S L^{-1} of the single-subdomain coarsest level, whose block rows are all
@@ -810,7 +883,8 @@ void launch_coarse_apply(const float* W, int64_t npad, const float* x, float* y,
 }
 
 template <typename T>
-void launch_potrf_step(const LevelDev& L, int k, int max_R, int max_tiles, int jmax, cudaStream_t st) {
+void launch_potrf_step(const LevelDev& L, int k, int max_R, int max_tiles, int jmax, cudaStream_t st, int skip_diag,
+                       int fuse_next) {
   const unsigned ns = (unsigned)L.n_sub;
   const size_t sm = 2 * NB * LDS * sizeof(T);
   const size_t sm_diag = 2 * NB * (NB + 1) * sizeof(T);
@@ -821,10 +895,14 @@ void launch_potrf_step(const LevelDev& L, int k, int max_R, int max_tiles, int j
     cudaFuncSetAttribute(k_syrk_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     attr = true;
   }
-  { note_launch(); k_potrf_diag<T><<<ns, 256, sm_diag, st>>>(L, k); }
+  static_assert(2 * NB * LDS >= 2 * NB * (NB + 1), "the update's shared memory holds the diagonal factorisation");
+  if (!skip_diag) { note_launch(); k_potrf_diag<T><<<ns, 256, sm_diag, st>>>(L, k); }
   const int panel = max_R - k - 1;
   if (panel > 0) { note_launch(); k_trsm_panel<T><<<dim3((unsigned)panel, ns), 256, sm, st>>>(L, k); }
-  if (max_tiles > 0) { note_launch(); k_syrk_update<T><<<dim3((unsigned)max_tiles, ns), 256, sm, st>>>(L, k, jmax); }
+  if (max_tiles > 0) {
+    note_launch();
+    k_syrk_update<T><<<dim3((unsigned)max_tiles, ns), 256, sm, st>>>(L, k, jmax, fuse_next);
+  }
 }
 
 template <typename T>
@@ -857,38 +935,100 @@ void launch_psi(const LevelDev& L, int max_nGb, int max_nc, cudaStream_t st) {
 
 // The solve-phase launches below take nr right-hand sides: local vectors of n_vec, per-subdomain
 // coarse vectors of sum nc entries per column.
+template <typename T, int MODE>
+void rows_matvec(const LevelDev& L, const T* vec, double* part, int64_t sum_nc, int max_nGb, int max_ncb,
+                 cudaStream_t st, int nr) {
+  const int zmax = rows_zmax(max_nGb);
+  const dim3 grid((unsigned)zmax, (unsigned)max_ncb, (unsigned)L.n_sub);
+  constexpr int kMaxNR = sizeof(T) == 4 ? 8 : 4;
+  for (int r0 = 0; r0 < nr;) {
+    const int left = nr - r0;
+    const int g = left >= kMaxNR ? kMaxNR : left >= 4 ? 4 : left >= 2 ? 2 : 1;
+    const T* v = vec + (int64_t)r0 * L.n_vec;
+    double* pt = part + (int64_t)r0 * sum_nc * zmax;
+    note_launch();
+    if (g == 8)
+      k_rows_matvec<T, (sizeof(T) == 4 ? 8 : 4), MODE><<<grid, 256, 0, st>>>(L, v, pt, zmax, sum_nc);
+    else if (g == 4)
+      k_rows_matvec<T, 4, MODE><<<grid, 256, 0, st>>>(L, v, pt, zmax, sum_nc);
+    else if (g == 2)
+      k_rows_matvec<T, 2, MODE><<<grid, 256, 0, st>>>(L, v, pt, zmax, sum_nc);
+    else
+      k_rows_matvec<T, 1, MODE><<<grid, 256, 0, st>>>(L, v, pt, zmax, sum_nc);
+    r0 += g;
+  }
+}
+
+template <typename T, int MODE>
+void cols_matvec(const LevelDev& L, T* vec, const double* zsub, int64_t sum_nc, int max_nGb, T sign, cudaStream_t st,
+                 int nr) {
+  const dim3 grid((unsigned)max_nGb, (unsigned)L.n_sub);
+  constexpr int kMaxNR = sizeof(T) == 4 ? 8 : 4;
+  for (int r0 = 0; r0 < nr;) {
+    const int left = nr - r0;
+    const int g = left >= kMaxNR ? kMaxNR : left >= 4 ? 4 : left >= 2 ? 2 : 1;
+    T* v = vec + (int64_t)r0 * L.n_vec;
+    const double* zz = zsub + (int64_t)r0 * sum_nc;
+    note_launch();
+    if (g == 8)
+      k_cols_matvec<T, (sizeof(T) == 4 ? 8 : 4), MODE><<<grid, 256, 0, st>>>(L, v, zz, sum_nc, sign);
+    else if (g == 4)
+      k_cols_matvec<T, 4, MODE><<<grid, 256, 0, st>>>(L, v, zz, sum_nc, sign);
+    else if (g == 2)
+      k_cols_matvec<T, 2, MODE><<<grid, 256, 0, st>>>(L, v, zz, sum_nc, sign);
+    else
+      k_cols_matvec<T, 1, MODE><<<grid, 256, 0, st>>>(L, v, zz, sum_nc, sign);
+    r0 += g;
+  }
+}
+
 template <typename T>
 void launch_constraint_corr(const LevelDev& L, T* vec, const int32_t* crow_sub, int64_t total_rows, double* t,
-                            double* mu, int max_nGb, cudaStream_t st, int nr) {
-  if (total_rows <= 0) return;
+                            double* mu, double* part, int max_nGb, int max_ncb, cudaStream_t st, int nr) {
+  if (total_rows <= 0 || max_nGb <= 0) return;
+  rows_matvec<T, 0>(L, vec, part, total_rows, max_nGb, max_ncb, st, nr);
+  const int zmax = rows_zmax(max_nGb);
+  note_launch();
+  k_sum_parts<<<dim3((unsigned)((total_rows + 255) / 256), (unsigned)nr), 256, 0, st>>>(part, zmax, total_rows, t);
   const unsigned g = (unsigned)((total_rows + 7) / 8);
-  { note_launch(); k_cc_yv<T><<<dim3(g, nr), 256, 0, st>>>(L, vec, crow_sub, total_rows, t); }
   { note_launch(); k_cc_mu<<<dim3(g, nr), 256, 0, st>>>(L, crow_sub, total_rows, t, mu); }
-  { note_launch(); k_cc_update<T><<<dim3((unsigned)((max_nGb * NB + 255) / 256), (unsigned)L.n_sub, nr), 256, 0, st>>>(L, vec, mu, total_rows); }
+  cols_matvec<T, 0>(L, vec, mu, total_rows, max_nGb, (T)-1, st, nr);
 }
 
 template <typename T>
-void launch_psi_t_apply(const LevelDev& L, const T* vec, double* part, int64_t sum_nc, double* rc_sub,
-                        cudaStream_t st, int nr) {
-  if (sum_nc <= 0) return;
-  { note_launch(); k_psi_t_part<T><<<dim3(kPsiSlices, (unsigned)L.n_sub, nr), 256, 0, st>>>(L, vec, part, sum_nc); }
-  { note_launch(); k_psi_t_final<<<dim3((unsigned)((sum_nc + 255) / 256), nr), 256, 0, st>>>(part, sum_nc, rc_sub); }
+void launch_psi_t_apply(const LevelDev& L, const T* vec, double* part, int64_t sum_nc, double* rc_sub, int max_nGb,
+                        int max_ncb, cudaStream_t st, int nr) {
+  if (sum_nc <= 0 || max_nGb <= 0) return;
+  rows_matvec<T, 1>(L, vec, part, sum_nc, max_nGb, max_ncb, st, nr);
+  const int zmax = rows_zmax(max_nGb);
+  note_launch();
+  k_sum_parts<<<dim3((unsigned)((sum_nc + 255) / 256), (unsigned)nr), 256, 0, st>>>(part, zmax, sum_nc, rc_sub);
 }
 
 template <typename T>
-void launch_psi_apply_add(const LevelDev& L, const double* zc_sub, int64_t sum_nc, T* vec, int max_nG,
+void launch_psi_apply_add(const LevelDev& L, const double* zc_sub, int64_t sum_nc, T* vec, int max_nGb, int max_ncb,
                           cudaStream_t st, int nr) {
-  if (max_nG <= 0) return;
-  { note_launch(); k_psi_apply_add<T><<<dim3((unsigned)((max_nG + 255) / 256), (unsigned)L.n_sub, nr), 256, 0, st>>>(L, zc_sub, sum_nc, vec); }
+  if (sum_nc <= 0 || max_nGb <= 0) return;
+  (void)max_ncb;
+  cols_matvec<T, 1>(L, vec, zc_sub, sum_nc, max_nGb, (T)1, st, nr);
+}
+
+template <typename T>
+void launch_psi_transpose(const LevelDev& L, int max_nGb, int max_ncb, cudaStream_t st) {
+  if (max_nGb <= 0 || max_ncb <= 0) return;
+  note_launch();
+  k_psi_transpose<T><<<dim3((unsigned)max_nGb, (unsigned)max_ncb, (unsigned)L.n_sub), 256, 0, st>>>(L);
 }
 
 #define INST(T)                                                                                 \
-  template void launch_potrf_step<T>(const LevelDev&, int, int, int, int, cudaStream_t);         \
+  template void launch_potrf_step<T>(const LevelDev&, int, int, int, int, cudaStream_t, int, int); \
   template void launch_psi<T>(const LevelDev&, int, int, cudaStream_t);                          \
-  template void launch_constraint_corr<T>(const LevelDev&, T*, const int32_t*, int64_t, double*, double*, int, \
-                                         cudaStream_t, int);                                              \
-  template void launch_psi_t_apply<T>(const LevelDev&, const T*, double*, int64_t, double*, cudaStream_t, int); \
-  template void launch_psi_apply_add<T>(const LevelDev&, const double*, int64_t, T*, int, cudaStream_t, int);
+  template void launch_constraint_corr<T>(const LevelDev&, T*, const int32_t*, int64_t, double*, double*, double*, \
+                                         int, int, cudaStream_t, int);                                     \
+  template void launch_psi_t_apply<T>(const LevelDev&, const T*, double*, int64_t, double*, int, int, cudaStream_t, \
+                                      int);                                                              \
+  template void launch_psi_apply_add<T>(const LevelDev&, const double*, int64_t, T*, int, int, cudaStream_t, int); \
+  template void launch_psi_transpose<T>(const LevelDev&, int, int, cudaStream_t);
 INST(float)
 INST(double)
 #undef INST

@@ -24,7 +24,6 @@
 namespace bddc {
 
 constexpr int NB = 64;            // tile edge
-constexpr int kPsiSlices = 8;     // interface-row slices per subdomain in the Psi^T product
 constexpr int64_t NB2 = NB * NB;
 
 struct SubMeta {
@@ -39,6 +38,7 @@ struct SubMeta {
   int64_t c_off;                  // offset of the per-subdomain coarse vector (nc)
   int64_t g_off;                  // offset of nc x nc matrices (G^{-1}, K_C)
   int64_t psi_off;                // offset of Psi_G (nGb*NB rows x nc, row-major)
+  int64_t psiT_off;               // offset of Psi_G^T as ncb x nGb tiles (set-up copy for the solve phase)
 };
 
 // Raw device pointers of one level, passed by value to kernels.
@@ -83,6 +83,7 @@ struct LevelDev {
   void* tiles;                    // factor tiles (float or double)
   void* dinv;                     // diagonal inverses
   void* psi;                      // Psi_G
+  void* psiT;                     // Psi_G^T in tiles: tile (rb, j) of a subdomain at psiT_off + (rb nGb + j) NB2
   void* sgn;                      // [n_vec] pivot signs of the signed Cholesky (T; +1 for SPD levels)
   const double* c_rho;            // [sum nc] 1 where a constraint row is augmented by rho, else 0
   int indefinite;                 // 1: negative pivots allowed (Stokes), 0: SPD
@@ -128,9 +129,13 @@ void launch_add_constraints(const LevelDev& L, cudaStream_t st);
 void launch_weights(const LevelDev& L, int multiplicity, const double* unused, cudaStream_t st);
 
 // ---------------------------------------------------------------- dense factor (dense.cu)
-// one block column k: diagonal tile + inverse, panel, trailing update of columns (k, jmax)
+// one block column k: diagonal tile + inverse, panel, trailing update of columns (k, jmax).
+// skip_diag: the diagonal tile k was factored by the previous step's update (fuse_next there);
+// fuse_next: the update's block for tile (k+1, k+1) factors it (only when max_tiles > 0 and
+// k + 1 < jmax, i.e. that tile receives its last update in this step).
 template <typename T>
-void launch_potrf_step(const LevelDev& L, int k, int max_R, int max_tiles, int jmax, cudaStream_t st);
+void launch_potrf_step(const LevelDev& L, int k, int max_R, int max_tiles, int jmax, cudaStream_t st,
+                       int skip_diag = 0, int fuse_next = 0);
 // update_tc.cu, FP32 levels with tensor cores: rank-(64 nt) update of the output columns
 // ib <= j < jend from the nt panel tile columns kb0 .. kb0+nt-1 (nt = 4 or 8).  k_split_panel
 // writes the two scaled FP16 parts of the panel tiles L(i, kb0 + q), i >= ib, at
@@ -173,13 +178,21 @@ void launch_sweep(const LevelDev& L, T* vec, const int2* tasks, int ntasks, int 
 // crow_sub: subdomain of every constraint row (flat over the level); t, mu: scratch [nr][total_rows]
 template <typename T>
 void launch_constraint_corr(const LevelDev& L, T* vec, const int32_t* crow_sub, int64_t total_rows, double* t,
-                            double* mu, int max_nGb, cudaStream_t st, int nr = 1);
+                            double* mu, double* part, int max_nGb, int max_ncb, cudaStream_t st, int nr = 1);
+// The products with Y_G (constraint block rows of the factor) and with Psi_G^T (psiT) stream
+// those tiles once per group of up to 8 right-hand sides: row products t = M v over chunks of 4
+// tile columns (partial sums part[(c_off + p) * zmax + z], zmax = ceil(max_nGb / 4), summed in a
+// fixed order), column products v += M^T z one CTA per interface tile column.
 template <typename T>
 void launch_psi_t_apply(const LevelDev& L, const T* vec, double* part, int64_t sum_nc, double* rc_sub,
-                        cudaStream_t st, int nr = 1);
+                        int max_nGb, int max_ncb, cudaStream_t st, int nr = 1);
 template <typename T>
-void launch_psi_apply_add(const LevelDev& L, const double* zc_sub, int64_t sum_nc, T* vec, int max_nG,
-                          cudaStream_t st, int nr = 1);
+void launch_psi_apply_add(const LevelDev& L, const double* zc_sub, int64_t sum_nc, T* vec, int max_nGb,
+                          int max_ncb, cudaStream_t st, int nr = 1);
+// psiT from Psi_G (set-up, after launch_psi)
+template <typename T>
+void launch_psi_transpose(const LevelDev& L, int max_nGb, int max_ncb, cudaStream_t st);
+inline int rows_zmax(int max_nGb) { return (max_nGb + 3) / 4; }
 
 // ---------------------------------------------------------------- vectors (vector.cu)
 template <typename T>

@@ -32,37 +32,51 @@ __device__ __forceinline__ void store4h(uint8_t* part, uint32_t off, const __hal
   *(uint2*)(part + off) = v;
 }
 
-// Split the panel tiles L(i, kb0 .. kb0 + NT - 1) of subdomain s; 64 NT threads, thread (r, c4)
-// takes row r of tile column kb0 + c4 (the NT threads of a row, adjacent lanes, share its scale).
+// Split the panel tiles L(i, kb0 .. kb0 + NT - 1) of subdomain s; 64 NT threads (2 NT warps).
+// Warp w takes tile column c = w / 2 and the rows 32 (w % 2) .. + 31; lane l the four entries
+// 4 (l % 16) .. + 3 of the rows 2k + l / 16, so that 16 lanes read a 256-byte row of a tile at
+// once and write its 128-byte FP16 image at once.  Pass 1 loads the warp's 32 rows (16 float4
+// per lane) and records each row's maximum within the tile; after one barrier, pass 2 takes the
+// row's maximum over the NT tiles and writes the scaled parts.
 template <int NT>
 __device__ __forceinline__ void split_row_tile(const LevelDev& L, int s, const SubMeta& m, int i, int kb0,
                                                uint8_t* __restrict__ split, uint8_t* __restrict__ split_signed,
                                                float* __restrict__ rscale, const int64_t* __restrict__ prow_off) {
   static_assert(NT == 4 || NT == 8, "panel width");
-  const int r = threadIdx.x / NT, c4 = threadIdx.x % NT;
+  __shared__ float pmax[NT][NB];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = warp >> 1, r0 = 32 * (warp & 1), u = lane & 15, half = lane >> 4;
   const float4* t =
-      (const float4*)((const float*)L.tiles + m.tile_off + split_tile_index(i, kb0 + c4, m.Bc) * NB2 + r * NB);
+      (const float4*)((const float*)L.tiles + m.tile_off + split_tile_index(i, kb0 + c, m.Bc) * NB2) + u;
   float4 v[16];
-  float mx = 0.f;
 #pragma unroll
-  for (int u = 0; u < 16; ++u) {
-    v[u] = __ldcg(t + u);
-    mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v[u].x), fabsf(v[u].y)), fmaxf(fabsf(v[u].z), fabsf(v[u].w))));
-  }
+  for (int k = 0; k < 16; ++k) {
+    const int r = r0 + 2 * k + half;
+    v[k] = __ldcg(t + r * (NB / 4));
+    float mx = fmaxf(fmaxf(fabsf(v[k].x), fabsf(v[k].y)), fmaxf(fabsf(v[k].z), fabsf(v[k].w)));
 #pragma unroll
-  for (int o = 1; o < NT; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  int ex = 0;
-  if (mx > 0.f) {
-    int k;
-    frexpf(mx, &k);   // mx = f 2^k, f in [0.5, 1)
-    ex = 15 - k;      // mx 2^ex in [2^14, 2^15)
+    for (int o = 8; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (u == 0) pmax[c][r] = mx;
   }
+  __syncthreads();
   const int64_t row = prow_off[s] + i;
-  if (c4 == 0) rscale[row * NB + r] = ldexpf(1.f, -ex);   // exact power of two
-  uint8_t* dst = split + (row * kPanelTiles + c4) * (int64_t)kSplitTile;
+  uint8_t* dst = split + (row * kPanelTiles + c) * (int64_t)kSplitTile;
+  uint8_t* dsg = split_signed ? split_signed + (row * kPanelTiles + c) * (int64_t)kSplitTile : nullptr;
+  const float* sq = (const float*)L.sgn + m.vec_off + (int64_t)(kb0 + c) * NB + 4 * u;   // pivot signs of the columns
 #pragma unroll
-  for (int u = 0; u < 16; ++u) {
-    const float a[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+  for (int k = 0; k < 16; ++k) {
+    const int r = r0 + 2 * k + half;
+    float mx = 0.f;
+#pragma unroll
+    for (int q = 0; q < NT; ++q) mx = fmaxf(mx, pmax[q][r]);
+    int ex = 0;
+    if (mx > 0.f) {
+      int e;
+      frexpf(mx, &e);   // mx = f 2^e, f in [0.5, 1)
+      ex = 15 - e;      // mx 2^ex in [2^14, 2^15)
+    }
+    if (c == 0 && u == 0) rscale[row * NB + r] = ldexpf(1.f, -ex);   // exact power of two
+    const float a[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
     __half h[4], l[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
@@ -73,9 +87,7 @@ __device__ __forceinline__ void split_row_tile(const LevelDev& L, int s, const S
     const uint32_t off = sw128_off(r, 4 * u);
     store4h(dst, off, h);
     store4h(dst + kTilePart, off, l);
-    if (split_signed) {   // indefinite levels: the B operand is L(j, q) S_q (pivot signs of column q)
-      const float* sq = (const float*)L.sgn + m.vec_off + (int64_t)(kb0 + c4) * NB + 4 * u;
-      uint8_t* dsg = split_signed + (row * kPanelTiles + c4) * (int64_t)kSplitTile;
+    if (dsg) {   // indefinite levels: the B operand is L(j, q) S_q (pivot signs of column q)
 #pragma unroll
       for (int e = 0; e < 4; ++e)
         if (sq[e] < 0.f) {

@@ -71,14 +71,15 @@ __global__ void __launch_bounds__(256) k_trmv_t(LevelDev L, const float* __restr
   }
 }
 
-// y_i = sum_{nIb <= j <= i} L(i,j) S_j y1_j; block (o, s, group) makes output block i = nIb + o.
-// Warp w takes rows w, w+8, ..., lane l the columns 2l, 2l+1.
+// y_i = sum_{nIb <= j <= i} L(i,j) S_j y1_j; block (o', s, group) makes output block i = nIb + o
+// with o = nGb - 1 - o' (the longest block rows are scheduled first, so that the short ones fill
+// the tail of the launch).  Warp w takes rows w, w+8, ..., lane l the columns 2l, 2l+1.
 template <int NR>
 __global__ void __launch_bounds__(256) k_trmv_n(LevelDev L, const float* __restrict__ y1, float* __restrict__ y) {
   const int s = blockIdx.y;
   const SubMeta m = L.meta[s];
-  const int o = blockIdx.x;
-  if (o >= m.nGb) return;
+  if ((int)blockIdx.x >= m.nGb) return;
+  const int o = m.nGb - 1 - (int)blockIdx.x;
   const int i = m.nIb + o;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t c0 = (int64_t)blockIdx.z * NR * L.n_vec;
