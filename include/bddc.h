@@ -133,6 +133,15 @@ typedef struct {
                                its bounded-wait error path and the call reports BDDC_ERR_TIMEOUT (the
                                results of such a call are meaningless; the CUDA context stays usable).
                                Tile-copy waits are not affected. */
+  int inner_operator;       /* mixed PCG, inner operator S~ of the outer refinement: 0 = automatic
+                               (the explicit form when the interior padding it needs adds at most 8 %
+                               to the interior factor, else the factor products), 1 = products with
+                               the stored interface factor, S~ x = L_GG S L_GG^T x - C^T R C x,
+                               2 = the explicit augmented Schur complement S_i + C_i^T R C_i, copied
+                               from the tiles when the interior is eliminated (the interior block
+                               count is padded to a multiple of 4 tiles), one pass over its lower
+                               triangle per product.  Elasticity and Poisson with tensor cores only;
+                               otherwise 1 */
 } bddc_opts;
 
 #define BDDC_KRYLOV_AUTO 0
@@ -179,6 +188,8 @@ typedef struct {
   double tune_ms;                              /* time spent autotuning in the last set-up (0 when cached) */
   double prepare_ms;                           /* device set-up of the last bddc_setup: level layouts, maps,
                                                   allocations and uploads (between analysis and factor) */
+  int inner_operator;                          /* inner operator of the mixed PCG: 0 none, 1 factor
+                                                  products, 2 explicit augmented Schur complement */
 } bddc_stats;
 
 /* Index maps of one level, library-owned, valid until bddc_free (for bit-exact checks).
@@ -255,6 +266,14 @@ int bddc_apply_precond(bddc_handle h, const double* r, double* z, int nrhs);
 /* The reduced interface operator of Sec. 2, y = S x = sum_i R_i^T (K_GG - K_GI K_II^{-1} K_IG) R_i x,
  * computed with discrete Dirichlet problems.  x, y: device [nrhs][n_iface] FP64. */
 int bddc_apply_schur(bddc_handle h, const double* x, double* y, int nrhs);
+
+/* The inner operator of the mixed form's outer refinement (mixed-precision PCG handles only):
+ * y = sum_i R_i^T S~_i R_i x with S~_i = S_i + C_i^T R C_i - C_i^T R C_i evaluated from FP32 data
+ * (the factor products or the explicit augmented Schur complement, see bddc_opts.inner_operator),
+ * FP32 products, FP64 in and out; it equals the FP64 operator of bddc_apply_schur up to the FP32
+ * factorisation's error.  Same layout and streams as bddc_apply_schur.  Errors: INVALID (no
+ * set-up, not a mixed-precision PCG handle), CUDA. */
+int bddc_apply_inner_schur(bddc_handle h, const double* x, double* y, int nrhs);
 
 /* Adjoint gradient of a scalar J(u) with u = K(coef)^{-1} f: solves K lambda_k = dJdu_k with
  * the same factors (K is symmetric), then grad_rhs = lambda and

@@ -34,7 +34,7 @@ EXPORTED = [
     "bddc_solve_host", "bddc_apply_precond", "bddc_apply_schur", "bddc_grad", "bddc_get_maps",
     "bddc_get_stats", "bddc_sizes", "bddc_free", "bddc_last_error", "bddc_kernel_launches",
     "bddc_reset_profile", "bddc_grad_noalloc", "bddc_batching_ablation", "bddc_get_coarse",
-    "bddc_tc_update_check",
+    "bddc_tc_update_check", "bddc_apply_inner_schur",
 ]
 PROF_TRSV, PROF_FACTOR, PROF_SPMV, PROF_TRMV, PROF_TRSV_IFACE, PROF_COARSE, PROF_TC_UPDATE, PROF_CLASSES = (
     0, 1, 2, 3, 4, 5, 6, 7)
@@ -62,7 +62,7 @@ class Opts(C.Structure):
         ("precision", C.c_int), ("weights", C.c_int), ("all_corners", C.c_uint), ("maxit", C.c_int),
         ("refine_steps", C.c_int), ("flexible", C.c_int), ("use_graph", C.c_int), ("verbose", C.c_int),
         ("profile", C.c_int), ("tensor_cores", C.c_int), ("inner_steps", C.c_int), ("inner_tol", C.c_double),
-        ("krylov", C.c_int), ("autotune", C.c_int), ("wait_probe", C.c_int),
+        ("krylov", C.c_int), ("autotune", C.c_int), ("wait_probe", C.c_int), ("inner_operator", C.c_int),
     ]
 
 
@@ -80,6 +80,7 @@ class Stats(C.Structure):
         ("prof_bytes", C.c_double * PROF_CLASSES), ("prof_flops", C.c_double * PROF_CLASSES),
         ("sweep_ctas", C.c_int * (2 * MAX_LEVELS)), ("sweep_deep", C.c_int * (2 * MAX_LEVELS)),
         ("sweep_order", C.c_int * (2 * MAX_LEVELS)), ("tune_ms", C.c_double), ("prepare_ms", C.c_double),
+        ("inner_operator", C.c_int),
     ]
 
 
@@ -121,6 +122,7 @@ def lib() -> C.CDLL:
                                   C.POINTER(Stats)]
     L.bddc_apply_precond.argtypes = [H, P, P, C.c_int]
     L.bddc_apply_schur.argtypes = [H, P, P, C.c_int]
+    L.bddc_apply_inner_schur.argtypes = [H, P, P, C.c_int]
     L.bddc_grad.argtypes = [H, P, P, C.c_int, C.c_double, P, P]
     L.bddc_grad_noalloc.argtypes = [H, P, P, C.c_int, C.c_double, P, P]
     L.bddc_get_maps.argtypes = [H, C.c_int, C.POINTER(LevelMaps)]

@@ -119,6 +119,13 @@ struct Level {
   int64_t n_vec = 0, tile_elems = 0, dinv_elems = 0, psi_elems = 0, g_elems = 0, sum_nc = 0;
   int max_R = 0, max_Bc = 0, max_nc = 0, max_nG = 0, max_nGb = 0, max_ncb = 0;
   int64_t psiT_elems = 0;
+  // explicit augmented Schur complement of the interface (mixed inner operator, level 1 only)
+  bool explicit_schur = false;
+  int64_t schur_elems = 0;
+  int64_t symv_stride = 0;            // floats of the symmetric product's column parts per right-hand side
+  int64_t* symv_part_off = nullptr;   // [n_sub] their offsets
+  float* symv_part = nullptr;         // [blk][symv_stride]
+  std::vector<char> snap_start, snap_mid;   // per super-panel p: some nIb == 8p / == 8p + 4
   std::vector<int> max_tiles;  // per factor step k
   std::vector<double> step_flops;  // tile flops of factor step k (all subdomains)
   std::vector<int> narrow_tiles;   // per step k: in-panel update tiles (256-wide sub-panels)
@@ -202,6 +209,7 @@ void alloc_level_work(Level& L, DevArena& A, int blk) {
     L.locB = A.alloc<double>(nv);
   }
   L.pub = A.alloc<double>(L.n_vec * std::min(blk, 8));
+  if (L.explicit_schur) L.symv_part = A.alloc<float>(std::max<int64_t>(L.symv_stride, 1) * blk);
   L.dl0 = A.alloc<double>(nv);
   L.dl1 = A.alloc<double>(nv);
   L.dl2 = A.alloc<double>(nv);
@@ -503,8 +511,22 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
   const LevelMesh& ms = L.mesh;
   const int64_t ns = mp.n_sub();
   L.meta.resize(ns);
-  int64_t tile = 0, dinv = 0, vec = 0, coff = 0, goff = 0, psi = 0, psiT = 0;
+  int64_t tile = 0, dinv = 0, vec = 0, coff = 0, goff = 0, psi = 0, psiT = 0, schur = 0, symv = 0;
   L.max_R = L.max_Bc = L.max_nc = L.max_nG = L.max_nGb = L.max_ncb = 0;
+  // the explicit inner operator snapshots the trailing interface block when the interior is
+  // eliminated; the batched factorisation reaches that point for every subdomain at a sub-panel
+  // boundary only if the interior block count is a multiple of kSub (identity tiles pad it)
+  L.explicit_schur = false;
+  if (&L == &h->lv[0] && L.fp32 && h->opts.tensor_cores && h->physics != BDDC_STOKES &&
+      krylov_kind(h) == BDDC_KRYLOV_PCG && h->opts.inner_operator != 1) {
+    double base = 0.0, padded = 0.0;
+    for (int64_t s = 0; s < ns; ++s) {
+      const double b = (double)ceil_div(mp.sub_nI[s], NB), bp = (double)(ceil_div(ceil_div(mp.sub_nI[s], NB), kSub) * kSub);
+      base += b * (b + 1) / 2;
+      padded += bp * (bp + 1) / 2;
+    }
+    L.explicit_schur = h->opts.inner_operator == 2 || padded <= 1.08 * base;
+  }
   for (int64_t s = 0; s < ns; ++s) {
     SubMeta& m = L.meta[s];
     m.n = (int32_t)(mp.sub_dof_ptr[s + 1] - mp.sub_dof_ptr[s]);
@@ -512,6 +534,7 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
     m.nG = m.n - m.nI;
     m.nc = (int32_t)(mp.sub_coarse_ptr[s + 1] - mp.sub_coarse_ptr[s]);
     m.nIb = (int32_t)ceil_div(m.nI, NB);
+    if (L.explicit_schur) m.nIb = (int32_t)(ceil_div(m.nIb, kSub) * kSub);
     m.nGb = (int32_t)ceil_div(m.nG, NB);
     m.ncb = (int32_t)ceil_div(m.nc, NB);
     m.Bc = m.nIb + m.nGb;
@@ -532,6 +555,9 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
     psi += (int64_t)m.nGb * NB * m.nc;
     m.psiT_off = psiT;
     psiT += (int64_t)m.ncb * m.nGb * NB2;
+    m.schur_off = schur;
+    if (L.explicit_schur) schur += (int64_t)m.nGb * (m.nGb + 1) / 2 * NB2;
+    symv += (int64_t)m.nGb * (m.nGb - 1) / 2 * NB;
     L.max_R = std::max(L.max_R, (int)m.R);
     L.max_Bc = std::max(L.max_Bc, (int)m.Bc);
     L.max_nc = std::max(L.max_nc, (int)m.nc);
@@ -544,6 +570,8 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
   L.dinv_elems = dinv;
   L.psi_elems = psi;
   L.psiT_elems = psiT;
+  L.schur_elems = schur;
+  L.symv_stride = L.explicit_schur ? symv : 0;
   L.g_elems = goff;
   L.sum_nc = coff;
   L.max_tiles.assign(L.max_Bc, 0);
@@ -551,8 +579,10 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
   L.narrow_tiles.assign(L.max_Bc, 0);
   L.panel_flops.assign(L.max_Bc, 0.0);
   const int n_super = (L.max_Bc + kPanel - 1) / kPanel + 1;
-  L.tc_items.assign(2 * (size_t)n_super, 0);
-  L.tc_flops.assign(2 * (size_t)n_super, 0.0);
+  L.tc_items.assign(3 * (size_t)n_super, 0);
+  L.tc_flops.assign(3 * (size_t)n_super, 0.0);
+  L.snap_start.assign(n_super, 0);
+  L.snap_mid.assign(n_super, 0);
   const double nb3 = (double)NB * NB * NB;
   const double wsz = L.fp32 ? 4.0 : 8.0;
   L.trsv_bytes[0] = L.trsv_bytes[1] = 0.0;
@@ -576,8 +606,14 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
       int64_t tiles[2] = {0, 0};
       for (int j = kb0 + kSub; j < std::min(kb0 + kPanel, (int)m.Bc); ++j) tiles[0] += m.R - j;
       for (int j = kb0 + kPanel; j < m.Bc; ++j) tiles[1] += m.R - j;
-      L.tc_flops[2 * (kb0 / kPanel)] += 2.0 * nb3 * kSub * (double)tiles[0];
-      L.tc_flops[2 * (kb0 / kPanel) + 1] += 2.0 * nb3 * kPanel * (double)tiles[1];
+      const int p = kb0 / kPanel;
+      L.tc_flops[3 * p] += 2.0 * nb3 * kSub * (double)tiles[0];
+      L.tc_flops[3 * p + 1] += 2.0 * nb3 * kPanel * (double)tiles[1];
+      L.tc_flops[3 * p + 2] += 2.0 * nb3 * kSub * (double)(tiles[0] + tiles[1]);
+    }
+    if (L.explicit_schur) {   // where this subdomain's interior ends: a super-panel start or middle
+      if (m.nIb % kPanel == 0) L.snap_start[m.nIb / kPanel] = 1;
+      else L.snap_mid[m.nIb / kPanel] = 1;
     }
     // a sweep reads the stored triangle once and the vector in and out
     L.trsv_bytes[0] += wsz * (0.5 * (double)m.nI * (m.nI + 1) + 2.0 * m.nI);
@@ -761,13 +797,15 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
     L.split = A.alloc<uint8_t>(rows * kPanel * 2 * NB2 * 2);
     if (h->physics == BDDC_STOKES) L.split_signed = A.alloc<uint8_t>(rows * kPanel * 2 * NB2 * 2);
     L.rscale = A.alloc<float>(rows * NB);
-    // work items (128 x 128 output blocks) of both updates of every super-panel, flattened over
-    // the subdomains; update 0 covers the columns [kb0 + kSub, kb0 + kPanel), update 1 the rest
+    // work items (128 x 128 output blocks) of the updates of every super-panel, flattened over the
+    // subdomains; update 0 covers the columns [kb0 + kSub, kb0 + kPanel), update 1 the columns
+    // >= kb0 + kPanel, update 2 (a super-panel where some interior ends in the middle, explicit
+    // inner operator) the columns >= kb0 + kSub
     const int nu = (int)L.tc_items.size();
     std::vector<int64_t> pref((size_t)nu * (ns + 1), 0);
     for (int u = 0; u < nu; ++u) {
-      const int kb0 = (u / 2) * kPanel;
-      const int jbeg = kb0 + (u % 2 ? kPanel : kSub), jend = u % 2 ? (1 << 30) : kb0 + kPanel;
+      const int kb0 = (u / 3) * kPanel;
+      const int jbeg = kb0 + (u % 3 == 1 ? kPanel : kSub), jend = u % 3 == 0 ? kb0 + kPanel : (1 << 30);
       int64_t acc = 0;
       for (int64_t s = 0; s < ns; ++s) {
         pref[(size_t)u * (ns + 1) + s] = acc;
@@ -788,11 +826,22 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
     d.dinv = A.alloc<float>(L.dinv_elems);
     d.psi = A.alloc<float>(L.psi_elems);
     d.psiT = A.alloc<float>(L.psiT_elems);
+    d.schur = L.explicit_schur ? A.alloc<float>(L.schur_elems) : nullptr;
+    if (L.explicit_schur) {
+      std::vector<int64_t> po(ns);
+      int64_t o = 0;
+      for (int64_t s2 = 0; s2 < ns; ++s2) {
+        po[s2] = o;
+        o += (int64_t)L.meta[s2].nGb * (L.meta[s2].nGb - 1) / 2 * NB;
+      }
+      L.symv_part_off = A.upload(po, st);
+    }
   } else {
     d.tiles = A.alloc<double>(L.tile_elems);
     d.dinv = A.alloc<double>(L.dinv_elems);
     d.psi = A.alloc<double>(L.psi_elems);
     d.psiT = A.alloc<double>(L.psiT_elems);
+    d.schur = nullptr;
   }
   (void)ts;
   d.status = h->d_status;
@@ -891,9 +940,20 @@ void factor_level(bddc_handle_s* h, Level& L, cudaStream_t st) {
     // rank-512 update of every trailing column after the second
     for (int kb0 = 0; kb0 < L.max_Bc; kb0 += kPanel) {
       const int p = kb0 / kPanel;
+      // explicit inner operator: the trailing interface block of every subdomain whose interior
+      // ends here is its augmented Schur complement (all interior updates applied, no interface
+      // column factored yet)
+      if (L.explicit_schur && L.snap_start[p]) launch_schur_snapshot(d, kb0, L.max_nGb, st);
+      // a super-panel in which some interior ends after its first half takes two rank-256
+      // updates of all trailing columns instead of the rank-256 / rank-512 pair, so that the
+      // Schur complement exists between them
+      const bool split_mid = L.explicit_schur && L.snap_mid[p];
       for (int half = 0; half < 2; ++half) {
         const int k0 = kb0 + half * kSub, k1 = k0 + kSub;
-        const int u = 2 * p + half;
+        const int u = 3 * p + (half ? 1 : (split_mid ? 2 : 0));
+        const int nq = split_mid ? kSub : (half ? kPanel : kSub);   // K tiles of the update
+        const int kq = split_mid ? k0 : kb0;                        // its first K column
+        const int jend = (half || split_mid) ? (1 << 30) : kb0 + kPanel;
         {
           double fl = 0.0;
           for (int k = k0; k < std::min(k1, L.max_Bc); ++k) fl += L.panel_flops[k];
@@ -905,17 +965,17 @@ void factor_level(bddc_handle_s* h, Level& L, cudaStream_t st) {
             fused = fuse;
           }
           if (L.split && L.tc_items[u] > 0)
-            launch_split_panel(d, kb0, half ? kPanel : kSub, k1, L.max_R, L.split, L.split_signed, L.rscale,
-                               L.prow_off, st);
+            launch_split_panel(d, kq, nq, k1, L.max_R, L.split, L.split_signed, L.rscale, L.prow_off, st);
         }
         const int64_t items = L.tc_items[u];
         if (L.split && items > 0) {   // no launch where no subdomain has columns left
-          ProfScope ps(h, BDDC_PROF_TC_UPDATE, 0.0, L.tc_flops[u], st);
-          launch_update_tc2(d, half ? kPanel : kSub, k1, half ? (1 << 30) : kb0 + kPanel,
-                            (int)std::min<int64_t>(items, h->grid_max / 2), L.split,
+          const double fl = (split_mid && half) ? 0.5 * L.tc_flops[u] : L.tc_flops[u];
+          ProfScope ps(h, BDDC_PROF_TC_UPDATE, 0.0, fl, st);
+          launch_update_tc2(d, nq, k1, jend, (int)std::min<int64_t>(items, h->grid_max / 2), L.split,
                             L.split_signed ? L.split_signed : L.split, L.rscale, L.prow_off,
                             L.item_pref + (size_t)u * (d.n_sub + 1), L.tile_tmap, st);
         }
+        if (split_mid && half == 0) launch_schur_snapshot(d, k1, L.max_nGb, st);
       }
     }
   } else {
@@ -1025,11 +1085,17 @@ void schur_apply(bddc_handle_s* h, const double* x, double* y, cudaStream_t st, 
   if (L.fp32 && h->cur_steps == 0) {
     launch_gather_iface<double>(L.d, x, 0, L.dl0, st, nb);
     launch_convert<double, float>(L.dl0, (float*)L.locA, n, st);
-    {
+    const float* yf = (const float*)L.locA;
+    if (L.explicit_schur) {   // one pass over the lower triangle of S_i + C_i^T R C_i
+      ProfScope ps(h, BDDC_PROF_TRMV, column_groups(nb, 4) * 0.5 * L.trmv_bytes, 0.0, st);
+      launch_schur_symv(L.d, L.max_nGb, L.symv_part_off, L.symv_stride, (const float*)L.locA, L.symv_part,
+                        (float*)L.locB, st, nb);
+      yf = (const float*)L.locB;
+    } else {
       ProfScope ps(h, BDDC_PROF_TRMV, column_groups(nb, 8) * L.trmv_bytes, 0.0, st);
       launch_trmv_schur(L.d, L.max_nGb, (const float*)L.locA, (float*)L.locB, (float*)L.locA, st, nb);
     }
-    launch_convert<float, double>((const float*)L.locA, L.dl1, n, st);
+    launch_convert<float, double>(yf, L.dl1, n, st);
     launch_sub_ctrc(L.d, L.crow_sub, L.sum_nc, L.dl0, L.dl1, st, nb);
     launch_scatter_iface<double>(L.d, L.dl1, 0, y, st, nb);
     return;
@@ -1352,6 +1418,7 @@ void numeric_setup(bddc_handle_s* h) {
     h->inner_steps = h->opts.inner_steps;
   }
   h->stats.inner_steps = h->use_outer ? h->inner_steps : -1;
+  h->stats.inner_operator = h->use_outer ? (h->lv[0].explicit_schur ? 2 : 1) : 0;
   h->factored = true;
 }
 
@@ -2285,6 +2352,7 @@ void bddc_default_opts(bddc_opts* o) {
   o->profile = 0;
   o->tensor_cores = 1;
   o->autotune = 1;
+  o->inner_operator = 0;
 }
 
 int bddc_analyze(const bddc_mesh* mesh, const bddc_partition* part, unsigned constraints, const bddc_opts* opts,
@@ -2395,6 +2463,23 @@ int bddc_apply_schur(bddc_handle h, const double* x, double* y, int nrhs) {
     if (nrhs > 1) ensure_block(h, std::min(nrhs, kMaxBlock));
     for (int k0 = 0; k0 < nrhs; k0 += h->blk)
       schur_apply(h, x + k0 * n, y + k0 * n, h->st, std::min(h->blk, nrhs - k0));
+    ck(cudaStreamSynchronize(h->st), "sync");
+    return BDDC_OK;
+  });
+}
+
+int bddc_apply_inner_schur(bddc_handle h, const double* x, double* y, int nrhs) {
+  return guarded([&]() {
+    if (!h || !h->factored || !x || !y || nrhs < 1) fail(BDDC_ERR_INVALID, "bad arguments");
+    if (!h->lv[0].fp32 || krylov_kind(h) != BDDC_KRYLOV_PCG)
+      fail(BDDC_ERR_INVALID, "the inner operator exists for mixed-precision PCG handles only");
+    const int64_t n = h->lv[0].d.n_iface;
+    if (nrhs > 1) ensure_block(h, std::min(nrhs, kMaxBlock));
+    const int saved = h->cur_steps;
+    h->cur_steps = 0;   // schur_apply's inner form
+    for (int k0 = 0; k0 < nrhs; k0 += h->blk)
+      schur_apply(h, x + k0 * n, y + k0 * n, h->st, std::min(h->blk, nrhs - k0));
+    h->cur_steps = saved;
     ck(cudaStreamSynchronize(h->st), "sync");
     return BDDC_OK;
   });

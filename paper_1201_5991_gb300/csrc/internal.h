@@ -39,6 +39,7 @@ struct SubMeta {
   int64_t g_off;                  // offset of nc x nc matrices (G^{-1}, K_C)
   int64_t psi_off;                // offset of Psi_G (nGb*NB rows x nc, row-major)
   int64_t psiT_off;               // offset of Psi_G^T as ncb x nGb tiles (set-up copy for the solve phase)
+  int64_t schur_off;              // offset of the explicit augmented Schur complement (nGb (nGb+1)/2 tiles)
 };
 
 // Raw device pointers of one level, passed by value to kernels.
@@ -84,6 +85,7 @@ struct LevelDev {
   void* dinv;                     // diagonal inverses
   void* psi;                      // Psi_G
   void* psiT;                     // Psi_G^T in tiles: tile (rb, j) of a subdomain at psiT_off + (rb nGb + j) NB2
+  float* schur;                   // explicit augmented Schur complement of the interface (mixed inner operator), or null
   void* sgn;                      // [n_vec] pivot signs of the signed Cholesky (T; +1 for SPD levels)
   const double* c_rho;            // [sum nc] 1 where a constraint row is augmented by rho, else 0
   int indefinite;                 // 1: negative pivots allowed (Stokes), 0: SPD
@@ -239,6 +241,17 @@ void launch_put_indexed(double* u, int64_t ustride, const int64_t* idx, const do
                         int nr = 1);
 // inner Schur operator from the stored factor (trmv.cu): y = L_GG S L_GG^T x over the
 // interface block rows of an FP32 level (y1 scratch), and y -= C^T R C x (FP64, local vectors)
+// Explicit form of the same operator: at the point of the factorisation where every interior
+// column has been eliminated and no interface column yet (block column b = nIb of the subdomain),
+// the trailing interface block of the tiles is S_i + C_i^T R C_i; launch_schur_snapshot copies it,
+// for the subdomains with nIb == b, as the lower triangle of tiles (i, j), 0 <= j <= i < nGb, at
+// schur + schur_off.  launch_schur_symv then applies it once per tile: y_i = sum_j M_ij x_j over
+// the stored lower tiles and, for j < i, the column part M_ij^T x_i into part (64 floats per tile
+// and right-hand side), added in a fixed order by a second kernel.  part holds
+// sum_s nGb (nGb - 1) / 2 x 64 floats per right-hand side (tri_off: its per-subdomain offsets).
+void launch_schur_snapshot(const LevelDev& L, int b, int max_nGb, cudaStream_t st);
+void launch_schur_symv(const LevelDev& L, int max_nGb, const int64_t* part_off, int64_t part_stride, const float* x,
+                       float* part, float* y, cudaStream_t st, int nr = 1);
 void launch_trmv_schur(const LevelDev& L, int max_nGb, const float* x, float* y1, float* y, cudaStream_t st,
                        int nr = 1);
 void launch_sub_ctrc(const LevelDev& L, const int32_t* crow_sub, int64_t total_rows, const double* x, double* y,

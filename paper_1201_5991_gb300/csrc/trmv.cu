@@ -141,7 +141,236 @@ __global__ void k_sub_ctrc(LevelDev L, const int32_t* __restrict__ crow_sub, int
   for (int64_t e = a + lane; e < b; e += 32) y[m.vec_off + L.c_pos[e]] -= rq * t * L.c_val[e];
 }
 
+// ---- explicit augmented Schur complement (snapshot of the trailing interface block) ----------
+
+// tile (i, j), 0 <= j <= i < nGb, of a subdomain's explicit Schur complement
+__device__ __forceinline__ int64_t schur_tile(const SubMeta& m, int i, int j) {
+  return m.schur_off + ((int64_t)i * (i + 1) / 2 + j) * NB2;
+}
+
+// block (t, s): copy interface tile t (row-major numbering of the lower triangle) of subdomain s
+// if its interior columns are all eliminated and no interface column yet (nIb == b)
+__global__ void __launch_bounds__(256) k_schur_snapshot(LevelDev L, int b) {
+  const int s = blockIdx.y;
+  const SubMeta m = L.meta[s];
+  if (m.nIb != b) return;
+  const int64_t t = blockIdx.x;
+  if (t >= (int64_t)m.nGb * (m.nGb + 1) / 2) return;
+  int i = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+  while ((int64_t)(i + 1) * (i + 2) / 2 <= t) ++i;
+  while ((int64_t)i * (i + 1) / 2 > t) --i;
+  const int j = (int)(t - (int64_t)i * (i + 1) / 2);
+  const float4* src = (const float4*)((const float*)L.tiles + m.tile_off + tile_index_t(m.nIb + i, m.nIb + j, m.Bc) * NB2);
+  float4* dst = (float4*)(L.schur + schur_tile(m, i, j));
+  for (int e = threadIdx.x; e < NB2 / 4; e += blockDim.x) dst[e] = __ldcg(src + e);
+}
+
+// One pass over the stored lower tiles of M for y = M x.  Block (o, s, group) takes block row
+// i = nGb - 1 - o (longest rows first).  The row's tiles stream through a ring of kSymvStages
+// shared-memory stages filled with cp.async (16 bytes per thread and copy, rows padded to 68
+// floats, kSymvStages - 1 tiles in flight).  Warp w, half h = lane / 16 own the columns
+// c0 = 8 w + 4 h .. c0 + 3 of every tile, lane r4 = lane % 16 the rows r4, r4 + 16, r4 + 32,
+// r4 + 48 (with the padding, a warp's 16-byte reads of a tile hit every bank pair once per
+// 128-byte wavefront).
+//   row part      y_i += M_ij x_j: per lane over its rows, added over the 16 column groups at the end;
+//   column part   M_ij^T x_i (j < i): summed over the 16 row groups of a half-warp by shuffles and
+//                 written to part (64 floats per tile and right-hand side), added later in order;
+// the diagonal tile holds M_ii in its lower triangle only (the factorisation updates the full
+// tile but its upper part never held the matrix): its row part uses the lower triangle, its
+// column part the strict lower triangle, both into y_i.
+constexpr int kSymvStages = 4;
+constexpr int kSymvLd = NB + 4;   // padded row of a staged tile (floats)
+
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+
+template <int NR>
+__global__ void __launch_bounds__(256) k_schur_symv_rows(LevelDev L, const float* __restrict__ x,
+                                                         const int64_t* __restrict__ part_off, int64_t part_stride,
+                                                         float* __restrict__ part, float* __restrict__ y) {
+  const int s = blockIdx.y;
+  const SubMeta m = L.meta[s];
+  if ((int)blockIdx.x >= m.nGb) return;
+  const int i = m.nGb - 1 - (int)blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int h = lane >> 4, r4 = lane & 15;
+  const int c0 = 8 * warp + 4 * h;
+  const int64_t c0q = (int64_t)blockIdx.z * NR * L.n_vec;   // first column of this group
+  const float* xv = x + c0q + m.vec_off + (int64_t)m.nIb * NB;
+  extern __shared__ __align__(16) float ring[];              // kSymvStages x NB x kSymvLd
+  __shared__ float red[16][NR][NB];
+  __shared__ float dcol[NR][NB];
+  const float* Mrow = L.schur + schur_tile(m, i, 0);
+  auto issue = [&](int j) {   // tile j of the row into stage j % kSymvStages
+    const float* src = Mrow + (int64_t)j * NB2;
+    float* dst = ring + (j % kSymvStages) * NB * kSymvLd;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int c = threadIdx.x + 256 * u;   // 16-byte chunk: row c / 16, column 4 (c % 16)
+      cp_async16(dst + (c >> 4) * kSymvLd + 4 * (c & 15), src + 4 * c);
+    }
+  };
+#pragma unroll
+  for (int j = 0; j < kSymvStages - 1; ++j) {
+    if (j <= i) issue(j);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
+  // x_i at this lane's rows
+  float xi[NR][4];
+#pragma unroll
+  for (int q = 0; q < NR; ++q)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) xi[q][k] = xv[q * L.n_vec + (int64_t)i * NB + r4 + 16 * k];
+  float racc[4][NR];
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int q = 0; q < NR; ++q) racc[k][q] = 0.f;
+  float* prow = part + (int64_t)blockIdx.z * NR * part_stride + part_off[s] + (int64_t)i * (i - 1) / 2 * NB;
+  for (int j = 0; j <= i; ++j) {
+    // tile j has landed (this thread's copies), then every thread's copies and the end of the
+    // previous tile's reads; then the stage read two tiles ago is refilled
+    asm volatile("cp.async.wait_group %0;" ::"n"(kSymvStages - 2) : "memory");
+    __syncthreads();
+    if (j + kSymvStages - 1 <= i) issue(j + kSymvStages - 1);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    const float* T = ring + (j % kSymvStages) * NB * kSymvLd;
+    float4 a[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a[k] = *(const float4*)(T + (r4 + 16 * k) * kSymvLd + c0);
+    if (j == i) {   // lower triangle only (strictly lower for the column part)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int r = r4 + 16 * k;
+        if (c0 + 0 > r) a[k].x = 0.f;
+        if (c0 + 1 > r) a[k].y = 0.f;
+        if (c0 + 2 > r) a[k].z = 0.f;
+        if (c0 + 3 > r) a[k].w = 0.f;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+      const float4 xj = *(const float4*)(xv + q * L.n_vec + (int64_t)j * NB + c0);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) racc[k][q] += a[k].x * xj.x + a[k].y * xj.y + a[k].z * xj.z + a[k].w * xj.w;
+    }
+    // column part: sum over the rows of the tile
+    float cp[NR][4];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+      float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int r = r4 + 16 * k;
+        // the diagonal tile's column part excludes the diagonal itself
+        const float xr = xi[q][k];
+        d0 += (j == i && c0 + 0 == r) ? 0.f : a[k].x * xr;
+        d1 += (j == i && c0 + 1 == r) ? 0.f : a[k].y * xr;
+        d2 += (j == i && c0 + 2 == r) ? 0.f : a[k].z * xr;
+        d3 += (j == i && c0 + 3 == r) ? 0.f : a[k].w * xr;
+      }
+      cp[q][0] = d0;
+      cp[q][1] = d1;
+      cp[q][2] = d2;
+      cp[q][3] = d3;
+    }
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1)
+#pragma unroll
+      for (int q = 0; q < NR; ++q)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) cp[q][e] += __shfl_xor_sync(0xffffffffu, cp[q][e], o);
+    if (r4 == 0) {
+#pragma unroll
+      for (int q = 0; q < NR; ++q) {
+        const float4 v = make_float4(cp[q][0], cp[q][1], cp[q][2], cp[q][3]);
+        if (j < i)
+          *(float4*)(prow + q * part_stride + (int64_t)j * NB + c0) = v;
+        else
+          *(float4*)&dcol[q][c0] = v;
+      }
+    }
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+#pragma unroll
+  for (int q = 0; q < NR; ++q)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) red[2 * warp + h][q][r4 + 16 * k] = racc[k][q];
+  __syncthreads();
+  float* yv = y + c0q + m.vec_off + (int64_t)m.nIb * NB + (int64_t)i * NB;
+  for (int e = threadIdx.x; e < NR * NB; e += blockDim.x) {
+    const int q = e / NB, c = e % NB;
+    float v = 0.f;
+#pragma unroll
+    for (int g = 0; g < 16; ++g) v += red[g][q][c];
+    yv[q * L.n_vec + c] = v + dcol[q][c];
+  }
+}
+
+// y_j += sum_{i > j} part(i, j), i ascending; block (j, s, group)
+template <int NR>
+__global__ void k_schur_symv_cols(LevelDev L, const int64_t* __restrict__ part_off, int64_t part_stride,
+                                  const float* __restrict__ part, float* __restrict__ y) {
+  const int s = blockIdx.y;
+  const SubMeta m = L.meta[s];
+  const int j = blockIdx.x;
+  if (j >= m.nGb - 1) return;
+  const int64_t c0q = (int64_t)blockIdx.z * NR;
+  for (int e = threadIdx.x; e < NR * NB; e += blockDim.x) {
+    const int q = e / NB, c = e % NB;
+    const float* p = part + (c0q + q) * part_stride + part_off[s];
+    float v = 0.f;
+    for (int i = j + 1; i < m.nGb; ++i) v += p[((int64_t)i * (i - 1) / 2 + j) * NB + c];
+    float* yv = y + (c0q + q) * L.n_vec + m.vec_off + (int64_t)m.nIb * NB + (int64_t)j * NB + c;
+    *yv = *yv + v;
+  }
+}
+
 }  // namespace
+
+void launch_schur_snapshot(const LevelDev& L, int b, int max_nGb, cudaStream_t st) {
+  if (max_nGb <= 0 || L.n_sub <= 0 || !L.schur) return;
+  note_launch();
+  k_schur_snapshot<<<dim3((unsigned)((int64_t)max_nGb * (max_nGb + 1) / 2), (unsigned)L.n_sub), 256, 0, st>>>(L, b);
+}
+
+template <int NR>
+void launch_symv_nr(const LevelDev& L, const dim3& grid, const int64_t* part_off, int64_t part_stride, const float* x,
+                    float* part, float* y, cudaStream_t st) {
+  const size_t dyn = sizeof(float) * kSymvStages * NB * kSymvLd;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_schur_symv_rows<NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    attr = true;
+  }
+  note_launch();
+  k_schur_symv_rows<NR><<<grid, 256, dyn, st>>>(L, x, part_off, part_stride, part, y);
+  note_launch();
+  k_schur_symv_cols<NR><<<grid, 256, 0, st>>>(L, part_off, part_stride, part, y);
+}
+
+void launch_schur_symv(const LevelDev& L, int max_nGb, const int64_t* part_off, int64_t part_stride, const float* x,
+                       float* part, float* y, cudaStream_t st, int nr) {
+  if (max_nGb <= 0 || L.n_sub <= 0 || nr <= 0) return;
+  // columns in groups of 4, 2, 1 (the row kernel keeps 4 NR row sums and 4 NR column sums per lane)
+  for (int r0 = 0; r0 < nr;) {
+    const int left = nr - r0;
+    const int g = left >= 4 ? 4 : left >= 2 ? 2 : 1;
+    const int ng = left / g;
+    const dim3 grid((unsigned)max_nGb, (unsigned)L.n_sub, (unsigned)ng);
+    const int64_t off = (int64_t)r0 * L.n_vec;
+    float* pp = part + (int64_t)r0 * part_stride;
+    if (g == 4)
+      launch_symv_nr<4>(L, grid, part_off, part_stride, x + off, pp, y + off, st);
+    else if (g == 2)
+      launch_symv_nr<2>(L, grid, part_off, part_stride, x + off, pp, y + off, st);
+    else
+      launch_symv_nr<1>(L, grid, part_off, part_stride, x + off, pp, y + off, st);
+    r0 += ng * g;
+  }
+}
 
 template <int NR>
 void launch_trmv_nr(const LevelDev& L, const dim3& grid, const float* x, float* y1, float* y, cudaStream_t st) {

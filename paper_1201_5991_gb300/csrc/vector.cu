@@ -74,9 +74,22 @@ __global__ void k_spmv(LevelDev L, const int64_t* __restrict__ rows, int64_t nro
   x += (int64_t)blockIdx.y * L.n_vec;
   y += (int64_t)blockIdx.y * L.n_vec;
   const double* xs = x + L.meta[s].vec_off;
-  double acc = 0.0;
-  if (valid)
-    for (int64_t q = L.row_ptr[row] + l; q < L.row_ptr[row + 1]; q += 16) acc += L.val[q] * xs[L.col[q]];
+  double acc = 0.0, acc2 = 0.0;
+  if (valid) {
+    // two entries per lane and iteration: both loads are issued before either product (the
+    // rows hold up to 81 entries, so a single chain of dependent loads left the kernel
+    // latency-bound); the two partial sums are added at the end, in a fixed order
+    const int64_t q1 = L.row_ptr[row + 1];
+    int64_t q = L.row_ptr[row] + l;
+    for (; q + 16 < q1; q += 32) {
+      const double v0 = L.val[q], v1 = L.val[q + 16];
+      const int c0 = L.col[q], c1 = L.col[q + 16];
+      acc += v0 * xs[c0];
+      acc2 += v1 * xs[c1];
+    }
+    if (q < q1) acc += L.val[q] * xs[L.col[q]];
+  }
+  acc += acc2;
   for (int o = 8; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (valid && l == 0) y[row] = (beta == 0.0 ? 0.0 : beta * y[row]) + alpha * acc;
 }

@@ -48,7 +48,7 @@ def host_mesh(prob, n_levels: Optional[int] = None) -> _HostMesh:
 
 def make_opts(precision="mixed", weights="stiffness", all_corners=0, maxit=500, refine_steps=0, flexible=-1,
               use_graph=1, profile=0, tensor_cores=1, inner_steps=0, inner_tol=0.0, krylov=0,
-              autotune=1, verbose=0, wait_probe=0) -> capi.Opts:
+              autotune=1, verbose=0, wait_probe=0, inner_operator=0) -> capi.Opts:
     o = capi.Opts()
     capi.lib().bddc_default_opts(C.byref(o))
     o.precision = capi.PREC_MIXED if precision == "mixed" else capi.PREC_FP64
@@ -66,6 +66,7 @@ def make_opts(precision="mixed", weights="stiffness", all_corners=0, maxit=500, 
     o.autotune = int(autotune)
     o.verbose = int(verbose)
     o.wait_probe = int(wait_probe)
+    o.inner_operator = int(inner_operator)
     return o
 
 
@@ -186,6 +187,14 @@ class BddcSolver:
         self._check_vec(x, self.n_iface)
         y = self.torch.empty_like(x)
         capi.check(capi.lib().bddc_apply_schur(self.hd.h, self._dptr(x), self._dptr(y), 1 if x.dim() == 1 else x.shape[0]))
+        return y
+
+    def apply_inner_schur(self, x):
+        """The mixed form's inner operator S~ (factor products or explicit Schur complement)."""
+        self._check_vec(x, self.n_iface)
+        y = self.torch.empty_like(x)
+        capi.check(capi.lib().bddc_apply_inner_schur(self.hd.h, self._dptr(x), self._dptr(y),
+                                                     1 if x.dim() == 1 else x.shape[0]))
         return y
 
     def grad(self, dJdu, u, tol: float = 1e-10, want_coef: bool = True, want_rhs: bool = True):
