@@ -853,7 +853,8 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
     std::vector<int64_t> by_len(ns);
     for (int64_t s = 0; s < ns; ++s) by_len[s] = s;
     std::stable_sort(by_len.begin(), by_len.end(), [&](int64_t a, int64_t b) {
-      const int la = part == 0 ? L.meta[a].nIb : L.meta[a].nGb, lb = part == 0 ? L.meta[b].nIb : L.meta[b].nGb;
+      const int la = part == 0 ? (int)ceil_div(L.meta[a].nI, NB) : L.meta[a].nGb;
+      const int lb = part == 0 ? (int)ceil_div(L.meta[b].nI, NB) : L.meta[b].nGb;
       return la > lb;
     });
     for (int order = 0; order < 2; ++order)
@@ -865,7 +866,9 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
           for (int64_t k = 0; k < ns; ++k) {
             const int64_t s = order == 0 ? k : by_len[k];
             const SubMeta& m = L.meta[s];
-            const int B0 = part == 0 ? 0 : m.nIb, B1 = part == 0 ? m.nIb : m.Bc;
+            // interior: the block rows holding interior DOFs (identity tiles that pad the
+            // interior block count carry no data: their rows and columns of L are unit vectors)
+            const int B0 = part == 0 ? 0 : m.nIb, B1 = part == 0 ? (int)ceil_div(m.nI, NB) : m.Bc;
             if (B0 + depth < B1) {
               more = true;
               tl.push_back(make_int2((int)s, dir == 0 ? B0 + depth : B1 - 1 - depth));

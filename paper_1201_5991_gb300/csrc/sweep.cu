@@ -145,7 +145,9 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int sub = tasks[t].x, i = tasks[t].y;
     const SubMeta m = L.meta[sub];
     if (!BWD && L.indefinite && tid < NB) s_sg[tid] = ((const T*)L.sgn)[m.vec_off + (int64_t)i * NB + tid];
-    const int B0 = part == 0 ? 0 : m.nIb, B1 = part == 0 ? m.nIb : m.Bc;
+    // interior part: the block rows that hold interior DOFs (padding identity block rows, whose
+    // rows and columns of L are unit vectors and whose right-hand sides are zero, are skipped)
+    const int B0 = part == 0 ? 0 : m.nIb, B1 = part == 0 ? (m.nI + NB - 1) / NB : m.Bc;
     const int nL = BWD ? (B1 - 1 - i) : (i - B0);   // factor tiles before D_i^{-1}
     const int ntile = nL + 1;
     const T* tiles = (const T*)L.tiles + m.tile_off;
