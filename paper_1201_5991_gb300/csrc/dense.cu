@@ -104,22 +104,61 @@ __device__ void factor_diag_tile(const LevelDev& L, const SubMeta& m, int s, int
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
   __shared__ T sg[NB];
-  // Right-looking elimination on the unscaled columns, one barrier per column: at column j
-  // every entry below the pivot is updated as a_ic -= a_ij a_cj / d_j (d_j = a_jj after the
-  // updates of the columns before j), which equals l_ij s_j l_cj with l_ij = a_ij / (s_j
-  // sqrt|d_j|), s_j = sign d_j; the columns are scaled to L afterwards.  Thread t owns row
-  // i = t / 4 and the columns c = t % 4 (mod 4); column j is only read at step j and only
-  // columns > j are written, so no entry is read and written in the same step.
+  __shared__ T dd[NB];   // pivots as used by the elimination (1 where a pivot failed)
+  // Right-looking elimination on the unscaled columns: at column j every entry below the pivot
+  // is updated as a_ic -= (a_ij / d_j) a_cj (d_j = a_jj after the updates of the columns before
+  // j), which equals l_ij s_j l_cj with l_ij = a_ij / (s_j sqrt|d_j|), s_j = sign d_j; the columns
+  // are scaled to L afterwards.  Blocked by panels of 16 columns, with three barriers per panel:
+  //   (a1) warp 0 eliminates inside the 16 x 16 diagonal block (warp-synchronous steps);
+  //   (a2) one thread per row below it applies the panel's 16 eliminations to its 16 panel
+  //        entries and keeps the multipliers a_ij / d_j (in X, unused until the inverse);
+  //   (b)  the trailing block takes a_rc -= sum_j (a_rj / d_j) a_cj over the panel columns.
+  // Every entry receives the same updates in the same order (j ascending) as column by column.
   {
-    const int i = threadIdx.x >> 2, cls = threadIdx.x & 3;
-    for (int j = 0; j < NB - 1; ++j) {
-      T d = A[j][j];
-      // a failed pivot (flagged below from the same value) continues as 1, as in the scaling
-      if (L.indefinite ? !(fabs(d) > (T)1e-30) : !(d > (T)0)) d = (T)1;
-      if (i > j) {
-        const T f = A[i][j] / d;
-        const int c1 = j + 1 + ((cls - j - 1) & 3);   // first column > j of this thread's class
-        for (int c = c1; c <= i; c += 4) A[i][c] -= f * A[c][j];
+    constexpr int PW = 16;
+    T(*F)[PW + 1] = (T(*)[PW + 1])(&X[0][0]);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int p0 = 0; p0 < NB; p0 += PW) {
+      if (warp == 0) {
+        const int i = p0 + (lane & 15), half = lane >> 4;
+        for (int jj = 0; jj < PW; ++jj) {
+          const int j = p0 + jj;
+          T d = A[j][j];
+          // a failed pivot (flagged below from the same value) continues as 1, as in the scaling
+          if (L.indefinite ? !(fabs(d) > (T)1e-30) : !(d > (T)0)) d = (T)1;
+          if (lane == 0) dd[j] = d;
+          if (i > j) {
+            const T f = A[i][j] / d;
+            for (int c = j + 1 + half; c <= i; c += 2) A[i][c] -= f * A[c][j];
+          }
+          __syncwarp();
+        }
+      }
+      __syncthreads();
+      const int nb = NB - p0 - PW;   // rows below the diagonal block
+      if (tid < nb) {
+        const int i = p0 + PW + tid;
+        T a[PW];
+#pragma unroll
+        for (int jj = 0; jj < PW; ++jj) a[jj] = A[i][p0 + jj];
+#pragma unroll
+        for (int jj = 0; jj < PW; ++jj) {
+          const T f = a[jj] / dd[p0 + jj];
+          F[tid][jj] = f;
+#pragma unroll
+          for (int c = jj + 1; c < PW; ++c) a[c] -= f * A[p0 + c][p0 + jj];
+        }
+#pragma unroll
+        for (int jj = 0; jj < PW; ++jj) A[i][p0 + jj] = a[jj];
+      }
+      __syncthreads();
+      for (int e = tid; e < nb * nb; e += blockDim.x) {
+        const int r = e / nb, c = e % nb;
+        if (c > r) continue;
+        T acc = A[p0 + PW + r][p0 + PW + c];
+#pragma unroll
+        for (int jj = 0; jj < PW; ++jj) acc -= F[r][jj] * A[p0 + PW + c][p0 + jj];
+        A[p0 + PW + r][p0 + PW + c] = acc;
       }
       __syncthreads();
     }
@@ -156,24 +195,46 @@ __device__ void factor_diag_tile(const LevelDev& L, const SubMeta& m, int s, int
   __syncthreads();
   if (threadIdx.x < NB) ((T*)L.sgn)[m.vec_off + (int64_t)k * NB + threadIdx.x] = sg[threadIdx.x];
   if (threadIdx.x == 0 && bad) flag_breakdown(L.status, s);
-  // X = L^{-1} by forward substitution on the columns, in shared memory: four threads per
-  // column c (thread t4 sums the terms q = t4 mod 4, and keeps the entries X[q][c] of that
-  // class, so no thread reads another's writes); the four partial sums meet by shuffles
+  // X = L^{-1} by 16 x 16 blocks: the four diagonal blocks X_PP = L_PP^{-1} by forward
+  // substitution (one warp each, one lane per column), then the blocks below the diagonal by
+  // their distance d = Q - P: X_QP = -X_QQ (sum_{P <= K < Q} L_QK X_KP), the inner sum into a
+  // scratch block first (3 - d + 1 blocks per distance, one entry per thread and block).
   {
-    const int c = threadIdx.x >> 2, t4 = threadIdx.x & 3;
-    const unsigned grp = 0xFu << (threadIdx.x & 28);
-    if (c < NB) {
-      if ((c & 3) == t4) X[c][c] = (T)1 / A[c][c];
-      for (int i = c + 1; i < NB; ++i) {
+    constexpr int PW = 16;
+    __shared__ T Tq[3][PW][PW + 1];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp < 4 && lane < PW) {
+      const int p0 = PW * warp, c = p0 + lane;
+      for (int r = p0; r < c; ++r) X[r][c] = (T)0;
+      X[c][c] = (T)1 / A[c][c];
+      for (int i = c + 1; i < p0 + PW; ++i) {
         T part = (T)0;
-        for (int q = c + ((t4 - c) & 3); q < i; q += 4) part += A[i][q] * X[q][c];
-        part += __shfl_xor_sync(grp, part, 1);
-        part += __shfl_xor_sync(grp, part, 2);
-        if ((i & 3) == t4) X[i][c] = -part / A[i][i];
+        for (int q = c; q < i; ++q) part += A[i][q] * X[q][c];
+        X[i][c] = -part / A[i][i];
       }
     }
+    __syncthreads();
+    for (int dist = 1; dist < 4; ++dist) {
+      const int nblk = 4 - dist;
+      for (int e = tid; e < nblk * PW * PW; e += blockDim.x) {   // T = sum_K L_QK X_KP
+        const int bq = e / (PW * PW), r = (e / PW) % PW, c = e % PW;
+        const int P = bq, Q = bq + dist;
+        T acc = (T)0;
+        for (int K = P; K < Q; ++K)
+          for (int q = 0; q < PW; ++q) acc += A[PW * Q + r][PW * K + q] * X[PW * K + q][PW * P + c];
+        Tq[bq][r][c] = acc;
+      }
+      __syncthreads();
+      for (int e = tid; e < nblk * PW * PW; e += blockDim.x) {   // X_QP = -X_QQ T
+        const int bq = e / (PW * PW), r = (e / PW) % PW, c = e % PW;
+        const int P = bq, Q = bq + dist;
+        T acc = (T)0;
+        for (int q = 0; q <= r; ++q) acc += X[PW * Q + r][PW * Q + q] * Tq[bq][q][c];
+        X[PW * Q + r][PW * P + c] = -acc;
+      }
+      __syncthreads();
+    }
   }
-  __syncthreads();
   T* dv = (T*)L.dinv + m.dinv_off + (int64_t)k * NB2;
   for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
     const int r = t / NB, c = t % NB;
