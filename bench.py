@@ -445,10 +445,13 @@ def run_gpu(args, rank, world, local_rank):
              capi.PROF_TRSV_IFACE: "k_sweep<float> forward/backward over interface block rows (subdomain corrections)",
              capi.PROF_COARSE: "coarsest-level solves (k_coarse_apply with the explicit FP32 inverse of the "
                                "FP64 coarse factor, else sweeps over it)",
-             capi.PROF_TRMV: "k_trmv_t + k_trmv_n (inner Schur operator: products with the stored interface factor)",
+             capi.PROF_TRMV: "inner Schur operator: k_schur_symv_rows + _cols over the explicit augmented Schur "
+                             "complement, else k_trmv_t + k_trmv_n with the stored interface factor",
              capi.PROF_SPMV: "k_spmv (FP64 CSR products with K_i)",
-             capi.PROF_FACTOR: "factorisation steps on CUDA cores (k_potrf_diag, k_trsm_panel, in-panel "
-                               "k_syrk_update, k_split_panel)",
+             capi.PROF_FACTOR: "factorisation steps on CUDA cores (diagonal blocks: k_potrf_diag, k_trsm_panel, "
+                               "k_syrk_update; k_block_inverse, k_split_inverse, k_split_panel)",
+             capi.PROF_TC_PANEL: "k_update_tc2 as the panel solve A(i, D) X^T S_D below each 256 x 256 diagonal "
+                                 "block (FP32-equivalent flops of the triangular solves it replaces)",
              capi.PROF_TC_UPDATE: "k_update_tc2 (rank-256 and rank-512 trailing updates of 512-wide super-panels "
                                   "on tcgen05, scaled two-part FP16 products, persistent, TMEM double-buffered)"}
     kernel_classes = {}
@@ -462,12 +465,13 @@ def run_gpu(args, rank, world, local_rank):
             e["frac_of_hbm"] = round(cb / (cms * 1e-3) / 1e9 / hbm, 4)
         if cf > 0:
             e["achieved_TFLOPs_fp32"] = round(cf / (cms * 1e-3) / 1e12, 2)
-        if c == capi.PROF_TC_UPDATE and cf > 0:
+        if c in (capi.PROF_TC_UPDATE, capi.PROF_TC_PANEL) and cf > 0:
             e["achieved_TFLOPs_fp16_mma"] = round(3.0 * cf / (cms * 1e-3) / 1e12, 1)
             e["frac_of_tensor_peak"] = round(3.0 * cf / (cms * 1e-3) / 1e12 / tc_peak, 4)
         kernel_classes[{capi.PROF_TRSV: "trsv_interior", capi.PROF_TRSV_IFACE: "trsv_interface",
                         capi.PROF_COARSE: "trsv_coarsest", capi.PROF_TRMV: "trmv", capi.PROF_SPMV: "spmv",
-                        capi.PROF_FACTOR: "factor_cuda_cores", capi.PROF_TC_UPDATE: "tc_update"}[c]] = e
+                        capi.PROF_FACTOR: "factor_cuda_cores", capi.PROF_TC_UPDATE: "tc_update",
+                        capi.PROF_TC_PANEL: "tc_panel_solve"}[c]] = e
     peak = tc_peak if tensor else hbm
     roofline = {
         "kernel": names[dom],

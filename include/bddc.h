@@ -109,10 +109,13 @@ typedef struct {
   int use_graph;            /* 1: capture one Krylov iteration in a CUDA graph */
   int verbose;              /* >= 2: phase times of the host index analysis on stderr */
   int profile;              /* 1: time kernel classes with CUDA events (bddc_stats.prof_*) */
-  int tensor_cores;         /* mixed: 1 = FP32 trailing updates of the factorisation on the tcgen05 tensor
-                               cores in 256-wide panels (two row-scaled FP16 parts, three products;
+  int tensor_cores;         /* mixed: 1 = FP32 trailing updates and panel solves of the factorisation on
+                               the tcgen05 tensor cores (two row-scaled FP16 parts, three products;
                                Stokes levels read a copy with the pivot signs on the columns as the
-                               second operand); 0 = FP32 CUDA cores */
+                               second operand): per 256-wide sub-panel the 256 x 256 diagonal block
+                               is factored and inverted on CUDA cores and the rows below it are
+                               solved as A(i, D) X^T S_D with X = L_D^{-1}; 2 = trailing updates only
+                               (panel solves tile by tile on CUDA cores); 0 = FP32 CUDA cores */
   int inner_steps;          /* mixed PCG: FP64 outer refinement x += S~^{-1}(g - S x) (residual with the
                                FP64 operator S) around an inner PCG with a cheaper operator S~:
                                0 = S~ from the stored interface factor (L_GG S L_GG^T - C^T R C, no
@@ -157,7 +160,9 @@ typedef struct {
 #define BDDC_PROF_TRSV_IFACE 4   /* sweeps over interface block rows (subdomain corrections) */
 #define BDDC_PROF_COARSE 5  /* sweeps of the coarsest level's FP64 factor */
 #define BDDC_PROF_TC_UPDATE 6   /* tensor-core trailing updates of the factorisation (FP32-equivalent flops) */
-#define BDDC_PROF_CLASSES 7
+#define BDDC_PROF_TC_PANEL 7    /* tensor-core panel solves below the diagonal blocks (flops of the
+                                   triangular solves they replace) */
+#define BDDC_PROF_CLASSES 8
 
 typedef struct {
   int iterations;           /* Krylov iterations of the last solve (max over right-hand sides) */

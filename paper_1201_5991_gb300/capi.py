@@ -36,8 +36,8 @@ EXPORTED = [
     "bddc_reset_profile", "bddc_grad_noalloc", "bddc_batching_ablation", "bddc_get_coarse",
     "bddc_tc_update_check", "bddc_apply_inner_schur",
 ]
-PROF_TRSV, PROF_FACTOR, PROF_SPMV, PROF_TRMV, PROF_TRSV_IFACE, PROF_COARSE, PROF_TC_UPDATE, PROF_CLASSES = (
-    0, 1, 2, 3, 4, 5, 6, 7)
+(PROF_TRSV, PROF_FACTOR, PROF_SPMV, PROF_TRMV, PROF_TRSV_IFACE, PROF_COARSE, PROF_TC_UPDATE, PROF_TC_PANEL,
+ PROF_CLASSES) = (0, 1, 2, 3, 4, 5, 6, 7, 8)
 
 
 class Mesh(C.Structure):

@@ -130,11 +130,17 @@ struct Level {
   std::vector<double> step_flops;  // tile flops of factor step k (all subdomains)
   std::vector<int> narrow_tiles;   // per step k: in-panel update tiles (256-wide sub-panels)
   std::vector<double> panel_flops; // per step k: flops of the CUDA-core steps (tensor-core path)
-  // per 512-wide super-panel p and update u (0: rank-256 update of the second half's columns,
-  // 1: rank-512 update of the trailing columns): 128 x 128 work items and FP32-equivalent flops
-  std::vector<int64_t> tc_items;    // [2 p + u], all subdomains
-  std::vector<double> tc_flops;     // [2 p + u]
-  int64_t* item_pref = nullptr;     // [2 p + u][n_sub + 1] first work item of every subdomain
+  std::vector<int> block_tiles;    // per step k: update tiles inside the sub-panel's diagonal block
+  std::vector<double> block_flops; // per step k: flops of the diagonal block's CUDA-core steps
+  bool tc_panels = false;          // panel solves below the diagonal blocks on the tensor cores
+  float* xinv = nullptr;           // [n_sub][4 x 4 tiles] inverse of the current diagonal block
+  // per 512-wide super-panel p and launch u of the tensor cores (0: rank-256 update of the second
+  // half's columns, 1: rank-512 update of the trailing columns, 2: rank-256 update of all trailing
+  // columns, 3 / 4: panel solve of the first / second half): 128 x 128 work items and
+  // FP32-equivalent flops (panel solves: those of the triangular solve they replace)
+  std::vector<int64_t> tc_items;    // [kTcLaunches p + u], all subdomains
+  std::vector<double> tc_flops;     // [kTcLaunches p + u]
+  int64_t* item_pref = nullptr;     // [kTcLaunches p + u][n_sub + 1] first work item of every subdomain
   uint8_t* split = nullptr;        // scaled FP16 parts of the current super-panel (pre-split update)
   uint8_t* split_signed = nullptr; // indefinite levels: the same with the pivot signs on the columns
   float* rscale = nullptr;         // their row unscaling factors (powers of two)
@@ -234,6 +240,7 @@ void alloc_level_work(Level& L, DevArena& A, int blk) {
 
 constexpr int kSub = 4;     // tile columns of a CUDA-core sub-panel (256)
 constexpr int kPanel = 8;   // tile columns of a tensor-core super-panel (512, two sub-panels)
+constexpr int kTcLaunches = 5;   // tensor-core launch kinds per super-panel (three updates, two panel solves)
 
 }  // namespace
 }  // namespace bddc
@@ -578,9 +585,11 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
   L.step_flops.assign(L.max_Bc, 0.0);
   L.narrow_tiles.assign(L.max_Bc, 0);
   L.panel_flops.assign(L.max_Bc, 0.0);
+  L.block_tiles.assign(L.max_Bc, 0);
+  L.block_flops.assign(L.max_Bc, 0.0);
   const int n_super = (L.max_Bc + kPanel - 1) / kPanel + 1;
-  L.tc_items.assign(3 * (size_t)n_super, 0);
-  L.tc_flops.assign(3 * (size_t)n_super, 0.0);
+  L.tc_items.assign(kTcLaunches * (size_t)n_super, 0);
+  L.tc_flops.assign(kTcLaunches * (size_t)n_super, 0.0);
   L.snap_start.assign(n_super, 0);
   L.snap_mid.assign(n_super, 0);
   const double nb3 = (double)NB * NB * NB;
@@ -601,15 +610,27 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
       for (int j = k + 1; j < std::min(kb1, (int)m.Bc); ++j) cnt += m.R - j;
       L.narrow_tiles[k] = std::max(L.narrow_tiles[k], (int)cnt);
       L.panel_flops[k] += nb3 / 3.0 + nb3 * (double)(m.R - k - 1) + 2.0 * nb3 * (double)cnt;
+      const int ilim = std::min(kb1, (int)m.Bc);   // the diagonal block's rows
+      int64_t bcnt = 0;
+      for (int j = k + 1; j < ilim; ++j) bcnt += ilim - j;
+      L.block_tiles[k] = std::max(L.block_tiles[k], (int)bcnt);
+      L.block_flops[k] += nb3 / 3.0 + nb3 * (double)(ilim - k - 1) + 2.0 * nb3 * (double)bcnt;
     }
     for (int kb0 = 0; kb0 < m.Bc; kb0 += kPanel) {
       int64_t tiles[2] = {0, 0};
       for (int j = kb0 + kSub; j < std::min(kb0 + kPanel, (int)m.Bc); ++j) tiles[0] += m.R - j;
       for (int j = kb0 + kPanel; j < m.Bc; ++j) tiles[1] += m.R - j;
       const int p = kb0 / kPanel;
-      L.tc_flops[3 * p] += 2.0 * nb3 * kSub * (double)tiles[0];
-      L.tc_flops[3 * p + 1] += 2.0 * nb3 * kPanel * (double)tiles[1];
-      L.tc_flops[3 * p + 2] += 2.0 * nb3 * kSub * (double)(tiles[0] + tiles[1]);
+      L.tc_flops[kTcLaunches * p] += 2.0 * nb3 * kSub * (double)tiles[0];
+      L.tc_flops[kTcLaunches * p + 1] += 2.0 * nb3 * kPanel * (double)tiles[1];
+      L.tc_flops[kTcLaunches * p + 2] += 2.0 * nb3 * kSub * (double)(tiles[0] + tiles[1]);
+      for (int half = 0; half < 2; ++half) {   // panel solves: rows below the block by its columns
+        const int k0 = kb0 + half * kSub;
+        const int nd = std::min(kSub, (int)m.Bc - k0);
+        if (nd <= 0) continue;
+        const double rows = (double)NB * (m.R - std::min(k0 + kSub, (int)m.Bc));
+        L.tc_flops[kTcLaunches * p + 3 + half] += rows * (double)(NB * nd) * (NB * nd);
+      }
     }
     if (L.explicit_schur) {   // where this subdomain's interior ends: a super-panel start or middle
       if (m.nIb % kPanel == 0) L.snap_start[m.nIb / kPanel] = 1;
@@ -797,6 +818,8 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
     L.split = A.alloc<uint8_t>(rows * kPanel * 2 * NB2 * 2);
     if (h->physics == BDDC_STOKES) L.split_signed = A.alloc<uint8_t>(rows * kPanel * 2 * NB2 * 2);
     L.rscale = A.alloc<float>(rows * NB);
+    L.tc_panels = h->opts.tensor_cores != 2;
+    if (L.tc_panels) L.xinv = A.alloc<float>(ns * 16 * NB2);
     // work items (128 x 128 output blocks) of the updates of every super-panel, flattened over the
     // subdomains; update 0 covers the columns [kb0 + kSub, kb0 + kPanel), update 1 the columns
     // >= kb0 + kPanel, update 2 (a super-panel where some interior ends in the middle, explicit
@@ -804,13 +827,18 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
     const int nu = (int)L.tc_items.size();
     std::vector<int64_t> pref((size_t)nu * (ns + 1), 0);
     for (int u = 0; u < nu; ++u) {
-      const int kb0 = (u / 3) * kPanel;
-      const int jbeg = kb0 + (u % 3 == 1 ? kPanel : kSub), jend = u % 3 == 0 ? kb0 + kPanel : (1 << 30);
+      const int kb0 = (u / kTcLaunches) * kPanel, v = u % kTcLaunches;
+      int jbeg = kb0 + (v == 1 ? kPanel : kSub), jend = v == 0 ? kb0 + kPanel : (1 << 30), ibeg = 0;
+      if (v >= 3) {   // panel solve of half v - 3: columns [k0, k0 + kSub), rows from k0 + kSub
+        jbeg = kb0 + (v - 3) * kSub;
+        jend = ibeg = jbeg + kSub;
+      }
       int64_t acc = 0;
       for (int64_t s = 0; s < ns; ++s) {
         pref[(size_t)u * (ns + 1) + s] = acc;
         const SubMeta& m = L.meta[s];
-        for (int j = jbeg; j < std::min((int)m.Bc, jend); j += 2) acc += (m.R - j + 1) / 2;
+        const int ib = std::min(ibeg, (int)m.Bc);
+        for (int j = jbeg; j < std::min((int)m.Bc, jend); j += 2) acc += (m.R - std::max(j, ib) + 1) / 2;
       }
       pref[(size_t)u * (ns + 1) + ns] = acc;
       L.tc_items[u] = acc;
@@ -938,9 +966,11 @@ void factor_level(bddc_handle_s* h, Level& L, cudaStream_t st) {
   launch_densify_rows<T>(d, L.row_sub, st);
   launch_add_constraints<T>(d, st);
   if (sizeof(T) == 4 && h->opts.tensor_cores) {
-    // 512-wide super-panels of two 256-wide sub-panels: in-sub-panel steps on CUDA cores; a
-    // rank-256 tcgen05 update of the second sub-panel's columns after the first, and one
-    // rank-512 update of every trailing column after the second
+    // 512-wide super-panels of two 256-wide sub-panels.  Per sub-panel: its 256 x 256 diagonal
+    // block factored on CUDA cores and inverted (X = L_D^{-1}); the rows below it solved on the
+    // tensor cores as L(i, D) = A(i, D) X^T S_D (tensor_cores = 2: on CUDA cores, tile by tile).
+    // After the first sub-panel a rank-256 tcgen05 update brings the second sub-panel's columns
+    // up to date; after the second, one rank-512 update serves every trailing column.
     for (int kb0 = 0; kb0 < L.max_Bc; kb0 += kPanel) {
       const int p = kb0 / kPanel;
       // explicit inner operator: the trailing interface block of every subdomain whose interior
@@ -953,11 +983,37 @@ void factor_level(bddc_handle_s* h, Level& L, cudaStream_t st) {
       const bool split_mid = L.explicit_schur && L.snap_mid[p];
       for (int half = 0; half < 2; ++half) {
         const int k0 = kb0 + half * kSub, k1 = k0 + kSub;
-        const int u = 3 * p + (half ? 1 : (split_mid ? 2 : 0));
+        const int u = kTcLaunches * p + (half ? 1 : (split_mid ? 2 : 0));
         const int nq = split_mid ? kSub : (half ? kPanel : kSub);   // K tiles of the update
         const int kq = split_mid ? k0 : kb0;                        // its first K column
         const int jend = (half || split_mid) ? (1 << 30) : kb0 + kPanel;
-        {
+        if (k0 < L.max_Bc && L.tc_panels) {
+          {
+            double fl = 0.0;
+            for (int k = k0; k < std::min(k1, L.max_Bc); ++k) fl += L.block_flops[k];
+            ProfScope ps(h, BDDC_PROF_FACTOR, 0.0, fl, st);
+            bool fused = false;
+            for (int k = k0; k < std::min(k1, L.max_Bc); ++k) {
+              const bool fuse = k + 1 < k1 && L.block_tiles[k] > 0;
+              launch_potrf_step<T>(d, k, L.max_R, L.block_tiles[k], k1, st, fused, fuse, k1);
+              fused = fuse;
+            }
+            launch_block_inverse(d, k0, L.xinv, st);
+            launch_split_inverse(d, k0, L.xinv, L.split, L.rscale, L.prow_off, st);
+            launch_split_panel(d, k0, kSub, k1, L.max_R, L.split, nullptr, L.rscale, L.prow_off, st, 1);
+          }
+          const int up = kTcLaunches * p + 3 + half;
+          if (L.tc_items[up] > 0) {
+            ProfScope ps(h, BDDC_PROF_TC_PANEL, 0.0, L.tc_flops[up], st);
+            launch_update_tc2(d, kSub, k0, k1, k1, (int)std::min<int64_t>(L.tc_items[up], h->grid_max / 2),
+                              L.split, L.split, L.rscale, L.prow_off, L.item_pref + (size_t)up * (d.n_sub + 1),
+                              L.tile_tmap, st);
+          }
+          if (L.split && L.tc_items[u] > 0) {
+            ProfScope ps(h, BDDC_PROF_FACTOR, 0.0, 0.0, st);
+            launch_split_panel(d, kq, nq, k1, L.max_R, L.split, L.split_signed, L.rscale, L.prow_off, st);
+          }
+        } else {
           double fl = 0.0;
           for (int k = k0; k < std::min(k1, L.max_Bc); ++k) fl += L.panel_flops[k];
           ProfScope ps(h, BDDC_PROF_FACTOR, 0.0, fl, st);
@@ -974,7 +1030,7 @@ void factor_level(bddc_handle_s* h, Level& L, cudaStream_t st) {
         if (L.split && items > 0) {   // no launch where no subdomain has columns left
           const double fl = (split_mid && half) ? 0.5 * L.tc_flops[u] : L.tc_flops[u];
           ProfScope ps(h, BDDC_PROF_TC_UPDATE, 0.0, fl, st);
-          launch_update_tc2(d, nq, k1, jend, (int)std::min<int64_t>(items, h->grid_max / 2), L.split,
+          launch_update_tc2(d, nq, k1, jend, 0, (int)std::min<int64_t>(items, h->grid_max / 2), L.split,
                             L.split_signed ? L.split_signed : L.split, L.rscale, L.prow_off,
                             L.item_pref + (size_t)u * (d.n_sub + 1), L.tile_tmap, st);
         }
@@ -2626,7 +2682,7 @@ int bddc_tc_update_check(int64_t n, int rank, float* a, double* ms) {
       ck(cudaEventCreate(&e1), "cudaEventCreate");
       launch_split_panel(d, 0, nt, nt, nb, split, nullptr, rscale, prow_off, st);
       ck(cudaEventRecord(e0, st), "cudaEventRecord");
-      launch_update_tc2(d, nt, nt, nb, (int)std::min<int64_t>(items, std::max(1, sms)), split, split, rscale,
+      launch_update_tc2(d, nt, nt, nb, 0, (int)std::min<int64_t>(items, std::max(1, sms)), split, split, rscale,
                         prow_off, item_pref, tmap, st);
       ck(cudaEventRecord(e1, st), "cudaEventRecord");
       ck(cudaGetLastError(), "tensor-core update launch");

@@ -135,9 +135,16 @@ void launch_weights(const LevelDev& L, int multiplicity, const double* unused, c
 // skip_diag: the diagonal tile k was factored by the previous step's update (fuse_next there);
 // fuse_next: the update's block for tile (k+1, k+1) factors it (only when max_tiles > 0 and
 // k + 1 < jmax, i.e. that tile receives its last update in this step).
+// rlim > 0: the rows of the diagonal block only (i < min(rlim, Bc) in the panel and the update).
 template <typename T>
 void launch_potrf_step(const LevelDev& L, int k, int max_R, int max_tiles, int jmax, cudaStream_t st,
-                       int skip_diag = 0, int fuse_next = 0);
+                       int skip_diag = 0, int fuse_next = 0, int rlim = 0);
+// The 256 x 256 diagonal block D of the sub-panel [k0, k0 + 4) of every subdomain (nd = min(4,
+// Bc - k0) tiles, factored as L_D S_D L_D^T by launch_potrf_step with rlim = k0 + 4): its inverse
+// X = L_D^{-1}, by block columns, X_PP = L_PP^{-1} (the stored inverse of the diagonal tile) and
+// X_QP = -X_QQ sum_{P <= K < Q} L_QK X_KP, written as 4 x 4 tiles of 64 x 64 (row-major blocks,
+// zero above the diagonal blocks) at xinv + s * 16 * 4096.  FP32 levels only.
+void launch_block_inverse(const LevelDev& L, int k0, float* xinv, cudaStream_t st);
 // update_tc.cu, FP32 levels with tensor cores: rank-(64 nt) update of the output columns
 // ib <= j < jend from the nt panel tile columns kb0 .. kb0+nt-1 (nt = 4 or 8).  k_split_panel
 // writes the two scaled FP16 parts of the panel tiles L(i, kb0 + q), i >= ib, at
@@ -146,8 +153,16 @@ void launch_potrf_step(const LevelDev& L, int k, int max_R, int max_tiles, int j
 // rscale[(prow_off[s] + i) * 64 + r]; the update (nq = nt, jbeg = ib) makes 128 x 128 output
 // blocks from them (persistent grid; item_pref[s] = first work item of subdomain s,
 // item_pref[n_sub] = number of items; split_b = split_signed on indefinite levels, else split)
+// panel_operand = 1: the rows i >= min(ib, Bc) of every subdomain with kb0 < Bc (the rows below
+// a sub-panel's diagonal block, before their panel solve), columns >= Bc as zeros, and the
+// source tiles set to zero after they are read (the panel solve adds its result into them).
 void launch_split_panel(const LevelDev& L, int kb0, int nt, int ib, int max_R, uint8_t* split, uint8_t* split_signed,
-                        float* rscale, const int64_t* prow_off, cudaStream_t st);
+                        float* rscale, const int64_t* prow_off, cudaStream_t st, int panel_operand = 0);
+// The B operand of a sub-panel's panel solve L(i, D) = A(i, D) X^T S_D: the rows of -S_D X (block
+// row Q of xinv, pivot signs of the block's columns) split like the panel rows into the split
+// rows prow_off[s] + k0 + Q, tile columns 0 .. 3, with their unscaling factors in rscale.
+void launch_split_inverse(const LevelDev& L, int k0, const float* xinv, uint8_t* split, float* rscale,
+                          const int64_t* prow_off, cudaStream_t st);
 // The update adds its output into the tiles with TMA reduce-adds through this tensor map: the
 // FP32 tile buffer viewed as [tile_elems / 64 rows][64 columns], 32 x 32 boxes, 128-byte
 // swizzle.  make_tile_tmap returns 0 or the driver's error code.
@@ -155,7 +170,9 @@ struct TensorMap128 {
   alignas(64) uint64_t opaque[16];   // a CUtensorMap
 };
 int make_tile_tmap(TensorMap128* map, float* tiles, int64_t tile_elems);
-void launch_update_tc2(const LevelDev& L, int nq, int jbeg, int jend, int grid, const uint8_t* split,
+// ibeg: the output rows start at max(j, min(ibeg, Bc)) (0 for a trailing update; k0 + 4 for the
+// panel solve of the sub-panel [k0, k0 + 4), whose output columns are jbeg = k0 .. jend = k0 + 4).
+void launch_update_tc2(const LevelDev& L, int nq, int jbeg, int jend, int ibeg, int grid, const uint8_t* split,
                        const uint8_t* split_b, const float* rscale, const int64_t* prow_off,
                        const int64_t* item_pref, const TensorMap128& tmap, cudaStream_t st);
 void launch_gram_chol(const LevelDev& L, int precision_fp32, int max_nc, cudaStream_t st);

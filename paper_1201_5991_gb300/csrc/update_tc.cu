@@ -93,18 +93,44 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 }
 
 
-// one block per panel row tile i (ib <= i < R) of every subdomain with output columns (ib < Bc)
+// one block per panel row tile i (ib <= i < R) of every subdomain with output columns (ib < Bc);
+// panel_operand: the rows i >= min(ib, Bc) of every subdomain with kb0 < Bc, read and cleared
 template <int NT>
-__global__ void __launch_bounds__(64 * NT) k_split_panel(LevelDev L, int kb0, int ib, uint8_t* __restrict__ split,
+__global__ void __launch_bounds__(64 * NT) k_split_panel(LevelDev L, int kb0, int ib, int panel_operand,
+                                                         uint8_t* __restrict__ split,
                                                          uint8_t* __restrict__ split_signed,
                                                          float* __restrict__ rscale,
                                                          const int64_t* __restrict__ prow_off) {
   const int s = blockIdx.y;
   const SubMeta m = L.meta[s];
-  if (ib >= m.Bc) return;
-  const int i = ib + (int)blockIdx.x;
+  int i;
+  if (panel_operand) {
+    if (kb0 >= m.Bc) return;
+    i = (ib < m.Bc ? ib : m.Bc) + (int)blockIdx.x;
+  } else {
+    if (ib >= m.Bc) return;
+    i = ib + (int)blockIdx.x;
+  }
   if (i >= m.R) return;
-  split_row_tile<NT>(L, s, m, i, kb0, split, split_signed, rscale, prow_off);
+  split_row_tile<NT>(L, s, m, i, kb0, split, split_signed, rscale, prow_off, panel_operand != 0);
+}
+
+// one block per block row Q of the inverse X of every subdomain's diagonal block (Q < nd): the
+// rows of -S_D X, the B operand of the panel solve (its update kernel subtracts A B^T)
+__global__ void __launch_bounds__(256) k_split_inverse(LevelDev L, int k0, const float* __restrict__ xinv,
+                                                       uint8_t* __restrict__ split, float* __restrict__ rscale,
+                                                       const int64_t* __restrict__ prow_off) {
+  const int s = blockIdx.y, Q = blockIdx.x;
+  const SubMeta m = L.meta[s];
+  const int nd = m.Bc - k0 < 4 ? m.Bc - k0 : 4;
+  if (Q >= nd) return;
+  __shared__ float rm[NB];
+  const float* sg = (const float*)L.sgn + m.vec_off + (int64_t)(k0 + Q) * NB;
+  if (threadIdx.x < NB) rm[threadIdx.x] = sg[threadIdx.x] < 0.f ? 1.f : -1.f;   // -s_r
+  __syncthreads();
+  const int c = threadIdx.x >> 6;   // block column of X; zero above the diagonal blocks
+  const float* src = c <= Q ? xinv + ((int64_t)s * 16 + Q * 4 + c) * NB2 : nullptr;
+  split_rows<4>(src, false, rm, prow_off[s] + k0 + Q, split, nullptr, rscale, nullptr);
 }
 
 // Persistent: CTA c takes the work items c, c + gridDim.x, ... of the panel (items of all
@@ -119,7 +145,7 @@ __global__ void __launch_bounds__(64 * NT) k_split_panel(LevelDev L, int kb0, in
 // lane adds the box into the tiles in L2 (the output is never read into the SM; every element
 // receives exactly one add per launch, so the result does not depend on timing).
 __global__ void __launch_bounds__(kThreads2, 1)
-    k_update_tc2(LevelDev L, int nq, int jbeg, int jend, const uint8_t* __restrict__ split,
+    k_update_tc2(LevelDev L, int nq, int jbeg, int jend, int ibeg, const uint8_t* __restrict__ split,
                  const uint8_t* __restrict__ split_b, const float* __restrict__ rscale,
                  const int64_t* __restrict__ prow_off, const int64_t* __restrict__ item_pref,
                  const __grid_constant__ CUtensorMap tmap) {
@@ -159,7 +185,8 @@ __global__ void __launch_bounds__(kThreads2, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
 
-  // item -> (subdomain, column pair j, j+1, row pair i0, i0+1)
+  // item -> (subdomain, column pair j, j+1, row pair i0, i0+1); the rows of column pair j start
+  // at max(j, min(ibeg, Bc))
   auto decode = [&](int64_t it, int& s, int& j, int& i0) {
     int lo = 0, hi = (int)L.n_sub - 1;
     while (lo < hi) {   // last s with item_pref[s] <= it
@@ -170,12 +197,14 @@ __global__ void __launch_bounds__(kThreads2, 1)
     const SubMeta& m = L.meta[s];
     int64_t t = it - item_pref[s];
     const int jlim = m.Bc < jend ? m.Bc : jend;
+    const int ib = ibeg < m.Bc ? ibeg : m.Bc;
     j = jbeg;
     i0 = -1;
     for (; j < jlim; j += 2) {
-      const int cnt = (m.R - j + 1) / 2;
+      const int rb = j > ib ? j : ib;
+      const int cnt = (m.R - rb + 1) / 2;
       if (t < cnt) {
-        i0 = j + 2 * (int)t;
+        i0 = rb + 2 * (int)t;
         break;
       }
       t -= cnt;
@@ -425,17 +454,25 @@ __global__ void __launch_bounds__(kThreads2, 1)
 }  // namespace
 
 void launch_split_panel(const LevelDev& L, int kb0, int nt, int ib, int max_R, uint8_t* split, uint8_t* split_signed,
-                        float* rscale, const int64_t* prow_off, cudaStream_t st) {
-  if (L.n_sub <= 0 || max_R <= ib) return;
+                        float* rscale, const int64_t* prow_off, cudaStream_t st, int panel_operand) {
+  const int first = panel_operand ? kb0 + 1 : ib;   // the rows of a panel operand start after kb0
+  if (L.n_sub <= 0 || max_R <= first) return;
   note_launch();
-  const dim3 grid((unsigned)(max_R - ib), (unsigned)L.n_sub);
+  const dim3 grid((unsigned)(max_R - first), (unsigned)L.n_sub);
   if (nt == 8)
-    k_split_panel<8><<<grid, 512, 0, st>>>(L, kb0, ib, split, split_signed, rscale, prow_off);
+    k_split_panel<8><<<grid, 512, 0, st>>>(L, kb0, ib, panel_operand, split, split_signed, rscale, prow_off);
   else
-    k_split_panel<4><<<grid, 256, 0, st>>>(L, kb0, ib, split, split_signed, rscale, prow_off);
+    k_split_panel<4><<<grid, 256, 0, st>>>(L, kb0, ib, panel_operand, split, split_signed, rscale, prow_off);
 }
 
-void launch_update_tc2(const LevelDev& L, int nq, int jbeg, int jend, int grid, const uint8_t* split,
+void launch_split_inverse(const LevelDev& L, int k0, const float* xinv, uint8_t* split, float* rscale,
+                          const int64_t* prow_off, cudaStream_t st) {
+  if (L.n_sub <= 0) return;
+  note_launch();
+  k_split_inverse<<<dim3(4, (unsigned)L.n_sub), 256, 0, st>>>(L, k0, xinv, split, rscale, prow_off);
+}
+
+void launch_update_tc2(const LevelDev& L, int nq, int jbeg, int jend, int ibeg, int grid, const uint8_t* split,
                        const uint8_t* split_b, const float* rscale, const int64_t* prow_off,
                        const int64_t* item_pref, const TensorMap128& tmap, cudaStream_t st) {
   if (grid <= 0 || L.n_sub <= 0 || nq <= 0 || nq > kPanelTiles) return;
@@ -449,7 +486,7 @@ void launch_update_tc2(const LevelDev& L, int nq, int jbeg, int jend, int grid, 
   CUtensorMap m;
   static_assert(sizeof(CUtensorMap) == sizeof(TensorMap128), "tensor map size");
   std::memcpy(&m, &tmap, sizeof(m));
-  k_update_tc2<<<(unsigned)grid, kThreads2, dyn, st>>>(L, nq, jbeg, jend, split, split_b, rscale, prow_off,
+  k_update_tc2<<<(unsigned)grid, kThreads2, dyn, st>>>(L, nq, jbeg, jend, ibeg, split, split_b, rscale, prow_off,
                                                         item_pref, m);
 }
 
