@@ -1005,7 +1005,7 @@ void factor_level(bddc_handle_s* h, Level& L, cudaStream_t st) {
           const int up = kTcLaunches * p + 3 + half;
           if (L.tc_items[up] > 0) {
             ProfScope ps(h, BDDC_PROF_TC_PANEL, 0.0, L.tc_flops[up], st);
-            launch_update_tc2(d, kSub, k0, k1, k1, (int)std::min<int64_t>(L.tc_items[up], h->grid_max / 2),
+            launch_update_tc2(d, kSub, k0, k1, k1, 1, (int)std::min<int64_t>(L.tc_items[up], h->grid_max / 2),
                               L.split, L.split, L.rscale, L.prow_off, L.item_pref + (size_t)up * (d.n_sub + 1),
                               L.tile_tmap, st);
           }
@@ -1030,7 +1030,7 @@ void factor_level(bddc_handle_s* h, Level& L, cudaStream_t st) {
         if (L.split && items > 0) {   // no launch where no subdomain has columns left
           const double fl = (split_mid && half) ? 0.5 * L.tc_flops[u] : L.tc_flops[u];
           ProfScope ps(h, BDDC_PROF_TC_UPDATE, 0.0, fl, st);
-          launch_update_tc2(d, nq, k1, jend, 0, (int)std::min<int64_t>(items, h->grid_max / 2), L.split,
+          launch_update_tc2(d, nq, k1, jend, 0, 0, (int)std::min<int64_t>(items, h->grid_max / 2), L.split,
                             L.split_signed ? L.split_signed : L.split, L.rscale, L.prow_off,
                             L.item_pref + (size_t)u * (d.n_sub + 1), L.tile_tmap, st);
         }
@@ -2682,7 +2682,7 @@ int bddc_tc_update_check(int64_t n, int rank, float* a, double* ms) {
       ck(cudaEventCreate(&e1), "cudaEventCreate");
       launch_split_panel(d, 0, nt, nt, nb, split, nullptr, rscale, prow_off, st);
       ck(cudaEventRecord(e0, st), "cudaEventRecord");
-      launch_update_tc2(d, nt, nt, nb, 0, (int)std::min<int64_t>(items, std::max(1, sms)), split, split, rscale,
+      launch_update_tc2(d, nt, nt, nb, 0, 0, (int)std::min<int64_t>(items, std::max(1, sms)), split, split, rscale,
                         prow_off, item_pref, tmap, st);
       ck(cudaEventRecord(e1, st), "cudaEventRecord");
       ck(cudaGetLastError(), "tensor-core update launch");

@@ -154,8 +154,7 @@ void launch_block_inverse(const LevelDev& L, int k0, float* xinv, cudaStream_t s
 // blocks from them (persistent grid; item_pref[s] = first work item of subdomain s,
 // item_pref[n_sub] = number of items; split_b = split_signed on indefinite levels, else split)
 // panel_operand = 1: the rows i >= min(ib, Bc) of every subdomain with kb0 < Bc (the rows below
-// a sub-panel's diagonal block, before their panel solve), columns >= Bc as zeros, and the
-// source tiles set to zero after they are read (the panel solve adds its result into them).
+// a sub-panel's diagonal block, before their panel solve), columns >= Bc as zeros.
 void launch_split_panel(const LevelDev& L, int kb0, int nt, int ib, int max_R, uint8_t* split, uint8_t* split_signed,
                         float* rscale, const int64_t* prow_off, cudaStream_t st, int panel_operand = 0);
 // The B operand of a sub-panel's panel solve L(i, D) = A(i, D) X^T S_D: the rows of -S_D X (block
@@ -172,7 +171,10 @@ struct TensorMap128 {
 int make_tile_tmap(TensorMap128* map, float* tiles, int64_t tile_elems);
 // ibeg: the output rows start at max(j, min(ibeg, Bc)) (0 for a trailing update; k0 + 4 for the
 // panel solve of the sub-panel [k0, k0 + 4), whose output columns are jbeg = k0 .. jend = k0 + 4).
-void launch_update_tc2(const LevelDev& L, int nq, int jbeg, int jend, int ibeg, int grid, const uint8_t* split,
+// panel = 1 (a panel solve): the output is stored instead of subtracted (the product is -A B^T
+// with B the split rows of -S_D X; the tiles' old contents are the A operand, already split), and
+// the column pair j, j + 1 takes the K steps 0 .. j - jbeg + 1 (X is block lower triangular).
+void launch_update_tc2(const LevelDev& L, int nq, int jbeg, int jend, int ibeg, int panel, int grid, const uint8_t* split,
                        const uint8_t* split_b, const float* rscale, const int64_t* prow_off,
                        const int64_t* item_pref, const TensorMap128& tmap, cudaStream_t st);
 void launch_gram_chol(const LevelDev& L, int precision_fp32, int max_nc, cudaStream_t st);

@@ -38,11 +38,10 @@ __device__ __forceinline__ void store4h(uint8_t* part, uint32_t off, const __hal
 // so that 16 lanes read a 256-byte row of a tile at once and write its 128-byte FP16 image at
 // once.  Pass 1 loads the warp's 32 rows (16 float4 per lane) and records each row's maximum
 // within the tile; after one barrier, pass 2 takes the row's maximum over the NT tiles and writes
-// the scaled parts.  clear: the source tile is set to zero after it is read (by the lanes that
-// read it).  rowmul: per-row factors (+-1) applied to the entries, or null.  sq: the pivot signs
+// the scaled parts.  rowmul: per-row factors (+-1) applied to the entries, or null.  sq: the pivot signs
 // of the warp's 64 columns for the signed copy (split_signed), or null (zero tile).
 template <int NT>
-__device__ __forceinline__ void split_rows(const float* src, bool clear, const float* __restrict__ rowmul,
+__device__ __forceinline__ void split_rows(const float* src, const float* __restrict__ rowmul,
                                            int64_t row, uint8_t* __restrict__ split,
                                            uint8_t* __restrict__ split_signed, float* __restrict__ rscale,
                                            const float* sq) {
@@ -60,11 +59,6 @@ __device__ __forceinline__ void split_rows(const float* src, bool clear, const f
 #pragma unroll
     for (int o = 8; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (u == 0) pmax[c][r] = mx;
-  }
-  if (clear && t) {
-    float4* w = (float4*)src + u;
-#pragma unroll
-    for (int k = 0; k < 16; ++k) w[(r0 + 2 * k + half) * (NB / 4)] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   __syncthreads();
   uint8_t* dst = split + (row * kPanelTiles + c) * (int64_t)kSplitTile;
@@ -115,13 +109,12 @@ __device__ __forceinline__ void split_rows(const float* src, bool clear, const f
 template <int NT>
 __device__ __forceinline__ void split_row_tile(const LevelDev& L, int s, const SubMeta& m, int i, int kb0,
                                                uint8_t* __restrict__ split, uint8_t* __restrict__ split_signed,
-                                               float* __restrict__ rscale, const int64_t* __restrict__ prow_off,
-                                               bool clear = false) {
+                                               float* __restrict__ rscale, const int64_t* __restrict__ prow_off) {
   const int c = threadIdx.x >> 6;
   const float* src =
       kb0 + c < m.Bc ? (const float*)L.tiles + m.tile_off + split_tile_index(i, kb0 + c, m.Bc) * NB2 : nullptr;
   const float* sq = src ? (const float*)L.sgn + m.vec_off + (int64_t)(kb0 + c) * NB : nullptr;   // column signs
-  split_rows<NT>(src, clear, nullptr, prow_off[s] + i, split, split_signed, rscale, sq);
+  split_rows<NT>(src, nullptr, prow_off[s] + i, split, split_signed, rscale, sq);
 }
 
 }  // namespace bddc

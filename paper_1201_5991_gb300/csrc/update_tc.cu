@@ -94,7 +94,7 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 
 
 // one block per panel row tile i (ib <= i < R) of every subdomain with output columns (ib < Bc);
-// panel_operand: the rows i >= min(ib, Bc) of every subdomain with kb0 < Bc, read and cleared
+// panel_operand: the rows i >= min(ib, Bc) of every subdomain with kb0 < Bc
 template <int NT>
 __global__ void __launch_bounds__(64 * NT) k_split_panel(LevelDev L, int kb0, int ib, int panel_operand,
                                                          uint8_t* __restrict__ split,
@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(64 * NT) k_split_panel(LevelDev L, int kb0, in
     i = ib + (int)blockIdx.x;
   }
   if (i >= m.R) return;
-  split_row_tile<NT>(L, s, m, i, kb0, split, split_signed, rscale, prow_off, panel_operand != 0);
+  split_row_tile<NT>(L, s, m, i, kb0, split, split_signed, rscale, prow_off);
 }
 
 // one block per block row Q of the inverse X of every subdomain's diagonal block (Q < nd): the
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(256) k_split_inverse(LevelDev L, int k0, const
   __syncthreads();
   const int c = threadIdx.x >> 6;   // block column of X; zero above the diagonal blocks
   const float* src = c <= Q ? xinv + ((int64_t)s * 16 + Q * 4 + c) * NB2 : nullptr;
-  split_rows<4>(src, false, rm, prow_off[s] + k0 + Q, split, nullptr, rscale, nullptr);
+  split_rows<4>(src, rm, prow_off[s] + k0 + Q, split, nullptr, rscale, nullptr);
 }
 
 // Persistent: CTA c takes the work items c, c + gridDim.x, ... of the panel (items of all
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(256) k_split_inverse(LevelDev L, int k0, const
 // lane adds the box into the tiles in L2 (the output is never read into the SM; every element
 // receives exactly one add per launch, so the result does not depend on timing).
 __global__ void __launch_bounds__(kThreads2, 1)
-    k_update_tc2(LevelDev L, int nq, int jbeg, int jend, int ibeg, const uint8_t* __restrict__ split,
+    k_update_tc2(LevelDev L, int nq, int jbeg, int jend, int ibeg, int panel, const uint8_t* __restrict__ split,
                  const uint8_t* __restrict__ split_b, const float* __restrict__ rscale,
                  const int64_t* __restrict__ prow_off, const int64_t* __restrict__ item_pref,
                  const __grid_constant__ CUtensorMap tmap) {
@@ -211,9 +211,20 @@ __global__ void __launch_bounds__(kThreads2, 1)
     }
   };
 
-  // steps of this CTA: its items in order, nq panel columns each
+  // steps of this CTA: its items in order, nq panel columns each; a panel solve's B operand (rows
+  // of the inverse of a lower triangular block) is zero beyond block column j - jbeg + 1, so the
+  // column pair j, j + 1 takes K steps 0 .. j - jbeg + 1 only
+  auto item_nq = [&](int j) { return panel ? min(nq, j - jbeg + 2) : nq; };
   const int64_t my_items = (n_items - (int64_t)blockIdx.x + gridDim.x - 1) / gridDim.x;
-  const uint32_t total = (uint32_t)(my_items * nq);
+  uint32_t total = (uint32_t)(my_items * nq);
+  if (panel && warp == 8) {
+    total = 0;
+    for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
+      int cs, cj, ci0;
+      decode(it, cs, cj, ci0);
+      total += (uint32_t)item_nq(cj);
+    }
+  }
   auto wait = [&](uint64_t* bar, uint32_t parity) {
     long long spins = 0;
     while (!mbar_try_wait(bar, parity))
@@ -235,14 +246,15 @@ __global__ void __launch_bounds__(kThreads2, 1)
       const uint8_t* rowB1 = nullptr;
       const float* pre[4] = {nullptr, nullptr, nullptr, nullptr};
       uint32_t gc = 0;
-      for (; gc < total; ++gc) {
+      int nqi = nq, q = 0;
+      for (int64_t k = 0; k < my_items; gc += 1) {
         const int st = (int)(gc % kStages2);
-        const int64_t k = gc / nq;
-        const int q = (int)(gc % nq);
         if (k != cached_k) {   // decode before waiting: the loads overlap the MMAs still reading the stage
           int cs = 0, cj = 0, ci0 = 0;
           decode(blockIdx.x + k * gridDim.x, cs, cj, ci0);
           cached_k = k;
+          nqi = item_nq(cj);
+          q = 0;
           const SubMeta m = L.meta[cs];
           const bool hasA1 = ci0 + 1 < m.R, hasB1 = cj + 1 < (m.Bc < jend ? m.Bc : jend);
           const int64_t rbase = prow_off[cs];
@@ -255,7 +267,7 @@ __global__ void __launch_bounds__(kThreads2, 1)
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
               const int ti = ci0 + a, tj = cj + c;
-              pre[2 * a + c] = ((a == 0 || hasA1) && (c == 0 || hasB1) && (ti >= m.Bc || tj <= ti))
+              pre[2 * a + c] = (!panel && (a == 0 || hasA1) && (c == 0 || hasB1) && (ti >= m.Bc || tj <= ti))
                                    ? (const float*)L.tiles + m.tile_off + tile_index(ti, tj, m.Bc) * NB2
                                    : nullptr;
             }
@@ -281,6 +293,7 @@ __global__ void __launch_bounds__(kThreads2, 1)
           bulk_g2s(sB + p * kOpnd, rowB0 + qo + p * kTilePart, kTilePart, &full_bar[st]);
           bulk_g2s(sB + p * kOpnd + kTilePart, rowB1 + qo + p * kTilePart, kTilePart, &full_bar[st]);
         }
+        if (++q == nqi) ++k;
       }
       s_requested = (int)gc;
       if (lost) atomicExch(L.status + 2, 4);
@@ -348,7 +361,8 @@ __global__ void __launch_bounds__(kThreads2, 1)
       float racc[64];
 #pragma unroll
       for (int c = 0; c < 64; ++c) racc[c] = 0.f;
-      for (int q = 0; q < nq; ++q, ++g) {
+      const int nqi = item_nq(j);
+      for (int q = 0; q < nqi; ++q, ++g) {
         const int b = g & 1;
         const uint32_t n = g >> 1;
         long long spins = 0;
@@ -414,11 +428,18 @@ __global__ void __launch_bounds__(kThreads2, 1)
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           __syncwarp();
           if (lane == 0) {
-            asm volatile(
-                "cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
-                    (uint64_t)&tmap),
-                "r"(32 * hh), "r"(y), "r"(smem_u32(box))
-                : "memory");
+            if (panel)   // a panel solve writes its tiles (their old contents are the split A operand)
+              asm volatile(
+                  "cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                      (uint64_t)&tmap),
+                  "r"(32 * hh), "r"(y), "r"(smem_u32(box))
+                  : "memory");
+            else
+              asm volatile(
+                  "cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                      (uint64_t)&tmap),
+                  "r"(32 * hh), "r"(y), "r"(smem_u32(box))
+                  : "memory");
             asm volatile("cp.async.bulk.commit_group;" ::: "memory");
           }
         }
@@ -472,7 +493,7 @@ void launch_split_inverse(const LevelDev& L, int k0, const float* xinv, uint8_t*
   k_split_inverse<<<dim3(4, (unsigned)L.n_sub), 256, 0, st>>>(L, k0, xinv, split, rscale, prow_off);
 }
 
-void launch_update_tc2(const LevelDev& L, int nq, int jbeg, int jend, int ibeg, int grid, const uint8_t* split,
+void launch_update_tc2(const LevelDev& L, int nq, int jbeg, int jend, int ibeg, int panel, int grid, const uint8_t* split,
                        const uint8_t* split_b, const float* rscale, const int64_t* prow_off,
                        const int64_t* item_pref, const TensorMap128& tmap, cudaStream_t st) {
   if (grid <= 0 || L.n_sub <= 0 || nq <= 0 || nq > kPanelTiles) return;
@@ -486,7 +507,7 @@ void launch_update_tc2(const LevelDev& L, int nq, int jbeg, int jend, int ibeg, 
   CUtensorMap m;
   static_assert(sizeof(CUtensorMap) == sizeof(TensorMap128), "tensor map size");
   std::memcpy(&m, &tmap, sizeof(m));
-  k_update_tc2<<<(unsigned)grid, kThreads2, dyn, st>>>(L, nq, jbeg, jend, ibeg, split, split_b, rscale, prow_off,
+  k_update_tc2<<<(unsigned)grid, kThreads2, dyn, st>>>(L, nq, jbeg, jend, ibeg, panel, split, split_b, rscale, prow_off,
                                                         item_pref, m);
 }
 
