@@ -84,6 +84,8 @@ cudaMemPool_t library_pool() {
 struct DevArena {
   std::vector<void*> ptrs;
   int64_t bytes = 0;
+  double upload_ms = 0.0;       // host time spent in upload (pageable copies stage synchronously)
+  int64_t upload_bytes = 0;
   cudaStream_t st = nullptr;   // allocations and frees are ordered on the handle's stream
   template <typename T>
   T* alloc(int64_t n) {
@@ -96,8 +98,11 @@ struct DevArena {
   }
   template <typename T>
   T* upload(const std::vector<T>& v, cudaStream_t st) {
+    const double t0 = now_ms();
     T* p = alloc<T>((int64_t)v.size());
     if (!v.empty()) ck(cudaMemcpyAsync(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st), "upload");
+    upload_ms += now_ms() - t0;
+    upload_bytes += (int64_t)(sizeof(T) * v.size());
     return p;
   }
   void release() {
@@ -995,10 +1000,9 @@ void factor_level(bddc_handle_s* h, Level& L, cudaStream_t st) {
             bool fused = false;
             for (int k = k0; k < std::min(k1, L.max_Bc); ++k) {
               const bool fuse = k + 1 < k1 && L.block_tiles[k] > 0;
-              launch_potrf_step<T>(d, k, L.max_R, L.block_tiles[k], k1, st, fused, fuse, k1);
+              launch_potrf_step<T>(d, k, L.max_R, L.block_tiles[k], k1, st, fused, fuse, k1, L.xinv, k0);
               fused = fuse;
             }
-            launch_block_inverse(d, k0, L.xinv, st);
             launch_split_inverse(d, k0, L.xinv, L.split, L.rscale, L.prow_off, st);
             launch_split_panel(d, k0, kSub, k1, L.max_R, L.split, nullptr, L.rscale, L.prow_off, st, 1);
           }
@@ -1612,8 +1616,13 @@ void device_setup(bddc_handle_s* h) {
   h->d_coef = A.alloc<double>(h->n_elems);
   h->d_free_of_full = A.upload(h->free_of_full, st);
   for (size_t l = 0; l < h->lv.size(); ++l) {
+    const double tl = now_ms(), u0 = A.upload_ms;
+    const int64_t b0 = A.upload_bytes;
     prepare_level(h, h->lv[l], A, st);
     if (l > 0) prepare_level_segments(h->lv[l], h->lv[l - 1], A, st);
+    if (h->opts.verbose >= 2)
+      fprintf(stderr, "bddc prepare: level %d %8.2f ms (uploads %.2f ms, %.1f MB)\n", (int)l + 1, now_ms() - tl,
+              A.upload_ms - u0, (double)(A.upload_bytes - b0) / 1e6);
   }
   if (h->has_lift) {
     // occurrences (slot, element row) of every free DOF in elements that touch a non-zero
@@ -1692,7 +1701,9 @@ void device_setup(bddc_handle_s* h) {
   const int64_t nbig = std::max<int64_t>(h->n_full, h->lv[0].n_vec);
   h->full_a = A.alloc<double>(nbig);
   h->full_b = A.alloc<double>(nbig);
+  const double ts = now_ms();
   ck(cudaStreamSynchronize(st), "sync");
+  if (h->opts.verbose >= 2) fprintf(stderr, "bddc prepare: final sync %8.2f ms\n", now_ms() - ts);
   h->stats.prepare_ms = now_ms() - t0;
 }
 

@@ -283,14 +283,75 @@ __global__ void k_trsm_panel(LevelDev L, int k, int rlim) {
   }
 }
 
+// ---- inverse of a sub-panel's 256 x 256 diagonal block (FP32, the tensor-core panel solve) ----
+// X = L_D^{-1} for the block D = [k0, k0 + nd) (nd = min(4, Bc - k0)): X_QQ = L_QQ^{-1} (the stored
+// inverse of the diagonal tile) and X_QP = -X_QQ sum_{P <= K < Q} L_QK X_KP for P < Q.  Block row
+// Q needs the tiles L_QK (K < Q) and the rows of X above it, so it is formed during step k0 + Q of
+// the block's factorisation, by blocks of that step's in-block update launch (next to the one that
+// factors tile Q + 1).  One CTA of 256 threads takes 16 columns c0 .. c0 + 15 of X_QP (thread:
+// row r, columns cg .. cg + 3), the sums in ascending K and t; X_QP is stored as a row-major tile
+// at xinv + (s * 16 + 4 Q + P) * 4096 (the diagonal tiles X_QQ are read from the inverses).
+__device__ void xinv_row_part(const LevelDev& L, const SubMeta& m, int s, int k0, int Q, int P, int c0,
+                              float* __restrict__ xinv, unsigned char* smem_raw) {
+  float(*Ls)[NB + 1] = (float(*)[NB + 1])smem_raw;                               // L_QK, then L_QQ^{-1}
+  float(*Xk)[16] = (float(*)[16])(smem_raw + sizeof(float) * NB * (NB + 1));     // X_KP(:, c0 ..)
+  float(*Ts)[16] = (float(*)[16])(smem_raw + sizeof(float) * NB * (NB + 1 + 16));
+  const int tid = threadIdx.x, r = tid >> 2, cg = 4 * (tid & 3);
+  const float* dinv = (const float*)L.dinv + m.dinv_off;
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int K = P; K < Q; ++K) {   // T = sum_K L_QK X_KP
+    const float* lq = tile_ptr<float>(m, L.tiles, k0 + Q, k0 + K);
+    const float* xk = K == P ? dinv + (int64_t)(k0 + P) * NB2 : xinv + ((int64_t)s * 16 + 4 * K + P) * NB2;
+    for (int e = tid; e < NB2; e += blockDim.x) Ls[e >> 6][e & 63] = lq[e];
+    for (int e = tid; e < NB * 16; e += blockDim.x) Xk[e >> 4][e & 15] = xk[(e >> 4) * NB + c0 + (e & 15)];
+    __syncthreads();
+#pragma unroll 8
+    for (int t = 0; t < NB; ++t) {
+      const float a = Ls[r][t];
+      const float4 x = *(const float4*)&Xk[t][cg];
+      acc[0] += a * x.x;
+      acc[1] += a * x.y;
+      acc[2] += a * x.z;
+      acc[3] += a * x.w;
+    }
+    __syncthreads();
+  }
+  *(float4*)&Ts[r][cg] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+  const float* dQ = dinv + (int64_t)(k0 + Q) * NB2;   // X_QP = -L_QQ^{-1} T (lower triangular)
+  for (int e = tid; e < NB2; e += blockDim.x) Ls[e >> 6][e & 63] = dQ[e];
+  __syncthreads();
+  float y[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int t = 0; t <= r; ++t) {
+    const float a = Ls[r][t];
+    const float4 x = *(const float4*)&Ts[t][cg];
+    y[0] += a * x.x;
+    y[1] += a * x.y;
+    y[2] += a * x.z;
+    y[3] += a * x.w;
+  }
+  float* dst = xinv + ((int64_t)s * 16 + 4 * Q + P) * NB2 + r * NB + c0 + cg;
+  *(float4*)dst = make_float4(-y[0], -y[1], -y[2], -y[3]);
+}
+
 // ---- step k, part 3: trailing update A(i,j) -= L(i,k) L(j,k)^T, k < j <= i, j < min(Bc, jmax) --
 // fuse_next: the block that updates the next diagonal tile (k+1, k+1) (always block 0 of its
 // subdomain) factors and inverts it right away, and step k+1 launches no k_potrf_diag.
-// rlim > 0: only rows i < min(rlim, Bc) (the diagonal block of a sub-panel).
+// rlim > 0: only rows i < min(rlim, Bc) (the diagonal block of a sub-panel).  xinv (FP32 panel
+// solves): the blocks n_upd .. n_upd + 4 xq - 1 of the grid form block row xq = k - k0 of the
+// inverse of the diagonal block [k0, k0 + 4) (block column P = e / 4, columns 16 (e % 4) ..).
 template <typename T>
-__global__ void k_syrk_update(LevelDev L, int k, int jmax, int fuse_next, int rlim) {
+__global__ void k_syrk_update(LevelDev L, int k, int jmax, int fuse_next, int rlim, int n_upd, float* xinv,
+                              int k0) {
   const int s = blockIdx.y;
   const SubMeta m = L.meta[s];
+  if ((int)blockIdx.x >= n_upd) {
+    if constexpr (sizeof(T) == 4) {
+      const int e = (int)blockIdx.x - n_upd, Q = k - k0;
+      extern __shared__ __align__(16) unsigned char smem_raw[];
+      if (xinv && Q < m.Bc - k0) xinv_row_part(L, m, s, k0, Q, e >> 2, 16 * (e & 3), xinv, smem_raw);
+    }
+    return;
+  }
   if (k >= m.Bc) return;
   const int jend = jmax < m.Bc ? jmax : m.Bc;
   const int ilim = rlim > 0 ? (rlim < m.Bc ? rlim : m.Bc) : m.R;
@@ -330,64 +391,6 @@ __global__ void k_syrk_update(LevelDev L, int k, int jmax, int fuse_next, int rl
   if (fuse_next && i == k + 1 && j == k + 1) {   // block-uniform
     __syncthreads();   // the updated tile is in global memory, visible to the whole block
     factor_diag_tile<T>(L, m, s, k + 1, smem_raw);
-  }
-}
-
-// ---- inverse of a sub-panel's 256 x 256 diagonal block (FP32, the tensor-core panel solve) ----
-// X = L_D^{-1} by block columns: column block P of X solves L_D X(:, P) = E_P, so X_PP = L_PP^{-1}
-// (the diagonal tile's stored inverse) and X_QP = -X_QQ sum_{P <= K < Q} L_QK X_KP for Q > P.  The
-// block columns are independent: block (P, c) of the grid takes the 16 columns 16 c .. + 15 of
-// column block P (thread: row r, columns cg .. cg + 3), every sum in ascending K and t.
-__global__ void __launch_bounds__(256) k_block_inverse(LevelDev L, int k0, float* __restrict__ xinv) {
-  const int s = blockIdx.y;
-  const SubMeta m = L.meta[s];
-  const int nd = m.Bc - k0 < 4 ? m.Bc - k0 : 4;
-  const int P = blockIdx.x >> 2, c0 = 16 * (blockIdx.x & 3);
-  if (P >= nd) return;
-  __shared__ float Ls[NB][NB + 1];                  // the tile being applied: L_QK, then L_QQ^{-1}
-  __shared__ __align__(16) float Xc[4][NB][16];     // X_KP(:, c0 .. c0 + 15), K = P .. nd - 1
-  __shared__ __align__(16) float Ts[NB][16];
-  const int tid = threadIdx.x, r = tid >> 2, cg = 4 * (tid & 3);
-  const float* dinv = (const float*)L.dinv + m.dinv_off;
-  const float* dP = dinv + (int64_t)(k0 + P) * NB2;
-  for (int e = tid; e < NB * 16; e += 256) Xc[P][e >> 4][e & 15] = dP[(e >> 4) * NB + c0 + (e & 15)];
-  __syncthreads();
-  for (int Q = P + 1; Q < nd; ++Q) {
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int K = P; K < Q; ++K) {   // T = sum_K L_QK X_KP
-      const float* lq = tile_ptr<float>(m, L.tiles, k0 + Q, k0 + K);
-      for (int e = tid; e < NB2; e += 256) Ls[e >> 6][e & 63] = lq[e];
-      __syncthreads();
-#pragma unroll 8
-      for (int t = 0; t < NB; ++t) {
-        const float a = Ls[r][t];
-        const float4 x = *(const float4*)&Xc[K][t][cg];
-        acc[0] += a * x.x;
-        acc[1] += a * x.y;
-        acc[2] += a * x.z;
-        acc[3] += a * x.w;
-      }
-      __syncthreads();
-    }
-    *(float4*)&Ts[r][cg] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-    const float* dQ = dinv + (int64_t)(k0 + Q) * NB2;   // X_QP = -L_QQ^{-1} T (lower triangular)
-    for (int e = tid; e < NB2; e += 256) Ls[e >> 6][e & 63] = dQ[e];
-    __syncthreads();
-    float y[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int t = 0; t <= r; ++t) {
-      const float a = Ls[r][t];
-      const float4 x = *(const float4*)&Ts[t][cg];
-      y[0] += a * x.x;
-      y[1] += a * x.y;
-      y[2] += a * x.z;
-      y[3] += a * x.w;
-    }
-    *(float4*)&Xc[Q][r][cg] = make_float4(-y[0], -y[1], -y[2], -y[3]);
-    __syncthreads();
-  }
-  for (int Q = P; Q < nd; ++Q) {
-    float* dst = xinv + ((int64_t)s * 16 + Q * 4 + P) * NB2;
-    for (int e = tid; e < NB * 16; e += 256) dst[(e >> 4) * NB + c0 + (e & 15)] = Xc[Q][e >> 4][e & 15];
   }
 }
 
@@ -1008,7 +1011,7 @@ void launch_coarse_apply(const float* W, int64_t npad, const float* x, float* y,
 
 template <typename T>
 void launch_potrf_step(const LevelDev& L, int k, int max_R, int max_tiles, int jmax, cudaStream_t st, int skip_diag,
-                       int fuse_next, int rlim) {
+                       int fuse_next, int rlim, float* xinv, int k0) {
   const unsigned ns = (unsigned)L.n_sub;
   const size_t sm = 2 * NB * LDS * sizeof(T);
   const size_t sm_diag = 2 * NB * (NB + 1) * sizeof(T);
@@ -1023,16 +1026,13 @@ void launch_potrf_step(const LevelDev& L, int k, int max_R, int max_tiles, int j
   if (!skip_diag) { note_launch(); k_potrf_diag<T><<<ns, 256, sm_diag, st>>>(L, k); }
   const int panel = (rlim > 0 && rlim < max_R ? rlim : max_R) - k - 1;
   if (panel > 0) { note_launch(); k_trsm_panel<T><<<dim3((unsigned)panel, ns), 256, sm, st>>>(L, k, rlim); }
-  if (max_tiles > 0) {
+  static_assert(sizeof(float) * NB * (NB + 1 + 32) <= 2 * NB * LDS * sizeof(float), "block inverse shared memory");
+  const int xq = xinv && sizeof(T) == 4 ? k - k0 : 0;   // block row of the diagonal block's inverse
+  if (max_tiles > 0 || xq > 0) {
     note_launch();
-    k_syrk_update<T><<<dim3((unsigned)max_tiles, ns), 256, sm, st>>>(L, k, jmax, fuse_next, rlim);
+    k_syrk_update<T><<<dim3((unsigned)(max_tiles + 4 * xq), ns), 256, sm, st>>>(L, k, jmax, fuse_next, rlim, max_tiles,
+                                                                               xinv, k0);
   }
-}
-
-void launch_block_inverse(const LevelDev& L, int k0, float* xinv, cudaStream_t st) {
-  if (L.n_sub <= 0) return;
-  note_launch();
-  k_block_inverse<<<dim3(16, (unsigned)L.n_sub), 256, 0, st>>>(L, k0, xinv);
 }
 
 template <typename T>
@@ -1151,7 +1151,7 @@ void launch_psi_transpose(const LevelDev& L, int max_nGb, int max_ncb, cudaStrea
 }
 
 #define INST(T)                                                                                 \
-  template void launch_potrf_step<T>(const LevelDev&, int, int, int, int, cudaStream_t, int, int, int); \
+  template void launch_potrf_step<T>(const LevelDev&, int, int, int, int, cudaStream_t, int, int, int, float*, int); \
   template void launch_psi<T>(const LevelDev&, int, int, cudaStream_t);                          \
   template void launch_constraint_corr<T>(const LevelDev&, T*, const int32_t*, int64_t, double*, double*, double*, \
                                          int, int, cudaStream_t, int);                                     \

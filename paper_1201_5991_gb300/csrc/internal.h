@@ -136,15 +136,13 @@ void launch_weights(const LevelDev& L, int multiplicity, const double* unused, c
 // fuse_next: the update's block for tile (k+1, k+1) factors it (only when max_tiles > 0 and
 // k + 1 < jmax, i.e. that tile receives its last update in this step).
 // rlim > 0: the rows of the diagonal block only (i < min(rlim, Bc) in the panel and the update).
+// xinv (FP32, rlim = k0 + 4): the step also forms block row k - k0 of X = L_D^{-1}, the inverse of
+// the diagonal block D = [k0, k0 + nd) (nd = min(4, Bc - k0)), X_QP = -X_QQ sum_{P <= K < Q} L_QK X_KP
+// for P < Q, as row-major 64 x 64 tiles at xinv + (s * 16 + 4 Q + P) * 4096 (X_QQ = L_QQ^{-1} stays
+// in the stored inverses); a step with no in-block update tiles then launches for X alone.
 template <typename T>
 void launch_potrf_step(const LevelDev& L, int k, int max_R, int max_tiles, int jmax, cudaStream_t st,
-                       int skip_diag = 0, int fuse_next = 0, int rlim = 0);
-// The 256 x 256 diagonal block D of the sub-panel [k0, k0 + 4) of every subdomain (nd = min(4,
-// Bc - k0) tiles, factored as L_D S_D L_D^T by launch_potrf_step with rlim = k0 + 4): its inverse
-// X = L_D^{-1}, by block columns, X_PP = L_PP^{-1} (the stored inverse of the diagonal tile) and
-// X_QP = -X_QQ sum_{P <= K < Q} L_QK X_KP, written as 4 x 4 tiles of 64 x 64 (row-major blocks,
-// zero above the diagonal blocks) at xinv + s * 16 * 4096.  FP32 levels only.
-void launch_block_inverse(const LevelDev& L, int k0, float* xinv, cudaStream_t st);
+                       int skip_diag = 0, int fuse_next = 0, int rlim = 0, float* xinv = nullptr, int k0 = 0);
 // update_tc.cu, FP32 levels with tensor cores: rank-(64 nt) update of the output columns
 // ib <= j < jend from the nt panel tile columns kb0 .. kb0+nt-1 (nt = 4 or 8).  k_split_panel
 // writes the two scaled FP16 parts of the panel tiles L(i, kb0 + q), i >= ib, at
@@ -158,8 +156,8 @@ void launch_block_inverse(const LevelDev& L, int k0, float* xinv, cudaStream_t s
 void launch_split_panel(const LevelDev& L, int kb0, int nt, int ib, int max_R, uint8_t* split, uint8_t* split_signed,
                         float* rscale, const int64_t* prow_off, cudaStream_t st, int panel_operand = 0);
 // The B operand of a sub-panel's panel solve L(i, D) = A(i, D) X^T S_D: the rows of -S_D X (block
-// row Q of xinv, pivot signs of the block's columns) split like the panel rows into the split
-// rows prow_off[s] + k0 + Q, tile columns 0 .. 3, with their unscaling factors in rscale.
+// row Q of xinv and L_QQ^{-1}, pivot signs of the block's columns) split like the panel rows into
+// the split rows prow_off[s] + k0 + Q, tile columns 0 .. 3, with their unscaling factors in rscale.
 void launch_split_inverse(const LevelDev& L, int k0, const float* xinv, uint8_t* split, float* rscale,
                           const int64_t* prow_off, cudaStream_t st);
 // The update adds its output into the tiles with TMA reduce-adds through this tensor map: the

@@ -129,7 +129,9 @@ __global__ void __launch_bounds__(256) k_split_inverse(LevelDev L, int k0, const
   if (threadIdx.x < NB) rm[threadIdx.x] = sg[threadIdx.x] < 0.f ? 1.f : -1.f;   // -s_r
   __syncthreads();
   const int c = threadIdx.x >> 6;   // block column of X; zero above the diagonal blocks
-  const float* src = c <= Q ? xinv + ((int64_t)s * 16 + Q * 4 + c) * NB2 : nullptr;
+  const float* src = c < Q    ? xinv + ((int64_t)s * 16 + Q * 4 + c) * NB2
+                     : c == Q ? (const float*)L.dinv + m.dinv_off + (int64_t)(k0 + Q) * NB2
+                              : nullptr;
   split_rows<4>(src, rm, prow_off[s] + k0 + Q, split, nullptr, rscale, nullptr);
 }
 
