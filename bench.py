@@ -374,9 +374,12 @@ def run_gpu(args, rank, world, local_rank):
         barrier()
         clk = sampler.stop() if sampler else None
         ms = max_over_ranks(sum(times) / len(times), world, dev)
+        last_times[:] = [round(t, 2) for t in times]
         return ms, stats, launches, prof, clk
 
+    last_times = []
     ms, stats, launches, prof, clk = timed("mixed", args.steps, args.warmup, profile=1, clocks=True)
+    step_ms = list(last_times)
     value = weak_scaling_value(prob.n_free, world, ms)
     st0 = stats[-1]
 
@@ -513,6 +516,7 @@ def run_gpu(args, rank, world, local_rank):
         "config": workload_config(prob, {"precision": "mixed (FP32 factors, FP64 Krylov and Schur operator)",
                                          "replicas": world}),
         "time_to_1e-8_ms": ms,
+        "step_ms": step_ms,
         "iterations": st0.iterations,
         "rel_residual": st0.rel_residual,
         "setup_ms": st0.analysis_ms + st0.prepare_ms + st0.factor_ms,

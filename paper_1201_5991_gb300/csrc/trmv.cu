@@ -166,23 +166,40 @@ __global__ void __launch_bounds__(256) k_schur_snapshot(LevelDev L, int b) {
 }
 
 // One pass over the stored lower tiles of M for y = M x.  Block (o, s, group) takes block row
-// i = nGb - 1 - o (longest rows first).  The row's tiles stream through a ring of kSymvStages
-// shared-memory stages filled with cp.async (16 bytes per thread and copy, rows padded to 68
-// floats, kSymvStages - 1 tiles in flight).  Warp w, half h = lane / 16 own the columns
-// c0 = 8 w + 4 h .. c0 + 3 of every tile, lane r4 = lane % 16 the rows r4, r4 + 16, r4 + 32,
-// r4 + 48 (with the padding, a warp's 16-byte reads of a tile hit every bank pair once per
-// 128-byte wavefront).
-//   row part      y_i += M_ij x_j: per lane over its rows, added over the 16 column groups at the end;
-//   column part   M_ij^T x_i (j < i): summed over the 16 row groups of a half-warp by shuffles and
-//                 written to part (64 floats per tile and right-hand side), added later in order;
+// i = nGb - 1 - o (longest rows first).  The row's tiles (contiguous) stream through a ring of
+// kSymvStages shared-memory stages, one 16 KB cp.async.bulk per tile (completion on an mbarrier
+// per stage; every stage but the one being read has its copy in flight).  Warp w takes the tile
+// rows w, w + 8, ..., w + 56, lane l the columns 2 l, 2 l + 1 (every row one 256-byte read).
+//   row part      y_i += M_ij x_j: per (row, right-hand side) over the lane's columns, added over
+//                 the lanes once at the end of the block row;
+//   column part   M_ij^T x_i (j < i): per lane over the warp's rows, then over the eight warps
+//                 through shared memory (double-buffered, one barrier per tile) and written to
+//                 part (64 floats per tile and right-hand side), added later in order;
 // the diagonal tile holds M_ii in its lower triangle only (the factorisation updates the full
 // tile but its upper part never held the matrix): its row part uses the lower triangle, its
-// column part the strict lower triangle, both into y_i.
+// column part the strict lower triangle, both into y_i.  Waits are bounded: a copy that never
+// lands sets status[2] (the result is then garbage and the host reports the timeout).
 constexpr int kSymvStages = 4;
-constexpr int kSymvLd = NB + 4;   // padded row of a staged tile (floats)
+constexpr long long kSymvSpins = 1ll << 24;
 
-__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ void tile_g2s(float* dst, const float* src, uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"((uint32_t)(NB2 * 4))
+               : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"((uint32_t)(NB2 * 4)), "r"(smem_u32(bar))
                : "memory");
 }
 
@@ -194,119 +211,126 @@ __global__ void __launch_bounds__(256) k_schur_symv_rows(LevelDev L, const float
   const SubMeta m = L.meta[s];
   if ((int)blockIdx.x >= m.nGb) return;
   const int i = m.nGb - 1 - (int)blockIdx.x;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int h = lane >> 4, r4 = lane & 15;
-  const int c0 = 8 * warp + 4 * h;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t c0q = (int64_t)blockIdx.z * NR * L.n_vec;   // first column of this group
   const float* xv = x + c0q + m.vec_off + (int64_t)m.nIb * NB;
-  extern __shared__ __align__(16) float ring[];              // kSymvStages x NB x kSymvLd
-  __shared__ float red[16][NR][NB];
+  extern __shared__ __align__(128) float ring[];             // kSymvStages x NB2
+  __shared__ __align__(8) uint64_t full[kSymvStages];
+  __shared__ __align__(16) float cred[2][8][NR][NB];
   __shared__ float dcol[NR][NB];
   const float* Mrow = L.schur + schur_tile(m, i, 0);
-  auto issue = [&](int j) {   // tile j of the row into stage j % kSymvStages
-    const float* src = Mrow + (int64_t)j * NB2;
-    float* dst = ring + (j % kSymvStages) * NB * kSymvLd;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int c = threadIdx.x + 256 * u;   // 16-byte chunk: row c / 16, column 4 (c % 16)
-      cp_async16(dst + (c >> 4) * kSymvLd + 4 * (c & 15), src + 4 * c);
-    }
-  };
-#pragma unroll
-  for (int j = 0; j < kSymvStages - 1; ++j) {
-    if (j <= i) issue(j);
-    asm volatile("cp.async.commit_group;" ::: "memory");
+  const int ntile = i + 1;
+  if (tid == 0) {
+    for (int k = 0; k < kSymvStages; ++k)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[k])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // x_i at this lane's rows
-  float xi[NR][4];
-#pragma unroll
-  for (int q = 0; q < NR; ++q)
-#pragma unroll
-    for (int k = 0; k < 4; ++k) xi[q][k] = xv[q * L.n_vec + (int64_t)i * NB + r4 + 16 * k];
-  float racc[4][NR];
-#pragma unroll
-  for (int k = 0; k < 4; ++k)
-#pragma unroll
-    for (int q = 0; q < NR; ++q) racc[k][q] = 0.f;
-  float* prow = part + (int64_t)blockIdx.z * NR * part_stride + part_off[s] + (int64_t)i * (i - 1) / 2 * NB;
-  for (int j = 0; j <= i; ++j) {
-    // tile j has landed (this thread's copies), then every thread's copies and the end of the
-    // previous tile's reads; then the stage read two tiles ago is refilled
-    asm volatile("cp.async.wait_group %0;" ::"n"(kSymvStages - 2) : "memory");
-    __syncthreads();
-    if (j + kSymvStages - 1 <= i) issue(j + kSymvStages - 1);
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    const float* T = ring + (j % kSymvStages) * NB * kSymvLd;
-    float4 a[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) a[k] = *(const float4*)(T + (r4 + 16 * k) * kSymvLd + c0);
-    if (j == i) {   // lower triangle only (strictly lower for the column part)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int r = r4 + 16 * k;
-        if (c0 + 0 > r) a[k].x = 0.f;
-        if (c0 + 1 > r) a[k].y = 0.f;
-        if (c0 + 2 > r) a[k].z = 0.f;
-        if (c0 + 3 > r) a[k].w = 0.f;
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < NR; ++q) {
-      const float4 xj = *(const float4*)(xv + q * L.n_vec + (int64_t)j * NB + c0);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) racc[k][q] += a[k].x * xj.x + a[k].y * xj.y + a[k].z * xj.z + a[k].w * xj.w;
-    }
-    // column part: sum over the rows of the tile
-    float cp[NR][4];
-#pragma unroll
-    for (int q = 0; q < NR; ++q) {
-      float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int r = r4 + 16 * k;
-        // the diagonal tile's column part excludes the diagonal itself
-        const float xr = xi[q][k];
-        d0 += (j == i && c0 + 0 == r) ? 0.f : a[k].x * xr;
-        d1 += (j == i && c0 + 1 == r) ? 0.f : a[k].y * xr;
-        d2 += (j == i && c0 + 2 == r) ? 0.f : a[k].z * xr;
-        d3 += (j == i && c0 + 3 == r) ? 0.f : a[k].w * xr;
-      }
-      cp[q][0] = d0;
-      cp[q][1] = d1;
-      cp[q][2] = d2;
-      cp[q][3] = d3;
-    }
-#pragma unroll
-    for (int o = 8; o > 0; o >>= 1)
-#pragma unroll
-      for (int q = 0; q < NR; ++q)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) cp[q][e] += __shfl_xor_sync(0xffffffffu, cp[q][e], o);
-    if (r4 == 0) {
-#pragma unroll
-      for (int q = 0; q < NR; ++q) {
-        const float4 v = make_float4(cp[q][0], cp[q][1], cp[q][2], cp[q][3]);
-        if (j < i)
-          *(float4*)(prow + q * part_stride + (int64_t)j * NB + c0) = v;
-        else
-          *(float4*)&dcol[q][c0] = v;
-      }
-    }
-  }
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
-#pragma unroll
-  for (int q = 0; q < NR; ++q)
-#pragma unroll
-    for (int k = 0; k < 4; ++k) red[2 * warp + h][q][r4 + 16 * k] = racc[k][q];
   __syncthreads();
-  float* yv = y + c0q + m.vec_off + (int64_t)m.nIb * NB + (int64_t)i * NB;
-  for (int e = threadIdx.x; e < NR * NB; e += blockDim.x) {
-    const int q = e / NB, c = e % NB;
-    float v = 0.f;
-#pragma unroll
-    for (int g = 0; g < 16; ++g) v += red[g][q][c];
-    yv[q * L.n_vec + c] = v + dcol[q][c];
+  uint32_t issued = 0;
+  if (tid == 0) {
+    const int pre = ntile < kSymvStages ? ntile : kSymvStages;
+    for (int k = 0; k < pre; ++k) tile_g2s(ring + k * NB2, Mrow + (int64_t)k * NB2, &full[k]);
+    issued = (uint32_t)pre;
   }
+  float xi[NR][8];   // x_i at this thread's rows
+#pragma unroll
+  for (int q = 0; q < NR; ++q)
+#pragma unroll
+    for (int r = 0; r < 8; ++r) xi[q][r] = xv[q * L.n_vec + (int64_t)i * NB + warp + 8 * r];
+  float acc[8][NR];
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int q = 0; q < NR; ++q) acc[r][q] = 0.f;
+  float* prow = part + (int64_t)blockIdx.z * NR * part_stride + part_off[s] + (int64_t)i * (i - 1) / 2 * NB;
+  bool lost = false;
+  for (int j = 0; j < ntile; ++j) {
+    float2 xj[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) xj[q] = __ldg((const float2*)(xv + q * L.n_vec + (int64_t)j * NB + 2 * lane));
+    const int slot = j % kSymvStages;
+    {
+      long long spins = 0;
+      while (!mbar_try_wait(&full[slot], (uint32_t)(j / kSymvStages) & 1u))
+        if (++spins > kSymvSpins) {
+          if (!lost) atomicExch(L.status + 2, 5);
+          lost = true;
+          break;
+        }
+    }
+    const float* T = ring + slot * NB2 + 2 * lane;
+    float2 a[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) a[r] = *(const float2*)(T + (warp + 8 * r) * NB);
+    float2 cs[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) cs[q] = make_float2(0.f, 0.f);
+    if (j < i) {
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+          acc[r][q] += a[r].x * xj[q].x + a[r].y * xj[q].y;
+          cs[q].x += a[r].x * xi[q][r];
+          cs[q].y += a[r].y * xi[q][r];
+        }
+    } else {   // diagonal tile: lower triangle for the row part, strict lower for the column part
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int row = warp + 8 * r, c = 2 * lane;
+        const float ax = c <= row ? a[r].x : 0.f, ay = c + 1 <= row ? a[r].y : 0.f;
+        const float bx = c < row ? a[r].x : 0.f, by = c + 1 < row ? a[r].y : 0.f;
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+          acc[r][q] += ax * xj[q].x + ay * xj[q].y;
+          cs[q].x += bx * xi[q][r];
+          cs[q].y += by * xi[q][r];
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NR; ++q) *(float2*)&cred[j & 1][warp][q][2 * lane] = cs[q];
+    __syncthreads();   // the stage is read by every thread; cred[j & 1] is complete
+    if (tid == 0 && j + kSymvStages < ntile) {
+      tile_g2s(ring + slot * NB2, Mrow + (int64_t)(j + kSymvStages) * NB2, &full[slot]);
+      ++issued;
+    }
+    // column sums of tile j over the warps (cred[j & 1] is next written at tile j + 2, after
+    // the barrier of tile j + 1, which these threads reach only after this reduction)
+    if (tid < NR * NB) {
+      const int q = tid / NB, c = tid % NB;
+      float v = 0.f;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) v += cred[j & 1][w][q][c];
+      if (j < i)
+        prow[q * part_stride + (int64_t)j * NB + c] = v;
+      else
+        dcol[q][c] = v;
+    }
+  }
+  // row sums over the lanes, fixed order (xor butterfly)
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int q = 0; q < NR; ++q)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[r][q] += __shfl_xor_sync(0xffffffffu, acc[r][q], o);
+  __syncthreads();   // dcol is complete
+  if (lane == 0) {
+    float* yv = y + c0q + m.vec_off + (int64_t)m.nIb * NB + (int64_t)i * NB;
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int q = 0; q < NR; ++q) yv[q * L.n_vec + warp + 8 * r] = acc[r][q] + dcol[q][warp + 8 * r];
+  }
+  // after a lost wait, copies may still be landing in this CTA's shared memory: wait (bounded)
+  // for the last phase issued on every stage before the CTA exits
+  if (tid == 0 && lost)
+    for (uint32_t c = issued > (uint32_t)kSymvStages ? issued - kSymvStages : 0u; c < issued; ++c) {
+      long long spins = 0;
+      while (!mbar_try_wait(&full[c % kSymvStages], (c / kSymvStages) & 1u) && ++spins < kSymvSpins) {
+      }
+    }
 }
 
 // y_j += sum_{i > j} part(i, j), i ascending; block (j, s, group)
@@ -339,7 +363,7 @@ void launch_schur_snapshot(const LevelDev& L, int b, int max_nGb, cudaStream_t s
 template <int NR>
 void launch_symv_nr(const LevelDev& L, const dim3& grid, const int64_t* part_off, int64_t part_stride, const float* x,
                     float* part, float* y, cudaStream_t st) {
-  const size_t dyn = sizeof(float) * kSymvStages * NB * kSymvLd;
+  const size_t dyn = sizeof(float) * kSymvStages * NB2;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_schur_symv_rows<NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
