@@ -145,6 +145,10 @@ typedef struct {
                                count is padded to a multiple of 4 tiles), one pass over its lower
                                triangle per product.  Elasticity and Poisson with tensor cores only;
                                otherwise 1 */
+  int retain_host_memory;   /* 1 (default): at the first set-up of the process, ask the C library's
+                               allocator (glibc) to keep freed heap memory (M_TOP_PAD 256 MB,
+                               M_TRIM_THRESHOLD 1 GB), so that repeated set-ups do not page-fault
+                               their host index arrays in again; 0: leave the allocator alone */
 } bddc_opts;
 
 #define BDDC_KRYLOV_AUTO 0

@@ -63,6 +63,7 @@ class Opts(C.Structure):
         ("refine_steps", C.c_int), ("flexible", C.c_int), ("use_graph", C.c_int), ("verbose", C.c_int),
         ("profile", C.c_int), ("tensor_cores", C.c_int), ("inner_steps", C.c_int), ("inner_tol", C.c_double),
         ("krylov", C.c_int), ("autotune", C.c_int), ("wait_probe", C.c_int), ("inner_operator", C.c_int),
+        ("retain_host_memory", C.c_int),
     ]
 
 

@@ -3,6 +3,9 @@
 // Every numerical step runs in the kernels of assemble.cu, dense.cu and vector.cu; this
 // file prepares index arrays, allocates device memory and enqueues launches.
 #include <cuda_runtime.h>
+#if defined(__GLIBC__) || defined(__linux__)
+#include <malloc.h>
+#endif
 
 #include <algorithm>
 #include <array>
@@ -1485,7 +1488,21 @@ void numeric_setup(bddc_handle_s* h) {
   h->factored = true;
 }
 
+// Repeated set-ups allocate and free tens of MB of host index arrays; with glibc's defaults the
+// freed heap top is returned to the kernel and the next set-up faults it in again.  Padding and
+// retaining the heap top keeps those pages (opts.retain_host_memory, once per process).
+void retain_host_heap() {
+#ifdef __GLIBC__
+  static std::once_flag once;
+  std::call_once(once, []() {
+    mallopt(M_TOP_PAD, 256 << 20);
+    mallopt(M_TRIM_THRESHOLD, 1 << 30);
+  });
+#endif
+}
+
 void analysis(bddc_handle_s* h, const bddc_mesh* mesh, const bddc_partition* part) {
+  if (h->opts.retain_host_memory) retain_host_heap();
   const double t0 = now_ms();
   if (!mesh || !part) fail(BDDC_ERR_INVALID, "null mesh or partition");
   if (h->opts.krylov < BDDC_KRYLOV_AUTO || h->opts.krylov > BDDC_KRYLOV_FGMRES) fail(BDDC_ERR_INVALID, "unknown Krylov method");
@@ -2423,6 +2440,7 @@ void bddc_default_opts(bddc_opts* o) {
   o->tensor_cores = 1;
   o->autotune = 1;
   o->inner_operator = 0;
+  o->retain_host_memory = 1;
 }
 
 int bddc_analyze(const bddc_mesh* mesh, const bddc_partition* part, unsigned constraints, const bddc_opts* opts,

@@ -48,7 +48,7 @@ def host_mesh(prob, n_levels: Optional[int] = None) -> _HostMesh:
 
 def make_opts(precision="mixed", weights="stiffness", all_corners=0, maxit=500, refine_steps=0, flexible=-1,
               use_graph=1, profile=0, tensor_cores=1, inner_steps=0, inner_tol=0.0, krylov=0,
-              autotune=1, verbose=0, wait_probe=0, inner_operator=0) -> capi.Opts:
+              autotune=1, verbose=0, wait_probe=0, inner_operator=0, retain_host_memory=1) -> capi.Opts:
     o = capi.Opts()
     capi.lib().bddc_default_opts(C.byref(o))
     o.precision = capi.PREC_MIXED if precision == "mixed" else capi.PREC_FP64
@@ -67,6 +67,7 @@ def make_opts(precision="mixed", weights="stiffness", all_corners=0, maxit=500, 
     o.verbose = int(verbose)
     o.wait_probe = int(wait_probe)
     o.inner_operator = int(inner_operator)
+    o.retain_host_memory = int(retain_host_memory)
     return o
 
 
