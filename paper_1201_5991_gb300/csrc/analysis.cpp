@@ -15,6 +15,8 @@
 #include "analysis.h"
 
 #include <algorithm>
+#include <condition_variable>
+#include <mutex>
 #include <atomic>
 #include <cmath>
 #include <functional>
@@ -64,24 +66,9 @@ double cross_norm(const Pt& p, const Pt& o, const double* u) {
   return std::sqrt(c0 * c0 + c1 * c1 + c2 * c2);
 }
 
-constexpr unsigned kWorkers = 16;
+constexpr unsigned kWorkers = kHostWorkers;
 
-// fn(i, w) for i in [0, n) on up to kWorkers host threads (independent iterations); w < kWorkers
-// names the thread, so that per-thread scratch can be indexed by it
-void parallel_range_worker(int64_t n, const std::function<void(int64_t, int)>& fn) {
-  const unsigned nt = std::max(1u, std::min(kWorkers, std::thread::hardware_concurrency()));
-  if (n < 4 || nt == 1) {
-    for (int64_t i = 0; i < n; ++i) fn(i, 0);
-    return;
-  }
-  std::atomic<int64_t> next{0};
-  std::vector<std::thread> th;
-  for (unsigned t = 0; t < nt; ++t)
-    th.emplace_back([&, t]() {
-      for (int64_t i; (i = next.fetch_add(1)) < n;) fn(i, (int)t);
-    });
-  for (auto& t : th) t.join();
-}
+void parallel_range_worker(int64_t n, const std::function<void(int64_t, int)>& fn) { host_parallel(n, fn); }
 
 void parallel_range(int64_t n, const std::function<void(int64_t)>& fn) {
   parallel_range_worker(n, [&](int64_t i, int) { fn(i); });
@@ -575,6 +562,86 @@ void next_level_mesh(const LevelMesh& mesh, const LevelMaps& maps, const int32_t
   n.rigid_mask = mesh.rigid_mask;
   n.rigid_points = mesh.rigid_points;
   n.last_comp = mesh.last_comp;
+}
+
+// ------------------------------------------------------------------ host thread pool
+namespace {
+
+// Persistent workers (created on first use, kept for the life of the process): a parallel region
+// publishes the job and an epoch under the mutex, the workers and the caller take iterations from
+// one atomic counter, and the caller waits until every worker has left the region.  Spawning
+// fresh threads for every region cost more than the short regions of a set-up themselves.
+class HostPool {
+ public:
+  explicit HostPool(int nw) {
+    for (int t = 1; t <= nw; ++t) th_.emplace_back([this, t]() { work(t); });
+  }
+  int workers() const { return (int)th_.size(); }
+  void run(int64_t n, const std::function<void(int64_t, int)>& fn) {
+    std::lock_guard<std::mutex> one(run_mu_);   // one region at a time (handles set up concurrently)
+    {
+      std::lock_guard<std::mutex> g(mu_);
+      fn_ = &fn;
+      n_ = n;
+      next_.store(0);
+      busy_ = (int)th_.size();
+      ++epoch_;
+    }
+    cv_.notify_all();
+    in_region() = true;
+    for (int64_t i; (i = next_.fetch_add(1)) < n;) fn(i, 0);
+    in_region() = false;
+    std::unique_lock<std::mutex> g(mu_);
+    done_.wait(g, [this]() { return busy_ == 0; });
+    fn_ = nullptr;
+  }
+  static bool& in_region() {
+    thread_local bool r = false;
+    return r;
+  }
+
+ private:
+  void work(int id) {
+    uint64_t seen = 0;
+    in_region() = true;   // a nested call from a worker runs serially
+    for (;;) {
+      const std::function<void(int64_t, int)>* fn;
+      int64_t n;
+      {
+        std::unique_lock<std::mutex> g(mu_);
+        cv_.wait(g, [&]() { return epoch_ != seen; });
+        seen = epoch_;
+        fn = fn_;
+        n = n_;
+      }
+      for (int64_t i; (i = next_.fetch_add(1)) < n;) (*fn)(i, id);
+      std::lock_guard<std::mutex> g(mu_);
+      if (--busy_ == 0) done_.notify_one();
+    }
+  }
+  std::vector<std::thread> th_;
+  std::mutex mu_, run_mu_;
+  std::condition_variable cv_, done_;
+  const std::function<void(int64_t, int)>* fn_ = nullptr;
+  int64_t n_ = 0;
+  std::atomic<int64_t> next_{0};
+  int busy_ = 0;
+  uint64_t epoch_ = 0;
+};
+
+}  // namespace
+
+void host_parallel(int64_t n, const std::function<void(int64_t, int)>& fn) {
+  static HostPool* pool = []() {
+    const unsigned hc = std::thread::hardware_concurrency();
+    const int nt = (int)std::max(1u, std::min((unsigned)kHostWorkers, hc == 0 ? 1u : hc));
+    return new HostPool(nt - 1);   // never destroyed: the workers sleep until the process exits
+  }();
+  if (n < 4 || pool->workers() == 0 || HostPool::in_region()) {
+    for (int64_t i = 0; i < n; ++i) fn(i, 0);
+    return;
+  }
+  pool->run(n, fn);
 }
 
 }  // namespace bddc

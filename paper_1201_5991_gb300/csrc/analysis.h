@@ -7,10 +7,19 @@
 #pragma once
 
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <vector>
 
 namespace bddc {
+
+// Host worker threads of the set-up, shared by the analysis and the preparation of the levels.
+constexpr int kHostWorkers = 16;
+// fn(i, w) for i in [0, n) (independent iterations) on the calling thread and up to
+// kHostWorkers - 1 persistent pool threads; w < kHostWorkers names the thread, so that per-thread
+// scratch can be indexed by it.  Small ranges, and calls from inside a parallel region, run on
+// the calling thread alone.
+void host_parallel(int64_t n, const std::function<void(int64_t, int)>& fn);
 
 enum GlobKind { kVertex = 0, kEdge = 1, kFace = 2 };
 

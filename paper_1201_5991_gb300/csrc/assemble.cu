@@ -32,7 +32,7 @@ __global__ void k_elem_q1p1(int physics, int64_t n_elems, const double* __restri
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t slot = (int64_t)blockIdx.x * WARPS + w;
   if (slot >= n_elems) return;
-  const int64_t e = slot_elem[slot];
+  const int64_t e = slot_elem ? slot_elem[slot] : slot;
   const double gq = 0.57735026918962576451;   // 1/sqrt(3)
   if (lane < NG) {
     double G[NN][DIM];
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(256) k_elem_q2q1(int64_t n_elems, const double
   constexpr int NE = 108, NLAP = 27 * 27, NB_ = 8 * 81, NACC = (NLAP + NB_ + 255) / 256;
   const int64_t slot = blockIdx.x;
   if (slot >= n_elems) return;
-  const int64_t e = slot_elem[slot];
+  const int64_t e = slot_elem ? slot_elem[slot] : slot;
   __shared__ double X[27][3], Gr[27][3], Gx[27][3], psi[8], Ji[3][3], wd;
   const int tid = threadIdx.x;
   if (tid < 81) X[tid / 3][tid % 3] = coords[(int64_t)conn[e * 27 + tid / 3] * 3 + tid % 3];
@@ -425,6 +425,23 @@ void launch_elem_q2q1(int64_t n_elems, const double* coords, const int32_t* conn
   if (n_elems <= 0) return;
   note_launch();
   k_elem_q2q1<<<(unsigned)n_elems, 256, 0, st>>>(n_elems, coords, conn, coef, slot_elem, ke);
+}
+
+// ke[k] = ke_elem[slot_elem[k]]: element matrices computed in element order, gathered into slots
+__global__ void k_gather_elems(int64_t n_elems, int64_t ne2, const int32_t* __restrict__ slot_elem,
+                               const double* __restrict__ ke_elem, double* __restrict__ ke) {
+  const int64_t k = blockIdx.x;
+  if (k >= n_elems) return;
+  const double* src = ke_elem + (int64_t)slot_elem[k] * ne2;
+  double* dst = ke + k * ne2;
+  for (int64_t t = threadIdx.x; t < ne2; t += blockDim.x) dst[t] = __ldcs(src + t);
+}
+
+void launch_gather_elems(int64_t n_elems, int ne, const int32_t* slot_elem, const double* ke_elem, double* ke,
+                         cudaStream_t st) {
+  if (n_elems <= 0) return;
+  note_launch();
+  k_gather_elems<<<(unsigned)n_elems, 128, 0, st>>>(n_elems, (int64_t)ne * ne, slot_elem, ke_elem, ke);
 }
 
 void launch_lift(int64_t n_free, int ne, const int64_t* lptr, const int32_t* lslot, const int32_t* la,

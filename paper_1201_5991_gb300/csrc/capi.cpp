@@ -108,6 +108,14 @@ struct DevArena {
     upload_bytes += (int64_t)(sizeof(T) * v.size());
     return p;
   }
+  void free_one(void* p) {   // return one allocation to the pool early (stream-ordered)
+    for (size_t k = 0; k < ptrs.size(); ++k)
+      if (ptrs[k] == p) {
+        cudaFreeAsync(p, st);
+        ptrs.erase(ptrs.begin() + (int64_t)k);
+        return;
+      }
+  }
   void release() {
     for (void* p : ptrs) cudaFreeAsync(p, st);
     if (!ptrs.empty()) cudaStreamSynchronize(st);
@@ -276,6 +284,10 @@ struct bddc_handle_s {
   double* d_coords = nullptr;
   int32_t* d_conn = nullptr;
   double* d_coef = nullptr;
+  // set-up only: level-1 element matrices in element order, computed while the host analyses
+  // the mesh (ke_early until numeric_setup gathers them into element slots)
+  double* ke_elem = nullptr;
+  bool ke_early = false;
   int64_t* d_free_of_full = nullptr;
   int* d_status = nullptr;
   // non-zero prescribed values: lift = -K_fd u_d, added to every right-hand side
@@ -432,47 +444,13 @@ void flush_profile(bddc_handle_s* h) {
   h->prof_pending.clear();
 }
 
-constexpr int kHostWorkers = 16;
 constexpr int64_t kMaxSubdomains = 65535;   // CUDA's limit on gridDim.y
 
-// fn(i, w) for i in [0, n) on up to kHostWorkers host threads; w < kHostWorkers names the thread,
-// so that per-thread scratch can be indexed by it
-void parallel_for_worker(int64_t n, const std::function<void(int64_t, int)>& fn) {
-  const unsigned nt = std::max(1u, std::min((unsigned)kHostWorkers, std::thread::hardware_concurrency()));
-  if (n < 4 || nt == 1) {
-    for (int64_t i = 0; i < n; ++i) fn(i, 0);
-    return;
-  }
-  std::vector<std::thread> th;
-  std::atomic<int64_t> next{0};
-  for (unsigned t = 0; t < nt; ++t)
-    th.emplace_back([&, t]() {
-      for (;;) {
-        const int64_t i = next.fetch_add(1);
-        if (i >= n) break;
-        fn(i, (int)t);
-      }
-    });
-  for (auto& t : th) t.join();
-}
+// fn(i, w) / fn(i) for i in [0, n) on the host worker pool (analysis.h)
+void parallel_for_worker(int64_t n, const std::function<void(int64_t, int)>& fn) { host_parallel(n, fn); }
 
 void parallel_for(int64_t n, const std::function<void(int64_t)>& fn) {
-  unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-  if (n < 4 || nt == 1) {
-    for (int64_t i = 0; i < n; ++i) fn(i);
-    return;
-  }
-  std::vector<std::thread> th;
-  std::atomic<int64_t> next{0};
-  for (unsigned t = 0; t < nt; ++t)
-    th.emplace_back([&]() {
-      for (;;) {
-        int64_t i = next.fetch_add(1);
-        if (i >= n) break;
-        fn(i);
-      }
-    });
-  for (auto& t : th) t.join();
+  host_parallel(n, [&](int64_t i, int) { fn(i); });
 }
 
 // ------------------------------------------------------------------ level preparation
@@ -525,6 +503,12 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
   const LevelMaps& mp = L.maps;
   const LevelMesh& ms = L.mesh;
   const int64_t ns = mp.n_sub();
+  double tph = now_ms();
+  auto ph = [&](const char* what) {   // opts.verbose >= 3: host times of the preparation's parts
+    const double t = now_ms();
+    if (h->opts.verbose >= 3) fprintf(stderr, "bddc prepare:   %-24s %8.2f ms\n", what, t - tph);
+    tph = t;
+  };
   L.meta.resize(ns);
   int64_t tile = 0, dinv = 0, vec = 0, coff = 0, goff = 0, psi = 0, psiT = 0, schur = 0, symv = 0;
   L.max_R = L.max_Bc = L.max_nc = L.max_nG = L.max_nGb = L.max_ncb = 0;
@@ -650,21 +634,39 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
     L.trmv_bytes += wsz * ((double)m.nG * (m.nG + 1) + 4.0 * m.nG);   // the triangle twice, vectors
   }
 
+  ph("layout");
   // element slots (subdomain order) and their padded local DOF positions; an element's matrix
   // DOFs are the DOFs of its nodes in node order
   const int64_t nel = ms.n_elems;
   std::vector<int32_t> slot_elem(nel);
   std::vector<int64_t> ke_off(nel + 1), ed_off(nel + 1);
-  for (int64_t s = 0; s < ns; ++s)
-    for (int64_t k = mp.sub_elem_ptr[s]; k < mp.sub_elem_ptr[s + 1]; ++k) slot_elem[k] = (int32_t)mp.sub_elems[k];
-  ke_off[0] = ed_off[0] = 0;
-  for (int64_t k = 0; k < nel; ++k) {
-    const int64_t e = slot_elem[k];
-    int64_t nek = 0;
-    for (int64_t q = ms.en_ptr[e]; q < ms.en_ptr[e + 1]; ++q) nek += ms.nd_ptr[ms.en[q] + 1] - ms.nd_ptr[ms.en[q]];
-    ed_off[k + 1] = ed_off[k] + nek;
-    ke_off[k + 1] = ke_off[k] + nek * nek;
+  // per subdomain (in parallel): the slots' element ids and DOF counts as offsets within the
+  // subdomain; then the subdomains' totals are scanned and added
+  std::vector<int64_t> sub_ed(ns + 1, 0), sub_ke(ns + 1, 0);
+  parallel_for(ns, [&](int64_t s) {
+    int64_t ed = 0, ke = 0;
+    for (int64_t k = mp.sub_elem_ptr[s]; k < mp.sub_elem_ptr[s + 1]; ++k) {
+      const int64_t e = mp.sub_elems[k];
+      slot_elem[k] = (int32_t)e;
+      int64_t nek = 0;
+      for (int64_t q = ms.en_ptr[e]; q < ms.en_ptr[e + 1]; ++q) nek += ms.nd_ptr[ms.en[q] + 1] - ms.nd_ptr[ms.en[q]];
+      ed_off[k + 1] = ed += nek;
+      ke_off[k + 1] = ke += nek * nek;
+    }
+    sub_ed[s + 1] = ed;
+    sub_ke[s + 1] = ke;
+  });
+  for (int64_t s = 0; s < ns; ++s) {
+    sub_ed[s + 1] += sub_ed[s];
+    sub_ke[s + 1] += sub_ke[s];
   }
+  ke_off[0] = ed_off[0] = 0;
+  parallel_for(ns, [&](int64_t s) {
+    for (int64_t k = mp.sub_elem_ptr[s]; k < mp.sub_elem_ptr[s + 1]; ++k) {
+      ed_off[k + 1] += sub_ed[s];
+      ke_off[k + 1] += sub_ke[s];
+    }
+  });
   std::vector<int32_t> eldof(ed_off[nel]);
   std::vector<int32_t> loc2iface(L.n_vec, -1), loc2glob(L.n_vec, -1), row_sub(L.n_vec);
   // row contributions (ascending element slot) per padded row: every row of subdomain s only
@@ -704,7 +706,21 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
     for (int64_t q = mp.sub_dof_ptr[s]; q < mp.sub_dof_ptr[s + 1]; ++q) pos[mp.sub_dofs[q]] = -1;
   });
   if (missing) fail(BDDC_ERR_INVALID, "an element DOF is missing from its subdomain's local numbering");
-  for (int64_t r = 0; r < L.n_vec; ++r) rc_ptr[r + 1] += rc_ptr[r];
+  {   // scan of the row counts: within every subdomain's rows in parallel, then across subdomains
+    std::vector<int64_t> tot(ns + 1, 0);
+    parallel_for(ns, [&](int64_t s) {
+      const SubMeta& m = L.meta[s];
+      int64_t* r = rc_ptr.data() + m.vec_off + 1;
+      for (int64_t p = 1; p < (int64_t)m.Bc * NB; ++p) r[p] += r[p - 1];
+      tot[s + 1] = m.Bc > 0 ? r[(int64_t)m.Bc * NB - 1] : 0;
+    });
+    for (int64_t s = 0; s < ns; ++s) tot[s + 1] += tot[s];
+    parallel_for(ns, [&](int64_t s) {
+      const SubMeta& m = L.meta[s];
+      int64_t* r = rc_ptr.data() + m.vec_off + 1;
+      for (int64_t p = 0; p < (int64_t)m.Bc * NB; ++p) r[p] += tot[s];
+    });
+  }
   std::vector<int32_t> rc_elem(rc_ptr[L.n_vec]), rc_a(rc_ptr[L.n_vec]);
   parallel_for(ns, [&](int64_t s) {
     const SubMeta& m = L.meta[s];
@@ -718,6 +734,7 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
           fill[r]++;
         }
   });
+  ph("element dofs, row lists");
   // constraint rows over padded positions
   std::vector<int64_t> c_ptr(mp.c_ptr.size());
   std::vector<int32_t> c_pos(mp.c_col.size());
@@ -750,6 +767,7 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
     for (size_t t = 0; t < mp.sub_coarse.size(); ++t) cinv_occ[fill[mp.sub_coarse[t]]++] = (int64_t)t;
   }
 
+  ph("constraint, occurrence");
   // ---- upload
   LevelDev& d = L.d;
   d.n_sub = ns;
@@ -765,6 +783,7 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
   d.rc_ptr = A.upload(rc_ptr, st);
   d.rc_elem = A.upload(rc_elem, st);
   d.rc_a = A.upload(rc_a, st);
+  ph("uploads 1");
   {
     // CSR pattern of every K_i over padded positions, built on the device: per row the union of
     // the local positions of the elements containing it (ascending)
@@ -785,6 +804,7 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
     d.val = A.alloc<double>(row_ptr[L.n_vec]);
     launch_csr_pattern(d, L.n_vec, L.row_sub, max_len, nullptr, d.row_ptr, (int32_t*)d.col, st);
   }
+  ph("csr pattern (device)");
   d.c_ptr = A.upload(c_ptr, st);
   d.c_pos = A.upload(c_pos, st);
   d.c_val = A.upload(mp.c_val, st);
@@ -881,6 +901,7 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
   }
   (void)ts;
   d.status = h->d_status;
+  ph("uploads 2, tc items");
   // sweep tasks: block rows of all subdomains, interleaved by depth so that every task's
   // dependencies come earlier in the list
   // (bucketing variant: within every depth the subdomains with the longest chains come first, so
@@ -925,27 +946,39 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
         }
       }
   }
+  ph("sweep tasks");
   L.ctrl = A.alloc<int>(1);   // task counter of the sweeps
   {
     std::vector<int64_t> rl[3];
     std::vector<int32_t> cs;
+    std::vector<int64_t> o0(ns + 1, 0), o1(ns + 1, 0), oc(ns + 1, 0);
     for (int64_t s = 0; s < ns; ++s) {
-      const SubMeta& m = L.meta[s];
-      for (int r = 0; r < m.nI; ++r) rl[0].push_back(m.vec_off + r);
-      for (int r = 0; r < m.nG; ++r) rl[1].push_back(m.vec_off + (int64_t)m.nIb * NB + r);
-      for (int q = 0; q < m.nc; ++q) cs.push_back((int32_t)s);
+      o0[s + 1] = o0[s] + L.meta[s].nI;
+      o1[s + 1] = o1[s] + L.meta[s].nG;
+      oc[s + 1] = oc[s] + L.meta[s].nc;
     }
-    rl[2] = rl[0];
-    rl[2].insert(rl[2].end(), rl[1].begin(), rl[1].end());
+    rl[0].resize(o0[ns]);
+    rl[1].resize(o1[ns]);
+    rl[2].resize(o0[ns] + o1[ns]);
+    cs.resize(oc[ns]);
+    parallel_for(ns, [&](int64_t s) {
+      const SubMeta& m = L.meta[s];
+      for (int r = 0; r < m.nI; ++r) rl[0][o0[s] + r] = rl[2][o0[s] + r] = m.vec_off + r;
+      for (int r = 0; r < m.nG; ++r)
+        rl[1][o1[s] + r] = rl[2][o0[ns] + o1[s] + r] = m.vec_off + (int64_t)m.nIb * NB + r;
+      for (int q = 0; q < m.nc; ++q) cs[oc[s] + q] = (int32_t)s;
+    });
     for (int k = 0; k < 3; ++k) {
       L.nrows[k] = (int64_t)rl[k].size();
       L.rows[k] = A.upload(rl[k], st);
     }
     L.crow_sub = A.upload(cs, st);
   }
+  ph("row lists");
   L.slot_elem = A.upload(slot_elem, st);
   L.iface_dofs = A.upload(mp.iface_dofs, st);
   alloc_level_work(L, A, 1);
+  ph("work buffers");
 }
 
 // Element matrices of levels > 1 come from the previous level's K_Ci: segment copies.
@@ -1420,7 +1453,12 @@ void numeric_setup(bddc_handle_s* h) {
   for (size_t l = 0; l < h->lv.size(); ++l) {
     Level& L = h->lv[l];
     if (l == 0) {
-      if (h->physics == BDDC_STOKES)
+      if (h->ke_early) {   // computed in element order at the start of the set-up
+        launch_gather_elems(h->n_elems, h->npe * h->ndof, L.slot_elem, h->ke_elem, L.d.ke, st);
+        h->arena.free_one(h->ke_elem);
+        h->ke_elem = nullptr;
+        h->ke_early = false;
+      } else if (h->physics == BDDC_STOKES)
         launch_elem_q2q1(h->n_elems, h->d_coords, h->d_conn, h->d_coef, L.slot_elem, L.d.ke, st);
       else
         launch_elem_q1p1(h->physics, h->dim, h->npe == h->dim + 1, h->n_elems, h->d_coords, h->d_conn, h->d_coef,
@@ -1501,7 +1539,8 @@ void retain_host_heap() {
 #endif
 }
 
-void analysis(bddc_handle_s* h, const bddc_mesh* mesh, const bddc_partition* part) {
+void analysis(bddc_handle_s* h, const bddc_mesh* mesh, const bddc_partition* part,
+              const std::function<void()>& after_input = {}) {
   if (h->opts.retain_host_memory) retain_host_heap();
   const double t0 = now_ms();
   if (!mesh || !part) fail(BDDC_ERR_INVALID, "null mesh or partition");
@@ -1589,6 +1628,10 @@ void analysis(bddc_handle_s* h, const bddc_mesh* mesh, const bddc_partition* par
     tp = t;
   };
   phase("input", 0);
+  if (after_input) {   // device work that needs only the validated inputs (overlaps the analysis)
+    after_input();
+    phase("early device", 0);
+  }
   for (int l = 0; l + 1 < h->n_levels; ++l) {
     Level& L = h->lv[l];
     if (l == 0)
@@ -1617,6 +1660,26 @@ void analysis(bddc_handle_s* h, const bddc_mesh* mesh, const bddc_partition* par
   h->stats.analysis_ms = now_ms() - t0;
 }
 
+// The level-1 element matrices depend only on the validated inputs: upload the mesh and compute
+// them in element order on the handle's stream right away, so that the GPU works while the host
+// analyses the mesh and prepares the levels; numeric_setup gathers them into element slots.
+void early_device(bddc_handle_s* h) {
+  cudaStream_t st = h->st;
+  DevArena& A = h->arena;
+  h->d_coords = A.upload(h->coords, st);
+  h->d_conn = A.upload(h->conn, st);
+  h->d_coef = A.alloc<double>(h->n_elems);
+  ck(cudaMemcpyAsync(h->d_coef, h->coef.data(), sizeof(double) * h->n_elems, cudaMemcpyHostToDevice, st), "coef");
+  const int64_t ne = (int64_t)h->npe * h->ndof;
+  h->ke_elem = A.alloc<double>(h->n_elems * ne * ne);
+  if (h->physics == BDDC_STOKES)
+    launch_elem_q2q1(h->n_elems, h->d_coords, h->d_conn, h->d_coef, nullptr, h->ke_elem, st);
+  else
+    launch_elem_q1p1(h->physics, h->dim, h->npe == h->dim + 1, h->n_elems, h->d_coords, h->d_conn, h->d_coef, h->nu,
+                     nullptr, h->ke_elem, st);
+  h->ke_early = true;
+}
+
 void device_setup(bddc_handle_s* h) {
   const double t0 = now_ms();
   cudaStream_t st = h->st;
@@ -1628,9 +1691,11 @@ void device_setup(bddc_handle_s* h) {
     h->grid_max = 2 * std::max(1, sms);
   }
   h->d_status = A.alloc<int>(4);
-  h->d_coords = A.upload(h->coords, st);
-  h->d_conn = A.upload(h->conn, st);
-  h->d_coef = A.alloc<double>(h->n_elems);
+  if (!h->d_coords) {
+    h->d_coords = A.upload(h->coords, st);
+    h->d_conn = A.upload(h->conn, st);
+    h->d_coef = A.alloc<double>(h->n_elems);
+  }
   h->d_free_of_full = A.upload(h->free_of_full, st);
   for (size_t l = 0; l < h->lv.size(); ++l) {
     const double tl = now_ms(), u0 = A.upload_ms;
@@ -2475,7 +2540,7 @@ int bddc_setup(const bddc_mesh* mesh, const bddc_partition* part, unsigned const
     h->st = (cudaStream_t)stream;
     h->arena.st = h->st;
     try {
-      analysis(h, mesh, part);
+      analysis(h, mesh, part, [h]() { early_device(h); });
       device_setup(h);
       numeric_setup(h);
     } catch (...) {

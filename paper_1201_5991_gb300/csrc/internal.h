@@ -113,11 +113,15 @@ struct GradView {
 };
 
 // ---------------------------------------------------------------- assembly (assemble.cu)
-// Q1 boxes (simplex = 0, 2**dim nodes) or linear simplices (simplex = 1, dim + 1 nodes)
+// Q1 boxes (simplex = 0, 2**dim nodes) or linear simplices (simplex = 1, dim + 1 nodes); element
+// slot k takes element slot_elem[k] (slot_elem null: element k) and its matrix goes to ke + k ne^2
 void launch_elem_q1p1(int physics, int dim, int simplex, int64_t n_elems, const double* coords, const int32_t* conn,
                       const double* coef, double nu, const int32_t* slot_elem, double* ke, cudaStream_t st);
 void launch_elem_q2q1(int64_t n_elems, const double* coords, const int32_t* conn, const double* coef,
                       const int32_t* slot_elem, double* ke, cudaStream_t st);
+// ke + k ne^2 = ke_elem + slot_elem[k] ne^2 for every slot k (ne^2 doubles each)
+void launch_gather_elems(int64_t n_elems, int ne, const int32_t* slot_elem, const double* ke_elem, double* ke,
+                         cudaStream_t st);
 void launch_lift(int64_t n_free, int ne, const int64_t* lptr, const int32_t* lslot, const int32_t* la,
                  const double* ke, const double* ud, double* lift, cudaStream_t st);
 // CSR pattern of K_i (pass 1: cnt[row] = row length; pass 2: col at row_ptr)
