@@ -109,11 +109,24 @@ bool analyze_level(const LevelMesh& mesh, unsigned constraints, bool all_corners
     for (int64_t e = 0; e < ne; ++e) m.sub_elems[fill[mesh.part[e]]++] = e;
   }
   // subdomain -> nodes (sorted unique)
-  for (int64_t q = 0; q < (int64_t)mesh.en.size(); ++q)
-    if (mesh.en[q] < 0 || mesh.en[q] >= nn) {
-      *err = "node id out of range in element connectivity entry " + std::to_string(q);
+  {   // connectivity check in chunks on the host pool; the first bad entry is reported
+    constexpr int64_t kChunk = 65536;
+    const int64_t nq = (int64_t)mesh.en.size();
+    std::atomic<int64_t> bad{INT64_MAX};
+    parallel_range((nq + kChunk - 1) / kChunk, [&](int64_t b) {
+      for (int64_t q = b * kChunk; q < std::min(nq, (b + 1) * kChunk); ++q)
+        if (mesh.en[q] < 0 || mesh.en[q] >= nn) {
+          int64_t cur = bad.load();
+          while (q < cur && !bad.compare_exchange_weak(cur, q)) {
+          }
+          break;
+        }
+    });
+    if (bad.load() != INT64_MAX) {
+      *err = "node id out of range in element connectivity entry " + std::to_string(bad.load());
       return false;
     }
+  }
   std::vector<std::vector<int64_t>> sub_nodes(ns);
   std::vector<std::vector<char>> seen(kWorkers);   // per worker: node already listed
   parallel_range_worker(ns, [&](int64_t s, int w) {

@@ -84,6 +84,29 @@ cudaMemPool_t library_pool() {
   return pool;
 }
 
+// Host arrays that are written in full before use: default-initialised elements (no zero fill
+// of tens of MB on the set-up's critical path).
+template <typename T>
+struct NoInitAlloc : std::allocator<T> {
+  template <typename U>
+  struct rebind {
+    using other = NoInitAlloc<U>;
+  };
+  NoInitAlloc() = default;
+  template <typename U>
+  NoInitAlloc(const NoInitAlloc<U>&) {}
+  template <typename U>
+  void construct(U* p) {
+    ::new ((void*)p) U;
+  }
+  template <typename U, typename... A>
+  void construct(U* p, A&&... a) {
+    ::new ((void*)p) U(std::forward<A>(a)...);
+  }
+};
+template <typename T>
+using raw_vector = std::vector<T, NoInitAlloc<T>>;
+
 struct DevArena {
   std::vector<void*> ptrs;
   int64_t bytes = 0;
@@ -98,6 +121,19 @@ struct DevArena {
     ptrs.push_back(p);
     bytes += (int64_t)sizeof(T) * n;
     return (T*)p;
+  }
+  template <typename T>
+  T* upload(const raw_vector<T>& v, cudaStream_t st) {
+    return upload_n(v.data(), (int64_t)v.size(), st);
+  }
+  template <typename T>
+  T* upload_n(const T* v, int64_t n, cudaStream_t st) {
+    const double t0 = now_ms();
+    T* p = alloc<T>(n);
+    if (n > 0) ck(cudaMemcpyAsync(p, v, sizeof(T) * n, cudaMemcpyHostToDevice, st), "upload");
+    upload_ms += now_ms() - t0;
+    upload_bytes += (int64_t)(sizeof(T) * n);
+    return p;
   }
   template <typename T>
   T* upload(const std::vector<T>& v, cudaStream_t st) {
@@ -638,8 +674,8 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
   // element slots (subdomain order) and their padded local DOF positions; an element's matrix
   // DOFs are the DOFs of its nodes in node order
   const int64_t nel = ms.n_elems;
-  std::vector<int32_t> slot_elem(nel);
-  std::vector<int64_t> ke_off(nel + 1), ed_off(nel + 1);
+  raw_vector<int32_t> slot_elem(nel);
+  raw_vector<int64_t> ke_off(nel + 1), ed_off(nel + 1);
   // per subdomain (in parallel): the slots' element ids and DOF counts as offsets within the
   // subdomain; then the subdomains' totals are scanned and added
   std::vector<int64_t> sub_ed(ns + 1, 0), sub_ke(ns + 1, 0);
@@ -667,7 +703,7 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
       ke_off[k + 1] += sub_ke[s];
     }
   });
-  std::vector<int32_t> eldof(ed_off[nel]);
+  raw_vector<int32_t> eldof(ed_off[nel]);
   std::vector<int32_t> loc2iface(L.n_vec, -1), loc2glob(L.n_vec, -1), row_sub(L.n_vec);
   // row contributions (ascending element slot) per padded row: every row of subdomain s only
   // receives contributions from the slots of s, so counts and lists are built per subdomain
@@ -721,7 +757,7 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
       for (int64_t p = 0; p < (int64_t)m.Bc * NB; ++p) r[p] += tot[s];
     });
   }
-  std::vector<int32_t> rc_elem(rc_ptr[L.n_vec]), rc_a(rc_ptr[L.n_vec]);
+  raw_vector<int32_t> rc_elem(rc_ptr[L.n_vec]), rc_a(rc_ptr[L.n_vec]);
   parallel_for(ns, [&](int64_t s) {
     const SubMeta& m = L.meta[s];
     std::vector<int64_t> fill(rc_ptr.begin() + m.vec_off, rc_ptr.begin() + m.vec_off + (int64_t)m.Bc * NB);
@@ -1571,10 +1607,31 @@ void analysis(bddc_handle_s* h, const bddc_mesh* mesh, const bddc_partition* par
   h->coords.assign(mesh->coords, mesh->coords + h->n_nodes * h->dim);
   h->conn.assign(mesh->conn, mesh->conn + h->n_elems * h->npe);
   h->coef.assign(mesh->coef, mesh->coef + h->n_elems);
-  for (int64_t e = 0; e < h->n_elems; ++e)
-    if (!(h->coef[e] > 0.0)) fail(BDDC_ERR_INVALID, "coefficient must be positive (element " + std::to_string(e) + ")");
-  for (int32_t p : h->conn)
-    if (p < 0 || p >= h->n_nodes) fail(BDDC_ERR_INVALID, "connectivity references a missing node");
+  {   // element checks in chunks on the host pool; the first failing element is reported
+    constexpr int64_t kChunk = 8192;
+    std::atomic<int64_t> bad_coef{INT64_MAX}, bad_conn{INT64_MAX};
+    host_parallel((h->n_elems + kChunk - 1) / kChunk, [&](int64_t b, int) {
+      const int64_t e0 = b * kChunk, e1 = std::min(h->n_elems, e0 + kChunk);
+      for (int64_t e = e0; e < e1; ++e) {
+        if (!(h->coef[e] > 0.0)) {
+          int64_t cur = bad_coef.load();
+          while (e < cur && !bad_coef.compare_exchange_weak(cur, e)) {
+          }
+        }
+        for (int a = 0; a < h->npe; ++a) {
+          const int32_t p = h->conn[e * h->npe + a];
+          if (p < 0 || p >= h->n_nodes) {
+            int64_t cur = bad_conn.load();
+            while (e < cur && !bad_conn.compare_exchange_weak(cur, e)) {
+            }
+          }
+        }
+      }
+    });
+    if (bad_coef.load() != INT64_MAX)
+      fail(BDDC_ERR_INVALID, "coefficient must be positive (element " + std::to_string(bad_coef.load()) + ")");
+    if (bad_conn.load() != INT64_MAX) fail(BDDC_ERR_INVALID, "connectivity references a missing node");
+  }
   if (h->npe == h->dim + 1)   // linear simplices: a flat element has no inverse Jacobian
     for (int64_t e = 0; e < h->n_elems; ++e) {
       double J[3][3] = {{0}}, h2 = 0.0;

@@ -333,22 +333,36 @@ __global__ void __launch_bounds__(256) k_schur_symv_rows(LevelDev L, const float
     }
 }
 
-// y_j += sum_{i > j} part(i, j), i ascending; block (j, s, group)
+// y_j += sum_{i > j} part(i, j); block (j, s, group).  Every column's rows i are split into 4
+// interleaved segments (i = j + 1 + g, j + 5 + g, ...), whose partial sums are added in segment
+// order: a fixed order, the same for any number of columns per launch.
 template <int NR>
-__global__ void k_schur_symv_cols(LevelDev L, const int64_t* __restrict__ part_off, int64_t part_stride,
-                                  const float* __restrict__ part, float* __restrict__ y) {
+__global__ void __launch_bounds__(256) k_schur_symv_cols(LevelDev L, const int64_t* __restrict__ part_off,
+                                                         int64_t part_stride, const float* __restrict__ part,
+                                                         float* __restrict__ y) {
+  constexpr int G = 4;   // row segments
   const int s = blockIdx.y;
   const SubMeta m = L.meta[s];
   const int j = blockIdx.x;
   if (j >= m.nGb - 1) return;
+  __shared__ float ps[G][NR * NB];
   const int64_t c0q = (int64_t)blockIdx.z * NR;
-  for (int e = threadIdx.x; e < NR * NB; e += blockDim.x) {
+  for (int w = threadIdx.x; w < G * NR * NB; w += blockDim.x) {
+    const int e = w % (NR * NB), g = w / (NR * NB);
     const int q = e / NB, c = e % NB;
     const float* p = part + (c0q + q) * part_stride + part_off[s];
     float v = 0.f;
-    for (int i = j + 1; i < m.nGb; ++i) v += p[((int64_t)i * (i - 1) / 2 + j) * NB + c];
+    for (int i = j + 1 + g; i < m.nGb; i += G) v += p[((int64_t)i * (i - 1) / 2 + j) * NB + c];
+    ps[g][e] = v;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < NR * NB; e += blockDim.x) {
+    const int q = e / NB, c = e % NB;
+    float t = ps[0][e];
+#pragma unroll
+    for (int h = 1; h < G; ++h) t += ps[h][e];
     float* yv = y + (c0q + q) * L.n_vec + m.vec_off + (int64_t)m.nIb * NB + (int64_t)j * NB + c;
-    *yv = *yv + v;
+    *yv = *yv + t;
   }
 }
 
