@@ -775,11 +775,11 @@ void prepare_level(bddc_handle_s* h, Level& L, DevArena& A, cudaStream_t st) {
   std::vector<int64_t> c_ptr(mp.c_ptr.size());
   std::vector<int32_t> c_pos(mp.c_col.size());
   for (size_t i = 0; i < mp.c_ptr.size(); ++i) c_ptr[i] = mp.c_ptr[i];
-  for (int64_t s = 0; s < ns; ++s) {
+  parallel_for(ns, [&](int64_t s) {
     const SubMeta& m = L.meta[s];
     int64_t r0 = mp.sub_coarse_ptr[s], r1 = mp.sub_coarse_ptr[s + 1];
     for (int64_t t = mp.c_ptr[r0]; t < mp.c_ptr[r1]; ++t) c_pos[t] = (int32_t)pad_pos(m, mp.c_col[t]);
-  }
+  });
   // interface and coarse occurrence lists (ascending subdomain)
   std::vector<int64_t> iface_ptr(mp.n_iface + 1, 0), cinv_ptr(mp.n_coarse + 1, 0);
   for (int64_t p = 0; p < L.n_vec; ++p)
