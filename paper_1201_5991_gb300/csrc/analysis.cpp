@@ -428,23 +428,45 @@ bool analyze_level(const LevelMesh& mesh, unsigned constraints, bool all_corners
   }
   m.n_coarse = (int64_t)m.coarse_glob.size();
 
-  // global interface numbering
-  for (int64_t p = 0; p < nn; ++p)
-    if (iface[p])
-      for (int64_t q = mesh.nd_ptr[p]; q < mesh.nd_ptr[p + 1]; ++q)
-        if (mesh.nd_id[q] >= 0) m.iface_dofs.push_back(mesh.nd_id[q]);
+  // global interface numbering: the interface nodes' DOFs in node order (counted and written by
+  // node chunks on the host pool, offsets scanned in chunk order), then sorted by id
+  constexpr int64_t kNodeChunk = 4096;
+  const int64_t nchunk = (nn + kNodeChunk - 1) / kNodeChunk;
+  {
+    std::vector<int64_t> cnt(nchunk + 1, 0);
+    parallel_range(nchunk, [&](int64_t b) {
+      int64_t c = 0;
+      for (int64_t p = b * kNodeChunk; p < std::min(nn, (b + 1) * kNodeChunk); ++p)
+        if (iface[p])
+          for (int64_t q = mesh.nd_ptr[p]; q < mesh.nd_ptr[p + 1]; ++q) c += mesh.nd_id[q] >= 0;
+      cnt[b + 1] = c;
+    });
+    for (int64_t b = 0; b < nchunk; ++b) cnt[b + 1] += cnt[b];
+    m.iface_dofs.resize(cnt[nchunk]);
+    parallel_range(nchunk, [&](int64_t b) {
+      int64_t w = cnt[b];
+      for (int64_t p = b * kNodeChunk; p < std::min(nn, (b + 1) * kNodeChunk); ++p)
+        if (iface[p])
+          for (int64_t q = mesh.nd_ptr[p]; q < mesh.nd_ptr[p + 1]; ++q)
+            if (mesh.nd_id[q] >= 0) m.iface_dofs[w++] = mesh.nd_id[q];
+    });
+  }
   if (!std::is_sorted(m.iface_dofs.begin(), m.iface_dofs.end()))   // level 1 numbers DOFs node by node
     std::sort(m.iface_dofs.begin(), m.iface_dofs.end());
   m.n_iface = (int64_t)m.iface_dofs.size();
   std::vector<int64_t> iface_pos(mesh.n_dof, -1);
-  for (int64_t k = 0; k < m.n_iface; ++k) iface_pos[m.iface_dofs[k]] = k;
+  parallel_range((m.n_iface + kNodeChunk - 1) / kNodeChunk, [&](int64_t b) {
+    for (int64_t k = b * kNodeChunk; k < std::min(m.n_iface, (b + 1) * kNodeChunk); ++k) iface_pos[m.iface_dofs[k]] = k;
+  });
 
   // per-subdomain local orderings, weights, constraint rows (computed per subdomain in
   // parallel, then concatenated in subdomain order)
   std::vector<int64_t> dof_node(mesh.n_dof, -1);
-  for (int64_t p = 0; p < nn; ++p)
-    for (int64_t q = mesh.nd_ptr[p]; q < mesh.nd_ptr[p + 1]; ++q)
-      if (mesh.nd_id[q] >= 0) dof_node[mesh.nd_id[q]] = p;
+  parallel_range(nchunk, [&](int64_t b) {   // every DOF id belongs to one node: disjoint writes
+    for (int64_t p = b * kNodeChunk; p < std::min(nn, (b + 1) * kNodeChunk); ++p)
+      for (int64_t q = mesh.nd_ptr[p]; q < mesh.nd_ptr[p + 1]; ++q)
+        if (mesh.nd_id[q] >= 0) dof_node[mesh.nd_id[q]] = p;
+  });
   struct SubOut {
     std::vector<int64_t> interior, inter, coarse, crow_len, ccol;
   };
